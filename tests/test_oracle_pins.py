@@ -1,0 +1,373 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Every check here ties the oracle to something other than itself: closed forms
+of Eq. 1, a dense all-pairs form of Eq. 1, exact integer arithmetic, brute
+force over all set partitions, the connectivity guarantee of the Leiden
+method, hand-derived fixtures under tests/golden/, and published SplitMix64
+test vectors. They run on the CPU only.
+"""
+import ctypes
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from tests._graphs import ari, dense, q_dense, q_times_4m2_exact, random_graph_with_loops
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MODES = (oracle.SEQ, oracle.SYNC)
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _from_golden_edges(d):
+    e = d["edges"]
+    u = [x[0] for x in e]
+    v = [x[1] for x in e]
+    w = [x[2] if len(x) > 2 else 1.0 for x in e]
+    return gen.from_edges(d["n"], u, v, w)
+
+
+# ----------------------------------------------------------------- Eq. 1
+@pytest.mark.parametrize("k,r", [(3, 4), (5, 16), (8, 30), (4, 7)])
+def test_ring_of_cliques_closed_form(k, r):
+    """Clique partition of r cliques K_k in a ring: Q = L/(L+1) - 1/r, L = k(k-1)/2."""
+    g = gen.ring_of_cliques(k, r)
+    L = k * (k - 1) / 2
+    memb = np.repeat(np.arange(r), k).astype(np.int32)
+    assert abs(oracle.modularity(g, memb) - (L / (L + 1) - 1.0 / r)) < 1e-12
+
+
+def test_two_disjoint_cliques_and_complete_graph():
+    # two disjoint K5: each community holds half of all edge weight -> Q = 2*(1/2 - 1/4) = 1/2
+    u, v = [], []
+    for base in (0, 5):
+        for a in range(5):
+            for b in range(a + 1, 5):
+                u.append(base + a)
+                v.append(base + b)
+    g = gen.from_edges(10, u, v)
+    assert abs(oracle.modularity(g, np.array([0] * 5 + [1] * 5)) - 0.5) < 1e-15
+    # K_n as one community: Q = 1 - 1 = 0
+    kn = gen.gnp(9, 1.0, seed=1)
+    assert abs(oracle.modularity(kn, np.zeros(9, np.int32))) < 1e-15
+    # no edges: Q = 0 by the convention for m = 0
+    empty = gen.from_edges(4, [], [])
+    assert oracle.modularity(empty, np.arange(4)) == 0.0
+
+
+def test_golden_two_triangles():
+    d = _golden("two_triangles_bridge.json")
+    g = _from_golden_edges(d)
+    assert abs(oracle.modularity(g, np.array(d["optimal_partition"])) - d["optimal_q"]) < 1e-15
+    assert abs(oracle.modularity(g, np.zeros(6, np.int32)) - d["single_community_q"]) < 1e-15
+    q, best = oracle.brute_force(g)
+    assert abs(q - d["optimal_q"]) < 1e-15
+    assert ari(best, d["optimal_partition"]) == 1.0
+    for mode in MODES:
+        r = oracle.leiden(g, mode=mode)
+        assert r.status == 0
+        assert abs(r.modularity - d["optimal_q"]) < 1e-15
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.5, 2.0])
+@pytest.mark.parametrize("seed", range(6))
+def test_modularity_matches_all_pairs_form(seed, gamma):
+    """Community form of Eq. 1 equals the all-pairs form (self-loops included)."""
+    g = random_graph_with_loops(14, 0.3, seed)
+    rng = np.random.default_rng(seed)
+    memb = rng.integers(0, 4, g.n).astype(np.int32)
+    assert abs(oracle.modularity(g, memb, gamma) - q_dense(dense(g), memb, gamma)) < 1e-12
+
+
+# ----------------------------------------------------------------- Eq. 2
+def test_golden_delta_q():
+    d = _golden("delta_q_star.json")
+    g = _from_golden_edges(d)
+    memb = np.array(d["membership"], np.int32)
+    mv = d["move"]
+    assert abs(oracle.delta_modularity(g, memb, mv["vertex"], mv["to"]) - d["expected_dq"]) < 1e-15
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.7])
+@pytest.mark.parametrize("seed", range(8))
+def test_delta_modularity_against_recomputation(seed, gamma):
+    """Eq. 2 equals Q(after) - Q(before) recomputed from scratch (dense form)."""
+    g = random_graph_with_loops(12, 0.35, seed)
+    A = dense(g)
+    rng = np.random.default_rng(100 + seed)
+    memb = rng.integers(0, 5, g.n).astype(np.int32)
+    for _ in range(20):
+        i = int(rng.integers(0, g.n))
+        c = int(rng.integers(0, 5))
+        if c == memb[i]:
+            continue
+        after = memb.copy()
+        after[i] = c
+        want = q_dense(A, after, gamma) - q_dense(A, memb, gamma)
+        got = oracle.delta_modularity(g, memb, i, c, gamma)
+        assert abs(got - want) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_delta_key_is_exact(seed):
+    """The integer key difference equals 2m^2 * dQ exactly: 2*key = (2m)^2 dQ."""
+    g = random_graph_with_loops(11, 0.4, seed, wmax=9)
+    A = dense(g)
+    rng = np.random.default_rng(200 + seed)
+    memb = rng.integers(0, 4, g.n).astype(np.int32)
+    base = q_times_4m2_exact(A, memb)
+    for _ in range(20):
+        i = int(rng.integers(0, g.n))
+        c = int(rng.integers(0, 4))
+        if c == memb[i]:
+            continue
+        after = memb.copy()
+        after[i] = c
+        assert 2 * oracle.delta_key(g, memb, i, c) == q_times_4m2_exact(A, after) - base
+
+
+# ------------------------------------------------------------ brute force
+def test_brute_force_enumerates_bell_numbers():
+    """On a graph with no edges every partition scores 0 except through the
+    enumeration count, so check the optimum on K_4 minus an edge instead and
+    the restricted-growth enumeration on a planted 3-block graph."""
+    g = gen.from_edges(4, [0, 0, 1, 1, 2], [1, 2, 2, 3, 3])  # K4 minus edge 0-3
+    q, best = oracle.brute_force(g)
+    # the best is a single community or two pairs; compare with the dense form
+    assert abs(q - q_dense(dense(g), best)) < 1e-15
+    # planted: three disjoint triangles -> optimum 3*(1/3 - 1/9) = 2/3
+    u, v = [], []
+    for b in range(3):
+        for a, c in ((0, 1), (0, 2), (1, 2)):
+            u.append(3 * b + a)
+            v.append(3 * b + c)
+    h = gen.from_edges(9, u, v)
+    q, best = oracle.brute_force(h)
+    assert abs(q - 2.0 / 3.0) < 1e-15
+    assert ari(best, np.repeat(np.arange(3), 3)) == 1.0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_oracle_never_beats_brute_force(mode):
+    """Q_oracle <= Q_opt on seeded G(n, p) graphs with n <= 10 (a heuristic may fall short)."""
+    gaps = []
+    for seed in range(60):
+        n = 6 + seed % 5
+        g = gen.gnp(n, 0.45, seed=seed, wmax=3)
+        if g.nnz == 0:
+            continue
+        q_opt, _ = oracle.brute_force(g)
+        r = oracle.leiden(g, mode=mode)
+        assert r.status == 0
+        assert r.modularity <= q_opt + 1e-12
+        assert abs(r.modularity - oracle.modularity(g, r.membership)) < 1e-15
+        gaps.append(q_opt - r.modularity)
+    assert np.median(gaps) < 0.02
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_oracle_reaches_optimum_on_designated_family(mode):
+    """Equality with brute force on graphs with a clear optimum (n <= 12)."""
+    fams = [gen.ring_of_cliques(3, 4),                       # ring of triangles (12 vertices)
+            gen.from_edges(8, [0, 0, 0, 1, 1, 2, 4, 4, 4, 5, 5, 6, 3],
+                           [1, 2, 3, 2, 3, 3, 5, 6, 7, 6, 7, 7, 4]),  # barbell: two K4 + bridge
+            _from_golden_edges(_golden("two_triangles_bridge.json"))]
+    for g in fams:
+        q_opt, _ = oracle.brute_force(g)
+        r = oracle.leiden(g, mode=mode)
+        assert abs(r.modularity - q_opt) < 1e-12
+
+
+# ---------------------------------------------------------- whole method
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("k,r", [(5, 16), (8, 30)])
+def test_oracle_finds_the_cliques(mode, k, r):
+    g = gen.ring_of_cliques(k, r)
+    res = oracle.leiden(g, mode=mode)
+    assert res.status == 0
+    L = k * (k - 1) / 2
+    assert abs(res.modularity - (L / (L + 1) - 1.0 / r)) < 1e-12
+    assert np.array_equal(res.membership, np.repeat(np.arange(r), k))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_special_cases(mode):
+    # empty graph
+    r = oracle.leiden(gen.from_edges(0, [], []), mode=mode)
+    assert r.status == 0 and r.membership.size == 0 and r.modularity == 0.0
+    # vertices without edges: singletons, Q = 0
+    r = oracle.leiden(gen.from_edges(5, [], []), mode=mode)
+    assert r.status == 0 and np.array_equal(r.membership, np.arange(5)) and r.modularity == 0.0
+    # K_n: one community
+    r = oracle.leiden(gen.gnp(8, 1.0, seed=3), mode=mode)
+    assert np.array_equal(r.membership, np.zeros(8)) and abs(r.modularity) < 1e-15
+    # isolated vertices stay alone next to a triangle
+    g = gen.from_edges(5, [0, 0, 1], [1, 2, 2])
+    r = oracle.leiden(g, mode=mode)
+    assert np.array_equal(r.membership, [0, 0, 0, 1, 2])
+
+
+def test_sync_mode_validation():
+    g = gen.ring_of_cliques(4, 4)
+    w = g.weights.copy()
+    w[0] = w[1] = 0.5
+    bad = gen.CSR(g.n, g.offsets, g.indices, w)
+    assert oracle.leiden(bad, mode=oracle.SYNC).status == oracle.ERR_UNSUPPORTED
+    assert oracle.leiden(g, mode=oracle.SYNC, resolution=0.5).status == oracle.ERR_UNSUPPORTED
+    big = gen.CSR(g.n, g.offsets, g.indices, np.full_like(g.weights, 2.0 ** 26))
+    assert oracle.leiden(big, mode=oracle.SYNC).status == oracle.ERR_OVERFLOW
+    idx = g.indices.copy()
+    idx[3] = g.n
+    assert oracle.leiden(gen.CSR(g.n, g.offsets, idx, g.weights)).status == oracle.ERR_INVALID
+    assert oracle.leiden(g, mode=oracle.SEQ, resolution=0.5).status == 0
+
+
+def test_planted_partition_recovered():
+    """SBM workload: the planted 50 blocks are found (ARI >= 0.95) and Q is
+    close to the planted partition's modularity (~9.95/14.85 - 1/50)."""
+    g, blocks = gen.sbm(10_000, 50, 0.05, 0.0005, seed=1, return_blocks=True)
+    q_planted = oracle.modularity(g, blocks)
+    assert abs(q_planted - (9.95 / 14.85 - 1 / 50)) < 0.01
+    for mode in MODES:
+        r = oracle.leiden(g, mode=mode)
+        assert r.status == 0
+        assert ari(r.membership, blocks) >= 0.95
+        assert r.modularity >= q_planted - 0.005
+
+
+# ------------------------------------------------------------- Algorithm 5
+def test_disconnected_counter():
+    g = gen.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5])  # two paths 0-1-2 and 3-4-5
+    assert oracle.disconnected(g, np.array([0, 0, 0, 3, 3, 3]))[0] == 0
+    k, flags = oracle.disconnected(g, np.array([0, 0, 0, 0, 3, 3]))  # vertex 3 cut off from 0..2
+    assert k == 1 and flags[0] == 1 and flags[3] == 0
+    assert oracle.disconnected(g, np.array([0, 1, 0, 3, 4, 3]))[0] == 2
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_every_community_connected(mode):
+    graphs = [gen.sbm_workload(), gen.road(150), gen.rmat(12, 16), gen.gnp(300, 0.02, seed=5, wmax=4)]
+    for g in graphs:
+        r = oracle.leiden(g, mode=mode, trace=True)
+        assert r.status == 0
+        assert oracle.disconnected(g, r.membership)[0] == 0
+        # refinement invariant (pass 0): every refined community lies inside one
+        # local-moving community and is connected
+        t0 = r.trace[0]
+        bound, refined = t0[oracle.T_MOVE], t0[oracle.T_REFINE]
+        for c in np.unique(refined):
+            assert np.unique(bound[refined == c]).size == 1
+        assert oracle.disconnected(g, refined)[0] == 0
+
+
+# ------------------------------------------------------------- Algorithm 4
+def test_golden_aggregate():
+    d = _golden("path4_aggregate.json")
+    g = _from_golden_edges(d)
+    off, deg, idx, w = oracle.aggregate(g.n, g.offsets, np.diff(g.offsets), g.indices, g.weights,
+                                        np.array(d["membership"]), 2)
+    assert off.tolist() == d["expected_offsets"]
+    assert deg.tolist() == d["expected_degree"]
+    for c, row in enumerate(d["expected_rows"]):
+        got = [[int(idx[e]), float(w[e])] for e in range(off[c], off[c] + deg[c])]
+        assert got == row
+    K = [float(w[off[c]:off[c] + deg[c]].sum()) for c in range(2)]
+    assert K == d["expected_K"]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_aggregation_invariants(seed):
+    g = random_graph_with_loops(40, 0.12, seed, wmax=7)
+    rng = np.random.default_rng(seed)
+    ncomm = 7
+    memb = rng.permutation(np.arange(g.n) % ncomm).astype(np.int32)
+    deg = np.diff(g.offsets).astype(np.int32)
+    off2, deg2, idx2, w2 = oracle.aggregate(g.n, g.offsets, deg, g.indices, g.weights, memb, ncomm)
+    # total weight (2m) preserved; K'' = sum of member K
+    real = np.concatenate([np.arange(off2[c], off2[c] + deg2[c]) for c in range(ncomm)])
+    assert w2[real].sum() == g.weights.astype(np.float64).sum()
+    K = np.bincount(np.repeat(np.arange(g.n), deg), weights=g.weights.astype(np.float64), minlength=g.n)
+    K2 = np.array([w2[off2[c]:off2[c] + deg2[c]].sum() for c in range(ncomm)])
+    assert np.array_equal(K2, np.bincount(memb, weights=K, minlength=ncomm))
+    # row capacity = communityTotalDegree; rows sorted, unique, symmetric weights
+    assert np.array_equal(np.diff(off2), np.bincount(memb, weights=deg, minlength=ncomm).astype(np.int64))
+    W = np.zeros((ncomm, ncomm))
+    for c in range(ncomm):
+        row = idx2[off2[c]:off2[c] + deg2[c]]
+        assert np.all(np.diff(row) > 0)
+        W[c, row] = w2[off2[c]:off2[c] + deg2[c]]
+    assert np.array_equal(W, W.T)
+    # Q(G'', L) == Q(G, L o memb) for any partition L of the super-vertices
+    for _ in range(5):
+        L = rng.integers(0, 3, ncomm).astype(np.int32)
+        q2 = oracle.modularity_holey(ncomm, off2, deg2, idx2, w2, L)
+        assert abs(q2 - oracle.modularity(g, L[memb])) < 1e-12
+    # community-vertex CSR is a permutation grouped by label
+    coff, members = oracle.community_vertices(memb, ncomm)
+    assert np.array_equal(np.sort(members), np.arange(g.n))
+    for c in range(ncomm):
+        assert np.all(memb[members[coff[c]:coff[c + 1]]] == c)
+
+
+# ---------------------------------------------------- local optimality
+@pytest.mark.parametrize("seed", range(4))
+def test_local_moving_reaches_local_optimum(seed):
+    """SEQ, tau = 0, no pruning, one pass: once a sweep moves nobody no single
+    move has dQ > 0 (checked against the dense all-pairs form of Eq. 1)."""
+    g = gen.gnp(60, 0.08, seed=seed, wmax=3)
+    r = oracle.leiden(g, mode=oracle.SEQ, tolerance=0.0, max_passes=1, max_iterations=10_000,
+                      flags=oracle.NO_PRUNE, trace=True)
+    assert r.trace[0][oracle.T_COUNTS][1] < 10_000
+    memb = r.trace[0][oracle.T_MOVE]
+    A = dense(g)
+    q0 = q_dense(A, memb)
+    for i in range(g.n):
+        for c in set(memb[g.indices[g.offsets[i]:g.offsets[i + 1]]]) - {memb[i]}:
+            after = memb.copy()
+            after[i] = c
+            assert q_dense(A, after) - q0 <= 1e-12
+
+
+# ----------------------------------------------------------- schedule (S0)
+def test_splitmix64_reference_vectors():
+    """Published SplitMix64 outputs (Vigna's reference splitmix64.c)."""
+    lib = oracle._lib()
+    lib.og_splitmix64_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    lib.og_splitmix64_at.restype = ctypes.c_uint64
+    assert [lib.og_splitmix64_at(1234567, i) for i in range(5)] == [
+        6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+        16408922859458223821]
+    assert lib.og_splitmix64_at(0, 0) == 0xE220A8397B1DCDAF
+
+
+@pytest.mark.parametrize("L,B", [(32, 16), (4, 3), (1, 1)])
+def test_schedule_properties(L, B):
+    g = gen.road(60)
+    deg = np.diff(g.offsets).astype(np.int32)
+    step, used = oracle.schedule(g.n, g.offsets, deg, g.indices, 7, L, B)
+    assert used == step.max() + 1 and used <= L - 1 + B
+    rows = np.repeat(np.arange(g.n), deg)
+    same = step[rows] == step[g.indices]
+    lower = step[rows] < L - 1
+    # below the cap no edge joins two vertices of the same step
+    assert not np.any(same & lower & (rows != g.indices))
+    # longest-path property: a vertex in layer k >= 1 (below the cap) has a neighbour in layer k-1
+    for v in np.nonzero((step > 0) & (step < L - 1))[0][:500]:
+        nb = g.indices[g.offsets[v]:g.offsets[v + 1]]
+        assert np.any(step[nb] == step[v] - 1)
+
+
+def test_ties_go_to_the_lowest_community_id():
+    """Path 1-0-2: vertex 0 sees communities 1 and 2 with equal dQ (Eq. 2 is
+    symmetric in them) and must take community 1 (reading R2); vertex 2 then
+    joins community 1 as well."""
+    g = gen.from_edges(3, [0, 0], [1, 2])
+    r = oracle.leiden(g, mode=oracle.SEQ, max_passes=1, trace=True)
+    assert r.trace[0][oracle.T_MOVE].tolist() == [1, 1, 1]
