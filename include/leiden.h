@@ -1,0 +1,149 @@
+/*
+ * leiden.h -- C ABI of the GB300 (sm_103a) Leiden community-detection library.
+ *
+ * The library runs the parallel Leiden method of "GVE-Leiden: Fast Leiden
+ * Algorithm for Community Detection in Shared Memory Setting" (Sahu, arXiv
+ * 2312.13936) on one GPU: the pass loop of Algorithm 1 with local-moving
+ * (Algorithm 2), refinement (Algorithm 3) and aggregation (Algorithm 4),
+ * threshold scaling and the aggregation-tolerance stop. Every step runs in
+ * the library's own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a leiden_status and never aborts the process.
+ *     leiden_last_error() gives a one-line description of the last failure
+ *     on the calling thread.
+ *   - Graphs are undirected and weighted (paper, Section 3 "Preliminaries":
+ *     w_ij = w_ji). They are passed as a symmetric CSR: offsets[n+1] (int64,
+ *     offsets[0] = 0, non-decreasing), indices[nnz] (int32 in [0, n)),
+ *     weights[nnz] (float32, finite, >= 0; NULL means unit weights). Each
+ *     undirected edge appears once in each direction; a self-loop is one
+ *     entry and counts once in K_i and in 2m.
+ *   - `where` tells where a pointer lives: LEIDEN_HOST or LEIDEN_DEVICE (a
+ *     pointer into memory of the current CUDA device, e.g.
+ *     torch.Tensor.data_ptr()).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). All work of a call is ordered on that stream.
+ *   - Inputs are borrowed for the duration of the call; outputs are owned by
+ *     the caller; a leiden_graph_t owns its device copies and workspace.
+ *   - A handle is not thread-safe; different handles may run concurrently on
+ *     different streams.
+ */
+#ifndef LEIDEN_GB300_H
+#define LEIDEN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LEIDEN_OK = 0,
+    LEIDEN_ERR_INVALID = -1,       /* bad argument or malformed CSR */
+    LEIDEN_ERR_NOT_SYMMETRIC = -2, /* validation found w_ij != w_ji */
+    LEIDEN_ERR_OOM = -3,           /* device allocation failed */
+    LEIDEN_ERR_CUDA = -4,          /* a CUDA runtime call or kernel failed */
+    LEIDEN_ERR_TIMEOUT = -5,       /* a bounded device loop gave up */
+    LEIDEN_ERR_UNSUPPORTED = -6,   /* mode/parameter combination not supported */
+    LEIDEN_ERR_OVERFLOW = -7       /* exact arithmetic would overflow */
+} leiden_status;
+
+enum { LEIDEN_HOST = 0, LEIDEN_DEVICE = 1 };
+
+/* mode: LEIDEN_ASYNC applies local-moving moves inside the kernels as soon
+ * as they are decided (the paper's asynchronous execution, Section 4.1);
+ * LEIDEN_DETERMINISTIC evaluates each schedule step against the state at
+ * the start of the step and decides in exact int64 arithmetic, so results
+ * are reproducible bit for bit (requires integer weights, resolution 1 and
+ * 2m < 2^31). */
+enum { LEIDEN_ASYNC = 0, LEIDEN_DETERMINISTIC = 1 };
+
+/* flags */
+enum {
+    LEIDEN_FLAG_VALIDATE = 1u,            /* check symmetry and weights on device */
+    LEIDEN_FLAG_REFINE_SINGLE_SWEEP = 2u, /* one refinement sweep, as Algorithm 3 prints it */
+    LEIDEN_FLAG_TRACE = 4u                /* keep per-pass intermediate results (leiden_trace_get) */
+};
+
+typedef struct {
+    double resolution;            /* gamma: multiplies the null-model term of Eq. 1 and Eq. 2; default 1 */
+    double tolerance;             /* tau: initial per-iteration tolerance (Algorithm 2); default 0.01 */
+    double aggregation_tolerance; /* tau_agg: stop when |Gamma|/|V'| exceeds it (Algorithm 1); default 0.8 */
+    double tolerance_drop;        /* TOLERANCE_DROP: tau /= drop after each pass (Algorithm 1); default 10 */
+    int32_t max_iterations;       /* MAX_ITERATIONS per phase (Algorithm 2); default 20 */
+    int32_t max_passes;           /* MAX_PASSES (Algorithm 1; not given in the paper); default 10 */
+    int32_t mode;                 /* LEIDEN_ASYNC or LEIDEN_DETERMINISTIC */
+    uint32_t flags;               /* LEIDEN_FLAG_* */
+    int32_t schedule_layers;      /* L: priority layers of the sweep schedule; default 32 */
+    int32_t schedule_buckets;     /* B: priority buckets after the last layer; default 16 */
+    uint64_t seed;                /* seed of the schedule's vertex priorities; default 0 */
+} leiden_params;
+
+typedef struct {
+    int32_t passes;               /* passes executed */
+    int32_t move_iterations;      /* local-moving sweeps, all passes */
+    int32_t refine_iterations;    /* refinement sweeps, all passes */
+    int32_t reserved;
+    int64_t communities;          /* communities in the returned membership */
+    double modularity;            /* Eq. 1 of the result on the input graph */
+    double ms_total;              /* device time of leiden_run (CUDA events) */
+    double ms_move, ms_refine, ms_aggregate, ms_other; /* per-phase device time */
+    int64_t kernel_launches;      /* kernels launched by the call */
+} leiden_stats;
+
+typedef struct leiden_graph_s *leiden_graph_t;
+
+/* Fill *p with the defaults listed above. */
+void leiden_params_default(leiden_params *p);
+
+/* Create a handle from a symmetric CSR (Section 3 graph model). The arrays
+ * are copied into device memory owned by the handle (from host or device
+ * memory, per `where`) and a workspace sized for the graph is reserved.
+ * n >= 0, nnz = offsets[n]; weights may be NULL (unit weights). With
+ * `validate` != 0 the CSR is checked on the device (offsets monotone,
+ * indices in range, weights finite and >= 0, w_ij == w_ji); failures return
+ * LEIDEN_ERR_INVALID or LEIDEN_ERR_NOT_SYMMETRIC and *out stays NULL. */
+leiden_status leiden_create(leiden_graph_t *out, int64_t n, int64_t nnz, const int64_t *offsets,
+                            const int32_t *indices, const float *weights, int32_t where, int32_t validate,
+                            void *stream);
+
+/* Run Algorithm 1 on the handle's graph. membership (n int32, host or device
+ * per `where`) receives canonical labels: community ids are ranks of each
+ * community's smallest vertex id. *modularity (nullable) receives Eq. 1 of
+ * the result on the input graph; *stats (nullable) the run statistics. The
+ * call returns after the results are written (it synchronises `stream`). */
+leiden_status leiden_run(leiden_graph_t g, const leiden_params *p, int32_t *membership, int32_t where,
+                         double *modularity, leiden_stats *stats);
+
+/* Release the handle and its device memory. NULL is accepted. */
+leiden_status leiden_destroy(leiden_graph_t g);
+
+/* Modularity (Eq. 1 with resolution gamma) of `membership` (n labels in
+ * [0, n)) on a symmetric CSR. All pointers are device pointers; the result
+ * is written to *q_out (host). Device scratch of 16 bytes per vertex is
+ * taken from the stream-ordered allocator for the duration of the call. */
+leiden_status leiden_modularity(int64_t n, const int64_t *offsets, const int32_t *indices, const float *weights,
+                                const int32_t *membership, double gamma, void *stream, double *q_out);
+
+/* Per-pass trace of the last leiden_run made with LEIDEN_FLAG_TRACE. what:
+ * 1 C' at the start of local-moving (int32[n']), 2 C' after local-moving
+ * (int32[n']), 3 C' after refinement (int32[n']), 4 counts (int64[4]: n',
+ * l_i, l_j, |Gamma|), 5 renumbered C' (int32[n']), 6/7/8/9 the aggregated
+ * holey CSR (offsets int64[|Gamma|+1], fill int32[|Gamma|], targets
+ * int32[cap], weights float64[cap]; entries past a row's fill are
+ * undefined), 10 dendrogram C after the lookup (int32[n0]). With dst NULL,
+ * *count receives the element count; otherwise up to *count elements are
+ * copied to host memory dst. Returns LEIDEN_ERR_INVALID if the pass or item
+ * was not recorded. */
+leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, void *dst, int64_t *count);
+
+/* Human-readable name of a status code. */
+const char *leiden_status_string(int32_t status);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *leiden_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEIDEN_GB300_H */

@@ -1,0 +1,214 @@
+"""GB300 (sm_103a) Leiden community detection: Python binding of the C ABI.
+
+The binding only marshals arguments to ``libleiden_gb300.so`` (declared in
+``include/leiden.h``); every step of the method runs in the library's CUDA
+kernels. PyTorch provides device memory and streams. There is no CPU
+fallback: if the library is missing, every call raises.
+
+Functions carry the C names (``leiden_create``, ``leiden_run``, ...);
+``Leiden`` is a small convenience wrapper around a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "LEIDEN_HOST", "LEIDEN_DEVICE", "LEIDEN_ASYNC", "LEIDEN_DETERMINISTIC", "FLAG_VALIDATE",
+    "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "LeidenError", "Params", "Stats", "library", "leiden_params_default",
+    "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity", "leiden_trace_get",
+    "leiden_status_string", "leiden_last_error", "Leiden", "modularity",
+]
+
+LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
+LEIDEN_ASYNC, LEIDEN_DETERMINISTIC = 0, 1
+FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE = 1, 2, 4
+TRACE_INIT, TRACE_MOVE, TRACE_REFINE, TRACE_COUNTS, TRACE_RENUMBER = 1, 2, 3, 4, 5
+TRACE_AGG_OFF, TRACE_AGG_DEG, TRACE_AGG_IDX, TRACE_AGG_W, TRACE_DENDRO = 6, 7, 8, 9, 10
+_TRACE_DTYPE = {1: np.int32, 2: np.int32, 3: np.int32, 4: np.int64, 5: np.int32, 6: np.int64, 7: np.int32,
+                8: np.int32, 9: np.float64, 10: np.int32}
+
+
+class LeidenError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} [{status}]")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("resolution", ctypes.c_double), ("tolerance", ctypes.c_double),
+                ("aggregation_tolerance", ctypes.c_double), ("tolerance_drop", ctypes.c_double),
+                ("max_iterations", ctypes.c_int32), ("max_passes", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("schedule_layers", ctypes.c_int32),
+                ("schedule_buckets", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_int32), ("move_iterations", ctypes.c_int32),
+                ("refine_iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("communities", ctypes.c_int64), ("modularity", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_move", ctypes.c_double), ("ms_refine", ctypes.c_double), ("ms_aggregate", ctypes.c_double),
+                ("ms_other", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_LIB = None
+_VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+
+
+def library(build_if_missing: bool = False) -> ctypes.CDLL:
+    """The loaded libleiden_gb300.so (raises if it is not built)."""
+    global _LIB
+    if _LIB is None:
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"{_build.LIB} is not built; run __graft_entry__.build() (needs nvcc)")
+        lib = ctypes.CDLL(_build.LIB)
+        lib.leiden_params_default.argtypes = [ctypes.POINTER(Params)]
+        lib.leiden_params_default.restype = None
+        lib.leiden_create.argtypes = [ctypes.POINTER(_VP), _I64, _I64, _VP, _VP, _VP, _I32, _I32, _VP]
+        lib.leiden_run.argtypes = [_VP, ctypes.POINTER(Params), _VP, _I32, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(Stats)]
+        lib.leiden_destroy.argtypes = [_VP]
+        lib.leiden_modularity.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.c_double, _VP,
+                                          ctypes.POINTER(ctypes.c_double)]
+        lib.leiden_trace_get.argtypes = [_VP, _I32, _I32, _VP, ctypes.POINTER(_I64)]
+        for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
+                  lib.leiden_trace_get):
+            f.restype = ctypes.c_int
+        lib.leiden_status_string.argtypes = [_I32]
+        lib.leiden_status_string.restype = ctypes.c_char_p
+        lib.leiden_last_error.argtypes = []
+        lib.leiden_last_error.restype = ctypes.c_char_p
+        _LIB = lib
+    return _LIB
+
+
+def _check(rc: int):
+    if rc != 0:
+        lib = library()
+        raise LeidenError(rc, f"{lib.leiden_status_string(rc).decode()}: {lib.leiden_last_error().decode()}")
+
+
+def leiden_status_string(status: int) -> str:
+    return library().leiden_status_string(status).decode()
+
+
+def leiden_last_error() -> str:
+    return library().leiden_last_error().decode()
+
+
+def leiden_params_default() -> Params:
+    p = Params()
+    library().leiden_params_default(ctypes.byref(p))
+    return p
+
+
+def leiden_create(n, nnz, offsets_ptr, indices_ptr, weights_ptr, where, validate, stream) -> int:
+    h = _VP()
+    _check(library().leiden_create(ctypes.byref(h), n, nnz, offsets_ptr, indices_ptr, weights_ptr, where,
+                                   validate, stream))
+    return h.value
+
+
+def leiden_run(handle, params: Params, membership_ptr, where):
+    q = ctypes.c_double(0.0)
+    st = Stats()
+    _check(library().leiden_run(handle, ctypes.byref(params), membership_ptr, where, ctypes.byref(q),
+                                ctypes.byref(st)))
+    return q.value, st
+
+
+def leiden_destroy(handle) -> None:
+    _check(library().leiden_destroy(handle))
+
+
+def leiden_modularity(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma, stream) -> float:
+    q = ctypes.c_double(0.0)
+    _check(library().leiden_modularity(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma, stream,
+                                       ctypes.byref(q)))
+    return q.value
+
+
+def leiden_trace_get(handle, pass_: int, what: int):
+    cnt = _I64(0)
+    _check(library().leiden_trace_get(handle, pass_, what, None, ctypes.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), dtype=_TRACE_DTYPE[what])
+    _check(library().leiden_trace_get(handle, pass_, what, out.ctypes.data_as(_VP), ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _VP(s.cuda_stream)
+
+
+def _ptr(t):
+    return _VP(t.data_ptr()) if t is not None else _VP(0)
+
+
+class Leiden:
+    """A graph resident on the GPU, ready for repeated leiden_run calls.
+
+    ``offsets``/``indices``/``weights`` are a symmetric CSR, as numpy arrays
+    or torch tensors (CPU or CUDA). ``run`` returns (membership, modularity,
+    stats) with membership a torch.int32 CUDA tensor of canonical labels.
+    """
+
+    def __init__(self, offsets, indices, weights=None, validate: bool = False, stream=None):
+        import torch
+        self._torch = torch
+        self.stream = stream
+        dev = torch.device("cuda", torch.cuda.current_device())
+        off = torch.as_tensor(offsets, dtype=torch.int64).to(dev).contiguous()
+        idx = torch.as_tensor(indices, dtype=torch.int32).to(dev).contiguous()
+        w = None if weights is None else torch.as_tensor(weights, dtype=torch.float32).to(dev).contiguous()
+        self.n = int(off.numel() - 1)
+        self.nnz = int(idx.numel())
+        self.handle = leiden_create(self.n, self.nnz, _ptr(off), _ptr(idx), _ptr(w), LEIDEN_DEVICE,
+                                    int(validate), _stream_ptr(stream))
+        self.device = dev
+        self._input = (off, idx, w)  # kept for modularity checks
+
+    def run(self, mode: int = LEIDEN_ASYNC, trace: bool = False, **kw):
+        p = leiden_params_default()
+        p.mode = mode
+        if trace:
+            p.flags |= FLAG_TRACE
+        for k, v in kw.items():
+            if k == "flags":
+                p.flags |= int(v)
+            else:
+                setattr(p, k, v)
+        memb = self._torch.empty(max(self.n, 1), dtype=self._torch.int32, device=self.device)
+        q, st = leiden_run(self.handle, p, _ptr(memb), LEIDEN_DEVICE)
+        return memb[:self.n], q, st
+
+    def trace(self, pass_: int, what: int):
+        return leiden_trace_get(self.handle, pass_, what)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            leiden_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def modularity(offsets, indices, weights, membership, resolution: float = 1.0, stream=None) -> float:
+    """Eq. 1 of ``membership`` (labels in [0, n)) on a CSR held in CUDA tensors."""
+    n = int(offsets.numel() - 1)
+    return leiden_modularity(n, _ptr(offsets), _ptr(indices), _ptr(weights), _ptr(membership), resolution,
+                             _stream_ptr(stream))

@@ -1,0 +1,108 @@
+// extern "C" entry points declared in include/leiden.h.
+#include <new>
+
+#include "engine.h"
+
+struct leiden_graph_s {
+    lgb::Handle h;
+};
+
+extern "C" {
+
+void leiden_params_default(leiden_params *p) {
+    if (!p) return;
+    p->resolution = 1.0;
+    p->tolerance = 0.01;
+    p->aggregation_tolerance = 0.8;
+    p->tolerance_drop = 10.0;
+    p->max_iterations = 20;
+    p->max_passes = 10;
+    p->mode = LEIDEN_ASYNC;
+    p->flags = 0;
+    p->schedule_layers = 32;
+    p->schedule_buckets = 16;
+    p->seed = 0;
+}
+
+leiden_status leiden_create(leiden_graph_t *out, int64_t n, int64_t nnz, const int64_t *offsets,
+                            const int32_t *indices, const float *weights, int32_t where, int32_t validate,
+                            void *stream) {
+    if (!out) {
+        lgb::set_last_error("out is NULL");
+        return LEIDEN_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (n < 0 || n > 0x7fffffffLL || nnz < 0 || !offsets || (nnz > 0 && !indices) ||
+        (where != LEIDEN_HOST && where != LEIDEN_DEVICE)) {
+        lgb::set_last_error("invalid CSR arguments");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (where == LEIDEN_HOST) {  // host arrays are checked here, device arrays by validate
+        if (offsets[0] != 0 || offsets[n] != nnz) {
+            lgb::set_last_error("offsets[0] must be 0 and offsets[n] must equal nnz");
+            return LEIDEN_ERR_INVALID;
+        }
+    }
+    leiden_graph_s *g = new (std::nothrow) leiden_graph_s;
+    if (!g) {
+        lgb::set_last_error("host allocation failed");
+        return LEIDEN_ERR_OOM;
+    }
+    leiden_status st = g->h.create(n, nnz, offsets, indices, weights, where, validate, stream);
+    if (st != LEIDEN_OK) {
+        delete g;
+        return st;
+    }
+    *out = g;
+    return LEIDEN_OK;
+}
+
+leiden_status leiden_run(leiden_graph_t g, const leiden_params *p, int32_t *membership, int32_t where,
+                         double *modularity, leiden_stats *stats) {
+    if (!g || !p) {
+        lgb::set_last_error("NULL handle or params");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (where != LEIDEN_HOST && where != LEIDEN_DEVICE) {
+        lgb::set_last_error("invalid where");
+        return LEIDEN_ERR_INVALID;
+    }
+    return g->h.run(*p, membership, where, modularity, stats);
+}
+
+leiden_status leiden_destroy(leiden_graph_t g) {
+    delete g;
+    return LEIDEN_OK;
+}
+
+leiden_status leiden_modularity(int64_t n, const int64_t *offsets, const int32_t *indices, const float *weights,
+                                const int32_t *membership, double gamma, void *stream, double *q_out) {
+    return lgb::modularity_device(n, offsets, indices, weights, membership, gamma,
+                                  static_cast<cudaStream_t>(stream), q_out);
+}
+
+leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, void *dst, int64_t *count) {
+    if (!g) {
+        lgb::set_last_error("NULL handle");
+        return LEIDEN_ERR_INVALID;
+    }
+    return g->h.trace_get(pass, what, dst, count);
+}
+
+const char *leiden_status_string(int32_t s) {
+    switch (s) {
+        case LEIDEN_OK: return "LEIDEN_OK";
+        case LEIDEN_ERR_INVALID: return "LEIDEN_ERR_INVALID";
+        case LEIDEN_ERR_NOT_SYMMETRIC: return "LEIDEN_ERR_NOT_SYMMETRIC";
+        case LEIDEN_ERR_OOM: return "LEIDEN_ERR_OOM";
+        case LEIDEN_ERR_CUDA: return "LEIDEN_ERR_CUDA";
+        case LEIDEN_ERR_TIMEOUT: return "LEIDEN_ERR_TIMEOUT";
+        case LEIDEN_ERR_UNSUPPORTED: return "LEIDEN_ERR_UNSUPPORTED";
+        case LEIDEN_ERR_OVERFLOW: return "LEIDEN_ERR_OVERFLOW";
+        default: return "LEIDEN_ERR_UNKNOWN";
+    }
+}
+
+const char *leiden_last_error(void) { return lgb::last_error(); }
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Device-side building blocks shared by the Leiden kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lgb {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Accumulation policies. Deterministic mode decides moves in exact int64
+// arithmetic on integer weights; asynchronous mode accumulates in fp64 (the
+// paper's hashtable precision, Section 5.1.2 "Configuration").
+struct Det {
+    using acc = long long;
+    static constexpr bool det = true;
+};
+struct Async {
+    using acc = double;
+    static constexpr bool det = false;
+};
+
+template <class A> struct AccLimits;
+template <> struct AccLimits<long long> {
+    __device__ static constexpr long long lowest() { return (long long)0x8000000000000000ULL; }
+};
+template <> struct AccLimits<double> {
+    __device__ static double lowest() { return __longlong_as_double(0xfff0000000000000LL); }  // -inf
+};
+
+template <class A, class W> __device__ __forceinline__ A wconv(W w) { return (A)w; }
+
+__device__ __forceinline__ void atomic_add_acc(long long *p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+__device__ __forceinline__ void atomic_add_acc(double *p, double v) { atomicAdd(p, v); }
+
+// Σ reads: the async mode sees concurrent atomics from other SMs, so it reads
+// through L2 (ld.global.cg); deterministic mode reads a snapshot.
+template <class A> __device__ __forceinline__ A load_cg(const A *p) { return __ldcg(p); }
+
+// Eq. 2 scaled by 2m^2: key(c) = 2m*K_{i->c} - gamma*K_i*Sigma_c. The vertex
+// moves to c* iff key(c*) > key_stay = 2m*K_{i->d} - gamma*K_i*(Sigma_d - K_i).
+__device__ __forceinline__ long long move_key(long long two_m, long long kic, long long ki, long long sc, double) {
+    return two_m * kic - ki * sc;
+}
+__device__ __forceinline__ double move_key(double two_m, double kic, double ki, double sc, double gamma) {
+    return two_m * kic - gamma * ki * sc;
+}
+__device__ __forceinline__ long long stay_key(long long two_m, long long kid, long long ki, long long sd, double) {
+    return two_m * kid - ki * (sd - ki);
+}
+__device__ __forceinline__ double stay_key(double two_m, double kid, double ki, double sd, double gamma) {
+    return two_m * kid - gamma * ki * (sd - ki);
+}
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number i+1 of the
+// generator whose state starts at s. Vertex priorities of the sweep schedule.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t s, uint64_t i) {
+    uint64_t z = s + (i + 1ULL) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+// u precedes v in the schedule order: higher priority first, ties by id.
+__device__ __forceinline__ bool precedes(uint64_t pu, int32_t u, uint64_t pv, int32_t v) {
+    return pu > pv || (pu == pv && u < v);
+}
+
+// Open-addressing hash table with linear probing (keys -1 = empty).
+__device__ __forceinline__ uint32_t hslot(int32_t key, int bits) {
+    return ((uint32_t)key * 0x9E3779B1u) >> (32 - bits);
+}
+template <class A>
+__device__ __forceinline__ bool hash_add(int32_t *keys, A *vals, int bits, int32_t k, A v) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t s = hslot(k, bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        int32_t cur = *((volatile int32_t *)&keys[s]);
+        if (cur == k) {
+            atomic_add_acc(&vals[s], v);
+            return true;
+        }
+        if (cur == -1) {
+            int32_t prev = atomicCAS(&keys[s], -1, k);
+            if (prev == -1 || prev == k) {
+                atomic_add_acc(&vals[s], v);
+                return true;
+            }
+        }
+        s = (s + 1u) & mask;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int ceil_log2(int64_t x) {
+    int b = 0;
+    while ((1LL << b) < x) ++b;
+    return b;
+}
+
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Device error word: kernels record the first failure here instead of
+// trapping; the host reads it after each phase.
+enum : int { kErrNone = 0, kErrHashFull = 1, kErrBadIndex = 2 };
+__device__ __forceinline__ void set_error(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+}  // namespace lgb

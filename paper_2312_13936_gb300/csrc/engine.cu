@@ -1,0 +1,691 @@
+// Host engine: one handle per graph. leiden_create copies the CSR to the
+// device; leiden_run drives the pass loop of Algorithm 1 (local-moving,
+// refinement, stop tests, renumbering, dendrogram lookup, aggregation,
+// move-based labels, threshold scaling) with the kernels of kernels.h. All
+// state stays on the device; per sweep the host reads back one scalar (the
+// sweep's delta-modularity or the refinement's move count) to decide whether
+// to continue, and per pass a handful of counts.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "engine.h"
+#include "kernels.h"
+
+namespace lgb {
+
+thread_local std::string g_last_error;
+void set_last_error(const std::string &s) { g_last_error = s; }
+const char *last_error() { return g_last_error.c_str(); }
+
+namespace {
+
+struct Scalars {  // device scalars, read back in one copy
+    int err;
+    int nonint;
+    unsigned long long vsum[2];
+    double two_m_f;
+    long long two_m_i;
+    double dq_f;
+    long long dq_i;
+    unsigned long long moved;
+    double wsum;
+    double msum[3];
+    int32_t maxdeg;
+    int32_t pad;
+    unsigned long long maxtdeg;
+};
+
+#define CK(x)                                                                              \
+    do {                                                                                   \
+        cudaError_t _e = (x);                                                              \
+        if (_e != cudaSuccess) {                                                           \
+            set_last_error(std::string(#x) + ": " + cudaGetErrorString(_e));              \
+            return (_e == cudaErrorMemoryAllocation) ? LEIDEN_ERR_OOM : LEIDEN_ERR_CUDA;   \
+        }                                                                                  \
+    } while (0)
+#define ST(x)                                  \
+    do {                                       \
+        leiden_status _s = (x);                \
+        if (_s != LEIDEN_OK) return _s;        \
+    } while (0)
+
+int ceil_log2_h(int64_t x) {
+    int b = 0;
+    while ((1LL << b) < x) ++b;
+    return b;
+}
+
+}  // namespace
+
+struct Handle::Impl {
+    int64_t n0 = 0, m0 = 0;
+    cudaStream_t s = nullptr;
+    int sm = 152;
+    bool nonint = false;
+    double wsum = 0;
+    // input CSR
+    int64_t *off0 = nullptr;
+    int32_t *idx0 = nullptr, *deg0 = nullptr;
+    float *w0 = nullptr;
+    // aggregated graphs (ping-pong)
+    struct Agg {
+        int64_t *off = nullptr;
+        int32_t *deg = nullptr, *idx = nullptr;
+        void *w = nullptr;
+        int64_t cap = 0;
+    } agg[2];
+    // per-vertex workspace
+    int32_t *C0 = nullptr, *Cp = nullptr, *CB = nullptr, *Cd = nullptr, *size = nullptr, *prop = nullptr,
+            *step = nullptr, *key = nullptr, *list = nullptr, *flag = nullptr, *members = nullptr, *cursor = nullptr,
+            *bnd = nullptr, *rep = nullptr, *label = nullptr, *minv = nullptr, *out = nullptr, *scnt = nullptr,
+            *slayer = nullptr, *sflist = nullptr, *sfcount = nullptr;
+    int64_t *pos = nullptr, *pos2 = nullptr, *coff = nullptr, *cnt = nullptr, *tdeg = nullptr, *key_cnt = nullptr,
+            *key_off = nullptr, *sfstart = nullptr;
+    void *K = nullptr, *Sig = nullptr, *Kagg = nullptr, *scan_tmp = nullptr;
+    long long *gain = nullptr;
+    uint8_t *unproc = nullptr;
+    double *sigtot = nullptr;
+    Scalars *dsc = nullptr, *hsc = nullptr;
+    // hub tables
+    int32_t *hub_keys = nullptr;
+    void *hub_vals = nullptr;
+    size_t hub_bytes = 0;
+    int key_cap = 0;
+    std::vector<int64_t> hkey_off;
+    long long launches = 0;
+    // trace
+    std::map<std::pair<int, int>, std::vector<char>> trace;
+    std::map<std::pair<int, int>, int64_t> trace_count;
+    std::vector<void *> allocs;
+
+    ~Impl() {
+        for (void *p : allocs) cudaFreeAsync(p, s);
+        if (hsc) cudaFreeHost(hsc);
+        cudaStreamSynchronize(s);
+    }
+    template <class T> leiden_status alloc(T **p, int64_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("device allocation of ") + std::to_string(count * (int64_t)sizeof(T)) +
+                           " bytes failed: " + cudaGetErrorString(e));
+            return LEIDEN_ERR_OOM;
+        }
+        allocs.push_back(q);
+        *p = static_cast<T *>(q);
+        return LEIDEN_OK;
+    }
+    leiden_status free_one(void *p) {
+        for (size_t i = 0; i < allocs.size(); ++i)
+            if (allocs[i] == p) {
+                cudaFreeAsync(p, s);
+                allocs.erase(allocs.begin() + i);
+                break;
+            }
+        return LEIDEN_OK;
+    }
+    leiden_status sync_scalars() {
+        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hsc->err) {
+            set_last_error("device error word " + std::to_string(hsc->err));
+            return LEIDEN_ERR_CUDA;
+        }
+        return LEIDEN_OK;
+    }
+    template <class T> void record(int pass, int what, const T *dev, int64_t count) {
+        std::vector<char> buf((size_t)count * sizeof(T));
+        if (count > 0) {
+            cudaMemcpyAsync(buf.data(), dev, buf.size(), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+        }
+        trace[{pass, what}] = std::move(buf);
+        trace_count[{pass, what}] = count;
+    }
+    leiden_status ensure_hub(int bits, int regions, bool det) {
+        const size_t per = ((size_t)1 << bits) * (sizeof(int32_t) + 8);
+        const size_t need = per * (size_t)regions;
+        if (need <= hub_bytes) return LEIDEN_OK;
+        if (hub_keys) free_one(hub_keys);
+        if (hub_vals) free_one(hub_vals);
+        hub_keys = nullptr;
+        hub_vals = nullptr;
+        hub_bytes = 0;
+        ST(alloc(&hub_keys, ((int64_t)1 << bits) * regions));
+        char *v = nullptr;
+        ST(alloc(&v, ((int64_t)1 << bits) * regions * 8));
+        hub_vals = v;
+        hub_bytes = need;
+        (void)det;
+        return LEIDEN_OK;
+    }
+    leiden_status ensure_agg(int x, int64_t cap) {
+        Agg &a = agg[x];
+        if (!a.off) {
+            ST(alloc(&a.off, n0 + 1));
+            ST(alloc(&a.deg, n0));
+        }
+        if (a.cap >= cap && a.idx) return LEIDEN_OK;
+        if (a.idx) free_one(a.idx);
+        if (a.w) free_one(a.w);
+        a.idx = nullptr;
+        a.w = nullptr;
+        ST(alloc(&a.idx, cap));
+        int32_t *w = nullptr;  // float or int32: 4 bytes either way
+        ST(alloc(&w, cap));
+        a.w = w;
+        a.cap = cap;
+        return LEIDEN_OK;
+    }
+};
+
+Handle::Handle() : p(new Impl) {}
+Handle::~Handle() { delete p; }
+
+leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices,
+                             const float *weights, int where, int validate, void *stream) {
+    Impl &q = *p;
+    q.s = static_cast<cudaStream_t>(stream);
+    q.n0 = n;
+    q.m0 = nnz;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&q.sm, cudaDevAttrMultiProcessorCount, dev));
+    {
+        cudaMemPool_t pool;
+        CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+        uint64_t thr = UINT64_MAX;
+        CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    }
+    CK(cudaMallocHost(&q.hsc, sizeof(Scalars)));
+    ST(q.alloc(&q.dsc, 1));
+    CK(cudaMemsetAsync(q.dsc, 0, sizeof(Scalars), q.s));
+    ST(q.alloc(&q.off0, n + 1));
+    ST(q.alloc(&q.idx0, nnz));
+    ST(q.alloc(&q.w0, nnz));
+    ST(q.alloc(&q.deg0, n));
+    const cudaMemcpyKind kind = where == LEIDEN_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(q.off0, offsets, sizeof(int64_t) * (n + 1), kind, q.s));
+    if (nnz > 0) CK(cudaMemcpyAsync(q.idx0, indices, sizeof(int32_t) * nnz, kind, q.s));
+    if (nnz > 0) {
+        if (weights) CK(cudaMemcpyAsync(q.w0, weights, sizeof(float) * nnz, kind, q.s));
+        else CK(launch_fill_i32(reinterpret_cast<int32_t *>(q.w0), 0x3f800000, nnz, q.s));  // unit weights: 1.0f
+    }
+    // workspace sized for the input graph (later graphs are smaller)
+    for (int32_t **a : {&q.C0, &q.Cp, &q.CB, &q.Cd, &q.size, &q.prop, &q.step, &q.key, &q.list, &q.flag, &q.members,
+                        &q.cursor, &q.bnd, &q.rep, &q.label, &q.minv, &q.out, &q.scnt, &q.slayer, &q.sflist})
+        ST(q.alloc(a, n));
+    for (int64_t **a : {&q.pos, &q.pos2, &q.coff})
+        ST(q.alloc(a, n + 1));
+    for (int64_t **a : {&q.cnt, &q.tdeg})
+        ST(q.alloc(a, n));
+    long long *k1, *k2, *k3;
+    ST(q.alloc(&k1, n));
+    ST(q.alloc(&k2, n));
+    ST(q.alloc(&k3, n));
+    q.K = k1;
+    q.Sig = k2;
+    q.Kagg = k3;
+    ST(q.alloc(&q.gain, n));
+    ST(q.alloc(&q.unproc, n));
+    ST(q.alloc(&q.sigtot, n));
+    char *tmp;
+    ST(q.alloc(&tmp, (int64_t)scan_tmp_bytes(n + 8192)));
+    q.scan_tmp = tmp;
+    ST(q.alloc(&q.sfstart, 4096 + 1));
+    ST(q.alloc(&q.sfcount, 4096 + 1));
+    q.key_cap = 8192;
+    ST(q.alloc(&q.key_cnt, q.key_cap));
+    ST(q.alloc(&q.key_off, q.key_cap + 1));
+    CK(launch_degrees(q.off0, q.deg0, n, &q.dsc->err, q.s));
+    if (validate) CK(launch_validate(n, q.off0, q.idx0, q.w0, &q.dsc->err, q.s));
+    CK(launch_weight_props(q.w0, nnz, &q.dsc->nonint, &q.dsc->wsum, q.s));
+    CK(cudaMemcpyAsync(q.hsc, q.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, q.s));
+    CK(cudaStreamSynchronize(q.s));
+    if (q.hsc->err) {
+        const int e = q.hsc->err;
+        set_last_error(e == 2 ? "CSR is not symmetric (w_ij != w_ji)" : "malformed CSR (offsets, indices or weights)");
+        return e == 2 ? LEIDEN_ERR_NOT_SYMMETRIC : LEIDEN_ERR_INVALID;
+    }
+    q.nonint = q.hsc->nonint != 0;
+    q.wsum = q.hsc->wsum;
+    return LEIDEN_OK;
+}
+
+leiden_status Handle::trace_get(int pass, int what, void *dst, int64_t *count) const {
+    auto it = p->trace.find({pass, what});
+    if (it == p->trace.end() || !count) {
+        set_last_error("trace item not recorded");
+        return LEIDEN_ERR_INVALID;
+    }
+    const int64_t have = p->trace_count.at({pass, what});
+    if (!dst) {
+        *count = have;
+        return LEIDEN_OK;
+    }
+    const int64_t k = *count < have ? *count : have;
+    const size_t esz = have ? it->second.size() / (size_t)have : 0;
+    std::memcpy(dst, it->second.data(), (size_t)k * esz);
+    *count = k;
+    return LEIDEN_OK;
+}
+
+leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int where, double *modularity,
+                          leiden_stats *stats) {
+    Impl &q = *p;
+    cudaStream_t s = q.s;
+    const bool det = prm.mode == LEIDEN_DETERMINISTIC;
+    const bool trace = (prm.flags & LEIDEN_FLAG_TRACE) != 0;
+    const int32_t L = prm.schedule_layers, B = prm.schedule_buckets;
+    if (prm.max_iterations < 1 || prm.max_passes < 0 || !(prm.tolerance_drop > 0) || L < 1 || B < 1 ||
+        (prm.mode != LEIDEN_ASYNC && prm.mode != LEIDEN_DETERMINISTIC) || !(prm.resolution >= 0) ||
+        !std::isfinite(prm.tolerance) || (q.n0 > 0 && !membership)) {
+        set_last_error("invalid leiden_params or membership pointer");
+        return LEIDEN_ERR_INVALID;
+    }
+    const int32_t nsteps = L - 1 + B;
+    const int32_t nkeys = nsteps * kNumBins;
+    if (nkeys > q.key_cap || L > 4096) {
+        set_last_error("schedule_layers + schedule_buckets too large");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (det) {
+        if (prm.resolution != 1.0 || q.nonint) {
+            set_last_error("deterministic mode needs integer weights and resolution 1");
+            return LEIDEN_ERR_UNSUPPORTED;
+        }
+        if (q.wsum >= 2147483648.0) {
+            set_last_error("deterministic mode needs 2m < 2^31");
+            return LEIDEN_ERR_OVERFLOW;
+        }
+    }
+    q.trace.clear();
+    q.trace_count.clear();
+    q.launches = 0;
+    cudaEvent_t ev0, ev1;
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+    CK(cudaEventRecord(ev0, s));
+    std::vector<std::pair<cudaEvent_t, int>> marks;  // phase boundary events (phase id of the span that starts)
+    auto mark = [&](int phase) -> leiden_status {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        CK(cudaEventRecord(e, s));
+        marks.push_back({e, phase});
+        return LEIDEN_OK;
+    };
+    leiden_stats st;
+    std::memset(&st, 0, sizeof(st));
+    const int64_t n0 = q.n0;
+    int tile_blocks = q.sm * 8, big_blocks = q.sm * 2;
+
+    CK(launch_iota(q.C0, n0, s));
+    q.launches++;
+    GraphView G;
+    G.n = n0;
+    G.off = q.off0;
+    G.deg = q.deg0;
+    G.idx = q.idx0;
+    G.w = q.w0;
+    G.w_int = false;
+    double tau = prm.tolerance;
+    bool broke = false;
+    int cur_agg = 1;  // next pass writes agg[cur_agg ^ 1]
+    int passes = 0;
+    const size_t accsz = 8;
+
+    for (int32_t lp = 0; lp < prm.max_passes; ++lp) {
+        const int64_t n = G.n;
+        ST(mark(3));
+        // vertexWeights(G') and 2m
+        CK(cudaMemsetAsync(&q.dsc->two_m_f, 0, sizeof(double) + sizeof(long long), s));
+        CK(launch_vertex_weights(G, det, q.K, det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, s));
+        q.launches += 2;
+        // schedule and (step, bin) lists
+        SchedWork sw{q.scnt, q.slayer, q.sflist, q.sfstart, q.sfcount};
+        CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s));
+        q.launches += L;
+        CK(launch_step_bin_keys(q.step, G.deg, n, q.key, s));
+        CK(launch_partition(q.key, n, nkeys, q.key_cnt, q.key_off, q.list, q.scan_tmp, s));
+        CK(launch_max_i32(G.deg, n, &q.dsc->maxdeg, s));
+        q.launches += 7;
+        q.hkey_off.assign(nkeys + 1, 0);
+        CK(cudaMemcpyAsync(q.hkey_off.data(), q.key_off, sizeof(int64_t) * (nkeys + 1), cudaMemcpyDeviceToHost, s));
+        ST(q.sync_scalars());
+        const double two_m_f = q.hsc->two_m_f;
+        const long long two_m_i = q.hsc->two_m_i;
+        if (det ? (two_m_i == 0) : !(two_m_f > 0)) {  // reading R12: no edges
+            CK(launch_iota(q.Cp, n, s));
+            broke = true;
+            passes++;
+            break;
+        }
+        passes++;
+        // C' and Sigma' at the start of local-moving (reading R3)
+        if (lp == 0) CK(launch_iota(q.Cp, n, s));
+        else CK(cudaMemcpyAsync(q.Cp, q.label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
+        CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
+        CK(launch_community_totals(q.Cp, q.K, det, n, q.Sig, q.size, s));
+        q.launches += 2;
+        if (trace) q.record(lp, 1, q.Cp, n);
+        // hub tables for bin 7
+        int hub_bits = 0, hub_regions = 0;
+        {
+            const int maxdeg = q.hsc->maxdeg;
+            if (maxdeg > kBlockMaxDeg) {
+                hub_bits = ceil_log2_h(2 * (int64_t)maxdeg);
+                const size_t per = ((size_t)1 << hub_bits) * 12;
+                hub_regions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
+                ST(q.ensure_hub(hub_bits, hub_regions, det));
+            }
+        }
+        SweepCtx sc;
+        sc.g = G;
+        sc.det = det;
+        sc.C = q.Cp;
+        sc.CB = q.CB;
+        sc.K = q.K;
+        sc.Sig = q.Sig;
+        sc.size = q.size;
+        sc.unproc = q.unproc;
+        sc.prop = q.prop;
+        sc.gain = q.gain;
+        sc.step = q.step;
+        sc.two_m_f = two_m_f;
+        sc.two_m_i = two_m_i;
+        sc.gamma = prm.resolution;
+        sc.cap_step = L - 1;
+        sc.dq_acc = det ? (void *)&q.dsc->dq_i : (void *)&q.dsc->dq_f;
+        sc.moved = &q.dsc->moved;
+        sc.hub_keys = q.hub_keys;
+        sc.hub_vals = q.hub_vals;
+        sc.hub_bits = hub_bits;
+        sc.err = &q.dsc->err;
+        const std::vector<int64_t> &ko = q.hkey_off;
+        auto run_steps = [&](bool refine) -> leiden_status {
+            sc.refine = refine;
+            for (int32_t k = 0; k < nsteps; ++k) {
+                sc.cur_step = k;
+                const int64_t a0 = ko[k * kNumBins], a1 = ko[(k + 1) * kNumBins];
+                if (a1 == a0) continue;
+                for (int b = 1; b < kNumBins; ++b) {
+                    const int64_t lo = ko[k * kNumBins + b], hi = ko[k * kNumBins + b + 1];
+                    if (hi == lo) continue;
+                    const int mb = b <= 5 ? tile_blocks : (b == 6 ? big_blocks : hub_regions);
+                    CK(launch_sweep_eval(sc, b, q.list + lo, hi - lo, mb, s));
+                    q.launches++;
+                }
+                if (refine) {
+                    CK(launch_refine_apply(sc, q.list + a0, a1 - a0, s));
+                    q.launches++;
+                } else if (det) {
+                    CK(launch_move_apply(sc, q.list + a0, a1 - a0, s));
+                    q.launches++;
+                }
+            }
+            return LEIDEN_OK;
+        };
+        // ---- local-moving phase (Algorithm 2)
+        ST(mark(0));
+        CK(cudaMemsetAsync(q.unproc, 1, (size_t)n, s));  // mark all vertices unprocessed
+        int li = 0;
+        for (int32_t it = 0; it < prm.max_iterations; ++it) {
+            li++;
+            CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double) + sizeof(long long), s));
+            ST(run_steps(false));
+            ST(q.sync_scalars());
+            const double dq = det ? 2.0 * (double)q.hsc->dq_i / ((double)two_m_i * (double)two_m_i)
+                                  : 2.0 * q.hsc->dq_f / (two_m_f * two_m_f);
+            if (dq <= tau) break;  // locally converged
+        }
+        st.move_iterations += li;
+        if (trace) q.record(lp, 2, q.Cp, n);
+        // ---- refinement phase (Algorithm 3)
+        ST(mark(1));
+        CK(cudaMemcpyAsync(q.CB, q.Cp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        CK(launch_iota(q.Cp, n, s));
+        CK(cudaMemcpyAsync(q.Sig, q.K, accsz * n, cudaMemcpyDeviceToDevice, s));
+        CK(launch_fill_i32(q.size, 1, n, s));
+        q.launches += 2;
+        int lj = 0;
+        for (int32_t it = 0; it < prm.max_iterations; ++it) {
+            lj++;
+            CK(cudaMemsetAsync(&q.dsc->moved, 0, sizeof(unsigned long long), s));
+            ST(run_steps(true));
+            ST(q.sync_scalars());
+            if (q.hsc->moved == 0 || (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP)) break;
+        }
+        st.refine_iterations += lj;
+        if (trace) q.record(lp, 3, q.Cp, n);
+        // ---- stop tests (readings R4, R5')
+        ST(mark(3));
+        CK(launch_nonempty_flags(q.size, n, q.flag, s));
+        CK(launch_exclusive_scan_i32(q.flag, q.pos, n, q.scan_tmp, s));
+        CK(launch_fill_i32(q.rep, 0, n, s));
+        CK(launch_mark_labels(q.CB, n, q.rep, s));
+        CK(launch_exclusive_scan_i32(q.rep, q.pos2, n, q.scan_tmp, s));
+        q.launches += 10;
+        int64_t counts[2];
+        CK(cudaMemcpyAsync(&counts[0], q.pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&counts[1], q.pos2 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        ST(q.sync_scalars());
+        const int64_t ncomm = counts[0], nbound = counts[1];
+        if (trace) {
+            int64_t c4[4] = {n, li, lj, ncomm};
+            std::vector<char> buf(sizeof(c4));
+            std::memcpy(buf.data(), c4, sizeof(c4));
+            q.trace[{lp, 4}] = buf;
+            q.trace_count[{lp, 4}] = 4;
+        }
+        if (li <= 1 && nbound == ncomm) {  // globally converged
+            broke = true;
+            break;
+        }
+        if ((double)ncomm / (double)n > prm.aggregation_tolerance) {  // low shrink
+            broke = true;
+            break;
+        }
+        // ---- renumber communities; lookup dendrogram
+        CK(launch_renumber(q.Cp, q.pos, q.Cd, n, s));
+        CK(launch_lookup(q.C0, q.Cd, n0, s));
+        q.launches += 2;
+        if (trace) {
+            q.record(lp, 5, q.Cd, n);
+            q.record(lp, 10, q.C0, n0);
+        }
+        // ---- aggregation phase (Algorithm 4)
+        ST(mark(2));
+        const int dst = cur_agg ^ 1;
+        CK(cudaMemsetAsync(q.cnt, 0, sizeof(int64_t) * ncomm, s));
+        CK(cudaMemsetAsync(q.tdeg, 0, sizeof(int64_t) * ncomm, s));
+        CK(launch_comm_counts(q.Cd, G.deg, n, q.cnt, q.tdeg, s));
+        CK(launch_exclusive_scan(q.cnt, q.coff, ncomm, q.scan_tmp, s));
+        CK(cudaMemsetAsync(q.cursor, 0, sizeof(int32_t) * ncomm, s));
+        CK(launch_comm_fill(q.Cd, n, q.coff, q.cursor, q.members, s));
+        if (!q.agg[dst].off) {
+            ST(q.alloc(&q.agg[dst].off, n0 + 1));
+            ST(q.alloc(&q.agg[dst].deg, n0));
+        }
+        CK(launch_exclusive_scan(q.tdeg, q.agg[dst].off, ncomm, q.scan_tmp, s));
+        CK(launch_comm_bin_keys(q.tdeg, ncomm, q.key, s));
+        CK(launch_partition(q.key, ncomm, kNumBins, q.key_cnt, q.key_off, q.list, q.scan_tmp, s));
+        CK(launch_max_i64(q.tdeg, ncomm, &q.dsc->maxtdeg, s));
+        q.launches += 16;
+        int64_t cap = 0;
+        int64_t ako[kNumBins + 1];
+        CK(cudaMemcpyAsync(&cap, q.agg[dst].off + ncomm, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(ako, q.key_off, sizeof(ako), cudaMemcpyDeviceToHost, s));
+        ST(q.sync_scalars());
+        ST(q.ensure_agg(dst, cap));
+        {
+            int64_t mt = (int64_t)q.hsc->maxtdeg;
+            if (mt > ncomm) mt = ncomm;
+            int abits = 0, aregions = 0;
+            if (ako[8] > ako[7]) {
+                abits = ceil_log2_h(2 * mt);
+                if (abits < 6) abits = 6;
+                const size_t per = ((size_t)1 << abits) * 12;
+                aregions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
+                ST(q.ensure_hub(abits, aregions, det));
+            }
+            AggCtx ac;
+            ac.g = G;
+            ac.det = det;
+            ac.Cd = q.Cd;
+            ac.coff = q.coff;
+            ac.members = q.members;
+            ac.out_off = q.agg[dst].off;
+            ac.out_deg = q.agg[dst].deg;
+            ac.out_idx = q.agg[dst].idx;
+            ac.out_w = q.agg[dst].w;
+            ac.out_K = q.Kagg;
+            ac.ncomm = ncomm;
+            ac.hub_keys = q.hub_keys;
+            ac.hub_vals = q.hub_vals;
+            ac.hub_bits = abits;
+            ac.err = &q.dsc->err;
+            for (int b = 1; b < kNumBins; ++b) {
+                const int64_t lo = ako[b], hi = ako[b + 1];
+                if (hi == lo) continue;
+                const int mb = b <= 5 ? tile_blocks : (b == 6 ? big_blocks : aregions);
+                CK(launch_aggregate(ac, b, q.list + lo, hi - lo, mb, s));
+                q.launches++;
+            }
+        }
+        // move-based labels of the super-vertices (reading R3)
+        CK(launch_bound_labels(q.Cd, q.CB, n, ncomm, q.bnd, q.rep, q.label, s));
+        q.launches += 4;
+        GraphView G2;
+        G2.n = ncomm;
+        G2.off = q.agg[dst].off;
+        G2.deg = q.agg[dst].deg;
+        G2.idx = q.agg[dst].idx;
+        G2.w = q.agg[dst].w;
+        G2.w_int = det;
+        ST(q.sync_scalars());
+        if (trace) {
+            q.record(lp, 6, G2.off, ncomm + 1);
+            q.record(lp, 7, G2.deg, ncomm);
+            q.record(lp, 8, G2.idx, cap);
+            // weights as fp64
+            std::vector<char> raw((size_t)cap * 4);
+            if (cap) {
+                CK(cudaMemcpyAsync(raw.data(), G2.w, raw.size(), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+            }
+            std::vector<char> buf((size_t)cap * sizeof(double));
+            double *d = reinterpret_cast<double *>(buf.data());
+            for (int64_t e = 0; e < cap; ++e) {
+                if (det) d[e] = (double)reinterpret_cast<const int32_t *>(raw.data())[e];
+                else d[e] = (double)reinterpret_cast<const float *>(raw.data())[e];
+            }
+            q.trace[{lp, 9}] = std::move(buf);
+            q.trace_count[{lp, 9}] = cap;
+        }
+        G = G2;
+        cur_agg = dst;
+        tau /= prm.tolerance_drop;  // threshold scaling
+    }
+    ST(mark(3));
+    // C <- lookup dendrogram using C to C' (reading R8)
+    if (broke) {
+        CK(launch_lookup(q.C0, q.Cp, n0, s));
+        q.launches++;
+    }
+    // canonical labels: rank of each community's smallest vertex id
+    int32_t *outp = (where == LEIDEN_DEVICE) ? membership : q.out;
+    CK(launch_min_vertex(q.C0, n0, q.minv, s));
+    CK(launch_first_flags(q.C0, q.minv, n0, q.flag, s));
+    CK(launch_exclusive_scan_i32(q.flag, q.pos, n0, q.scan_tmp, s));
+    CK(launch_canonical(q.C0, q.minv, q.pos, n0, outp, s));
+    q.launches += 7;
+    // modularity (Eq. 1) of the result on the input graph
+    CK(cudaMemsetAsync(q.sigtot, 0, sizeof(double) * n0, s));
+    CK(cudaMemsetAsync(q.dsc->msum, 0, sizeof(double) * 3, s));
+    CK(launch_modularity_parts(n0, q.off0, q.idx0, q.w0, outp, q.sigtot, q.dsc->msum, s));
+    CK(launch_sum_squares(q.sigtot, n0, &q.dsc->msum[2], s));
+    q.launches += 2;
+    int64_t ncomm_out = 0;
+    CK(cudaMemcpyAsync(&ncomm_out, q.pos + n0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    if (where != LEIDEN_DEVICE && n0 > 0)
+        CK(cudaMemcpyAsync(membership, q.out, sizeof(int32_t) * n0, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ev1, s));
+    ST(q.sync_scalars());
+    const double two_m = q.hsc->msum[1];
+    const double Q = two_m > 0 ? q.hsc->msum[0] / two_m - prm.resolution * q.hsc->msum[2] / (two_m * two_m) : 0.0;
+    if (modularity) *modularity = Q;
+    if (stats) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        st.passes = passes;
+        st.communities = ncomm_out;
+        st.modularity = Q;
+        st.ms_total = ms;
+        double ph[4] = {0, 0, 0, 0};
+        for (size_t i = 0; i < marks.size(); ++i) {
+            cudaEvent_t end = (i + 1 < marks.size()) ? marks[i + 1].first : ev1;
+            float t = 0;
+            cudaEventElapsedTime(&t, marks[i].first, end);
+            ph[marks[i].second] += t;
+        }
+        st.ms_move = ph[0];
+        st.ms_refine = ph[1];
+        st.ms_aggregate = ph[2];
+        st.ms_other = ph[3];
+        st.kernel_launches = q.launches;
+        *stats = st;
+    }
+    for (auto &m : marks) cudaEventDestroy(m.first);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return LEIDEN_OK;
+}
+
+// Modularity (Eq. 1) of a membership on a CSR given as device pointers, with
+// scratch from the stream-ordered allocator.
+leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                                const int32_t *memb, double gamma, cudaStream_t s, double *q_out) {
+    if (n < 0 || !q_out || (n > 0 && (!off || !idx || !memb))) {
+        set_last_error("invalid arguments to leiden_modularity");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (n == 0) {
+        *q_out = 0.0;
+        return LEIDEN_OK;
+    }
+    double *sig = nullptr, *sums = nullptr;
+    cudaError_t e = cudaMallocAsync(&sig, sizeof(double) * n, s);
+    if (e != cudaSuccess) {
+        set_last_error("scratch allocation failed");
+        return LEIDEN_ERR_OOM;
+    }
+    e = cudaMallocAsync(&sums, sizeof(double) * 3, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(sig, s);
+        set_last_error("scratch allocation failed");
+        return LEIDEN_ERR_OOM;
+    }
+    double h[3] = {0, 0, 0};
+    cudaMemsetAsync(sig, 0, sizeof(double) * n, s);
+    cudaMemsetAsync(sums, 0, sizeof(double) * 3, s);
+    launch_modularity_parts(n, off, idx, w, memb, sig, sums, s);
+    launch_sum_squares(sig, n, &sums[2], s);
+    cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(sig, s);
+    cudaFreeAsync(sums, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("leiden_modularity: ") + cudaGetErrorString(e));
+        return LEIDEN_ERR_CUDA;
+    }
+    *q_out = h[1] > 0 ? h[0] / h[1] - gamma * h[2] / (h[1] * h[1]) : 0.0;
+    return LEIDEN_OK;
+}
+
+}  // namespace lgb

@@ -1,0 +1,34 @@
+// Host engine behind the C ABI (include/leiden.h).
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/leiden.h"
+
+namespace lgb {
+
+void set_last_error(const std::string &s);
+const char *last_error();
+
+class Handle {
+  public:
+    Handle();
+    ~Handle();
+    Handle(const Handle &) = delete;
+    Handle &operator=(const Handle &) = delete;
+    leiden_status create(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices, const float *weights,
+                         int where, int validate, void *stream);
+    leiden_status run(const leiden_params &p, int32_t *membership, int where, double *modularity, leiden_stats *stats);
+    leiden_status trace_get(int pass, int what, void *dst, int64_t *count) const;
+
+  private:
+    struct Impl;
+    Impl *p;
+};
+
+leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                                const int32_t *memb, double gamma, cudaStream_t s, double *q_out);
+
+}  // namespace lgb

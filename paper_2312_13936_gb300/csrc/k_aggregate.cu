@@ -1,0 +1,325 @@
+// Aggregation (Algorithm 4): for every community c of the renumbered refined
+// membership, accumulate H[C'[j]] += w over all edges (self-loops included)
+// of all member vertices and write the merged (d, w) pairs as row c of the
+// super-vertex graph G'' (a holey CSR whose row capacity is the community's
+// total degree). The row sum is K''[c]. Communities are binned by total
+// degree like the sweep kernels: a tile of lanes (<= 32 member edges), one
+// warp with a shared-memory table (<= 256), one block with a shared-memory
+// table (<= 4096), one block with a global-memory table (larger).
+// Row order inside G'' is unspecified; deterministic mode writes exact
+// integer sums, so the rows are equal as sets.
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lgb {
+namespace {
+
+template <class P, class Wi, class Wo> struct AV {
+    using A = typename P::acc;
+    const int64_t *off;
+    const int32_t *deg;
+    const int32_t *idx;
+    const Wi *w;
+    const int32_t *Cd;
+    const int64_t *coff;
+    const int32_t *members;
+    const int64_t *out_off;
+    int32_t *out_deg;
+    int32_t *out_idx;
+    Wo *out_w;
+    A *out_K;
+    int32_t *hub_keys;
+    A *hub_vals;
+    int hub_bits;
+    int64_t ncomm;
+    int *err;
+};
+
+template <class P, class Wi, class Wo> AV<P, Wi, Wo> aview(const AggCtx &c) {
+    using A = typename P::acc;
+    AV<P, Wi, Wo> a;
+    a.off = c.g.off;
+    a.deg = c.g.deg;
+    a.idx = c.g.idx;
+    a.w = static_cast<const Wi *>(c.g.w);
+    a.Cd = c.Cd;
+    a.coff = c.coff;
+    a.members = c.members;
+    a.out_off = c.out_off;
+    a.out_deg = c.out_deg;
+    a.out_idx = c.out_idx;
+    a.out_w = static_cast<Wo *>(c.out_w);
+    a.out_K = static_cast<A *>(c.out_K);
+    a.hub_keys = c.hub_keys;
+    a.hub_vals = static_cast<A *>(c.hub_vals);
+    a.hub_bits = c.hub_bits;
+    a.ncomm = c.ncomm;
+    a.err = c.err;
+    return a;
+}
+
+// stored weight of a merged entry, and its value as the next pass sees it
+template <class Wo, class A> __device__ __forceinline__ Wo out_weight(A s) { return (Wo)s; }
+
+// ------------------------------------------------------------- tile bins
+template <class P, class Wi, class Wo, int T>
+__global__ void __launch_bounds__(256) k_agg_tile(AV<P, Wi, Wo> a, const int32_t *__restrict__ list, int64_t count) {
+    using A = typename P::acc;
+    const int lane = threadIdx.x & 31;
+    const int tl = lane & (T - 1);
+    const int base_lane = lane & ~(T - 1);
+    const unsigned tmask = (T == 32) ? kFull : (((1u << T) - 1u) << base_lane);
+    const int64_t tiles = (int64_t)gridDim.x * (blockDim.x / T);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; t < count; t += tiles) {
+        const int32_t c = list[t];
+        const int64_t m0 = a.coff[c];
+        const int32_t nm = (int32_t)(a.coff[c + 1] - m0);
+        // member of this lane and its edge range
+        int32_t du = 0;
+        int64_t su = 0;
+        if (tl < nm) {
+            const int32_t u = a.members[m0 + tl];
+            du = a.deg[u];
+            su = a.off[u];
+        }
+        int32_t incl = du;
+#pragma unroll
+        for (int o = 1; o < T; o <<= 1) {
+            const int32_t x = __shfl_up_sync(tmask, incl, o, T);
+            if (tl >= o) incl += x;
+        }
+        const int32_t excl = incl - du;
+        const int32_t total = __shfl_sync(tmask, incl, T - 1, T);
+        // the lane whose member owns edge slot tl
+        int owner = 0;
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            const int32_t ek = __shfl_sync(tmask, excl, k, T);
+            const int32_t ik = __shfl_sync(tmask, incl, k, T);
+            if (tl >= ek && tl < ik) owner = k;
+        }
+        const int64_t s_own = __shfl_sync(tmask, su, owner, T);
+        const int32_t e_own = __shfl_sync(tmask, excl, owner, T);
+        int32_t key = -1;
+        A wv = 0;
+        if (tl < total) {
+            const int64_t e = s_own + (tl - e_own);
+            key = a.Cd[a.idx[e]];
+            wv = wconv<A>(a.w[e]);
+        }
+        A sum = 0;
+        bool lead = (key >= 0);
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+            const int32_t kk = __shfl_sync(tmask, key, k, T);
+            const A wk = __shfl_sync(tmask, wv, k, T);
+            if (key >= 0 && kk == key) {
+                sum += wk;
+                if (k < tl) lead = false;
+            }
+        }
+        const unsigned ball = (__ballot_sync(tmask, lead) & tmask) >> base_lane;
+        const int pos = __popc(ball & ((1u << tl) - 1u));
+        const int64_t o0 = a.out_off[c];
+        A kpart = 0;
+        if (lead) {
+            const Wo wo = out_weight<Wo>(sum);
+            a.out_idx[o0 + pos] = key;
+            a.out_w[o0 + pos] = wo;
+            kpart = wconv<A>(wo);
+        }
+#pragma unroll
+        for (int o = T / 2; o > 0; o >>= 1) kpart += __shfl_xor_sync(tmask, kpart, o, T);
+        if (tl == 0) {
+            a.out_deg[c] = __popc(ball);
+            a.out_K[c] = kpart;
+        }
+    }
+}
+
+// insert all member edges of community c into a table (threads of a warp
+// take members round-robin; used by the warp bin)
+template <class P, class Wi, class Wo>
+__device__ __forceinline__ void fill_members_lanes(const AV<P, Wi, Wo> &a, int64_t m0, int32_t nm, int32_t *keys,
+                                                   typename P::acc *vals, int bits, int lane) {
+    using A = typename P::acc;
+    for (int32_t k = lane; k < nm; k += 32) {
+        const int32_t u = a.members[m0 + k];
+        const int64_t e0 = a.off[u];
+        const int32_t du = a.deg[u];
+        for (int32_t e = 0; e < du; ++e)
+            if (!hash_add(keys, vals, bits, a.Cd[a.idx[e0 + e]], wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
+    }
+}
+
+// ------------------------------------------------------- warp-table bin
+template <class P, class Wi, class Wo>
+__global__ void __launch_bounds__(256) k_agg_warp(AV<P, Wi, Wo> a, const int32_t *__restrict__ list, int64_t count) {
+    using A = typename P::acc;
+    __shared__ int32_t skeys[8][kWarpSlots];
+    __shared__ A svals[8][kWarpSlots];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t *keys = skeys[wib];
+    A *vals = svals[wib];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; t < count; t += nwarps) {
+        const int32_t c = list[t];
+        const int64_t m0 = a.coff[c];
+        const int32_t nm = (int32_t)(a.coff[c + 1] - m0);
+        const int64_t cap = a.out_off[c + 1] - a.out_off[c];
+        int bits = ceil_log2(2 * cap);
+        if (bits < 6) bits = 6;
+        const int S = 1 << bits;
+        for (int s = lane; s < S; s += 32) {
+            keys[s] = -1;
+            vals[s] = 0;
+        }
+        __syncwarp();
+        fill_members_lanes(a, m0, nm, keys, vals, bits, lane);
+        __syncwarp();
+        const int64_t o0 = a.out_off[c];
+        int written = 0;
+        A kpart = 0;
+        for (int s0 = 0; s0 < S; s0 += 32) {
+            const int s = s0 + lane;
+            const int32_t k = keys[s];
+            const unsigned ball = __ballot_sync(kFull, k >= 0);
+            if (k >= 0) {
+                const int pos = written + __popc(ball & ((1u << lane) - 1u));
+                const Wo wo = out_weight<Wo>(vals[s]);
+                a.out_idx[o0 + pos] = k;
+                a.out_w[o0 + pos] = wo;
+                kpart += wconv<A>(wo);
+            }
+            written += __popc(ball);
+        }
+        kpart = warp_sum(kpart);
+        if (lane == 0) {
+            a.out_deg[c] = written;
+            a.out_K[c] = kpart;
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------ block / hub table bins
+constexpr int kAggThreads = 512;
+
+template <class P, class Wi, class Wo, bool HUB>
+__global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, const int32_t *__restrict__ list,
+                                                          int64_t count) {
+    using A = typename P::acc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_written;
+    __shared__ A s_k[kAggThreads / 32];
+    int32_t *keys;
+    A *vals;
+    if (HUB) {
+        keys = a.hub_keys + ((int64_t)blockIdx.x << a.hub_bits);
+        vals = a.hub_vals + ((int64_t)blockIdx.x << a.hub_bits);
+    } else {
+        vals = reinterpret_cast<A *>(smem_raw);
+        keys = reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
+    }
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
+    for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+        const int32_t c = list[t];
+        const int64_t m0 = a.coff[c];
+        const int32_t nm = (int32_t)(a.coff[c + 1] - m0);
+        int64_t cap = a.out_off[c + 1] - a.out_off[c];
+        if (cap > a.ncomm) cap = a.ncomm;  // distinct targets <= number of communities
+        int bits = ceil_log2(2 * cap);
+        if (bits < 6) bits = 6;
+        __syncthreads();
+        if (HUB && bits > a.hub_bits) {
+            if (tid == 0) set_error(a.err, kErrHashFull);
+            continue;
+        }
+        const int64_t S = 1LL << bits;
+        for (int64_t s = tid; s < S; s += blockDim.x) {
+            keys[s] = -1;
+            vals[s] = 0;
+        }
+        if (tid == 0) s_written = 0;
+        __syncthreads();
+        // warps take members round-robin, lanes stride over a member's edges
+        for (int32_t k = wib; k < nm; k += nw) {
+            const int32_t u = a.members[m0 + k];
+            const int64_t e0 = a.off[u];
+            const int32_t du = a.deg[u];
+            for (int32_t e = lane; e < du; e += 32)
+                if (!hash_add(keys, vals, bits, a.Cd[a.idx[e0 + e]], wconv<A>(a.w[e0 + e])))
+                    set_error(a.err, kErrHashFull);
+        }
+        __syncthreads();
+        const int64_t o0 = a.out_off[c];
+        A kpart = 0;
+        for (int64_t s0 = (int64_t)wib * 32; s0 < S; s0 += (int64_t)nw * 32) {
+            const int64_t s = s0 + lane;
+            const int32_t k = keys[s];
+            const unsigned ball = __ballot_sync(kFull, k >= 0);
+            int base = 0;
+            if (lane == 0 && ball) base = atomicAdd(&s_written, __popc(ball));
+            base = __shfl_sync(kFull, base, 0);
+            if (k >= 0) {
+                const int pos = base + __popc(ball & ((1u << lane) - 1u));
+                const Wo wo = out_weight<Wo>(vals[s]);
+                a.out_idx[o0 + pos] = k;
+                a.out_w[o0 + pos] = wo;
+                kpart += wconv<A>(wo);
+            }
+        }
+        kpart = warp_sum(kpart);
+        if (lane == 0) s_k[wib] = kpart;
+        __syncthreads();
+        if (tid == 0) {
+            A ks = 0;
+            for (int w2 = 0; w2 < nw; ++w2) ks += s_k[w2];
+            a.out_deg[c] = s_written;
+            a.out_K[c] = ks;
+        }
+    }
+}
+
+template <class P, class Wi, class Wo>
+cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks, cudaStream_t s) {
+    auto a = aview<P, Wi, Wo>(c);
+    auto grid = [&](int64_t per_block) {
+        int64_t b = (count + per_block - 1) / per_block;
+        return (int)(b < max_blocks ? (b < 1 ? 1 : b) : max_blocks);
+    };
+    switch (bin) {
+        case 1: k_agg_tile<P, Wi, Wo, 4><<<grid(64), 256, 0, s>>>(a, list, count); break;
+        case 2: k_agg_tile<P, Wi, Wo, 8><<<grid(32), 256, 0, s>>>(a, list, count); break;
+        case 3: k_agg_tile<P, Wi, Wo, 16><<<grid(16), 256, 0, s>>>(a, list, count); break;
+        case 4: k_agg_tile<P, Wi, Wo, 32><<<grid(8), 256, 0, s>>>(a, list, count); break;
+        case 5: k_agg_warp<P, Wi, Wo><<<grid(8), 256, 0, s>>>(a, list, count); break;
+        case 6: {
+            const size_t sm = (sizeof(typename P::acc) + sizeof(int32_t)) * kBlockSlots;
+            auto kern = k_agg_block<P, Wi, Wo, false>;
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            kern<<<grid(1), kAggThreads, sm, s>>>(a, list, count);
+            break;
+        }
+        case 7: k_agg_block<P, Wi, Wo, true><<<grid(1), kAggThreads, 0, s>>>(a, list, count); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
+                             cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (c.det) {
+        if (c.g.w_int) return agg_typed<Det, int32_t, int32_t>(c, bin, list, count, max_blocks, s);
+        return agg_typed<Det, float, int32_t>(c, bin, list, count, max_blocks, s);
+    }
+    return agg_typed<Async, float, float>(c, bin, list, count, max_blocks, s);
+}
+
+}  // namespace lgb

@@ -1,0 +1,306 @@
+// Utility kernels: fills, degrees, vertex weights (Algorithm 1,
+// vertexWeights), exclusive scans (Algorithm 4's exclusiveScan and the
+// renumbering), bucket partition by (schedule step, degree bin), CSR
+// validation.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lgb {
+namespace {
+
+inline int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b > cap ? cap : b);
+}
+
+__global__ void k_iota(int32_t *a, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+__global__ void k_fill_i32(int32_t *a, int32_t v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+__global__ void k_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = off[i + 1] - off[i];
+        if (d < 0 || d > 0x7fffffff) set_error(err, kErrBadIndex);
+        deg[i] = (int32_t)(d < 0 ? 0 : d);
+    }
+}
+
+// K_i = sum of row i. Rows up to 64 entries by one thread, longer rows by a warp.
+template <class A, class W>
+__global__ void k_vertex_weights(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K, A *two_m) {
+    A local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = deg[i];
+        if (d > 64) continue;
+        const int64_t e0 = off[i];
+        A s = 0;
+        for (int32_t e = 0; e < d; ++e) s += wconv<A>(w[e0 + e]);
+        K[i] = s;
+        local += s;
+    }
+    local = warp_sum(local);
+    if ((threadIdx.x & 31) == 0 && local != (A)0) atomic_add_acc(two_m, local);
+}
+template <class A, class W>
+__global__ void k_vertex_weights_long(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K, A *two_m) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const int32_t d = deg[i];
+        if (d <= 64) continue;
+        const int64_t e0 = off[i];
+        A s = 0;
+        for (int32_t e = lane; e < d; e += 32) s += wconv<A>(w[e0 + e]);
+        s = warp_sum(s);
+        if (lane == 0) {
+            K[i] = s;
+            atomic_add_acc(two_m, s);
+        }
+    }
+}
+
+// ---- exclusive scan: tile reduce, scan of tile sums, tile rescan
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *s_warp, int64_t *total) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wib] = x;
+    __syncthreads();
+    if (wib == 0) {
+        const int nw = blockDim.x >> 5;
+        int64_t t = lane < nw ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) s_warp[lane] = t;
+    }
+    __syncthreads();
+    const int64_t before = wib > 0 ? s_warp[wib - 1] : 0;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <class T> __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T *in, int64_t n, int64_t *part) {
+    __shared__ int64_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) s += (int64_t)in[i];
+    }
+    int64_t total;
+    block_excl_scan(s, s_warp, &total);
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+__global__ void __launch_bounds__(1024) k_scan_parts(int64_t *part, int64_t nb) {
+    __shared__ int64_t s_warp[32];
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        const int64_t v = i < nb ? part[i] : 0;
+        int64_t total;
+        const int64_t ex = block_excl_scan(v, s_warp, &total);
+        if (i < nb) part[i] = carry + ex;
+        carry += total;
+    }
+}
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const T *in, int64_t *out, int64_t n, const int64_t *part,
+                                                            int64_t nb) {
+    __shared__ int64_t s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k;
+        v[k] = i < n ? (int64_t)in[i] : 0;
+        s += v[k];
+    }
+    int64_t total;
+    int64_t run = block_excl_scan(s, s_warp, &total) + part[blockIdx.x];
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = part[blockIdx.x] + total;
+}
+
+template <class T> cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
+    if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    int64_t *part = static_cast<int64_t *>(tmp);
+    k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+    k_scan_parts<<<1, 1024, 0, s>>>(part, nb);
+    k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part, nb);
+    return cudaGetLastError();
+}
+
+// ---- partition by key: histogram, scan, scatter
+__global__ void k_part_count(const int32_t *key, int64_t n, int32_t nkeys, int64_t *counts) {
+    extern __shared__ int32_t s_cnt[];
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_cnt[k] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = key[i];
+        if (k >= 0) atomicAdd(&s_cnt[k], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x)
+        if (s_cnt[k]) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[k]), (unsigned long long)s_cnt[k]);
+}
+__global__ void k_part_scatter(const int32_t *key, int64_t n, const int64_t *key_off, int64_t *cursor, int32_t *list) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const int32_t k = i < n ? key[i] : -1;
+        const unsigned peers = __match_any_sync(kFull, k);
+        const int leader = __ffs(peers) - 1;
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        int64_t base = 0;
+        if (lane == leader && k >= 0)
+            base = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[k]), (unsigned long long)__popc(peers));
+        base = __shfl_sync(kFull, base, leader);
+        if (k >= 0) list[key_off[k] + base + rank] = (int32_t)i;
+    }
+}
+
+__global__ void k_max_i32(const int32_t *a, int64_t n, int32_t *out) {
+    int32_t m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, a[i]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// CSR validation: offsets monotone, indices in range, weights finite and
+// >= 0, and the multiset of (i, j, w) equal to that of (j, i, w), compared
+// through sums of a 64-bit mix of each triple (a mismatch is found with
+// probability 1 - 2^-64 per differing entry).
+__device__ __forceinline__ uint64_t mix_triple(uint64_t i, uint64_t j, uint32_t wbits) {
+    uint64_t z = i * 0x9E3779B97F4A7C15ULL ^ (j + 0x632BE59BD9B4E019ULL) * 0xC2B2AE3D27D4EB4FULL ^ (uint64_t)wbits << 17;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__global__ void k_validate(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int *err,
+                           unsigned long long *sums) {
+    unsigned long long fwd = 0, bwd = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = off[i], b = off[i + 1];
+        if (b < a) {
+            set_error(err, 1);
+            continue;
+        }
+        for (int64_t e = a; e < b; ++e) {
+            const int32_t j = idx[e];
+            if (j < 0 || j >= n) {
+                set_error(err, 1);
+                continue;
+            }
+            const float x = w ? w[e] : 1.0f;
+            if (!(x >= 0.0f) || isinf(x)) set_error(err, 1);
+            const uint32_t bits = __float_as_uint(x);
+            fwd += mix_triple((uint64_t)i, (uint64_t)j, bits);
+            bwd += mix_triple((uint64_t)j, (uint64_t)i, bits);
+        }
+    }
+    fwd = warp_sum(fwd);
+    bwd = warp_sum(bwd);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sums[0], fwd);
+        atomicAdd(&sums[1], bwd);
+    }
+}
+__global__ void k_validate_finish(const unsigned long long *sums, int *err) {
+    if (sums[0] != sums[1]) set_error(err, 2);
+}
+
+}  // namespace
+
+cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_iota<<<grid_for(n, 256), 256, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill_i32(int32_t *a, int32_t v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(a, v, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_degrees<<<grid_for(n, 256), 256, 0, s>>>(off, deg, n, err);
+    return cudaGetLastError();
+}
+cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *two_m, cudaStream_t s) {
+    if (g.n <= 0) return cudaSuccess;
+    const int gb = grid_for(g.n, 256), gw = grid_for(g.n * 32, 256);
+    if (det) {
+        auto *k = static_cast<long long *>(K);
+        auto *t = static_cast<long long *>(two_m);
+        if (g.w_int) {
+            k_vertex_weights<long long, int32_t><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
+            k_vertex_weights_long<long long, int32_t><<<gw, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
+        } else {
+            k_vertex_weights<long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+            k_vertex_weights_long<long long, float><<<gw, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+        }
+    } else {
+        auto *k = static_cast<double *>(K);
+        auto *t = static_cast<double *>(two_m);
+        k_vertex_weights<double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+        k_vertex_weights_long<double, float><<<gw, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+    }
+    return cudaGetLastError();
+}
+size_t scan_tmp_bytes(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile + 1) * sizeof(int64_t); }
+cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
+    return scan_impl<int64_t>(in, out, n, tmp, s);
+}
+cudaError_t launch_exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
+    return scan_impl<int32_t>(in, out, n, tmp, s);
+}
+cudaError_t launch_partition(const int32_t *key, int64_t n, int32_t nkeys, int64_t *counts, int64_t *key_off,
+                             int32_t *list, void *tmp, cudaStream_t s) {
+    if (nkeys > 8192) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * nkeys, s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) k_part_count<<<grid_for(n, 256, 152 * 4), 256, sizeof(int32_t) * nkeys, s>>>(key, n, nkeys, counts);
+    if ((e = scan_impl<int64_t>(counts, key_off, nkeys, tmp, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * nkeys, s)) != cudaSuccess) return e;
+    if (n > 0) k_part_scatter<<<grid_for(n, 256), 256, 0, s>>>(key, n, key_off, counts, list);
+    return cudaGetLastError();
+}
+cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    k_max_i32<<<grid_for(n, 256), 256, 0, s>>>(a, n, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_validate(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int *err,
+                            cudaStream_t s) {
+    // sums live right after the error word (caller provides int[4] aligned to 8)
+    unsigned long long *sums = reinterpret_cast<unsigned long long *>(err + 2);
+    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) k_validate<<<grid_for(n, 256), 256, 0, s>>>(n, off, idx, w, err, sums);
+    k_validate_finish<<<1, 1, 0, s>>>(sums, err);
+    return cudaGetLastError();
+}
+
+}  // namespace lgb

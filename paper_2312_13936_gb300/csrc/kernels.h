@@ -1,0 +1,155 @@
+// Host-side launchers of the Leiden kernels. Every launcher enqueues work on
+// the given stream and returns the launch status; none synchronises.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lgb {
+
+// Degree bins of the sweep and aggregation kernels: a vertex (or community)
+// of degree d goes to the first bin whose bound holds it. Bin 0 (no edges)
+// is never listed.
+constexpr int kNumBins = 8;
+constexpr int kTileBins = 4;        // bins 1..4: a tile of 4/8/16/32 lanes per vertex
+constexpr int kWarpMaxDeg = 256;    // bin 5: one warp, shared-memory table
+constexpr int kBlockMaxDeg = 4096;  // bin 6: one block, shared-memory table; bin 7: global table
+constexpr int kWarpSlots = 512;
+constexpr int kBlockSlots = 8192;
+__host__ __device__ inline int degree_bin(int64_t d) {
+    return d <= 0 ? 0 : d <= 4 ? 1 : d <= 8 ? 2 : d <= 16 ? 3 : d <= 32 ? 4 : d <= kWarpMaxDeg ? 5 : d <= kBlockMaxDeg ? 6 : 7;
+}
+
+// The current graph G' (a holey CSR, paper Fig. 5): row i is
+// idx/w[off[i] .. off[i]+deg[i]). Weights are float, or int32 in
+// deterministic mode after the first aggregation.
+struct GraphView {
+    int64_t n = 0;
+    const int64_t *off = nullptr;
+    const int32_t *deg = nullptr;
+    const int32_t *idx = nullptr;
+    const void *w = nullptr;
+    bool w_int = false;
+};
+
+// State of one local-moving or refinement sweep step.
+struct SweepCtx {
+    GraphView g;
+    bool det = false;         // Det (int64) or Async (fp64) policy
+    bool refine = false;      // Algorithm 3 (bounded scan, isolated vertices) vs Algorithm 2
+    int32_t *C = nullptr;     // C' (membership of G' vertices)
+    const int32_t *CB = nullptr;  // C'_B, community bound (refinement)
+    const void *K = nullptr;  // K' (acc type)
+    void *Sig = nullptr;      // Sigma' (acc type)
+    int32_t *size = nullptr;  // members per community
+    uint8_t *unproc = nullptr;    // Algorithm 2 pruning flags (1 = unprocessed)
+    int32_t *prop = nullptr;      // proposed target (-1 none)
+    long long *gain = nullptr;    // det: key gain of the proposal
+    const int32_t *step = nullptr;  // schedule step of every vertex
+    double two_m_f = 0;
+    long long two_m_i = 0;
+    double gamma = 1;
+    int32_t cur_step = 0, cap_step = 0;  // steps >= cap_step may hold adjacent vertices
+    void *dq_acc = nullptr;       // sweep delta-modularity numerator (acc type)
+    unsigned long long *moved = nullptr;  // refinement: accepted moves
+    int32_t *hub_keys = nullptr;  // global tables for bin 7 (one region per block)
+    void *hub_vals = nullptr;
+    int hub_bits = 0;
+    int *err = nullptr;
+};
+
+// evaluate one (step, bin) vertex list
+cudaError_t launch_sweep_eval(const SweepCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
+                              cudaStream_t s);
+// deterministic local-moving: apply a step's proposals (list covers all bins)
+cudaError_t launch_move_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s);
+// refinement: accept (rule S5) and apply a step's proposals
+cudaError_t launch_refine_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s);
+
+// Aggregation (Algorithm 4) of G' by dense labels Cd into the holey CSR G''.
+struct AggCtx {
+    GraphView g;
+    bool det = false;
+    const int32_t *Cd = nullptr;      // renumbered refined membership, [0, ncomm)
+    const int64_t *coff = nullptr;    // community-vertex CSR offsets
+    const int32_t *members = nullptr;
+    const int64_t *out_off = nullptr; // offsets of G'' (scan of community total degree)
+    int32_t *out_deg = nullptr;
+    int32_t *out_idx = nullptr;
+    void *out_w = nullptr;            // float (async) or int32 (det)
+    void *out_K = nullptr;            // K'' (acc type): row sums of G''
+    int64_t ncomm = 0;
+    int32_t *hub_keys = nullptr;
+    void *hub_vals = nullptr;
+    int hub_bits = 0;
+    int *err = nullptr;
+};
+cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
+                             cudaStream_t s);
+
+// ---- utilities (k_util.cu)
+cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s);
+cudaError_t launch_fill_i32(int32_t *a, int32_t v, int64_t n, cudaStream_t s);
+cudaError_t launch_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err, cudaStream_t s);
+// K[i] = sum of row i (acc type), *two_m += sum of K (acc type)
+cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *two_m, cudaStream_t s);
+// exclusive scan of n int64 counts into out[0..n] (out[n] = total); tmp >= scan_tmp_bytes(n)
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
+cudaError_t launch_exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
+// bucket partition: key[i] in [0, nkeys) or -1 (dropped); counts/offsets sized nkeys(+1)
+cudaError_t launch_partition(const int32_t *key, int64_t n, int32_t nkeys, int64_t *counts, int64_t *key_off,
+                             int32_t *list, void *tmp, cudaStream_t s);
+cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *out, cudaStream_t s);
+cudaError_t launch_validate(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int *err,
+                            cudaStream_t s);
+
+// ---- schedule (k_schedule.cu): step of every vertex (reading S0)
+struct SchedWork {
+    int32_t *cnt, *layer, *flist;  // n each
+    int64_t *fstart;               // L+1
+    int32_t *fcount;               // L+1
+};
+cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
+                            int32_t *step, cudaStream_t s);
+// key[i] = step[i]*kNumBins + degree_bin(deg[i]) (or -1 if deg == 0)
+cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t *key, cudaStream_t s);
+
+// ---- pass bookkeeping (k_pass.cu)
+// Sigma[c] += K[i], size[c] += 1 over C (acc type)
+cudaError_t launch_community_totals(const int32_t *C, const void *K, bool det, int64_t n, void *Sig, int32_t *size,
+                                    cudaStream_t s);
+// flag[c] = (size[c] > 0)
+cudaError_t launch_nonempty_flags(const int32_t *size, int64_t n, int32_t *flag, cudaStream_t s);
+// flag[CB[i]] = 1
+cudaError_t launch_mark_labels(const int32_t *lab, int64_t n, int32_t *flag, cudaStream_t s);
+// out[i] = map[in[i]] (in-place allowed when out == in)
+cudaError_t launch_gather_map(const int32_t *map_pos, const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+// dense id of community c = (int32)pos[c] where pos is the exclusive scan of flags
+cudaError_t launch_renumber(const int32_t *C, const int64_t *pos, int32_t *Cd, int64_t n, cudaStream_t s);
+// C0[v] = map[C0[v]] for the dendrogram
+cudaError_t launch_lookup(int32_t *C0, const int32_t *map, int64_t n0, cudaStream_t s);
+// community-vertex CSR: cnt[Cd[i]]++, tdeg[Cd[i]] += deg[i]
+cudaError_t launch_comm_counts(const int32_t *Cd, const int32_t *deg, int64_t n, int64_t *cnt, int64_t *tdeg,
+                               cudaStream_t s);
+cudaError_t launch_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, int32_t *cursor, int32_t *members,
+                             cudaStream_t s);
+// bins of communities by total degree
+cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key, cudaStream_t s);
+// move-based labels: bnd[Cd[i]] = CB[i]; rep[b] = min s; label[s] = rep[bnd[s]]
+cudaError_t launch_bound_labels(const int32_t *Cd, const int32_t *CB, int64_t n, int64_t ncomm, int32_t *bnd,
+                                int32_t *rep, int32_t *label, cudaStream_t s);
+// canonical labels: rank of the smallest vertex of each community
+cudaError_t launch_min_vertex(const int32_t *C0, int64_t n0, int32_t *minv, cudaStream_t s);
+cudaError_t launch_first_flags(const int32_t *C0, const int32_t *minv, int64_t n0, int32_t *first, cudaStream_t s);
+cudaError_t launch_canonical(const int32_t *C0, const int32_t *minv, const int64_t *rank, int64_t n0, int32_t *out,
+                             cudaStream_t s);
+// modularity (Eq. 1) of labels C (in [0,n)) on a plain CSR: sums[0] += intra
+// weight, sums[1] += 2m, sigtot[c] += K_i; then sums[2] += sum_c sigtot[c]^2
+cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                                    const int32_t *C, double *sigtot, double *sums, cudaStream_t s);
+cudaError_t launch_sum_squares(const double *x, int64_t n, double *out, cudaStream_t s);
+cudaError_t launch_max_i64(const int64_t *a, int64_t n, unsigned long long *out, cudaStream_t s);
+// nonint = 1 if some weight is not an integer; sum += sum of weights (fp64)
+cudaError_t launch_weight_props(const float *w, int64_t m, int *nonint, double *sum, cudaStream_t s);
+
+}  // namespace lgb

@@ -1,0 +1,65 @@
+"""GPU-test helpers: run the library through the C ABI and compare its
+per-pass trace with the oracle's."""
+import numpy as np
+
+import oracle
+import paper_2312_13936_gb300 as lg
+
+TRACE_ITEMS = (lg.TRACE_INIT, lg.TRACE_MOVE, lg.TRACE_REFINE, lg.TRACE_COUNTS, lg.TRACE_RENUMBER, lg.TRACE_DENDRO)
+
+
+def run_gpu(g, mode, trace=False, **kw):
+    h = lg.Leiden(g.offsets, g.indices, g.weights)
+    try:
+        memb, q, st = h.run(mode=mode, trace=trace, **kw)
+        tr = {}
+        if trace:
+            for p in range(st.passes):
+                for w in TRACE_ITEMS + (lg.TRACE_AGG_OFF, lg.TRACE_AGG_DEG, lg.TRACE_AGG_IDX, lg.TRACE_AGG_W):
+                    try:
+                        tr.setdefault(p, {})[w] = h.trace(p, w)
+                    except lg.LeidenError:
+                        pass
+        return memb.cpu().numpy(), q, st, tr
+    finally:
+        h.close()
+
+
+def rows(off, deg, idx, w):
+    """holey CSR rows as sorted (target, weight) lists"""
+    out = []
+    for c in range(len(deg)):
+        a = int(off[c])
+        pairs = sorted(zip(idx[a:a + deg[c]].tolist(), w[a:a + deg[c]].tolist()))
+        out.append(pairs)
+    return out
+
+
+def compare_traces(gpu_tr, ora_tr):
+    """Bit-exact per-phase comparison; returns a list of mismatch descriptions."""
+    bad = []
+    if sorted(gpu_tr) != sorted(ora_tr):
+        bad.append(f"passes differ: gpu {sorted(gpu_tr)} oracle {sorted(ora_tr)}")
+    for p in sorted(set(gpu_tr) & set(ora_tr)):
+        G, O = gpu_tr[p], ora_tr[p]
+        for w in TRACE_ITEMS:
+            if (w in G) != (w in O):
+                bad.append(f"pass {p} item {w}: recorded on one side only")
+            elif w in G and not np.array_equal(G[w], O[w]):
+                d = np.nonzero(np.asarray(G[w]) != np.asarray(O[w]))[0] if len(G[w]) == len(O[w]) else []
+                bad.append(f"pass {p} item {w}: differs ({len(d)} entries, first {d[:5]})")
+        if lg.TRACE_AGG_OFF in O:
+            if lg.TRACE_AGG_OFF not in G:
+                bad.append(f"pass {p}: aggregated graph missing on GPU")
+                continue
+            if not np.array_equal(G[lg.TRACE_AGG_OFF], O[oracle.T_AGG_OFF]):
+                bad.append(f"pass {p}: aggregated offsets differ")
+            if not np.array_equal(G[lg.TRACE_AGG_DEG], O[oracle.T_AGG_DEG]):
+                bad.append(f"pass {p}: aggregated degrees differ")
+            else:
+                rg = rows(G[6], G[7], G[8], G[9])
+                ro = rows(O[6], O[7], O[8], O[9])
+                nd = sum(1 for a, b in zip(rg, ro) if a != b)
+                if nd:
+                    bad.append(f"pass {p}: {nd} aggregated rows differ")
+    return bad

@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
+
+Deterministic mode: every phase of every pass (local-moving, refinement,
+counts, renumbering, dendrogram, aggregated holey CSR with rows compared as
+sets) and the final membership are bit-exact against oracle SYNC.
+Asynchronous mode: modularity within 0.005 of oracle SEQ, every community
+connected (Algorithm 5) and the reported modularity within 1e-9 relative of
+the oracle's recomputation from the returned membership.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_2312_13936_gb300 as lg
+from tests._gpu import compare_traces, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+Q_TOL_ASYNC = 0.005   # modularity tolerance of the asynchronous mode
+Q_REL_REPORT = 1e-9   # reported Q against the oracle's recomputation
+
+
+def hub_graph(seed=7):
+    """R-MAT core plus hubs of degree 300 (warp/block bins) and 5000 (global
+    table bin), integer weights."""
+    base = gen.rmat(13, 8, seed=seed)
+    n = base.n
+    deg = np.diff(base.offsets)
+    rows = np.repeat(np.arange(n), deg)
+    keep = rows < base.indices
+    u = list(rows[keep])
+    v = list(base.indices[keep])
+    rng = np.random.default_rng(seed)
+    for hub, k in ((0, 5000), (1, 300), (2, 3000)):
+        nb = rng.choice(np.arange(3, n), size=k, replace=False)
+        u += [hub] * k
+        v += nb.tolist()
+    pairs = {(min(a, b), max(a, b)) for a, b in zip(u, v) if a != b}
+    uu = np.array([p[0] for p in pairs])
+    vv = np.array([p[1] for p in pairs])
+    ww = rng.integers(1, 4, len(uu)).astype(np.float32)
+    return gen.from_edges(n, uu, vv, ww)
+
+
+DET_GRAPHS = {
+    "ring5x16": lambda: gen.ring_of_cliques(5, 16),
+    "sbm_workload": gen.sbm_workload,
+    "road_60": lambda: gen.road(60),
+    "road_300": lambda: gen.road(300),
+    "gnp_weighted": lambda: gen.gnp(400, 0.03, seed=9, wmax=5),
+    "rmat_12": lambda: gen.rmat(12, 16),
+    "hubs": hub_graph,
+}
+
+
+@pytest.mark.parametrize("name", sorted(DET_GRAPHS))
+def test_deterministic_phases_bit_exact(name):
+    g = DET_GRAPHS[name]()
+    ref = oracle.leiden(g, mode=oracle.SYNC, trace=True)
+    assert ref.status == 0
+    memb, q, st, tr = run_gpu(g, lg.LEIDEN_DETERMINISTIC, trace=True)
+    bad = compare_traces(tr, ref.trace)
+    assert not bad, "\n".join(bad[:10])
+    assert st.passes == ref.passes
+    assert np.array_equal(memb, ref.membership)
+    assert abs(q - ref.modularity) <= Q_REL_REPORT * max(1.0, abs(ref.modularity))
+
+
+@pytest.mark.parametrize("L,B,seed", [(4, 3, 5), (1, 1, 0), (64, 8, 123)])
+def test_deterministic_schedule_parameters(L, B, seed):
+    g = gen.road(120)
+    ref = oracle.leiden(g, mode=oracle.SYNC, schedule_layers=L, schedule_buckets=B, seed=seed, trace=True)
+    memb, q, st, tr = run_gpu(g, lg.LEIDEN_DETERMINISTIC, trace=True, schedule_layers=L, schedule_buckets=B,
+                              seed=seed)
+    assert not compare_traces(tr, ref.trace)
+    assert np.array_equal(memb, ref.membership)
+
+
+def test_deterministic_single_sweep_refinement_and_limits():
+    g = gen.sbm(3000, 12, 0.04, 0.002, seed=4)
+    for kw in ({"flags": lg.FLAG_REFINE_SINGLE_SWEEP}, {"max_passes": 1}, {"max_iterations": 2},
+               {"tolerance": 0.0, "max_iterations": 7}, {"aggregation_tolerance": 0.99}):
+        okw = dict(kw)
+        if "flags" in okw:
+            okw["flags"] = oracle.REFINE_SINGLE_SWEEP
+        ref = oracle.leiden(g, mode=oracle.SYNC, **okw)
+        memb, q, st, _ = run_gpu(g, lg.LEIDEN_DETERMINISTIC, **kw)
+        assert np.array_equal(memb, ref.membership), kw
+
+
+def test_deterministic_repeatable():
+    g = gen.road(200)
+    a = run_gpu(g, lg.LEIDEN_DETERMINISTIC)[0]
+    b = run_gpu(g, lg.LEIDEN_DETERMINISTIC)[0]
+    assert np.array_equal(a, b)
+
+
+ASYNC_GRAPHS = {
+    "ring8x30": lambda: gen.ring_of_cliques(8, 30),
+    "sbm_workload": gen.sbm_workload,
+    "road_300": lambda: gen.road(300),
+    "road_1000": lambda: gen.road(1000),
+    "gnp_weighted": lambda: gen.gnp(2000, 0.004, seed=3, wmax=9),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ASYNC_GRAPHS))
+def test_async_quality_and_connectivity(name):
+    g = ASYNC_GRAPHS[name]()
+    seq = oracle.leiden(g, mode=oracle.SEQ)
+    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC)
+    assert abs(q - seq.modularity) <= Q_TOL_ASYNC, (q, seq.modularity)
+    assert oracle.disconnected(g, memb)[0] == 0
+    q_re = oracle.modularity(g, memb)
+    assert abs(q - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re))
+    # canonical labels: community ids are ranks of the smallest member
+    first = np.unique(memb, return_index=True)[1]
+    assert np.array_equal(np.sort(first), first)
+    assert memb.max() + 1 == st.communities
+
+
+def test_async_hubs_connected_and_consistent():
+    g = hub_graph()
+    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC)
+    assert oracle.disconnected(g, memb)[0] == 0
+    assert abs(q - oracle.modularity(g, memb)) <= Q_REL_REPORT
+    seq = oracle.leiden(g, mode=oracle.SEQ)
+    assert q >= seq.modularity - 0.02  # heavy-tailed graphs are order sensitive (see design notes)
+
+
+@pytest.mark.parametrize("gamma", [0.5, 2.0])
+def test_async_resolution(gamma):
+    g = gen.sbm(3000, 20, 0.05, 0.001, seed=6)
+    seq = oracle.leiden(g, mode=oracle.SEQ, resolution=gamma)
+    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC, resolution=gamma)
+    assert abs(q - seq.modularity) <= Q_TOL_ASYNC
+    assert abs(q - oracle.modularity(g, memb, gamma)) <= Q_REL_REPORT * max(1.0, abs(q))
+    assert oracle.disconnected(g, memb)[0] == 0
+
+
+# ------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("mode", [lg.LEIDEN_ASYNC, lg.LEIDEN_DETERMINISTIC])
+def test_degenerate_graphs(mode):
+    omode = oracle.SEQ if mode == lg.LEIDEN_ASYNC else oracle.SYNC
+    cases = [gen.from_edges(1, [], []), gen.from_edges(6, [], []), gen.from_edges(1, [0], [0], [3.0]),
+             gen.gnp(9, 1.0, seed=2), gen.from_edges(5, [0, 0, 1], [1, 2, 2]),
+             gen.from_edges(10, [0, 0, 1, 5, 5, 6], [1, 2, 2, 6, 7, 7])]
+    for g in cases:
+        ref = oracle.leiden(g, mode=omode)
+        memb, q, st, _ = run_gpu(g, mode)
+        assert np.array_equal(memb, ref.membership), (g.n, memb, ref.membership)
+        assert abs(q - ref.modularity) <= 1e-12
+
+
+def test_empty_graph():
+    import torch
+    h = lg.Leiden(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    memb, q, st = h.run()
+    assert memb.numel() == 0 and q == 0.0
+    h.close()
+
+
+def test_invalid_inputs_rejected():
+    import torch
+    g = gen.ring_of_cliques(4, 4)
+    # asymmetric weights -> NOT_SYMMETRIC with validation
+    w = g.weights.copy()
+    w[0] = 2.0
+    with pytest.raises(lg.LeidenError) as e:
+        lg.Leiden(g.offsets, g.indices, w, validate=True)
+    assert e.value.status == -2
+    # index out of range -> INVALID with validation
+    idx = g.indices.copy()
+    idx[5] = g.n + 3
+    with pytest.raises(lg.LeidenError) as e:
+        lg.Leiden(g.offsets, idx, g.weights, validate=True)
+    assert e.value.status == -1
+    # negative weight -> INVALID
+    w = g.weights.copy()
+    w[:] = -1.0
+    with pytest.raises(lg.LeidenError) as e:
+        lg.Leiden(g.offsets, g.indices, w, validate=True)
+    assert e.value.status == -1
+    # deterministic mode needs integer weights, resolution 1 and 2m < 2^31
+    h = lg.Leiden(g.offsets, g.indices, g.weights * 0.5)
+    with pytest.raises(lg.LeidenError) as e:
+        h.run(mode=lg.LEIDEN_DETERMINISTIC)
+    assert e.value.status == -6
+    h.close()
+    h = lg.Leiden(g.offsets, g.indices, g.weights)
+    with pytest.raises(lg.LeidenError) as e:
+        h.run(mode=lg.LEIDEN_DETERMINISTIC, resolution=0.5)
+    assert e.value.status == -6
+    with pytest.raises(lg.LeidenError) as e:
+        h.run(max_iterations=0)
+    assert e.value.status == -1
+    h.close()
+    h = lg.Leiden(g.offsets, g.indices, np.full_like(g.weights, 2.0 ** 26))
+    with pytest.raises(lg.LeidenError) as e:
+        h.run(mode=lg.LEIDEN_DETERMINISTIC)
+    assert e.value.status == -7
+    h.close()
+
+
+def test_host_buffers_round_trip():
+    """leiden_create from host arrays and leiden_run into a host buffer."""
+    import ctypes
+    g = gen.sbm(1500, 6, 0.05, 0.002, seed=8)
+    off = np.ascontiguousarray(g.offsets)
+    idx = np.ascontiguousarray(g.indices)
+    w = np.ascontiguousarray(g.weights)
+    h = lg.leiden_create(g.n, g.nnz, off.ctypes.data_as(ctypes.c_void_p), idx.ctypes.data_as(ctypes.c_void_p),
+                         w.ctypes.data_as(ctypes.c_void_p), lg.LEIDEN_HOST, 1, None)
+    out = np.zeros(g.n, np.int32)
+    p = lg.leiden_params_default()
+    p.mode = lg.LEIDEN_DETERMINISTIC
+    q, st = lg.leiden_run(h, p, out.ctypes.data_as(ctypes.c_void_p), lg.LEIDEN_HOST)
+    lg.leiden_destroy(h)
+    ref = oracle.leiden(g, mode=oracle.SYNC)
+    assert np.array_equal(out, ref.membership)
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.3])
+def test_modularity_entry_point(gamma):
+    import torch
+    g = gen.road(100)
+    rng = np.random.default_rng(1)
+    dev = torch.device("cuda")
+    off = torch.as_tensor(g.offsets).to(dev)
+    idx = torch.as_tensor(g.indices).to(dev)
+    w = torch.as_tensor(g.weights).to(dev)
+    for labels in (rng.integers(0, 50, g.n), np.arange(g.n), np.zeros(g.n), np.arange(g.n) // 100):
+        m = torch.as_tensor(labels.astype(np.int32)).to(dev)
+        q = lg.modularity(off, idx, w, m, gamma)
+        want = oracle.modularity(g, labels.astype(np.int32), gamma)
+        assert abs(q - want) <= 1e-9 * max(1.0, abs(want))
