@@ -34,7 +34,7 @@ struct Scalars {  // device scalars, read back in one copy
     long long dq_i;
     unsigned long long moved;
     double wsum;
-    double msum[3];
+    double msum[4];
     int32_t maxdeg;
     int32_t pad;
     unsigned long long maxtdeg;
@@ -523,6 +523,8 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(cudaMemcpyAsync(ako, q.key_off, sizeof(ako), cudaMemcpyDeviceToHost, s));
         ST(q.sync_scalars());
         ST(q.ensure_agg(dst, cap));
+        // rows of communities without edges (bin 0) are never visited: empty
+        CK(cudaMemsetAsync(q.agg[dst].deg, 0, sizeof(int32_t) * ncomm, s));
         {
             int64_t mt = (int64_t)q.hsc->maxtdeg;
             if (mt > ncomm) mt = ncomm;
@@ -607,7 +609,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     q.launches += 7;
     // modularity (Eq. 1) of the result on the input graph
     CK(cudaMemsetAsync(q.sigtot, 0, sizeof(double) * n0, s));
-    CK(cudaMemsetAsync(q.dsc->msum, 0, sizeof(double) * 3, s));
+    CK(cudaMemsetAsync(q.dsc->msum, 0, sizeof(double) * 4, s));
     CK(launch_modularity_parts(n0, q.off0, q.idx0, q.w0, outp, q.sigtot, q.dsc->msum, s));
     CK(launch_sum_squares(q.sigtot, n0, &q.dsc->msum[2], s));
     q.launches += 2;
@@ -665,15 +667,15 @@ leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *id
         set_last_error("scratch allocation failed");
         return LEIDEN_ERR_OOM;
     }
-    e = cudaMallocAsync(&sums, sizeof(double) * 3, s);
+    e = cudaMallocAsync(&sums, sizeof(double) * 4, s);
     if (e != cudaSuccess) {
         cudaFreeAsync(sig, s);
         set_last_error("scratch allocation failed");
         return LEIDEN_ERR_OOM;
     }
-    double h[3] = {0, 0, 0};
+    double h[4] = {0, 0, 0, 0};
     cudaMemsetAsync(sig, 0, sizeof(double) * n, s);
-    cudaMemsetAsync(sums, 0, sizeof(double) * 3, s);
+    cudaMemsetAsync(sums, 0, sizeof(double) * 4, s);
     launch_modularity_parts(n, off, idx, w, memb, sig, sums, s);
     launch_sum_squares(sig, n, &sums[2], s);
     cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -683,6 +685,10 @@ leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *id
     if (e != cudaSuccess) {
         set_last_error(std::string("leiden_modularity: ") + cudaGetErrorString(e));
         return LEIDEN_ERR_CUDA;
+    }
+    if (h[3] != 0.0) {
+        set_last_error("leiden_modularity: membership labels must lie in [0, n)");
+        return LEIDEN_ERR_INVALID;
     }
     *q_out = h[1] > 0 ? h[0] / h[1] - gamma * h[2] / (h[1] * h[1]) : 0.0;
     return LEIDEN_OK;

@@ -83,6 +83,10 @@ __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t 
     double intra = 0, tot = 0;
     GRID_STRIDE(i, n) {
         const int32_t ci = C[i];
+        if (ci < 0 || ci >= n) {  // label out of range: counted in sums[3], not used
+            atomicAdd(&sums[3], 1.0);
+            continue;
+        }
         double k = 0, in = 0;
         for (int64_t e = off[i]; e < off[i + 1]; ++e) {
             const double x = w ? (double)w[e] : 1.0;

@@ -144,7 +144,8 @@ cudaError_t launch_first_flags(const int32_t *C0, const int32_t *minv, int64_t n
 cudaError_t launch_canonical(const int32_t *C0, const int32_t *minv, const int64_t *rank, int64_t n0, int32_t *out,
                              cudaStream_t s);
 // modularity (Eq. 1) of labels C (in [0,n)) on a plain CSR: sums[0] += intra
-// weight, sums[1] += 2m, sigtot[c] += K_i; then sums[2] += sum_c sigtot[c]^2
+// weight, sums[1] += 2m, sigtot[c] += K_i, sums[3] += labels out of range;
+// then sums[2] += sum_c sigtot[c]^2
 cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                     const int32_t *C, double *sigtot, double *sums, cudaStream_t s);
 cudaError_t launch_sum_squares(const double *x, int64_t n, double *out, cudaStream_t s);

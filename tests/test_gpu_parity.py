@@ -3,7 +3,8 @@
 Deterministic mode: every phase of every pass (local-moving, refinement,
 counts, renumbering, dendrogram, aggregated holey CSR with rows compared as
 sets) and the final membership are bit-exact against oracle SYNC.
-Asynchronous mode: modularity within 0.005 of oracle SEQ, every community
+Asynchronous mode: modularity no lower than oracle SEQ's minus 0.005 (a
+higher value is a better partition, not a mismatch), every community
 connected (Algorithm 5) and the reported modularity within 1e-9 relative of
 the oracle's recomputation from the returned membership.
 """
@@ -110,7 +111,7 @@ def test_async_quality_and_connectivity(name):
     g = ASYNC_GRAPHS[name]()
     seq = oracle.leiden(g, mode=oracle.SEQ)
     memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC)
-    assert abs(q - seq.modularity) <= Q_TOL_ASYNC, (q, seq.modularity)
+    assert q >= seq.modularity - Q_TOL_ASYNC, (q, seq.modularity)
     assert oracle.disconnected(g, memb)[0] == 0
     q_re = oracle.modularity(g, memb)
     assert abs(q - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re))
@@ -134,7 +135,7 @@ def test_async_resolution(gamma):
     g = gen.sbm(3000, 20, 0.05, 0.001, seed=6)
     seq = oracle.leiden(g, mode=oracle.SEQ, resolution=gamma)
     memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC, resolution=gamma)
-    assert abs(q - seq.modularity) <= Q_TOL_ASYNC
+    assert q >= seq.modularity - Q_TOL_ASYNC
     assert abs(q - oracle.modularity(g, memb, gamma)) <= Q_REL_REPORT * max(1.0, abs(q))
     assert oracle.disconnected(g, memb)[0] == 0
 
