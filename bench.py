@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Leiden edges/s on one GB300.
+
+One step is one leiden_run (every phase of the method: local-moving,
+refinement, aggregation over all passes, final labels and modularity) on the
+road-network workload: a 5000 x 5000 lattice with 10% of its edges dropped,
+1% diagonal shortcuts and integer weights in [1, 10] (25M vertices, ~91M
+directed CSR entries). value = directed CSR entries / step time, with the
+input resident in HBM. Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own replica
+of the workload: the method has no data-parallel split of one graph, so the
+multi-GPU form is independent replicas ("scaling": "weak").
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Leiden edges/s on 1 GB300 (% HBM roofline); batched graphs/s, p99 latency"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="road", choices=["road", "sbm", "rmat"])
+    ap.add_argument("--side", type=int, default=5000, help="road lattice side")
+    ap.add_argument("--rmat-scale", type=int, default=25)
+    ap.add_argument("--mode", default="async", choices=["async", "det"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-side", type=int, default=3000, help="road side of the CPU-baseline sample")
+    ap.add_argument("--ref-side", type=int, default=1500, help="road side of each reference-arm step")
+    return ap.parse_args()
+
+
+def workload(args):
+    import gen
+    if args.workload == "road":
+        g = gen.road(args.side, 0.10, 0.01, 1, 10, seed=2)
+        name = (f"road lattice {args.side}x{args.side}, 10% edges dropped, 1% diagonal shortcuts, "
+                f"integer weights 1-10, seed 2")
+    elif args.workload == "sbm":
+        g = gen.sbm_workload()
+        name = "SBM 10,000 vertices, 50 blocks, p_in 0.05, p_out 0.0005, seed 1"
+    else:
+        g = gen.rmat(args.rmat_scale, 56, 0.57, 0.19, 0.19, seed=3)
+        name = f"R-MAT scale {args.rmat_scale}, edge factor 56, (0.57,0.19,0.19,0.05), seed 3"
+    return g, name
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("k_sweep.cu", "k_aggregate.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2312_13936_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(cls_name, workload_name):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary,
+    if it was taken on the current kernel sources and this workload."""
+    try:
+        with open(TRAFFIC) as f:
+            t = json.load(f)
+        if t.get("source_hash") != kernel_source_hash() or t.get("workload") != workload_name:
+            return None
+        return t["classes"].get(cls_name, {}).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def cpu_baseline(side):
+    import gen
+    import oracle
+    g = gen.road(side, 0.10, 0.01, 1, 10, seed=2)
+    t = time.perf_counter()
+    r = oracle.leiden(g, mode=oracle.SEQ)
+    dt = time.perf_counter() - t
+    assert r.status == 0
+    return {"value": g.nnz / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one sequential oracle run (SEQ mode) on the same recipe at side {side}: "
+                       f"{g.n} vertices, {g.nnz} directed entries, {dt:.1f} s on 1 host core "
+                       f"of {os.cpu_count()}")}
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle timed on host cores, same metric and unit."""
+    if rank != 0:
+        return
+    import gen
+    import oracle
+    g = gen.road(args.ref_side, 0.10, 0.01, 1, 10, seed=2)
+    for _ in range(args.warmup):
+        oracle.leiden(g, mode=oracle.SEQ)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.leiden(g, mode=oracle.SEQ)
+    dt = time.perf_counter() - t
+    value = args.steps * g.nnz / dt
+    sample = (f"each step one sequential oracle run (SEQ mode) on the road recipe at side {args.ref_side}: "
+              f"{g.n} vertices, {g.nnz} directed entries, 1 host core of {os.cpu_count()}")
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "edges/s", "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"road lattice {args.ref_side}x{args.ref_side} (bounded sample of the "
+                               f"{args.side}x{args.side} workload)", "modularity": r.modularity},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2312_13936_gb300 as lg
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    g, wname = workload(args)
+    mode = lg.LEIDEN_ASYNC if args.mode == "async" else lg.LEIDEN_DETERMINISTIC
+    dev = torch.device("cuda", local)
+    off = torch.as_tensor(g.offsets).to(dev)
+    idx = torch.as_tensor(g.indices).to(dev)
+    w = torch.as_tensor(g.weights).to(dev)
+    stream = torch.cuda.current_stream()
+    h = lg.Leiden(off, idx, w)
+    for _ in range(args.warmup):
+        h.run(mode=mode)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the run's stream)
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prof = {}
+    launches = 0
+    qs = []
+    for _ in range(args.steps):
+        memb, q, st = h.run(mode=mode, flags=lg.FLAG_PROFILE)
+        qs.append(q)
+        launches += st.kernel_launches
+        for k, v in h.profile().items():
+            a = prof.setdefault(k, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            a["launches"] += v["launches"]
+            a["ms"] += v["ms"]
+            a["bytes"] += v["bytes"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    value = world * args.steps * g.nnz / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (H2D and D2H inside)
+    e2e = None
+    if not args.no_e2e:
+        import ctypes
+        hoff = np.ascontiguousarray(g.offsets)
+        hidx = np.ascontiguousarray(g.indices)
+        hw = np.ascontiguousarray(g.weights)
+        out = np.zeros(g.n, np.int32)
+        P = lg.leiden_params_default()
+        P.mode = mode
+        vp = ctypes.c_void_p
+
+        def one():
+            hh = lg.leiden_create(g.n, g.nnz, vp(hoff.ctypes.data), vp(hidx.ctypes.data), vp(hw.ctypes.data),
+                                  lg.LEIDEN_HOST, 0, vp(stream.cuda_stream))
+            lg.leiden_run(hh, P, vp(out.ctypes.data), lg.LEIDEN_HOST)
+            lg.leiden_destroy(hh)
+        one()
+        ne = max(2, args.steps // 2)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            one()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * ne * g.nnz / te, "unit": "edges/s",
+               "h2d_bytes_per_step": hoff.nbytes + hidx.nbytes + hw.nbytes, "d2h_bytes_per_step": out.nbytes + 8}
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    # ---- roofline of the dominant kernel class (algorithmic bytes / event time)
+    peak, peak_kind = hbm_peak()
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    roofline = None
+    if top:
+        (phase, binname), a = top
+        achieved = a["bytes"] / (a["ms"] / 1e3) / 1e9
+        cls = f"{phase}/{binname}"
+        traffic = traffic_for(cls, wname)
+        total_ms = sum(v["ms"] for v in prof.values())
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "kernel": cls, "peak_source": f"{peak_kind} hbm_gbs",
+                    "bytes_per_launch": a["bytes"] / a["launches"], "ms_per_launch": a["ms"] / a["launches"],
+                    "share_of_profiled_ms": a["ms"] / total_ms}
+    cpu = None if (args.no_cpu or world > 1) else cpu_baseline(args.cpu_side)
+    line = {
+        "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wname, "n": g.n, "nnz": g.nnz, "mode": args.mode,
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
+                       (g.offsets.nbytes + g.indices.nbytes + g.weights.nbytes) / 1e9),
+                   "modularity": statistics.median(qs), "passes": st.passes,
+                   "move_sweeps": st.move_iterations, "refine_sweeps": st.refine_iterations,
+                   "phase_ms": {"move": st.ms_move, "refine": st.ms_refine, "aggregate": st.ms_aggregate,
+                                "other": st.ms_other}},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
+        "kernel_classes": {f"{k[0]}/{k[1]}": v for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

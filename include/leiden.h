@@ -62,7 +62,8 @@ enum { LEIDEN_ASYNC = 0, LEIDEN_DETERMINISTIC = 1 };
 enum {
     LEIDEN_FLAG_VALIDATE = 1u,            /* check symmetry and weights on device */
     LEIDEN_FLAG_REFINE_SINGLE_SWEEP = 2u, /* one refinement sweep, as Algorithm 3 prints it */
-    LEIDEN_FLAG_TRACE = 4u                /* keep per-pass intermediate results (leiden_trace_get) */
+    LEIDEN_FLAG_TRACE = 4u,               /* keep per-pass intermediate results (leiden_trace_get) */
+    LEIDEN_FLAG_PROFILE = 8u              /* time every sweep/aggregation launch (leiden_profile_get) */
 };
 
 typedef struct {
@@ -90,6 +91,26 @@ typedef struct {
     double ms_move, ms_refine, ms_aggregate, ms_other; /* per-phase device time */
     int64_t kernel_launches;      /* kernels launched by the call */
 } leiden_stats;
+
+/* Per-kernel-class profile of the last leiden_run made with
+ * LEIDEN_FLAG_PROFILE. Class index = phase * 8 + bin, with phase 0 the
+ * local-moving sweep (Algorithm 2), 1 the refinement sweep (Algorithm 3), 2
+ * the aggregation (Algorithm 4), and bin 1..7 the degree bin (tile of
+ * 4/8/16/32 lanes, warp table, block table, global table). bytes counts the
+ * algorithmic bytes of the launches (each array element the method reads or
+ * writes counted once at its own size; random gathers count their element,
+ * not the memory sector), from work counters the kernels accumulate. */
+typedef struct {
+    int64_t launches;  /* kernel launches of this class */
+    double ms;         /* device time of those launches (CUDA events on the run's stream) */
+    double bytes;      /* algorithmic bytes */
+    int64_t items;     /* vertices (communities) evaluated */
+    int64_t skipped;   /* listed vertices skipped (pruned or not isolated) */
+    int64_t edges;     /* CSR entries scanned */
+    int64_t distinct;  /* distinct neighbour communities accumulated */
+    int64_t moved;     /* moves made or proposed (entries written, aggregation) */
+} leiden_kernel_profile;
+enum { LEIDEN_PROFILE_CLASSES = 24 };
 
 typedef struct leiden_graph_s *leiden_graph_t;
 
@@ -136,6 +157,11 @@ leiden_status leiden_modularity(int64_t n, const int64_t *offsets, const int32_t
  * copied to host memory dst. Returns LEIDEN_ERR_INVALID if the pass or item
  * was not recorded. */
 leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, void *dst, int64_t *count);
+
+/* Copy the LEIDEN_PROFILE_CLASSES entries of the last profiled run into
+ * out (host memory). Returns LEIDEN_ERR_INVALID if the last run was not
+ * profiled. */
+leiden_status leiden_profile_get(leiden_graph_t g, leiden_kernel_profile *out);
 
 /* Human-readable name of a status code. */
 const char *leiden_status_string(int32_t status);

@@ -19,14 +19,18 @@ from . import _build
 
 __all__ = [
     "LEIDEN_HOST", "LEIDEN_DEVICE", "LEIDEN_ASYNC", "LEIDEN_DETERMINISTIC", "FLAG_VALIDATE",
-    "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "LeidenError", "Params", "Stats", "library", "leiden_params_default",
-    "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity", "leiden_trace_get",
+    "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "FLAG_PROFILE", "LeidenError", "Params", "Stats", "KernelProfile",
+    "library", "leiden_params_default", "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity",
+    "leiden_trace_get", "leiden_profile_get",
     "leiden_status_string", "leiden_last_error", "Leiden", "modularity",
 ]
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
 LEIDEN_ASYNC, LEIDEN_DETERMINISTIC = 0, 1
-FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE = 1, 2, 4
+FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE, FLAG_PROFILE = 1, 2, 4, 8
+PROFILE_CLASSES = 24
+PROFILE_PHASES = ("move", "refine", "aggregate")
+PROFILE_BINS = (None, "tile4", "tile8", "tile16", "tile32", "warp", "block", "global")
 TRACE_INIT, TRACE_MOVE, TRACE_REFINE, TRACE_COUNTS, TRACE_RENUMBER = 1, 2, 3, 4, 5
 TRACE_AGG_OFF, TRACE_AGG_DEG, TRACE_AGG_IDX, TRACE_AGG_W, TRACE_DENDRO = 6, 7, 8, 9, 10
 _TRACE_DTYPE = {1: np.int32, 2: np.int32, 3: np.int32, 4: np.int64, 5: np.int32, 6: np.int64, 7: np.int32,
@@ -58,6 +62,12 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("items", ctypes.c_int64), ("skipped", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("distinct", ctypes.c_int64), ("moved", ctypes.c_int64)]
+
+
 _LIB = None
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 
@@ -80,8 +90,9 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.leiden_modularity.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.c_double, _VP,
                                           ctypes.POINTER(ctypes.c_double)]
         lib.leiden_trace_get.argtypes = [_VP, _I32, _I32, _VP, ctypes.POINTER(_I64)]
+        lib.leiden_profile_get.argtypes = [_VP, ctypes.POINTER(KernelProfile)]
         for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
-                  lib.leiden_trace_get):
+                  lib.leiden_trace_get, lib.leiden_profile_get):
             f.restype = ctypes.c_int
         lib.leiden_status_string.argtypes = [_I32]
         lib.leiden_status_string.restype = ctypes.c_char_p
@@ -145,6 +156,18 @@ def leiden_trace_get(handle, pass_: int, what: int):
     return out[:cnt.value]
 
 
+def leiden_profile_get(handle):
+    """Per-class profile of the last profiled run: {(phase, bin): dict}."""
+    arr = (KernelProfile * PROFILE_CLASSES)()
+    _check(library().leiden_profile_get(handle, arr))
+    out = {}
+    for k in range(PROFILE_CLASSES):
+        e = arr[k]
+        if e.launches:
+            out[(PROFILE_PHASES[k // 8], PROFILE_BINS[k % 8])] = {f: getattr(e, f) for f, _ in e._fields_}
+    return out
+
+
 def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -194,6 +217,9 @@ class Leiden:
 
     def trace(self, pass_: int, what: int):
         return leiden_trace_get(self.handle, pass_, what)
+
+    def profile(self):
+        return leiden_profile_get(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

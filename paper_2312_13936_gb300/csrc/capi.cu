@@ -89,6 +89,14 @@ leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, voi
     return g->h.trace_get(pass, what, dst, count);
 }
 
+leiden_status leiden_profile_get(leiden_graph_t g, leiden_kernel_profile *out) {
+    if (!g) {
+        lgb::set_last_error("NULL handle");
+        return LEIDEN_ERR_INVALID;
+    }
+    return g->h.profile_get(out);
+}
+
 const char *leiden_status_string(int32_t s) {
     switch (s) {
         case LEIDEN_OK: return "LEIDEN_OK";

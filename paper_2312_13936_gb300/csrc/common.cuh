@@ -104,6 +104,18 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Profiling counters: every lane holds partial counts; one atomic per warp.
+struct ProfCounts {
+    unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
+    __device__ __forceinline__ void flush(unsigned long long *dst) {
+        if (!dst) return;
+        for (int k = 0; k < 6; ++k) {
+            const unsigned long long s = warp_sum(v[k]);
+            if ((threadIdx.x & 31) == 0 && s) atomicAdd(&dst[k], s);
+        }
+    }
+};
+
 // Device error word: kernels record the first failure here instead of
 // trapping; the host reads it after each phase.
 enum : int { kErrNone = 0, kErrHashFull = 1, kErrBadIndex = 2 };

@@ -102,8 +102,26 @@ struct Handle::Impl {
     std::map<std::pair<int, int>, std::vector<char>> trace;
     std::map<std::pair<int, int>, int64_t> trace_count;
     std::vector<void *> allocs;
+    // profiling (LEIDEN_FLAG_PROFILE)
+    unsigned long long *prof_cnt = nullptr;  // LEIDEN_PROFILE_CLASSES x kProfCounters
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> prof_spans;  // (class, index of the start event)
+    std::vector<int64_t> prof_launches;
+    leiden_kernel_profile prof_out[LEIDEN_PROFILE_CLASSES];
+    bool prof_valid = false;
+
+    cudaEvent_t next_event() {
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ev_pool.push_back(e);
+        }
+        return ev_pool[ev_used++];
+    }
 
     ~Impl() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         for (void *p : allocs) cudaFreeAsync(p, s);
         if (hsc) cudaFreeHost(hsc);
         cudaStreamSynchronize(s);
@@ -162,6 +180,47 @@ struct Handle::Impl {
         hub_vals = v;
         hub_bytes = need;
         (void)det;
+        return LEIDEN_OK;
+    }
+    // Sum the event spans per class and turn the work counters into
+    // algorithmic bytes (element sizes of what each kernel reads and writes).
+    leiden_status finish_profile() {
+        std::vector<unsigned long long> c((size_t)LEIDEN_PROFILE_CLASSES * kProfCounters);
+        CK(cudaMemcpyAsync(c.data(), prof_cnt, c.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::memset(prof_out, 0, sizeof(prof_out));
+        for (auto &sp : prof_spans) {
+            float t = 0;
+            cudaEventElapsedTime(&t, ev_pool[sp.second], ev_pool[sp.second + 1]);
+            prof_out[sp.first].ms += t;
+        }
+        for (int k = 0; k < LEIDEN_PROFILE_CLASSES; ++k) {
+            const unsigned long long *v = &c[(size_t)k * kProfCounters];
+            leiden_kernel_profile &o = prof_out[k];
+            o.launches = prof_launches[k];
+            const int phase = k / 8;
+            if (phase < 2) {
+                o.items = (int64_t)v[0];
+                o.skipped = (int64_t)v[1];
+                o.edges = (int64_t)v[2];
+                o.distinct = (int64_t)v[3];
+                o.moved = (int64_t)v[4];
+                if (phase == 0)  // list, flag r/w, C, K, offset, degree, Sigma_d | idx, w, C[j] | Sigma_c | move
+                    o.bytes = 38.0 * v[0] + 5.0 * v[1] + 12.0 * v[2] + 8.0 * v[3] + 28.0 * v[4] + 1.0 * v[5];
+                else  // + bound C'_B of i and of every neighbour, isolation test, proposal write
+                    o.bytes = 48.0 * v[0] + 16.0 * v[1] + 16.0 * v[2] + 8.0 * v[3];
+            } else {
+                o.items = (int64_t)v[0];
+                o.edges = (int64_t)v[2];
+                o.moved = (int64_t)v[3];
+                o.skipped = 0;
+                o.distinct = (int64_t)v[3];
+                // community: list, offsets in/out, fill, K''; member: id, offset, degree;
+                // edge: idx, w, label; written entry: idx, w
+                o.bytes = 48.0 * v[0] + 16.0 * v[1] + 12.0 * v[2] + 8.0 * v[3];
+            }
+        }
+        prof_valid = true;
         return LEIDEN_OK;
     }
     leiden_status ensure_agg(int x, int64_t cap) {
@@ -239,6 +298,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     q.scan_tmp = tmp;
     ST(q.alloc(&q.sfstart, 4096 + 1));
     ST(q.alloc(&q.sfcount, 4096 + 1));
+    ST(q.alloc(&q.prof_cnt, (int64_t)LEIDEN_PROFILE_CLASSES * kProfCounters));
     q.key_cap = 8192;
     ST(q.alloc(&q.key_cnt, q.key_cap));
     ST(q.alloc(&q.key_off, q.key_cap + 1));
@@ -307,6 +367,24 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     q.trace.clear();
     q.trace_count.clear();
     q.launches = 0;
+    const bool profile = (prm.flags & LEIDEN_FLAG_PROFILE) != 0;
+    q.prof_valid = false;
+    q.ev_used = 0;
+    q.prof_spans.clear();
+    q.prof_launches.assign(LEIDEN_PROFILE_CLASSES, 0);
+    if (profile)
+        CK(cudaMemsetAsync(q.prof_cnt, 0, sizeof(unsigned long long) * LEIDEN_PROFILE_CLASSES * kProfCounters, s));
+    // brackets one profiled launch of class cls with events on the run's stream
+    auto prof_begin = [&](int cls) -> unsigned long long * {
+        if (!profile) return nullptr;
+        q.prof_spans.push_back({cls, q.ev_used});
+        cudaEventRecord(q.next_event(), s);
+        q.prof_launches[cls]++;
+        return q.prof_cnt + (size_t)cls * kProfCounters;
+    };
+    auto prof_end = [&]() {
+        if (profile) cudaEventRecord(q.next_event(), s);
+    };
     cudaEvent_t ev0, ev1;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
@@ -418,7 +496,9 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                     const int64_t lo = ko[k * kNumBins + b], hi = ko[k * kNumBins + b + 1];
                     if (hi == lo) continue;
                     const int mb = b <= 5 ? tile_blocks : (b == 6 ? big_blocks : hub_regions);
+                    sc.prof = prof_begin((refine ? 8 : 0) + b);
                     CK(launch_sweep_eval(sc, b, q.list + lo, hi - lo, mb, s));
+                    prof_end();
                     q.launches++;
                 }
                 if (refine) {
@@ -556,7 +636,9 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                 const int64_t lo = ako[b], hi = ako[b + 1];
                 if (hi == lo) continue;
                 const int mb = b <= 5 ? tile_blocks : (b == 6 ? big_blocks : aregions);
+                ac.prof = prof_begin(16 + b);
                 CK(launch_aggregate(ac, b, q.list + lo, hi - lo, mb, s));
+                prof_end();
                 q.launches++;
             }
         }
@@ -646,6 +728,16 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     for (auto &m : marks) cudaEventDestroy(m.first);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
+    if (profile) ST(q.finish_profile());
+    return LEIDEN_OK;
+}
+
+leiden_status Handle::profile_get(leiden_kernel_profile *out) const {
+    if (!p->prof_valid || !out) {
+        set_last_error("the last run was not profiled");
+        return LEIDEN_ERR_INVALID;
+    }
+    std::memcpy(out, p->prof_out, sizeof(p->prof_out));
     return LEIDEN_OK;
 }
 

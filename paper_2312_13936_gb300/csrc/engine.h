@@ -22,6 +22,7 @@ class Handle {
                          int where, int validate, void *stream);
     leiden_status run(const leiden_params &p, int32_t *membership, int where, double *modularity, leiden_stats *stats);
     leiden_status trace_get(int pass, int what, void *dst, int64_t *count) const;
+    leiden_status profile_get(leiden_kernel_profile *out) const;
 
   private:
     struct Impl;

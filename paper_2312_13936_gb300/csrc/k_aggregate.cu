@@ -35,6 +35,7 @@ template <class P, class Wi, class Wo> struct AV {
     int hub_bits;
     int64_t ncomm;
     int *err;
+    unsigned long long *prof;
 };
 
 template <class P, class Wi, class Wo> AV<P, Wi, Wo> aview(const AggCtx &c) {
@@ -57,6 +58,7 @@ template <class P, class Wi, class Wo> AV<P, Wi, Wo> aview(const AggCtx &c) {
     a.hub_bits = c.hub_bits;
     a.ncomm = c.ncomm;
     a.err = c.err;
+    a.prof = c.prof;
     return a;
 }
 
@@ -72,6 +74,7 @@ __global__ void __launch_bounds__(256) k_agg_tile(AV<P, Wi, Wo> a, const int32_t
     const int base_lane = lane & ~(T - 1);
     const unsigned tmask = (T == 32) ? kFull : (((1u << T) - 1u) << base_lane);
     const int64_t tiles = (int64_t)gridDim.x * (blockDim.x / T);
+    ProfCounts pc;
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; t < count; t += tiles) {
         const int32_t c = list[t];
         const int64_t m0 = a.coff[c];
@@ -135,8 +138,13 @@ __global__ void __launch_bounds__(256) k_agg_tile(AV<P, Wi, Wo> a, const int32_t
         if (tl == 0) {
             a.out_deg[c] = __popc(ball);
             a.out_K[c] = kpart;
+            pc.v[0]++;
+            pc.v[1] += nm;
+            pc.v[2] += total;
+            pc.v[3] += __popc(ball);
         }
     }
+    pc.flush(a.prof);
 }
 
 // insert all member edges of community c into a table (threads of a warp
@@ -164,6 +172,7 @@ __global__ void __launch_bounds__(256) k_agg_warp(AV<P, Wi, Wo> a, const int32_t
     int32_t *keys = skeys[wib];
     A *vals = svals[wib];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    ProfCounts pc;
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; t < count; t += nwarps) {
         const int32_t c = list[t];
         const int64_t m0 = a.coff[c];
@@ -199,9 +208,14 @@ __global__ void __launch_bounds__(256) k_agg_warp(AV<P, Wi, Wo> a, const int32_t
         if (lane == 0) {
             a.out_deg[c] = written;
             a.out_K[c] = kpart;
+            pc.v[0]++;
+            pc.v[1] += nm;
+            pc.v[2] += cap;
+            pc.v[3] += written;
         }
         __syncwarp();
     }
+    pc.flush(a.prof);
 }
 
 // ------------------------------------------------ block / hub table bins
@@ -224,6 +238,7 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
         keys = reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
     }
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
+    ProfCounts pc;
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
         const int32_t c = list[t];
         const int64_t m0 = a.coff[c];
@@ -279,8 +294,13 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
             for (int w2 = 0; w2 < nw; ++w2) ks += s_k[w2];
             a.out_deg[c] = s_written;
             a.out_K[c] = ks;
+            pc.v[0]++;
+            pc.v[1] += nm;
+            pc.v[2] += a.out_off[c + 1] - a.out_off[c];
+            pc.v[3] += s_written;
         }
     }
+    pc.flush(a.prof);
 }
 
 template <class P, class Wi, class Wo>

@@ -45,6 +45,7 @@ template <class P, class W> struct SV {
     A *hub_vals;
     int hub_bits;
     int *err;
+    unsigned long long *prof;
 };
 
 template <class P, class W> SV<P, W> view(const SweepCtx &c) {
@@ -73,6 +74,7 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.hub_vals = static_cast<A *>(c.hub_vals);
     a.hub_bits = c.hub_bits;
     a.err = c.err;
+    a.prof = c.prof;
     return a;
 }
 
@@ -140,9 +142,11 @@ __device__ __forceinline__ bool take_vertex(const SV<P, W> &a, int32_t v, int32_
         d = a.C[v];
         return __ldg(&a.size[d]) == 1;
     }
-    d = a.C[v];
     const bool e = a.unproc[v] != 0;
-    if (e) a.unproc[v] = 0;
+    if (e) {
+        a.unproc[v] = 0;
+        d = a.C[v];
+    }
     return e;
 }
 
@@ -155,6 +159,7 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
     const unsigned tmask = (T == 32) ? kFull : (((1u << T) - 1u) << (lane & ~(T - 1)));
     const int64_t tiles = (int64_t)gridDim.x * (blockDim.x / T);
     A local_gain = 0;
+    ProfCounts pc;
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; t < count; t += tiles) {
         const int32_t v = list[t];
         int32_t d = 0;
@@ -164,6 +169,7 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
         d = __shfl_sync(tmask, d, 0, T);
         if (!elig) {
             if (tl == 0 && (REFINE || P::det)) a.prop[v] = -1;
+            if (tl == 0) pc.v[1]++;
             continue;
         }
         const A Kv = a.K[v];
@@ -213,6 +219,19 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
         }
         int mv = 0;
         if (tl == 0) mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain) ? 1 : 0;
+        if (a.prof) {
+            const unsigned lb = __ballot_sync(tmask, lead) & tmask;
+            if (tl == 0) {
+                pc.v[0]++;
+                pc.v[2] += dv;
+                pc.v[3] += __popc(lb);
+                const bool any = (REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0);
+                if (any) {
+                    pc.v[4]++;
+                    pc.v[5] += dv;
+                }
+            }
+        }
         if (!REFINE && !P::det) {
             mv = __shfl_sync(tmask, mv, 0, T);
             if (mv && tl < dv) a.unproc[j] = 1;  // neighbours (self-loop included) of a mover
@@ -222,6 +241,7 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
         const A s = warp_sum(local_gain);
         if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
     }
+    pc.flush(a.prof);
 }
 
 // ------------------------------------------------------- warp-table bin
@@ -236,6 +256,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
     A *vals = svals[wib];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     A local_gain = 0;
+    ProfCounts pc;
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; t < count; t += nwarps) {
         const int32_t v = list[t];
         int32_t d = 0;
@@ -245,6 +266,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
         d = __shfl_sync(kFull, d, 0);
         if (!elig) {
             if (lane == 0 && (REFINE || P::det)) a.prop[v] = -1;
+            if (lane == 0) pc.v[1]++;
             continue;
         }
         const A Kv = a.K[v];
@@ -272,6 +294,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
         for (int s = lane; s < S; s += 32) {
             const int32_t k = keys[s];
             if (k < 0) continue;
+            pc.v[3]++;
             const A sum = vals[s];
             if (k == d) {
                 kvd = sum;
@@ -293,7 +316,15 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
         }
         kvd = warp_sum(kvd);
         int mv = 0;
-        if (lane == 0) mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain) ? 1 : 0;
+        if (lane == 0) {
+            mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain) ? 1 : 0;
+            pc.v[0]++;
+            pc.v[2] += dv;
+            if ((REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0)) {
+                pc.v[4]++;
+                pc.v[5] += dv;
+            }
+        }
         if (!REFINE && !P::det) {
             mv = __shfl_sync(kFull, mv, 0);
             if (mv)
@@ -305,6 +336,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
         const A s = warp_sum(local_gain);
         if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
     }
+    pc.flush(a.prof);
 }
 
 // ------------------------------------------------ block / hub table bins
@@ -329,6 +361,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
     }
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     A local_gain = 0;
+    ProfCounts pc;
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
         const int32_t v = list[t];
         __syncthreads();
@@ -337,6 +370,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
             s_elig = take_vertex<P, W, REFINE>(a, v, d) ? 1 : 0;
             s_d = d;
             if (!s_elig && (REFINE || P::det)) a.prop[v] = -1;
+            if (!s_elig) pc.v[1]++;
         }
         __syncthreads();
         if (!s_elig) continue;
@@ -371,6 +405,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
         for (int64_t s = tid; s < S; s += blockDim.x) {
             const int32_t k = keys[s];
             if (k < 0) continue;
+            pc.v[3]++;
             const A sum = vals[s];
             if (k == d) {
                 kvd = sum;
@@ -408,6 +443,12 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
                 kd += s_kvd[w2];
             }
             s_mv = decide<P, W, REFINE>(a, v, d, Kv, bk, bc, kd, local_gain) ? 1 : 0;
+            pc.v[0]++;
+            pc.v[2] += dv;
+            if ((REFINE || P::det) ? (a.prop[v] >= 0) : (s_mv != 0)) {
+                pc.v[4]++;
+                pc.v[5] += dv;
+            }
         }
         __syncthreads();
         if (!REFINE && !P::det && s_mv)
@@ -417,6 +458,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
         const A s = warp_sum(local_gain);
         if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
     }
+    pc.flush(a.prof);
 }
 
 // ------------------------------------------------------------ apply steps

@@ -55,7 +55,13 @@ struct SweepCtx {
     void *hub_vals = nullptr;
     int hub_bits = 0;
     int *err = nullptr;
+    unsigned long long *prof = nullptr;  // 8 work counters of this launch's class, or null
 };
+
+// Work counters (kernels add to them when profiling): sweep kernels
+// {evaluated, skipped, edges, distinct, moved, moved_edges}; aggregation
+// {communities, members, edges, written}.
+constexpr int kProfCounters = 8;
 
 // evaluate one (step, bin) vertex list
 cudaError_t launch_sweep_eval(const SweepCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
@@ -82,6 +88,7 @@ struct AggCtx {
     void *hub_vals = nullptr;
     int hub_bits = 0;
     int *err = nullptr;
+    unsigned long long *prof = nullptr;
 };
 cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
                              cudaStream_t s);
