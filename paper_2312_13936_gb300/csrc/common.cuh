@@ -118,7 +118,7 @@ struct ProfCounts {
 
 // Device error word: kernels record the first failure here instead of
 // trapping; the host reads it after each phase.
-enum : int { kErrNone = 0, kErrHashFull = 1, kErrBadIndex = 2 };
+enum : int { kErrNone = 0, kErrHashFull = 1, kErrBadIndex = 2, kErrTimeout = 3 };
 __device__ __forceinline__ void set_error(int *err, int code) {
     if (err) atomicCAS(err, 0, code);
 }

@@ -104,6 +104,7 @@ struct Handle::Impl {
     std::vector<void *> allocs;
     // profiling (LEIDEN_FLAG_PROFILE)
     unsigned long long *prof_cnt = nullptr;  // LEIDEN_PROFILE_CLASSES x kProfCounters
+    unsigned *bar = nullptr;                 // grid barrier of the persistent sweep kernel
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, size_t>> prof_spans;  // (class, index of the start event)
@@ -151,8 +152,10 @@ struct Handle::Impl {
         CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (hsc->err) {
-            set_last_error("device error word " + std::to_string(hsc->err));
-            return LEIDEN_ERR_CUDA;
+            const int code = hsc->err;
+            set_last_error(code == 3 ? "a grid barrier of the persistent sweep kernel timed out"
+                                     : "device error word " + std::to_string(code));
+            return code == 3 ? LEIDEN_ERR_TIMEOUT : LEIDEN_ERR_CUDA;
         }
         return LEIDEN_OK;
     }
@@ -299,6 +302,8 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     ST(q.alloc(&q.sfstart, 4096 + 1));
     ST(q.alloc(&q.sfcount, 4096 + 1));
     ST(q.alloc(&q.prof_cnt, (int64_t)LEIDEN_PROFILE_CLASSES * kProfCounters));
+    ST(q.alloc(&q.bar, 2));
+    CK(cudaMemsetAsync(q.bar, 0, 2 * sizeof(unsigned), q.s));
     q.key_cap = 8192;
     ST(q.alloc(&q.key_cnt, q.key_cap));
     ST(q.alloc(&q.key_off, q.key_cap + 1));
@@ -428,7 +433,8 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         SchedWork sw{q.scnt, q.slayer, q.sflist, q.sfstart, q.sfcount};
         CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s));
         q.launches += L;
-        CK(launch_step_bin_keys(q.step, G.deg, n, q.key, s));
+        // one vertex list per (schedule step, degree bin), step-major
+        CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
         CK(launch_partition(q.key, n, nkeys, q.key_cnt, q.key_off, q.list, q.scan_tmp, s));
         CK(launch_max_i32(G.deg, n, &q.dsc->maxdeg, s));
         q.launches += 7;
@@ -486,8 +492,26 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         sc.hub_bits = hub_bits;
         sc.err = &q.dsc->err;
         const std::vector<int64_t> &ko = q.hkey_off;
+        sc.nsteps = nsteps;
+        sc.key_off = q.key_off;
+        sc.bar = q.bar;
+        sc.hub_regions = hub_regions;
+        const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
         auto run_steps = [&](bool refine) -> leiden_status {
             sc.refine = refine;
+            if (!step_launches) {
+                // the whole sweep in one persistent cooperative launch
+                const int per_sm = sweep_coop_blocks_per_sm(det, G.w_int, refine);
+                if (per_sm > 0) {
+                    int grid = per_sm * q.sm;
+                    if (hub_regions > 0 && sc.hub_regions > grid) sc.hub_regions = grid;
+                    sc.prof = prof_begin(refine ? 8 : 0);
+                    CK(launch_sweep_coop(sc, q.list, grid, s));
+                    prof_end();
+                    q.launches++;
+                    return LEIDEN_OK;
+                }
+            }
             for (int32_t k = 0; k < nsteps; ++k) {
                 sc.cur_step = k;
                 const int64_t a0 = ko[k * kNumBins], a1 = ko[(k + 1) * kNumBins];
@@ -501,11 +525,9 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                     prof_end();
                     q.launches++;
                 }
-                if (refine) {
-                    CK(launch_refine_apply(sc, q.list + a0, a1 - a0, s));
-                    q.launches++;
-                } else if (det) {
-                    CK(launch_move_apply(sc, q.list + a0, a1 - a0, s));
+                if (refine || det) {
+                    if (refine) CK(launch_refine_apply(sc, q.list + a0, a1 - a0, s));
+                    else CK(launch_move_apply(sc, q.list + a0, a1 - a0, s));
                     q.launches++;
                 }
             }

@@ -80,10 +80,11 @@ __global__ void k_sched_finish(int64_t n, uint64_t state, int32_t L, int32_t B, 
     }
 }
 
-__global__ void k_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t *key) {
+__global__ void k_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
+                                int32_t *key) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int b = degree_bin(deg[v]);
-        key[v] = b == 0 ? -1 : step[v] * kNumBins + b;
+        key[v] = b == 0 ? -1 : (bin_major ? b * nsteps + step[v] : step[v] * kNumBins + b);
     }
 }
 
@@ -110,9 +111,10 @@ cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t *key, cudaStream_t s) {
+cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
+                                 int32_t *key, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_step_bin_keys<<<grid_for(n, 256), 256, 0, s>>>(step, deg, n, key);
+    k_step_bin_keys<<<grid_for(n, 256), 256, 0, s>>>(step, deg, n, nsteps, bin_major, key);
     return cudaGetLastError();
 }
 

@@ -1,18 +1,29 @@
-// Local-moving (Algorithm 2) and refinement (Algorithm 3) sweep kernels.
+// Local-moving (Algorithm 2) and refinement (Algorithm 3) sweeps.
 //
-// One launch evaluates the vertices of one (schedule step, degree bin) list.
-// For each vertex i the kernel accumulates K_{i->c} over the neighbour
-// communities (scanCommunities / scanBounded), computes the Eq. 2 gain of
-// every candidate, takes the best (ties: lowest community id) and compares
-// it with staying. The accumulation structure depends on the degree bin:
+// For each vertex i the kernels accumulate K_{i->c} over the neighbour
+// communities (scanCommunities / scanBounded), compute the Eq. 2 gain of
+// every candidate, take the best (ties: lowest community id) and compare it
+// with staying. The accumulation structure depends on the degree bin:
 //   bins 1-4  a tile of 4/8/16/32 lanes holds one edge per lane; equal
 //             communities are merged with register shuffles;
-//   bin 5     one warp per vertex with an open-addressing table in shared memory;
-//   bin 6     one block per vertex with a shared-memory table;
-//   bin 7     one block per vertex with a table in global memory (hubs).
-// Asynchronous local-moving applies a move at once (atomics on Sigma); the
-// deterministic mode and the refinement record proposals that the apply
-// kernels below commit after the whole step was evaluated.
+//   bin 5     one warp per vertex, open-addressing table in shared memory;
+//   bin 6     one block per vertex, shared-memory table;
+//   bin 7     one block per vertex, table in global memory (hubs).
+//
+// A sweep visits the schedule steps in order (reading S0). The main kernel,
+// k_sweep_coop, is persistent: one cooperative launch runs every step of a
+// sweep and separates steps with a grid barrier, so a sweep costs one launch
+// whatever the number of steps. Asynchronous local-moving applies each move
+// at once (atomics on Sigma, the paper's asynchronous execution); the
+// deterministic mode records proposals and commits them after the step's
+// evaluation, and the refinement in both modes records proposals that the
+// step's apply phase accepts by reading S5. The per-(step, bin) kernels
+// below run the same routines one launch at a time; the engine uses them if
+// a cooperative launch is not possible.
+//
+// State that changes during a sweep (C, Sigma, sizes, flags, proposals) is
+// read through L2 (ld.global.cg) so that a step sees every write made before
+// the preceding barrier.
 #include <climits>
 
 #include "common.cuh"
@@ -38,12 +49,14 @@ template <class P, class W> struct SV {
     const int32_t *step;
     A two_m;
     double gamma;
-    int32_t cur_step, cap_step;
+    int32_t cur_step, cap_step, nsteps;
+    const int64_t *key_off;
     A *dq_acc;
     unsigned long long *moved;
     int32_t *hub_keys;
     A *hub_vals;
-    int hub_bits;
+    int hub_bits, hub_regions;
+    unsigned *bar;
     int *err;
     unsigned long long *prof;
 };
@@ -68,52 +81,47 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.gamma = c.gamma;
     a.cur_step = c.cur_step;
     a.cap_step = c.cap_step;
+    a.nsteps = c.nsteps;
+    a.key_off = c.key_off;
     a.dq_acc = static_cast<A *>(c.dq_acc);
     a.moved = c.moved;
     a.hub_keys = c.hub_keys;
     a.hub_vals = static_cast<A *>(c.hub_vals);
     a.hub_bits = c.hub_bits;
+    a.hub_regions = c.hub_regions;
+    a.bar = c.bar;
     a.err = c.err;
     a.prof = c.prof;
     return a;
 }
 
-// Community of neighbour j: asynchronous local-moving reads through L2 since
-// other SMs move vertices concurrently; elsewhere C is constant in a launch.
-template <class P, bool REFINE> __device__ __forceinline__ int32_t comm_of(const int32_t *C, int32_t j) {
-    if (P::det || REFINE) return __ldg(&C[j]);
-    return __ldcg(&C[j]);
-}
-template <class P, bool REFINE, class A> __device__ __forceinline__ A sigma_of(const A *Sig, int32_t c) {
-    if (P::det || REFINE) return __ldg(&Sig[c]);
-    return load_cg(&Sig[c]);
-}
+__device__ __forceinline__ int32_t ldm(const int32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ double ldm(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ long long ldm(const long long *p) { return __ldcg(p); }
+__device__ __forceinline__ uint8_t ldm(const uint8_t *p) { return __ldcg(p); }
 
 // Better candidate: larger key, then smaller community id.
 template <class A> __device__ __forceinline__ bool better(A k1, int32_t c1, A k2, int32_t c2) {
     return k1 > k2 || (k1 == k2 && c1 < c2);
 }
 
-// Final decision for vertex v with best candidate (key, cand) and
-// K_{v->d} = kvd. Run by one thread. Returns true if an asynchronous move was
-// applied (its neighbours must then be marked unprocessed).
+// Decision for vertex v (one thread) with best candidate (key, cand) and
+// K_{v->d} = kvd. Returns true if an asynchronous move was applied (its
+// neighbours must then be marked unprocessed).
 template <class P, class W, bool REFINE>
 __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
                                        typename P::acc key, int32_t cand, typename P::acc kvd,
-                                       typename P::acc &local_gain) {
+                                       typename P::acc &local_gain, int32_t cur_step) {
     using A = typename P::acc;
     bool mv = false;
     A g = 0;
     if (cand != INT_MAX) {
-        const A sd = sigma_of<P, REFINE>(a.Sig, d);
-        const A ks = stay_key(a.two_m, kvd, Kv, sd, a.gamma);
+        const A ks = stay_key(a.two_m, kvd, Kv, ldm(&a.Sig[d]), a.gamma);
         mv = key > ks;
-        if (!REFINE && mv && a.cur_step >= a.cap_step) {
-            // S2: in steps that may hold adjacent vertices, a single-vertex
+        if (!REFINE && mv && cur_step >= a.cap_step) {
+            // S2: where neighbours may move together, a single-vertex
             // community does not move into a larger-id single-vertex one.
-            const int32_t szd = P::det ? __ldg(&a.size[d]) : __ldcg(&a.size[d]);
-            const int32_t szc = P::det ? __ldg(&a.size[cand]) : __ldcg(&a.size[cand]);
-            if (szd == 1 && szc == 1 && cand > d) mv = false;
+            if (ldm(&a.size[d]) == 1 && ldm(&a.size[cand]) == 1 && cand > d) mv = false;
         }
         g = key - ks;
     }
@@ -133,34 +141,33 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
     return mv;
 }
 
-// Eligibility: local-moving processes unprocessed vertices (and marks them
-// processed, Algorithm 2 pruning); refinement processes isolated vertices
-// (the community of v has v as its only member, reading R7).
+// Eligibility: local-moving takes unprocessed vertices and marks them
+// processed (Algorithm 2 pruning); refinement takes isolated vertices (the
+// community of v has v as its only member, reading R7).
 template <class P, class W, bool REFINE>
 __device__ __forceinline__ bool take_vertex(const SV<P, W> &a, int32_t v, int32_t &d) {
     if (REFINE) {
-        d = a.C[v];
-        return __ldg(&a.size[d]) == 1;
+        d = ldm(&a.C[v]);
+        return ldm(&a.size[d]) == 1;
     }
-    const bool e = a.unproc[v] != 0;
+    const bool e = ldm(&a.unproc[v]) != 0;
     if (e) {
         a.unproc[v] = 0;
-        d = a.C[v];
+        d = ldm(&a.C[v]);
     }
     return e;
 }
 
-// -------------------------------------------------------------- tile bins
+// ----------------------------------------------------------- tile bins
 template <class P, class W, int T, bool REFINE>
-__global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+__device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
+                                         int32_t cur_step, typename P::acc &local_gain, ProfCounts &pc) {
     using A = typename P::acc;
     const int lane = threadIdx.x & 31;
     const int tl = lane & (T - 1);
     const unsigned tmask = (T == 32) ? kFull : (((1u << T) - 1u) << (lane & ~(T - 1)));
     const int64_t tiles = (int64_t)gridDim.x * (blockDim.x / T);
-    A local_gain = 0;
-    ProfCounts pc;
-    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; t < count; t += tiles) {
+    for (int64_t t = lo + (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; t < hi; t += tiles) {
         const int32_t v = list[t];
         int32_t d = 0;
         int elig = 0;
@@ -183,9 +190,9 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
             wv = wconv<A>(a.w[e0 + tl]);
             bool ok = (j != v);
             if (REFINE && ok) ok = (__ldg(&a.CB[j]) == bv);
-            if (ok) c = comm_of<P, REFINE>(a.C, j);
+            if (ok) c = ldm(&a.C[j]);
         }
-        // merge equal communities: every lane sums the lanes of its community
+        // merge equal communities: each lane sums the lanes of its community
         // in lane order; the first lane of each community leads
         A sum = 0;
         bool lead = (c >= 0);
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
         A key = AccLimits<A>::lowest();
         int32_t cand = INT_MAX;
         if (lead && c != d) {
-            key = move_key(a.two_m, sum, Kv, sigma_of<P, REFINE>(a.Sig, c), a.gamma);
+            key = move_key(a.two_m, sum, Kv, ldm(&a.Sig[c]), a.gamma);
             cand = c;
         }
 #pragma unroll
@@ -218,15 +225,14 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
             }
         }
         int mv = 0;
-        if (tl == 0) mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain) ? 1 : 0;
+        if (tl == 0) mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain, cur_step) ? 1 : 0;
         if (a.prof) {
             const unsigned lb = __ballot_sync(tmask, lead) & tmask;
             if (tl == 0) {
                 pc.v[0]++;
                 pc.v[2] += dv;
                 pc.v[3] += __popc(lb);
-                const bool any = (REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0);
-                if (any) {
+                if ((REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0)) {
                     pc.v[4]++;
                     pc.v[5] += dv;
                 }
@@ -237,27 +243,17 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
             if (mv && tl < dv) a.unproc[j] = 1;  // neighbours (self-loop included) of a mover
         }
     }
-    if (!REFINE && !P::det) {
-        const A s = warp_sum(local_gain);
-        if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
-    }
-    pc.flush(a.prof);
 }
 
 // ------------------------------------------------------- warp-table bin
 template <class P, class W, bool REFINE>
-__global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+__device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
+                                         int32_t cur_step, int32_t *keys, typename P::acc *vals,
+                                         typename P::acc &local_gain, ProfCounts &pc) {
     using A = typename P::acc;
-    __shared__ int32_t skeys[8][kWarpSlots];
-    __shared__ A svals[8][kWarpSlots];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    int32_t *keys = skeys[wib];
-    A *vals = svals[wib];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    A local_gain = 0;
-    ProfCounts pc;
-    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; t < count; t += nwarps) {
+    for (int64_t t = lo + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < hi; t += nwarps) {
         const int32_t v = list[t];
         int32_t d = 0;
         int elig = 0;
@@ -285,8 +281,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
             const int32_t j = a.idx[e0 + e];
             if (j == v) continue;
             if (REFINE && __ldg(&a.CB[j]) != bv) continue;
-            const int32_t c = comm_of<P, REFINE>(a.C, j);
-            if (!hash_add(keys, vals, bits, c, wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
+            if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
         }
         __syncwarp();
         A key = AccLimits<A>::lowest(), kvd = 0;
@@ -300,7 +295,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(a.two_m, sum, Kv, sigma_of<P, REFINE>(a.Sig, k), a.gamma);
+            const A kk = move_key(a.two_m, sum, Kv, ldm(&a.Sig[k]), a.gamma);
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -317,7 +312,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
         kvd = warp_sum(kvd);
         int mv = 0;
         if (lane == 0) {
-            mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain) ? 1 : 0;
+            mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain, cur_step) ? 1 : 0;
             pc.v[0]++;
             pc.v[2] += dv;
             if ((REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0)) {
@@ -332,37 +327,23 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
         }
         __syncwarp();
     }
-    if (!REFINE && !P::det) {
-        const A s = warp_sum(local_gain);
-        if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
-    }
-    pc.flush(a.prof);
 }
 
 // ------------------------------------------------ block / hub table bins
-constexpr int kBlockThreads = 512;
-
+// One block per vertex (HUB: a global-memory table per block; only blocks
+// below hub_regions take part).
 template <class P, class W, bool REFINE, bool HUB>
-__global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const int32_t *__restrict__ list,
-                                                             int64_t count) {
+__device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
+                                          int32_t cur_step, int32_t *keys, typename P::acc *vals, int max_bits,
+                                          typename P::acc &local_gain, ProfCounts &pc) {
     using A = typename P::acc;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_elig, s_d, s_mv;
-    __shared__ A s_key[kBlockThreads / 32], s_kvd[kBlockThreads / 32];
-    __shared__ int32_t s_cand[kBlockThreads / 32];
-    int32_t *keys;
-    A *vals;
-    if (HUB) {
-        keys = a.hub_keys + ((int64_t)blockIdx.x << a.hub_bits);
-        vals = a.hub_vals + ((int64_t)blockIdx.x << a.hub_bits);
-    } else {
-        vals = reinterpret_cast<A *>(smem_raw);
-        keys = reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
-    }
-    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    A local_gain = 0;
-    ProfCounts pc;
-    for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+    __shared__ A s_key[32], s_kvd[32];
+    __shared__ int32_t s_cand[32];
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t nblk = HUB ? (int64_t)a.hub_regions : (int64_t)gridDim.x;
+    if (HUB && (int64_t)blockIdx.x >= nblk) return;
+    for (int64_t t = lo + blockIdx.x; t < hi; t += nblk) {
         const int32_t v = list[t];
         __syncthreads();
         if (tid == 0) {
@@ -381,9 +362,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
         const int32_t bv = REFINE ? a.CB[v] : 0;
         int bits = ceil_log2(2 * (int64_t)dv);
         if (bits < 6) bits = 6;
-        if (HUB && bits > a.hub_bits) {
-            if (tid == 0) set_error(a.err, kErrHashFull);
-            if (tid == 0 && (REFINE || P::det)) a.prop[v] = -1;
+        if (bits > max_bits) {
+            if (tid == 0) {
+                set_error(a.err, kErrHashFull);
+                if (REFINE || P::det) a.prop[v] = -1;
+            }
             continue;
         }
         const int64_t S = 1LL << bits;
@@ -396,8 +379,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
             const int32_t j = a.idx[e0 + e];
             if (j == v) continue;
             if (REFINE && __ldg(&a.CB[j]) != bv) continue;
-            const int32_t c = comm_of<P, REFINE>(a.C, j);
-            if (!hash_add(keys, vals, bits, c, wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
+            if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
         }
         __syncthreads();
         A key = AccLimits<A>::lowest(), kvd = 0;
@@ -411,7 +393,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(a.two_m, sum, Kv, sigma_of<P, REFINE>(a.Sig, k), a.gamma);
+            const A kk = move_key(a.two_m, sum, Kv, ldm(&a.Sig[k]), a.gamma);
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -435,14 +417,14 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
         if (tid == 0) {
             A bk = s_key[0], kd = s_kvd[0];
             int32_t bc = s_cand[0];
-            for (int w2 = 1; w2 < (int)(blockDim.x >> 5); ++w2) {
+            for (int w2 = 1; w2 < nw; ++w2) {
                 if (better(s_key[w2], s_cand[w2], bk, bc)) {
                     bk = s_key[w2];
                     bc = s_cand[w2];
                 }
                 kd += s_kvd[w2];
             }
-            s_mv = decide<P, W, REFINE>(a, v, d, Kv, bk, bc, kd, local_gain) ? 1 : 0;
+            s_mv = decide<P, W, REFINE>(a, v, d, Kv, bk, bc, kd, local_gain, cur_step) ? 1 : 0;
             pc.v[0]++;
             pc.v[2] += dv;
             if ((REFINE || P::det) ? (a.prop[v] >= 0) : (s_mv != 0)) {
@@ -454,49 +436,45 @@ __global__ void __launch_bounds__(kBlockThreads) k_eval_block(SV<P, W> a, const 
         if (!REFINE && !P::det && s_mv)
             for (int64_t e = tid; e < dv; e += blockDim.x) a.unproc[a.idx[e0 + e]] = 1;
     }
-    if (!REFINE && !P::det) {
-        const A s = warp_sum(local_gain);
-        if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
-    }
-    pc.flush(a.prof);
+    __syncthreads();
 }
 
 // ------------------------------------------------------------ apply steps
-// Deterministic local-moving: commit the proposals of one step (all bins).
+// Deterministic local-moving: commit the proposals of one step.
 template <class P, class W>
-__global__ void __launch_bounds__(256) k_move_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
-    long long g = 0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo,
+                                               int64_t hi, long long &g) {
+    for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi;
+         t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = list[t];
-        const int32_t c = a.prop[v];
+        const int32_t c = ldm(&a.prop[v]);
         if (c < 0) continue;
-        const int32_t d = a.C[v];
+        const int32_t d = ldm(&a.C[v]);
         const auto Kv = a.K[v];
         atomic_add_acc(&a.Sig[d], -Kv);
         atomic_add_acc(&a.Sig[c], Kv);
         atomicSub(&a.size[d], 1);
         atomicAdd(&a.size[c], 1);
         a.C[v] = c;
-        g += a.gain[v];
+        g += ldm(&a.gain[v]);
         const int64_t e0 = a.off[v];
         const int32_t dv = a.deg[v];
         for (int32_t e = 0; e < dv; ++e) a.unproc[a.idx[e0 + e]] = 1;
     }
-    g = warp_sum(g);
-    if ((threadIdx.x & 31) == 0 && g != 0) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), g);
 }
 
 // Refinement: accept proposal v -> t unless t is a single-vertex community
-// whose vertex proposes in the same step; a mutual pair keeps the larger id's
-// move (reading S5). Accepted vertices join t.
+// whose vertex proposes in the same step; of a mutual pair the larger id
+// moves (reading S5). Accepted vertices join t.
 template <class P, class W>
-__global__ void __launch_bounds__(256) k_refine_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
-    unsigned long long mv = 0;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo,
+                                                 int64_t hi, int32_t cur_step, unsigned long long &mv) {
+    for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi;
+         t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = list[t];
-        const int32_t tg = a.prop[v];
+        const int32_t tg = ldm(&a.prop[v]);
         if (tg < 0) continue;
-        const int32_t pt = (a.step[tg] == a.cur_step) ? a.prop[tg] : -1;
+        const int32_t pt = (__ldg(&a.step[tg]) == cur_step) ? ldm(&a.prop[tg]) : -1;
         if (!(pt < 0 || (pt == v && v > tg))) continue;
         const auto Kv = a.K[v];
         atomic_add_acc(&a.Sig[v], -Kv);
@@ -506,14 +484,185 @@ __global__ void __launch_bounds__(256) k_refine_apply(SV<P, W> a, const int32_t 
         a.C[v] = tg;
         mv++;
     }
+}
+
+// Grid-wide barrier of a cooperative launch. Spins are bounded: after about a
+// second without progress the kernel records kErrTimeout and every later
+// barrier returns at once, so the launch always ends.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = *((volatile int *)err) == 0;
+        if (ok) {
+            volatile unsigned *gen = bar + 1;
+            const unsigned g = *gen;
+            __threadfence();
+            if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+                atomicExch(&bar[0], 0u);
+                __threadfence();
+                atomicAdd(&bar[1], 1u);
+            } else {
+                unsigned long long spins = 0;
+                while (*gen == g) {
+                    if (++spins > (1ULL << 24)) {
+                        set_error(err, kErrTimeout);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------------- persistent sweep
+constexpr int kCoopThreads = 256;
+
+// shared-memory tables: 8 warp tables of kWarpSlots slots, or one block table
+// of kBlockSlots slots (values first, then keys)
+template <class A> constexpr size_t table_bytes() { return (sizeof(A) + sizeof(int32_t)) * kBlockSlots; }
+template <class A> __device__ __forceinline__ A *table_vals() {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return reinterpret_cast<A *>(smem_raw);
+}
+template <class A> __device__ __forceinline__ int32_t *table_keys() {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
+}
+
+template <class P, class W, bool REFINE>
+__global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, const int32_t *__restrict__ list) {
+    using A = typename P::acc;
+    int32_t *skeys = table_keys<A>();
+    A *svals = table_vals<A>();
+    const int wib = threadIdx.x >> 5;
+    A local_gain = 0;
+    long long det_gain = 0;
+    unsigned long long moved = 0;
+    ProfCounts pc;
+    for (int32_t k = 0; k < a.nsteps; ++k) {
+        const int64_t *ko = a.key_off + (int64_t)k * kNumBins;
+        const int64_t b0 = __ldcg(&ko[0]), b8 = __ldcg(&ko[8]);
+        if (b0 == b8) continue;  // empty step: every block sees the same counts
+        run_tile<P, W, 4, REFINE>(a, list, __ldcg(&ko[1]), __ldcg(&ko[2]), k, local_gain, pc);
+        run_tile<P, W, 8, REFINE>(a, list, __ldcg(&ko[2]), __ldcg(&ko[3]), k, local_gain, pc);
+        run_tile<P, W, 16, REFINE>(a, list, __ldcg(&ko[3]), __ldcg(&ko[4]), k, local_gain, pc);
+        run_tile<P, W, 32, REFINE>(a, list, __ldcg(&ko[4]), __ldcg(&ko[5]), k, local_gain, pc);
+        run_warp<P, W, REFINE>(a, list, __ldcg(&ko[5]), __ldcg(&ko[6]), k, skeys + wib * kWarpSlots,
+                               svals + wib * kWarpSlots, local_gain, pc);
+        const int64_t b6 = __ldcg(&ko[6]), b7 = __ldcg(&ko[7]);
+        if (b7 > b6) {
+            __syncthreads();  // the warp tables become one block table
+            run_block<P, W, REFINE, false>(a, list, b6, b7, k, skeys, svals, ceil_log2(kBlockSlots), local_gain, pc);
+        }
+        if (b8 > b7) {
+            const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
+            run_block<P, W, REFINE, true>(a, list, b7, b8, k, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
+                                          local_gain, pc);
+        }
+        if (!grid_barrier(a.bar, a.err)) break;
+        if (REFINE || P::det) {
+            if (REFINE) run_refine_apply(a, list, b0, b8, k, moved);
+            else run_move_apply(a, list, b0, b8, det_gain);
+            if (!grid_barrier(a.bar, a.err)) break;
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    if (REFINE) {
+        moved = warp_sum(moved);
+        if (lane == 0 && moved) atomicAdd(a.moved, moved);
+    } else if (P::det) {
+        det_gain = warp_sum(det_gain);
+        if (lane == 0 && det_gain) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), det_gain);
+    } else {
+        const A s = warp_sum(local_gain);
+        if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+    }
+    pc.flush(a.prof);
+}
+
+// ------------------------------------------- one (step, bin) per launch
+template <class P, class W, int T, bool REFINE>
+__global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+    using A = typename P::acc;
+    A local_gain = 0;
+    ProfCounts pc;
+    run_tile<P, W, T, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
+    if (!REFINE && !P::det) {
+        const A s = warp_sum(local_gain);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+    }
+    pc.flush(a.prof);
+}
+template <class P, class W, bool REFINE>
+__global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+    using A = typename P::acc;
+    int32_t *skeys = table_keys<A>();
+    A *svals = table_vals<A>();
+    const int wib = threadIdx.x >> 5;
+    A local_gain = 0;
+    ProfCounts pc;
+    run_warp<P, W, REFINE>(a, list, 0, count, a.cur_step, skeys + wib * kWarpSlots, svals + wib * kWarpSlots,
+                           local_gain, pc);
+    if (!REFINE && !P::det) {
+        const A s = warp_sum(local_gain);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+    }
+    pc.flush(a.prof);
+}
+template <class P, class W, bool REFINE, bool HUB>
+__global__ void __launch_bounds__(256) k_eval_block(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+    using A = typename P::acc;
+    int32_t *skeys = table_keys<A>();
+    A *svals = table_vals<A>();
+    A local_gain = 0;
+    ProfCounts pc;
+    if (HUB) {
+        const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
+        run_block<P, W, REFINE, true>(a, list, 0, count, a.cur_step, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
+                                      local_gain, pc);
+    } else {
+        run_block<P, W, REFINE, false>(a, list, 0, count, a.cur_step, skeys, svals, ceil_log2(kBlockSlots), local_gain,
+                                       pc);
+    }
+    if (!REFINE && !P::det) {
+        const A s = warp_sum(local_gain);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+    }
+    pc.flush(a.prof);
+}
+template <class P, class W>
+__global__ void __launch_bounds__(256) k_move_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+    long long g = 0;
+    run_move_apply(a, list, 0, count, g);
+    g = warp_sum(g);
+    if ((threadIdx.x & 31) == 0 && g != 0) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), g);
+}
+template <class P, class W>
+__global__ void __launch_bounds__(256) k_refine_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+    unsigned long long mv = 0;
+    run_refine_apply(a, list, 0, count, a.cur_step, mv);
     mv = warp_sum(mv);
     if ((threadIdx.x & 31) == 0 && mv) atomicAdd(a.moved, mv);
+}
+
+// raise the dynamic shared-memory limit of a kernel (a host-side attribute:
+// cheap, and set before every launch so no kernel can miss it)
+template <class K> cudaError_t allow_table_smem(K kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <class P, class W, bool REFINE>
 cudaError_t eval_typed(const SweepCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
                        cudaStream_t s) {
     SV<P, W> a = view<P, W>(c);
+    constexpr size_t tb = table_bytes<typename P::acc>();
     auto grid = [&](int64_t per_block) {
         int64_t b = (count + per_block - 1) / per_block;
         return (int)(b < max_blocks ? (b < 1 ? 1 : b) : max_blocks);
@@ -523,16 +672,22 @@ cudaError_t eval_typed(const SweepCtx &c, int bin, const int32_t *list, int64_t 
         case 2: k_eval_tile<P, W, 8, REFINE><<<grid(32), 256, 0, s>>>(a, list, count); break;
         case 3: k_eval_tile<P, W, 16, REFINE><<<grid(16), 256, 0, s>>>(a, list, count); break;
         case 4: k_eval_tile<P, W, 32, REFINE><<<grid(8), 256, 0, s>>>(a, list, count); break;
-        case 5: k_eval_warp<P, W, REFINE><<<grid(8), 256, 0, s>>>(a, list, count); break;
-        case 6: {
-            const size_t sm = (sizeof(typename P::acc) + sizeof(int32_t)) * kBlockSlots;
-            auto kern = k_eval_block<P, W, REFINE, false>;
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        case 5: {
+            cudaError_t e = allow_table_smem(k_eval_warp<P, W, REFINE>, tb);
             if (e != cudaSuccess) return e;
-            kern<<<grid(1), kBlockThreads, sm, s>>>(a, list, count);
+            k_eval_warp<P, W, REFINE><<<grid(8), 256, tb, s>>>(a, list, count);
             break;
         }
-        case 7: k_eval_block<P, W, REFINE, true><<<grid(1), kBlockThreads, 0, s>>>(a, list, count); break;
+        case 6: {
+            cudaError_t e = allow_table_smem(k_eval_block<P, W, REFINE, false>, tb);
+            if (e != cudaSuccess) return e;
+            k_eval_block<P, W, REFINE, false><<<grid(1), 256, tb, s>>>(a, list, count);
+            break;
+        }
+        case 7:
+            a.hub_regions = max_blocks;
+            k_eval_block<P, W, REFINE, true><<<grid(1), 256, 0, s>>>(a, list, count);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -547,6 +702,26 @@ cudaError_t eval_mode(const SweepCtx &c, int bin, const int32_t *list, int64_t c
 int apply_grid(int64_t count) {
     int64_t b = (count + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+template <class P, class W, bool REFINE>
+cudaError_t coop_typed(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s) {
+    SV<P, W> a = view<P, W>(c);
+    constexpr size_t tb = table_bytes<typename P::acc>();
+    cudaError_t e = allow_table_smem(k_sweep_coop<P, W, REFINE>, tb);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&a, (void *)&list};
+    return cudaLaunchCooperativeKernel((const void *)k_sweep_coop<P, W, REFINE>, dim3(grid), dim3(kCoopThreads), args,
+                                       tb, s);
+}
+template <class P, class W, bool REFINE> int coop_blocks_typed() {
+    constexpr size_t tb = table_bytes<typename P::acc>();
+    if (allow_table_smem(k_sweep_coop<P, W, REFINE>, tb) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_coop<P, W, REFINE>, kCoopThreads, tb) !=
+        cudaSuccess)
+        return 0;
+    return per_sm;
 }
 
 }  // namespace
@@ -578,6 +753,23 @@ cudaError_t launch_refine_apply(const SweepCtx &c, const int32_t *list, int64_t 
         k_refine_apply<Async, float><<<apply_grid(count), 256, 0, s>>>(view<Async, float>(c), list, count);
     }
     return cudaGetLastError();
+}
+
+int sweep_coop_blocks_per_sm(bool det, bool w_int, bool refine) {
+    if (det) {
+        if (w_int) return refine ? coop_blocks_typed<Det, int32_t, true>() : coop_blocks_typed<Det, int32_t, false>();
+        return refine ? coop_blocks_typed<Det, float, true>() : coop_blocks_typed<Det, float, false>();
+    }
+    return refine ? coop_blocks_typed<Async, float, true>() : coop_blocks_typed<Async, float, false>();
+}
+
+cudaError_t launch_sweep_coop(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s) {
+    if (c.det) {
+        if (c.g.w_int)
+            return c.refine ? coop_typed<Det, int32_t, true>(c, list, grid, s) : coop_typed<Det, int32_t, false>(c, list, grid, s);
+        return c.refine ? coop_typed<Det, float, true>(c, list, grid, s) : coop_typed<Det, float, false>(c, list, grid, s);
+    }
+    return c.refine ? coop_typed<Async, float, true>(c, list, grid, s) : coop_typed<Async, float, false>(c, list, grid, s);
 }
 
 }  // namespace lgb

@@ -12,9 +12,9 @@ namespace lgb {
 constexpr int kNumBins = 8;
 constexpr int kTileBins = 4;        // bins 1..4: a tile of 4/8/16/32 lanes per vertex
 constexpr int kWarpMaxDeg = 256;    // bin 5: one warp, shared-memory table
-constexpr int kBlockMaxDeg = 4096;  // bin 6: one block, shared-memory table; bin 7: global table
-constexpr int kWarpSlots = 512;
-constexpr int kBlockSlots = 8192;
+constexpr int kBlockMaxDeg = 2048;  // bin 6: one block, shared-memory table; bin 7: global table
+constexpr int kWarpSlots = 512;     // 8 warp tables fill the same 48 KB as one block table
+constexpr int kBlockSlots = 4096;
 __host__ __device__ inline int degree_bin(int64_t d) {
     return d <= 0 ? 0 : d <= 4 ? 1 : d <= 8 ? 2 : d <= 16 ? 3 : d <= 32 ? 4 : d <= kWarpMaxDeg ? 5 : d <= kBlockMaxDeg ? 6 : 7;
 }
@@ -49,11 +49,14 @@ struct SweepCtx {
     long long two_m_i = 0;
     double gamma = 1;
     int32_t cur_step = 0, cap_step = 0;  // steps >= cap_step may hold adjacent vertices
+    int32_t nsteps = 0;                  // persistent sweep: steps and their (step, bin) offsets
+    const int64_t *key_off = nullptr;    // device, nsteps*kNumBins+1 entries (step-major)
     void *dq_acc = nullptr;       // sweep delta-modularity numerator (acc type)
     unsigned long long *moved = nullptr;  // refinement: accepted moves
     int32_t *hub_keys = nullptr;  // global tables for bin 7 (one region per block)
     void *hub_vals = nullptr;
-    int hub_bits = 0;
+    int hub_bits = 0, hub_regions = 0;
+    unsigned *bar = nullptr;      // grid barrier state (2 words, zero-initialised once)
     int *err = nullptr;
     unsigned long long *prof = nullptr;  // 8 work counters of this launch's class, or null
 };
@@ -70,6 +73,9 @@ cudaError_t launch_sweep_eval(const SweepCtx &c, int bin, const int32_t *list, i
 cudaError_t launch_move_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s);
 // refinement: accept (rule S5) and apply a step's proposals
 cudaError_t launch_refine_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s);
+// one whole sweep (every step, grid barriers between steps) in one cooperative launch
+cudaError_t launch_sweep_coop(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s);
+int sweep_coop_blocks_per_sm(bool det, bool w_int, bool refine);
 
 // Aggregation (Algorithm 4) of G' by dense labels Cd into the holey CSR G''.
 struct AggCtx {
@@ -118,8 +124,10 @@ struct SchedWork {
 };
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
                             int32_t *step, cudaStream_t s);
-// key[i] = step[i]*kNumBins + degree_bin(deg[i]) (or -1 if deg == 0)
-cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t *key, cudaStream_t s);
+// key[i] = step*kNumBins + bin (step-major: one list per step and bin), or
+// bin*nsteps + step (bin-major: one step-ordered list per bin); -1 if deg == 0
+cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
+                                 int32_t *key, cudaStream_t s);
 
 // ---- pass bookkeeping (k_pass.cu)
 // Sigma[c] += K[i], size[c] += 1 over C (acc type)

@@ -68,6 +68,16 @@ def test_deterministic_phases_bit_exact(name):
     assert abs(q - ref.modularity) <= Q_REL_REPORT * max(1.0, abs(ref.modularity))
 
 
+@pytest.mark.parametrize("name", ["road_300", "hubs", "rmat_12"])
+def test_deterministic_step_launch_path(name):
+    """The per-(step, bin) launch path gives the same bits as the persistent sweep."""
+    g = DET_GRAPHS[name]()
+    ref = oracle.leiden(g, mode=oracle.SYNC, trace=True)
+    memb, q, st, tr = run_gpu(g, lg.LEIDEN_DETERMINISTIC, trace=True, flags=lg.FLAG_STEP_LAUNCHES)
+    assert not compare_traces(tr, ref.trace)
+    assert np.array_equal(memb, ref.membership)
+
+
 @pytest.mark.parametrize("L,B,seed", [(4, 3, 5), (1, 1, 0), (64, 8, 123)])
 def test_deterministic_schedule_parameters(L, B, seed):
     g = gen.road(120)
@@ -106,11 +116,12 @@ ASYNC_GRAPHS = {
 }
 
 
+@pytest.mark.parametrize("flags", [0, lg.FLAG_STEP_LAUNCHES])
 @pytest.mark.parametrize("name", sorted(ASYNC_GRAPHS))
-def test_async_quality_and_connectivity(name):
+def test_async_quality_and_connectivity(name, flags):
     g = ASYNC_GRAPHS[name]()
     seq = oracle.leiden(g, mode=oracle.SEQ)
-    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC)
+    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC, flags=flags)
     assert q >= seq.modularity - Q_TOL_ASYNC, (q, seq.modularity)
     assert oracle.disconnected(g, memb)[0] == 0
     q_re = oracle.modularity(g, memb)
