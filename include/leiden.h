@@ -149,6 +149,22 @@ leiden_status leiden_destroy(leiden_graph_t g);
 leiden_status leiden_modularity(int64_t n, const int64_t *offsets, const int32_t *indices, const float *weights,
                                 const int32_t *membership, double gamma, void *stream, double *q_out);
 
+/* Modularity as leiden_modularity computes it, without allocating any
+ * device memory. The paper has no counterpart: this entry point is for
+ * callers that cannot allocate device memory when they need the score (a
+ * host framework that owns all device memory through its own pool, a
+ * process at its memory cap, a path that must not call an allocator). Its
+ * scratch is a fixed static device array (8 MiB + 32 bytes) that every GPU
+ * loading the library keeps until the process exits, so n is limited to
+ * 1,048,576 vertices (larger n returns LEIDEN_ERR_INVALID). The first call
+ * on a device looks up the array's address there; make that call before any
+ * stream capture. All calls on a device share the array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller. Arguments
+ * and result as for leiden_modularity. */
+leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *offsets, const int32_t *indices,
+                                        const float *weights, const int32_t *membership, double gamma, void *stream,
+                                        double *q_out);
+
 /* Per-pass trace of the last leiden_run made with LEIDEN_FLAG_TRACE. what:
  * 1 C' at the start of local-moving (int32[n']), 2 C' after local-moving
  * (int32[n']), 3 C' after refinement (int32[n']), 4 counts (int64[4]: n',

@@ -21,7 +21,7 @@ __all__ = [
     "LEIDEN_HOST", "LEIDEN_DEVICE", "LEIDEN_ASYNC", "LEIDEN_DETERMINISTIC", "FLAG_VALIDATE",
     "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "FLAG_PROFILE", "FLAG_STEP_LAUNCHES", "LeidenError", "Params", "Stats", "KernelProfile",
     "library", "leiden_params_default", "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity",
-    "leiden_trace_get", "leiden_profile_get",
+    "leiden_trace_get", "leiden_profile_get", "leiden_modularity_noalloc",
     "leiden_status_string", "leiden_last_error", "Leiden", "modularity",
 ]
 
@@ -89,6 +89,9 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.leiden_destroy.argtypes = [_VP]
         lib.leiden_modularity.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.c_double, _VP,
                                           ctypes.POINTER(ctypes.c_double)]
+        lib.leiden_modularity_noalloc.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.c_double, _VP,
+                                                  ctypes.POINTER(ctypes.c_double)]
+        lib.leiden_modularity_noalloc.restype = ctypes.c_int
         lib.leiden_trace_get.argtypes = [_VP, _I32, _I32, _VP, ctypes.POINTER(_I64)]
         lib.leiden_profile_get.argtypes = [_VP, ctypes.POINTER(KernelProfile)]
         for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
@@ -145,6 +148,14 @@ def leiden_modularity(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, 
     q = ctypes.c_double(0.0)
     _check(library().leiden_modularity(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma, stream,
                                        ctypes.byref(q)))
+    return q.value
+
+
+def leiden_modularity_noalloc(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma, stream) -> float:
+    """leiden_modularity without device allocation (static scratch, n <= 2**20)."""
+    q = ctypes.c_double(0.0)
+    _check(library().leiden_modularity_noalloc(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma,
+                                               stream, ctypes.byref(q)))
     return q.value
 
 
