@@ -64,8 +64,10 @@ enum {
     LEIDEN_FLAG_REFINE_SINGLE_SWEEP = 2u, /* one refinement sweep, as Algorithm 3 prints it */
     LEIDEN_FLAG_TRACE = 4u,               /* keep per-pass intermediate results (leiden_trace_get) */
     LEIDEN_FLAG_PROFILE = 8u,             /* time every sweep/aggregation launch (leiden_profile_get) */
-    LEIDEN_FLAG_STEP_LAUNCHES = 16u       /* one launch per schedule step and degree bin instead of one
+    LEIDEN_FLAG_STEP_LAUNCHES = 16u,      /* one launch per schedule step and degree bin instead of one
                                              persistent launch per sweep (same results; for testing) */
+    LEIDEN_FLAG_NO_RELABEL = 32u          /* asynchronous mode: sweep large graphs in their own vertex order
+                                             instead of a copy relabelled by schedule step (for comparison) */
 };
 
 typedef struct {
@@ -97,8 +99,10 @@ typedef struct {
 /* Per-kernel-class profile of the last leiden_run made with
  * LEIDEN_FLAG_PROFILE. Class index = phase * 8 + bin, with phase 0 the
  * local-moving sweep (Algorithm 2), 1 the refinement sweep (Algorithm 3), 2
- * the aggregation (Algorithm 4), and bin 1..7 the degree bin (tile of
- * 4/8/16/32 lanes, warp table, block table, global table); bin 0 is the
+ * the aggregation (Algorithm 4), and bin 1..6 the degree bin (degree <= 8:
+ * a thread per vertex, or a tile of 8 lanes per community; <= 16 and <= 32:
+ * a tile of 16/32 lanes; <= 256: warp table; <= 2048: block table; larger:
+ * global-memory table); bin 0 is the
  * persistent kernel that runs a whole sweep (all bins) in one launch. bytes counts the
  * algorithmic bytes of the launches (each array element the method reads or
  * writes counted once at its own size; random gathers count their element,

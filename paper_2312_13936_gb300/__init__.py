@@ -19,7 +19,7 @@ from . import _build
 
 __all__ = [
     "LEIDEN_HOST", "LEIDEN_DEVICE", "LEIDEN_ASYNC", "LEIDEN_DETERMINISTIC", "FLAG_VALIDATE",
-    "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "FLAG_PROFILE", "FLAG_STEP_LAUNCHES", "LeidenError", "Params", "Stats", "KernelProfile",
+    "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "FLAG_PROFILE", "FLAG_STEP_LAUNCHES", "FLAG_NO_RELABEL", "LeidenError", "Params", "Stats", "KernelProfile",
     "library", "leiden_params_default", "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity",
     "leiden_trace_get", "leiden_profile_get", "leiden_modularity_noalloc",
     "leiden_status_string", "leiden_last_error", "Leiden", "modularity",
@@ -27,10 +27,11 @@ __all__ = [
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
 LEIDEN_ASYNC, LEIDEN_DETERMINISTIC = 0, 1
-FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE, FLAG_PROFILE, FLAG_STEP_LAUNCHES = 1, 2, 4, 8, 16
+FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE, FLAG_PROFILE, FLAG_STEP_LAUNCHES, FLAG_NO_RELABEL = \
+    1, 2, 4, 8, 16, 32
 PROFILE_CLASSES = 24
 PROFILE_PHASES = ("move", "refine", "aggregate")
-PROFILE_BINS = ("sweep", "tile4", "tile8", "tile16", "tile32", "warp", "block", "global")
+PROFILE_BINS = ("sweep", "thread", "tile16", "tile32", "warp", "block", "global", "unused")
 TRACE_INIT, TRACE_MOVE, TRACE_REFINE, TRACE_COUNTS, TRACE_RENUMBER = 1, 2, 3, 4, 5
 TRACE_AGG_OFF, TRACE_AGG_DEG, TRACE_AGG_IDX, TRACE_AGG_W, TRACE_DENDRO = 6, 7, 8, 9, 10
 _TRACE_DTYPE = {1: np.int32, 2: np.int32, 3: np.int32, 4: np.int64, 5: np.int32, 6: np.int64, 7: np.int32,

@@ -36,7 +36,7 @@ struct Scalars {  // device scalars, read back in one copy
     double wsum;
     double msum[4];
     int32_t maxdeg;
-    int32_t pad;
+    int32_t iters;
     unsigned long long maxtdeg;
 };
 
@@ -53,6 +53,9 @@ struct Scalars {  // device scalars, read back in one copy
         leiden_status _s = (x);                \
         if (_s != LEIDEN_OK) return _s;        \
     } while (0)
+
+// graphs below this size fit in L2 and are swept without relabelling
+constexpr int64_t kRelabelMinVertices = 1 << 16;
 
 int ceil_log2_h(int64_t x) {
     int b = 0;
@@ -83,10 +86,10 @@ struct Handle::Impl {
     int32_t *C0 = nullptr, *Cp = nullptr, *CB = nullptr, *Cd = nullptr, *size = nullptr, *prop = nullptr,
             *step = nullptr, *key = nullptr, *list = nullptr, *flag = nullptr, *members = nullptr, *cursor = nullptr,
             *bnd = nullptr, *rep = nullptr, *label = nullptr, *minv = nullptr, *out = nullptr, *scnt = nullptr,
-            *slayer = nullptr, *sflist = nullptr, *sfcount = nullptr;
+            *slayer = nullptr;
     int64_t *pos = nullptr, *pos2 = nullptr, *coff = nullptr, *cnt = nullptr, *tdeg = nullptr, *key_cnt = nullptr,
-            *key_off = nullptr, *sfstart = nullptr;
-    void *K = nullptr, *Sig = nullptr, *Kagg = nullptr, *scan_tmp = nullptr;
+            *key_off = nullptr;
+    void *K = nullptr, *Sig = nullptr, *Kagg = nullptr, *scan_tmp = nullptr, *part_tmp = nullptr;
     long long *gain = nullptr;
     uint8_t *unproc = nullptr;
     double *sigtot = nullptr;
@@ -105,6 +108,9 @@ struct Handle::Impl {
     // profiling (LEIDEN_FLAG_PROFILE)
     unsigned long long *prof_cnt = nullptr;  // LEIDEN_PROFILE_CLASSES x kProfCounters
     unsigned *bar = nullptr;                 // grid barrier of the persistent sweep kernel
+    long long *phase_dq = nullptr;           // per-sweep sums of a persistent phase
+    unsigned long long *phase_moved = nullptr;
+    int32_t phase_cap = 0;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, size_t>> prof_spans;  // (class, index of the start event)
@@ -226,6 +232,45 @@ struct Handle::Impl {
         prof_valid = true;
         return LEIDEN_OK;
     }
+    // relabelled copy of a pass's graph and arrays (asynchronous sweeps)
+    int64_t *roff = nullptr;
+    int32_t *rdeg = nullptr, *ridx = nullptr, *rinv = nullptr, *rC = nullptr, *rCB = nullptr, *rstep = nullptr,
+            *iota_list = nullptr;
+    void *rw = nullptr, *rK = nullptr;
+    int64_t rcap = -1;
+    leiden_status ensure_relabel(int64_t cap) {
+        if (!roff) {
+            ST(alloc(&roff, n0 + 1));
+            for (int32_t **a : {&rdeg, &rinv, &rC, &rCB, &rstep}) ST(alloc(a, n0));
+            long long *k = nullptr;
+            ST(alloc(&k, n0));
+            rK = k;
+        }
+        if (cap > rcap) {
+            if (ridx) free_one(ridx);
+            if (rw) free_one(rw);
+            ridx = nullptr;
+            rw = nullptr;
+            ST(alloc(&ridx, cap));
+            int32_t *w = nullptr;
+            ST(alloc(&w, cap));
+            rw = w;
+            rcap = cap;
+        }
+        return LEIDEN_OK;
+    }
+    size_t part_tmp_bytes = 0;
+    leiden_status ensure_part_tmp(size_t bytes) {
+        if (bytes <= part_tmp_bytes) return LEIDEN_OK;
+        if (part_tmp) free_one(part_tmp);
+        part_tmp = nullptr;
+        part_tmp_bytes = 0;
+        char *p = nullptr;
+        ST(alloc(&p, (int64_t)bytes));
+        part_tmp = p;
+        part_tmp_bytes = bytes;
+        return LEIDEN_OK;
+    }
     leiden_status ensure_agg(int x, int64_t cap) {
         Agg &a = agg[x];
         if (!a.off) {
@@ -280,7 +325,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     }
     // workspace sized for the input graph (later graphs are smaller)
     for (int32_t **a : {&q.C0, &q.Cp, &q.CB, &q.Cd, &q.size, &q.prop, &q.step, &q.key, &q.list, &q.flag, &q.members,
-                        &q.cursor, &q.bnd, &q.rep, &q.label, &q.minv, &q.out, &q.scnt, &q.slayer, &q.sflist})
+                        &q.cursor, &q.bnd, &q.rep, &q.label, &q.minv, &q.out, &q.scnt, &q.slayer})
         ST(q.alloc(a, n));
     for (int64_t **a : {&q.pos, &q.pos2, &q.coff})
         ST(q.alloc(a, n + 1));
@@ -299,14 +344,15 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     char *tmp;
     ST(q.alloc(&tmp, (int64_t)scan_tmp_bytes(n + 8192)));
     q.scan_tmp = tmp;
-    ST(q.alloc(&q.sfstart, 4096 + 1));
-    ST(q.alloc(&q.sfcount, 4096 + 1));
+    ST(q.ensure_part_tmp(partition_tmp_bytes(n, (32 - 1 + 16) * kNumBins + 1)));  // default schedule
     ST(q.alloc(&q.prof_cnt, (int64_t)LEIDEN_PROFILE_CLASSES * kProfCounters));
     ST(q.alloc(&q.bar, 2));
     CK(cudaMemsetAsync(q.bar, 0, 2 * sizeof(unsigned), q.s));
     q.key_cap = 8192;
     ST(q.alloc(&q.key_cnt, q.key_cap));
     ST(q.alloc(&q.key_off, q.key_cap + 1));
+    ST(q.alloc(&q.iota_list, n));
+    CK(launch_iota(q.iota_list, n, q.s));
     CK(launch_degrees(q.off0, q.deg0, n, &q.dsc->err, q.s));
     if (validate) CK(launch_validate(n, q.off0, q.idx0, q.w0, &q.dsc->err, q.s));
     CK(launch_weight_props(q.w0, nnz, &q.dsc->nonint, &q.dsc->wsum, q.s));
@@ -358,6 +404,16 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     if (nkeys > q.key_cap || L > 4096) {
         set_last_error("schedule_layers + schedule_buckets too large");
         return LEIDEN_ERR_INVALID;
+    }
+    ST(q.ensure_part_tmp(partition_tmp_bytes(q.n0, nkeys + 1)));
+    if (prm.max_iterations > q.phase_cap) {
+        if (q.phase_dq) q.free_one(q.phase_dq);
+        if (q.phase_moved) q.free_one(q.phase_moved);
+        q.phase_dq = nullptr;
+        q.phase_moved = nullptr;
+        ST(q.alloc(&q.phase_dq, prm.max_iterations));
+        ST(q.alloc(&q.phase_moved, prm.max_iterations));
+        q.phase_cap = prm.max_iterations;
     }
     if (det) {
         if (prm.resolution != 1.0 || q.nonint) {
@@ -419,6 +475,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     double tau = prm.tolerance;
     bool broke = false;
     int cur_agg = 1;  // next pass writes agg[cur_agg ^ 1]
+    int64_t Gcap = q.m0;  // entry capacity of G' (holey after aggregation)
     int passes = 0;
     const size_t accsz = 8;
 
@@ -428,18 +485,18 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         // vertexWeights(G') and 2m
         CK(cudaMemsetAsync(&q.dsc->two_m_f, 0, sizeof(double) + sizeof(long long), s));
         CK(launch_vertex_weights(G, det, q.K, det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, s));
-        q.launches += 2;
+        q.launches += 1;
         // schedule and (step, bin) lists
-        SchedWork sw{q.scnt, q.slayer, q.sflist, q.sfstart, q.sfcount};
+        SchedWork sw{q.scnt, q.slayer};
         CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s));
-        q.launches += L;
+        q.launches += L > 1 ? L : 2;
         // one vertex list per (schedule step, degree bin), step-major
         CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
-        CK(launch_partition(q.key, n, nkeys, q.key_cnt, q.key_off, q.list, q.scan_tmp, s));
+        CK(launch_partition(q.key, n, nkeys + 1, q.key_off, q.list, q.part_tmp, s));  // + edgeless bucket
         CK(launch_max_i32(G.deg, n, &q.dsc->maxdeg, s));
         q.launches += 7;
-        q.hkey_off.assign(nkeys + 1, 0);
-        CK(cudaMemcpyAsync(q.hkey_off.data(), q.key_off, sizeof(int64_t) * (nkeys + 1), cudaMemcpyDeviceToHost, s));
+        q.hkey_off.assign(nkeys + 2, 0);
+        CK(cudaMemcpyAsync(q.hkey_off.data(), q.key_off, sizeof(int64_t) * (nkeys + 2), cudaMemcpyDeviceToHost, s));
         ST(q.sync_scalars());
         const double two_m_f = q.hsc->two_m_f;
         const long long two_m_i = q.hsc->two_m_i;
@@ -453,11 +510,43 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         // C' and Sigma' at the start of local-moving (reading R3)
         if (lp == 0) CK(launch_iota(q.Cp, n, s));
         else CK(cudaMemcpyAsync(q.Cp, q.label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        if (trace) q.record(lp, 1, q.Cp, n);
+        // Sweep space. The asynchronous mode relabels large graphs so that
+        // every (step, bin) list is a contiguous id range, ascending in the
+        // ids of G' (consecutive threads then read consecutive vertices and
+        // nearby neighbours); the sweeps run on the relabelled copy and
+        // their labels are mapped back afterwards. Vertex p of the copy is
+        // vertex perm[p] = list[p] of G'.
+        const bool relabel = !det && !(prm.flags & LEIDEN_FLAG_NO_RELABEL) && n >= kRelabelMinVertices;
+        GraphView sG = G;
+        int32_t *sC = q.Cp, *sCB = q.CB, *sStep = q.step;
+        const int32_t *sList = q.list;
+        void *sK = q.K;
+        if (relabel) {
+            ST(q.ensure_relabel(Gcap));
+            const int32_t *perm = q.list;
+            CK(launch_inverse(perm, n, q.rinv, s));
+            CK(launch_gather_i32(G.deg, perm, n, q.rdeg, s));
+            CK(launch_exclusive_scan_i32(q.rdeg, q.roff, n, q.scan_tmp, s));
+            CK(launch_permute_rows(G, perm, q.rinv, q.roff, q.ridx, q.rw, s));
+            CK(launch_gather_8b(q.K, perm, n, q.rK, s));
+            CK(launch_gather_i32(q.step, perm, n, q.rstep, s));
+            CK(launch_labels_to_new(q.Cp, perm, q.rinv, n, q.rC, s));
+            q.launches += 9;
+            sG.off = q.roff;
+            sG.deg = q.rdeg;
+            sG.idx = q.ridx;
+            sG.w = q.rw;
+            sC = q.rC;
+            sCB = q.rCB;
+            sStep = q.rstep;
+            sList = q.iota_list;
+            sK = q.rK;
+        }
         CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
         CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
-        CK(launch_community_totals(q.Cp, q.K, det, n, q.Sig, q.size, s));
-        q.launches += 2;
-        if (trace) q.record(lp, 1, q.Cp, n);
+        CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));
+        q.launches += 1;
         // hub tables for bin 7
         int hub_bits = 0, hub_regions = 0;
         {
@@ -470,17 +559,17 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             }
         }
         SweepCtx sc;
-        sc.g = G;
+        sc.g = sG;
         sc.det = det;
-        sc.C = q.Cp;
-        sc.CB = q.CB;
-        sc.K = q.K;
+        sc.C = sC;
+        sc.CB = sCB;
+        sc.K = sK;
         sc.Sig = q.Sig;
         sc.size = q.size;
         sc.unproc = q.unproc;
         sc.prop = q.prop;
         sc.gain = q.gain;
-        sc.step = q.step;
+        sc.step = sStep;
         sc.two_m_f = two_m_f;
         sc.two_m_i = two_m_i;
         sc.gamma = prm.resolution;
@@ -497,21 +586,9 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         sc.bar = q.bar;
         sc.hub_regions = hub_regions;
         const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
+        // one sweep as per-(step, bin) launches (fallback and test path)
         auto run_steps = [&](bool refine) -> leiden_status {
             sc.refine = refine;
-            if (!step_launches) {
-                // the whole sweep in one persistent cooperative launch
-                const int per_sm = sweep_coop_blocks_per_sm(det, G.w_int, refine);
-                if (per_sm > 0) {
-                    int grid = per_sm * q.sm;
-                    if (hub_regions > 0 && sc.hub_regions > grid) sc.hub_regions = grid;
-                    sc.prof = prof_begin(refine ? 8 : 0);
-                    CK(launch_sweep_coop(sc, q.list, grid, s));
-                    prof_end();
-                    q.launches++;
-                    return LEIDEN_OK;
-                }
-            }
             for (int32_t k = 0; k < nsteps; ++k) {
                 sc.cur_step = k;
                 const int64_t a0 = ko[k * kNumBins], a1 = ko[(k + 1) * kNumBins];
@@ -519,55 +596,104 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                 for (int b = 1; b < kNumBins; ++b) {
                     const int64_t lo = ko[k * kNumBins + b], hi = ko[k * kNumBins + b + 1];
                     if (hi == lo) continue;
-                    const int mb = b <= 5 ? tile_blocks : (b == 6 ? big_blocks : hub_regions);
+                    const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : hub_regions);
                     sc.prof = prof_begin((refine ? 8 : 0) + b);
-                    CK(launch_sweep_eval(sc, b, q.list + lo, hi - lo, mb, s));
+                    CK(launch_sweep_eval(sc, b, sList + lo, hi - lo, mb, s));
                     prof_end();
                     q.launches++;
                 }
                 if (refine || det) {
-                    if (refine) CK(launch_refine_apply(sc, q.list + a0, a1 - a0, s));
-                    else CK(launch_move_apply(sc, q.list + a0, a1 - a0, s));
+                    if (refine) CK(launch_refine_apply(sc, sList + a0, a1 - a0, s));
+                    else CK(launch_move_apply(sc, sList + a0, a1 - a0, s));
                     q.launches++;
                 }
             }
+            return LEIDEN_OK;
+        };
+        // One phase (Algorithm 2 or 3): sweeps until convergence. Normally one
+        // persistent cooperative launch that tests convergence on the device;
+        // otherwise one host-driven sweep at a time. Returns the sweeps run.
+        auto run_phase = [&](bool refine, int *iters) -> leiden_status {
+            sc.refine = refine;
+            const bool single = refine && (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP);
+            const int per_sm = step_launches ? 0 : sweep_coop_blocks_per_sm(det, sG.w_int, refine);
+            if (per_sm > 0) {
+                // enough blocks for the graph (about 2048 vertices each), so
+                // small graphs do not pay a full-GPU barrier per step
+                int grid = per_sm * q.sm;
+                const int64_t want = (n + 2047) / 2048;
+                if (want < grid) grid = (int)(want < 1 ? 1 : want);
+                sc.hub_regions = hub_regions > grid ? grid : hub_regions;
+                sc.max_it = prm.max_iterations;
+                sc.single_sweep = single ? 1 : 0;
+                sc.tau = tau;
+                sc.dq_arr = q.phase_dq;
+                sc.moved_arr = q.phase_moved;
+                sc.iters_out = &q.dsc->iters;
+                CK(cudaMemsetAsync(q.phase_dq, 0, sizeof(long long) * prm.max_iterations, s));
+                CK(cudaMemsetAsync(q.phase_moved, 0, sizeof(unsigned long long) * prm.max_iterations, s));
+                sc.prof = prof_begin(refine ? 8 : 0);
+                CK(launch_sweep_coop(sc, sList, grid, s));
+                prof_end();
+                q.launches++;
+                ST(q.sync_scalars());
+                *iters = q.hsc->iters;
+                sc.hub_regions = hub_regions;
+                return LEIDEN_OK;
+            }
+            int k = 0;
+            for (int32_t it = 0; it < prm.max_iterations; ++it) {
+                k++;
+                CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double) + sizeof(long long), s));
+                CK(cudaMemsetAsync(&q.dsc->moved, 0, sizeof(unsigned long long), s));
+                ST(run_steps(refine));
+                ST(q.sync_scalars());
+                if (refine) {
+                    if (q.hsc->moved == 0 || single) break;
+                } else {
+                    const double dq = det ? 2.0 * (double)q.hsc->dq_i / ((double)two_m_i * (double)two_m_i)
+                                          : 2.0 * q.hsc->dq_f / (two_m_f * two_m_f);
+                    if (dq <= tau) break;  // locally converged
+                }
+            }
+            *iters = k;
             return LEIDEN_OK;
         };
         // ---- local-moving phase (Algorithm 2)
         ST(mark(0));
         CK(cudaMemsetAsync(q.unproc, 1, (size_t)n, s));  // mark all vertices unprocessed
         int li = 0;
-        for (int32_t it = 0; it < prm.max_iterations; ++it) {
-            li++;
-            CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double) + sizeof(long long), s));
-            ST(run_steps(false));
-            ST(q.sync_scalars());
-            const double dq = det ? 2.0 * (double)q.hsc->dq_i / ((double)two_m_i * (double)two_m_i)
-                                  : 2.0 * q.hsc->dq_f / (two_m_f * two_m_f);
-            if (dq <= tau) break;  // locally converged
-        }
+        ST(run_phase(false, &li));
         st.move_iterations += li;
-        if (trace) q.record(lp, 2, q.Cp, n);
+        if (trace) {
+            if (relabel) {
+                CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cd, s));
+                q.record(lp, 2, q.Cd, n);
+            } else {
+                q.record(lp, 2, q.Cp, n);
+            }
+        }
         // ---- refinement phase (Algorithm 3)
         ST(mark(1));
-        CK(cudaMemcpyAsync(q.CB, q.Cp, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        CK(launch_iota(q.Cp, n, s));
-        CK(cudaMemcpyAsync(q.Sig, q.K, accsz * n, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(sCB, sC, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+        CK(launch_iota(sC, n, s));
+        CK(cudaMemcpyAsync(q.Sig, sK, accsz * n, cudaMemcpyDeviceToDevice, s));
         CK(launch_fill_i32(q.size, 1, n, s));
         q.launches += 2;
         int lj = 0;
-        for (int32_t it = 0; it < prm.max_iterations; ++it) {
-            lj++;
-            CK(cudaMemsetAsync(&q.dsc->moved, 0, sizeof(unsigned long long), s));
-            ST(run_steps(true));
-            ST(q.sync_scalars());
-            if (q.hsc->moved == 0 || (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP)) break;
+        ST(run_phase(true, &lj));
+        if (relabel) {  // back to the ids of G'
+            CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cp, s));
+            CK(launch_labels_to_old(sCB, q.list, q.rinv, n, q.CB, s));
+            q.launches += 2;
         }
         st.refine_iterations += lj;
         if (trace) q.record(lp, 3, q.Cp, n);
         // ---- stop tests (readings R4, R5')
         ST(mark(3));
-        CK(launch_nonempty_flags(q.size, n, q.flag, s));
+        // non-empty refined communities: the labels present in C' (ids of G')
+        CK(launch_fill_i32(q.flag, 0, n, s));
+        CK(launch_mark_labels(q.Cp, n, q.flag, s));
         CK(launch_exclusive_scan_i32(q.flag, q.pos, n, q.scan_tmp, s));
         CK(launch_fill_i32(q.rep, 0, n, s));
         CK(launch_mark_labels(q.CB, n, q.rep, s));
@@ -616,7 +742,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         }
         CK(launch_exclusive_scan(q.tdeg, q.agg[dst].off, ncomm, q.scan_tmp, s));
         CK(launch_comm_bin_keys(q.tdeg, ncomm, q.key, s));
-        CK(launch_partition(q.key, ncomm, kNumBins, q.key_cnt, q.key_off, q.list, q.scan_tmp, s));
+        CK(launch_partition(q.key, ncomm, kNumBins, q.key_off, q.list, q.part_tmp, s));
         CK(launch_max_i64(q.tdeg, ncomm, &q.dsc->maxtdeg, s));
         q.launches += 16;
         int64_t cap = 0;
@@ -631,7 +757,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             int64_t mt = (int64_t)q.hsc->maxtdeg;
             if (mt > ncomm) mt = ncomm;
             int abits = 0, aregions = 0;
-            if (ako[8] > ako[7]) {
+            if (ako[kBinHub + 1] > ako[kBinHub]) {
                 abits = ceil_log2_h(2 * mt);
                 if (abits < 6) abits = 6;
                 const size_t per = ((size_t)1 << abits) * 12;
@@ -657,7 +783,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             for (int b = 1; b < kNumBins; ++b) {
                 const int64_t lo = ako[b], hi = ako[b + 1];
                 if (hi == lo) continue;
-                const int mb = b <= 5 ? tile_blocks : (b == 6 ? big_blocks : aregions);
+                const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : aregions);
                 ac.prof = prof_begin(16 + b);
                 CK(launch_aggregate(ac, b, q.list + lo, hi - lo, mb, s));
                 prof_end();
@@ -695,6 +821,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             q.trace_count[{lp, 9}] = cap;
         }
         G = G2;
+        Gcap = cap;
         cur_agg = dst;
         tau /= prm.tolerance_drop;  // threshold scaling
     }

@@ -311,12 +311,11 @@ cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t cou
         return (int)(b < max_blocks ? (b < 1 ? 1 : b) : max_blocks);
     };
     switch (bin) {
-        case 1: k_agg_tile<P, Wi, Wo, 4><<<grid(64), 256, 0, s>>>(a, list, count); break;
-        case 2: k_agg_tile<P, Wi, Wo, 8><<<grid(32), 256, 0, s>>>(a, list, count); break;
-        case 3: k_agg_tile<P, Wi, Wo, 16><<<grid(16), 256, 0, s>>>(a, list, count); break;
-        case 4: k_agg_tile<P, Wi, Wo, 32><<<grid(8), 256, 0, s>>>(a, list, count); break;
-        case 5: k_agg_warp<P, Wi, Wo><<<grid(8), 256, 0, s>>>(a, list, count); break;
-        case 6: {
+        case 1: k_agg_tile<P, Wi, Wo, 8><<<grid(32), 256, 0, s>>>(a, list, count); break;
+        case 2: k_agg_tile<P, Wi, Wo, 16><<<grid(16), 256, 0, s>>>(a, list, count); break;
+        case 3: k_agg_tile<P, Wi, Wo, 32><<<grid(8), 256, 0, s>>>(a, list, count); break;
+        case 4: k_agg_warp<P, Wi, Wo><<<grid(8), 256, 0, s>>>(a, list, count); break;
+        case 5: {
             const size_t sm = (sizeof(typename P::acc) + sizeof(int32_t)) * kBlockSlots;
             auto kern = k_agg_block<P, Wi, Wo, false>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -324,7 +323,7 @@ cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t cou
             kern<<<grid(1), kAggThreads, sm, s>>>(a, list, count);
             break;
         }
-        case 7: k_agg_block<P, Wi, Wo, true><<<grid(1), kAggThreads, 0, s>>>(a, list, count); break;
+        case 6: k_agg_block<P, Wi, Wo, true><<<grid(1), kAggThreads, 0, s>>>(a, list, count); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -2,8 +2,8 @@
 // SplitMix64; u precedes v when prio(u) > prio(v) (ties: smaller id).
 // layer(v) = 1 + max layer of v's preceding neighbours (0 if none): the
 // rounds of Jones & Plassmann's parallel colouring. They are found level by
-// level: cnt[v] counts v's preceding neighbours; a vertex enters round r+1
-// when the last of them is settled in round r. Rounds stop at layer L-2;
+// level: cnt[v] counts v's preceding neighbours; a vertex enters layer r+1
+// when the last of them is released in round r. Rounds stop at layer L-2;
 // every vertex not placed by then takes step L-1 + ((prio >> 32) mod B).
 #include "common.cuh"
 #include "kernels.h"
@@ -11,58 +11,39 @@
 namespace lgb {
 namespace {
 
-constexpr int kSchedLanes = 8;  // lanes per vertex
-
+// cnt[v] = number of v's preceding neighbours; layer[v] = 0 if none
 __global__ void __launch_bounds__(256) k_sched_init(int64_t n, const int64_t *off, const int32_t *deg,
                                                     const int32_t *idx, uint64_t state, int32_t *cnt,
-                                                    int32_t *layer, int32_t *flist, int32_t *fcount) {
-    const int lane = threadIdx.x & 31;
-    const int tl = lane & (kSchedLanes - 1);
-    const unsigned tmask = 0xffu << (lane & ~(kSchedLanes - 1));
-    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kSchedLanes);
-    for (int64_t v = (int64_t)blockIdx.x * (blockDim.x / kSchedLanes) + threadIdx.x / kSchedLanes; v < n;
-         v += groups) {
+                                                    int32_t *layer) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t pv = splitmix64_at(state, (uint64_t)v);
         const int64_t e0 = off[v];
         const int32_t dv = deg[v];
         int32_t c = 0;
-        for (int32_t e = tl; e < dv; e += kSchedLanes) {
+        for (int32_t e = 0; e < dv; ++e) {
             const int32_t u = idx[e0 + e];
             if (u != (int32_t)v && precedes(splitmix64_at(state, (uint64_t)u), u, pv, (int32_t)v)) c++;
         }
-        for (int o = kSchedLanes / 2; o > 0; o >>= 1) c += __shfl_xor_sync(tmask, c, o, kSchedLanes);
-        if (tl == 0) {
-            cnt[v] = c;
-            layer[v] = c == 0 ? 0 : -1;
-            if (c == 0) flist[atomicAdd(&fcount[0], 1)] = (int32_t)v;
-        }
+        cnt[v] = c;
+        layer[v] = c == 0 ? 0 : -1;
     }
 }
 
-// round r: settle the successors of the vertices of layer r
-__global__ void __launch_bounds__(256) k_sched_round(const int64_t *off, const int32_t *deg, const int32_t *idx,
-                                                     uint64_t state, int32_t r, int32_t *cnt, int32_t *layer,
-                                                     int32_t *flist, int64_t *fstart, int32_t *fcount) {
-    const int lane = threadIdx.x & 31;
-    const int tl = lane & (kSchedLanes - 1);
-    const int64_t start = fstart[r];
-    const int64_t count = fcount[r];
-    const int64_t next = start + count;
-    if (blockIdx.x == 0 && threadIdx.x == 0) fstart[r + 1] = next;
-    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kSchedLanes);
-    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x / kSchedLanes) + threadIdx.x / kSchedLanes; t < count;
-         t += groups) {
-        const int32_t v = flist[start + t];
+// round r: every vertex of layer r releases its succeeding neighbours; a
+// neighbour whose last preceding neighbour is released joins layer r+1. The
+// round scans the layer array (coalesced) instead of keeping frontier lists.
+__global__ void __launch_bounds__(256) k_sched_round(int64_t n, const int64_t *off, const int32_t *deg,
+                                                     const int32_t *idx, uint64_t state, int32_t r, int32_t *cnt,
+                                                     int32_t *layer) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (__ldcg(&layer[v]) != r) continue;
         const uint64_t pv = splitmix64_at(state, (uint64_t)v);
         const int64_t e0 = off[v];
         const int32_t dv = deg[v];
-        for (int32_t e = tl; e < dv; e += kSchedLanes) {
+        for (int32_t e = 0; e < dv; ++e) {
             const int32_t u = idx[e0 + e];
-            if (u == v || !precedes(pv, v, splitmix64_at(state, (uint64_t)u), u)) continue;
-            if (atomicSub(&cnt[u], 1) == 1) {
-                layer[u] = r + 1;
-                flist[next + atomicAdd(&fcount[r + 1], 1)] = u;
-            }
+            if (u == (int32_t)v || !precedes(pv, (int32_t)v, splitmix64_at(state, (uint64_t)u), u)) continue;
+            if (atomicSub(&cnt[u], 1) == 1) layer[u] = r + 1;
         }
     }
 }
@@ -84,7 +65,8 @@ __global__ void k_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t
                                 int32_t *key) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int b = degree_bin(deg[v]);
-        key[v] = b == 0 ? -1 : (bin_major ? b * nsteps + step[v] : step[v] * kNumBins + b);
+        // vertices without edges go to a trailing bucket (never swept)
+        key[v] = b == 0 ? nsteps * kNumBins : (bin_major ? b * nsteps + step[v] : step[v] * kNumBins + b);
     }
 }
 
@@ -99,18 +81,13 @@ inline int grid_for(int64_t items, int per_block) {
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
                             int32_t *step, cudaStream_t s) {
     if (g.n <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(w.fcount, 0, sizeof(int32_t) * (L + 1), s);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(w.fstart, 0, sizeof(int64_t) * (L + 1), s)) != cudaSuccess) return e;
-    k_sched_init<<<grid_for(g.n, 256 / kSchedLanes), 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, w.cnt, w.layer,
-                                                                 w.flist, w.fcount);
+    const int grid = grid_for(g.n, 256);
+    k_sched_init<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, w.cnt, w.layer);
     for (int32_t r = 0; r + 2 <= L - 1; ++r)  // produce layers 1 .. L-2
-        k_sched_round<<<grid_for(g.n, 256 / kSchedLanes), 256, 0, s>>>(g.off, g.deg, g.idx, state, r, w.cnt, w.layer,
-                                                                      w.flist, w.fstart, w.fcount);
-    k_sched_finish<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, state, L, B, w.layer, step);
+        k_sched_round<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, r, w.cnt, w.layer);
+    k_sched_finish<<<grid, 256, 0, s>>>(g.n, state, L, B, w.layer, step);
     return cudaGetLastError();
 }
-
 cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
                                  int32_t *key, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

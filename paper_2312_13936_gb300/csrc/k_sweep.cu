@@ -4,11 +4,13 @@
 // communities (scanCommunities / scanBounded), compute the Eq. 2 gain of
 // every candidate, take the best (ties: lowest community id) and compare it
 // with staying. The accumulation structure depends on the degree bin:
-//   bins 1-4  a tile of 4/8/16/32 lanes holds one edge per lane; equal
+//   bin 1     one thread per vertex, up to 8 edges in registers, merged by
+//             pairwise comparison (32 vertices per warp, 8 loads in flight each);
+//   bins 2-3  a tile of 16/32 lanes holds one edge per lane; equal
 //             communities are merged with register shuffles;
-//   bin 5     one warp per vertex, open-addressing table in shared memory;
-//   bin 6     one block per vertex, shared-memory table;
-//   bin 7     one block per vertex, table in global memory (hubs).
+//   bin 4     one warp per vertex, open-addressing table in shared memory;
+//   bin 5     one block per vertex, shared-memory table;
+//   bin 6     one block per vertex, table in global memory (hubs).
 //
 // A sweep visits the schedule steps in order (reading S0). The main kernel,
 // k_sweep_coop, is persistent: one cooperative launch runs every step of a
@@ -51,6 +53,11 @@ template <class P, class W> struct SV {
     double gamma;
     int32_t cur_step, cap_step, nsteps;
     const int64_t *key_off;
+    int32_t max_it, single_sweep;
+    double tau;
+    A *dq_arr;                     // per-sweep gain sums (persistent phase)
+    unsigned long long *moved_arr; // per-sweep refinement moves (persistent phase)
+    int32_t *iters_out;
     A *dq_acc;
     unsigned long long *moved;
     int32_t *hub_keys;
@@ -83,6 +90,12 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.cap_step = c.cap_step;
     a.nsteps = c.nsteps;
     a.key_off = c.key_off;
+    a.max_it = c.max_it;
+    a.single_sweep = c.single_sweep;
+    a.tau = c.tau;
+    a.dq_arr = static_cast<A *>(c.dq_arr);
+    a.moved_arr = c.moved_arr;
+    a.iters_out = c.iters_out;
     a.dq_acc = static_cast<A *>(c.dq_acc);
     a.moved = c.moved;
     a.hub_keys = c.hub_keys;
@@ -156,6 +169,89 @@ __device__ __forceinline__ bool take_vertex(const SV<P, W> &a, int32_t v, int32_
         d = ldm(&a.C[v]);
     }
     return e;
+}
+
+// --------------------------------------------------------- thread bin
+template <class P, class W, bool REFINE>
+__device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
+                                           int32_t cur_step, typename P::acc &local_gain, ProfCounts &pc) {
+    using A = typename P::acc;
+    constexpr int E = kThreadMaxDeg;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += nthreads) {
+        const int32_t v = list[t];
+        int32_t d = 0;
+        if (!take_vertex<P, W, REFINE>(a, v, d)) {
+            if (REFINE || P::det) a.prop[v] = -1;
+            pc.v[1]++;
+            continue;
+        }
+        const A Kv = a.K[v];
+        const int64_t e0 = a.off[v];
+        const int32_t dv = a.deg[v];
+        const int32_t bv = REFINE ? a.CB[v] : 0;
+        int32_t jj[E];
+        A wt[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            jj[k] = -1;
+            wt[k] = 0;
+            if (k < dv) {
+                jj[k] = a.idx[e0 + k];
+                wt[k] = wconv<A>(a.w[e0 + k]);
+            }
+        }
+        int32_t c[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            c[k] = -1;
+            bool ok = k < dv && jj[k] != v;
+            if (REFINE && ok) ok = (__ldg(&a.CB[jj[k]]) == bv);
+            if (ok) c[k] = ldm(&a.C[jj[k]]);
+        }
+        // merge equal communities into their first entry, in edge order
+#pragma unroll
+        for (int k = 1; k < E; ++k)
+#pragma unroll
+            for (int k2 = 0; k2 < k; ++k2)
+                if (c[k] >= 0 && c[k2] == c[k]) {
+                    wt[k2] += wt[k];
+                    c[k] = -1;
+                }
+        A kvd = 0;
+        A key = AccLimits<A>::lowest();
+        int32_t cand = INT_MAX;
+        int distinct = 0;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            if (c[k] < 0) continue;
+            distinct++;
+            if (c[k] == d) {
+                kvd = wt[k];
+                continue;
+            }
+            const A kk = move_key(a.two_m, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma);
+            if (better(kk, c[k], key, cand)) {
+                key = kk;
+                cand = c[k];
+            }
+        }
+        const bool mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain, cur_step);
+        if (a.prof) {
+            pc.v[0]++;
+            pc.v[2] += dv;
+            pc.v[3] += distinct;
+            if ((REFINE || P::det) ? (a.prop[v] >= 0) : mv) {
+                pc.v[4]++;
+                pc.v[5] += dv;
+            }
+        }
+        if (!REFINE && !P::det && mv) {
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+                if (k < dv) a.unproc[jj[k]] = 1;  // neighbours (self-loop included) of a mover
+        }
+    }
 }
 
 // ----------------------------------------------------------- tile bins
@@ -536,58 +632,92 @@ template <class A> __device__ __forceinline__ int32_t *table_keys() {
     return reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
 }
 
+// One whole phase: sweeps until the phase converges -- local-moving stops
+// when a sweep's delta-modularity (reading S4 for the deterministic mode) is
+// at most tau (Algorithm 2), refinement when a sweep moves nobody (reading
+// R6) -- or max_it sweeps ran. The test reads per-sweep sums after a grid
+// barrier, so every block takes the same decision.
 template <class P, class W, bool REFINE>
 __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, const int32_t *__restrict__ list) {
     using A = typename P::acc;
     int32_t *skeys = table_keys<A>();
     A *svals = table_vals<A>();
-    const int wib = threadIdx.x >> 5;
-    A local_gain = 0;
-    long long det_gain = 0;
-    unsigned long long moved = 0;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ProfCounts pc;
-    for (int32_t k = 0; k < a.nsteps; ++k) {
-        const int64_t *ko = a.key_off + (int64_t)k * kNumBins;
-        const int64_t b0 = __ldcg(&ko[0]), b8 = __ldcg(&ko[8]);
-        if (b0 == b8) continue;  // empty step: every block sees the same counts
-        run_tile<P, W, 4, REFINE>(a, list, __ldcg(&ko[1]), __ldcg(&ko[2]), k, local_gain, pc);
-        run_tile<P, W, 8, REFINE>(a, list, __ldcg(&ko[2]), __ldcg(&ko[3]), k, local_gain, pc);
-        run_tile<P, W, 16, REFINE>(a, list, __ldcg(&ko[3]), __ldcg(&ko[4]), k, local_gain, pc);
-        run_tile<P, W, 32, REFINE>(a, list, __ldcg(&ko[4]), __ldcg(&ko[5]), k, local_gain, pc);
-        run_warp<P, W, REFINE>(a, list, __ldcg(&ko[5]), __ldcg(&ko[6]), k, skeys + wib * kWarpSlots,
-                               svals + wib * kWarpSlots, local_gain, pc);
-        const int64_t b6 = __ldcg(&ko[6]), b7 = __ldcg(&ko[7]);
-        if (b7 > b6) {
-            __syncthreads();  // the warp tables become one block table
-            run_block<P, W, REFINE, false>(a, list, b6, b7, k, skeys, svals, ceil_log2(kBlockSlots), local_gain, pc);
+    int32_t it = 0;
+    bool ok = true;
+    while (ok && it < a.max_it) {
+        A local_gain = 0;
+        long long det_gain = 0;
+        unsigned long long moved = 0;
+        for (int32_t k = 0; k < a.nsteps && ok; ++k) {
+            const int64_t *ko = a.key_off + (int64_t)k * kNumBins;
+            const int64_t b0 = __ldcg(&ko[0]), b8 = __ldcg(&ko[8]);
+            if (b0 == b8) continue;  // empty step: every block sees the same counts
+            run_thread<P, W, REFINE>(a, list, __ldcg(&ko[1]), __ldcg(&ko[2]), k, local_gain, pc);
+            run_tile<P, W, 16, REFINE>(a, list, __ldcg(&ko[2]), __ldcg(&ko[3]), k, local_gain, pc);
+            run_tile<P, W, 32, REFINE>(a, list, __ldcg(&ko[3]), __ldcg(&ko[4]), k, local_gain, pc);
+            run_warp<P, W, REFINE>(a, list, __ldcg(&ko[4]), __ldcg(&ko[5]), k, skeys + wib * kWarpSlots,
+                                   svals + wib * kWarpSlots, local_gain, pc);
+            const int64_t b5 = __ldcg(&ko[5]), b6 = __ldcg(&ko[6]), b7 = __ldcg(&ko[7]);
+            if (b6 > b5) {
+                __syncthreads();  // the warp tables become one block table
+                run_block<P, W, REFINE, false>(a, list, b5, b6, k, skeys, svals, ceil_log2(kBlockSlots), local_gain,
+                                               pc);
+            }
+            if (b7 > b6) {
+                const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
+                run_block<P, W, REFINE, true>(a, list, b6, b7, k, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
+                                              local_gain, pc);
+            }
+            if (!(ok = grid_barrier(a.bar, a.err))) break;
+            if (REFINE || P::det) {
+                if (REFINE) run_refine_apply(a, list, b0, b8, k, moved);
+                else run_move_apply(a, list, b0, b8, det_gain);
+                if (!(ok = grid_barrier(a.bar, a.err))) break;
+            }
         }
-        if (b8 > b7) {
-            const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
-            run_block<P, W, REFINE, true>(a, list, b7, b8, k, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
-                                          local_gain, pc);
+        if (!ok) break;
+        // this sweep's totals, then the convergence test
+        if (REFINE) {
+            moved = warp_sum(moved);
+            if (lane == 0 && moved) atomicAdd(&a.moved_arr[it], moved);
+        } else if (P::det) {
+            det_gain = warp_sum(det_gain);
+            if (lane == 0 && det_gain) atomic_add_acc(reinterpret_cast<long long *>(&a.dq_arr[it]), det_gain);
+        } else {
+            const A s = warp_sum(local_gain);
+            if (lane == 0 && s != (A)0) atomic_add_acc(&a.dq_arr[it], s);
         }
-        if (!grid_barrier(a.bar, a.err)) break;
-        if (REFINE || P::det) {
-            if (REFINE) run_refine_apply(a, list, b0, b8, k, moved);
-            else run_move_apply(a, list, b0, b8, det_gain);
-            if (!grid_barrier(a.bar, a.err)) break;
+        if (!(ok = grid_barrier(a.bar, a.err))) break;
+        bool stop;
+        if (REFINE) {
+            stop = __ldcg(&a.moved_arr[it]) == 0ULL || a.single_sweep;
+        } else {
+            const double tm = (double)a.two_m;
+            const double dq = 2.0 * (double)ldm(&a.dq_arr[it]) / (tm * tm);
+            stop = dq <= a.tau;
         }
+        ++it;
+        if (stop) break;
     }
-    const int lane = threadIdx.x & 31;
-    if (REFINE) {
-        moved = warp_sum(moved);
-        if (lane == 0 && moved) atomicAdd(a.moved, moved);
-    } else if (P::det) {
-        det_gain = warp_sum(det_gain);
-        if (lane == 0 && det_gain) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), det_gain);
-    } else {
-        const A s = warp_sum(local_gain);
-        if (lane == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters_out = it;
     pc.flush(a.prof);
 }
 
 // ------------------------------------------- one (step, bin) per launch
+template <class P, class W, bool REFINE>
+__global__ void __launch_bounds__(256) k_eval_thread(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
+    using A = typename P::acc;
+    A local_gain = 0;
+    ProfCounts pc;
+    run_thread<P, W, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
+    if (!REFINE && !P::det) {
+        const A s = warp_sum(local_gain);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+    }
+    pc.flush(a.prof);
+}
 template <class P, class W, int T, bool REFINE>
 __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
     using A = typename P::acc;
@@ -668,23 +798,22 @@ cudaError_t eval_typed(const SweepCtx &c, int bin, const int32_t *list, int64_t 
         return (int)(b < max_blocks ? (b < 1 ? 1 : b) : max_blocks);
     };
     switch (bin) {
-        case 1: k_eval_tile<P, W, 4, REFINE><<<grid(64), 256, 0, s>>>(a, list, count); break;
-        case 2: k_eval_tile<P, W, 8, REFINE><<<grid(32), 256, 0, s>>>(a, list, count); break;
-        case 3: k_eval_tile<P, W, 16, REFINE><<<grid(16), 256, 0, s>>>(a, list, count); break;
-        case 4: k_eval_tile<P, W, 32, REFINE><<<grid(8), 256, 0, s>>>(a, list, count); break;
-        case 5: {
+        case 1: k_eval_thread<P, W, REFINE><<<grid(256), 256, 0, s>>>(a, list, count); break;
+        case 2: k_eval_tile<P, W, 16, REFINE><<<grid(16), 256, 0, s>>>(a, list, count); break;
+        case 3: k_eval_tile<P, W, 32, REFINE><<<grid(8), 256, 0, s>>>(a, list, count); break;
+        case 4: {
             cudaError_t e = allow_table_smem(k_eval_warp<P, W, REFINE>, tb);
             if (e != cudaSuccess) return e;
             k_eval_warp<P, W, REFINE><<<grid(8), 256, tb, s>>>(a, list, count);
             break;
         }
-        case 6: {
+        case 5: {
             cudaError_t e = allow_table_smem(k_eval_block<P, W, REFINE, false>, tb);
             if (e != cudaSuccess) return e;
             k_eval_block<P, W, REFINE, false><<<grid(1), 256, tb, s>>>(a, list, count);
             break;
         }
-        case 7:
+        case 6:
             a.hub_regions = max_blocks;
             k_eval_block<P, W, REFINE, true><<<grid(1), 256, 0, s>>>(a, list, count);
             break;

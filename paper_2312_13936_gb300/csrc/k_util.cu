@@ -30,38 +30,40 @@ __global__ void k_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err)
     }
 }
 
-// K_i = sum of row i. Rows up to 64 entries by one thread, longer rows by a warp.
+// K_i = sum of row i. One thread per row; rows longer than 64 entries are
+// summed by the whole warp, one such row after another.
 template <class A, class W>
 __global__ void k_vertex_weights(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K, A *two_m) {
-    A local = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t d = deg[i];
-        if (d > 64) continue;
-        const int64_t e0 = off[i];
-        A s = 0;
-        for (int32_t e = 0; e < d; ++e) s += wconv<A>(w[e0 + e]);
-        K[i] = s;
-        local += s;
-    }
-    local = warp_sum(local);
-    if ((threadIdx.x & 31) == 0 && local != (A)0) atomic_add_acc(two_m, local);
-}
-template <class A, class W>
-__global__ void k_vertex_weights_long(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K, A *two_m) {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
-        const int32_t d = deg[i];
-        if (d <= 64) continue;
-        const int64_t e0 = off[i];
-        A s = 0;
-        for (int32_t e = lane; e < d; e += 32) s += wconv<A>(w[e0 + e]);
-        s = warp_sum(s);
-        if (lane == 0) {
+    A local = 0;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        const int32_t d = i < n ? deg[i] : 0;
+        if (i < n && d <= 64) {
+            const int64_t e0 = off[i];
+            A s = 0;
+            for (int32_t e = 0; e < d; ++e) s += wconv<A>(w[e0 + e]);
             K[i] = s;
-            atomic_add_acc(two_m, s);
+            local += s;
+        }
+        unsigned longs = __ballot_sync(kFull, i < n && d > 64);
+        while (longs) {
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int64_t r = __shfl_sync(kFull, i, src);
+            const int32_t dr = __shfl_sync(kFull, d, src);
+            const int64_t e0 = off[r];
+            A s = 0;
+            for (int32_t e = lane; e < dr; e += 32) s += wconv<A>(w[e0 + e]);
+            s = warp_sum(s);
+            if (lane == src) {
+                K[r] = s;
+                local += s;
+            }
         }
     }
+    local = warp_sum(local);
+    if (lane == 0 && local != (A)0) atomic_add_acc(two_m, local);
 }
 
 // ---- exclusive scan: tile reduce, scan of tile sums, tile rescan
@@ -150,32 +152,66 @@ template <class T> cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, v
     return cudaGetLastError();
 }
 
-// ---- partition by key: histogram, scan, scatter
-__global__ void k_part_count(const int32_t *key, int64_t n, int32_t nkeys, int64_t *counts) {
+// ---- stable partition by key (a counting sort): every block owns a tile of
+// kPartTile consecutive items; counts per (key, block) are scanned key-major,
+// so the items of one key keep their input order.
+constexpr int kPartThreads = 256;
+constexpr int kPartRounds = 8;
+constexpr int kPartTile = kPartThreads * kPartRounds;
+
+__global__ void __launch_bounds__(kPartThreads) k_spart_count(const int32_t *key, int64_t n, int32_t nkeys,
+                                                              int64_t nblocks, int64_t *counts) {
     extern __shared__ int32_t s_cnt[];
     for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_cnt[k] = 0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t k = key[i];
-        if (k >= 0) atomicAdd(&s_cnt[k], 1);
+    const int64_t base = (int64_t)blockIdx.x * kPartTile;
+    for (int r = 0; r < kPartRounds; ++r) {
+        const int64_t i = base + (int64_t)r * kPartThreads + threadIdx.x;
+        if (i < n) {
+            const int32_t k = key[i];
+            if (k >= 0) atomicAdd(&s_cnt[k], 1);
+        }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nkeys; k += blockDim.x)
-        if (s_cnt[k]) atomicAdd(reinterpret_cast<unsigned long long *>(&counts[k]), (unsigned long long)s_cnt[k]);
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) counts[(int64_t)k * nblocks + blockIdx.x] = s_cnt[k];
 }
-__global__ void k_part_scatter(const int32_t *key, int64_t n, const int64_t *key_off, int64_t *cursor, int32_t *list) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
+
+__global__ void k_spart_key_off(const int64_t *pos, int32_t nkeys, int64_t nblocks, int64_t *key_off) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= nkeys; k += (int64_t)gridDim.x * blockDim.x)
+        key_off[k] = pos[k * nblocks];
+}
+
+// within a tile, warps take the items of a round in lane order; per key, a
+// warp's items land after those of lower warps and earlier rounds
+__global__ void __launch_bounds__(kPartThreads) k_spart_scatter(const int32_t *key, int64_t n, int32_t nkeys,
+                                                                int64_t nblocks, const int64_t *pos, int32_t *list) {
+    extern __shared__ int32_t s_run[];      // nkeys running counts
+    __shared__ int32_t s_wcnt[kPartThreads / 32][32];  // per warp: count of the key its lane leads
+    __shared__ int32_t s_wkey[kPartThreads / 32][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < nkeys; k += blockDim.x) s_run[k] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kPartTile;
+    for (int r = 0; r < kPartRounds; ++r) {
+        const int64_t i = base + (int64_t)r * kPartThreads + threadIdx.x;
         const int32_t k = i < n ? key[i] : -1;
         const unsigned peers = __match_any_sync(kFull, k);
         const int leader = __ffs(peers) - 1;
         const int rank = __popc(peers & ((1u << lane) - 1u));
-        int64_t base = 0;
-        if (lane == leader && k >= 0)
-            base = (int64_t)atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[k]), (unsigned long long)__popc(peers));
-        base = __shfl_sync(kFull, base, leader);
-        if (k >= 0) list[key_off[k] + base + rank] = (int32_t)i;
+        // leaders publish their key and count
+        s_wkey[wib][lane] = (lane == leader && k >= 0) ? k : -1;
+        s_wcnt[wib][lane] = (lane == leader && k >= 0) ? __popc(peers) : 0;
+        __syncthreads();
+        if (k >= 0) {
+            int before = 0;  // items of key k in lower warps of this round
+            for (int w2 = 0; w2 < wib; ++w2)
+                for (int l2 = 0; l2 < 32; ++l2)
+                    if (s_wkey[w2][l2] == k) before += s_wcnt[w2][l2];
+            list[pos[(int64_t)k * nblocks + blockIdx.x] + s_run[k] + before + rank] = (int32_t)i;
+        }
+        __syncthreads();
+        if (k >= 0 && lane == leader) atomicAdd(&s_run[k], __popc(peers));
+        __syncthreads();
     }
 }
 
@@ -249,22 +285,15 @@ cudaError_t launch_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err
 }
 cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *two_m, cudaStream_t s) {
     if (g.n <= 0) return cudaSuccess;
-    const int gb = grid_for(g.n, 256), gw = grid_for(g.n * 32, 256);
+    const int gb = grid_for(g.n, 256);
     if (det) {
         auto *k = static_cast<long long *>(K);
         auto *t = static_cast<long long *>(two_m);
-        if (g.w_int) {
-            k_vertex_weights<long long, int32_t><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
-            k_vertex_weights_long<long long, int32_t><<<gw, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
-        } else {
-            k_vertex_weights<long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
-            k_vertex_weights_long<long long, float><<<gw, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
-        }
+        if (g.w_int) k_vertex_weights<long long, int32_t><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
+        else k_vertex_weights<long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
     } else {
-        auto *k = static_cast<double *>(K);
-        auto *t = static_cast<double *>(two_m);
-        k_vertex_weights<double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
-        k_vertex_weights_long<double, float><<<gw, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+        k_vertex_weights<double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, static_cast<double *>(K),
+                                                          static_cast<double *>(two_m));
     }
     return cudaGetLastError();
 }
@@ -275,15 +304,31 @@ cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, vo
 cudaError_t launch_exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
     return scan_impl<int32_t>(in, out, n, tmp, s);
 }
-cudaError_t launch_partition(const int32_t *key, int64_t n, int32_t nkeys, int64_t *counts, int64_t *key_off,
-                             int32_t *list, void *tmp, cudaStream_t s) {
+size_t partition_tmp_bytes(int64_t n, int32_t nkeys) {
+    const int64_t nblocks = (n + kPartTile - 1) / kPartTile;
+    const int64_t cells = (int64_t)nkeys * (nblocks < 1 ? 1 : nblocks) + 1;
+    return (size_t)(2 * cells) * sizeof(int64_t) + scan_tmp_bytes(cells);
+}
+cudaError_t launch_partition(const int32_t *key, int64_t n, int32_t nkeys, int64_t *key_off, int32_t *list, void *tmp,
+                             cudaStream_t s) {
     if (nkeys > 8192) return cudaErrorInvalidValue;
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * nkeys, s);
-    if (e != cudaSuccess) return e;
-    if (n > 0) k_part_count<<<grid_for(n, 256, 152 * 4), 256, sizeof(int32_t) * nkeys, s>>>(key, n, nkeys, counts);
-    if ((e = scan_impl<int64_t>(counts, key_off, nkeys, tmp, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * nkeys, s)) != cudaSuccess) return e;
-    if (n > 0) k_part_scatter<<<grid_for(n, 256), 256, 0, s>>>(key, n, key_off, counts, list);
+    int64_t nblocks = (n + kPartTile - 1) / kPartTile;
+    if (nblocks < 1) nblocks = 1;
+    const int64_t cells = (int64_t)nkeys * nblocks;
+    int64_t *counts = static_cast<int64_t *>(tmp);
+    int64_t *pos = counts + cells + 1;
+    void *stmp = pos + cells + 1;
+    cudaError_t e;
+    if (n > 0) {
+        k_spart_count<<<(unsigned)nblocks, kPartThreads, sizeof(int32_t) * nkeys, s>>>(key, n, nkeys, nblocks, counts);
+    } else if ((e = cudaMemsetAsync(counts, 0, sizeof(int64_t) * cells, s)) != cudaSuccess) {
+        return e;
+    }
+    if ((e = scan_impl<int64_t>(counts, pos, cells, stmp, s)) != cudaSuccess) return e;
+    k_spart_key_off<<<grid_for(nkeys + 1, 256), 256, 0, s>>>(pos, nkeys, nblocks, key_off);
+    if (n > 0)
+        k_spart_scatter<<<(unsigned)nblocks, kPartThreads, sizeof(int32_t) * nkeys, s>>>(key, n, nkeys, nblocks, pos,
+                                                                                       list);
     return cudaGetLastError();
 }
 cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *out, cudaStream_t s) {

@@ -8,15 +8,22 @@ namespace lgb {
 
 // Degree bins of the sweep and aggregation kernels: a vertex (or community)
 // of degree d goes to the first bin whose bound holds it. Bin 0 (no edges)
-// is never listed.
+// is never listed; bin 7 is unused.
+//   bin 1  d <= 8      one thread per vertex (sweeps), a tile of 8 lanes (aggregation)
+//   bin 2  d <= 16     a tile of 16 lanes
+//   bin 3  d <= 32     a tile of 32 lanes
+//   bin 4  d <= 256    one warp, shared-memory table
+//   bin 5  d <= 2048   one block, shared-memory table
+//   bin 6  larger      one block, global-memory table
 constexpr int kNumBins = 8;
-constexpr int kTileBins = 4;        // bins 1..4: a tile of 4/8/16/32 lanes per vertex
-constexpr int kWarpMaxDeg = 256;    // bin 5: one warp, shared-memory table
-constexpr int kBlockMaxDeg = 2048;  // bin 6: one block, shared-memory table; bin 7: global table
+constexpr int kThreadMaxDeg = 8;
+constexpr int kWarpMaxDeg = 256;
+constexpr int kBlockMaxDeg = 2048;
 constexpr int kWarpSlots = 512;     // 8 warp tables fill the same 48 KB as one block table
 constexpr int kBlockSlots = 4096;
+constexpr int kBinHub = 6;
 __host__ __device__ inline int degree_bin(int64_t d) {
-    return d <= 0 ? 0 : d <= 4 ? 1 : d <= 8 ? 2 : d <= 16 ? 3 : d <= 32 ? 4 : d <= kWarpMaxDeg ? 5 : d <= kBlockMaxDeg ? 6 : 7;
+    return d <= 0 ? 0 : d <= kThreadMaxDeg ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= kWarpMaxDeg ? 4 : d <= kBlockMaxDeg ? 5 : 6;
 }
 
 // The current graph G' (a holey CSR, paper Fig. 5): row i is
@@ -51,6 +58,12 @@ struct SweepCtx {
     int32_t cur_step = 0, cap_step = 0;  // steps >= cap_step may hold adjacent vertices
     int32_t nsteps = 0;                  // persistent sweep: steps and their (step, bin) offsets
     const int64_t *key_off = nullptr;    // device, nsteps*kNumBins+1 entries (step-major)
+    // persistent phase: at most max_it sweeps, convergence tested on the device
+    int32_t max_it = 1, single_sweep = 0;
+    double tau = 0;
+    void *dq_arr = nullptr;                 // max_it gain sums (acc type), zeroed
+    unsigned long long *moved_arr = nullptr;  // max_it move counts, zeroed
+    int32_t *iters_out = nullptr;           // sweeps executed
     void *dq_acc = nullptr;       // sweep delta-modularity numerator (acc type)
     unsigned long long *moved = nullptr;  // refinement: accepted moves
     int32_t *hub_keys = nullptr;  // global tables for bin 7 (one region per block)
@@ -73,7 +86,8 @@ cudaError_t launch_sweep_eval(const SweepCtx &c, int bin, const int32_t *list, i
 cudaError_t launch_move_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s);
 // refinement: accept (rule S5) and apply a step's proposals
 cudaError_t launch_refine_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s);
-// one whole sweep (every step, grid barriers between steps) in one cooperative launch
+// one whole phase (sweeps of every step, grid barriers between steps, the
+// convergence test on the device) in one cooperative launch
 cudaError_t launch_sweep_coop(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s);
 int sweep_coop_blocks_per_sm(bool det, bool w_int, bool refine);
 
@@ -109,23 +123,25 @@ cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *t
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t launch_exclusive_scan(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
 cudaError_t launch_exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
-// bucket partition: key[i] in [0, nkeys) or -1 (dropped); counts/offsets sized nkeys(+1)
-cudaError_t launch_partition(const int32_t *key, int64_t n, int32_t nkeys, int64_t *counts, int64_t *key_off,
-                             int32_t *list, void *tmp, cudaStream_t s);
+// stable partition of the items 0..n-1 by key[i] in [0, nkeys) (-1: dropped):
+// list holds the items grouped by key, ascending within a key; key_off has
+// nkeys+1 entries; tmp >= partition_tmp_bytes(n, nkeys)
+size_t partition_tmp_bytes(int64_t n, int32_t nkeys);
+cudaError_t launch_partition(const int32_t *key, int64_t n, int32_t nkeys, int64_t *key_off, int32_t *list, void *tmp,
+                             cudaStream_t s);
 cudaError_t launch_max_i32(const int32_t *a, int64_t n, int32_t *out, cudaStream_t s);
 cudaError_t launch_validate(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int *err,
                             cudaStream_t s);
 
 // ---- schedule (k_schedule.cu): step of every vertex (reading S0)
 struct SchedWork {
-    int32_t *cnt, *layer, *flist;  // n each
-    int64_t *fstart;               // L+1
-    int32_t *fcount;               // L+1
+    int32_t *cnt, *layer;  // n each
 };
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
                             int32_t *step, cudaStream_t s);
 // key[i] = step*kNumBins + bin (step-major: one list per step and bin), or
-// bin*nsteps + step (bin-major: one step-ordered list per bin); -1 if deg == 0
+// bin*nsteps + step (bin-major: one step-ordered list per bin); vertices
+// without edges get key nsteps*kNumBins (a trailing bucket)
 cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
                                  int32_t *key, cudaStream_t s);
 
@@ -165,6 +181,17 @@ cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t
                                     const int32_t *C, double *sigtot, double *sums, cudaStream_t s);
 cudaError_t launch_sum_squares(const double *x, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_max_i64(const int64_t *a, int64_t n, unsigned long long *out, cudaStream_t s);
+// relabelling of a pass's graph for the asynchronous sweeps: vertex p of the
+// relabelled graph is vertex perm[p] of G'; inv is the inverse permutation
+cudaError_t launch_inverse(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s);
+cudaError_t launch_gather_i32(const int32_t *src, const int32_t *map, int64_t n, int32_t *dst, cudaStream_t s);
+cudaError_t launch_gather_8b(const void *src, const int32_t *map, int64_t n, void *dst, cudaStream_t s);
+cudaError_t launch_labels_to_new(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst,
+                                 cudaStream_t s);
+cudaError_t launch_labels_to_old(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst,
+                                 cudaStream_t s);
+cudaError_t launch_permute_rows(const GraphView &g, const int32_t *perm, const int32_t *inv, const int64_t *off2,
+                                int32_t *idx2, void *w2, cudaStream_t s);
 // nonint = 1 if some weight is not an integer; sum += sum of weights (fp64)
 cudaError_t launch_weight_props(const float *w, int64_t m, int *nonint, double *sum, cudaStream_t s);
 
