@@ -8,15 +8,22 @@ namespace lgb {
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Accumulation policies. Deterministic mode decides moves in exact int64
-// arithmetic on integer weights; asynchronous mode accumulates in fp64 (the
-// paper's hashtable precision, Section 5.1.2 "Configuration").
+// Arithmetic policies. acc is the type of per-edge sums (K_{i->c}), vertex
+// weights K_i and move keys; tot the type of community totals Sigma_c and of
+// the sweep's delta-modularity sums. The deterministic mode decides moves in
+// exact int64 arithmetic on integer weights. The asynchronous mode keeps
+// Sigma and 2m in fp64 and everything per edge in fp32: on this GPU the fp64
+// pipe is a small fraction of the fp32 rate, and the move key
+// K_{i->c} - gamma K_i Sigma_c / 2m has terms of the order of K_i, so fp32
+// keeps its relative precision.
 struct Det {
     using acc = long long;
+    using tot = long long;
     static constexpr bool det = true;
 };
 struct Async {
-    using acc = double;
+    using acc = float;
+    using tot = double;
     static constexpr bool det = false;
 };
 
@@ -27,6 +34,9 @@ template <> struct AccLimits<long long> {
 template <> struct AccLimits<double> {
     __device__ static double lowest() { return __longlong_as_double(0xfff0000000000000LL); }  // -inf
 };
+template <> struct AccLimits<float> {
+    __device__ static float lowest() { return __int_as_float(0xff800000); }  // -inf
+};
 
 template <class A, class W> __device__ __forceinline__ A wconv(W w) { return (A)w; }
 
@@ -34,24 +44,29 @@ __device__ __forceinline__ void atomic_add_acc(long long *p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
 }
 __device__ __forceinline__ void atomic_add_acc(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_acc(float *p, float v) { atomicAdd(p, v); }
 
 // Σ reads: the async mode sees concurrent atomics from other SMs, so it reads
 // through L2 (ld.global.cg); deterministic mode reads a snapshot.
 template <class A> __device__ __forceinline__ A load_cg(const A *p) { return __ldcg(p); }
 
-// Eq. 2 scaled by 2m^2: key(c) = 2m*K_{i->c} - gamma*K_i*Sigma_c. The vertex
-// moves to c* iff key(c*) > key_stay = 2m*K_{i->d} - gamma*K_i*(Sigma_d - K_i).
+// Move keys (Eq. 2). Deterministic mode, Eq. 2 times 2m^2 (kscale = 2m):
+//   key(c) = 2m K_{i->c} - K_i Sigma_c,  stay = 2m K_{i->d} - K_i (Sigma_d - K_i).
+// Asynchronous mode, Eq. 2 times m (kscale = 1/2m):
+//   key(c) = K_{i->c} - gamma K_i Sigma_c / 2m,  stay = K_{i->d} - gamma K_i (Sigma_d - K_i) / 2m.
+// The vertex moves to c* iff key(c*) > stay; the gain key(c*) - stay is
+// 2m^2 dQ (deterministic) or m dQ (asynchronous).
 __device__ __forceinline__ long long move_key(long long two_m, long long kic, long long ki, long long sc, double) {
     return two_m * kic - ki * sc;
 }
-__device__ __forceinline__ double move_key(double two_m, double kic, double ki, double sc, double gamma) {
-    return two_m * kic - gamma * ki * sc;
+__device__ __forceinline__ float move_key(float inv2m, float kic, float ki, double sc, double gamma) {
+    return kic - (float)gamma * ki * ((float)sc * inv2m);
 }
 __device__ __forceinline__ long long stay_key(long long two_m, long long kid, long long ki, long long sd, double) {
     return two_m * kid - ki * (sd - ki);
 }
-__device__ __forceinline__ double stay_key(double two_m, double kid, double ki, double sd, double gamma) {
-    return two_m * kid - gamma * ki * (sd - ki);
+__device__ __forceinline__ float stay_key(float inv2m, float kid, float ki, double sd, double gamma) {
+    return kid - (float)gamma * ki * (((float)sd - ki) * inv2m);
 }
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number i+1 of the

@@ -117,6 +117,7 @@ struct Handle::Impl {
     std::vector<int64_t> prof_launches;
     leiden_kernel_profile prof_out[LEIDEN_PROFILE_CLASSES];
     bool prof_valid = false;
+    bool prof_det = false;
 
     cudaEvent_t next_event() {
         if (ev_used == ev_pool.size()) {
@@ -214,10 +215,11 @@ struct Handle::Impl {
                 o.edges = (int64_t)v[2];
                 o.distinct = (int64_t)v[3];
                 o.moved = (int64_t)v[4];
+                const double ksz = prof_det ? 8.0 : 4.0;  // K' is int64 or fp32
                 if (phase == 0)  // list, flag r/w, C, K, offset, degree, Sigma_d | idx, w, C[j] | Sigma_c | move
-                    o.bytes = 38.0 * v[0] + 5.0 * v[1] + 12.0 * v[2] + 8.0 * v[3] + 28.0 * v[4] + 1.0 * v[5];
+                    o.bytes = (30.0 + ksz) * v[0] + 5.0 * v[1] + 12.0 * v[2] + 8.0 * v[3] + 28.0 * v[4] + 1.0 * v[5];
                 else  // + bound C'_B of i and of every neighbour, isolation test, proposal write
-                    o.bytes = 48.0 * v[0] + 16.0 * v[1] + 16.0 * v[2] + 8.0 * v[3];
+                    o.bytes = (40.0 + ksz) * v[0] + 16.0 * v[1] + 16.0 * v[2] + 8.0 * v[3];
             } else {
                 o.items = (int64_t)v[0];
                 o.edges = (int64_t)v[2];
@@ -430,6 +432,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     q.launches = 0;
     const bool profile = (prm.flags & LEIDEN_FLAG_PROFILE) != 0;
     q.prof_valid = false;
+    q.prof_det = det;
     q.ev_used = 0;
     q.prof_spans.clear();
     q.prof_launches.assign(LEIDEN_PROFILE_CLASSES, 0);
@@ -529,7 +532,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             CK(launch_gather_i32(G.deg, perm, n, q.rdeg, s));
             CK(launch_exclusive_scan_i32(q.rdeg, q.roff, n, q.scan_tmp, s));
             CK(launch_permute_rows(G, perm, q.rinv, q.roff, q.ridx, q.rw, s));
-            CK(launch_gather_8b(q.K, perm, n, q.rK, s));
+            CK(launch_gather_i32(static_cast<const int32_t *>(q.K), perm, n, static_cast<int32_t *>(q.rK), s));  // fp32 K
             CK(launch_gather_i32(q.step, perm, n, q.rstep, s));
             CK(launch_labels_to_new(q.Cp, perm, q.rinv, n, q.rC, s));
             q.launches += 9;
@@ -652,7 +655,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                     if (q.hsc->moved == 0 || single) break;
                 } else {
                     const double dq = det ? 2.0 * (double)q.hsc->dq_i / ((double)two_m_i * (double)two_m_i)
-                                          : 2.0 * q.hsc->dq_f / (two_m_f * two_m_f);
+                                          : 2.0 * q.hsc->dq_f / two_m_f;
                     if (dq <= tau) break;  // locally converged
                 }
             }
@@ -677,8 +680,9 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         ST(mark(1));
         CK(cudaMemcpyAsync(sCB, sC, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
         CK(launch_iota(sC, n, s));
-        CK(cudaMemcpyAsync(q.Sig, sK, accsz * n, cudaMemcpyDeviceToDevice, s));
-        CK(launch_fill_i32(q.size, 1, n, s));
+        CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
+        CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
+        CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));  // Sigma' <- K', one member each
         q.launches += 2;
         int lj = 0;
         ST(run_phase(true, &lj));

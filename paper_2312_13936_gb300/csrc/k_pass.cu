@@ -16,11 +16,11 @@ inline int grid_for(int64_t n, int threads) {
 #define GRID_STRIDE(i, n) \
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-template <class A>
-__global__ void k_community_totals(const int32_t *C, const A *K, int64_t n, A *Sig, int32_t *size) {
+template <class A, class T>
+__global__ void k_community_totals(const int32_t *C, const A *K, int64_t n, T *Sig, int32_t *size) {
     GRID_STRIDE(i, n) {
         const int32_t c = C[i];
-        atomic_add_acc(&Sig[c], K[i]);
+        atomic_add_acc(&Sig[c], (T)K[i]);
         atomicAdd(&size[c], 1);
     }
 }
@@ -188,9 +188,10 @@ cudaError_t launch_community_totals(const int32_t *C, const void *K, bool det, i
                                     cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (det)
-        k_community_totals<long long><<<grid_for(n, 256), 256, 0, s>>>(C, (const long long *)K, n, (long long *)Sig, size);
+        k_community_totals<long long, long long><<<grid_for(n, 256), 256, 0, s>>>(C, (const long long *)K, n,
+                                                                                  (long long *)Sig, size);
     else
-        k_community_totals<double><<<grid_for(n, 256), 256, 0, s>>>(C, (const double *)K, n, (double *)Sig, size);
+        k_community_totals<float, double><<<grid_for(n, 256), 256, 0, s>>>(C, (const float *)K, n, (double *)Sig, size);
     return cudaGetLastError();
 }
 cudaError_t launch_nonempty_flags(const int32_t *size, int64_t n, int32_t *flag, cudaStream_t s) {

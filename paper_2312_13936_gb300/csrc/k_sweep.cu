@@ -36,6 +36,7 @@ namespace {
 
 template <class P, class W> struct SV {
     using A = typename P::acc;
+    using T = typename P::tot;
     const int64_t *off;
     const int32_t *deg;
     const int32_t *idx;
@@ -43,22 +44,23 @@ template <class P, class W> struct SV {
     int32_t *C;
     const int32_t *CB;
     const A *K;
-    A *Sig;
+    T *Sig;
     int32_t *size;
     uint8_t *unproc;
     int32_t *prop;
     long long *gain;
     const int32_t *step;
-    A two_m;
+    A kscale;       // 2m (deterministic) or 1/2m (asynchronous), see move_key
+    double two_m_d;
     double gamma;
     int32_t cur_step, cap_step, nsteps;
     const int64_t *key_off;
     int32_t max_it, single_sweep;
     double tau;
-    A *dq_arr;                     // per-sweep gain sums (persistent phase)
+    T *dq_arr;                     // per-sweep gain sums (persistent phase)
     unsigned long long *moved_arr; // per-sweep refinement moves (persistent phase)
     int32_t *iters_out;
-    A *dq_acc;
+    T *dq_acc;
     unsigned long long *moved;
     int32_t *hub_keys;
     A *hub_vals;
@@ -70,6 +72,7 @@ template <class P, class W> struct SV {
 
 template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     using A = typename P::acc;
+    using T = typename P::tot;
     SV<P, W> a;
     a.off = c.g.off;
     a.deg = c.g.deg;
@@ -78,13 +81,14 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.C = c.C;
     a.CB = c.CB;
     a.K = static_cast<const A *>(c.K);
-    a.Sig = static_cast<A *>(c.Sig);
+    a.Sig = static_cast<T *>(c.Sig);
     a.size = c.size;
     a.unproc = c.unproc;
     a.prop = c.prop;
     a.gain = c.gain;
     a.step = c.step;
-    a.two_m = P::det ? (A)c.two_m_i : (A)c.two_m_f;
+    a.kscale = P::det ? (A)c.two_m_i : (A)(1.0 / c.two_m_f);
+    a.two_m_d = P::det ? (double)c.two_m_i : c.two_m_f;
     a.gamma = c.gamma;
     a.cur_step = c.cur_step;
     a.cap_step = c.cap_step;
@@ -93,10 +97,10 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.max_it = c.max_it;
     a.single_sweep = c.single_sweep;
     a.tau = c.tau;
-    a.dq_arr = static_cast<A *>(c.dq_arr);
+    a.dq_arr = static_cast<T *>(c.dq_arr);
     a.moved_arr = c.moved_arr;
     a.iters_out = c.iters_out;
-    a.dq_acc = static_cast<A *>(c.dq_acc);
+    a.dq_acc = static_cast<T *>(c.dq_acc);
     a.moved = c.moved;
     a.hub_keys = c.hub_keys;
     a.hub_vals = static_cast<A *>(c.hub_vals);
@@ -109,6 +113,7 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
 }
 
 __device__ __forceinline__ int32_t ldm(const int32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldm(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldm(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ long long ldm(const long long *p) { return __ldcg(p); }
 __device__ __forceinline__ uint8_t ldm(const uint8_t *p) { return __ldcg(p); }
@@ -129,7 +134,7 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
     bool mv = false;
     A g = 0;
     if (cand != INT_MAX) {
-        const A ks = stay_key(a.two_m, kvd, Kv, ldm(&a.Sig[d]), a.gamma);
+        const A ks = stay_key(a.kscale, kvd, Kv, ldm(&a.Sig[d]), a.gamma);
         mv = key > ks;
         if (!REFINE && mv && cur_step >= a.cap_step) {
             // S2: where neighbours may move together, a single-vertex
@@ -144,8 +149,9 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
         return false;
     }
     if (mv) {
-        atomic_add_acc(&a.Sig[d], -Kv);
-        atomic_add_acc(&a.Sig[cand], Kv);
+        using T = typename P::tot;
+        atomic_add_acc(&a.Sig[d], -(T)Kv);
+        atomic_add_acc(&a.Sig[cand], (T)Kv);
         atomicSub(&a.size[d], 1);
         atomicAdd(&a.size[cand], 1);
         a.C[v] = cand;
@@ -230,7 +236,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
                 kvd = wt[k];
                 continue;
             }
-            const A kk = move_key(a.two_m, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma);
+            const A kk = move_key(a.kscale, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma);
             if (better(kk, c[k], key, cand)) {
                 key = kk;
                 cand = c[k];
@@ -308,7 +314,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
         A key = AccLimits<A>::lowest();
         int32_t cand = INT_MAX;
         if (lead && c != d) {
-            key = move_key(a.two_m, sum, Kv, ldm(&a.Sig[c]), a.gamma);
+            key = move_key(a.kscale, sum, Kv, ldm(&a.Sig[c]), a.gamma);
             cand = c;
         }
 #pragma unroll
@@ -391,7 +397,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(a.two_m, sum, Kv, ldm(&a.Sig[k]), a.gamma);
+            const A kk = move_key(a.kscale, sum, Kv, ldm(&a.Sig[k]), a.gamma);
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -489,7 +495,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(a.two_m, sum, Kv, ldm(&a.Sig[k]), a.gamma);
+            const A kk = move_key(a.kscale, sum, Kv, ldm(&a.Sig[k]), a.gamma);
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -546,7 +552,7 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
         const int32_t c = ldm(&a.prop[v]);
         if (c < 0) continue;
         const int32_t d = ldm(&a.C[v]);
-        const auto Kv = a.K[v];
+        const auto Kv = (typename P::tot)a.K[v];
         atomic_add_acc(&a.Sig[d], -Kv);
         atomic_add_acc(&a.Sig[c], Kv);
         atomicSub(&a.size[d], 1);
@@ -572,7 +578,7 @@ __device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_
         if (tg < 0) continue;
         const int32_t pt = (__ldg(&a.step[tg]) == cur_step) ? ldm(&a.prop[tg]) : -1;
         if (!(pt < 0 || (pt == v && v > tg))) continue;
-        const auto Kv = a.K[v];
+        const auto Kv = (typename P::tot)a.K[v];
         atomic_add_acc(&a.Sig[v], -Kv);
         atomic_add_acc(&a.Sig[tg], Kv);
         atomicSub(&a.size[v], 1);
@@ -687,15 +693,18 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
             if (lane == 0 && det_gain) atomic_add_acc(reinterpret_cast<long long *>(&a.dq_arr[it]), det_gain);
         } else {
             const A s = warp_sum(local_gain);
-            if (lane == 0 && s != (A)0) atomic_add_acc(&a.dq_arr[it], s);
+            if (lane == 0 && s != (A)0) atomic_add_acc(&a.dq_arr[it], (typename P::tot)s);
         }
         if (!(ok = grid_barrier(a.bar, a.err))) break;
         bool stop;
         if (REFINE) {
             stop = __ldcg(&a.moved_arr[it]) == 0ULL || a.single_sweep;
         } else {
-            const double tm = (double)a.two_m;
-            const double dq = 2.0 * (double)ldm(&a.dq_arr[it]) / (tm * tm);
+            // sweep delta-modularity from the summed gains: 2 num / (2m)^2
+            // (deterministic, reading S4) or 2 sum / 2m (asynchronous)
+            const double tm = a.two_m_d;
+            const double sum = (double)ldm(&a.dq_arr[it]);
+            const double dq = P::det ? 2.0 * sum / (tm * tm) : 2.0 * sum / tm;
             stop = dq <= a.tau;
         }
         ++it;
@@ -714,7 +723,7 @@ __global__ void __launch_bounds__(256) k_eval_thread(SV<P, W> a, const int32_t *
     run_thread<P, W, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
     if (!REFINE && !P::det) {
         const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
     }
     pc.flush(a.prof);
 }
@@ -726,7 +735,7 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
     run_tile<P, W, T, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
     if (!REFINE && !P::det) {
         const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
     }
     pc.flush(a.prof);
 }
@@ -742,7 +751,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
                            local_gain, pc);
     if (!REFINE && !P::det) {
         const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
     }
     pc.flush(a.prof);
 }
@@ -763,7 +772,7 @@ __global__ void __launch_bounds__(256) k_eval_block(SV<P, W> a, const int32_t *_
     }
     if (!REFINE && !P::det) {
         const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, s);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
     }
     pc.flush(a.prof);
 }

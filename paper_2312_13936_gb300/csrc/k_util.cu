@@ -32,10 +32,10 @@ __global__ void k_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err)
 
 // K_i = sum of row i. One thread per row; rows longer than 64 entries are
 // summed by the whole warp, one such row after another.
-template <class A, class W>
-__global__ void k_vertex_weights(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K, A *two_m) {
+template <class A, class T, class W>
+__global__ void k_vertex_weights(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K, T *two_m) {
     const int lane = threadIdx.x & 31;
-    A local = 0;
+    T local = 0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = i0 + threadIdx.x;
         const int32_t d = i < n ? deg[i] : 0;
@@ -63,7 +63,7 @@ __global__ void k_vertex_weights(int64_t n, const int64_t *off, const int32_t *d
         }
     }
     local = warp_sum(local);
-    if (lane == 0 && local != (A)0) atomic_add_acc(two_m, local);
+    if (lane == 0 && local != (T)0) atomic_add_acc(two_m, local);
 }
 
 // ---- exclusive scan: tile reduce, scan of tile sums, tile rescan
@@ -289,11 +289,12 @@ cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *t
     if (det) {
         auto *k = static_cast<long long *>(K);
         auto *t = static_cast<long long *>(two_m);
-        if (g.w_int) k_vertex_weights<long long, int32_t><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
-        else k_vertex_weights<long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+        if (g.w_int)
+            k_vertex_weights<long long, long long, int32_t><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
+        else k_vertex_weights<long long, long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
     } else {
-        k_vertex_weights<double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, static_cast<double *>(K),
-                                                          static_cast<double *>(two_m));
+        k_vertex_weights<float, double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w,
+                                                                 static_cast<float *>(K), static_cast<double *>(two_m));
     }
     return cudaGetLastError();
 }
