@@ -86,7 +86,7 @@ struct Handle::Impl {
     int32_t *C0 = nullptr, *Cp = nullptr, *CB = nullptr, *Cd = nullptr, *size = nullptr, *prop = nullptr,
             *step = nullptr, *key = nullptr, *list = nullptr, *flag = nullptr, *members = nullptr, *cursor = nullptr,
             *bnd = nullptr, *rep = nullptr, *label = nullptr, *minv = nullptr, *out = nullptr, *scnt = nullptr,
-            *slayer = nullptr;
+            *slayer = nullptr, *sfcount = nullptr;
     int64_t *pos = nullptr, *pos2 = nullptr, *coff = nullptr, *cnt = nullptr, *tdeg = nullptr, *key_cnt = nullptr,
             *key_off = nullptr;
     void *K = nullptr, *Sig = nullptr, *Kagg = nullptr, *scan_tmp = nullptr, *part_tmp = nullptr;
@@ -353,6 +353,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     q.key_cap = 8192;
     ST(q.alloc(&q.key_cnt, q.key_cap));
     ST(q.alloc(&q.key_off, q.key_cap + 1));
+    ST(q.alloc(&q.sfcount, 4096 + 1));
     ST(q.alloc(&q.iota_list, n));
     CK(launch_iota(q.iota_list, n, q.s));
     CK(launch_degrees(q.off0, q.deg0, n, &q.dsc->err, q.s));
@@ -490,7 +491,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(launch_vertex_weights(G, det, q.K, det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, s));
         q.launches += 1;
         // schedule and (step, bin) lists
-        SchedWork sw{q.scnt, q.slayer};
+        SchedWork sw{q.scnt, q.slayer, q.sfcount};
         CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s));
         q.launches += L > 1 ? L : 2;
         // one vertex list per (schedule step, degree bin), step-major
@@ -605,7 +606,10 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                     prof_end();
                     q.launches++;
                 }
-                if (refine || det) {
+                // apply phase: deterministic mode, and refinement proposals where
+                // neighbours may share a step (asynchronous refinement applies
+                // its joins at once below the capped step)
+                if (det || (refine && k >= sc.cap_step)) {
                     if (refine) CK(launch_refine_apply(sc, sList + a0, a1 - a0, s));
                     else CK(launch_move_apply(sc, sList + a0, a1 - a0, s));
                     q.launches++;

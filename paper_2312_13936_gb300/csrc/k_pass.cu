@@ -67,8 +67,17 @@ __global__ void k_rep_min(const int32_t *bnd, int64_t ncomm, int32_t *rep) {
 __global__ void k_labels(const int32_t *bnd, const int32_t *rep, int64_t ncomm, int32_t *label) {
     GRID_STRIDE(s, ncomm) label[s] = rep[bnd[s]];
 }
+// smallest vertex of each community: lanes of a warp that share a label
+// reduce among themselves first (few large communities would otherwise
+// serialise on one address)
 __global__ void k_min_vertex(const int32_t *C0, int64_t n0, int32_t *minv) {
-    GRID_STRIDE(v, n0) atomicMin(&minv[C0[v]], (int32_t)v);
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n0; v0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + threadIdx.x;
+        const int32_t c = v < n0 ? C0[v] : -1;
+        const unsigned peers = __match_any_sync(kFull, c);
+        const unsigned m = __reduce_min_sync(peers, (unsigned)(v < n0 ? v : 0x7fffffff));
+        if (c >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMin(&minv[c], (int32_t)m);
+    }
 }
 __global__ void k_first(const int32_t *C0, const int32_t *minv, int64_t n0, int32_t *first) {
     GRID_STRIDE(v, n0) first[v] = (minv[C0[v]] == (int32_t)v) ? 1 : 0;

@@ -11,10 +11,14 @@
 namespace lgb {
 namespace {
 
-// cnt[v] = number of v's preceding neighbours; layer[v] = 0 if none
+// cnt[v] = number of v's preceding neighbours; layer[v] = 0 if none.
+// settled[0] counts the layer-0 vertices.
 __global__ void __launch_bounds__(256) k_sched_init(int64_t n, const int64_t *off, const int32_t *deg,
-                                                    const int32_t *idx, uint64_t state, int32_t *cnt,
-                                                    int32_t *layer) {
+                                                    const int32_t *idx, uint64_t state, int32_t *cnt, int32_t *layer,
+                                                    int32_t *settled) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t pv = splitmix64_at(state, (uint64_t)v);
         const int64_t e0 = off[v];
@@ -26,15 +30,23 @@ __global__ void __launch_bounds__(256) k_sched_init(int64_t n, const int64_t *of
         }
         cnt[v] = c;
         layer[v] = c == 0 ? 0 : -1;
+        if (c == 0) atomicAdd(&s_cnt, 1);
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(&settled[0], s_cnt);
 }
 
 // round r: every vertex of layer r releases its succeeding neighbours; a
 // neighbour whose last preceding neighbour is released joins layer r+1. The
-// round scans the layer array (coalesced) instead of keeping frontier lists.
+// round scans the layer array, so layer-r vertices are visited in id order;
+// it returns at once when layer r is empty (settled[r] == 0).
 __global__ void __launch_bounds__(256) k_sched_round(int64_t n, const int64_t *off, const int32_t *deg,
                                                      const int32_t *idx, uint64_t state, int32_t r, int32_t *cnt,
-                                                     int32_t *layer) {
+                                                     int32_t *layer, int32_t *settled) {
+    if (__ldcg(&settled[r]) == 0) return;
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         if (__ldcg(&layer[v]) != r) continue;
         const uint64_t pv = splitmix64_at(state, (uint64_t)v);
@@ -43,9 +55,14 @@ __global__ void __launch_bounds__(256) k_sched_round(int64_t n, const int64_t *o
         for (int32_t e = 0; e < dv; ++e) {
             const int32_t u = idx[e0 + e];
             if (u == (int32_t)v || !precedes(pv, (int32_t)v, splitmix64_at(state, (uint64_t)u), u)) continue;
-            if (atomicSub(&cnt[u], 1) == 1) layer[u] = r + 1;
+            if (atomicSub(&cnt[u], 1) == 1) {
+                layer[u] = r + 1;
+                atomicAdd(&s_cnt, 1);
+            }
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(&settled[r + 1], s_cnt);
 }
 
 __global__ void k_sched_finish(int64_t n, uint64_t state, int32_t L, int32_t B, const int32_t *layer,
@@ -82,9 +99,11 @@ cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32
                             int32_t *step, cudaStream_t s) {
     if (g.n <= 0) return cudaSuccess;
     const int grid = grid_for(g.n, 256);
-    k_sched_init<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, w.cnt, w.layer);
+    cudaError_t e = cudaMemsetAsync(w.settled, 0, sizeof(int32_t) * (L + 1), s);
+    if (e != cudaSuccess) return e;
+    k_sched_init<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, w.cnt, w.layer, w.settled);
     for (int32_t r = 0; r + 2 <= L - 1; ++r)  // produce layers 1 .. L-2
-        k_sched_round<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, r, w.cnt, w.layer);
+        k_sched_round<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, r, w.cnt, w.layer, w.settled);
     k_sched_finish<<<grid, 256, 0, s>>>(g.n, state, L, B, w.layer, step);
     return cudaGetLastError();
 }

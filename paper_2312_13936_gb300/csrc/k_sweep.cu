@@ -123,18 +123,20 @@ template <class A> __device__ __forceinline__ bool better(A k1, int32_t c1, A k2
     return k1 > k2 || (k1 == k2 && c1 < c2);
 }
 
-// Decision for vertex v (one thread) with best candidate (key, cand) and
-// K_{v->d} = kvd. Returns true if an asynchronous move was applied (its
-// neighbours must then be marked unprocessed).
+// Decision for vertex v (one thread) with best candidate (key, cand),
+// K_{v->d} = kvd and Sigma_d = sd. Returns true if an asynchronous
+// local-moving move was applied (its neighbours must then be marked
+// unprocessed).
 template <class P, class W, bool REFINE>
-__device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
-                                       typename P::acc key, int32_t cand, typename P::acc kvd,
-                                       typename P::acc &local_gain, int32_t cur_step) {
+__device__ __forceinline__ bool decide_sd(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
+                                          typename P::acc key, int32_t cand, typename P::acc kvd,
+                                          typename P::tot sd, typename P::acc &local_gain, int32_t cur_step) {
     using A = typename P::acc;
+    using T = typename P::tot;
     bool mv = false;
     A g = 0;
     if (cand != INT_MAX) {
-        const A ks = stay_key(a.kscale, kvd, Kv, ldm(&a.Sig[d]), a.gamma);
+        const A ks = stay_key(a.kscale, kvd, Kv, sd, a.gamma);
         mv = key > ks;
         if (!REFINE && mv && cur_step >= a.cap_step) {
             // S2: where neighbours may move together, a single-vertex
@@ -143,13 +145,27 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
         }
         g = key - ks;
     }
+    if (REFINE && !P::det && cur_step < a.cap_step) {
+        // Asynchronous refinement below the capped step: no two vertices of
+        // a step are adjacent, so the neighbour through which v saw cand
+        // stays in cand and nobody joins v while it leaves: the join is
+        // applied at once (local_gain counts joins in this phase).
+        if (mv) {
+            atomic_add_acc(&a.Sig[d], -(T)Kv);
+            atomic_add_acc(&a.Sig[cand], (T)Kv);
+            atomicSub(&a.size[d], 1);
+            atomicAdd(&a.size[cand], 1);
+            a.C[v] = cand;
+            local_gain += (A)1;
+        }
+        return false;
+    }
     if (REFINE || P::det) {
         a.prop[v] = mv ? cand : -1;
         if (!REFINE && mv) a.gain[v] = (long long)g;
         return false;
     }
     if (mv) {
-        using T = typename P::tot;
         atomic_add_acc(&a.Sig[d], -(T)Kv);
         atomic_add_acc(&a.Sig[cand], (T)Kv);
         atomicSub(&a.size[d], 1);
@@ -158,6 +174,12 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
         local_gain += g;
     }
     return mv;
+}
+template <class P, class W, bool REFINE>
+__device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
+                                       typename P::acc key, int32_t cand, typename P::acc kvd,
+                                       typename P::acc &local_gain, int32_t cur_step) {
+    return decide_sd<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, ldm(&a.Sig[d]), local_gain, cur_step);
 }
 
 // Eligibility: local-moving takes unprocessed vertices and marks them
@@ -186,15 +208,20 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += nthreads) {
         const int32_t v = list[t];
-        int32_t d = 0;
-        if (!take_vertex<P, W, REFINE>(a, v, d)) {
+        // the vertex's header loads are independent: issue them together
+        const int32_t d = ldm(&a.C[v]);
+        const uint8_t up = REFINE ? (uint8_t)1 : ldm(&a.unproc[v]);
+        const A Kv = a.K[v];
+        const int64_t e0 = a.off[v];
+        const int32_t dv = a.deg[v];
+        const bool elig = REFINE ? (ldm(&a.size[d]) == 1) : (up != 0);
+        if (!elig) {
             if (REFINE || P::det) a.prop[v] = -1;
             pc.v[1]++;
             continue;
         }
-        const A Kv = a.K[v];
-        const int64_t e0 = a.off[v];
-        const int32_t dv = a.deg[v];
+        if (!REFINE) a.unproc[v] = 0;  // processed (Algorithm 2 pruning)
+        const typename P::tot sd = ldm(&a.Sig[d]);
         const int32_t bv = REFINE ? a.CB[v] : 0;
         int32_t jj[E];
         A wt[E];
@@ -242,7 +269,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
                 cand = c[k];
             }
         }
-        const bool mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain, cur_step);
+        const bool mv = decide_sd<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, sd, local_gain, cur_step);
         if (a.prof) {
             pc.v[0]++;
             pc.v[2] += dv;
@@ -677,7 +704,10 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                                               local_gain, pc);
             }
             if (!(ok = grid_barrier(a.bar, a.err))) break;
-            if (REFINE || P::det) {
+            // apply phase: deterministic mode, and refinement proposals where
+            // neighbours may share a step (asynchronous refinement applies
+            // its joins at once below the capped step)
+            if (P::det || (REFINE && k >= a.cap_step)) {
                 if (REFINE) run_refine_apply(a, list, b0, b8, k, moved);
                 else run_move_apply(a, list, b0, b8, det_gain);
                 if (!(ok = grid_barrier(a.bar, a.err))) break;
@@ -686,6 +716,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
         if (!ok) break;
         // this sweep's totals, then the convergence test
         if (REFINE) {
+            if (!P::det) moved += (unsigned long long)(local_gain + (A)0.5);
             moved = warp_sum(moved);
             if (lane == 0 && moved) atomicAdd(&a.moved_arr[it], moved);
         } else if (P::det) {
@@ -715,16 +746,28 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
 }
 
 // ------------------------------------------- one (step, bin) per launch
+// local-moving gains into the sweep's delta-modularity sum; asynchronous
+// refinement joins into the move count
+template <class P, class W, bool REFINE>
+__device__ __forceinline__ void flush_gain(const SV<P, W> &a, typename P::acc local_gain) {
+    using A = typename P::acc;
+    if (P::det) return;
+    if (REFINE) {
+        const unsigned long long c = warp_sum((unsigned long long)(local_gain + (A)0.5));
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.moved, c);
+    } else {
+        const A s = warp_sum(local_gain);
+        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
+    }
+}
+
 template <class P, class W, bool REFINE>
 __global__ void __launch_bounds__(256) k_eval_thread(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
     using A = typename P::acc;
     A local_gain = 0;
     ProfCounts pc;
     run_thread<P, W, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
-    if (!REFINE && !P::det) {
-        const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
-    }
+    flush_gain<P, W, REFINE>(a, local_gain);
     pc.flush(a.prof);
 }
 template <class P, class W, int T, bool REFINE>
@@ -733,10 +776,7 @@ __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__
     A local_gain = 0;
     ProfCounts pc;
     run_tile<P, W, T, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
-    if (!REFINE && !P::det) {
-        const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
-    }
+    flush_gain<P, W, REFINE>(a, local_gain);
     pc.flush(a.prof);
 }
 template <class P, class W, bool REFINE>
@@ -749,10 +789,7 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
     ProfCounts pc;
     run_warp<P, W, REFINE>(a, list, 0, count, a.cur_step, skeys + wib * kWarpSlots, svals + wib * kWarpSlots,
                            local_gain, pc);
-    if (!REFINE && !P::det) {
-        const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
-    }
+    flush_gain<P, W, REFINE>(a, local_gain);
     pc.flush(a.prof);
 }
 template <class P, class W, bool REFINE, bool HUB>
@@ -770,10 +807,7 @@ __global__ void __launch_bounds__(256) k_eval_block(SV<P, W> a, const int32_t *_
         run_block<P, W, REFINE, false>(a, list, 0, count, a.cur_step, skeys, svals, ceil_log2(kBlockSlots), local_gain,
                                        pc);
     }
-    if (!REFINE && !P::det) {
-        const A s = warp_sum(local_gain);
-        if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
-    }
+    flush_gain<P, W, REFINE>(a, local_gain);
     pc.flush(a.prof);
 }
 template <class P, class W>

@@ -136,6 +136,7 @@ cudaError_t launch_validate(int64_t n, const int64_t *off, const int32_t *idx, c
 // ---- schedule (k_schedule.cu): step of every vertex (reading S0)
 struct SchedWork {
     int32_t *cnt, *layer;  // n each
+    int32_t *settled;      // L+1: vertices placed in each layer
 };
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
                             int32_t *step, cudaStream_t s);
