@@ -13,6 +13,13 @@ input resident in HBM. Prints one JSON line.
 With N > 1 (torchrun, one process per GPU) every rank solves its own replica
 of the workload: the method has no data-parallel split of one graph, so the
 multi-GPU form is independent replicas ("scaling": "weak").
+
+The same line carries the batched form ("batched"): 4096 seeded SBM graphs
+(vertex counts log-uniform in [100, 100000], 4-64 blocks, mean degree 8-32,
+p_out/p_in = 0.02; ~61M vertices, ~1.2e9 entries) packed as one segmented CSR
+and solved by leiden_batch_run, in graphs/s, next to a per-graph loop of
+plain leiden_run calls timed on a sample of the same graphs. With N > 1 the
+graphs are split across ranks in contiguous ranges.
 """
 import argparse
 import hashlib
@@ -48,6 +55,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-side", type=int, default=3000, help="road side of the CPU-baseline sample")
     ap.add_argument("--ref-side", type=int, default=1500, help="road side of each reference-arm step")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-sample", type=int, default=128, help="graphs of the per-graph loop")
     return ap.parse_args()
 
 
@@ -143,6 +154,78 @@ def traffic_for(cls_name, workload_name):
         return t["classes"].get(cls_name, {}).get("dram_bytes_per_launch")
     except Exception:
         return None
+
+
+def batched_form(args, rank, world, mode, flags):
+    """graphs/s of one leiden_batch_run over this rank's share of the batch,
+    and of a per-graph loop of plain leiden_run calls on a sample of it."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import gen
+    import paper_2312_13936_gb300 as lg
+    b = gen.sbm_batch(args.batch_graphs, seed=4)
+    G = b.num_graphs
+    lo, hi = rank * G // world, (rank + 1) * G // world
+    v0, v1 = int(b.vseg[lo]), int(b.vseg[hi])
+    e0, e1 = int(b.offsets[v0]), int(b.offsets[v1])
+    vseg = b.vseg[lo:hi + 1] - v0
+    off = b.offsets[v0:v1 + 1] - e0
+    h = lg.LeidenBatch(vseg, off, b.indices[e0:e1], b.weights[e0:e1])
+    h.run(mode=mode, flags=flags)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    for _ in range(args.batch_steps):
+        memb, q, st = h.run(mode=mode, flags=flags)
+    t1.record(s)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / args.batch_steps
+    passes, comm = h.info()
+    h.close()
+    # per-graph loop of plain launches on a sample of the same graphs
+    S = max(1, min(args.batch_sample, hi - lo))
+    pick = np.linspace(0, hi - lo - 1, S).astype(int)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    hs = []
+    for k in pick:
+        gk = b.graph(lo + int(k))
+        hs.append(lg.Leiden(torch.as_tensor(gk.offsets).to(dev), torch.as_tensor(gk.indices).to(dev),
+                            torch.as_tensor(gk.weights).to(dev)))
+    for hh in hs[:4]:
+        hh.run(mode=mode, flags=flags)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ql = [hh.run(mode=mode, flags=flags)[1] for hh in hs]
+    torch.cuda.synchronize()
+    tl = time.perf_counter() - t
+    for hh in hs:
+        hh.close()
+    stats = torch.tensor([ms, tl / S, float(q.sum()), float(len(q)), float(np.sum(ql)), float(np.sum(q[pick])),
+                          float(S)], dtype=torch.float64, device=dev)
+    if world > 1:
+        mx = stats[:2].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(stats, op=dist.ReduceOp.SUM)
+        stats[:2] = mx
+    ms, per_graph_s, qsum, qn, qls, qbs, ns = stats.tolist()
+    return {
+        "workload": (f"{G} SBM graphs, vertices log-uniform in [100, 100000], 4-64 blocks, mean degree 8-32, "
+                     f"p_out/p_in 0.02, unit weights, seed 4; one segmented CSR per rank"),
+        "graphs": G, "vertices": b.n, "entries": b.nnz, "mode": "async" if mode == lg.LEIDEN_ASYNC else "det",
+        "graphs_per_s": G / (ms / 1e3), "ms_per_batch": ms, "edges_per_s": b.nnz / (ms / 1e3),
+        "steps": args.batch_steps, "union_passes_rank0": st.passes, "max_graph_passes_rank0": int(passes.max()),
+        "loop_graphs_per_s": world / per_graph_s, "loop_sample_graphs": int(ns),
+        "speedup_vs_loop": (G / (ms / 1e3)) / (world / per_graph_s),
+        "modularity_mean": qsum / qn, "modularity_mean_sample_batch": qbs / ns,
+        "modularity_mean_sample_loop": qls / ns,
+    }
 
 
 def cpu_baseline(side):
@@ -280,6 +363,8 @@ def main():
         e2e = {"value": world * ne * g.nnz / te, "unit": "edges/s",
                "h2d_bytes_per_step": hoff.nbytes + hidx.nbytes + hw.nbytes, "d2h_bytes_per_step": out.nbytes + 8}
 
+    batched = None if args.no_batch else batched_form(args, rank, world, mode, base_flags)
+
     if rank != 0:
         dist.destroy_process_group()
         return
@@ -310,6 +395,7 @@ def main():
                    "phase_ms": {"move": st.ms_move, "refine": st.ms_refine, "aggregate": st.ms_aggregate,
                                 "other": st.ms_other}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
+        "batched": batched,
         "kernel_classes": {f"{k[0]}/{k[1]}": v for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
     }
     print(json.dumps(line), flush=True)

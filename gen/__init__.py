@@ -81,6 +81,9 @@ def _lib():
                                       ctypes.c_void_p] + out
         for f in (lib.gg_sbm, lib.gg_road, lib.gg_rmat, lib.gg_gnp, lib.gg_from_edges):
             f.restype = ctypes.c_int
+        lib.gg_sbm_batch.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, P64] + out
+        lib.gg_sbm_batch.restype = ctypes.c_int
         lib.gg_free.argtypes = [ctypes.c_void_p]
         lib.gg_free.restype = None
         _lib_handle = lib
@@ -159,6 +162,89 @@ def ring_of_cliques(k: int, r: int) -> CSR:
         us.append(base)
         vs.append(nxt + 1 if k > 1 else nxt)
     return from_edges(k * r, us, vs)
+
+
+@dataclass
+class Batch:
+    """Independent graphs packed one after another: graph g owns vertices
+    [vseg[g], vseg[g+1]); offsets index the packed indices/weights; indices
+    are local to each graph."""
+
+    vseg: np.ndarray     # int64[G+1]
+    offsets: np.ndarray  # int64[N+1]
+    indices: np.ndarray  # int32[nnz], local
+    weights: np.ndarray  # float32[nnz]
+    params: dict         # per-graph recipe parameters (numpy arrays)
+
+    @property
+    def num_graphs(self) -> int:
+        return int(len(self.vseg) - 1)
+
+    @property
+    def n(self) -> int:
+        return int(self.vseg[-1])
+
+    @property
+    def nnz(self) -> int:
+        return int(self.offsets[-1])
+
+    def graph(self, g: int) -> CSR:
+        """Graph g as a standalone CSR."""
+        a, b = int(self.vseg[g]), int(self.vseg[g + 1])
+        e0, e1 = int(self.offsets[a]), int(self.offsets[b])
+        return CSR(b - a, self.offsets[a:b + 1] - e0, self.indices[e0:e1].copy(), self.weights[e0:e1].copy())
+
+
+def sbm_batch_params(count: int, seed: int, nmin: int = 100, nmax: int = 100_000, bmin: int = 4, bmax: int = 64,
+                     dmin: float = 8.0, dmax: float = 32.0, ratio: float = 0.02) -> dict:
+    """Per-graph SBM parameters of a batch: n log-uniform in [nmin, nmax],
+    blocks uniform in {bmin..bmax} (at most n/2), mean degree uniform in
+    [dmin, dmax], p_out = ratio * p_in with p_in = d / ((s-1) + ratio (n-s)),
+    s = n / blocks, p_in clamped to 1. Drawn with numpy's PCG64 from seed."""
+    rng = np.random.default_rng(seed)
+    n = np.rint(np.exp(rng.uniform(np.log(nmin), np.log(nmax), count))).astype(np.int64)
+    blocks = rng.integers(bmin, bmax + 1, count).astype(np.int32)
+    blocks = np.maximum(1, np.minimum(blocks, n // 2)).astype(np.int32)
+    dbar = rng.uniform(dmin, dmax, count)
+    s = n / blocks
+    p_in = np.minimum(1.0, dbar / ((s - 1) + ratio * (n - s)))
+    p_out = ratio * p_in
+    seeds = (np.uint64(seed) << np.uint64(32)) + np.arange(count, dtype=np.uint64)
+    return {"n": n, "blocks": blocks, "mean_degree": dbar, "p_in": p_in, "p_out": p_out, "seeds": seeds}
+
+
+def sbm_batch(count: int, seed: int, **kw) -> Batch:
+    """A batch of seeded SBM graphs (see sbm_batch_params), generated in
+    parallel; graph g equals sbm(n[g], blocks[g], p_in[g], p_out[g], seeds[g])."""
+    prm = sbm_batch_params(count, seed, **kw)
+    lib = _lib()
+    vp = ctypes.c_void_p
+    arrs = [np.ascontiguousarray(prm[k]) for k in ("n", "blocks", "p_in", "p_out", "seeds")]
+    vseg = ctypes.POINTER(ctypes.c_int64)()
+    off = ctypes.POINTER(ctypes.c_int64)()
+    idx = ctypes.POINTER(ctypes.c_int32)()
+    w = ctypes.POINTER(ctypes.c_float)()
+    nnz = ctypes.c_int64(0)
+    rc = lib.gg_sbm_batch(count, *[vp(a.ctypes.data) for a in arrs], ctypes.byref(vseg), ctypes.byref(off),
+                          ctypes.byref(idx), ctypes.byref(w), ctypes.byref(nnz))
+    if rc != 0:
+        raise RuntimeError(f"batch generator failed with code {rc}")
+    try:
+        vs = np.ctypeslib.as_array(vseg, shape=(count + 1,)).copy()
+        N, m = int(vs[-1]), nnz.value
+        offsets = np.ctypeslib.as_array(off, shape=(N + 1,)).copy()
+        indices = np.ctypeslib.as_array(idx, shape=(max(m, 1),))[:m].copy()
+        weights = np.ctypeslib.as_array(w, shape=(max(m, 1),))[:m].copy()
+    finally:
+        for p in (vseg, off, idx, w):
+            lib.gg_free(ctypes.cast(p, ctypes.c_void_p))
+    return Batch(vs, offsets, indices, weights, prm)
+
+
+def sbm_batch_workload(count: int = 4096) -> Batch:
+    """4096 SBM graphs, n log-uniform in [100, 100000], 4-64 blocks, mean
+    degree in [8, 32], p_out / p_in = 0.02, unit weights, seed 4."""
+    return sbm_batch(count, seed=4)
 
 
 # Workload recipes (seeds fixed; sizes as the workloads define them).

@@ -234,6 +234,75 @@ int gg_sbm(int64_t n, int32_t blocks, double p_in, double p_out, uint64_t seed,
     return rc;
 }
 
+/* Batch of SBM graphs, each generated exactly as gg_sbm generates it alone
+ * (graph g: n[g] vertices, blocks[g] near-equal blocks, p_in[g], p_out[g],
+ * seeds[g]), in parallel over graphs, then packed one after another: vseg
+ * (G+1 vertex offsets), off (N+1 offsets into the packed idx/w), idx (LOCAL
+ * to each graph), w; *nnz = total entries. */
+int gg_sbm_batch(int32_t G, const int64_t *n, const int32_t *blocks, const double *p_in, const double *p_out,
+                 const uint64_t *seeds, int64_t **vseg_out, int64_t **off_out, int32_t **idx_out, float **w_out,
+                 int64_t *nnz_out) {
+    if (G < 0) return -2;
+    int64_t **offs = (int64_t **)calloc((size_t)G + 1, sizeof(int64_t *));
+    int32_t **idxs = (int32_t **)calloc((size_t)G + 1, sizeof(int32_t *));
+    float **ws = (float **)calloc((size_t)G + 1, sizeof(float *));
+    int64_t *m = (int64_t *)calloc((size_t)G + 1, sizeof(int64_t));
+    int64_t *vseg = (int64_t *)malloc(((size_t)G + 1) * sizeof(int64_t));
+    int64_t *eseg = (int64_t *)malloc(((size_t)G + 1) * sizeof(int64_t));
+    int err = !offs || !idxs || !ws || !m || !vseg || !eseg;
+    if (!err) {
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+        for (int32_t g = 0; g < G; ++g)
+            err |= gg_sbm(n[g], blocks[g], p_in[g], p_out[g], seeds[g], &offs[g], &idxs[g], &ws[g], &m[g], NULL) != 0;
+    }
+    int64_t *off = NULL;
+    int32_t *idx = NULL;
+    float *w = NULL;
+    if (!err) {
+        vseg[0] = 0;
+        eseg[0] = 0;
+        for (int32_t g = 0; g < G; ++g) {
+            vseg[g + 1] = vseg[g] + n[g];
+            eseg[g + 1] = eseg[g] + m[g];
+        }
+        if (vseg[G] > INT32_MAX) err = 1;
+    }
+    if (!err) {
+        off = (int64_t *)malloc(((size_t)vseg[G] + 1) * sizeof(int64_t));
+        idx = (int32_t *)malloc((size_t)(eseg[G] ? eseg[G] : 1) * sizeof(int32_t));
+        w = (float *)malloc((size_t)(eseg[G] ? eseg[G] : 1) * sizeof(float));
+        err = !off || !idx || !w;
+    }
+    if (!err) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int32_t g = 0; g < G; ++g) {
+            for (int64_t i = 0; i < n[g]; ++i) off[vseg[g] + i] = offs[g][i] + eseg[g];
+            if (m[g]) {
+                memcpy(idx + eseg[g], idxs[g], (size_t)m[g] * sizeof(int32_t));
+                memcpy(w + eseg[g], ws[g], (size_t)m[g] * sizeof(float));
+            }
+        }
+        off[vseg[G]] = eseg[G];
+    }
+    for (int32_t g = 0; g < G && offs; ++g) {
+        free(offs[g]);
+        if (idxs) free(idxs[g]);
+        if (ws) free(ws[g]);
+    }
+    free(offs); free(idxs); free(ws); free(eseg);
+    if (err) {
+        free(m); free(vseg); free(off); free(idx); free(w);
+        return -1;
+    }
+    *nnz_out = vseg[G] >= 0 ? off[vseg[G]] : 0;
+    free(m);
+    *vseg_out = vseg;
+    *off_out = off;
+    *idx_out = idx;
+    *w_out = w;
+    return 0;
+}
+
 /* ------------------------------------------------------------- road grid */
 /* side x side 4-neighbour lattice (vertex r*side+c). Each lattice edge is kept
  * with probability 1-drop. Then round(diag_frac * #lattice edges) diagonal

@@ -135,7 +135,8 @@ leiden_status leiden_create(leiden_graph_t *out, int64_t n, int64_t nnz, const i
                             const int32_t *indices, const float *weights, int32_t where, int32_t validate,
                             void *stream);
 
-/* Run Algorithm 1 on the handle's graph. membership (n int32, host or device
+/* Run Algorithm 1 on the handle's graph (a handle from leiden_create;
+ * batch handles of more than one graph return LEIDEN_ERR_INVALID). membership (n int32, host or device
  * per `where`) receives canonical labels: community ids are ranks of each
  * community's smallest vertex id. *modularity (nullable) receives Eq. 1 of
  * the result on the input graph; *stats (nullable) the run statistics. The
@@ -145,6 +146,42 @@ leiden_status leiden_run(leiden_graph_t g, const leiden_params *p, int32_t *memb
 
 /* Release the handle and its device memory. NULL is accepted. */
 leiden_status leiden_destroy(leiden_graph_t g);
+
+/* Batches: many independent graphs, each run through Algorithm 1 exactly as
+ * leiden_run would run it alone, solved together by one set of launches per
+ * pass (the paper runs one graph at a time; the batch is a disjoint union
+ * whose graphs keep their own 2m, their own convergence and stop tests and
+ * their own pass count, and leave the union when they stop).
+ *
+ * Create a batch handle from num_graphs >= 1 graphs packed one after the
+ * other: graph g owns vertices [vtx_seg[g], vtx_seg[g+1]) of the packed CSR
+ * (vtx_seg: num_graphs+1 int64 in HOST memory, vtx_seg[0] = 0,
+ * non-decreasing; empty graphs allowed), offsets has vtx_seg[num_graphs]+1
+ * entries indexing the packed indices/weights (nnz = offsets[n]), and the
+ * indices of graph g are LOCAL to it (in [0, n_g)): each graph's CSR is
+ * appended unchanged but for the shift of its offsets. Other arguments and
+ * checks as for leiden_create; a local index outside its graph returns
+ * LEIDEN_ERR_INVALID. In deterministic mode the 2m < 2^31 rule holds per
+ * graph. */
+leiden_status leiden_batch_create(leiden_graph_t *out, int32_t num_graphs, const int64_t *vtx_seg, int64_t nnz,
+                                  const int64_t *offsets, const int32_t *indices, const float *weights, int32_t where,
+                                  int32_t validate, void *stream);
+
+/* Run Algorithm 1 on every graph of a batch handle. membership (n int32,
+ * host or device per `where`) receives every graph's canonical labels, local
+ * to the graph (ranks of each community's smallest vertex inside it);
+ * modularity (nullable, num_graphs doubles in HOST memory) receives Eq. 1 of
+ * every graph's result on its input; stats (nullable) describes the whole
+ * batch (passes of the union, total communities, mean modularity). Trace and
+ * per-step launches are single-graph features (LEIDEN_ERR_UNSUPPORTED). A
+ * handle from leiden_create is a batch of one graph. */
+leiden_status leiden_batch_run(leiden_graph_t g, const leiden_params *p, int32_t *membership, int32_t where,
+                               double *modularity, leiden_stats *stats);
+
+/* Per-graph results of the last run on the handle: passes executed and
+ * communities found (host arrays of num_graphs entries; either may be
+ * NULL). *num_graphs (nullable) receives the handle's graph count. */
+leiden_status leiden_batch_info(leiden_graph_t g, int32_t *num_graphs, int32_t *passes, int64_t *communities);
 
 /* Modularity (Eq. 1 with resolution gamma) of `membership` (n labels in
  * [0, n)) on a symmetric CSR. All pointers are device pointers; the result

@@ -22,7 +22,8 @@ __all__ = [
     "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "FLAG_PROFILE", "FLAG_STEP_LAUNCHES", "FLAG_NO_RELABEL", "LeidenError", "Params", "Stats", "KernelProfile",
     "library", "leiden_params_default", "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity",
     "leiden_trace_get", "leiden_profile_get", "leiden_modularity_noalloc",
-    "leiden_status_string", "leiden_last_error", "Leiden", "modularity",
+    "leiden_status_string", "leiden_last_error", "Leiden", "modularity", "leiden_batch_create",
+    "leiden_batch_run", "leiden_batch_info", "LeidenBatch", "pack_batch",
 ]
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
@@ -95,8 +96,12 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.leiden_modularity_noalloc.restype = ctypes.c_int
         lib.leiden_trace_get.argtypes = [_VP, _I32, _I32, _VP, ctypes.POINTER(_I64)]
         lib.leiden_profile_get.argtypes = [_VP, ctypes.POINTER(KernelProfile)]
+        lib.leiden_batch_create.argtypes = [ctypes.POINTER(_VP), _I32, _VP, _I64, _VP, _VP, _VP, _I32, _I32, _VP]
+        lib.leiden_batch_run.argtypes = [_VP, ctypes.POINTER(Params), _VP, _I32, _VP, ctypes.POINTER(Stats)]
+        lib.leiden_batch_info.argtypes = [_VP, ctypes.POINTER(_I32), _VP, _VP]
         for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
-                  lib.leiden_trace_get, lib.leiden_profile_get):
+                  lib.leiden_trace_get, lib.leiden_profile_get, lib.leiden_batch_create, lib.leiden_batch_run,
+                  lib.leiden_batch_info):
             f.restype = ctypes.c_int
         lib.leiden_status_string.argtypes = [_I32]
         lib.leiden_status_string.restype = ctypes.c_char_p
@@ -139,6 +144,35 @@ def leiden_run(handle, params: Params, membership_ptr, where):
     _check(library().leiden_run(handle, ctypes.byref(params), membership_ptr, where, ctypes.byref(q),
                                 ctypes.byref(st)))
     return q.value, st
+
+
+def leiden_batch_create(num_graphs, vtx_seg, nnz, offsets_ptr, indices_ptr, weights_ptr, where, validate,
+                        stream) -> int:
+    """vtx_seg: host int64 array of num_graphs+1 vertex offsets; indices local to each graph."""
+    seg = np.ascontiguousarray(vtx_seg, dtype=np.int64)
+    h = _VP()
+    _check(library().leiden_batch_create(ctypes.byref(h), num_graphs, seg.ctypes.data_as(_VP), nnz, offsets_ptr,
+                                         indices_ptr, weights_ptr, where, validate, stream))
+    return h.value
+
+
+def leiden_batch_run(handle, params: Params, membership_ptr, where, num_graphs: int):
+    """Returns (per-graph modularity as a numpy array, Stats of the whole batch)."""
+    q = np.zeros(max(num_graphs, 1), dtype=np.float64)
+    st = Stats()
+    _check(library().leiden_batch_run(handle, ctypes.byref(params), membership_ptr, where,
+                                      q.ctypes.data_as(_VP), ctypes.byref(st)))
+    return q[:num_graphs], st
+
+
+def leiden_batch_info(handle):
+    """(passes, communities) per graph of the last run, as numpy arrays."""
+    g = _I32(0)
+    _check(library().leiden_batch_info(handle, ctypes.byref(g), None, None))
+    passes = np.zeros(max(g.value, 1), dtype=np.int32)
+    comm = np.zeros(max(g.value, 1), dtype=np.int64)
+    _check(library().leiden_batch_info(handle, None, passes.ctypes.data_as(_VP), comm.ctypes.data_as(_VP)))
+    return passes[:g.value], comm[:g.value]
 
 
 def leiden_destroy(handle) -> None:
@@ -232,6 +266,78 @@ class Leiden:
 
     def profile(self):
         return leiden_profile_get(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            leiden_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_batch(graphs):
+    """Pack CSRs (objects with offsets/indices/weights numpy arrays) into the
+    segmented layout of leiden_batch_create: (vtx_seg, offsets, indices,
+    weights) with offsets shifted and indices kept local to each graph."""
+    ns = [int(len(g.offsets) - 1) for g in graphs]
+    ms = [int(g.offsets[-1]) for g in graphs]
+    vseg = np.zeros(len(graphs) + 1, dtype=np.int64)
+    vseg[1:] = np.cumsum(ns)
+    eseg = np.zeros(len(graphs) + 1, dtype=np.int64)
+    eseg[1:] = np.cumsum(ms)
+    off = np.empty(int(vseg[-1]) + 1, dtype=np.int64)
+    off[-1] = eseg[-1]
+    for k, g in enumerate(graphs):
+        off[vseg[k]:vseg[k + 1]] = np.asarray(g.offsets[:-1], dtype=np.int64) + eseg[k]
+    idx = np.concatenate([np.asarray(g.indices, dtype=np.int32) for g in graphs]) if graphs else \
+        np.zeros(0, np.int32)
+    w = np.concatenate([np.asarray(g.weights, dtype=np.float32) for g in graphs]) if graphs else \
+        np.zeros(0, np.float32)
+    return vseg, off, idx, w
+
+
+class LeidenBatch:
+    """Many graphs resident on the GPU as one segmented CSR, solved together.
+
+    Takes the packed layout of ``pack_batch``. ``run`` returns (membership,
+    per-graph modularity, stats); membership holds every graph's labels,
+    local to the graph, in the packed vertex order.
+    """
+
+    def __init__(self, vtx_seg, offsets, indices, weights=None, validate: bool = False, stream=None):
+        import torch
+        self._torch = torch
+        self.stream = stream
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.vtx_seg = np.ascontiguousarray(vtx_seg, dtype=np.int64)
+        self.num_graphs = int(len(self.vtx_seg) - 1)
+        off = torch.as_tensor(offsets, dtype=torch.int64).to(dev).contiguous()
+        idx = torch.as_tensor(indices, dtype=torch.int32).to(dev).contiguous()
+        w = None if weights is None else torch.as_tensor(weights, dtype=torch.float32).to(dev).contiguous()
+        self.n = int(off.numel() - 1)
+        self.nnz = int(idx.numel())
+        self.handle = leiden_batch_create(self.num_graphs, self.vtx_seg, self.nnz, _ptr(off), _ptr(idx), _ptr(w),
+                                          LEIDEN_DEVICE, int(validate), _stream_ptr(stream))
+        self.device = dev
+
+    def run(self, mode: int = LEIDEN_ASYNC, **kw):
+        p = leiden_params_default()
+        p.mode = mode
+        for k, v in kw.items():
+            if k == "flags":
+                p.flags |= int(v)
+            else:
+                setattr(p, k, v)
+        memb = self._torch.empty(max(self.n, 1), dtype=self._torch.int32, device=self.device)
+        q, st = leiden_batch_run(self.handle, p, _ptr(memb), LEIDEN_DEVICE, self.num_graphs)
+        return memb[:self.n], q, st
+
+    def info(self):
+        return leiden_batch_info(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -67,7 +67,75 @@ leiden_status leiden_run(leiden_graph_t g, const leiden_params *p, int32_t *memb
         lgb::set_last_error("invalid where");
         return LEIDEN_ERR_INVALID;
     }
+    if (g->h.num_graphs() != 1) {
+        lgb::set_last_error("leiden_run takes a single graph; use leiden_batch_run for a batch");
+        return LEIDEN_ERR_INVALID;
+    }
     return g->h.run(*p, membership, where, modularity, stats);
+}
+
+leiden_status leiden_batch_create(leiden_graph_t *out, int32_t num_graphs, const int64_t *vtx_seg, int64_t nnz,
+                                  const int64_t *offsets, const int32_t *indices, const float *weights, int32_t where,
+                                  int32_t validate, void *stream) {
+    if (!out) {
+        lgb::set_last_error("out is NULL");
+        return LEIDEN_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (num_graphs < 1 || !vtx_seg || vtx_seg[0] != 0) {
+        lgb::set_last_error("a batch needs num_graphs >= 1 and vtx_seg[0] == 0");
+        return LEIDEN_ERR_INVALID;
+    }
+    for (int32_t g = 0; g < num_graphs; ++g)
+        if (vtx_seg[g + 1] < vtx_seg[g]) {
+            lgb::set_last_error("vtx_seg must be non-decreasing");
+            return LEIDEN_ERR_INVALID;
+        }
+    const int64_t n = vtx_seg[num_graphs];
+    if (n > 0x7fffffffLL || nnz < 0 || !offsets || (nnz > 0 && !indices) ||
+        (where != LEIDEN_HOST && where != LEIDEN_DEVICE)) {
+        lgb::set_last_error("invalid CSR arguments");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (where == LEIDEN_HOST && (offsets[0] != 0 || offsets[n] != nnz)) {
+        lgb::set_last_error("offsets[0] must be 0 and offsets[n] must equal nnz");
+        return LEIDEN_ERR_INVALID;
+    }
+    leiden_graph_s *g = new (std::nothrow) leiden_graph_s;
+    if (!g) {
+        lgb::set_last_error("host allocation failed");
+        return LEIDEN_ERR_OOM;
+    }
+    leiden_status st = g->h.create(n, nnz, offsets, indices, weights, where, validate, stream, num_graphs, vtx_seg);
+    if (st != LEIDEN_OK) {
+        delete g;
+        return st;
+    }
+    *out = g;
+    return LEIDEN_OK;
+}
+
+leiden_status leiden_batch_run(leiden_graph_t g, const leiden_params *p, int32_t *membership, int32_t where,
+                               double *modularity, leiden_stats *stats) {
+    if (!g || !p) {
+        lgb::set_last_error("NULL handle or params");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (where != LEIDEN_HOST && where != LEIDEN_DEVICE) {
+        lgb::set_last_error("invalid where");
+        return LEIDEN_ERR_INVALID;
+    }
+    return g->h.run(*p, membership, where, modularity, stats);
+}
+
+leiden_status leiden_batch_info(leiden_graph_t g, int32_t *num_graphs, int32_t *passes, int64_t *communities) {
+    if (!g) {
+        lgb::set_last_error("NULL handle");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (num_graphs) *num_graphs = g->h.num_graphs();
+    if (!passes && !communities) return LEIDEN_OK;
+    return g->h.graph_info(passes, communities);
 }
 
 leiden_status leiden_destroy(leiden_graph_t g) {

@@ -45,6 +45,29 @@ __device__ __forceinline__ void atomic_add_acc(long long *p, long long v) {
 }
 __device__ __forceinline__ void atomic_add_acc(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add_acc(float *p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_acc(unsigned long long *p, unsigned long long v) { atomicAdd(p, v); }
+
+// Running per-graph sum of one thread (sweep gains, move counts). In a batch
+// of graphs the sum of the previous graph goes to its slot base[g] when the
+// thread reaches a vertex of another graph; a single graph never flushes
+// here and reduces per warp at the end of the sweep instead.
+template <class V> struct GAcc {
+    V v = 0;
+    int32_t g = 0;
+};
+template <class V, class D>
+__device__ __forceinline__ void gacc_add(GAcc<V> &acc, bool batch, int32_t g, V x, D *base) {
+    if (batch && g != acc.g) {
+        if (acc.v != (V)0) atomic_add_acc(&base[acc.g], (D)acc.v);
+        acc.v = 0;
+        acc.g = g;
+    }
+    acc.v += x;
+}
+template <class V, class D> __device__ __forceinline__ void gacc_flush(GAcc<V> &acc, D *base) {
+    if (acc.v != (V)0) atomic_add_acc(&base[acc.g], (D)acc.v);
+    acc.v = 0;
+}
 
 // Σ reads: the async mode sees concurrent atomics from other SMs, so it reads
 // through L2 (ld.global.cg); deterministic mode reads a snapshot.

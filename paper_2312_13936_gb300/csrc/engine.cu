@@ -1,10 +1,16 @@
-// Host engine: one handle per graph. leiden_create copies the CSR to the
-// device; leiden_run drives the pass loop of Algorithm 1 (local-moving,
-// refinement, stop tests, renumbering, dendrogram lookup, aggregation,
-// move-based labels, threshold scaling) with the kernels of kernels.h. All
-// state stays on the device; per sweep the host reads back one scalar (the
-// sweep's delta-modularity or the refinement's move count) to decide whether
-// to continue, and per pass a handful of counts.
+// Host engine: one handle per graph or per batch of graphs. leiden_create
+// copies the CSR to the device; leiden_run drives the pass loop of
+// Algorithm 1 (local-moving, refinement, stop tests, renumbering, dendrogram
+// lookup, aggregation, move-based labels, threshold scaling) with the kernels
+// of kernels.h. All state stays on the device; each phase is one persistent
+// launch that tests convergence itself, and per pass the host reads back a
+// handful of counts.
+//
+// A batch of G graphs runs as one disjoint union: one set of launches per
+// pass serves every graph, each graph keeps its own 2m, convergence tests,
+// stop tests and pass count (per-graph arrays of k_batch.cu), and a graph
+// that stops leaves the union at the next renumbering. A single graph is the
+// case G = 1 without per-vertex graph ids.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -118,6 +124,20 @@ struct Handle::Impl {
     leiden_kernel_profile prof_out[LEIDEN_PROFILE_CLASSES];
     bool prof_valid = false;
     bool prof_det = false;
+    // batch of graphs (per-vertex graph ids only when G > 1)
+    int32_t G = 1;
+    std::vector<int64_t> hvseg0;           // vertex offsets of the graphs in the input
+    std::vector<double> hgw;               // weight sum of every graph (fp64)
+    int64_t *vseg0 = nullptr, *vseg = nullptr, *vseg2 = nullptr;  // G+1 each: input, this pass, next pass
+    int32_t *gid0 = nullptr, *gidA = nullptr, *gidB = nullptr, *rgid = nullptr;
+    int32_t *gstate = nullptr, *gdone = nullptr, *gli = nullptr, *glj = nullptr, *gpasses = nullptr;
+    int64_t *gkeep = nullptr, *gcomm = nullptr;
+    long long *gsumk = nullptr;            // per-graph sums of K (int64 or fp64 bits)
+    long long *gks = nullptr;              // per-graph key scale (int64 2m or fp32 1/2m)
+    double *g2m = nullptr, *gq = nullptr, *gmsum = nullptr;
+    unsigned *gactive = nullptr;
+    std::vector<int32_t> hpasses;          // per graph, after a run
+    std::vector<int64_t> hcomm;
 
     cudaEvent_t next_event() {
         if (ev_used == ev_pool.size()) {
@@ -242,6 +262,7 @@ struct Handle::Impl {
     int64_t rcap = -1;
     leiden_status ensure_relabel(int64_t cap) {
         if (!roff) {
+            if (G > 1) ST(alloc(&rgid, n0));
             ST(alloc(&roff, n0 + 1));
             for (int32_t **a : {&rdeg, &rinv, &rC, &rCB, &rstep}) ST(alloc(a, n0));
             long long *k = nullptr;
@@ -297,11 +318,15 @@ Handle::Handle() : p(new Impl) {}
 Handle::~Handle() { delete p; }
 
 leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices,
-                             const float *weights, int where, int validate, void *stream) {
+                             const float *weights, int where, int validate, void *stream, int32_t num_graphs,
+                             const int64_t *vtx_seg) {
     Impl &q = *p;
     q.s = static_cast<cudaStream_t>(stream);
     q.n0 = n;
     q.m0 = nnz;
+    q.G = num_graphs;
+    if (vtx_seg) q.hvseg0.assign(vtx_seg, vtx_seg + num_graphs + 1);
+    else q.hvseg0 = {0, n};
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&q.sm, cudaDevAttrMultiProcessorCount, dev));
@@ -344,7 +369,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     ST(q.alloc(&q.unproc, n));
     ST(q.alloc(&q.sigtot, n));
     char *tmp;
-    ST(q.alloc(&tmp, (int64_t)scan_tmp_bytes(n + 8192)));
+    ST(q.alloc(&tmp, (int64_t)scan_tmp_bytes((n > num_graphs ? n : num_graphs) + 8192)));
     q.scan_tmp = tmp;
     ST(q.ensure_part_tmp(partition_tmp_bytes(n, (32 - 1 + 16) * kNumBins + 1)));  // default schedule
     ST(q.alloc(&q.prof_cnt, (int64_t)LEIDEN_PROFILE_CLASSES * kProfCounters));
@@ -357,7 +382,25 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     ST(q.alloc(&q.iota_list, n));
     CK(launch_iota(q.iota_list, n, q.s));
     CK(launch_degrees(q.off0, q.deg0, n, &q.dsc->err, q.s));
+    // per-graph state (one graph: G = 1, no graph ids)
+    const int32_t G = q.G;
+    for (int64_t **a : {&q.vseg0, &q.vseg, &q.vseg2}) ST(q.alloc(a, G + 1));
+    for (int32_t **a : {&q.gstate, &q.gdone, &q.gli, &q.glj, &q.gpasses}) ST(q.alloc(a, G));
+    for (int64_t **a : {&q.gkeep, &q.gcomm}) ST(q.alloc(a, G));
+    ST(q.alloc(&q.gsumk, G));
+    ST(q.alloc(&q.gks, G));
+    ST(q.alloc(&q.g2m, G));
+    ST(q.alloc(&q.gq, G));
+    ST(q.alloc(&q.gmsum, 3 * (int64_t)G));
+    CK(cudaMemcpyAsync(q.vseg0, q.hvseg0.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, q.s));
+    if (G > 1) {
+        for (int32_t **a : {&q.gid0, &q.gidA, &q.gidB}) ST(q.alloc(a, n));
+        CK(launch_graph_ids(q.vseg0, G, n, q.gid0, q.s));
+        // indices arrive local to each graph
+        CK(launch_globalize_indices(q.vseg0, q.gid0, n, q.off0, nnz, q.idx0, &q.dsc->err, q.s));
+    }
     if (validate) CK(launch_validate(n, q.off0, q.idx0, q.w0, &q.dsc->err, q.s));
+    CK(cudaMemsetAsync(&q.dsc->wsum, 0, sizeof(double), q.s));
     CK(launch_weight_props(q.w0, nnz, &q.dsc->nonint, &q.dsc->wsum, q.s));
     CK(cudaMemcpyAsync(q.hsc, q.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, q.s));
     CK(cudaStreamSynchronize(q.s));
@@ -368,6 +411,21 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     }
     q.nonint = q.hsc->nonint != 0;
     q.wsum = q.hsc->wsum;
+    if (G > 1) {  // weight sum of every graph, for the deterministic mode's 2m < 2^31 rule
+        GraphView g0;
+        g0.n = n;
+        g0.off = q.off0;
+        g0.deg = q.deg0;
+        g0.idx = q.idx0;
+        g0.w = q.w0;
+        CK(cudaMemsetAsync(q.gmsum, 0, sizeof(double) * G, q.s));
+        CK(cudaMemsetAsync(&q.dsc->wsum, 0, sizeof(double), q.s));
+        CK(launch_vertex_weights(g0, false, q.K, &q.dsc->wsum, q.s));  // fp32 row sums into K
+        CK(launch_graph_sums(q.K, false, q.gid0, n, q.gmsum, q.s));
+        q.hgw.assign(G, 0.0);
+        CK(cudaMemcpyAsync(q.hgw.data(), q.gmsum, sizeof(double) * G, cudaMemcpyDeviceToHost, q.s));
+        CK(cudaStreamSynchronize(q.s));
+    }
     return LEIDEN_OK;
 }
 
@@ -396,6 +454,8 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     const bool det = prm.mode == LEIDEN_DETERMINISTIC;
     const bool trace = (prm.flags & LEIDEN_FLAG_TRACE) != 0;
     const int32_t L = prm.schedule_layers, B = prm.schedule_buckets;
+    const int32_t NG = q.G;
+    const bool batch = NG > 1;
     if (prm.max_iterations < 1 || prm.max_passes < 0 || !(prm.tolerance_drop > 0) || L < 1 || B < 1 ||
         (prm.mode != LEIDEN_ASYNC && prm.mode != LEIDEN_DETERMINISTIC) || !(prm.resolution >= 0) ||
         !std::isfinite(prm.tolerance) || (q.n0 > 0 && !membership)) {
@@ -408,14 +468,21 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         set_last_error("schedule_layers + schedule_buckets too large");
         return LEIDEN_ERR_INVALID;
     }
+    if (batch && (trace || (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES))) {
+        set_last_error("a batch of graphs runs without trace and without per-step launches");
+        return LEIDEN_ERR_UNSUPPORTED;
+    }
     ST(q.ensure_part_tmp(partition_tmp_bytes(q.n0, nkeys + 1)));
-    if (prm.max_iterations > q.phase_cap) {
+    if (prm.max_iterations > q.phase_cap) {  // per-sweep sums: max_iterations x G
         if (q.phase_dq) q.free_one(q.phase_dq);
         if (q.phase_moved) q.free_one(q.phase_moved);
+        if (q.gactive) q.free_one(q.gactive);
         q.phase_dq = nullptr;
         q.phase_moved = nullptr;
-        ST(q.alloc(&q.phase_dq, prm.max_iterations));
-        ST(q.alloc(&q.phase_moved, prm.max_iterations));
+        q.gactive = nullptr;
+        ST(q.alloc(&q.phase_dq, (int64_t)prm.max_iterations * NG));
+        ST(q.alloc(&q.phase_moved, (int64_t)prm.max_iterations * NG));
+        ST(q.alloc(&q.gactive, prm.max_iterations));
         q.phase_cap = prm.max_iterations;
     }
     if (det) {
@@ -423,8 +490,13 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             set_last_error("deterministic mode needs integer weights and resolution 1");
             return LEIDEN_ERR_UNSUPPORTED;
         }
-        if (q.wsum >= 2147483648.0) {
-            set_last_error("deterministic mode needs 2m < 2^31");
+        double wmax = q.wsum;
+        if (batch) {
+            wmax = 0;
+            for (double x : q.hgw) wmax = x > wmax ? x : wmax;
+        }
+        if (wmax >= 2147483648.0) {
+            set_last_error("deterministic mode needs 2m < 2^31 (in every graph of a batch)");
             return LEIDEN_ERR_OVERFLOW;
         }
     }
@@ -469,6 +541,17 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
 
     CK(launch_iota(q.C0, n0, s));
     q.launches++;
+    // per-graph state: graphs with vertices start active
+    {
+        std::vector<int32_t> st0(NG);
+        for (int32_t g = 0; g < NG; ++g)
+            st0[g] = q.hvseg0[g + 1] > q.hvseg0[g] ? kGraphActive : kGraphFinished;
+        CK(cudaMemcpyAsync(q.gstate, st0.data(), sizeof(int32_t) * NG, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(q.vseg, q.vseg0, sizeof(int64_t) * (NG + 1), cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(q.gpasses, 0, sizeof(int32_t) * NG, s));
+        CK(cudaStreamSynchronize(s));  // st0 is a local
+    }
+    const int32_t *cur_gid = batch ? q.gid0 : nullptr;  // graph of every vertex of G'
     GraphView G;
     G.n = n0;
     G.off = q.off0;
@@ -477,7 +560,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     G.w = q.w0;
     G.w_int = false;
     double tau = prm.tolerance;
-    bool broke = false;
+    bool no_edges = false;
     int cur_agg = 1;  // next pass writes agg[cur_agg ^ 1]
     int64_t Gcap = q.m0;  // entry capacity of G' (holey after aggregation)
     int passes = 0;
@@ -485,14 +568,24 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
 
     for (int32_t lp = 0; lp < prm.max_passes; ++lp) {
         const int64_t n = G.n;
+        if (n == 0) break;
         ST(mark(3));
-        // vertexWeights(G') and 2m
+        // vertexWeights(G') and 2m (of every graph of a batch)
         CK(cudaMemsetAsync(&q.dsc->two_m_f, 0, sizeof(double) + sizeof(long long), s));
         CK(launch_vertex_weights(G, det, q.K, det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, s));
+        if (batch) {
+            CK(cudaMemsetAsync(q.gsumk, 0, sizeof(long long) * NG, s));
+            CK(launch_graph_sums(q.K, det, cur_gid, n, q.gsumk, s));
+            CK(launch_graph_scales(q.gsumk, det, NG, q.gks, q.g2m, s));
+            q.launches += 2;
+        } else {
+            CK(launch_graph_scales(det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, det, 1, q.gks, q.g2m, s));
+            q.launches += 1;
+        }
         q.launches += 1;
         // schedule and (step, bin) lists
         SchedWork sw{q.scnt, q.slayer, q.sfcount};
-        CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s));
+        CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s, cur_gid, batch ? q.vseg : nullptr));
         q.launches += L > 1 ? L : 2;
         // one vertex list per (schedule step, degree bin), step-major
         CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
@@ -504,9 +597,9 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         ST(q.sync_scalars());
         const double two_m_f = q.hsc->two_m_f;
         const long long two_m_i = q.hsc->two_m_i;
-        if (det ? (two_m_i == 0) : !(two_m_f > 0)) {  // reading R12: no edges
+        if (!batch && (det ? (two_m_i == 0) : !(two_m_f > 0))) {  // reading R12: no edges
             CK(launch_iota(q.Cp, n, s));
-            broke = true;
+            no_edges = true;
             passes++;
             break;
         }
@@ -537,6 +630,10 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             CK(launch_gather_i32(q.step, perm, n, q.rstep, s));
             CK(launch_labels_to_new(q.Cp, perm, q.rinv, n, q.rC, s));
             q.launches += 9;
+            if (batch) {
+                CK(launch_gather_i32(cur_gid, perm, n, q.rgid, s));
+                q.launches++;
+            }
             sG.off = q.roff;
             sG.deg = q.rdeg;
             sG.idx = q.ridx;
@@ -589,6 +686,12 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         sc.key_off = q.key_off;
         sc.bar = q.bar;
         sc.hub_regions = hub_regions;
+        sc.gid = batch ? (relabel ? q.rgid : cur_gid) : nullptr;
+        sc.gks = q.gks;
+        sc.g2m = q.g2m;
+        sc.gdone = q.gdone;
+        sc.gactive = q.gactive;
+        sc.G = NG;
         const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
         // one sweep as per-(step, bin) launches (fallback and test path)
         auto run_steps = [&](bool refine) -> leiden_status {
@@ -620,10 +723,16 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         // One phase (Algorithm 2 or 3): sweeps until convergence. Normally one
         // persistent cooperative launch that tests convergence on the device;
         // otherwise one host-driven sweep at a time. Returns the sweeps run.
-        auto run_phase = [&](bool refine, int *iters) -> leiden_status {
+        auto run_phase = [&](bool refine, int *iters, int32_t *giters) -> leiden_status {
             sc.refine = refine;
             const bool single = refine && (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP);
             const int per_sm = step_launches ? 0 : sweep_coop_blocks_per_sm(det, sG.w_int, refine);
+            CK(launch_phase_init(q.gstate, NG, q.gdone, giters, s));
+            sc.giters = giters;
+            if (batch && per_sm <= 0) {
+                set_last_error("a batch of graphs needs the cooperative sweep kernel");
+                return LEIDEN_ERR_UNSUPPORTED;
+            }
             if (per_sm > 0) {
                 // enough blocks for the graph (about 2048 vertices each), so
                 // small graphs do not pay a full-GPU barrier per step
@@ -637,8 +746,9 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                 sc.dq_arr = q.phase_dq;
                 sc.moved_arr = q.phase_moved;
                 sc.iters_out = &q.dsc->iters;
-                CK(cudaMemsetAsync(q.phase_dq, 0, sizeof(long long) * prm.max_iterations, s));
-                CK(cudaMemsetAsync(q.phase_moved, 0, sizeof(unsigned long long) * prm.max_iterations, s));
+                CK(cudaMemsetAsync(q.phase_dq, 0, sizeof(long long) * prm.max_iterations * NG, s));
+                CK(cudaMemsetAsync(q.phase_moved, 0, sizeof(unsigned long long) * prm.max_iterations * NG, s));
+                CK(cudaMemsetAsync(q.gactive, 0, sizeof(unsigned) * prm.max_iterations, s));
                 sc.prof = prof_begin(refine ? 8 : 0);
                 CK(launch_sweep_coop(sc, sList, grid, s));
                 prof_end();
@@ -664,13 +774,14 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
                 }
             }
             *iters = k;
+            CK(launch_fill_i32(giters, k, 1, s));
             return LEIDEN_OK;
         };
         // ---- local-moving phase (Algorithm 2)
         ST(mark(0));
         CK(cudaMemsetAsync(q.unproc, 1, (size_t)n, s));  // mark all vertices unprocessed
         int li = 0;
-        ST(run_phase(false, &li));
+        ST(run_phase(false, &li, q.gli));
         st.move_iterations += li;
         if (trace) {
             if (relabel) {
@@ -689,7 +800,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));  // Sigma' <- K', one member each
         q.launches += 2;
         int lj = 0;
-        ST(run_phase(true, &lj));
+        ST(run_phase(true, &lj, q.glj));
         if (relabel) {  // back to the ids of G'
             CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cp, s));
             CK(launch_labels_to_old(sCB, q.list, q.rinv, n, q.CB, s));
@@ -706,31 +817,34 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(launch_fill_i32(q.rep, 0, n, s));
         CK(launch_mark_labels(q.CB, n, q.rep, s));
         CK(launch_exclusive_scan_i32(q.rep, q.pos2, n, q.scan_tmp, s));
-        q.launches += 10;
-        int64_t counts[2];
+        // every graph takes Algorithm 1's two break tests on its own counts;
+        // the graphs that go on keep their refined communities, densely
+        // renumbered after those of the graphs before them
+        CK(launch_graph_stop(q.vseg, q.pos, q.pos2, q.gli, q.g2m, prm.aggregation_tolerance, NG, q.gstate, q.gkeep,
+                             q.gpasses, s));
+        CK(launch_exclusive_scan(q.gkeep, q.vseg2, NG, q.scan_tmp, s));
+        q.launches += 14;
+        int64_t counts[3];
         CK(cudaMemcpyAsync(&counts[0], q.pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(&counts[1], q.pos2 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(&counts[2], q.vseg2 + NG, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
         ST(q.sync_scalars());
-        const int64_t ncomm = counts[0], nbound = counts[1];
+        const int64_t ncomm_all = counts[0];
+        const int64_t ncomm = counts[2];  // communities of the graphs that go on: vertices of the next graph
         if (trace) {
-            int64_t c4[4] = {n, li, lj, ncomm};
+            int64_t c4[4] = {n, li, lj, ncomm_all};
             std::vector<char> buf(sizeof(c4));
             std::memcpy(buf.data(), c4, sizeof(c4));
             q.trace[{lp, 4}] = buf;
             q.trace_count[{lp, 4}] = 4;
         }
-        if (li <= 1 && nbound == ncomm) {  // globally converged
-            broke = true;
-            break;
-        }
-        if ((double)ncomm / (double)n > prm.aggregation_tolerance) {  // low shrink
-            broke = true;
-            break;
-        }
-        // ---- renumber communities; lookup dendrogram
-        CK(launch_renumber(q.Cp, q.pos, q.Cd, n, s));
-        CK(launch_lookup(q.C0, q.Cd, n0, s));
-        q.launches += 2;
+        // ---- renumber communities; lookup dendrogram (graphs that stop take
+        // their refined labels, reading R8)
+        CK(launch_renumber_batch(q.Cp, q.pos, cur_gid, q.vseg, q.vseg2, q.gstate, q.Cd, n, s));
+        CK(launch_lookup_batch(q.C0, batch ? q.gid0 : nullptr, q.vseg0, q.vseg, q.gstate, q.Cd, q.Cp, n0, s));
+        CK(launch_commit_states(q.gstate, NG, s));
+        q.launches += 3;
+        if (ncomm == 0) break;  // every graph stopped (globally converged or low shrink)
         if (trace) {
             q.record(lp, 5, q.Cd, n);
             q.record(lp, 10, q.C0, n0);
@@ -801,6 +915,13 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         // move-based labels of the super-vertices (reading R3)
         CK(launch_bound_labels(q.Cd, q.CB, n, ncomm, q.bnd, q.rep, q.label, s));
         q.launches += 4;
+        if (batch) {  // graph of every super-vertex; segments of the next graph
+            int32_t *nxt = cur_gid == q.gidA ? q.gidB : q.gidA;
+            CK(launch_next_gid(q.Cd, cur_gid, n, nxt, s));
+            cur_gid = nxt;
+            q.launches++;
+        }
+        std::swap(q.vseg, q.vseg2);
         GraphView G2;
         G2.n = ncomm;
         G2.off = q.agg[dst].off;
@@ -834,33 +955,68 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         tau /= prm.tolerance_drop;  // threshold scaling
     }
     ST(mark(3));
-    // C <- lookup dendrogram using C to C' (reading R8)
-    if (broke) {
+    // C <- lookup dendrogram using C to C' (reading R8): a graph without
+    // edges ends on its singletons; graphs of a batch still running after
+    // the last pass take ids of the last aggregated graph, moved into their
+    // own range of the input
+    if (no_edges) {
         CK(launch_lookup(q.C0, q.Cp, n0, s));
         q.launches++;
     }
-    // canonical labels: rank of each community's smallest vertex id
+    if (batch) {
+        CK(launch_finalize_batch(q.C0, q.gid0, q.vseg0, q.vseg, q.gstate, n0, s));
+        q.launches++;
+    }
+    // canonical labels: rank of each community's smallest vertex id (inside
+    // its own graph)
     int32_t *outp = (where == LEIDEN_DEVICE) ? membership : q.out;
     CK(launch_min_vertex(q.C0, n0, q.minv, s));
     CK(launch_first_flags(q.C0, q.minv, n0, q.flag, s));
     CK(launch_exclusive_scan_i32(q.flag, q.pos, n0, q.scan_tmp, s));
-    CK(launch_canonical(q.C0, q.minv, q.pos, n0, outp, s));
+    if (batch) CK(launch_canonical_batch(q.C0, q.minv, q.pos, q.gid0, q.vseg0, n0, outp, s));
+    else CK(launch_canonical(q.C0, q.minv, q.pos, n0, outp, s));
     q.launches += 7;
-    // modularity (Eq. 1) of the result on the input graph
+    // modularity (Eq. 1) of the result on the input graph (each graph's own)
     CK(cudaMemsetAsync(q.sigtot, 0, sizeof(double) * n0, s));
     CK(cudaMemsetAsync(q.dsc->msum, 0, sizeof(double) * 4, s));
-    CK(launch_modularity_parts(n0, q.off0, q.idx0, q.w0, outp, q.sigtot, q.dsc->msum, s));
-    CK(launch_sum_squares(q.sigtot, n0, &q.dsc->msum[2], s));
-    q.launches += 2;
+    if (batch) {
+        CK(cudaMemsetAsync(q.gmsum, 0, sizeof(double) * 3 * NG, s));
+        CK(launch_modularity_batch(n0, q.off0, q.idx0, q.w0, outp, q.gid0, q.vseg0, NG, prm.resolution, q.sigtot,
+                                   q.gmsum, &q.dsc->msum[3], q.gq, s));
+        CK(launch_graph_counts(q.pos, q.vseg0, NG, q.gcomm, s));
+        q.launches += 4;
+    } else {
+        CK(launch_modularity_parts(n0, q.off0, q.idx0, q.w0, outp, q.sigtot, q.dsc->msum, s));
+        CK(launch_sum_squares(q.sigtot, n0, &q.dsc->msum[2], s));
+        q.launches += 2;
+    }
     int64_t ncomm_out = 0;
     CK(cudaMemcpyAsync(&ncomm_out, q.pos + n0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     if (where != LEIDEN_DEVICE && n0 > 0)
         CK(cudaMemcpyAsync(membership, q.out, sizeof(int32_t) * n0, cudaMemcpyDeviceToHost, s));
+    std::vector<double> qg(batch ? NG : 0);
+    q.hpasses.assign(NG, 0);
+    q.hcomm.assign(NG, 0);
+    if (batch) {
+        CK(cudaMemcpyAsync(qg.data(), q.gq, sizeof(double) * NG, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(q.hpasses.data(), q.gpasses, sizeof(int32_t) * NG, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(q.hcomm.data(), q.gcomm, sizeof(int64_t) * NG, cudaMemcpyDeviceToHost, s));
+    }
     CK(cudaEventRecord(ev1, s));
     ST(q.sync_scalars());
-    const double two_m = q.hsc->msum[1];
-    const double Q = two_m > 0 ? q.hsc->msum[0] / two_m - prm.resolution * q.hsc->msum[2] / (two_m * two_m) : 0.0;
-    if (modularity) *modularity = Q;
+    double Q;
+    if (batch) {  // per-graph scores; the statistics carry their mean
+        Q = 0;
+        for (double x : qg) Q += x;
+        Q /= NG;
+        if (modularity) std::memcpy(modularity, qg.data(), sizeof(double) * NG);
+    } else {
+        const double two_m = q.hsc->msum[1];
+        Q = two_m > 0 ? q.hsc->msum[0] / two_m - prm.resolution * q.hsc->msum[2] / (two_m * two_m) : 0.0;
+        if (modularity) *modularity = Q;
+        q.hpasses[0] = passes;
+        q.hcomm[0] = ncomm_out;
+    }
     if (stats) {
         float ms = 0;
         cudaEventElapsedTime(&ms, ev0, ev1);
@@ -886,6 +1042,18 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     if (profile) ST(q.finish_profile());
+    return LEIDEN_OK;
+}
+
+int32_t Handle::num_graphs() const { return p->G; }
+
+leiden_status Handle::graph_info(int32_t *passes, int64_t *communities) const {
+    if (p->hpasses.size() != (size_t)p->G) {
+        set_last_error("no run has finished on this handle");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (passes) std::memcpy(passes, p->hpasses.data(), sizeof(int32_t) * p->G);
+    if (communities) std::memcpy(communities, p->hcomm.data(), sizeof(int64_t) * p->G);
     return LEIDEN_OK;
 }
 

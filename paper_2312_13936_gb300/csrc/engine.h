@@ -18,9 +18,16 @@ class Handle {
     ~Handle();
     Handle(const Handle &) = delete;
     Handle &operator=(const Handle &) = delete;
+    // one graph (num_graphs = 1, vtx_seg null) or a batch: graph g owns
+    // vertices [vtx_seg[g], vtx_seg[g+1]) and its indices are local to it
     leiden_status create(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices, const float *weights,
-                         int where, int validate, void *stream);
+                         int where, int validate, void *stream, int32_t num_graphs = 1,
+                         const int64_t *vtx_seg = nullptr);
+    // modularity: one value, or num_graphs values for a batch (host)
     leiden_status run(const leiden_params &p, int32_t *membership, int where, double *modularity, leiden_stats *stats);
+    int32_t num_graphs() const;
+    // per-graph passes and communities of the last run (host arrays)
+    leiden_status graph_info(int32_t *passes, int64_t *communities) const;
     leiden_status trace_get(int pass, int what, void *dst, int64_t *count) const;
     leiden_status profile_get(leiden_kernel_profile *out) const;
 

@@ -42,6 +42,7 @@ __global__ void k_lookup(int32_t *C0, const int32_t *map, int64_t n0) {
 __global__ void k_comm_counts(const int32_t *Cd, const int32_t *deg, int64_t n, int64_t *cnt, int64_t *tdeg) {
     GRID_STRIDE(i, n) {
         const int32_t c = Cd[i];
+        if (c < 0) continue;  // a graph of a batch that stopped
         atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[c]), 1ULL);
         atomicAdd(reinterpret_cast<unsigned long long *>(&tdeg[c]), (unsigned long long)deg[i]);
     }
@@ -49,6 +50,7 @@ __global__ void k_comm_counts(const int32_t *Cd, const int32_t *deg, int64_t n, 
 __global__ void k_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, int32_t *cursor, int32_t *members) {
     GRID_STRIDE(i, n) {
         const int32_t c = Cd[i];
+        if (c < 0) continue;
         members[coff[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
     }
 }
@@ -59,7 +61,10 @@ __global__ void k_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key
     }
 }
 __global__ void k_bound_of(const int32_t *Cd, const int32_t *CB, int64_t n, int32_t *bnd) {
-    GRID_STRIDE(i, n) bnd[Cd[i]] = CB[i];  // all members of a refined community share one bound
+    GRID_STRIDE(i, n) {
+        const int32_t c = Cd[i];
+        if (c >= 0) bnd[c] = CB[i];  // all members of a refined community share one bound
+    }
 }
 __global__ void k_rep_min(const int32_t *bnd, int64_t ncomm, int32_t *rep) {
     GRID_STRIDE(s, ncomm) atomicMin(&rep[bnd[s]], (int32_t)s);

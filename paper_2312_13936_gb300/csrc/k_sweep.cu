@@ -68,6 +68,25 @@ template <class P, class W> struct SV {
     unsigned *bar;
     int *err;
     unsigned long long *prof;
+    // batch of graphs (gid == null: one graph)
+    const int32_t *gid;
+    const A *gks;
+    const double *g2m;
+    int32_t *gdone;
+    int32_t *giters;
+    unsigned *gactive;
+    int32_t G;
+};
+
+// A thread's sweep sums: gains or joins (asynchronous), applied gains
+// (deterministic local-moving), applied proposals (refinement), and this
+// sweep's per-graph slots they go to.
+template <class P> struct Sums {
+    GAcc<typename P::acc> gain;
+    GAcc<long long> dgain;
+    GAcc<unsigned long long> moved;
+    typename P::tot *dq;
+    unsigned long long *mv;
 };
 
 template <class P, class W> SV<P, W> view(const SweepCtx &c) {
@@ -109,11 +128,17 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.bar = c.bar;
     a.err = c.err;
     a.prof = c.prof;
+    a.gid = c.gid;
+    a.gks = static_cast<const A *>(c.gks);
+    a.g2m = c.g2m;
+    a.gdone = c.gdone;
+    a.giters = c.giters;
+    a.gactive = c.gactive;
+    a.G = c.G;
     return a;
 }
 
 __device__ __forceinline__ int32_t ldm(const int32_t *p) { return __ldcg(p); }
-__device__ __forceinline__ float ldm(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldm(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ long long ldm(const long long *p) { return __ldcg(p); }
 __device__ __forceinline__ uint8_t ldm(const uint8_t *p) { return __ldcg(p); }
@@ -123,20 +148,32 @@ template <class A> __device__ __forceinline__ bool better(A k1, int32_t c1, A k2
     return k1 > k2 || (k1 == k2 && c1 < c2);
 }
 
-// Decision for vertex v (one thread) with best candidate (key, cand),
-// K_{v->d} = kvd and Sigma_d = sd. Returns true if an asynchronous
-// local-moving move was applied (its neighbours must then be marked
-// unprocessed).
-template <class P, class W, bool REFINE>
+// graph of vertex v and its key scale
+// (B: the kernel serves a batch of graphs; the single-graph instantiations
+// carry no per-graph code)
+template <bool B, class P, class W> __device__ __forceinline__ int32_t graph_of(const SV<P, W> &a, int32_t v) {
+    return B ? __ldg(&a.gid[v]) : 0;
+}
+template <bool B, class P, class W>
+__device__ __forceinline__ typename P::acc kscale_of(const SV<P, W> &a, int32_t gv) {
+    return B ? __ldg(&a.gks[gv]) : a.kscale;
+}
+
+// Decision for vertex v (one thread, graph gv, key scale kscale) with best
+// candidate (key, cand), K_{v->d} = kvd and Sigma_d = sd. Returns true if
+// an asynchronous local-moving move was applied (its neighbours must then be
+// marked unprocessed).
+template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ bool decide_sd(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
                                           typename P::acc key, int32_t cand, typename P::acc kvd,
-                                          typename P::tot sd, typename P::acc &local_gain, int32_t cur_step) {
+                                          typename P::tot sd, Sums<P> &sm, int32_t cur_step, int32_t gv,
+                                          typename P::acc kscale) {
     using A = typename P::acc;
     using T = typename P::tot;
     bool mv = false;
     A g = 0;
     if (cand != INT_MAX) {
-        const A ks = stay_key(a.kscale, kvd, Kv, sd, a.gamma);
+        const A ks = stay_key(kscale, kvd, Kv, sd, a.gamma);
         mv = key > ks;
         if (!REFINE && mv && cur_step >= a.cap_step) {
             // S2: where neighbours may move together, a single-vertex
@@ -149,14 +186,14 @@ __device__ __forceinline__ bool decide_sd(const SV<P, W> &a, int32_t v, int32_t 
         // Asynchronous refinement below the capped step: no two vertices of
         // a step are adjacent, so the neighbour through which v saw cand
         // stays in cand and nobody joins v while it leaves: the join is
-        // applied at once (local_gain counts joins in this phase).
+        // applied at once (the gain sum counts joins in this phase).
         if (mv) {
             atomic_add_acc(&a.Sig[d], -(T)Kv);
             atomic_add_acc(&a.Sig[cand], (T)Kv);
             atomicSub(&a.size[d], 1);
             atomicAdd(&a.size[cand], 1);
             a.C[v] = cand;
-            local_gain += (A)1;
+            gacc_add(sm.gain, B, gv, (A)1, sm.mv);
         }
         return false;
     }
@@ -171,22 +208,24 @@ __device__ __forceinline__ bool decide_sd(const SV<P, W> &a, int32_t v, int32_t 
         atomicSub(&a.size[d], 1);
         atomicAdd(&a.size[cand], 1);
         a.C[v] = cand;
-        local_gain += g;
+        gacc_add(sm.gain, B, gv, g, sm.dq);
     }
     return mv;
 }
-template <class P, class W, bool REFINE>
+template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
-                                       typename P::acc key, int32_t cand, typename P::acc kvd,
-                                       typename P::acc &local_gain, int32_t cur_step) {
-    return decide_sd<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, ldm(&a.Sig[d]), local_gain, cur_step);
+                                       typename P::acc key, int32_t cand, typename P::acc kvd, Sums<P> &sm,
+                                       int32_t cur_step, int32_t gv, typename P::acc kscale) {
+    return decide_sd<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, ldm(&a.Sig[d]), sm, cur_step, gv, kscale);
 }
 
 // Eligibility: local-moving takes unprocessed vertices and marks them
 // processed (Algorithm 2 pruning); refinement takes isolated vertices (the
-// community of v has v as its only member, reading R7).
-template <class P, class W, bool REFINE>
-__device__ __forceinline__ bool take_vertex(const SV<P, W> &a, int32_t v, int32_t &d) {
+// community of v has v as its only member, reading R7). In a batch, the
+// vertices of a graph whose phase has converged are left alone.
+template <class P, class W, bool REFINE, bool B>
+__device__ __forceinline__ bool take_vertex(const SV<P, W> &a, int32_t v, int32_t &d, int32_t gv) {
+    if (B && ldm(&a.gdone[gv])) return false;
     if (REFINE) {
         d = ldm(&a.C[v]);
         return ldm(&a.size[d]) == 1;
@@ -200,9 +239,9 @@ __device__ __forceinline__ bool take_vertex(const SV<P, W> &a, int32_t v, int32_
 }
 
 // --------------------------------------------------------- thread bin
-template <class P, class W, bool REFINE>
+template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
-                                           int32_t cur_step, typename P::acc &local_gain, ProfCounts &pc) {
+                                           int32_t cur_step, Sums<P> &sm, ProfCounts &pc) {
     using A = typename P::acc;
     constexpr int E = kThreadMaxDeg;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -214,7 +253,8 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
         const A Kv = a.K[v];
         const int64_t e0 = a.off[v];
         const int32_t dv = a.deg[v];
-        const bool elig = REFINE ? (ldm(&a.size[d]) == 1) : (up != 0);
+        const int32_t gv = graph_of<B>(a, v);
+        const bool elig = (REFINE ? (ldm(&a.size[d]) == 1) : (up != 0)) && !(B && ldm(&a.gdone[gv]));
         if (!elig) {
             if (REFINE || P::det) a.prop[v] = -1;
             pc.v[1]++;
@@ -255,6 +295,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
         A key = AccLimits<A>::lowest();
         int32_t cand = INT_MAX;
         int distinct = 0;
+        const A ks = kscale_of<B>(a, gv);
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             if (c[k] < 0) continue;
@@ -263,13 +304,13 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
                 kvd = wt[k];
                 continue;
             }
-            const A kk = move_key(a.kscale, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma);
+            const A kk = move_key(ks, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma);
             if (better(kk, c[k], key, cand)) {
                 key = kk;
                 cand = c[k];
             }
         }
-        const bool mv = decide_sd<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, sd, local_gain, cur_step);
+        const bool mv = decide_sd<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, sd, sm, cur_step, gv, ks);
         if (a.prof) {
             pc.v[0]++;
             pc.v[2] += dv;
@@ -288,9 +329,9 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
 }
 
 // ----------------------------------------------------------- tile bins
-template <class P, class W, int T, bool REFINE>
+template <class P, class W, int T, bool REFINE, bool B>
 __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
-                                         int32_t cur_step, typename P::acc &local_gain, ProfCounts &pc) {
+                                         int32_t cur_step, Sums<P> &sm, ProfCounts &pc) {
     using A = typename P::acc;
     const int lane = threadIdx.x & 31;
     const int tl = lane & (T - 1);
@@ -298,9 +339,10 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
     const int64_t tiles = (int64_t)gridDim.x * (blockDim.x / T);
     for (int64_t t = lo + (int64_t)blockIdx.x * (blockDim.x / T) + threadIdx.x / T; t < hi; t += tiles) {
         const int32_t v = list[t];
+        const int32_t gv = graph_of<B>(a, v);
         int32_t d = 0;
         int elig = 0;
-        if (tl == 0) elig = take_vertex<P, W, REFINE>(a, v, d) ? 1 : 0;
+        if (tl == 0) elig = take_vertex<P, W, REFINE, B>(a, v, d, gv) ? 1 : 0;
         elig = __shfl_sync(tmask, elig, 0, T);
         d = __shfl_sync(tmask, d, 0, T);
         if (!elig) {
@@ -340,8 +382,9 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
         const A kvd = dball ? kvd_b : (A)0;
         A key = AccLimits<A>::lowest();
         int32_t cand = INT_MAX;
+        const A ks = kscale_of<B>(a, gv);
         if (lead && c != d) {
-            key = move_key(a.kscale, sum, Kv, ldm(&a.Sig[c]), a.gamma);
+            key = move_key(ks, sum, Kv, ldm(&a.Sig[c]), a.gamma);
             cand = c;
         }
 #pragma unroll
@@ -354,7 +397,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
             }
         }
         int mv = 0;
-        if (tl == 0) mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain, cur_step) ? 1 : 0;
+        if (tl == 0) mv = decide<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, sm, cur_step, gv, ks) ? 1 : 0;
         if (a.prof) {
             const unsigned lb = __ballot_sync(tmask, lead) & tmask;
             if (tl == 0) {
@@ -375,18 +418,19 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
 }
 
 // ------------------------------------------------------- warp-table bin
-template <class P, class W, bool REFINE>
+template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
-                                         int32_t cur_step, int32_t *keys, typename P::acc *vals,
-                                         typename P::acc &local_gain, ProfCounts &pc) {
+                                         int32_t cur_step, int32_t *keys, typename P::acc *vals, Sums<P> &sm,
+                                         ProfCounts &pc) {
     using A = typename P::acc;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t t = lo + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < hi; t += nwarps) {
         const int32_t v = list[t];
+        const int32_t gv = graph_of<B>(a, v);
         int32_t d = 0;
         int elig = 0;
-        if (lane == 0) elig = take_vertex<P, W, REFINE>(a, v, d) ? 1 : 0;
+        if (lane == 0) elig = take_vertex<P, W, REFINE, B>(a, v, d, gv) ? 1 : 0;
         elig = __shfl_sync(kFull, elig, 0);
         d = __shfl_sync(kFull, d, 0);
         if (!elig) {
@@ -415,6 +459,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
         __syncwarp();
         A key = AccLimits<A>::lowest(), kvd = 0;
         int32_t cand = INT_MAX;
+        const A ks = kscale_of<B>(a, gv);
         for (int s = lane; s < S; s += 32) {
             const int32_t k = keys[s];
             if (k < 0) continue;
@@ -424,7 +469,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(a.kscale, sum, Kv, ldm(&a.Sig[k]), a.gamma);
+            const A kk = move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma);
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -441,7 +486,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
         kvd = warp_sum(kvd);
         int mv = 0;
         if (lane == 0) {
-            mv = decide<P, W, REFINE>(a, v, d, Kv, key, cand, kvd, local_gain, cur_step) ? 1 : 0;
+            mv = decide<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, sm, cur_step, gv, ks) ? 1 : 0;
             pc.v[0]++;
             pc.v[2] += dv;
             if ((REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0)) {
@@ -461,10 +506,10 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
 // ------------------------------------------------ block / hub table bins
 // One block per vertex (HUB: a global-memory table per block; only blocks
 // below hub_regions take part).
-template <class P, class W, bool REFINE, bool HUB>
+template <class P, class W, bool REFINE, bool HUB, bool B>
 __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo, int64_t hi,
                                           int32_t cur_step, int32_t *keys, typename P::acc *vals, int max_bits,
-                                          typename P::acc &local_gain, ProfCounts &pc) {
+                                          Sums<P> &sm, ProfCounts &pc) {
     using A = typename P::acc;
     __shared__ int s_elig, s_d, s_mv;
     __shared__ A s_key[32], s_kvd[32];
@@ -474,10 +519,11 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
     if (HUB && (int64_t)blockIdx.x >= nblk) return;
     for (int64_t t = lo + blockIdx.x; t < hi; t += nblk) {
         const int32_t v = list[t];
+        const int32_t gv = graph_of<B>(a, v);
         __syncthreads();
         if (tid == 0) {
             int32_t d = 0;
-            s_elig = take_vertex<P, W, REFINE>(a, v, d) ? 1 : 0;
+            s_elig = take_vertex<P, W, REFINE, B>(a, v, d, gv) ? 1 : 0;
             s_d = d;
             if (!s_elig && (REFINE || P::det)) a.prop[v] = -1;
             if (!s_elig) pc.v[1]++;
@@ -513,6 +559,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
         __syncthreads();
         A key = AccLimits<A>::lowest(), kvd = 0;
         int32_t cand = INT_MAX;
+        const A ks = kscale_of<B>(a, gv);
         for (int64_t s = tid; s < S; s += blockDim.x) {
             const int32_t k = keys[s];
             if (k < 0) continue;
@@ -522,7 +569,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(a.kscale, sum, Kv, ldm(&a.Sig[k]), a.gamma);
+            const A kk = move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma);
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -553,7 +600,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
                 }
                 kd += s_kvd[w2];
             }
-            s_mv = decide<P, W, REFINE>(a, v, d, Kv, bk, bc, kd, local_gain, cur_step) ? 1 : 0;
+            s_mv = decide<P, W, REFINE, B>(a, v, d, Kv, bk, bc, kd, sm, cur_step, gv, ks) ? 1 : 0;
             pc.v[0]++;
             pc.v[2] += dv;
             if ((REFINE || P::det) ? (a.prop[v] >= 0) : (s_mv != 0)) {
@@ -570,9 +617,9 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
 
 // ------------------------------------------------------------ apply steps
 // Deterministic local-moving: commit the proposals of one step.
-template <class P, class W>
+template <class P, class W, bool B>
 __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo,
-                                               int64_t hi, long long &g) {
+                                               int64_t hi, Sums<P> &sm) {
     for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = list[t];
@@ -585,7 +632,7 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
         atomicSub(&a.size[d], 1);
         atomicAdd(&a.size[c], 1);
         a.C[v] = c;
-        g += ldm(&a.gain[v]);
+        gacc_add(sm.dgain, B, graph_of<B>(a, v), ldm(&a.gain[v]), reinterpret_cast<long long *>(sm.dq));
         const int64_t e0 = a.off[v];
         const int32_t dv = a.deg[v];
         for (int32_t e = 0; e < dv; ++e) a.unproc[a.idx[e0 + e]] = 1;
@@ -595,9 +642,9 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
 // Refinement: accept proposal v -> t unless t is a single-vertex community
 // whose vertex proposes in the same step; of a mutual pair the larger id
 // moves (reading S5). Accepted vertices join t.
-template <class P, class W>
+template <class P, class W, bool B>
 __device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo,
-                                                 int64_t hi, int32_t cur_step, unsigned long long &mv) {
+                                                 int64_t hi, int32_t cur_step, Sums<P> &sm) {
     for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = list[t];
@@ -611,7 +658,7 @@ __device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_
         atomicSub(&a.size[v], 1);
         atomicAdd(&a.size[tg], 1);
         a.C[v] = tg;
-        mv++;
+        gacc_add(sm.moved, B, graph_of<B>(a, v), 1ULL, sm.mv);
     }
 }
 
@@ -669,114 +716,165 @@ template <class A> __device__ __forceinline__ int32_t *table_keys() {
 // when a sweep's delta-modularity (reading S4 for the deterministic mode) is
 // at most tau (Algorithm 2), refinement when a sweep moves nobody (reading
 // R6) -- or max_it sweeps ran. The test reads per-sweep sums after a grid
-// barrier, so every block takes the same decision.
-template <class P, class W, bool REFINE>
+// barrier, so every block takes the same decision. In a batch every graph
+// takes the test on its own sums; the phase ends when no graph is left.
+template <class P, class W, bool REFINE, bool B>
 __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, const int32_t *__restrict__ list) {
     using A = typename P::acc;
+    using T = typename P::tot;
     int32_t *skeys = table_keys<A>();
     A *svals = table_vals<A>();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr bool batch = B;
     ProfCounts pc;
     int32_t it = 0;
     bool ok = true;
     while (ok && it < a.max_it) {
-        A local_gain = 0;
-        long long det_gain = 0;
-        unsigned long long moved = 0;
+        Sums<P> sm;
+        sm.dq = a.dq_arr + (size_t)it * a.G;
+        sm.mv = a.moved_arr + (size_t)it * a.G;
         for (int32_t k = 0; k < a.nsteps && ok; ++k) {
             const int64_t *ko = a.key_off + (int64_t)k * kNumBins;
             const int64_t b0 = __ldcg(&ko[0]), b8 = __ldcg(&ko[8]);
             if (b0 == b8) continue;  // empty step: every block sees the same counts
-            run_thread<P, W, REFINE>(a, list, __ldcg(&ko[1]), __ldcg(&ko[2]), k, local_gain, pc);
-            run_tile<P, W, 16, REFINE>(a, list, __ldcg(&ko[2]), __ldcg(&ko[3]), k, local_gain, pc);
-            run_tile<P, W, 32, REFINE>(a, list, __ldcg(&ko[3]), __ldcg(&ko[4]), k, local_gain, pc);
-            run_warp<P, W, REFINE>(a, list, __ldcg(&ko[4]), __ldcg(&ko[5]), k, skeys + wib * kWarpSlots,
-                                   svals + wib * kWarpSlots, local_gain, pc);
+            run_thread<P, W, REFINE, B>(a, list, __ldcg(&ko[1]), __ldcg(&ko[2]), k, sm, pc);
+            run_tile<P, W, 16, REFINE, B>(a, list, __ldcg(&ko[2]), __ldcg(&ko[3]), k, sm, pc);
+            run_tile<P, W, 32, REFINE, B>(a, list, __ldcg(&ko[3]), __ldcg(&ko[4]), k, sm, pc);
+            run_warp<P, W, REFINE, B>(a, list, __ldcg(&ko[4]), __ldcg(&ko[5]), k, skeys + wib * kWarpSlots,
+                                   svals + wib * kWarpSlots, sm, pc);
             const int64_t b5 = __ldcg(&ko[5]), b6 = __ldcg(&ko[6]), b7 = __ldcg(&ko[7]);
             if (b6 > b5) {
                 __syncthreads();  // the warp tables become one block table
-                run_block<P, W, REFINE, false>(a, list, b5, b6, k, skeys, svals, ceil_log2(kBlockSlots), local_gain,
-                                               pc);
+                run_block<P, W, REFINE, false, B>(a, list, b5, b6, k, skeys, svals, ceil_log2(kBlockSlots), sm, pc);
             }
             if (b7 > b6) {
                 const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
-                run_block<P, W, REFINE, true>(a, list, b6, b7, k, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
-                                              local_gain, pc);
+                run_block<P, W, REFINE, true, B>(a, list, b6, b7, k, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
+                                              sm, pc);
             }
             if (!(ok = grid_barrier(a.bar, a.err))) break;
             // apply phase: deterministic mode, and refinement proposals where
             // neighbours may share a step (asynchronous refinement applies
             // its joins at once below the capped step)
             if (P::det || (REFINE && k >= a.cap_step)) {
-                if (REFINE) run_refine_apply(a, list, b0, b8, k, moved);
-                else run_move_apply(a, list, b0, b8, det_gain);
+                if (REFINE) run_refine_apply<P, W, B>(a, list, b0, b8, k, sm);
+                else run_move_apply<P, W, B>(a, list, b0, b8, sm);
                 if (!(ok = grid_barrier(a.bar, a.err))) break;
             }
         }
         if (!ok) break;
-        // this sweep's totals, then the convergence test
-        if (REFINE) {
-            if (!P::det) moved += (unsigned long long)(local_gain + (A)0.5);
+        // this sweep's sums: one graph reduces per warp, a batch flushes
+        // every thread's running sum into its graph's slot
+        if (batch) {
+            if (REFINE) {
+                if (!P::det) gacc_flush(sm.gain, sm.mv);
+                gacc_flush(sm.moved, sm.mv);
+            } else if (P::det) {
+                gacc_flush(sm.dgain, reinterpret_cast<long long *>(sm.dq));
+            } else {
+                gacc_flush(sm.gain, sm.dq);
+            }
+        } else if (REFINE) {
+            unsigned long long moved = sm.moved.v;
+            if (!P::det) moved += (unsigned long long)(sm.gain.v + (A)0.5);
             moved = warp_sum(moved);
-            if (lane == 0 && moved) atomicAdd(&a.moved_arr[it], moved);
+            if (lane == 0 && moved) atomicAdd(&sm.mv[0], moved);
         } else if (P::det) {
-            det_gain = warp_sum(det_gain);
-            if (lane == 0 && det_gain) atomic_add_acc(reinterpret_cast<long long *>(&a.dq_arr[it]), det_gain);
+            const long long g = warp_sum(sm.dgain.v);
+            if (lane == 0 && g) atomic_add_acc(reinterpret_cast<long long *>(&sm.dq[0]), g);
         } else {
-            const A s = warp_sum(local_gain);
-            if (lane == 0 && s != (A)0) atomic_add_acc(&a.dq_arr[it], (typename P::tot)s);
+            const A g = warp_sum(sm.gain.v);
+            if (lane == 0 && g != (A)0) atomic_add_acc(&sm.dq[0], (T)g);
         }
         if (!(ok = grid_barrier(a.bar, a.err))) break;
         bool stop;
-        if (REFINE) {
-            stop = __ldcg(&a.moved_arr[it]) == 0ULL || a.single_sweep;
+        if (batch) {
+            // every graph still running takes its own test; graphs that
+            // stop record their sweep count, the others are counted
+            unsigned running = 0;
+            for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.G;
+                 g += (int64_t)gridDim.x * blockDim.x) {
+                if (__ldcg(&a.gdone[g])) continue;
+                bool sg;
+                if (REFINE) {
+                    sg = __ldcg(&sm.mv[g]) == 0ULL || a.single_sweep;
+                } else {
+                    const double tm = a.g2m[g];
+                    const double sum = (double)ldm(&sm.dq[g]);
+                    // a graph without edges (2m = 0) has nothing to move
+                    sg = !(tm > 0) || (P::det ? 2.0 * sum / (tm * tm) : 2.0 * sum / tm) <= a.tau;
+                }
+                if (sg) {
+                    a.gdone[g] = 1;
+                    a.giters[g] = it + 1;
+                } else {
+                    running++;
+                }
+            }
+            running = warp_sum(running);
+            if (lane == 0 && running) atomicAdd(&a.gactive[it], running);
+            if (!(ok = grid_barrier(a.bar, a.err))) break;
+            stop = __ldcg(&a.gactive[it]) == 0u;
+        } else if (REFINE) {
+            stop = __ldcg(&sm.mv[0]) == 0ULL || a.single_sweep;
         } else {
             // sweep delta-modularity from the summed gains: 2 num / (2m)^2
             // (deterministic, reading S4) or 2 sum / 2m (asynchronous)
             const double tm = a.two_m_d;
-            const double sum = (double)ldm(&a.dq_arr[it]);
+            const double sum = (double)ldm(&sm.dq[0]);
             const double dq = P::det ? 2.0 * sum / (tm * tm) : 2.0 * sum / tm;
             stop = dq <= a.tau;
         }
         ++it;
         if (stop) break;
     }
+    if (batch) {
+        // graphs still running when the phase ends ran every sweep
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.G; g += (int64_t)gridDim.x * blockDim.x)
+            if (!__ldcg(&a.gdone[g])) a.giters[g] = it;
+    } else if (blockIdx.x == 0 && threadIdx.x == 0 && a.giters) {
+        a.giters[0] = it;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters_out = it;
     pc.flush(a.prof);
 }
 
 // ------------------------------------------- one (step, bin) per launch
-// local-moving gains into the sweep's delta-modularity sum; asynchronous
-// refinement joins into the move count
+// (one graph only) local-moving gains into the sweep's delta-modularity sum;
+// asynchronous refinement joins into the move count
+template <class P, class W> __device__ __forceinline__ Sums<P> scalar_sums(const SV<P, W> &a) {
+    Sums<P> sm;
+    sm.dq = a.dq_acc;
+    sm.mv = a.moved;
+    return sm;
+}
 template <class P, class W, bool REFINE>
-__device__ __forceinline__ void flush_gain(const SV<P, W> &a, typename P::acc local_gain) {
+__device__ __forceinline__ void flush_gain(const SV<P, W> &a, Sums<P> &sm) {
     using A = typename P::acc;
     if (P::det) return;
     if (REFINE) {
-        const unsigned long long c = warp_sum((unsigned long long)(local_gain + (A)0.5));
+        const unsigned long long c = warp_sum((unsigned long long)(sm.gain.v + (A)0.5));
         if ((threadIdx.x & 31) == 0 && c) atomicAdd(a.moved, c);
     } else {
-        const A s = warp_sum(local_gain);
+        const A s = warp_sum(sm.gain.v);
         if ((threadIdx.x & 31) == 0 && s != (A)0) atomic_add_acc(a.dq_acc, (typename P::tot)s);
     }
 }
 
 template <class P, class W, bool REFINE>
 __global__ void __launch_bounds__(256) k_eval_thread(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
-    using A = typename P::acc;
-    A local_gain = 0;
+    Sums<P> sm = scalar_sums(a);
     ProfCounts pc;
-    run_thread<P, W, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
-    flush_gain<P, W, REFINE>(a, local_gain);
+    run_thread<P, W, REFINE, false>(a, list, 0, count, a.cur_step, sm, pc);
+    flush_gain<P, W, REFINE>(a, sm);
     pc.flush(a.prof);
 }
 template <class P, class W, int T, bool REFINE>
 __global__ void __launch_bounds__(256) k_eval_tile(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
-    using A = typename P::acc;
-    A local_gain = 0;
+    Sums<P> sm = scalar_sums(a);
     ProfCounts pc;
-    run_tile<P, W, T, REFINE>(a, list, 0, count, a.cur_step, local_gain, pc);
-    flush_gain<P, W, REFINE>(a, local_gain);
+    run_tile<P, W, T, REFINE, false>(a, list, 0, count, a.cur_step, sm, pc);
+    flush_gain<P, W, REFINE>(a, sm);
     pc.flush(a.prof);
 }
 template <class P, class W, bool REFINE>
@@ -785,11 +883,11 @@ __global__ void __launch_bounds__(256) k_eval_warp(SV<P, W> a, const int32_t *__
     int32_t *skeys = table_keys<A>();
     A *svals = table_vals<A>();
     const int wib = threadIdx.x >> 5;
-    A local_gain = 0;
+    Sums<P> sm = scalar_sums(a);
     ProfCounts pc;
-    run_warp<P, W, REFINE>(a, list, 0, count, a.cur_step, skeys + wib * kWarpSlots, svals + wib * kWarpSlots,
-                           local_gain, pc);
-    flush_gain<P, W, REFINE>(a, local_gain);
+    run_warp<P, W, REFINE, false>(a, list, 0, count, a.cur_step, skeys + wib * kWarpSlots, svals + wib * kWarpSlots, sm,
+                           pc);
+    flush_gain<P, W, REFINE>(a, sm);
     pc.flush(a.prof);
 }
 template <class P, class W, bool REFINE, bool HUB>
@@ -797,31 +895,30 @@ __global__ void __launch_bounds__(256) k_eval_block(SV<P, W> a, const int32_t *_
     using A = typename P::acc;
     int32_t *skeys = table_keys<A>();
     A *svals = table_vals<A>();
-    A local_gain = 0;
+    Sums<P> sm = scalar_sums(a);
     ProfCounts pc;
     if (HUB) {
         const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
-        run_block<P, W, REFINE, true>(a, list, 0, count, a.cur_step, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
-                                      local_gain, pc);
+        run_block<P, W, REFINE, true, false>(a, list, 0, count, a.cur_step, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
+                                      sm, pc);
     } else {
-        run_block<P, W, REFINE, false>(a, list, 0, count, a.cur_step, skeys, svals, ceil_log2(kBlockSlots), local_gain,
-                                       pc);
+        run_block<P, W, REFINE, false, false>(a, list, 0, count, a.cur_step, skeys, svals, ceil_log2(kBlockSlots), sm, pc);
     }
-    flush_gain<P, W, REFINE>(a, local_gain);
+    flush_gain<P, W, REFINE>(a, sm);
     pc.flush(a.prof);
 }
 template <class P, class W>
 __global__ void __launch_bounds__(256) k_move_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
-    long long g = 0;
-    run_move_apply(a, list, 0, count, g);
-    g = warp_sum(g);
+    Sums<P> sm = scalar_sums(a);
+    run_move_apply<P, W, false>(a, list, 0, count, sm);
+    const long long g = warp_sum(sm.dgain.v);
     if ((threadIdx.x & 31) == 0 && g != 0) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), g);
 }
 template <class P, class W>
 __global__ void __launch_bounds__(256) k_refine_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
-    unsigned long long mv = 0;
-    run_refine_apply(a, list, 0, count, a.cur_step, mv);
-    mv = warp_sum(mv);
+    Sums<P> sm = scalar_sums(a);
+    run_refine_apply<P, W, false>(a, list, 0, count, a.cur_step, sm);
+    const unsigned long long mv = warp_sum(sm.moved.v);
     if ((threadIdx.x & 31) == 0 && mv) atomicAdd(a.moved, mv);
 }
 
@@ -876,24 +973,33 @@ int apply_grid(int64_t count) {
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
 
-template <class P, class W, bool REFINE>
-cudaError_t coop_typed(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s) {
+template <class P, class W, bool REFINE, bool B>
+cudaError_t coop_launch(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s) {
     SV<P, W> a = view<P, W>(c);
     constexpr size_t tb = table_bytes<typename P::acc>();
-    cudaError_t e = allow_table_smem(k_sweep_coop<P, W, REFINE>, tb);
+    cudaError_t e = allow_table_smem(k_sweep_coop<P, W, REFINE, B>, tb);
     if (e != cudaSuccess) return e;
     void *args[] = {&a, (void *)&list};
-    return cudaLaunchCooperativeKernel((const void *)k_sweep_coop<P, W, REFINE>, dim3(grid), dim3(kCoopThreads), args,
-                                       tb, s);
+    return cudaLaunchCooperativeKernel((const void *)k_sweep_coop<P, W, REFINE, B>, dim3(grid), dim3(kCoopThreads),
+                                       args, tb, s);
 }
-template <class P, class W, bool REFINE> int coop_blocks_typed() {
+template <class P, class W, bool REFINE>
+cudaError_t coop_typed(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s) {
+    return c.gid ? coop_launch<P, W, REFINE, true>(c, list, grid, s) : coop_launch<P, W, REFINE, false>(c, list, grid, s);
+}
+template <class P, class W, bool REFINE, bool B> int coop_blocks_b() {
     constexpr size_t tb = table_bytes<typename P::acc>();
-    if (allow_table_smem(k_sweep_coop<P, W, REFINE>, tb) != cudaSuccess) return 0;
+    if (allow_table_smem(k_sweep_coop<P, W, REFINE, B>, tb) != cudaSuccess) return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_coop<P, W, REFINE>, kCoopThreads, tb) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_coop<P, W, REFINE, B>, kCoopThreads, tb) !=
         cudaSuccess)
         return 0;
     return per_sm;
+}
+template <class P, class W, bool REFINE> int coop_blocks_typed() {
+    // both forms share the launch bounds; take the smaller occupancy
+    const int a = coop_blocks_b<P, W, REFINE, false>(), b = coop_blocks_b<P, W, REFINE, true>();
+    return a < b ? a : b;
 }
 
 }  // namespace

@@ -25,7 +25,7 @@ __global__ void k_fill_i32(int32_t *a, int32_t v, int64_t n) {
 __global__ void k_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = off[i + 1] - off[i];
-        if (d < 0 || d > 0x7fffffff) set_error(err, kErrBadIndex);
+        if (d < 0 || d > 0x7fffffff) set_error(err, 1);  // malformed offsets
         deg[i] = (int32_t)(d < 0 ? 0 : d);
     }
 }

@@ -72,6 +72,16 @@ struct SweepCtx {
     unsigned *bar = nullptr;      // grid barrier state (2 words, zero-initialised once)
     int *err = nullptr;
     unsigned long long *prof = nullptr;  // 8 work counters of this launch's class, or null
+    // A batch of G independent graphs swept as one (a disjoint union): every
+    // vertex uses its own graph's 2m, and every graph converges on its own.
+    // gid == null means one graph (index 0) and the scalars above.
+    const int32_t *gid = nullptr;  // graph of every vertex (sweep space)
+    const void *gks = nullptr;     // per-graph key scale (acc type): 2m (det) or 1/2m (async)
+    const double *g2m = nullptr;   // per-graph 2m, for the convergence test
+    int32_t *gdone = nullptr;      // per-graph "phase converged" flags (1 = skip its vertices)
+    int32_t *giters = nullptr;     // per-graph sweeps executed in the phase
+    unsigned *gactive = nullptr;   // per sweep: graphs still running after it (max_it, zeroed)
+    int32_t G = 1;                 // dq_arr and moved_arr hold max_it x G sums
 };
 
 // Work counters (kernels add to them when profiling): sweep kernels
@@ -138,13 +148,69 @@ struct SchedWork {
     int32_t *cnt, *layer;  // n each
     int32_t *settled;      // L+1: vertices placed in each layer
 };
+// (gid, vseg: a batch of graphs, priorities drawn at indices inside each graph)
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
-                            int32_t *step, cudaStream_t s);
+                            int32_t *step, cudaStream_t s, const int32_t *gid = nullptr,
+                            const int64_t *vseg = nullptr);
 // key[i] = step*kNumBins + bin (step-major: one list per step and bin), or
 // bin*nsteps + step (bin-major: one step-ordered list per bin); vertices
 // without edges get key nsteps*kNumBins (a trailing bucket)
 cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
                                  int32_t *key, cudaStream_t s);
+
+// ---- batches of graphs (k_batch.cu). vseg has G+1 vertex offsets (graph g
+// owns vertices [vseg[g], vseg[g+1])); gid maps a vertex to its graph.
+enum : int32_t { kGraphActive = 0, kGraphFinishing = 1, kGraphFinished = 2 };
+// gid[v] = the g with vseg[g] <= v < vseg[g+1] (binary search)
+cudaError_t launch_graph_ids(const int64_t *vseg, int32_t G, int64_t n, int32_t *gid, cudaStream_t s);
+// local row indices to global ids: idx[e] += vseg[gid[v]] for the edges of v
+// (m entries in all); *err = 1 if a local index is outside [0, n_g) or a row
+// lies outside [0, m)
+cudaError_t launch_globalize_indices(const int64_t *vseg, const int32_t *gid, int64_t n, const int64_t *off,
+                                     int64_t m, int32_t *idx, int *err, cudaStream_t s);
+// out[gid[i]] += x[i] (acc type of K: float -> double sums, int64 -> int64)
+cudaError_t launch_graph_sums(const void *K, bool det, const int32_t *gid, int64_t n, void *out, cudaStream_t s);
+// per-graph key scale and 2m from the per-graph sums of K
+cudaError_t launch_graph_scales(const void *sums, bool det, int32_t G, void *gks, double *g2m, cudaStream_t s);
+// phase start: gdone[g] = (state[g] != active); giters[g] = 0
+cudaError_t launch_phase_init(const int32_t *state, int32_t G, int32_t *gdone, int32_t *giters, cudaStream_t s);
+// stop tests of Algorithm 1 per graph (readings R4, R5', R12): from the scans
+// pos (refined labels) and pos2 (bound labels), li and the aggregation
+// tolerance; active graphs that stop become finishing; keep[g] = refined
+// communities of the graphs that go on (0 otherwise); passes[g]++ for active graphs
+cudaError_t launch_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
+                              const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
+                              int32_t *passes, cudaStream_t s);
+// dense ids of the next graph: Cd[i] = vseg2[g] + pos[C[i]] - pos[vseg[g]]
+// for graphs that go on, -1 for graphs that stop
+cudaError_t launch_renumber_batch(const int32_t *C, const int64_t *pos, const int32_t *gid, const int64_t *vseg,
+                                  const int64_t *vseg2, const int32_t *state, int32_t *Cd, int64_t n, cudaStream_t s);
+// dendrogram: active graphs C0[v] = Cd[C0[v]]; finishing graphs end on their
+// refined label, stored as vseg0[g] + (Cp[C0[v]] - vseg[g]) (an id in the
+// input graph's range of g)
+cudaError_t launch_lookup_batch(int32_t *C0, const int32_t *gid0, const int64_t *vseg0, const int64_t *vseg,
+                                const int32_t *state, const int32_t *Cd, const int32_t *Cp, int64_t n0,
+                                cudaStream_t s);
+// graphs still active when the pass loop ends: C0[v] = vseg0[g] + (C0[v] - vseg[g])
+cudaError_t launch_finalize_batch(int32_t *C0, const int32_t *gid0, const int64_t *vseg0, const int64_t *vseg,
+                                  const int32_t *state, int64_t n0, cudaStream_t s);
+// finishing -> finished
+cudaError_t launch_commit_states(int32_t *state, int32_t G, cudaStream_t s);
+// out[g] = pos[vseg[g+1]] - pos[vseg[g]]
+cudaError_t launch_graph_counts(const int64_t *pos, const int64_t *vseg, int32_t G, int64_t *out, cudaStream_t s);
+// graph of every super-vertex: gid2[Cd[i]] = gid[i] (Cd >= 0)
+cudaError_t launch_next_gid(const int32_t *Cd, const int32_t *gid, int64_t n, int32_t *gid2, cudaStream_t s);
+// canonical labels inside each graph: out[v] = rank[minv[C0[v]]] - rank[vseg0[gid0[v]]]
+cudaError_t launch_canonical_batch(const int32_t *C0, const int32_t *minv, const int64_t *rank, const int32_t *gid0,
+                                   const int64_t *vseg0, int64_t n0, int32_t *out, cudaStream_t s);
+// Eq. 1 per graph on the input batch with labels local to each graph:
+// gsum[3g+0] += intra weight, gsum[3g+1] += 2m, sigtot[vseg0[g] + label] += K_i,
+// then gsum[3g+2] += sum of squares over the graph's range; *bad counts labels
+// outside [0, n_g); q[g] from the sums
+cudaError_t launch_modularity_batch(int64_t n0, const int64_t *off, const int32_t *idx, const float *w,
+                                    const int32_t *C, const int32_t *gid0, const int64_t *vseg0, int32_t G,
+                                    double gamma, double *sigtot, double *gsum, double *bad, double *q,
+                                    cudaStream_t s);
 
 // ---- pass bookkeeping (k_pass.cu)
 // Sigma[c] += K[i], size[c] += 1 over C (acc type)
@@ -160,14 +226,14 @@ cudaError_t launch_gather_map(const int32_t *map_pos, const int32_t *in, int32_t
 cudaError_t launch_renumber(const int32_t *C, const int64_t *pos, int32_t *Cd, int64_t n, cudaStream_t s);
 // C0[v] = map[C0[v]] for the dendrogram
 cudaError_t launch_lookup(int32_t *C0, const int32_t *map, int64_t n0, cudaStream_t s);
-// community-vertex CSR: cnt[Cd[i]]++, tdeg[Cd[i]] += deg[i]
+// community-vertex CSR: cnt[Cd[i]]++, tdeg[Cd[i]] += deg[i] (Cd < 0: skipped)
 cudaError_t launch_comm_counts(const int32_t *Cd, const int32_t *deg, int64_t n, int64_t *cnt, int64_t *tdeg,
                                cudaStream_t s);
 cudaError_t launch_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, int32_t *cursor, int32_t *members,
                              cudaStream_t s);
 // bins of communities by total degree
 cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key, cudaStream_t s);
-// move-based labels: bnd[Cd[i]] = CB[i]; rep[b] = min s; label[s] = rep[bnd[s]]
+// move-based labels: bnd[Cd[i]] = CB[i]; rep[b] = min s; label[s] = rep[bnd[s]] (Cd < 0: skipped)
 cudaError_t launch_bound_labels(const int32_t *Cd, const int32_t *CB, int64_t n, int64_t ncomm, int32_t *bnd,
                                 int32_t *rep, int32_t *label, cudaStream_t s);
 // canonical labels: rank of the smallest vertex of each community

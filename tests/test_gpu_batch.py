@@ -1,0 +1,164 @@
+"""GPU tests of the batched form: many graphs packed as one segmented CSR and
+solved by one set of launches per pass (leiden_batch_create/run).
+
+Every graph of a batch must come out as it does alone. Deterministic mode:
+membership, pass count, community count and modularity bit-exact against
+single-graph runs of the same library, and membership against the oracle's
+SYNC mode. Asynchronous mode: every community connected, reported modularity
+within 1e-9 of the recomputation, and modularity against the oracle's SEQ
+mode within 0.005 on the batch mean. A single small graph may end in
+another local optimum than SEQ's sequential order finds (on the sparse SBM
+graphs here the deterministic schedule itself lands up to 0.008 below SEQ on
+one graph and 0.002 above on the mean), so each graph is held to a looser
+floor of 0.04; the same holds for a graph alone and in the batch.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_2312_13936_gb300 as lg
+from tests._gpu import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+Q_TOL_ASYNC = 0.005        # on the mean over a batch's graphs
+Q_TOL_ASYNC_GRAPH = 0.04   # on each graph
+Q_REL_REPORT = 1e-9
+
+
+def mixed_graphs():
+    """SBM graphs of uneven sizes plus the degenerate cases a batch must carry:
+    an empty graph, an edgeless graph, a single vertex with a self-loop, a
+    ring of cliques and a weighted road lattice."""
+    b = gen.sbm_batch(20, seed=11, nmin=30, nmax=3000)
+    graphs = [b.graph(g) for g in range(b.num_graphs)]
+    graphs.insert(3, gen.from_edges(0, [], []))
+    graphs.insert(7, gen.from_edges(5, [], []))
+    graphs.insert(9, gen.from_edges(1, [0], [0], [3.0]))
+    graphs.append(gen.ring_of_cliques(5, 6))
+    graphs.append(gen.road(30))
+    graphs.append(gen.from_edges(0, [], []))
+    return graphs
+
+
+def run_batch(graphs, mode, **kw):
+    vseg, off, idx, w = lg.pack_batch(graphs)
+    h = lg.LeidenBatch(vseg, off, idx, w, validate=True)
+    try:
+        memb, q, st = h.run(mode=mode, **kw)
+        passes, comm = h.info()
+        return vseg, memb.cpu().numpy(), q, st, passes, comm
+    finally:
+        h.close()
+
+
+def test_batch_deterministic_equals_single_runs():
+    graphs = mixed_graphs()
+    vseg, memb, q, st, passes, comm = run_batch(graphs, lg.LEIDEN_DETERMINISTIC)
+    assert len(q) == len(graphs)
+    for g, G in enumerate(graphs):
+        mb = memb[vseg[g]:vseg[g + 1]]
+        ms, qs, sts, _ = run_gpu(G, lg.LEIDEN_DETERMINISTIC)
+        assert np.array_equal(mb, ms), g
+        assert abs(q[g] - qs) <= 1e-12 * max(1.0, abs(qs)), (g, q[g], qs)
+        if G.n > 0:
+            assert passes[g] == sts.passes, (g, passes[g], sts.passes)
+            assert comm[g] == sts.communities
+        else:
+            assert comm[g] == 0
+    assert st.communities == comm.sum()
+
+
+def test_batch_deterministic_matches_oracle():
+    graphs = mixed_graphs()
+    vseg, memb, q, _, _, _ = run_batch(graphs, lg.LEIDEN_DETERMINISTIC)
+    for g in (0, 2, 5, 7, 9, len(graphs) - 3, len(graphs) - 2):
+        ref = oracle.leiden(graphs[g], mode=oracle.SYNC)
+        assert np.array_equal(memb[vseg[g]:vseg[g + 1]], ref.membership), g
+        assert abs(q[g] - ref.modularity) <= Q_REL_REPORT * max(1.0, abs(ref.modularity))
+
+
+def test_batch_deterministic_schedule_and_limits():
+    b = gen.sbm_batch(8, seed=13, nmin=200, nmax=2000)
+    graphs = [b.graph(g) for g in range(b.num_graphs)]
+    for kw in ({"schedule_layers": 4, "schedule_buckets": 3, "seed": 9}, {"max_passes": 2},
+               {"max_iterations": 2}, {"flags": lg.FLAG_REFINE_SINGLE_SWEEP}):
+        vseg, memb, q, _, _, _ = run_batch(graphs, lg.LEIDEN_DETERMINISTIC, **kw)
+        for g, G in enumerate(graphs):
+            ms = run_gpu(G, lg.LEIDEN_DETERMINISTIC, **kw)[0]
+            assert np.array_equal(memb[vseg[g]:vseg[g + 1]], ms), (kw, g)
+
+
+@pytest.mark.parametrize("flags", [0, lg.FLAG_NO_RELABEL])
+def test_batch_async_quality(flags):
+    # about 100k vertices in all: the batch is swept relabelled unless asked not to
+    b = gen.sbm_batch(40, seed=12, nmin=500, nmax=8000)
+    graphs = [b.graph(g) for g in range(b.num_graphs)]
+    vseg, memb, q, st, passes, comm = run_batch(graphs, lg.LEIDEN_ASYNC, flags=flags)
+    seq_q = np.array([oracle.leiden(G, mode=oracle.SEQ).modularity for G in graphs])
+    assert q.mean() >= seq_q.mean() - Q_TOL_ASYNC, (q.mean(), seq_q.mean())
+    for g, G in enumerate(graphs):
+        mb = memb[vseg[g]:vseg[g + 1]]
+        assert q[g] >= seq_q[g] - Q_TOL_ASYNC_GRAPH, (g, q[g], seq_q[g])
+        assert oracle.disconnected(G, mb)[0] == 0, g
+        q_re = oracle.modularity(G, mb)
+        assert abs(q[g] - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re)), g
+        first = np.unique(mb, return_index=True)[1]
+        assert np.array_equal(np.sort(first), first)
+        assert mb.max() + 1 == comm[g]
+
+
+def test_batch_async_same_alone_and_in_batch():
+    graphs = mixed_graphs()
+    vseg, memb, q, _, _, _ = run_batch(graphs, lg.LEIDEN_ASYNC)
+    alone = np.array([run_gpu(G, lg.LEIDEN_ASYNC)[1] for G in graphs])
+    assert abs(q.mean() - alone.mean()) <= Q_TOL_ASYNC, (q.mean(), alone.mean())
+    for g, G in enumerate(graphs):
+        assert abs(q[g] - alone[g]) <= Q_TOL_ASYNC_GRAPH, (g, q[g], alone[g])
+        assert oracle.disconnected(G, memb[vseg[g]:vseg[g + 1]])[0] == 0
+
+
+def test_batch_of_one_equals_single_run():
+    G = gen.road(200)
+    vseg, memb, q, st, passes, comm = run_batch([G], lg.LEIDEN_DETERMINISTIC)
+    ms, qs, sts, _ = run_gpu(G, lg.LEIDEN_DETERMINISTIC)
+    assert np.array_equal(memb, ms)
+    assert q[0] == qs and passes[0] == sts.passes and comm[0] == sts.communities
+
+
+def test_batch_invalid_inputs():
+    graphs = [gen.ring_of_cliques(4, 3), gen.ring_of_cliques(3, 4)]
+    vseg, off, idx, w = lg.pack_batch(graphs)
+    # a local index outside its graph
+    bad = idx.copy()
+    bad[-1] = graphs[1].n
+    with pytest.raises(lg.LeidenError) as e:
+        lg.LeidenBatch(vseg, off, bad, w)
+    assert e.value.status == -1
+    # decreasing segments
+    with pytest.raises(lg.LeidenError) as e:
+        lg.LeidenBatch(np.array([0, 12, 10, 24]), off, idx, w)
+    assert e.value.status == -1
+    h = lg.LeidenBatch(vseg, off, idx, w)
+    try:
+        # a batch is not a single graph
+        import torch
+        out = torch.empty(h.n, dtype=torch.int32, device="cuda")
+        with pytest.raises(lg.LeidenError) as e:
+            lg.leiden_run(h.handle, lg.leiden_params_default(), lg._ptr(out), lg.LEIDEN_DEVICE)
+        assert e.value.status == -1
+        # trace is a single-graph feature
+        with pytest.raises(lg.LeidenError) as e:
+            h.run(flags=lg.FLAG_TRACE)
+        assert e.value.status == -6
+    finally:
+        h.close()
+    # deterministic mode needs integer weights
+    h = lg.LeidenBatch(vseg, off, idx, w * 0.5)
+    try:
+        with pytest.raises(lg.LeidenError) as e:
+            h.run(mode=lg.LEIDEN_DETERMINISTIC)
+        assert e.value.status == -6
+    finally:
+        h.close()
