@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--side", type=int, default=5000, help="road lattice side")
     ap.add_argument("--rmat-scale", type=int, default=25)
     ap.add_argument("--mode", default="async", choices=["async", "det"])
-    ap.add_argument("--no-relabel", action="store_true", help="sweep in the graph's own vertex order")
+    ap.add_argument("--relabel", action="store_true", help="sweep on a copy relabelled by schedule step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-side", type=int, default=3000, help="road side of the CPU-baseline sample")
@@ -287,7 +287,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     g, wname = workload(args)
     mode = lg.LEIDEN_ASYNC if args.mode == "async" else lg.LEIDEN_DETERMINISTIC
-    base_flags = lg.FLAG_NO_RELABEL if args.no_relabel else 0
+    base_flags = lg.FLAG_RELABEL if args.relabel else 0
     dev = torch.device("cuda", local)
     off = torch.as_tensor(g.offsets).to(dev)
     idx = torch.as_tensor(g.indices).to(dev)

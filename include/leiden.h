@@ -66,8 +66,10 @@ enum {
     LEIDEN_FLAG_PROFILE = 8u,             /* time every sweep/aggregation launch (leiden_profile_get) */
     LEIDEN_FLAG_STEP_LAUNCHES = 16u,      /* one launch per schedule step and degree bin instead of one
                                              persistent launch per sweep (same results; for testing) */
-    LEIDEN_FLAG_NO_RELABEL = 32u          /* asynchronous mode: sweep large graphs in their own vertex order
-                                             instead of a copy relabelled by schedule step (for comparison) */
+    LEIDEN_FLAG_RELABEL = 32u             /* asynchronous mode: sweep graphs of >= 65,536 vertices on a copy
+                                             relabelled so that every schedule step and degree bin is a
+                                             contiguous id range (measured slower than the graph's own
+                                             vertex order; kept for comparison) */
 };
 
 typedef struct {

@@ -608,13 +608,13 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         if (lp == 0) CK(launch_iota(q.Cp, n, s));
         else CK(cudaMemcpyAsync(q.Cp, q.label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
         if (trace) q.record(lp, 1, q.Cp, n);
-        // Sweep space. The asynchronous mode relabels large graphs so that
-        // every (step, bin) list is a contiguous id range, ascending in the
-        // ids of G' (consecutive threads then read consecutive vertices and
-        // nearby neighbours); the sweeps run on the relabelled copy and
-        // their labels are mapped back afterwards. Vertex p of the copy is
-        // vertex perm[p] = list[p] of G'.
-        const bool relabel = !det && !(prm.flags & LEIDEN_FLAG_NO_RELABEL) && n >= kRelabelMinVertices;
+        // Sweep space. On request (LEIDEN_FLAG_RELABEL) the asynchronous
+        // mode relabels large graphs so that every (step, bin) list is a
+        // contiguous id range, ascending in the ids of G'; the sweeps run on
+        // the relabelled copy and their labels are mapped back afterwards.
+        // Vertex p of the copy is vertex perm[p] = list[p] of G'. The copy
+        // costs about what it saves in the sweeps, so it is off by default.
+        const bool relabel = !det && (prm.flags & LEIDEN_FLAG_RELABEL) && n >= kRelabelMinVertices;
         GraphView sG = G;
         int32_t *sC = q.Cp, *sCB = q.CB, *sStep = q.step;
         const int32_t *sList = q.list;

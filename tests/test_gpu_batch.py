@@ -90,9 +90,9 @@ def test_batch_deterministic_schedule_and_limits():
             assert np.array_equal(memb[vseg[g]:vseg[g + 1]], ms), (kw, g)
 
 
-@pytest.mark.parametrize("flags", [0, lg.FLAG_NO_RELABEL])
+@pytest.mark.parametrize("flags", [0, lg.FLAG_RELABEL])
 def test_batch_async_quality(flags):
-    # about 100k vertices in all: the batch is swept relabelled unless asked not to
+    # about 100k vertices in all: large enough for the relabelled sweep
     b = gen.sbm_batch(40, seed=12, nmin=500, nmax=8000)
     graphs = [b.graph(g) for g in range(b.num_graphs)]
     vseg, memb, q, st, passes, comm = run_batch(graphs, lg.LEIDEN_ASYNC, flags=flags)

@@ -116,7 +116,7 @@ ASYNC_GRAPHS = {
 }
 
 
-@pytest.mark.parametrize("flags", [0, lg.FLAG_STEP_LAUNCHES, lg.FLAG_NO_RELABEL])
+@pytest.mark.parametrize("flags", [0, lg.FLAG_STEP_LAUNCHES, lg.FLAG_RELABEL])
 @pytest.mark.parametrize("name", sorted(ASYNC_GRAPHS))
 def test_async_quality_and_connectivity(name, flags):
     g = ASYNC_GRAPHS[name]()
