@@ -71,6 +71,22 @@ int ceil_log2_h(int64_t x) {
 
 }  // namespace
 
+// State of one run (or one serving step) that the passes share.
+struct Run {
+    const leiden_params *prm = nullptr;
+    bool det = false, trace = false, profile = false, batch = false;
+    int32_t L = 0, B = 0, nsteps = 0, nkeys = 0, NG = 1;
+    leiden_stats st{};
+    std::vector<std::pair<cudaEvent_t, int>> marks;  // phase boundary events (phase id of the span that starts)
+    GraphView G;                  // current graph G'
+    int64_t Gcap = 0;             // entry capacity of G' (holey after aggregation)
+    int cur_agg = 1;              // the next aggregation writes agg[cur_agg ^ 1]
+    const int32_t *cur_gid = nullptr;  // graph of every vertex of G' (batches)
+    double tau = 0;
+    int passes = 0;
+    bool no_edges = false;
+};
+
 struct Handle::Impl {
     int64_t n0 = 0, m0 = 0;
     cudaStream_t s = nullptr;
@@ -139,6 +155,26 @@ struct Handle::Impl {
     std::vector<int32_t> hpasses;          // per graph, after a run
     std::vector<int64_t> hcomm;
 
+    leiden_status pass(Run &r, int32_t lp, bool &stop);
+    // brackets one profiled launch of class cls with events on the run's stream
+    unsigned long long *prof_begin(Run &r, int cls) {
+        if (!r.profile) return nullptr;
+        prof_spans.push_back({cls, ev_used});
+        cudaEventRecord(next_event(), s);
+        prof_launches[cls]++;
+        return prof_cnt + (size_t)cls * kProfCounters;
+    }
+    void prof_end(Run &r) {
+        if (r.profile) cudaEventRecord(next_event(), s);
+    }
+    // phase boundary for the per-phase times of the statistics
+    leiden_status mark(Run &r, int phase) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        CK(cudaEventRecord(e, s));
+        r.marks.push_back({e, phase});
+        return LEIDEN_OK;
+    }
     cudaEvent_t next_event() {
         if (ev_used == ev_pool.size()) {
             cudaEvent_t e;
@@ -429,6 +465,428 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     return LEIDEN_OK;
 }
 
+// One pass of Algorithm 1 over the current graph G' (every graph of a
+// batch at once): vertex weights, schedule, local-moving, refinement, the
+// stop tests, renumbering, dendrogram lookup and, for the graphs that go on,
+// aggregation and move-based labels. Sets stop when no graph goes on.
+leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
+    Impl &q = *this;
+    cudaStream_t s = q.s;
+    const leiden_params &prm = *r.prm;
+    const bool det = r.det, trace = r.trace, batch = r.batch;
+    const int32_t L = r.L, B = r.B, nsteps = r.nsteps, nkeys = r.nkeys, NG = r.NG;
+    const int64_t n0 = q.n0;
+    const int tile_blocks = q.sm * 8, big_blocks = q.sm * 2;
+    GraphView &G = r.G;
+    int64_t &Gcap = r.Gcap;
+    int &cur_agg = r.cur_agg;
+    const int32_t *&cur_gid = r.cur_gid;
+    double &tau = r.tau;
+    int &passes = r.passes;
+    bool &no_edges = r.no_edges;
+    leiden_stats &st = r.st;
+    const size_t accsz = 8;
+    auto mark = [&](int phase) { return q.mark(r, phase); };
+    auto prof_begin = [&](int cls) { return q.prof_begin(r, cls); };
+    auto prof_end = [&]() { q.prof_end(r); };
+    stop = false;
+
+    const int64_t n = G.n;
+    if (n == 0) {
+        stop = true;
+        return LEIDEN_OK;
+    }
+    ST(mark(3));
+    // vertexWeights(G') and 2m (of every graph of a batch)
+    CK(cudaMemsetAsync(&q.dsc->two_m_f, 0, sizeof(double) + sizeof(long long), s));
+    CK(launch_vertex_weights(G, det, q.K, det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, s));
+    if (batch) {
+        CK(cudaMemsetAsync(q.gsumk, 0, sizeof(long long) * NG, s));
+        CK(launch_graph_sums(q.K, det, cur_gid, n, q.gsumk, s));
+        CK(launch_graph_scales(q.gsumk, det, NG, q.gks, q.g2m, s));
+        q.launches += 2;
+    } else {
+        CK(launch_graph_scales(det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, det, 1, q.gks, q.g2m, s));
+        q.launches += 1;
+    }
+    q.launches += 1;
+    // schedule and (step, bin) lists
+    SchedWork sw{q.scnt, q.slayer, q.sfcount};
+    CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s, cur_gid, batch ? q.vseg : nullptr));
+    q.launches += L > 1 ? L : 2;
+    // one vertex list per (schedule step, degree bin), step-major
+    CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
+    CK(launch_partition(q.key, n, nkeys + 1, q.key_off, q.list, q.part_tmp, s));  // + edgeless bucket
+    CK(launch_max_i32(G.deg, n, &q.dsc->maxdeg, s));
+    q.launches += 7;
+    q.hkey_off.assign(nkeys + 2, 0);
+    CK(cudaMemcpyAsync(q.hkey_off.data(), q.key_off, sizeof(int64_t) * (nkeys + 2), cudaMemcpyDeviceToHost, s));
+    ST(q.sync_scalars());
+    const double two_m_f = q.hsc->two_m_f;
+    const long long two_m_i = q.hsc->two_m_i;
+    if (!batch && (det ? (two_m_i == 0) : !(two_m_f > 0))) {  // reading R12: no edges
+        CK(launch_iota(q.Cp, n, s));
+        no_edges = true;
+        passes++;
+        stop = true;
+        return LEIDEN_OK;
+    }
+    passes++;
+    // C' and Sigma' at the start of local-moving (reading R3)
+    if (lp == 0) CK(launch_iota(q.Cp, n, s));
+    else CK(cudaMemcpyAsync(q.Cp, q.label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    if (trace) q.record(lp, 1, q.Cp, n);
+    // Sweep space. On request (LEIDEN_FLAG_RELABEL) the asynchronous
+    // mode relabels large graphs so that every (step, bin) list is a
+    // contiguous id range, ascending in the ids of G'; the sweeps run on
+    // the relabelled copy and their labels are mapped back afterwards.
+    // Vertex p of the copy is vertex perm[p] = list[p] of G'. The copy
+    // costs about what it saves in the sweeps, so it is off by default.
+    const bool relabel = !det && (prm.flags & LEIDEN_FLAG_RELABEL) && n >= kRelabelMinVertices;
+    GraphView sG = G;
+    int32_t *sC = q.Cp, *sCB = q.CB, *sStep = q.step;
+    const int32_t *sList = q.list;
+    void *sK = q.K;
+    if (relabel) {
+        ST(q.ensure_relabel(Gcap));
+        const int32_t *perm = q.list;
+        CK(launch_inverse(perm, n, q.rinv, s));
+        CK(launch_gather_i32(G.deg, perm, n, q.rdeg, s));
+        CK(launch_exclusive_scan_i32(q.rdeg, q.roff, n, q.scan_tmp, s));
+        CK(launch_permute_rows(G, perm, q.rinv, q.roff, q.ridx, q.rw, s));
+        CK(launch_gather_i32(static_cast<const int32_t *>(q.K), perm, n, static_cast<int32_t *>(q.rK), s));  // fp32 K
+        CK(launch_gather_i32(q.step, perm, n, q.rstep, s));
+        CK(launch_labels_to_new(q.Cp, perm, q.rinv, n, q.rC, s));
+        q.launches += 9;
+        if (batch) {
+            CK(launch_gather_i32(cur_gid, perm, n, q.rgid, s));
+            q.launches++;
+        }
+        sG.off = q.roff;
+        sG.deg = q.rdeg;
+        sG.idx = q.ridx;
+        sG.w = q.rw;
+        sC = q.rC;
+        sCB = q.rCB;
+        sStep = q.rstep;
+        sList = q.iota_list;
+        sK = q.rK;
+    }
+    CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
+    CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
+    CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));
+    q.launches += 1;
+    // hub tables for bin 7
+    int hub_bits = 0, hub_regions = 0;
+    {
+        const int maxdeg = q.hsc->maxdeg;
+        if (maxdeg > kBlockMaxDeg) {
+            hub_bits = ceil_log2_h(2 * (int64_t)maxdeg);
+            const size_t per = ((size_t)1 << hub_bits) * 12;
+            hub_regions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
+            ST(q.ensure_hub(hub_bits, hub_regions, det));
+        }
+    }
+    SweepCtx sc;
+    sc.g = sG;
+    sc.det = det;
+    sc.C = sC;
+    sc.CB = sCB;
+    sc.K = sK;
+    sc.Sig = q.Sig;
+    sc.size = q.size;
+    sc.unproc = q.unproc;
+    sc.prop = q.prop;
+    sc.gain = q.gain;
+    sc.step = sStep;
+    sc.two_m_f = two_m_f;
+    sc.two_m_i = two_m_i;
+    sc.gamma = prm.resolution;
+    sc.cap_step = L - 1;
+    sc.dq_acc = det ? (void *)&q.dsc->dq_i : (void *)&q.dsc->dq_f;
+    sc.moved = &q.dsc->moved;
+    sc.hub_keys = q.hub_keys;
+    sc.hub_vals = q.hub_vals;
+    sc.hub_bits = hub_bits;
+    sc.err = &q.dsc->err;
+    const std::vector<int64_t> &ko = q.hkey_off;
+    sc.nsteps = nsteps;
+    sc.key_off = q.key_off;
+    sc.bar = q.bar;
+    sc.hub_regions = hub_regions;
+    sc.gid = batch ? (relabel ? q.rgid : cur_gid) : nullptr;
+    sc.gks = q.gks;
+    sc.g2m = q.g2m;
+    sc.gdone = q.gdone;
+    sc.gactive = q.gactive;
+    sc.G = NG;
+    const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
+    // one sweep as per-(step, bin) launches (fallback and test path)
+    auto run_steps = [&](bool refine) -> leiden_status {
+        sc.refine = refine;
+        for (int32_t k = 0; k < nsteps; ++k) {
+            sc.cur_step = k;
+            const int64_t a0 = ko[k * kNumBins], a1 = ko[(k + 1) * kNumBins];
+            if (a1 == a0) continue;
+            for (int b = 1; b < kNumBins; ++b) {
+                const int64_t lo = ko[k * kNumBins + b], hi = ko[k * kNumBins + b + 1];
+                if (hi == lo) continue;
+                const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : hub_regions);
+                sc.prof = prof_begin((refine ? 8 : 0) + b);
+                CK(launch_sweep_eval(sc, b, sList + lo, hi - lo, mb, s));
+                prof_end();
+                q.launches++;
+            }
+            // apply phase: deterministic mode, and refinement proposals where
+            // neighbours may share a step (asynchronous refinement applies
+            // its joins at once below the capped step)
+            if (det || (refine && k >= sc.cap_step)) {
+                if (refine) CK(launch_refine_apply(sc, sList + a0, a1 - a0, s));
+                else CK(launch_move_apply(sc, sList + a0, a1 - a0, s));
+                q.launches++;
+            }
+        }
+        return LEIDEN_OK;
+    };
+    // One phase (Algorithm 2 or 3): sweeps until convergence. Normally one
+    // persistent cooperative launch that tests convergence on the device;
+    // otherwise one host-driven sweep at a time. Returns the sweeps run.
+    auto run_phase = [&](bool refine, int *iters, int32_t *giters) -> leiden_status {
+        sc.refine = refine;
+        const bool single = refine && (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP);
+        const int per_sm = step_launches ? 0 : sweep_coop_blocks_per_sm(det, sG.w_int, refine);
+        CK(launch_phase_init(q.gstate, NG, q.gdone, giters, s));
+        sc.giters = giters;
+        if (batch && per_sm <= 0) {
+            set_last_error("a batch of graphs needs the cooperative sweep kernel");
+            return LEIDEN_ERR_UNSUPPORTED;
+        }
+        if (per_sm > 0) {
+            // enough blocks for the graph (about 2048 vertices each), so
+            // small graphs do not pay a full-GPU barrier per step
+            int grid = per_sm * q.sm;
+            const int64_t want = (n + 2047) / 2048;
+            if (want < grid) grid = (int)(want < 1 ? 1 : want);
+            sc.hub_regions = hub_regions > grid ? grid : hub_regions;
+            sc.max_it = prm.max_iterations;
+            sc.single_sweep = single ? 1 : 0;
+            sc.tau = tau;
+            sc.dq_arr = q.phase_dq;
+            sc.moved_arr = q.phase_moved;
+            sc.iters_out = &q.dsc->iters;
+            CK(cudaMemsetAsync(q.phase_dq, 0, sizeof(long long) * prm.max_iterations * NG, s));
+            CK(cudaMemsetAsync(q.phase_moved, 0, sizeof(unsigned long long) * prm.max_iterations * NG, s));
+            CK(cudaMemsetAsync(q.gactive, 0, sizeof(unsigned) * prm.max_iterations, s));
+            sc.prof = prof_begin(refine ? 8 : 0);
+            CK(launch_sweep_coop(sc, sList, grid, s));
+            prof_end();
+            q.launches++;
+            ST(q.sync_scalars());
+            *iters = q.hsc->iters;
+            sc.hub_regions = hub_regions;
+            return LEIDEN_OK;
+        }
+        int k = 0;
+        for (int32_t it = 0; it < prm.max_iterations; ++it) {
+            k++;
+            CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double) + sizeof(long long), s));
+            CK(cudaMemsetAsync(&q.dsc->moved, 0, sizeof(unsigned long long), s));
+            ST(run_steps(refine));
+            ST(q.sync_scalars());
+            if (refine) {
+                if (q.hsc->moved == 0 || single) break;
+            } else {
+                const double dq = det ? 2.0 * (double)q.hsc->dq_i / ((double)two_m_i * (double)two_m_i)
+                                      : 2.0 * q.hsc->dq_f / two_m_f;
+                if (dq <= tau) break;  // locally converged
+            }
+        }
+        *iters = k;
+        CK(launch_fill_i32(giters, k, 1, s));
+        return LEIDEN_OK;
+    };
+    // ---- local-moving phase (Algorithm 2)
+    ST(mark(0));
+    CK(cudaMemsetAsync(q.unproc, 1, (size_t)n, s));  // mark all vertices unprocessed
+    int li = 0;
+    ST(run_phase(false, &li, q.gli));
+    st.move_iterations += li;
+    if (trace) {
+        if (relabel) {
+            CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cd, s));
+            q.record(lp, 2, q.Cd, n);
+        } else {
+            q.record(lp, 2, q.Cp, n);
+        }
+    }
+    // ---- refinement phase (Algorithm 3)
+    ST(mark(1));
+    CK(cudaMemcpyAsync(sCB, sC, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    CK(launch_iota(sC, n, s));
+    CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
+    CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
+    CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));  // Sigma' <- K', one member each
+    q.launches += 2;
+    int lj = 0;
+    ST(run_phase(true, &lj, q.glj));
+    if (relabel) {  // back to the ids of G'
+        CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cp, s));
+        CK(launch_labels_to_old(sCB, q.list, q.rinv, n, q.CB, s));
+        q.launches += 2;
+    }
+    st.refine_iterations += lj;
+    if (trace) q.record(lp, 3, q.Cp, n);
+    // ---- stop tests (readings R4, R5')
+    ST(mark(3));
+    // non-empty refined communities: the labels present in C' (ids of G')
+    CK(launch_fill_i32(q.flag, 0, n, s));
+    CK(launch_mark_labels(q.Cp, n, q.flag, s));
+    CK(launch_exclusive_scan_i32(q.flag, q.pos, n, q.scan_tmp, s));
+    CK(launch_fill_i32(q.rep, 0, n, s));
+    CK(launch_mark_labels(q.CB, n, q.rep, s));
+    CK(launch_exclusive_scan_i32(q.rep, q.pos2, n, q.scan_tmp, s));
+    // every graph takes Algorithm 1's two break tests on its own counts;
+    // the graphs that go on keep their refined communities, densely
+    // renumbered after those of the graphs before them
+    CK(launch_graph_stop(q.vseg, q.pos, q.pos2, q.gli, q.g2m, prm.aggregation_tolerance, NG, q.gstate, q.gkeep,
+                         q.gpasses, s));
+    CK(launch_exclusive_scan(q.gkeep, q.vseg2, NG, q.scan_tmp, s));
+    q.launches += 14;
+    int64_t counts[3];
+    CK(cudaMemcpyAsync(&counts[0], q.pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&counts[1], q.pos2 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&counts[2], q.vseg2 + NG, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ST(q.sync_scalars());
+    const int64_t ncomm_all = counts[0];
+    const int64_t ncomm = counts[2];  // communities of the graphs that go on: vertices of the next graph
+    if (trace) {
+        int64_t c4[4] = {n, li, lj, ncomm_all};
+        std::vector<char> buf(sizeof(c4));
+        std::memcpy(buf.data(), c4, sizeof(c4));
+        q.trace[{lp, 4}] = buf;
+        q.trace_count[{lp, 4}] = 4;
+    }
+    // ---- renumber communities; lookup dendrogram (graphs that stop take
+    // their refined labels, reading R8)
+    CK(launch_renumber_batch(q.Cp, q.pos, cur_gid, q.vseg, q.vseg2, q.gstate, q.Cd, n, s));
+    CK(launch_lookup_batch(q.C0, batch ? q.gid0 : nullptr, q.vseg0, q.vseg, q.gstate, q.Cd, q.Cp, n0, s));
+    CK(launch_commit_states(q.gstate, NG, s));
+    q.launches += 3;
+    if (ncomm == 0) {  // every graph stopped (globally converged or low shrink)
+        stop = true;
+        return LEIDEN_OK;
+    }
+    if (trace) {
+        q.record(lp, 5, q.Cd, n);
+        q.record(lp, 10, q.C0, n0);
+    }
+    // ---- aggregation phase (Algorithm 4)
+    ST(mark(2));
+    const int dst = cur_agg ^ 1;
+    CK(cudaMemsetAsync(q.cnt, 0, sizeof(int64_t) * ncomm, s));
+    CK(cudaMemsetAsync(q.tdeg, 0, sizeof(int64_t) * ncomm, s));
+    CK(launch_comm_counts(q.Cd, G.deg, n, q.cnt, q.tdeg, s));
+    CK(launch_exclusive_scan(q.cnt, q.coff, ncomm, q.scan_tmp, s));
+    CK(cudaMemsetAsync(q.cursor, 0, sizeof(int32_t) * ncomm, s));
+    CK(launch_comm_fill(q.Cd, n, q.coff, q.cursor, q.members, s));
+    if (!q.agg[dst].off) {
+        ST(q.alloc(&q.agg[dst].off, n0 + 1));
+        ST(q.alloc(&q.agg[dst].deg, n0));
+    }
+    CK(launch_exclusive_scan(q.tdeg, q.agg[dst].off, ncomm, q.scan_tmp, s));
+    CK(launch_comm_bin_keys(q.tdeg, ncomm, q.key, s));
+    CK(launch_partition(q.key, ncomm, kNumBins, q.key_off, q.list, q.part_tmp, s));
+    CK(launch_max_i64(q.tdeg, ncomm, &q.dsc->maxtdeg, s));
+    q.launches += 16;
+    int64_t cap = 0;
+    int64_t ako[kNumBins + 1];
+    CK(cudaMemcpyAsync(&cap, q.agg[dst].off + ncomm, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ako, q.key_off, sizeof(ako), cudaMemcpyDeviceToHost, s));
+    ST(q.sync_scalars());
+    ST(q.ensure_agg(dst, cap));
+    // rows of communities without edges (bin 0) are never visited: empty
+    CK(cudaMemsetAsync(q.agg[dst].deg, 0, sizeof(int32_t) * ncomm, s));
+    {
+        int64_t mt = (int64_t)q.hsc->maxtdeg;
+        if (mt > ncomm) mt = ncomm;
+        int abits = 0, aregions = 0;
+        if (ako[kBinHub + 1] > ako[kBinHub]) {
+            abits = ceil_log2_h(2 * mt);
+            if (abits < 6) abits = 6;
+            const size_t per = ((size_t)1 << abits) * 12;
+            aregions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
+            ST(q.ensure_hub(abits, aregions, det));
+        }
+        AggCtx ac;
+        ac.g = G;
+        ac.det = det;
+        ac.Cd = q.Cd;
+        ac.coff = q.coff;
+        ac.members = q.members;
+        ac.out_off = q.agg[dst].off;
+        ac.out_deg = q.agg[dst].deg;
+        ac.out_idx = q.agg[dst].idx;
+        ac.out_w = q.agg[dst].w;
+        ac.out_K = q.Kagg;
+        ac.ncomm = ncomm;
+        ac.hub_keys = q.hub_keys;
+        ac.hub_vals = q.hub_vals;
+        ac.hub_bits = abits;
+        ac.err = &q.dsc->err;
+        for (int b = 1; b < kNumBins; ++b) {
+            const int64_t lo = ako[b], hi = ako[b + 1];
+            if (hi == lo) continue;
+            const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : aregions);
+            ac.prof = prof_begin(16 + b);
+            CK(launch_aggregate(ac, b, q.list + lo, hi - lo, mb, s));
+            prof_end();
+            q.launches++;
+        }
+    }
+    // move-based labels of the super-vertices (reading R3)
+    CK(launch_bound_labels(q.Cd, q.CB, n, ncomm, q.bnd, q.rep, q.label, s));
+    q.launches += 4;
+    if (batch) {  // graph of every super-vertex; segments of the next graph
+        int32_t *nxt = cur_gid == q.gidA ? q.gidB : q.gidA;
+        CK(launch_next_gid(q.Cd, cur_gid, n, nxt, s));
+        cur_gid = nxt;
+        q.launches++;
+    }
+    std::swap(q.vseg, q.vseg2);
+    GraphView G2;
+    G2.n = ncomm;
+    G2.off = q.agg[dst].off;
+    G2.deg = q.agg[dst].deg;
+    G2.idx = q.agg[dst].idx;
+    G2.w = q.agg[dst].w;
+    G2.w_int = det;
+    ST(q.sync_scalars());
+    if (trace) {
+        q.record(lp, 6, G2.off, ncomm + 1);
+        q.record(lp, 7, G2.deg, ncomm);
+        q.record(lp, 8, G2.idx, cap);
+        // weights as fp64
+        std::vector<char> raw((size_t)cap * 4);
+        if (cap) {
+            CK(cudaMemcpyAsync(raw.data(), G2.w, raw.size(), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        std::vector<char> buf((size_t)cap * sizeof(double));
+        double *d = reinterpret_cast<double *>(buf.data());
+        for (int64_t e = 0; e < cap; ++e) {
+            if (det) d[e] = (double)reinterpret_cast<const int32_t *>(raw.data())[e];
+            else d[e] = (double)reinterpret_cast<const float *>(raw.data())[e];
+        }
+        q.trace[{lp, 9}] = std::move(buf);
+        q.trace_count[{lp, 9}] = cap;
+    }
+    G = G2;
+    Gcap = cap;
+    cur_agg = dst;
+    tau /= prm.tolerance_drop;  // threshold scaling
+    return LEIDEN_OK;
+}
+
 leiden_status Handle::trace_get(int pass, int what, void *dst, int64_t *count) const {
     auto it = p->trace.find({pass, what});
     if (it == p->trace.end() || !count) {
@@ -511,33 +969,25 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     q.prof_launches.assign(LEIDEN_PROFILE_CLASSES, 0);
     if (profile)
         CK(cudaMemsetAsync(q.prof_cnt, 0, sizeof(unsigned long long) * LEIDEN_PROFILE_CLASSES * kProfCounters, s));
-    // brackets one profiled launch of class cls with events on the run's stream
-    auto prof_begin = [&](int cls) -> unsigned long long * {
-        if (!profile) return nullptr;
-        q.prof_spans.push_back({cls, q.ev_used});
-        cudaEventRecord(q.next_event(), s);
-        q.prof_launches[cls]++;
-        return q.prof_cnt + (size_t)cls * kProfCounters;
-    };
-    auto prof_end = [&]() {
-        if (profile) cudaEventRecord(q.next_event(), s);
-    };
+    Run r;
+    r.prm = &prm;
+    r.det = det;
+    r.trace = trace;
+    r.profile = profile;
+    r.batch = batch;
+    r.L = L;
+    r.B = B;
+    r.nsteps = nsteps;
+    r.nkeys = nkeys;
+    r.NG = NG;
     cudaEvent_t ev0, ev1;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
     CK(cudaEventRecord(ev0, s));
-    std::vector<std::pair<cudaEvent_t, int>> marks;  // phase boundary events (phase id of the span that starts)
-    auto mark = [&](int phase) -> leiden_status {
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e));
-        CK(cudaEventRecord(e, s));
-        marks.push_back({e, phase});
-        return LEIDEN_OK;
-    };
-    leiden_stats st;
-    std::memset(&st, 0, sizeof(st));
+    std::vector<std::pair<cudaEvent_t, int>> &marks = r.marks;
+    auto mark = [&](int phase) { return q.mark(r, phase); };
+    leiden_stats &st = r.st;
     const int64_t n0 = q.n0;
-    int tile_blocks = q.sm * 8, big_blocks = q.sm * 2;
 
     CK(launch_iota(q.C0, n0, s));
     q.launches++;
@@ -551,408 +1001,23 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(cudaMemsetAsync(q.gpasses, 0, sizeof(int32_t) * NG, s));
         CK(cudaStreamSynchronize(s));  // st0 is a local
     }
-    const int32_t *cur_gid = batch ? q.gid0 : nullptr;  // graph of every vertex of G'
-    GraphView G;
-    G.n = n0;
-    G.off = q.off0;
-    G.deg = q.deg0;
-    G.idx = q.idx0;
-    G.w = q.w0;
-    G.w_int = false;
-    double tau = prm.tolerance;
-    bool no_edges = false;
-    int cur_agg = 1;  // next pass writes agg[cur_agg ^ 1]
-    int64_t Gcap = q.m0;  // entry capacity of G' (holey after aggregation)
-    int passes = 0;
-    const size_t accsz = 8;
+    r.cur_gid = batch ? q.gid0 : nullptr;  // graph of every vertex of G'
+    r.G.n = n0;
+    r.G.off = q.off0;
+    r.G.deg = q.deg0;
+    r.G.idx = q.idx0;
+    r.G.w = q.w0;
+    r.G.w_int = false;
+    r.tau = prm.tolerance;
+    r.cur_agg = 1;  // next pass writes agg[cur_agg ^ 1]
+    r.Gcap = q.m0;  // entry capacity of G' (holey after aggregation)
+    const bool &no_edges = r.no_edges;
+    const int &passes = r.passes;
 
     for (int32_t lp = 0; lp < prm.max_passes; ++lp) {
-        const int64_t n = G.n;
-        if (n == 0) break;
-        ST(mark(3));
-        // vertexWeights(G') and 2m (of every graph of a batch)
-        CK(cudaMemsetAsync(&q.dsc->two_m_f, 0, sizeof(double) + sizeof(long long), s));
-        CK(launch_vertex_weights(G, det, q.K, det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, s));
-        if (batch) {
-            CK(cudaMemsetAsync(q.gsumk, 0, sizeof(long long) * NG, s));
-            CK(launch_graph_sums(q.K, det, cur_gid, n, q.gsumk, s));
-            CK(launch_graph_scales(q.gsumk, det, NG, q.gks, q.g2m, s));
-            q.launches += 2;
-        } else {
-            CK(launch_graph_scales(det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, det, 1, q.gks, q.g2m, s));
-            q.launches += 1;
-        }
-        q.launches += 1;
-        // schedule and (step, bin) lists
-        SchedWork sw{q.scnt, q.slayer, q.sfcount};
-        CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s, cur_gid, batch ? q.vseg : nullptr));
-        q.launches += L > 1 ? L : 2;
-        // one vertex list per (schedule step, degree bin), step-major
-        CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
-        CK(launch_partition(q.key, n, nkeys + 1, q.key_off, q.list, q.part_tmp, s));  // + edgeless bucket
-        CK(launch_max_i32(G.deg, n, &q.dsc->maxdeg, s));
-        q.launches += 7;
-        q.hkey_off.assign(nkeys + 2, 0);
-        CK(cudaMemcpyAsync(q.hkey_off.data(), q.key_off, sizeof(int64_t) * (nkeys + 2), cudaMemcpyDeviceToHost, s));
-        ST(q.sync_scalars());
-        const double two_m_f = q.hsc->two_m_f;
-        const long long two_m_i = q.hsc->two_m_i;
-        if (!batch && (det ? (two_m_i == 0) : !(two_m_f > 0))) {  // reading R12: no edges
-            CK(launch_iota(q.Cp, n, s));
-            no_edges = true;
-            passes++;
-            break;
-        }
-        passes++;
-        // C' and Sigma' at the start of local-moving (reading R3)
-        if (lp == 0) CK(launch_iota(q.Cp, n, s));
-        else CK(cudaMemcpyAsync(q.Cp, q.label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        if (trace) q.record(lp, 1, q.Cp, n);
-        // Sweep space. On request (LEIDEN_FLAG_RELABEL) the asynchronous
-        // mode relabels large graphs so that every (step, bin) list is a
-        // contiguous id range, ascending in the ids of G'; the sweeps run on
-        // the relabelled copy and their labels are mapped back afterwards.
-        // Vertex p of the copy is vertex perm[p] = list[p] of G'. The copy
-        // costs about what it saves in the sweeps, so it is off by default.
-        const bool relabel = !det && (prm.flags & LEIDEN_FLAG_RELABEL) && n >= kRelabelMinVertices;
-        GraphView sG = G;
-        int32_t *sC = q.Cp, *sCB = q.CB, *sStep = q.step;
-        const int32_t *sList = q.list;
-        void *sK = q.K;
-        if (relabel) {
-            ST(q.ensure_relabel(Gcap));
-            const int32_t *perm = q.list;
-            CK(launch_inverse(perm, n, q.rinv, s));
-            CK(launch_gather_i32(G.deg, perm, n, q.rdeg, s));
-            CK(launch_exclusive_scan_i32(q.rdeg, q.roff, n, q.scan_tmp, s));
-            CK(launch_permute_rows(G, perm, q.rinv, q.roff, q.ridx, q.rw, s));
-            CK(launch_gather_i32(static_cast<const int32_t *>(q.K), perm, n, static_cast<int32_t *>(q.rK), s));  // fp32 K
-            CK(launch_gather_i32(q.step, perm, n, q.rstep, s));
-            CK(launch_labels_to_new(q.Cp, perm, q.rinv, n, q.rC, s));
-            q.launches += 9;
-            if (batch) {
-                CK(launch_gather_i32(cur_gid, perm, n, q.rgid, s));
-                q.launches++;
-            }
-            sG.off = q.roff;
-            sG.deg = q.rdeg;
-            sG.idx = q.ridx;
-            sG.w = q.rw;
-            sC = q.rC;
-            sCB = q.rCB;
-            sStep = q.rstep;
-            sList = q.iota_list;
-            sK = q.rK;
-        }
-        CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
-        CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
-        CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));
-        q.launches += 1;
-        // hub tables for bin 7
-        int hub_bits = 0, hub_regions = 0;
-        {
-            const int maxdeg = q.hsc->maxdeg;
-            if (maxdeg > kBlockMaxDeg) {
-                hub_bits = ceil_log2_h(2 * (int64_t)maxdeg);
-                const size_t per = ((size_t)1 << hub_bits) * 12;
-                hub_regions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
-                ST(q.ensure_hub(hub_bits, hub_regions, det));
-            }
-        }
-        SweepCtx sc;
-        sc.g = sG;
-        sc.det = det;
-        sc.C = sC;
-        sc.CB = sCB;
-        sc.K = sK;
-        sc.Sig = q.Sig;
-        sc.size = q.size;
-        sc.unproc = q.unproc;
-        sc.prop = q.prop;
-        sc.gain = q.gain;
-        sc.step = sStep;
-        sc.two_m_f = two_m_f;
-        sc.two_m_i = two_m_i;
-        sc.gamma = prm.resolution;
-        sc.cap_step = L - 1;
-        sc.dq_acc = det ? (void *)&q.dsc->dq_i : (void *)&q.dsc->dq_f;
-        sc.moved = &q.dsc->moved;
-        sc.hub_keys = q.hub_keys;
-        sc.hub_vals = q.hub_vals;
-        sc.hub_bits = hub_bits;
-        sc.err = &q.dsc->err;
-        const std::vector<int64_t> &ko = q.hkey_off;
-        sc.nsteps = nsteps;
-        sc.key_off = q.key_off;
-        sc.bar = q.bar;
-        sc.hub_regions = hub_regions;
-        sc.gid = batch ? (relabel ? q.rgid : cur_gid) : nullptr;
-        sc.gks = q.gks;
-        sc.g2m = q.g2m;
-        sc.gdone = q.gdone;
-        sc.gactive = q.gactive;
-        sc.G = NG;
-        const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
-        // one sweep as per-(step, bin) launches (fallback and test path)
-        auto run_steps = [&](bool refine) -> leiden_status {
-            sc.refine = refine;
-            for (int32_t k = 0; k < nsteps; ++k) {
-                sc.cur_step = k;
-                const int64_t a0 = ko[k * kNumBins], a1 = ko[(k + 1) * kNumBins];
-                if (a1 == a0) continue;
-                for (int b = 1; b < kNumBins; ++b) {
-                    const int64_t lo = ko[k * kNumBins + b], hi = ko[k * kNumBins + b + 1];
-                    if (hi == lo) continue;
-                    const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : hub_regions);
-                    sc.prof = prof_begin((refine ? 8 : 0) + b);
-                    CK(launch_sweep_eval(sc, b, sList + lo, hi - lo, mb, s));
-                    prof_end();
-                    q.launches++;
-                }
-                // apply phase: deterministic mode, and refinement proposals where
-                // neighbours may share a step (asynchronous refinement applies
-                // its joins at once below the capped step)
-                if (det || (refine && k >= sc.cap_step)) {
-                    if (refine) CK(launch_refine_apply(sc, sList + a0, a1 - a0, s));
-                    else CK(launch_move_apply(sc, sList + a0, a1 - a0, s));
-                    q.launches++;
-                }
-            }
-            return LEIDEN_OK;
-        };
-        // One phase (Algorithm 2 or 3): sweeps until convergence. Normally one
-        // persistent cooperative launch that tests convergence on the device;
-        // otherwise one host-driven sweep at a time. Returns the sweeps run.
-        auto run_phase = [&](bool refine, int *iters, int32_t *giters) -> leiden_status {
-            sc.refine = refine;
-            const bool single = refine && (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP);
-            const int per_sm = step_launches ? 0 : sweep_coop_blocks_per_sm(det, sG.w_int, refine);
-            CK(launch_phase_init(q.gstate, NG, q.gdone, giters, s));
-            sc.giters = giters;
-            if (batch && per_sm <= 0) {
-                set_last_error("a batch of graphs needs the cooperative sweep kernel");
-                return LEIDEN_ERR_UNSUPPORTED;
-            }
-            if (per_sm > 0) {
-                // enough blocks for the graph (about 2048 vertices each), so
-                // small graphs do not pay a full-GPU barrier per step
-                int grid = per_sm * q.sm;
-                const int64_t want = (n + 2047) / 2048;
-                if (want < grid) grid = (int)(want < 1 ? 1 : want);
-                sc.hub_regions = hub_regions > grid ? grid : hub_regions;
-                sc.max_it = prm.max_iterations;
-                sc.single_sweep = single ? 1 : 0;
-                sc.tau = tau;
-                sc.dq_arr = q.phase_dq;
-                sc.moved_arr = q.phase_moved;
-                sc.iters_out = &q.dsc->iters;
-                CK(cudaMemsetAsync(q.phase_dq, 0, sizeof(long long) * prm.max_iterations * NG, s));
-                CK(cudaMemsetAsync(q.phase_moved, 0, sizeof(unsigned long long) * prm.max_iterations * NG, s));
-                CK(cudaMemsetAsync(q.gactive, 0, sizeof(unsigned) * prm.max_iterations, s));
-                sc.prof = prof_begin(refine ? 8 : 0);
-                CK(launch_sweep_coop(sc, sList, grid, s));
-                prof_end();
-                q.launches++;
-                ST(q.sync_scalars());
-                *iters = q.hsc->iters;
-                sc.hub_regions = hub_regions;
-                return LEIDEN_OK;
-            }
-            int k = 0;
-            for (int32_t it = 0; it < prm.max_iterations; ++it) {
-                k++;
-                CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double) + sizeof(long long), s));
-                CK(cudaMemsetAsync(&q.dsc->moved, 0, sizeof(unsigned long long), s));
-                ST(run_steps(refine));
-                ST(q.sync_scalars());
-                if (refine) {
-                    if (q.hsc->moved == 0 || single) break;
-                } else {
-                    const double dq = det ? 2.0 * (double)q.hsc->dq_i / ((double)two_m_i * (double)two_m_i)
-                                          : 2.0 * q.hsc->dq_f / two_m_f;
-                    if (dq <= tau) break;  // locally converged
-                }
-            }
-            *iters = k;
-            CK(launch_fill_i32(giters, k, 1, s));
-            return LEIDEN_OK;
-        };
-        // ---- local-moving phase (Algorithm 2)
-        ST(mark(0));
-        CK(cudaMemsetAsync(q.unproc, 1, (size_t)n, s));  // mark all vertices unprocessed
-        int li = 0;
-        ST(run_phase(false, &li, q.gli));
-        st.move_iterations += li;
-        if (trace) {
-            if (relabel) {
-                CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cd, s));
-                q.record(lp, 2, q.Cd, n);
-            } else {
-                q.record(lp, 2, q.Cp, n);
-            }
-        }
-        // ---- refinement phase (Algorithm 3)
-        ST(mark(1));
-        CK(cudaMemcpyAsync(sCB, sC, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-        CK(launch_iota(sC, n, s));
-        CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
-        CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
-        CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));  // Sigma' <- K', one member each
-        q.launches += 2;
-        int lj = 0;
-        ST(run_phase(true, &lj, q.glj));
-        if (relabel) {  // back to the ids of G'
-            CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cp, s));
-            CK(launch_labels_to_old(sCB, q.list, q.rinv, n, q.CB, s));
-            q.launches += 2;
-        }
-        st.refine_iterations += lj;
-        if (trace) q.record(lp, 3, q.Cp, n);
-        // ---- stop tests (readings R4, R5')
-        ST(mark(3));
-        // non-empty refined communities: the labels present in C' (ids of G')
-        CK(launch_fill_i32(q.flag, 0, n, s));
-        CK(launch_mark_labels(q.Cp, n, q.flag, s));
-        CK(launch_exclusive_scan_i32(q.flag, q.pos, n, q.scan_tmp, s));
-        CK(launch_fill_i32(q.rep, 0, n, s));
-        CK(launch_mark_labels(q.CB, n, q.rep, s));
-        CK(launch_exclusive_scan_i32(q.rep, q.pos2, n, q.scan_tmp, s));
-        // every graph takes Algorithm 1's two break tests on its own counts;
-        // the graphs that go on keep their refined communities, densely
-        // renumbered after those of the graphs before them
-        CK(launch_graph_stop(q.vseg, q.pos, q.pos2, q.gli, q.g2m, prm.aggregation_tolerance, NG, q.gstate, q.gkeep,
-                             q.gpasses, s));
-        CK(launch_exclusive_scan(q.gkeep, q.vseg2, NG, q.scan_tmp, s));
-        q.launches += 14;
-        int64_t counts[3];
-        CK(cudaMemcpyAsync(&counts[0], q.pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&counts[1], q.pos2 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(&counts[2], q.vseg2 + NG, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        ST(q.sync_scalars());
-        const int64_t ncomm_all = counts[0];
-        const int64_t ncomm = counts[2];  // communities of the graphs that go on: vertices of the next graph
-        if (trace) {
-            int64_t c4[4] = {n, li, lj, ncomm_all};
-            std::vector<char> buf(sizeof(c4));
-            std::memcpy(buf.data(), c4, sizeof(c4));
-            q.trace[{lp, 4}] = buf;
-            q.trace_count[{lp, 4}] = 4;
-        }
-        // ---- renumber communities; lookup dendrogram (graphs that stop take
-        // their refined labels, reading R8)
-        CK(launch_renumber_batch(q.Cp, q.pos, cur_gid, q.vseg, q.vseg2, q.gstate, q.Cd, n, s));
-        CK(launch_lookup_batch(q.C0, batch ? q.gid0 : nullptr, q.vseg0, q.vseg, q.gstate, q.Cd, q.Cp, n0, s));
-        CK(launch_commit_states(q.gstate, NG, s));
-        q.launches += 3;
-        if (ncomm == 0) break;  // every graph stopped (globally converged or low shrink)
-        if (trace) {
-            q.record(lp, 5, q.Cd, n);
-            q.record(lp, 10, q.C0, n0);
-        }
-        // ---- aggregation phase (Algorithm 4)
-        ST(mark(2));
-        const int dst = cur_agg ^ 1;
-        CK(cudaMemsetAsync(q.cnt, 0, sizeof(int64_t) * ncomm, s));
-        CK(cudaMemsetAsync(q.tdeg, 0, sizeof(int64_t) * ncomm, s));
-        CK(launch_comm_counts(q.Cd, G.deg, n, q.cnt, q.tdeg, s));
-        CK(launch_exclusive_scan(q.cnt, q.coff, ncomm, q.scan_tmp, s));
-        CK(cudaMemsetAsync(q.cursor, 0, sizeof(int32_t) * ncomm, s));
-        CK(launch_comm_fill(q.Cd, n, q.coff, q.cursor, q.members, s));
-        if (!q.agg[dst].off) {
-            ST(q.alloc(&q.agg[dst].off, n0 + 1));
-            ST(q.alloc(&q.agg[dst].deg, n0));
-        }
-        CK(launch_exclusive_scan(q.tdeg, q.agg[dst].off, ncomm, q.scan_tmp, s));
-        CK(launch_comm_bin_keys(q.tdeg, ncomm, q.key, s));
-        CK(launch_partition(q.key, ncomm, kNumBins, q.key_off, q.list, q.part_tmp, s));
-        CK(launch_max_i64(q.tdeg, ncomm, &q.dsc->maxtdeg, s));
-        q.launches += 16;
-        int64_t cap = 0;
-        int64_t ako[kNumBins + 1];
-        CK(cudaMemcpyAsync(&cap, q.agg[dst].off + ncomm, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(ako, q.key_off, sizeof(ako), cudaMemcpyDeviceToHost, s));
-        ST(q.sync_scalars());
-        ST(q.ensure_agg(dst, cap));
-        // rows of communities without edges (bin 0) are never visited: empty
-        CK(cudaMemsetAsync(q.agg[dst].deg, 0, sizeof(int32_t) * ncomm, s));
-        {
-            int64_t mt = (int64_t)q.hsc->maxtdeg;
-            if (mt > ncomm) mt = ncomm;
-            int abits = 0, aregions = 0;
-            if (ako[kBinHub + 1] > ako[kBinHub]) {
-                abits = ceil_log2_h(2 * mt);
-                if (abits < 6) abits = 6;
-                const size_t per = ((size_t)1 << abits) * 12;
-                aregions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
-                ST(q.ensure_hub(abits, aregions, det));
-            }
-            AggCtx ac;
-            ac.g = G;
-            ac.det = det;
-            ac.Cd = q.Cd;
-            ac.coff = q.coff;
-            ac.members = q.members;
-            ac.out_off = q.agg[dst].off;
-            ac.out_deg = q.agg[dst].deg;
-            ac.out_idx = q.agg[dst].idx;
-            ac.out_w = q.agg[dst].w;
-            ac.out_K = q.Kagg;
-            ac.ncomm = ncomm;
-            ac.hub_keys = q.hub_keys;
-            ac.hub_vals = q.hub_vals;
-            ac.hub_bits = abits;
-            ac.err = &q.dsc->err;
-            for (int b = 1; b < kNumBins; ++b) {
-                const int64_t lo = ako[b], hi = ako[b + 1];
-                if (hi == lo) continue;
-                const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : aregions);
-                ac.prof = prof_begin(16 + b);
-                CK(launch_aggregate(ac, b, q.list + lo, hi - lo, mb, s));
-                prof_end();
-                q.launches++;
-            }
-        }
-        // move-based labels of the super-vertices (reading R3)
-        CK(launch_bound_labels(q.Cd, q.CB, n, ncomm, q.bnd, q.rep, q.label, s));
-        q.launches += 4;
-        if (batch) {  // graph of every super-vertex; segments of the next graph
-            int32_t *nxt = cur_gid == q.gidA ? q.gidB : q.gidA;
-            CK(launch_next_gid(q.Cd, cur_gid, n, nxt, s));
-            cur_gid = nxt;
-            q.launches++;
-        }
-        std::swap(q.vseg, q.vseg2);
-        GraphView G2;
-        G2.n = ncomm;
-        G2.off = q.agg[dst].off;
-        G2.deg = q.agg[dst].deg;
-        G2.idx = q.agg[dst].idx;
-        G2.w = q.agg[dst].w;
-        G2.w_int = det;
-        ST(q.sync_scalars());
-        if (trace) {
-            q.record(lp, 6, G2.off, ncomm + 1);
-            q.record(lp, 7, G2.deg, ncomm);
-            q.record(lp, 8, G2.idx, cap);
-            // weights as fp64
-            std::vector<char> raw((size_t)cap * 4);
-            if (cap) {
-                CK(cudaMemcpyAsync(raw.data(), G2.w, raw.size(), cudaMemcpyDeviceToHost, s));
-                CK(cudaStreamSynchronize(s));
-            }
-            std::vector<char> buf((size_t)cap * sizeof(double));
-            double *d = reinterpret_cast<double *>(buf.data());
-            for (int64_t e = 0; e < cap; ++e) {
-                if (det) d[e] = (double)reinterpret_cast<const int32_t *>(raw.data())[e];
-                else d[e] = (double)reinterpret_cast<const float *>(raw.data())[e];
-            }
-            q.trace[{lp, 9}] = std::move(buf);
-            q.trace_count[{lp, 9}] = cap;
-        }
-        G = G2;
-        Gcap = cap;
-        cur_agg = dst;
-        tau /= prm.tolerance_drop;  // threshold scaling
+        bool stop = false;
+        ST(q.pass(r, lp, stop));
+        if (stop) break;
     }
     ST(mark(3));
     // C <- lookup dendrogram using C to C' (reading R8): a graph without
