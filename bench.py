@@ -20,6 +20,14 @@ p_out/p_in = 0.02; ~61M vertices, ~1.2e9 entries) packed as one segmented CSR
 and solved by leiden_batch_run, in graphs/s, next to a per-graph loop of
 plain leiden_run calls timed on a sample of the same graphs. With N > 1 the
 graphs are split across ranks in contiguous ranges.
+
+And the served form ("served"): a Poisson stream of seeded SBM (1k-4M
+vertices) and R-MAT (scale 14-22, edge factor 16) graphs from host memory,
+served by the continuous-batching server (leiden_server_*) and, on the same
+arrival times, by a plain server that runs one leiden_run at a time. The
+offered rate is set to 90% of the plain server's measured service rate;
+p50/p99 latency (arrival to result on the host), graphs/s and the mean
+modularity of both are reported. Rank 0 only.
 """
 import argparse
 import hashlib
@@ -59,6 +67,10 @@ def parse():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-sample", type=int, default=128, help="graphs of the per-graph loop")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served form")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-pool", type=int, default=24, help="distinct graphs the requests cycle through")
+    ap.add_argument("--serve-load", type=float, default=0.9, help="offered rate / plain server's service rate")
     return ap.parse_args()
 
 
@@ -228,6 +240,120 @@ def batched_form(args, rank, world, mode, flags):
     }
 
 
+def serve_pool(count, seed=5):
+    """count seeded graphs: half SBM (n log-uniform in [1k, 4M], 4-64 blocks,
+    mean degree 8-32, p_out/p_in 0.02), half R-MAT (scale 14-22, edge factor
+    16, (0.57, 0.19, 0.19, 0.05)), unit weights."""
+    import numpy as np
+
+    import gen
+    rng = np.random.default_rng(seed)
+    pool, kinds = [], []
+    for k in range(count):
+        if k % 2 == 0:
+            p = gen.sbm_batch_params(1, seed=seed * 1000 + k, nmin=1000, nmax=4_000_000)
+            pool.append(gen.sbm(int(p["n"][0]), int(p["blocks"][0]), float(p["p_in"][0]), float(p["p_out"][0]),
+                                int(p["seeds"][0])))
+            kinds.append("sbm")
+        else:
+            pool.append(gen.rmat(int(rng.integers(14, 23)), 16, 0.57, 0.19, 0.19, seed=seed * 1000 + k))
+            kinds.append("rmat")
+    return pool, kinds
+
+
+def served_form(args, mode, flags):
+    """Continuous-batching server against a plain one-at-a-time server on the
+    same Poisson arrivals (times measured on the host, results on the host)."""
+    import numpy as np
+    import torch
+
+    import paper_2312_13936_gb300 as lg
+    pool, kinds = serve_pool(args.serve_pool)
+    R = args.serve_requests
+    stream = torch.cuda.current_stream()
+    sp = lg._VP(stream.cuda_stream)
+
+    def plain_one(g):
+        h = lg.leiden_create(g.n, g.nnz, g.offsets.ctypes.data_as(lg._VP), g.indices.ctypes.data_as(lg._VP),
+                             g.weights.ctypes.data_as(lg._VP), lg.LEIDEN_HOST, 0, sp)
+        out = np.zeros(max(g.n, 1), np.int32)
+        p = lg.leiden_params_default()
+        p.mode = mode
+        p.flags = flags
+        q, st = lg.leiden_run(h, p, out.ctypes.data_as(lg._VP), lg.LEIDEN_HOST)
+        lg.leiden_destroy(h)
+        return q
+    # service rate of the plain server (every pool graph once, after a warm-up)
+    for g in pool[:2]:
+        plain_one(g)
+    t = time.perf_counter()
+    for g in pool:
+        plain_one(g)
+    service = (time.perf_counter() - t) / len(pool)
+    rate = args.serve_load / service
+    rng = np.random.default_rng(55)
+    arrive = np.cumsum(rng.exponential(1.0 / rate, R))
+    order = [k % len(pool) for k in range(R)]
+
+    def summary(lat, t_end, qs):
+        lat = np.asarray(lat)
+        return {"graphs_per_s": R / t_end, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                "modularity_mean": float(np.mean(qs))}
+
+    # plain server: first come, first served, one leiden_run at a time
+    lat, qs = [], []
+    t0 = time.perf_counter()
+    for k in range(R):
+        now = time.perf_counter() - t0
+        if now < arrive[k]:
+            time.sleep(arrive[k] - now)
+        qs.append(plain_one(pool[order[k]]))
+        lat.append(time.perf_counter() - t0 - arrive[k])
+    plain = summary(lat, time.perf_counter() - t0, qs)
+    # continuous batching
+    cap_v = max(g.n for g in pool) * 4
+    cap_e = max(g.nnz for g in pool) * 4
+    srv = lg.LeidenServer(cap_v, cap_e, max_graphs=256, mode=mode)
+    for g in pool[:2]:  # warm-up
+        srv.submit(g.offsets, g.indices, g.weights)
+    while len(srv.results()) < 2:
+        srv.step()
+    lat, qs, steps = {}, {}, 0
+    ids = {}
+    t0 = time.perf_counter()
+    k = 0
+    while len(lat) < R:
+        now = time.perf_counter() - t0
+        while k < R and arrive[k] <= now:
+            g = pool[order[k]]
+            ids[srv.submit(g.offsets, g.indices, g.weights)] = k
+            k += 1
+        info = srv.info()
+        if info["in_flight"] == 0 and info["waiting"] == 0:
+            if k < R:
+                time.sleep(max(0.0, arrive[k] - (time.perf_counter() - t0)))
+            continue
+        srv.step()
+        steps += 1
+        for rid, memb, q, passes, comm in srv.results():
+            j = ids.pop(rid)
+            lat[j] = time.perf_counter() - t0 - arrive[j]
+            qs[j] = q
+    cb = summary([lat[j] for j in range(R)], time.perf_counter() - t0, [qs[j] for j in range(R)])
+    srv.close()
+    cb["steps"] = steps
+    return {
+        "workload": (f"Poisson arrivals of {R} requests cycling through {len(pool)} seeded graphs (SBM n in [1k, 4M] "
+                     f"log-uniform, R-MAT scale 14-22 edge factor 16; {sum(g.nnz for g in pool) / 1e6:.0f}M entries "
+                     f"in the pool), unit weights, from host memory"),
+        "mode": "async" if mode == lg.LEIDEN_ASYNC else "det",
+        "offered_rate_per_s": rate, "load_vs_plain": args.serve_load, "plain_service_ms": service * 1e3,
+        "continuous": cb, "plain": plain,
+        "graphs_per_s_ratio": cb["graphs_per_s"] / plain["graphs_per_s"],
+    }
+
+
 def cpu_baseline(side):
     import gen
     import oracle
@@ -383,6 +509,7 @@ def main():
                     "bytes_per_launch": a["bytes"] / a["launches"], "ms_per_launch": a["ms"] / a["launches"],
                     "share_of_profiled_ms": a["ms"] / total_ms}
     cpu = None if (args.no_cpu or world > 1) else cpu_baseline(args.cpu_side)
+    served = None if (args.no_serve or world > 1) else served_form(args, mode, base_flags)
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -396,6 +523,7 @@ def main():
                                 "other": st.ms_other}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
         "batched": batched,
+        "served": served,
         "kernel_classes": {f"{k[0]}/{k[1]}": v for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
     }
     print(json.dumps(line), flush=True)

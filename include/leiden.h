@@ -122,6 +122,19 @@ typedef struct {
 enum { LEIDEN_PROFILE_CLASSES = 24 };
 
 typedef struct leiden_graph_s *leiden_graph_t;
+typedef struct leiden_server_s *leiden_server_t;
+
+/* State of a serving handle (filled by leiden_server_info). */
+typedef struct {
+    int32_t waiting;          /* submitted graphs not yet in flight */
+    int32_t in_flight;        /* graphs in the union */
+    int32_t finished;         /* finished graphs whose results are unread */
+    int32_t reserved;
+    int64_t union_vertices;   /* vertices of the union's current graph */
+    int64_t union_entries;    /* CSR entries of the union's current graph */
+    int64_t device_bytes;     /* device bytes held by the requests' own buffers */
+    int64_t steps;            /* steps run */
+} leiden_server_state;
 
 /* Fill *p with the defaults listed above. */
 void leiden_params_default(leiden_params *p);
@@ -179,6 +192,56 @@ leiden_status leiden_batch_create(leiden_graph_t *out, int32_t num_graphs, const
  * handle from leiden_create is a batch of one graph. */
 leiden_status leiden_batch_run(leiden_graph_t g, const leiden_params *p, int32_t *membership, int32_t where,
                                double *modularity, leiden_stats *stats);
+
+/* Serving with continuous batching. A server holds a union of graphs in
+ * flight, each at its own pass of Algorithm 1. leiden_server_step admits
+ * waiting graphs at the pass boundary (first come, first served, while a
+ * slot, union capacity and the device budget allow), then runs one pass of
+ * every graph in flight with one set of launches; graphs that stop leave
+ * the union with their results. Every graph's result is the one leiden_run
+ * gives alone (bit for bit in deterministic mode). The caller drives the
+ * loop: submit graphs as they arrive, call step, read finished results.
+ *
+ * Create a server for graphs of up to max_vertices vertices and max_entries
+ * CSR entries in flight together (one graph may not exceed either), at most
+ * max_graphs graphs in flight, and device_budget bytes for the submitted
+ * graphs' own buffers (CSR copy and result; <= 0: half the free device
+ * memory after the server's workspace). p fixes the parameters of every run
+ * (LEIDEN_FLAG_RELABEL, _TRACE, _PROFILE and _STEP_LAUNCHES are ignored). */
+leiden_status leiden_server_create(leiden_server_t *out, const leiden_params *p, int64_t max_vertices,
+                                   int64_t max_entries, int32_t max_graphs, int64_t device_budget, void *stream);
+
+/* Submit one graph (a symmetric CSR with indices in [0, n), as for
+ * leiden_create; it is checked as with validate). The arrays are copied at
+ * once: to device memory when the budget allows, else to host memory until
+ * it does. *request_id receives the graph's id. Graphs without vertices are
+ * finished at once. Returns LEIDEN_ERR_INVALID for a graph larger than the
+ * server's capacity; in deterministic mode LEIDEN_ERR_UNSUPPORTED or
+ * LEIDEN_ERR_OVERFLOW as leiden_run would. */
+leiden_status leiden_server_submit(leiden_server_t s, int64_t n, int64_t nnz, const int64_t *offsets,
+                                   const int32_t *indices, const float *weights, int32_t where, int64_t *request_id);
+
+/* One step: admit, run one pass of every graph in flight, finish the graphs
+ * that stop. *finished (nullable) receives the number of graphs finished by
+ * the step. Returns at once when nothing is in flight or waiting. */
+leiden_status leiden_server_step(leiden_server_t s, int32_t *finished);
+
+/* Id of the oldest finished graph whose result is unread, or -1. */
+leiden_status leiden_server_next(leiden_server_t s, int64_t *request_id);
+
+/* Read and release the result of a finished graph: membership (n int32,
+ * host or device per `where`; canonical labels as leiden_run gives them),
+ * and (nullable) modularity, passes and communities. Returns
+ * LEIDEN_ERR_INVALID for an unknown or unfinished id, or the graph's own
+ * error status if it failed when it was copied to the device. */
+leiden_status leiden_server_result(leiden_server_t s, int64_t request_id, int32_t *membership, int32_t where,
+                                   double *modularity, int32_t *passes, int64_t *communities);
+
+/* Current state of the server (host struct). */
+leiden_status leiden_server_info(leiden_server_t s, leiden_server_state *out);
+
+/* Release the server, its workspace and every graph it holds. NULL is accepted. */
+leiden_status leiden_server_destroy(leiden_server_t s);
 
 /* Per-graph results of the last run on the handle: passes executed and
  * communities found (host arrays of num_graphs entries; either may be

@@ -23,7 +23,9 @@ __all__ = [
     "library", "leiden_params_default", "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity",
     "leiden_trace_get", "leiden_profile_get", "leiden_modularity_noalloc",
     "leiden_status_string", "leiden_last_error", "Leiden", "modularity", "leiden_batch_create",
-    "leiden_batch_run", "leiden_batch_info", "LeidenBatch", "pack_batch",
+    "leiden_batch_run", "leiden_batch_info", "LeidenBatch", "pack_batch", "ServerState", "leiden_server_create",
+    "leiden_server_submit", "leiden_server_step", "leiden_server_next", "leiden_server_result", "leiden_server_info",
+    "leiden_server_destroy", "LeidenServer",
 ]
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
@@ -70,6 +72,15 @@ class KernelProfile(ctypes.Structure):
                 ("distinct", ctypes.c_int64), ("moved", ctypes.c_int64)]
 
 
+class ServerState(ctypes.Structure):
+    _fields_ = [("waiting", ctypes.c_int32), ("in_flight", ctypes.c_int32), ("finished", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("union_vertices", ctypes.c_int64), ("union_entries", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("steps", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 _LIB = None
 _VP, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
 
@@ -99,9 +110,20 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.leiden_batch_create.argtypes = [ctypes.POINTER(_VP), _I32, _VP, _I64, _VP, _VP, _VP, _I32, _I32, _VP]
         lib.leiden_batch_run.argtypes = [_VP, ctypes.POINTER(Params), _VP, _I32, _VP, ctypes.POINTER(Stats)]
         lib.leiden_batch_info.argtypes = [_VP, ctypes.POINTER(_I32), _VP, _VP]
+        lib.leiden_server_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Params), _I64, _I64, _I32, _I64,
+                                             _VP]
+        lib.leiden_server_submit.argtypes = [_VP, _I64, _I64, _VP, _VP, _VP, _I32, ctypes.POINTER(_I64)]
+        lib.leiden_server_step.argtypes = [_VP, ctypes.POINTER(_I32)]
+        lib.leiden_server_next.argtypes = [_VP, ctypes.POINTER(_I64)]
+        lib.leiden_server_result.argtypes = [_VP, _I64, _VP, _I32, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(_I32), ctypes.POINTER(_I64)]
+        lib.leiden_server_info.argtypes = [_VP, ctypes.POINTER(ServerState)]
+        lib.leiden_server_destroy.argtypes = [_VP]
         for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
                   lib.leiden_trace_get, lib.leiden_profile_get, lib.leiden_batch_create, lib.leiden_batch_run,
-                  lib.leiden_batch_info):
+                  lib.leiden_batch_info, lib.leiden_server_create, lib.leiden_server_submit, lib.leiden_server_step,
+                  lib.leiden_server_next, lib.leiden_server_result, lib.leiden_server_info,
+                  lib.leiden_server_destroy):
             f.restype = ctypes.c_int
         lib.leiden_status_string.argtypes = [_I32]
         lib.leiden_status_string.restype = ctypes.c_char_p
@@ -173,6 +195,52 @@ def leiden_batch_info(handle):
     comm = np.zeros(max(g.value, 1), dtype=np.int64)
     _check(library().leiden_batch_info(handle, None, passes.ctypes.data_as(_VP), comm.ctypes.data_as(_VP)))
     return passes[:g.value], comm[:g.value]
+
+
+def leiden_server_create(params: Params, max_vertices, max_entries, max_graphs, device_budget, stream) -> int:
+    h = _VP()
+    _check(library().leiden_server_create(ctypes.byref(h), ctypes.byref(params), max_vertices, max_entries,
+                                          max_graphs, device_budget, stream))
+    return h.value
+
+
+def leiden_server_submit(server, n, nnz, offsets_ptr, indices_ptr, weights_ptr, where) -> int:
+    rid = _I64(0)
+    _check(library().leiden_server_submit(server, n, nnz, offsets_ptr, indices_ptr, weights_ptr, where,
+                                          ctypes.byref(rid)))
+    return rid.value
+
+
+def leiden_server_step(server) -> int:
+    f = _I32(0)
+    _check(library().leiden_server_step(server, ctypes.byref(f)))
+    return f.value
+
+
+def leiden_server_next(server) -> int:
+    rid = _I64(0)
+    _check(library().leiden_server_next(server, ctypes.byref(rid)))
+    return rid.value
+
+
+def leiden_server_result(server, rid, membership_ptr, where):
+    """(modularity, passes, communities) of a finished graph; its labels go to membership_ptr."""
+    q = ctypes.c_double(0.0)
+    passes = _I32(0)
+    comm = _I64(0)
+    _check(library().leiden_server_result(server, rid, membership_ptr, where, ctypes.byref(q), ctypes.byref(passes),
+                                          ctypes.byref(comm)))
+    return q.value, passes.value, comm.value
+
+
+def leiden_server_info(server) -> dict:
+    st = ServerState()
+    _check(library().leiden_server_info(server, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def leiden_server_destroy(server) -> None:
+    _check(library().leiden_server_destroy(server))
 
 
 def leiden_destroy(handle) -> None:
@@ -342,6 +410,80 @@ class LeidenBatch:
     def close(self):
         if getattr(self, "handle", None):
             leiden_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LeidenServer:
+    """Serving with continuous batching: submit graphs as they arrive, call
+    ``step`` (admission at the pass boundary, then one pass of every graph in
+    flight), collect finished graphs with ``results``. Graphs are CSRs as
+    numpy arrays (copied from host) or CUDA tensors (copied on the device).
+    """
+
+    def __init__(self, max_vertices: int, max_entries: int, max_graphs: int = 1024, device_budget: int = 0,
+                 mode: int = LEIDEN_ASYNC, stream=None, **kw):
+        import torch
+        self._torch = torch
+        p = leiden_params_default()
+        p.mode = mode
+        for k, v in kw.items():
+            setattr(p, k, v)
+        self.stream = stream
+        self.handle = leiden_server_create(p, max_vertices, max_entries, max_graphs, device_budget,
+                                           _stream_ptr(stream))
+        self.sizes = {}
+
+    def submit(self, offsets, indices, weights=None) -> int:
+        t = self._torch
+        if isinstance(offsets, t.Tensor) and offsets.is_cuda:
+            off = offsets.to(t.int64).contiguous()
+            idx = indices.to(t.int32).contiguous()
+            w = None if weights is None else weights.to(t.float32).contiguous()
+            n, m = int(off.numel() - 1), int(idx.numel())
+            rid = leiden_server_submit(self.handle, n, m, _ptr(off), _ptr(idx), _ptr(w), LEIDEN_DEVICE)
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            idx = np.ascontiguousarray(indices, dtype=np.int32)
+            w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+            n, m = int(len(off) - 1), int(len(idx))
+            rid = leiden_server_submit(self.handle, n, m, off.ctypes.data_as(_VP), idx.ctypes.data_as(_VP),
+                                       None if w is None else w.ctypes.data_as(_VP), LEIDEN_HOST)
+        self.sizes[rid] = n
+        return rid
+
+    def step(self) -> int:
+        return leiden_server_step(self.handle)
+
+    def results(self, device: bool = False):
+        """Drain finished graphs: list of (id, membership, modularity, passes, communities)."""
+        out = []
+        while True:
+            rid = leiden_server_next(self.handle)
+            if rid < 0:
+                return out
+            n = self.sizes.pop(rid)
+            if device:
+                memb = self._torch.empty(max(n, 1), dtype=self._torch.int32, device="cuda")
+                q, passes, comm = leiden_server_result(self.handle, rid, _ptr(memb), LEIDEN_DEVICE)
+                memb = memb[:n]
+            else:
+                memb = np.zeros(max(n, 1), dtype=np.int32)
+                q, passes, comm = leiden_server_result(self.handle, rid, memb.ctypes.data_as(_VP), LEIDEN_HOST)
+                memb = memb[:n]
+            out.append((rid, memb, q, passes, comm))
+
+    def info(self) -> dict:
+        return leiden_server_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            leiden_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

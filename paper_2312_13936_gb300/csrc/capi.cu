@@ -6,6 +6,9 @@
 struct leiden_graph_s {
     lgb::Handle h;
 };
+struct leiden_server_s {
+    lgb::Handle h;
+};
 
 extern "C" {
 
@@ -136,6 +139,78 @@ leiden_status leiden_batch_info(leiden_graph_t g, int32_t *num_graphs, int32_t *
     if (num_graphs) *num_graphs = g->h.num_graphs();
     if (!passes && !communities) return LEIDEN_OK;
     return g->h.graph_info(passes, communities);
+}
+
+leiden_status leiden_server_create(leiden_server_t *out, const leiden_params *p, int64_t max_vertices,
+                                   int64_t max_entries, int32_t max_graphs, int64_t device_budget, void *stream) {
+    if (!out || !p) {
+        lgb::set_last_error("out or params is NULL");
+        return LEIDEN_ERR_INVALID;
+    }
+    *out = nullptr;
+    leiden_server_s *sv = new (std::nothrow) leiden_server_s;
+    if (!sv) {
+        lgb::set_last_error("host allocation failed");
+        return LEIDEN_ERR_OOM;
+    }
+    leiden_status st = sv->h.server_init(*p, max_vertices, max_entries, max_graphs, device_budget, stream);
+    if (st != LEIDEN_OK) {
+        delete sv;
+        return st;
+    }
+    *out = sv;
+    return LEIDEN_OK;
+}
+
+leiden_status leiden_server_submit(leiden_server_t s, int64_t n, int64_t nnz, const int64_t *offsets,
+                                   const int32_t *indices, const float *weights, int32_t where, int64_t *request_id) {
+    if (!s) {
+        lgb::set_last_error("NULL server");
+        return LEIDEN_ERR_INVALID;
+    }
+    return s->h.server_submit(n, nnz, offsets, indices, weights, where, request_id);
+}
+
+leiden_status leiden_server_step(leiden_server_t s, int32_t *finished) {
+    if (!s) {
+        lgb::set_last_error("NULL server");
+        return LEIDEN_ERR_INVALID;
+    }
+    return s->h.server_step(finished);
+}
+
+leiden_status leiden_server_next(leiden_server_t s, int64_t *request_id) {
+    if (!s) {
+        lgb::set_last_error("NULL server");
+        return LEIDEN_ERR_INVALID;
+    }
+    return s->h.server_next(request_id);
+}
+
+leiden_status leiden_server_result(leiden_server_t s, int64_t request_id, int32_t *membership, int32_t where,
+                                   double *modularity, int32_t *passes, int64_t *communities) {
+    if (!s) {
+        lgb::set_last_error("NULL server");
+        return LEIDEN_ERR_INVALID;
+    }
+    if (where != LEIDEN_HOST && where != LEIDEN_DEVICE) {
+        lgb::set_last_error("invalid where");
+        return LEIDEN_ERR_INVALID;
+    }
+    return s->h.server_result(request_id, membership, where, modularity, passes, communities);
+}
+
+leiden_status leiden_server_info(leiden_server_t s, leiden_server_state *out) {
+    if (!s) {
+        lgb::set_last_error("NULL server");
+        return LEIDEN_ERR_INVALID;
+    }
+    return s->h.server_info(out);
+}
+
+leiden_status leiden_server_destroy(leiden_server_t s) {
+    delete s;
+    return LEIDEN_OK;
 }
 
 leiden_status leiden_destroy(leiden_graph_t g) {

@@ -19,336 +19,13 @@
 #include <utility>
 #include <vector>
 
-#include "engine.h"
-#include "kernels.h"
+#include "engine_impl.h"
 
 namespace lgb {
 
 thread_local std::string g_last_error;
 void set_last_error(const std::string &s) { g_last_error = s; }
 const char *last_error() { return g_last_error.c_str(); }
-
-namespace {
-
-struct Scalars {  // device scalars, read back in one copy
-    int err;
-    int nonint;
-    unsigned long long vsum[2];
-    double two_m_f;
-    long long two_m_i;
-    double dq_f;
-    long long dq_i;
-    unsigned long long moved;
-    double wsum;
-    double msum[4];
-    int32_t maxdeg;
-    int32_t iters;
-    unsigned long long maxtdeg;
-};
-
-#define CK(x)                                                                              \
-    do {                                                                                   \
-        cudaError_t _e = (x);                                                              \
-        if (_e != cudaSuccess) {                                                           \
-            set_last_error(std::string(#x) + ": " + cudaGetErrorString(_e));              \
-            return (_e == cudaErrorMemoryAllocation) ? LEIDEN_ERR_OOM : LEIDEN_ERR_CUDA;   \
-        }                                                                                  \
-    } while (0)
-#define ST(x)                                  \
-    do {                                       \
-        leiden_status _s = (x);                \
-        if (_s != LEIDEN_OK) return _s;        \
-    } while (0)
-
-// graphs below this size fit in L2 and are swept without relabelling
-constexpr int64_t kRelabelMinVertices = 1 << 16;
-
-int ceil_log2_h(int64_t x) {
-    int b = 0;
-    while ((1LL << b) < x) ++b;
-    return b;
-}
-
-}  // namespace
-
-// State of one run (or one serving step) that the passes share.
-struct Run {
-    const leiden_params *prm = nullptr;
-    bool det = false, trace = false, profile = false, batch = false;
-    int32_t L = 0, B = 0, nsteps = 0, nkeys = 0, NG = 1;
-    leiden_stats st{};
-    std::vector<std::pair<cudaEvent_t, int>> marks;  // phase boundary events (phase id of the span that starts)
-    GraphView G;                  // current graph G'
-    int64_t Gcap = 0;             // entry capacity of G' (holey after aggregation)
-    int cur_agg = 1;              // the next aggregation writes agg[cur_agg ^ 1]
-    const int32_t *cur_gid = nullptr;  // graph of every vertex of G' (batches)
-    double tau = 0;
-    int passes = 0;
-    bool no_edges = false;
-};
-
-struct Handle::Impl {
-    int64_t n0 = 0, m0 = 0;
-    cudaStream_t s = nullptr;
-    int sm = 152;
-    bool nonint = false;
-    double wsum = 0;
-    // input CSR
-    int64_t *off0 = nullptr;
-    int32_t *idx0 = nullptr, *deg0 = nullptr;
-    float *w0 = nullptr;
-    // aggregated graphs (ping-pong)
-    struct Agg {
-        int64_t *off = nullptr;
-        int32_t *deg = nullptr, *idx = nullptr;
-        void *w = nullptr;
-        int64_t cap = 0;
-    } agg[2];
-    // per-vertex workspace
-    int32_t *C0 = nullptr, *Cp = nullptr, *CB = nullptr, *Cd = nullptr, *size = nullptr, *prop = nullptr,
-            *step = nullptr, *key = nullptr, *list = nullptr, *flag = nullptr, *members = nullptr, *cursor = nullptr,
-            *bnd = nullptr, *rep = nullptr, *label = nullptr, *minv = nullptr, *out = nullptr, *scnt = nullptr,
-            *slayer = nullptr, *sfcount = nullptr;
-    int64_t *pos = nullptr, *pos2 = nullptr, *coff = nullptr, *cnt = nullptr, *tdeg = nullptr, *key_cnt = nullptr,
-            *key_off = nullptr;
-    void *K = nullptr, *Sig = nullptr, *Kagg = nullptr, *scan_tmp = nullptr, *part_tmp = nullptr;
-    long long *gain = nullptr;
-    uint8_t *unproc = nullptr;
-    double *sigtot = nullptr;
-    Scalars *dsc = nullptr, *hsc = nullptr;
-    // hub tables
-    int32_t *hub_keys = nullptr;
-    void *hub_vals = nullptr;
-    size_t hub_bytes = 0;
-    int key_cap = 0;
-    std::vector<int64_t> hkey_off;
-    long long launches = 0;
-    // trace
-    std::map<std::pair<int, int>, std::vector<char>> trace;
-    std::map<std::pair<int, int>, int64_t> trace_count;
-    std::vector<void *> allocs;
-    // profiling (LEIDEN_FLAG_PROFILE)
-    unsigned long long *prof_cnt = nullptr;  // LEIDEN_PROFILE_CLASSES x kProfCounters
-    unsigned *bar = nullptr;                 // grid barrier of the persistent sweep kernel
-    long long *phase_dq = nullptr;           // per-sweep sums of a persistent phase
-    unsigned long long *phase_moved = nullptr;
-    int32_t phase_cap = 0;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    std::vector<std::pair<int, size_t>> prof_spans;  // (class, index of the start event)
-    std::vector<int64_t> prof_launches;
-    leiden_kernel_profile prof_out[LEIDEN_PROFILE_CLASSES];
-    bool prof_valid = false;
-    bool prof_det = false;
-    // batch of graphs (per-vertex graph ids only when G > 1)
-    int32_t G = 1;
-    std::vector<int64_t> hvseg0;           // vertex offsets of the graphs in the input
-    std::vector<double> hgw;               // weight sum of every graph (fp64)
-    int64_t *vseg0 = nullptr, *vseg = nullptr, *vseg2 = nullptr;  // G+1 each: input, this pass, next pass
-    int32_t *gid0 = nullptr, *gidA = nullptr, *gidB = nullptr, *rgid = nullptr;
-    int32_t *gstate = nullptr, *gdone = nullptr, *gli = nullptr, *glj = nullptr, *gpasses = nullptr;
-    int64_t *gkeep = nullptr, *gcomm = nullptr;
-    long long *gsumk = nullptr;            // per-graph sums of K (int64 or fp64 bits)
-    long long *gks = nullptr;              // per-graph key scale (int64 2m or fp32 1/2m)
-    double *g2m = nullptr, *gq = nullptr, *gmsum = nullptr;
-    unsigned *gactive = nullptr;
-    std::vector<int32_t> hpasses;          // per graph, after a run
-    std::vector<int64_t> hcomm;
-
-    leiden_status pass(Run &r, int32_t lp, bool &stop);
-    // brackets one profiled launch of class cls with events on the run's stream
-    unsigned long long *prof_begin(Run &r, int cls) {
-        if (!r.profile) return nullptr;
-        prof_spans.push_back({cls, ev_used});
-        cudaEventRecord(next_event(), s);
-        prof_launches[cls]++;
-        return prof_cnt + (size_t)cls * kProfCounters;
-    }
-    void prof_end(Run &r) {
-        if (r.profile) cudaEventRecord(next_event(), s);
-    }
-    // phase boundary for the per-phase times of the statistics
-    leiden_status mark(Run &r, int phase) {
-        cudaEvent_t e;
-        CK(cudaEventCreate(&e));
-        CK(cudaEventRecord(e, s));
-        r.marks.push_back({e, phase});
-        return LEIDEN_OK;
-    }
-    cudaEvent_t next_event() {
-        if (ev_used == ev_pool.size()) {
-            cudaEvent_t e;
-            cudaEventCreate(&e);
-            ev_pool.push_back(e);
-        }
-        return ev_pool[ev_used++];
-    }
-
-    ~Impl() {
-        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-        for (void *p : allocs) cudaFreeAsync(p, s);
-        if (hsc) cudaFreeHost(hsc);
-        cudaStreamSynchronize(s);
-    }
-    template <class T> leiden_status alloc(T **p, int64_t count) {
-        void *q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
-        if (e != cudaSuccess) {
-            set_last_error(std::string("device allocation of ") + std::to_string(count * (int64_t)sizeof(T)) +
-                           " bytes failed: " + cudaGetErrorString(e));
-            return LEIDEN_ERR_OOM;
-        }
-        allocs.push_back(q);
-        *p = static_cast<T *>(q);
-        return LEIDEN_OK;
-    }
-    leiden_status free_one(void *p) {
-        for (size_t i = 0; i < allocs.size(); ++i)
-            if (allocs[i] == p) {
-                cudaFreeAsync(p, s);
-                allocs.erase(allocs.begin() + i);
-                break;
-            }
-        return LEIDEN_OK;
-    }
-    leiden_status sync_scalars() {
-        CK(cudaMemcpyAsync(hsc, dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (hsc->err) {
-            const int code = hsc->err;
-            set_last_error(code == 3 ? "a grid barrier of the persistent sweep kernel timed out"
-                                     : "device error word " + std::to_string(code));
-            return code == 3 ? LEIDEN_ERR_TIMEOUT : LEIDEN_ERR_CUDA;
-        }
-        return LEIDEN_OK;
-    }
-    template <class T> void record(int pass, int what, const T *dev, int64_t count) {
-        std::vector<char> buf((size_t)count * sizeof(T));
-        if (count > 0) {
-            cudaMemcpyAsync(buf.data(), dev, buf.size(), cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
-        }
-        trace[{pass, what}] = std::move(buf);
-        trace_count[{pass, what}] = count;
-    }
-    leiden_status ensure_hub(int bits, int regions, bool det) {
-        const size_t per = ((size_t)1 << bits) * (sizeof(int32_t) + 8);
-        const size_t need = per * (size_t)regions;
-        if (need <= hub_bytes) return LEIDEN_OK;
-        if (hub_keys) free_one(hub_keys);
-        if (hub_vals) free_one(hub_vals);
-        hub_keys = nullptr;
-        hub_vals = nullptr;
-        hub_bytes = 0;
-        ST(alloc(&hub_keys, ((int64_t)1 << bits) * regions));
-        char *v = nullptr;
-        ST(alloc(&v, ((int64_t)1 << bits) * regions * 8));
-        hub_vals = v;
-        hub_bytes = need;
-        (void)det;
-        return LEIDEN_OK;
-    }
-    // Sum the event spans per class and turn the work counters into
-    // algorithmic bytes (element sizes of what each kernel reads and writes).
-    leiden_status finish_profile() {
-        std::vector<unsigned long long> c((size_t)LEIDEN_PROFILE_CLASSES * kProfCounters);
-        CK(cudaMemcpyAsync(c.data(), prof_cnt, c.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        std::memset(prof_out, 0, sizeof(prof_out));
-        for (auto &sp : prof_spans) {
-            float t = 0;
-            cudaEventElapsedTime(&t, ev_pool[sp.second], ev_pool[sp.second + 1]);
-            prof_out[sp.first].ms += t;
-        }
-        for (int k = 0; k < LEIDEN_PROFILE_CLASSES; ++k) {
-            const unsigned long long *v = &c[(size_t)k * kProfCounters];
-            leiden_kernel_profile &o = prof_out[k];
-            o.launches = prof_launches[k];
-            const int phase = k / 8;
-            if (phase < 2) {
-                o.items = (int64_t)v[0];
-                o.skipped = (int64_t)v[1];
-                o.edges = (int64_t)v[2];
-                o.distinct = (int64_t)v[3];
-                o.moved = (int64_t)v[4];
-                const double ksz = prof_det ? 8.0 : 4.0;  // K' is int64 or fp32
-                if (phase == 0)  // list, flag r/w, C, K, offset, degree, Sigma_d | idx, w, C[j] | Sigma_c | move
-                    o.bytes = (30.0 + ksz) * v[0] + 5.0 * v[1] + 12.0 * v[2] + 8.0 * v[3] + 28.0 * v[4] + 1.0 * v[5];
-                else  // + bound C'_B of i and of every neighbour, isolation test, proposal write
-                    o.bytes = (40.0 + ksz) * v[0] + 16.0 * v[1] + 16.0 * v[2] + 8.0 * v[3];
-            } else {
-                o.items = (int64_t)v[0];
-                o.edges = (int64_t)v[2];
-                o.moved = (int64_t)v[3];
-                o.skipped = 0;
-                o.distinct = (int64_t)v[3];
-                // community: list, offsets in/out, fill, K''; member: id, offset, degree;
-                // edge: idx, w, label; written entry: idx, w
-                o.bytes = 48.0 * v[0] + 16.0 * v[1] + 12.0 * v[2] + 8.0 * v[3];
-            }
-        }
-        prof_valid = true;
-        return LEIDEN_OK;
-    }
-    // relabelled copy of a pass's graph and arrays (asynchronous sweeps)
-    int64_t *roff = nullptr;
-    int32_t *rdeg = nullptr, *ridx = nullptr, *rinv = nullptr, *rC = nullptr, *rCB = nullptr, *rstep = nullptr,
-            *iota_list = nullptr;
-    void *rw = nullptr, *rK = nullptr;
-    int64_t rcap = -1;
-    leiden_status ensure_relabel(int64_t cap) {
-        if (!roff) {
-            if (G > 1) ST(alloc(&rgid, n0));
-            ST(alloc(&roff, n0 + 1));
-            for (int32_t **a : {&rdeg, &rinv, &rC, &rCB, &rstep}) ST(alloc(a, n0));
-            long long *k = nullptr;
-            ST(alloc(&k, n0));
-            rK = k;
-        }
-        if (cap > rcap) {
-            if (ridx) free_one(ridx);
-            if (rw) free_one(rw);
-            ridx = nullptr;
-            rw = nullptr;
-            ST(alloc(&ridx, cap));
-            int32_t *w = nullptr;
-            ST(alloc(&w, cap));
-            rw = w;
-            rcap = cap;
-        }
-        return LEIDEN_OK;
-    }
-    size_t part_tmp_bytes = 0;
-    leiden_status ensure_part_tmp(size_t bytes) {
-        if (bytes <= part_tmp_bytes) return LEIDEN_OK;
-        if (part_tmp) free_one(part_tmp);
-        part_tmp = nullptr;
-        part_tmp_bytes = 0;
-        char *p = nullptr;
-        ST(alloc(&p, (int64_t)bytes));
-        part_tmp = p;
-        part_tmp_bytes = bytes;
-        return LEIDEN_OK;
-    }
-    leiden_status ensure_agg(int x, int64_t cap) {
-        Agg &a = agg[x];
-        if (!a.off) {
-            ST(alloc(&a.off, n0 + 1));
-            ST(alloc(&a.deg, n0));
-        }
-        if (a.cap >= cap && a.idx) return LEIDEN_OK;
-        if (a.idx) free_one(a.idx);
-        if (a.w) free_one(a.w);
-        a.idx = nullptr;
-        a.w = nullptr;
-        ST(alloc(&a.idx, cap));
-        int32_t *w = nullptr;  // float or int32: 4 bytes either way
-        ST(alloc(&w, cap));
-        a.w = w;
-        a.cap = cap;
-        return LEIDEN_OK;
-    }
-};
 
 Handle::Handle() : p(new Impl) {}
 Handle::~Handle() { delete p; }
@@ -363,18 +40,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     q.G = num_graphs;
     if (vtx_seg) q.hvseg0.assign(vtx_seg, vtx_seg + num_graphs + 1);
     else q.hvseg0 = {0, n};
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&q.sm, cudaDevAttrMultiProcessorCount, dev));
-    {
-        cudaMemPool_t pool;
-        CK(cudaDeviceGetDefaultMemPool(&pool, dev));
-        uint64_t thr = UINT64_MAX;
-        CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-    }
-    CK(cudaMallocHost(&q.hsc, sizeof(Scalars)));
-    ST(q.alloc(&q.dsc, 1));
-    CK(cudaMemsetAsync(q.dsc, 0, sizeof(Scalars), q.s));
+    ST(q.init_device());
     ST(q.alloc(&q.off0, n + 1));
     ST(q.alloc(&q.idx0, nnz));
     ST(q.alloc(&q.w0, nnz));
@@ -386,48 +52,9 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
         if (weights) CK(cudaMemcpyAsync(q.w0, weights, sizeof(float) * nnz, kind, q.s));
         else CK(launch_fill_i32(reinterpret_cast<int32_t *>(q.w0), 0x3f800000, nnz, q.s));  // unit weights: 1.0f
     }
-    // workspace sized for the input graph (later graphs are smaller)
-    for (int32_t **a : {&q.C0, &q.Cp, &q.CB, &q.Cd, &q.size, &q.prop, &q.step, &q.key, &q.list, &q.flag, &q.members,
-                        &q.cursor, &q.bnd, &q.rep, &q.label, &q.minv, &q.out, &q.scnt, &q.slayer})
-        ST(q.alloc(a, n));
-    for (int64_t **a : {&q.pos, &q.pos2, &q.coff})
-        ST(q.alloc(a, n + 1));
-    for (int64_t **a : {&q.cnt, &q.tdeg})
-        ST(q.alloc(a, n));
-    long long *k1, *k2, *k3;
-    ST(q.alloc(&k1, n));
-    ST(q.alloc(&k2, n));
-    ST(q.alloc(&k3, n));
-    q.K = k1;
-    q.Sig = k2;
-    q.Kagg = k3;
-    ST(q.alloc(&q.gain, n));
-    ST(q.alloc(&q.unproc, n));
-    ST(q.alloc(&q.sigtot, n));
-    char *tmp;
-    ST(q.alloc(&tmp, (int64_t)scan_tmp_bytes((n > num_graphs ? n : num_graphs) + 8192)));
-    q.scan_tmp = tmp;
-    ST(q.ensure_part_tmp(partition_tmp_bytes(n, (32 - 1 + 16) * kNumBins + 1)));  // default schedule
-    ST(q.alloc(&q.prof_cnt, (int64_t)LEIDEN_PROFILE_CLASSES * kProfCounters));
-    ST(q.alloc(&q.bar, 2));
-    CK(cudaMemsetAsync(q.bar, 0, 2 * sizeof(unsigned), q.s));
-    q.key_cap = 8192;
-    ST(q.alloc(&q.key_cnt, q.key_cap));
-    ST(q.alloc(&q.key_off, q.key_cap + 1));
-    ST(q.alloc(&q.sfcount, 4096 + 1));
-    ST(q.alloc(&q.iota_list, n));
-    CK(launch_iota(q.iota_list, n, q.s));
+    ST(q.alloc_workspace(n, num_graphs));
     CK(launch_degrees(q.off0, q.deg0, n, &q.dsc->err, q.s));
-    // per-graph state (one graph: G = 1, no graph ids)
     const int32_t G = q.G;
-    for (int64_t **a : {&q.vseg0, &q.vseg, &q.vseg2}) ST(q.alloc(a, G + 1));
-    for (int32_t **a : {&q.gstate, &q.gdone, &q.gli, &q.glj, &q.gpasses}) ST(q.alloc(a, G));
-    for (int64_t **a : {&q.gkeep, &q.gcomm}) ST(q.alloc(a, G));
-    ST(q.alloc(&q.gsumk, G));
-    ST(q.alloc(&q.gks, G));
-    ST(q.alloc(&q.g2m, G));
-    ST(q.alloc(&q.gq, G));
-    ST(q.alloc(&q.gmsum, 3 * (int64_t)G));
     CK(cudaMemcpyAsync(q.vseg0, q.hvseg0.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, q.s));
     if (G > 1) {
         for (int32_t **a : {&q.gid0, &q.gidA, &q.gidB}) ST(q.alloc(a, n));
@@ -475,7 +102,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     const leiden_params &prm = *r.prm;
     const bool det = r.det, trace = r.trace, batch = r.batch;
     const int32_t L = r.L, B = r.B, nsteps = r.nsteps, nkeys = r.nkeys, NG = r.NG;
-    const int64_t n0 = q.n0;
+    const int64_t n0 = r.n0;
     const int tile_blocks = q.sm * 8, big_blocks = q.sm * 2;
     GraphView &G = r.G;
     int64_t &Gcap = r.Gcap;
@@ -512,7 +139,8 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     q.launches += 1;
     // schedule and (step, bin) lists
     SchedWork sw{q.scnt, q.slayer, q.sfcount};
-    CK(launch_schedule(G, prm.seed + (uint64_t)lp, L, B, sw, q.step, s, cur_gid, batch ? q.vseg : nullptr));
+    CK(launch_schedule(G, prm.seed + (r.gpass ? 0 : (uint64_t)lp), L, B, sw, q.step, s, cur_gid,
+                       batch ? q.vseg : nullptr, r.gpass));
     q.launches += L > 1 ? L : 2;
     // one vertex list per (schedule step, degree bin), step-major
     CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
@@ -533,7 +161,8 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     }
     passes++;
     // C' and Sigma' at the start of local-moving (reading R3)
-    if (lp == 0) CK(launch_iota(q.Cp, n, s));
+    if (r.n_cont >= 0) CK(launch_init_labels(q.label, r.n_cont, n, q.Cp, s));
+    else if (lp == 0) CK(launch_iota(q.Cp, n, s));
     else CK(cudaMemcpyAsync(q.Cp, q.label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     if (trace) q.record(lp, 1, q.Cp, n);
     // Sweep space. On request (LEIDEN_FLAG_RELABEL) the asynchronous
@@ -619,6 +248,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     sc.g2m = q.g2m;
     sc.gdone = q.gdone;
     sc.gactive = q.gactive;
+    sc.gtau = r.gtau;
     sc.G = NG;
     const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
     // one sweep as per-(step, bin) launches (fallback and test path)
@@ -749,7 +379,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     // the graphs that go on keep their refined communities, densely
     // renumbered after those of the graphs before them
     CK(launch_graph_stop(q.vseg, q.pos, q.pos2, q.gli, q.g2m, prm.aggregation_tolerance, NG, q.gstate, q.gkeep,
-                         q.gpasses, s));
+                         q.gpasses, s, r.gpass, r.graph_max_passes));
     CK(launch_exclusive_scan(q.gkeep, q.vseg2, NG, q.scan_tmp, s));
     q.launches += 14;
     int64_t counts[3];
@@ -789,9 +419,9 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     CK(launch_exclusive_scan(q.cnt, q.coff, ncomm, q.scan_tmp, s));
     CK(cudaMemsetAsync(q.cursor, 0, sizeof(int32_t) * ncomm, s));
     CK(launch_comm_fill(q.Cd, n, q.coff, q.cursor, q.members, s));
-    if (!q.agg[dst].off) {
-        ST(q.alloc(&q.agg[dst].off, n0 + 1));
-        ST(q.alloc(&q.agg[dst].deg, n0));
+    if (!q.agg[dst].off) {  // sized for the largest graph the handle takes
+        ST(q.alloc(&q.agg[dst].off, q.n0 + 1));
+        ST(q.alloc(&q.agg[dst].deg, q.n0));
     }
     CK(launch_exclusive_scan(q.tdeg, q.agg[dst].off, ncomm, q.scan_tmp, s));
     CK(launch_comm_bin_keys(q.tdeg, ncomm, q.key, s));
@@ -931,18 +561,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         return LEIDEN_ERR_UNSUPPORTED;
     }
     ST(q.ensure_part_tmp(partition_tmp_bytes(q.n0, nkeys + 1)));
-    if (prm.max_iterations > q.phase_cap) {  // per-sweep sums: max_iterations x G
-        if (q.phase_dq) q.free_one(q.phase_dq);
-        if (q.phase_moved) q.free_one(q.phase_moved);
-        if (q.gactive) q.free_one(q.gactive);
-        q.phase_dq = nullptr;
-        q.phase_moved = nullptr;
-        q.gactive = nullptr;
-        ST(q.alloc(&q.phase_dq, (int64_t)prm.max_iterations * NG));
-        ST(q.alloc(&q.phase_moved, (int64_t)prm.max_iterations * NG));
-        ST(q.alloc(&q.gactive, prm.max_iterations));
-        q.phase_cap = prm.max_iterations;
-    }
+    ST(q.ensure_phase(prm.max_iterations, NG));
     if (det) {
         if (prm.resolution != 1.0 || q.nonint) {
             set_last_error("deterministic mode needs integer weights and resolution 1");
@@ -1001,6 +620,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(cudaMemsetAsync(q.gpasses, 0, sizeof(int32_t) * NG, s));
         CK(cudaStreamSynchronize(s));  // st0 is a local
     }
+    r.n0 = n0;
     r.cur_gid = batch ? q.gid0 : nullptr;  // graph of every vertex of G'
     r.G.n = n0;
     r.G.off = q.off0;

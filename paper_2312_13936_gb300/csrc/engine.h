@@ -28,11 +28,24 @@ class Handle {
     int32_t num_graphs() const;
     // per-graph passes and communities of the last run (host arrays)
     leiden_status graph_info(int32_t *passes, int64_t *communities) const;
+    // serving (continuous batching): capacity for the graphs in flight; a
+    // step admits waiting graphs at the pass boundary and runs one pass of
+    // every graph in flight
+    leiden_status server_init(const leiden_params &p, int64_t max_vertices, int64_t max_entries, int32_t max_graphs,
+                              int64_t device_budget, void *stream);
+    leiden_status server_submit(int64_t n, int64_t nnz, const int64_t *off, const int32_t *idx, const float *w,
+                                int where, int64_t *id);
+    leiden_status server_step(int32_t *finished);
+    leiden_status server_next(int64_t *id);
+    leiden_status server_result(int64_t id, int32_t *membership, int where, double *q, int32_t *passes,
+                                int64_t *communities);
+    leiden_status server_info(leiden_server_state *out) const;
     leiden_status trace_get(int pass, int what, void *dst, int64_t *count) const;
     leiden_status profile_get(leiden_kernel_profile *out) const;
 
+    struct Impl;  // device state (engine_impl.h)
+
   private:
-    struct Impl;
     Impl *p;
 };
 

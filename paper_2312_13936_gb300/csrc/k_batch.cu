@@ -92,7 +92,7 @@ __global__ void k_phase_init(const int32_t *state, int32_t G, int32_t *gdone, in
 
 __global__ void k_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                              const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
-                             int32_t *passes) {
+                             int32_t *passes, const int32_t *gpass, int32_t max_passes) {
     GRID_STRIDE(g, G) {
         if (state[g] != kGraphActive) {
             keep[g] = 0;
@@ -103,7 +103,8 @@ __global__ void k_graph_stop(const int64_t *vseg, const int64_t *pos, const int6
         const int64_t ncomm = pos[b] - pos[a], nbound = pos2[b] - pos2[a];
         const bool stop = !(g2m[g] > 0)                              // reading R12: no edges
                           || (li[g] <= 1 && nbound == ncomm)         // globally converged (R5')
-                          || (double)ncomm / (double)(b - a) > agg_tol;  // low shrink (R4)
+                          || (double)ncomm / (double)(b - a) > agg_tol   // low shrink (R4)
+                          || (gpass && gpass[g] + 1 >= max_passes);   // its MAX_PASSES
         if (stop) {
             state[g] = kGraphFinishing;
             keep[g] = 0;
@@ -141,6 +142,33 @@ __global__ void k_finalize_batch(int32_t *C0, const int32_t *gid0, const int64_t
 
 __global__ void k_commit_states(int32_t *state, int32_t G) {
     GRID_STRIDE(g, G) if (state[g] == kGraphFinishing) state[g] = kGraphFinished;
+}
+
+__global__ void k_init_labels(const int32_t *label, int64_t n_cont, int64_t n, int32_t *Cp) {
+    GRID_STRIDE(v, n) Cp[v] = v < n_cont ? label[v] : (int32_t)v;
+}
+
+// one thread per row of the appended graph
+__global__ void k_append_graph(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int64_t v0,
+                               int64_t e0, bool w_int, int32_t g, int64_t *out_off, int32_t *out_deg,
+                               int32_t *out_idx, float *out_wf, int32_t *out_wi, int32_t *gid, int32_t *C0,
+                               int64_t a0) {
+    GRID_STRIDE(i, n) {
+        const int64_t a = off[i], b = off[i + 1];
+        out_off[v0 + i] = e0 + a;
+        out_deg[v0 + i] = (int32_t)(b - a);
+        for (int64_t e = a; e < b; ++e) {
+            out_idx[e0 + e] = (int32_t)(v0 + idx[e]);
+            if (w_int) out_wi[e0 + e] = (int32_t)w[e];
+            else out_wf[e0 + e] = w[e];
+        }
+        gid[v0 + i] = g;
+        C0[a0 + i] = (int32_t)(v0 + i);
+    }
+}
+
+__global__ void k_shift_labels(const int32_t *src, int64_t n, int64_t off, int32_t *dst) {
+    GRID_STRIDE(v, n) dst[v] = (int32_t)(src[v] - off);
 }
 
 __global__ void k_graph_counts(const int64_t *pos, const int64_t *vseg, int32_t G, int64_t *out) {
@@ -245,9 +273,10 @@ cudaError_t launch_phase_init(const int32_t *state, int32_t G, int32_t *gdone, i
 }
 cudaError_t launch_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                               const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
-                              int32_t *passes, cudaStream_t s) {
+                              int32_t *passes, cudaStream_t s, const int32_t *gpass, int32_t max_passes) {
     if (G <= 0) return cudaSuccess;
-    k_graph_stop<<<grid_for(G, 256), 256, 0, s>>>(vseg, pos, pos2, li, g2m, agg_tol, G, state, keep, passes);
+    k_graph_stop<<<grid_for(G, 256), 256, 0, s>>>(vseg, pos, pos2, li, g2m, agg_tol, G, state, keep, passes, gpass,
+                                                  max_passes);
     return cudaGetLastError();
 }
 cudaError_t launch_renumber_batch(const int32_t *C, const int64_t *pos, const int32_t *gid, const int64_t *vseg,
@@ -272,6 +301,26 @@ cudaError_t launch_finalize_batch(int32_t *C0, const int32_t *gid0, const int64_
 cudaError_t launch_commit_states(int32_t *state, int32_t G, cudaStream_t s) {
     if (G <= 0) return cudaSuccess;
     k_commit_states<<<grid_for(G, 256), 256, 0, s>>>(state, G);
+    return cudaGetLastError();
+}
+cudaError_t launch_init_labels(const int32_t *label, int64_t n_cont, int64_t n, int32_t *Cp, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_init_labels<<<grid_for(n, 256), 256, 0, s>>>(label, n_cont, n, Cp);
+    return cudaGetLastError();
+}
+cudaError_t launch_append_graph(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int64_t v0,
+                                int64_t e0, bool w_int, int32_t g, int64_t *out_off, int32_t *out_deg,
+                                int32_t *out_idx, void *out_w, int32_t *gid, int32_t *C0, int64_t a0,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_append_graph<<<grid_for(n, 256), 256, 0, s>>>(n, off, idx, w, v0, e0, w_int, g, out_off, out_deg, out_idx,
+                                                    static_cast<float *>(out_w), static_cast<int32_t *>(out_w),
+                                                    gid, C0, a0);
+    return cudaGetLastError();
+}
+cudaError_t launch_shift_labels(const int32_t *src, int64_t n, int64_t off, int32_t *dst, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_shift_labels<<<grid_for(n, 256), 256, 0, s>>>(src, n, off, dst);
     return cudaGetLastError();
 }
 cudaError_t launch_graph_counts(const int64_t *pos, const int64_t *vseg, int32_t G, int64_t *out, cudaStream_t s) {

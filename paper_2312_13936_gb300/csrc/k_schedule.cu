@@ -6,7 +6,8 @@
 // when the last of them is released in round r. Rounds stop at layer L-2;
 // every vertex not placed by then takes step L-1 + ((prio >> 32) mod B).
 // In a batch of graphs a vertex's priority is drawn at its index inside its
-// own graph, so every graph gets the schedule it would get alone.
+// own graph (and, when graphs are at different passes, from the state of its
+// own graph's pass), so every graph gets the schedule it would get alone.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -17,18 +18,24 @@ namespace {
 __device__ __forceinline__ int64_t graph_base(const int32_t *gid, const int64_t *vseg, int64_t v) {
     return gid ? __ldg(&vseg[__ldg(&gid[v])]) : 0;
 }
+// generator state of v's graph: the pass state, advanced by the graph's own
+// pass index when graphs are at different passes
+__device__ __forceinline__ uint64_t graph_state(uint64_t state, const int32_t *gid, const int32_t *gpass, int64_t v) {
+    return gpass ? state + (uint64_t)__ldg(&gpass[__ldg(&gid[v])]) : state;
+}
 
 // cnt[v] = number of v's preceding neighbours; layer[v] = 0 if none.
 // settled[0] counts the layer-0 vertices.
 __global__ void __launch_bounds__(256) k_sched_init(int64_t n, const int64_t *off, const int32_t *deg,
-                                                    const int32_t *idx, uint64_t state, const int32_t *gid,
-                                                    const int64_t *vseg, int32_t *cnt, int32_t *layer,
-                                                    int32_t *settled) {
+                                                    const int32_t *idx, uint64_t state0, const int32_t *gid,
+                                                    const int64_t *vseg, const int32_t *gpass, int32_t *cnt,
+                                                    int32_t *layer, int32_t *settled) {
     __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t base = graph_base(gid, vseg, v);
+        const uint64_t state = graph_state(state0, gid, gpass, v);
         const uint64_t pv = splitmix64_at(state, (uint64_t)(v - base));
         const int64_t e0 = off[v];
         const int32_t dv = deg[v];
@@ -50,9 +57,9 @@ __global__ void __launch_bounds__(256) k_sched_init(int64_t n, const int64_t *of
 // round scans the layer array, so layer-r vertices are visited in id order;
 // it returns at once when layer r is empty (settled[r] == 0).
 __global__ void __launch_bounds__(256) k_sched_round(int64_t n, const int64_t *off, const int32_t *deg,
-                                                     const int32_t *idx, uint64_t state, const int32_t *gid,
-                                                     const int64_t *vseg, int32_t r, int32_t *cnt, int32_t *layer,
-                                                     int32_t *settled) {
+                                                     const int32_t *idx, uint64_t state0, const int32_t *gid,
+                                                     const int64_t *vseg, const int32_t *gpass, int32_t r,
+                                                     int32_t *cnt, int32_t *layer, int32_t *settled) {
     if (__ldcg(&settled[r]) == 0) return;
     __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
@@ -60,6 +67,7 @@ __global__ void __launch_bounds__(256) k_sched_round(int64_t n, const int64_t *o
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         if (__ldcg(&layer[v]) != r) continue;
         const int64_t base = graph_base(gid, vseg, v);
+        const uint64_t state = graph_state(state0, gid, gpass, v);
         const uint64_t pv = splitmix64_at(state, (uint64_t)(v - base));
         const int64_t e0 = off[v];
         const int32_t dv = deg[v];
@@ -76,14 +84,14 @@ __global__ void __launch_bounds__(256) k_sched_round(int64_t n, const int64_t *o
     if (threadIdx.x == 0 && s_cnt) atomicAdd(&settled[r + 1], s_cnt);
 }
 
-__global__ void k_sched_finish(int64_t n, uint64_t state, int32_t L, int32_t B, const int32_t *gid,
-                               const int64_t *vseg, const int32_t *layer, int32_t *step) {
+__global__ void k_sched_finish(int64_t n, uint64_t state0, int32_t L, int32_t B, const int32_t *gid,
+                               const int64_t *vseg, const int32_t *gpass, const int32_t *layer, int32_t *step) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t l = layer[v];
         if (l >= 0 && l < L - 1) {
             step[v] = l;
         } else {
-            const uint64_t p = splitmix64_at(state, (uint64_t)(v - graph_base(gid, vseg, v)));
+            const uint64_t p = splitmix64_at(graph_state(state0, gid, gpass, v), (uint64_t)(v - graph_base(gid, vseg, v)));
             step[v] = L - 1 + (int32_t)((p >> 32) % (uint64_t)B);
         }
     }
@@ -107,16 +115,18 @@ inline int grid_for(int64_t items, int per_block) {
 }  // namespace
 
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
-                            int32_t *step, cudaStream_t s, const int32_t *gid, const int64_t *vseg) {
+                            int32_t *step, cudaStream_t s, const int32_t *gid, const int64_t *vseg,
+                            const int32_t *gpass) {
     if (g.n <= 0) return cudaSuccess;
     const int grid = grid_for(g.n, 256);
     cudaError_t e = cudaMemsetAsync(w.settled, 0, sizeof(int32_t) * (L + 1), s);
     if (e != cudaSuccess) return e;
-    k_sched_init<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, gid, vseg, w.cnt, w.layer, w.settled);
+    k_sched_init<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, gid, vseg, gpass, w.cnt, w.layer,
+                                      w.settled);
     for (int32_t r = 0; r + 2 <= L - 1; ++r)  // produce layers 1 .. L-2
-        k_sched_round<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, gid, vseg, r, w.cnt, w.layer,
+        k_sched_round<<<grid, 256, 0, s>>>(g.n, g.off, g.deg, g.idx, state, gid, vseg, gpass, r, w.cnt, w.layer,
                                             w.settled);
-    k_sched_finish<<<grid, 256, 0, s>>>(g.n, state, L, B, gid, vseg, w.layer, step);
+    k_sched_finish<<<grid, 256, 0, s>>>(g.n, state, L, B, gid, vseg, gpass, w.layer, step);
     return cudaGetLastError();
 }
 cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,

@@ -75,6 +75,7 @@ template <class P, class W> struct SV {
     int32_t *gdone;
     int32_t *giters;
     unsigned *gactive;
+    const double *gtau;
     int32_t G;
 };
 
@@ -134,6 +135,7 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.gdone = c.gdone;
     a.giters = c.giters;
     a.gactive = c.gactive;
+    a.gtau = c.gtau;
     a.G = c.G;
     return a;
 }
@@ -802,7 +804,8 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                     const double tm = a.g2m[g];
                     const double sum = (double)ldm(&sm.dq[g]);
                     // a graph without edges (2m = 0) has nothing to move
-                    sg = !(tm > 0) || (P::det ? 2.0 * sum / (tm * tm) : 2.0 * sum / tm) <= a.tau;
+                    const double tau = a.gtau ? a.gtau[g] : a.tau;
+                    sg = !(tm > 0) || (P::det ? 2.0 * sum / (tm * tm) : 2.0 * sum / tm) <= tau;
                 }
                 if (sg) {
                     a.gdone[g] = 1;

@@ -80,6 +80,7 @@ struct SweepCtx {
     const double *g2m = nullptr;   // per-graph 2m, for the convergence test
     int32_t *gdone = nullptr;      // per-graph "phase converged" flags (1 = skip its vertices)
     int32_t *giters = nullptr;     // per-graph sweeps executed in the phase
+    const double *gtau = nullptr;  // per-graph tolerance (graphs at different passes), or tau for all
     unsigned *gactive = nullptr;   // per sweep: graphs still running after it (max_it, zeroed)
     int32_t G = 1;                 // dq_arr and moved_arr hold max_it x G sums
 };
@@ -148,10 +149,11 @@ struct SchedWork {
     int32_t *cnt, *layer;  // n each
     int32_t *settled;      // L+1: vertices placed in each layer
 };
-// (gid, vseg: a batch of graphs, priorities drawn at indices inside each graph)
+// (gid, vseg: a batch of graphs, priorities drawn at indices inside each
+// graph; gpass: graphs at different passes, state + gpass[g] for graph g)
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
                             int32_t *step, cudaStream_t s, const int32_t *gid = nullptr,
-                            const int64_t *vseg = nullptr);
+                            const int64_t *vseg = nullptr, const int32_t *gpass = nullptr);
 // key[i] = step*kNumBins + bin (step-major: one list per step and bin), or
 // bin*nsteps + step (bin-major: one step-ordered list per bin); vertices
 // without edges get key nsteps*kNumBins (a trailing bucket)
@@ -177,10 +179,24 @@ cudaError_t launch_phase_init(const int32_t *state, int32_t G, int32_t *gdone, i
 // stop tests of Algorithm 1 per graph (readings R4, R5', R12): from the scans
 // pos (refined labels) and pos2 (bound labels), li and the aggregation
 // tolerance; active graphs that stop become finishing; keep[g] = refined
-// communities of the graphs that go on (0 otherwise); passes[g]++ for active graphs
+// communities of the graphs that go on (0 otherwise); passes[g]++ for active
+// graphs. With gpass (graphs at different passes) a graph also stops when
+// gpass[g] + 1 reaches max_passes.
 cudaError_t launch_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                               const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
-                              int32_t *passes, cudaStream_t s);
+                              int32_t *passes, cudaStream_t s, const int32_t *gpass = nullptr,
+                              int32_t max_passes = 0);
+// C' at the start of local-moving: the first n_cont vertices continue with
+// their move-based labels, the others start as singletons
+cudaError_t launch_init_labels(const int32_t *label, int64_t n_cont, int64_t n, int32_t *Cp, cudaStream_t s);
+// append graph g (n rows of a CSR with local indices and fp32 weights) to the
+// holey CSR of a union at row v0 and entry e0: out_off/out_deg/out_idx (ids
+// + v0)/out_w (fp32, or int32 when w_int), gid[v0+i] = g, and the
+// dendrogram of its vertices C0[a0+i] = v0+i
+cudaError_t launch_append_graph(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int64_t v0,
+                                int64_t e0, bool w_int, int32_t g, int64_t *out_off, int32_t *out_deg,
+                                int32_t *out_idx, void *out_w, int32_t *gid, int32_t *C0, int64_t a0,
+                                cudaStream_t s);
 // dense ids of the next graph: Cd[i] = vseg2[g] + pos[C[i]] - pos[vseg[g]]
 // for graphs that go on, -1 for graphs that stop
 cudaError_t launch_renumber_batch(const int32_t *C, const int64_t *pos, const int32_t *gid, const int64_t *vseg,
@@ -196,6 +212,8 @@ cudaError_t launch_finalize_batch(int32_t *C0, const int32_t *gid0, const int64_
                                   const int32_t *state, int64_t n0, cudaStream_t s);
 // finishing -> finished
 cudaError_t launch_commit_states(int32_t *state, int32_t G, cudaStream_t s);
+// dst[v] = src[v] - off (a graph's dendrogram ids into its own range)
+cudaError_t launch_shift_labels(const int32_t *src, int64_t n, int64_t off, int32_t *dst, cudaStream_t s);
 // out[g] = pos[vseg[g+1]] - pos[vseg[g]]
 cudaError_t launch_graph_counts(const int64_t *pos, const int64_t *vseg, int32_t G, int64_t *out, cudaStream_t s);
 // graph of every super-vertex: gid2[Cd[i]] = gid[i] (Cd >= 0)

@@ -1,0 +1,163 @@
+"""GPU tests of the served form: continuous batching (leiden_server_*).
+
+Graphs are submitted while others are in flight; each step admits waiting
+graphs at the pass boundary and runs one pass of every graph in flight.
+Deterministic mode: every graph's result (membership, passes, communities,
+modularity) is bit-exact the single-graph result of leiden_run, whatever it
+was mixed with. Asynchronous mode: every community connected, reported
+modularity equal to the recomputation, and mean modularity within 0.005 of
+the graphs run alone (each graph within 0.04; see the batched-form tests).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import paper_2312_13936_gb300 as lg
+from tests._gpu import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def serve_mix():
+    b = gen.sbm_batch(16, seed=21, nmin=50, nmax=4000)
+    graphs = [b.graph(g) for g in range(b.num_graphs)]
+    graphs.insert(2, gen.ring_of_cliques(5, 8))
+    graphs.insert(5, gen.road(40))
+    graphs.insert(6, gen.from_edges(4, [], []))
+    graphs.insert(8, gen.from_edges(0, [], []))
+    graphs.insert(11, gen.from_edges(1, [0], [0], [2.0]))
+    graphs.append(gen.rmat(11, 8, seed=5))
+    return graphs
+
+
+def serve(graphs, mode, arrivals_per_step=3, **kw):
+    """Submit a few graphs before every step (so later graphs join graphs
+    already in flight) and run steps until everything finished."""
+    cap_v = max(1, sum(g.n for g in graphs))
+    cap_e = max(1, sum(g.nnz for g in graphs))
+    srv = lg.LeidenServer(cap_v, cap_e, max_graphs=len(graphs) + 1, mode=mode, **kw)
+    ids, res = [], {}
+    k = 0
+    steps = 0
+    try:
+        while k < len(graphs) or len(res) < len(graphs):
+            for _ in range(arrivals_per_step):
+                if k < len(graphs):
+                    g = graphs[k]
+                    ids.append(srv.submit(g.offsets, g.indices, g.weights))
+                    k += 1
+            srv.step()
+            steps += 1
+            for rid, memb, q, passes, comm in srv.results():
+                res[rid] = (memb, q, passes, comm)
+            assert steps < 1000
+        info = srv.info()
+    finally:
+        srv.close()
+    return [res[i] for i in ids], info, steps
+
+
+def test_serve_deterministic_same_alone_and_in_mix():
+    graphs = serve_mix()
+    out, info, steps = serve(graphs, lg.LEIDEN_DETERMINISTIC)
+    assert info["in_flight"] == 0 and info["waiting"] == 0 and info["finished"] == 0
+    assert info["device_bytes"] == 0
+    assert steps > 3
+    for g, (G, (memb, q, passes, comm)) in enumerate(zip(graphs, out)):
+        ms, qs, sts, _ = run_gpu(G, lg.LEIDEN_DETERMINISTIC)
+        assert np.array_equal(memb, ms), g
+        assert abs(q - qs) <= 1e-12 * max(1.0, abs(qs)), (g, q, qs)
+        if G.n > 0:
+            assert passes == sts.passes, (g, passes, sts.passes)
+            assert comm == sts.communities
+
+
+def test_serve_deterministic_matches_oracle():
+    graphs = serve_mix()[:8]
+    out, _, _ = serve(graphs, lg.LEIDEN_DETERMINISTIC, arrivals_per_step=2)
+    for g, G in enumerate(graphs):
+        ref = oracle.leiden(G, mode=oracle.SYNC)
+        assert np.array_equal(out[g][0], ref.membership), g
+
+
+def test_serve_deterministic_limits():
+    graphs = serve_mix()[:10]
+    for kw in ({"max_passes": 2}, {"max_iterations": 3}, {"schedule_layers": 5, "schedule_buckets": 2, "seed": 3}):
+        out, _, _ = serve(graphs, lg.LEIDEN_DETERMINISTIC, arrivals_per_step=4, **kw)
+        for g, G in enumerate(graphs):
+            ms = run_gpu(G, lg.LEIDEN_DETERMINISTIC, **kw)[0]
+            assert np.array_equal(out[g][0], ms), (kw, g)
+
+
+def test_serve_async_quality():
+    graphs = serve_mix()
+    out, _, _ = serve(graphs, lg.LEIDEN_ASYNC)
+    alone = []
+    for g, (G, (memb, q, passes, comm)) in enumerate(zip(graphs, out)):
+        assert oracle.disconnected(G, memb)[0] == 0, g
+        q_re = oracle.modularity(G, memb)
+        assert abs(q - q_re) <= 1e-9 * max(1.0, abs(q_re)), g
+        qa = run_gpu(G, lg.LEIDEN_ASYNC)[1]
+        assert abs(q - qa) <= 0.04, (g, q, qa)
+        alone.append(qa)
+    assert abs(np.mean([o[1] for o in out]) - np.mean(alone)) <= 0.005
+
+
+def test_serve_admission_waits_for_capacity():
+    # room for two graphs in flight and a device budget of about one graph:
+    # the others wait (on the host) and still come out exact
+    graphs = [gen.sbm(800, 6, 0.05, 0.003, seed=s) for s in range(6)]
+    cap_v = 2 * max(g.n for g in graphs)
+    cap_e = 2 * max(g.nnz for g in graphs)
+    budget = 20 * (graphs[0].n + graphs[0].nnz)
+    srv = lg.LeidenServer(cap_v, cap_e, max_graphs=2, device_budget=budget, mode=lg.LEIDEN_DETERMINISTIC)
+    try:
+        ids = [srv.submit(g.offsets, g.indices, g.weights) for g in graphs]
+        info = srv.info()
+        assert info["waiting"] == len(graphs) and info["in_flight"] == 0
+        res = {}
+        peak = 0
+        for _ in range(200):
+            srv.step()
+            peak = max(peak, srv.info()["in_flight"])
+            for rid, memb, q, passes, comm in srv.results():
+                res[rid] = memb
+            if len(res) == len(graphs):
+                break
+        assert peak <= 2
+        for rid, G in zip(ids, graphs):
+            assert np.array_equal(res[rid], run_gpu(G, lg.LEIDEN_DETERMINISTIC)[0])
+        assert srv.info()["device_bytes"] == 0
+        # a graph larger than the capacity is refused
+        big = gen.sbm(cap_v + 1, 4, 0.01, 0.001, seed=1)
+        with pytest.raises(lg.LeidenError) as e:
+            srv.submit(big.offsets, big.indices, big.weights)
+        assert e.value.status == -1
+    finally:
+        srv.close()
+
+
+def test_serve_rejects_bad_graphs():
+    g = gen.ring_of_cliques(4, 5)
+    srv = lg.LeidenServer(1000, 10000, mode=lg.LEIDEN_DETERMINISTIC)
+    try:
+        w = g.weights.copy()
+        w[0] = 2.0
+        with pytest.raises(lg.LeidenError) as e:
+            srv.submit(g.offsets, g.indices, w)
+        assert e.value.status == -2
+        with pytest.raises(lg.LeidenError) as e:
+            srv.submit(g.offsets, g.indices, g.weights * 0.5)
+        assert e.value.status == -6
+        # the server still works afterwards
+        rid = srv.submit(g.offsets, g.indices, g.weights)
+        for _ in range(50):
+            srv.step()
+            r = srv.results()
+            if r:
+                break
+        assert r[0][0] == rid and np.array_equal(r[0][1], run_gpu(g, lg.LEIDEN_DETERMINISTIC)[0])
+        assert srv.info()["device_bytes"] == 0
+    finally:
+        srv.close()
