@@ -315,34 +315,59 @@ def served_form(args, mode, flags):
     cap_v = max(g.n for g in pool) * 4
     cap_e = max(g.nnz for g in pool) * 4
     srv = lg.LeidenServer(cap_v, cap_e, max_graphs=256, mode=mode)
+    max_steps = 100_000  # every loop below ends: graphs finish within MAX_PASSES steps of admission
+
+    def drain(count):
+        got = 0
+        for _ in range(max_steps):
+            if got >= count:
+                return
+            srv.step()
+            got += len(srv.results())
+        raise RuntimeError("server made no progress")
     for g in pool[:2]:  # warm-up
         srv.submit(g.offsets, g.indices, g.weights)
-    while len(srv.results()) < 2:
-        srv.step()
+    drain(2)
     lat, qs, steps = {}, {}, 0
     ids = {}
     t0 = time.perf_counter()
     k = 0
     while len(lat) < R:
+        if steps > max_steps:
+            raise RuntimeError("server made no progress")
         now = time.perf_counter() - t0
         while k < R and arrive[k] <= now:
             g = pool[order[k]]
             ids[srv.submit(g.offsets, g.indices, g.weights)] = k
             k += 1
         info = srv.info()
-        if info["in_flight"] == 0 and info["waiting"] == 0:
-            if k < R:
-                time.sleep(max(0.0, arrive[k] - (time.perf_counter() - t0)))
+        if info["in_flight"] == 0 and info["waiting"] == 0 and info["finished"] == 0:
+            if k >= R:
+                raise RuntimeError("requests lost by the server")
+            time.sleep(max(0.0, arrive[k] - (time.perf_counter() - t0)))
             continue
-        srv.step()
-        steps += 1
+        if info["in_flight"] or info["waiting"]:
+            srv.step()
+            steps += 1
         for rid, memb, q, passes, comm in srv.results():
             j = ids.pop(rid)
             lat[j] = time.perf_counter() - t0 - arrive[j]
             qs[j] = q
     cb = summary([lat[j] for j in range(R)], time.perf_counter() - t0, [qs[j] for j in range(R)])
-    srv.close()
     cb["steps"] = steps
+    # saturated: every graph of two rounds of the pool waiting at once
+    S = 2 * len(pool)
+    t = time.perf_counter()
+    for k in range(S):
+        g = pool[k % len(pool)]
+        srv.submit(g.offsets, g.indices, g.weights)
+    drain(S)
+    sat_cb = S / (time.perf_counter() - t)
+    srv.close()
+    t = time.perf_counter()
+    for k in range(S):
+        plain_one(pool[k % len(pool)])
+    sat_plain = S / (time.perf_counter() - t)
     return {
         "workload": (f"Poisson arrivals of {R} requests cycling through {len(pool)} seeded graphs (SBM n in [1k, 4M] "
                      f"log-uniform, R-MAT scale 14-22 edge factor 16; {sum(g.nnz for g in pool) / 1e6:.0f}M entries "
@@ -350,7 +375,8 @@ def served_form(args, mode, flags):
         "mode": "async" if mode == lg.LEIDEN_ASYNC else "det",
         "offered_rate_per_s": rate, "load_vs_plain": args.serve_load, "plain_service_ms": service * 1e3,
         "continuous": cb, "plain": plain,
-        "graphs_per_s_ratio": cb["graphs_per_s"] / plain["graphs_per_s"],
+        "saturated": {"graphs": S, "continuous_graphs_per_s": sat_cb, "plain_graphs_per_s": sat_plain,
+                      "ratio": sat_cb / sat_plain},
     }
 
 

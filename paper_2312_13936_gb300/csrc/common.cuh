@@ -142,6 +142,21 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// arr[key] += x for every lane of a full warp (key < 0: nothing), with one
+// atomic per distinct key: lanes that share a key sum first. Cheap when a
+// warp's keys repeat (labels of nearby vertices).
+__device__ __forceinline__ void warp_add_by_key(double *arr, int64_t key, double x) {
+    unsigned todo = __ballot_sync(kFull, key >= 0);
+    while (todo) {
+        const int lead = __ffs(todo) - 1;
+        const int64_t k = __shfl_sync(kFull, key, lead);
+        const unsigned same = __ballot_sync(kFull, key == k);
+        const double s = warp_sum(key == k ? x : 0.0);
+        if ((int)(threadIdx.x & 31) == lead && s != 0.0) atomicAdd(&arr[k], s);
+        todo &= ~same;
+    }
+}
+
 // Profiling counters: every lane holds partial counts; one atomic per warp.
 struct ProfCounts {
     unsigned long long v[6] = {0, 0, 0, 0, 0, 0};

@@ -292,10 +292,11 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             return LEIDEN_ERR_UNSUPPORTED;
         }
         if (per_sm > 0) {
-            // enough blocks for the graph (about 2048 vertices each), so
-            // small graphs do not pay a full-GPU barrier per step
+            // enough blocks for the graph (about kCoopVerticesPerBlock
+            // each), so small graphs do not pay a full-GPU barrier per step
+            // and graphs of one block synchronise with __syncthreads only
             int grid = per_sm * q.sm;
-            const int64_t want = (n + 2047) / 2048;
+            const int64_t want = (n + kCoopVerticesPerBlock - 1) / kCoopVerticesPerBlock;
             if (want < grid) grid = (int)(want < 1 ? 1 : want);
             sc.hub_regions = hub_regions > grid ? grid : hub_regions;
             sc.max_it = prm.max_iterations;
@@ -307,6 +308,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             CK(cudaMemsetAsync(q.phase_dq, 0, sizeof(long long) * prm.max_iterations * NG, s));
             CK(cudaMemsetAsync(q.phase_moved, 0, sizeof(unsigned long long) * prm.max_iterations * NG, s));
             CK(cudaMemsetAsync(q.gactive, 0, sizeof(unsigned) * prm.max_iterations, s));
+            CK(cudaMemsetAsync(q.bar, 0, 2 * sizeof(unsigned), s));  // barrier state starts clean
             sc.prof = prof_begin(refine ? 8 : 0);
             CK(launch_sweep_coop(sc, sList, grid, s));
             prof_end();

@@ -49,6 +49,11 @@ struct Scalars {  // device scalars, read back in one copy
 
 // graphs below this size fit in L2 and are swept without relabelling
 constexpr int64_t kRelabelMinVertices = 1 << 16;
+// vertices per block of the persistent sweep kernel (below a full grid):
+// a step's latency grows with the vertices each thread takes in turn, so
+// small graphs get many blocks (4096 per block measured slower than 2048 on
+// the aggregated passes of the road workload)
+constexpr int64_t kCoopVerticesPerBlock = 2048;
 
 inline int ceil_log2_h(int64_t x) {
     int b = 0;

@@ -207,6 +207,7 @@ __global__ void k_modularity_batch(int64_t n0, const int64_t *off, const int32_t
         // lanes past the end count nothing in the graph of the warp's first vertex
         const int32_t g = i < n0 ? gid0[i] : gid0[v0];
         double k = 0, in = 0;
+        int64_t key = -1;  // slot of Sigma_c
         if (i < n0) {
             const int64_t base = vseg0[g], ng = vseg0[g + 1] - base;
             const int32_t ci = C[i];
@@ -218,9 +219,10 @@ __global__ void k_modularity_batch(int64_t n0, const int64_t *off, const int32_t
                     k += x;
                     if (C[idx[e]] == ci) in += x;
                 }
-                if (k != 0.0) atomicAdd(&sigtot[base + ci], k);
+                if (k != 0.0) key = base + ci;
             }
         }
+        warp_add_by_key(sigtot, key, k);
         graph_add(gsum, g, 0, in);
         graph_add(gsum, g, 1, k);
     }

@@ -91,23 +91,31 @@ __global__ void k_canonical(const int32_t *C0, const int32_t *minv, const int64_
     GRID_STRIDE(v, n0) out[v] = (int32_t)rank[minv[C0[v]]];
 }
 
-// Eq. 1: intra-community weight, 2m and Sigma_c of each community.
+// Eq. 1: intra-community weight, 2m and Sigma_c of each community (whole
+// warps step through the vertices so that Sigma_c is summed per label in
+// the warp before its atomic).
 __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                    const int32_t *C, double *sigtot, double *sums) {
     double intra = 0, tot = 0;
-    GRID_STRIDE(i, n) {
-        const int32_t ci = C[i];
-        if (ci < 0 || ci >= n) {  // label out of range: counted in sums[3], not used
-            atomicAdd(&sums[3], 1.0);
-            continue;
-        }
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        int32_t ci = -1;
         double k = 0, in = 0;
-        for (int64_t e = off[i]; e < off[i + 1]; ++e) {
-            const double x = w ? (double)w[e] : 1.0;
-            k += x;
-            if (C[idx[e]] == ci) in += x;
+        if (i < n) {
+            ci = C[i];
+            if (ci < 0 || ci >= n) {  // label out of range: counted in sums[3], not used
+                atomicAdd(&sums[3], 1.0);
+                ci = -1;
+            } else {
+                const int64_t e1 = off[i + 1];
+                for (int64_t e = off[i]; e < e1; ++e) {
+                    const double x = w ? (double)w[e] : 1.0;
+                    k += x;
+                    if (C[idx[e]] == ci) in += x;
+                }
+            }
         }
-        if (k != 0.0) atomicAdd(&sigtot[ci], k);
+        warp_add_by_key(sigtot, k != 0.0 ? ci : -1, k);
         intra += in;
         tot += k;
     }

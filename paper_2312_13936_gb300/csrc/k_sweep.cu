@@ -664,12 +664,15 @@ __device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_
     }
 }
 
-// Grid-wide barrier of a cooperative launch. Spins are bounded: after about a
-// second without progress the kernel records kErrTimeout and every later
-// barrier returns at once, so the launch always ends.
+// Grid-wide barrier of a cooperative launch: blocks count in on bar[0]; the
+// last one resets it and advances the generation bar[1] that the others
+// poll. Spins are bounded: after about a second without progress the kernel
+// records kErrTimeout and every later barrier returns at once, so the launch
+// always ends. A grid of one block needs only __syncthreads.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
     __shared__ int s_ok;
     __syncthreads();
+    if (gridDim.x == 1) return true;
     if (threadIdx.x == 0) {
         int ok = *((volatile int *)err) == 0;
         if (ok) {
