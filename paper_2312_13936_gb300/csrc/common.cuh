@@ -142,6 +142,45 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Row i of a CSR against labels C: K_i (sum of weights) and the weight to
+// vertices labelled ci, over entries [from, to) of the row with stride step.
+__device__ __forceinline__ void row_part(const int32_t *idx, const float *w, const int32_t *C, int64_t e0,
+                                         int64_t from, int64_t to, int step, int32_t ci, double &k, double &in) {
+    for (int64_t e = e0 + from; e < e0 + to; e += step) {
+        const double x = w ? (double)w[e] : 1.0;
+        k += x;
+        if (C[idx[e]] == ci) in += x;
+    }
+}
+// the same for every lane's row of a full warp: short rows by their lane,
+// rows longer than 64 entries (LONG) by the whole warp in turn (valid: the
+// lane has a row)
+template <bool LONG>
+__device__ __forceinline__ void warp_rows(const int64_t *off, const int32_t *idx, const float *w, const int32_t *C,
+                                          bool valid, int64_t i, int32_t ci, double &k, double &in) {
+    const int lane = threadIdx.x & 31;
+    int64_t e0 = 0, d = 0;
+    if (valid) {
+        e0 = off[i];
+        d = off[i + 1] - e0;
+        if (!LONG || d <= 64) row_part(idx, w, C, e0, 0, d, 1, ci, k, in);
+    }
+    unsigned longs = LONG ? __ballot_sync(kFull, valid && d > 64) : 0u;
+    while (longs) {
+        const int src = __ffs(longs) - 1;
+        longs &= longs - 1;
+        double kl = 0, il = 0;
+        row_part(idx, w, C, __shfl_sync(kFull, e0, src), lane, __shfl_sync(kFull, d, src), 32,
+                 __shfl_sync(kFull, ci, src), kl, il);
+        kl = warp_sum(kl);
+        il = warp_sum(il);
+        if (lane == src) {
+            k = kl;
+            in = il;
+        }
+    }
+}
+
 // arr[key] += x for every lane of a full warp (key < 0: nothing), with one
 // atomic per distinct key: lanes that share a key sum first. Cheap when a
 // warp's keys repeat (labels of nearby vertices).

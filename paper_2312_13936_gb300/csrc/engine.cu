@@ -54,6 +54,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     }
     ST(q.alloc_workspace(n, num_graphs));
     CK(launch_degrees(q.off0, q.deg0, n, &q.dsc->err, q.s));
+    CK(launch_max_i32(q.deg0, n, &q.dsc->maxdeg, q.s));
     const int32_t G = q.G;
     CK(cudaMemcpyAsync(q.vseg0, q.hvseg0.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, q.s));
     if (G > 1) {
@@ -74,6 +75,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     }
     q.nonint = q.hsc->nonint != 0;
     q.wsum = q.hsc->wsum;
+    q.maxdeg0 = q.hsc->maxdeg;
     if (G > 1) {  // weight sum of every graph, for the deterministic mode's 2m < 2^31 rule
         GraphView g0;
         g0.n = n;
@@ -140,7 +142,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     // schedule and (step, bin) lists
     SchedWork sw{q.scnt, q.slayer, q.sfcount};
     CK(launch_schedule(G, prm.seed + (r.gpass ? 0 : (uint64_t)lp), L, B, sw, q.step, s, cur_gid,
-                       batch ? q.vseg : nullptr, r.gpass));
+                       batch ? q.vseg : nullptr, r.gpass, r.deg_bound > kLongRow));
     q.launches += L > 1 ? L : 2;
     // one vertex list per (schedule step, degree bin), step-major
     CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
@@ -267,10 +269,10 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
                 prof_end();
                 q.launches++;
             }
-            // apply phase: deterministic mode, and refinement proposals where
-            // neighbours may share a step (asynchronous refinement applies
-            // its joins at once below the capped step)
-            if (det || (refine && k >= sc.cap_step)) {
+            // apply phase: deterministic mode, and proposals where
+            // neighbours may share a step (below the capped step the
+            // asynchronous mode moves and joins at once)
+            if (det || k >= sc.cap_step) {
                 if (refine) CK(launch_refine_apply(sc, sList + a0, a1 - a0, s));
                 else CK(launch_move_apply(sc, sList + a0, a1 - a0, s));
                 q.launches++;
@@ -440,6 +442,8 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     CK(cudaMemsetAsync(q.agg[dst].deg, 0, sizeof(int32_t) * ncomm, s));
     {
         int64_t mt = (int64_t)q.hsc->maxtdeg;
+        r.deg_bound = mt < ncomm ? mt : ncomm;  // degrees of G'' (the next graph)
+        if (mt > kGiantAggEntries) mt = kGiantAggEntries;  // larger ones are bin 7
         if (mt > ncomm) mt = ncomm;
         int abits = 0, aregions = 0;
         if (ako[kBinHub + 1] > ako[kBinHub]) {
@@ -465,7 +469,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         ac.hub_vals = q.hub_vals;
         ac.hub_bits = abits;
         ac.err = &q.dsc->err;
-        for (int b = 1; b < kNumBins; ++b) {
+        for (int b = 1; b < kBinGiant; ++b) {
             const int64_t lo = ako[b], hi = ako[b + 1];
             if (hi == lo) continue;
             const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : aregions);
@@ -473,6 +477,31 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             CK(launch_aggregate(ac, b, q.list + lo, hi - lo, mb, s));
             prof_end();
             q.launches++;
+        }
+        // giant communities: one at a time, the whole GPU on each
+        const int64_t ng = ako[kBinGiant + 1] - ako[kBinGiant];
+        if (ng > 0) {
+            std::vector<int32_t> giants((size_t)ng);
+            CK(cudaMemcpyAsync(giants.data(), q.list + ako[kBinGiant], sizeof(int32_t) * ng, cudaMemcpyDeviceToHost,
+                               s));
+            std::vector<int64_t> gdeg((size_t)ng);
+            CK(cudaStreamSynchronize(s));
+            for (int64_t k = 0; k < ng; ++k)
+                CK(cudaMemcpyAsync(&gdeg[k], q.tdeg + giants[k], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int64_t k = 0; k < ng; ++k) {
+                const int64_t cap = gdeg[k] < ncomm ? gdeg[k] : ncomm;  // distinct targets
+                int bits = ceil_log2_h(2 * cap);
+                if (bits < 6) bits = 6;
+                ST(q.ensure_hub(bits, 1, det));
+                ac.hub_keys = q.hub_keys;
+                ac.hub_vals = q.hub_vals;
+                ac.hub_bits = bits;
+                ac.prof = prof_begin(16 + kBinGiant);
+                CK(launch_aggregate_giant(ac, giants[k], q.sm * 8, s));
+                prof_end();
+                q.launches += 2;
+            }
         }
     }
     // move-based labels of the super-vertices (reading R3)
@@ -623,6 +652,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(cudaStreamSynchronize(s));  // st0 is a local
     }
     r.n0 = n0;
+    r.deg_bound = q.maxdeg0;
     r.cur_gid = batch ? q.gid0 : nullptr;  // graph of every vertex of G'
     r.G.n = n0;
     r.G.off = q.off0;
@@ -669,11 +699,11 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     if (batch) {
         CK(cudaMemsetAsync(q.gmsum, 0, sizeof(double) * 3 * NG, s));
         CK(launch_modularity_batch(n0, q.off0, q.idx0, q.w0, outp, q.gid0, q.vseg0, NG, prm.resolution, q.sigtot,
-                                   q.gmsum, &q.dsc->msum[3], q.gq, s));
+                                   q.gmsum, &q.dsc->msum[3], q.gq, s, q.maxdeg0 > kLongRow));
         CK(launch_graph_counts(q.pos, q.vseg0, NG, q.gcomm, s));
         q.launches += 4;
     } else {
-        CK(launch_modularity_parts(n0, q.off0, q.idx0, q.w0, outp, q.sigtot, q.dsc->msum, s));
+        CK(launch_modularity_parts(n0, q.off0, q.idx0, q.w0, outp, q.sigtot, q.dsc->msum, s, q.maxdeg0 > kLongRow));
         CK(launch_sum_squares(q.sigtot, n0, &q.dsc->msum[2], s));
         q.launches += 2;
     }

@@ -79,6 +79,7 @@ struct Run {
     int passes = 0;
     bool no_edges = false;
     int64_t n0 = 0;               // vertices of the dendrogram C0
+    int64_t deg_bound = INT64_MAX;  // bound on the degrees of G' (picks the long-row kernels)
     // graphs at different passes (serving): the first n_cont vertices of G'
     // continue with move-based labels, the others start as singletons;
     // gpass/gtau are per-graph pass indices and tolerances; a graph stops at
@@ -141,6 +142,7 @@ struct Serve {
 
 struct Handle::Impl {
     int64_t n0 = 0, m0 = 0;
+    int64_t maxdeg0 = INT64_MAX;  // largest degree of the input graph
     Serve *srv = nullptr;
     cudaStream_t s = nullptr;
     int sm = 152;

@@ -303,6 +303,68 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
     pc.flush(a.prof);
 }
 
+// ------------------------------------------------------ giant communities
+// Every warp of the grid takes members of community c in turn; its lanes
+// stride over the member's entries and insert them into the one table.
+template <class P, class Wi, class Wo>
+__global__ void __launch_bounds__(256) k_agg_giant_insert(AV<P, Wi, Wo> a, int32_t c) {
+    using A = typename P::acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t m0 = a.coff[c];
+    const int64_t nm = a.coff[c + 1] - m0;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nm; k += warps) {
+        const int32_t u = a.members[m0 + k];
+        const int64_t e0 = a.off[u];
+        const int32_t du = a.deg[u];
+        for (int32_t e = lane; e < du; e += 32)
+            if (!hash_add(a.hub_keys, a.hub_vals, a.hub_bits, a.Cd[a.idx[e0 + e]], wconv<A>(a.w[e0 + e])))
+                set_error(a.err, kErrHashFull);
+    }
+}
+// Write the table's entries as row c (order unspecified); out_deg[c] counts
+// them (it starts at 0) and out_K[c] sums their weights (started at 0).
+template <class P, class Wi, class Wo>
+__global__ void __launch_bounds__(256) k_agg_giant_write(AV<P, Wi, Wo> a, int32_t c) {
+    using A = typename P::acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t S = 1LL << a.hub_bits;
+    const int64_t o0 = a.out_off[c];
+    A kpart = 0;
+    for (int64_t s0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)); s0 < S;
+         s0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = s0 + lane;
+        const int32_t k = s < S ? a.hub_keys[s] : -1;
+        const unsigned ball = __ballot_sync(kFull, k >= 0);
+        int base = 0;
+        if (lane == 0 && ball) base = atomicAdd(&a.out_deg[c], (int)__popc(ball));
+        base = __shfl_sync(kFull, base, 0);
+        if (k >= 0) {
+            const int pos = base + __popc(ball & ((1u << lane) - 1u));
+            const Wo wo = out_weight<Wo>(a.hub_vals[s]);
+            a.out_idx[o0 + pos] = k;
+            a.out_w[o0 + pos] = wo;
+            kpart += wconv<A>(wo);
+        }
+    }
+    kpart = warp_sum(kpart);
+    if (lane == 0 && kpart != (A)0) atomic_add_acc(&a.out_K[c], kpart);
+}
+
+template <class P, class Wi, class Wo>
+cudaError_t giant_typed(const AggCtx &c, int32_t comm, int blocks, cudaStream_t s) {
+    using A = typename P::acc;
+    auto a = aview<P, Wi, Wo>(c);
+    const size_t S = (size_t)1 << c.hub_bits;
+    cudaError_t e = cudaMemsetAsync(c.hub_keys, 0xff, S * sizeof(int32_t), s);  // keys -1: empty
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.hub_vals, 0, S * sizeof(A), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(static_cast<A *>(c.out_K) + comm, 0, sizeof(A), s);
+    if (e != cudaSuccess) return e;
+    k_agg_giant_insert<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, comm);
+    k_agg_giant_write<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, comm);
+    return cudaGetLastError();
+}
+
 template <class P, class Wi, class Wo>
 cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks, cudaStream_t s) {
     auto a = aview<P, Wi, Wo>(c);
@@ -330,6 +392,14 @@ cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t cou
 }
 
 }  // namespace
+
+cudaError_t launch_aggregate_giant(const AggCtx &c, int32_t comm, int blocks, cudaStream_t s) {
+    if (c.det) {
+        if (c.g.w_int) return giant_typed<Det, int32_t, int32_t>(c, comm, blocks, s);
+        return giant_typed<Det, float, int32_t>(c, comm, blocks, s);
+    }
+    return giant_typed<Async, float, float>(c, comm, blocks, s);
+}
 
 cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
                              cudaStream_t s) {

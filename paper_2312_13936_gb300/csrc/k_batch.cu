@@ -199,6 +199,7 @@ __device__ __forceinline__ void graph_add(double *gsum, int32_t g, int k, double
     }
 }
 
+template <bool LONG>
 __global__ void k_modularity_batch(int64_t n0, const int64_t *off, const int32_t *idx, const float *w,
                                    const int32_t *C, const int32_t *gid0, const int64_t *vseg0, double *sigtot,
                                    double *gsum, double *bad) {
@@ -208,20 +209,17 @@ __global__ void k_modularity_batch(int64_t n0, const int64_t *off, const int32_t
         const int32_t g = i < n0 ? gid0[i] : gid0[v0];
         double k = 0, in = 0;
         int64_t key = -1;  // slot of Sigma_c
+        int32_t ci = -1;
         if (i < n0) {
-            const int64_t base = vseg0[g], ng = vseg0[g + 1] - base;
-            const int32_t ci = C[i];
+            const int64_t ng = vseg0[g + 1] - vseg0[g];
+            ci = C[i];
             if (ci < 0 || ci >= ng) {
                 atomicAdd(bad, 1.0);
-            } else {
-                for (int64_t e = off[i]; e < off[i + 1]; ++e) {
-                    const double x = w ? (double)w[e] : 1.0;
-                    k += x;
-                    if (C[idx[e]] == ci) in += x;
-                }
-                if (k != 0.0) key = base + ci;
+                ci = -1;
             }
         }
+        warp_rows<LONG>(off, idx, w, C, ci >= 0, i, ci, k, in);
+        if (ci >= 0 && k != 0.0) key = vseg0[g] + ci;
         warp_add_by_key(sigtot, key, k);
         graph_add(gsum, g, 0, in);
         graph_add(gsum, g, 1, k);
@@ -344,10 +342,11 @@ cudaError_t launch_canonical_batch(const int32_t *C0, const int32_t *minv, const
 cudaError_t launch_modularity_batch(int64_t n0, const int64_t *off, const int32_t *idx, const float *w,
                                     const int32_t *C, const int32_t *gid0, const int64_t *vseg0, int32_t G,
                                     double gamma, double *sigtot, double *gsum, double *bad, double *q,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, bool long_rows) {
     if (G <= 0) return cudaSuccess;
     if (n0 > 0) {
-        k_modularity_batch<<<grid_for(n0, 256), 256, 0, s>>>(n0, off, idx, w, C, gid0, vseg0, sigtot, gsum, bad);
+        auto kern = long_rows ? k_modularity_batch<true> : k_modularity_batch<false>;
+        kern<<<grid_for(n0, 256), 256, 0, s>>>(n0, off, idx, w, C, gid0, vseg0, sigtot, gsum, bad);
         k_square_sums_batch<<<grid_for(n0, 256), 256, 0, s>>>(sigtot, gid0, n0, gsum);
     }
     k_graph_q<<<grid_for(G, 256), 256, 0, s>>>(gsum, G, gamma, q);

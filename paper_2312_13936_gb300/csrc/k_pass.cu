@@ -56,7 +56,7 @@ __global__ void k_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, i
 }
 __global__ void k_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key) {
     GRID_STRIDE(c, ncomm) {
-        const int b = degree_bin(tdeg[c]);
+        const int b = tdeg[c] > kGiantAggEntries ? kBinGiant : degree_bin(tdeg[c]);
         key[c] = b == 0 ? -1 : b;
     }
 }
@@ -93,7 +93,8 @@ __global__ void k_canonical(const int32_t *C0, const int32_t *minv, const int64_
 
 // Eq. 1: intra-community weight, 2m and Sigma_c of each community (whole
 // warps step through the vertices so that Sigma_c is summed per label in
-// the warp before its atomic).
+// the warp before its atomic; LONG: long rows by the whole warp).
+template <bool LONG>
 __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                    const int32_t *C, double *sigtot, double *sums) {
     double intra = 0, tot = 0;
@@ -106,15 +107,9 @@ __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t 
             if (ci < 0 || ci >= n) {  // label out of range: counted in sums[3], not used
                 atomicAdd(&sums[3], 1.0);
                 ci = -1;
-            } else {
-                const int64_t e1 = off[i + 1];
-                for (int64_t e = off[i]; e < e1; ++e) {
-                    const double x = w ? (double)w[e] : 1.0;
-                    k += x;
-                    if (C[idx[e]] == ci) in += x;
-                }
             }
         }
+        warp_rows<LONG>(off, idx, w, C, ci >= 0, i, ci, k, in);
         warp_add_by_key(sigtot, k != 0.0 ? ci : -1, k);
         intra += in;
         tot += k;
@@ -287,9 +282,11 @@ cudaError_t launch_canonical(const int32_t *C0, const int32_t *minv, const int64
     return cudaGetLastError();
 }
 cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
-                                    const int32_t *C, double *sigtot, double *sums, cudaStream_t s) {
+                                    const int32_t *C, double *sigtot, double *sums, cudaStream_t s,
+                                    bool long_rows) {
     if (n <= 0) return cudaSuccess;
-    k_modularity_parts<<<grid_for(n, 256), 256, 0, s>>>(n, off, idx, w, C, sigtot, sums);
+    auto kern = long_rows ? k_modularity_parts<true> : k_modularity_parts<false>;
+    kern<<<grid_for(n, 256), 256, 0, s>>>(n, off, idx, w, C, sigtot, sums);
     return cudaGetLastError();
 }
 cudaError_t launch_inverse(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s) {

@@ -16,10 +16,11 @@
 // k_sweep_coop, is persistent: one cooperative launch runs every step of a
 // sweep and separates steps with a grid barrier, so a sweep costs one launch
 // whatever the number of steps. Asynchronous local-moving applies each move
-// at once (atomics on Sigma, the paper's asynchronous execution); the
-// deterministic mode records proposals and commits them after the step's
-// evaluation, and the refinement in both modes records proposals that the
-// step's apply phase accepts by reading S5. The per-(step, bin) kernels
+// at once below the capped step (atomics on Sigma, the paper's asynchronous
+// execution) and records proposals in the capped steps, where neighbours
+// share a step; the deterministic mode records proposals in every step. An
+// apply phase after the step's evaluation commits them; the refinement's
+// proposals are accepted by reading S5. The per-(step, bin) kernels
 // below run the same routines one launch at a time; the engine uses them if
 // a cooperative launch is not possible.
 //
@@ -161,6 +162,21 @@ __device__ __forceinline__ typename P::acc kscale_of(const SV<P, W> &a, int32_t 
     return B ? __ldg(&a.gks[gv]) : a.kscale;
 }
 
+// Whether a step decides by proposals that an apply phase commits after
+// the step's evaluation, rather than moving at once: always in the
+// deterministic mode and in the refinement, and in the asynchronous
+// local-moving in the capped steps, where neighbours may share a step (on
+// heavy-tailed graphs most vertices are there, and moving at once let
+// neighbours chase each other).
+template <class P, bool REFINE> __device__ __forceinline__ bool proposing(int32_t cur_step, int32_t cap_step) {
+    return REFINE || P::det || cur_step >= cap_step;
+}
+// the gain of a local-moving proposal, in the accumulator's own type
+__device__ __forceinline__ void store_gain(long long *gain, int32_t v, long long g) { gain[v] = g; }
+__device__ __forceinline__ void store_gain(long long *gain, int32_t v, float g) {
+    reinterpret_cast<float *>(gain)[v] = g;
+}
+
 // Decision for vertex v (one thread, graph gv, key scale kscale) with best
 // candidate (key, cand), K_{v->d} = kvd and Sigma_d = sd. Returns true if
 // an asynchronous local-moving move was applied (its neighbours must then be
@@ -199,9 +215,9 @@ __device__ __forceinline__ bool decide_sd(const SV<P, W> &a, int32_t v, int32_t 
         }
         return false;
     }
-    if (REFINE || P::det) {
+    if (proposing<P, REFINE>(cur_step, a.cap_step)) {
         a.prop[v] = mv ? cand : -1;
-        if (!REFINE && mv) a.gain[v] = (long long)g;
+        if (!REFINE && mv) store_gain(a.gain, v, g);
         return false;
     }
     if (mv) {
@@ -258,7 +274,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
         const int32_t gv = graph_of<B>(a, v);
         const bool elig = (REFINE ? (ldm(&a.size[d]) == 1) : (up != 0)) && !(B && ldm(&a.gdone[gv]));
         if (!elig) {
-            if (REFINE || P::det) a.prop[v] = -1;
+            if (proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
             pc.v[1]++;
             continue;
         }
@@ -317,7 +333,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
             pc.v[0]++;
             pc.v[2] += dv;
             pc.v[3] += distinct;
-            if ((REFINE || P::det) ? (a.prop[v] >= 0) : mv) {
+            if (proposing<P, REFINE>(cur_step, a.cap_step) ? (a.prop[v] >= 0) : mv) {
                 pc.v[4]++;
                 pc.v[5] += dv;
             }
@@ -348,7 +364,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
         elig = __shfl_sync(tmask, elig, 0, T);
         d = __shfl_sync(tmask, d, 0, T);
         if (!elig) {
-            if (tl == 0 && (REFINE || P::det)) a.prop[v] = -1;
+            if (tl == 0 && proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
             if (tl == 0) pc.v[1]++;
             continue;
         }
@@ -406,7 +422,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
                 pc.v[0]++;
                 pc.v[2] += dv;
                 pc.v[3] += __popc(lb);
-                if ((REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0)) {
+                if (proposing<P, REFINE>(cur_step, a.cap_step) ? (a.prop[v] >= 0) : (mv != 0)) {
                     pc.v[4]++;
                     pc.v[5] += dv;
                 }
@@ -436,7 +452,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
         elig = __shfl_sync(kFull, elig, 0);
         d = __shfl_sync(kFull, d, 0);
         if (!elig) {
-            if (lane == 0 && (REFINE || P::det)) a.prop[v] = -1;
+            if (lane == 0 && proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
             if (lane == 0) pc.v[1]++;
             continue;
         }
@@ -491,7 +507,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
             mv = decide<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, sm, cur_step, gv, ks) ? 1 : 0;
             pc.v[0]++;
             pc.v[2] += dv;
-            if ((REFINE || P::det) ? (a.prop[v] >= 0) : (mv != 0)) {
+            if (proposing<P, REFINE>(cur_step, a.cap_step) ? (a.prop[v] >= 0) : (mv != 0)) {
                 pc.v[4]++;
                 pc.v[5] += dv;
             }
@@ -527,7 +543,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
             int32_t d = 0;
             s_elig = take_vertex<P, W, REFINE, B>(a, v, d, gv) ? 1 : 0;
             s_d = d;
-            if (!s_elig && (REFINE || P::det)) a.prop[v] = -1;
+            if (!s_elig && proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
             if (!s_elig) pc.v[1]++;
         }
         __syncthreads();
@@ -542,7 +558,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
         if (bits > max_bits) {
             if (tid == 0) {
                 set_error(a.err, kErrHashFull);
-                if (REFINE || P::det) a.prop[v] = -1;
+                if (proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
             }
             continue;
         }
@@ -605,7 +621,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
             s_mv = decide<P, W, REFINE, B>(a, v, d, Kv, bk, bc, kd, sm, cur_step, gv, ks) ? 1 : 0;
             pc.v[0]++;
             pc.v[2] += dv;
-            if ((REFINE || P::det) ? (a.prop[v] >= 0) : (s_mv != 0)) {
+            if (proposing<P, REFINE>(cur_step, a.cap_step) ? (a.prop[v] >= 0) : (s_mv != 0)) {
                 pc.v[4]++;
                 pc.v[5] += dv;
             }
@@ -618,26 +634,50 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
 }
 
 // ------------------------------------------------------------ apply steps
-// Deterministic local-moving: commit the proposals of one step.
+// Local-moving proposals of one step (deterministic mode; asynchronous mode
+// in the capped steps): commit them.
 template <class P, class W, bool B>
 __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo,
                                                int64_t hi, Sums<P> &sm) {
-    for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = list[t];
-        const int32_t c = ldm(&a.prop[v]);
-        if (c < 0) continue;
-        const int32_t d = ldm(&a.C[v]);
-        const auto Kv = (typename P::tot)a.K[v];
-        atomic_add_acc(&a.Sig[d], -Kv);
-        atomic_add_acc(&a.Sig[c], Kv);
-        atomicSub(&a.size[d], 1);
-        atomicAdd(&a.size[c], 1);
-        a.C[v] = c;
-        gacc_add(sm.dgain, B, graph_of<B>(a, v), ldm(&a.gain[v]), reinterpret_cast<long long *>(sm.dq));
-        const int64_t e0 = a.off[v];
-        const int32_t dv = a.deg[v];
-        for (int32_t e = 0; e < dv; ++e) a.unproc[a.idx[e0 + e]] = 1;
+    // whole warps step through the list, so that the neighbours of a mover
+    // with a long row are flagged by the whole warp
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t0 = lo + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < hi; t0 += stride) {
+        const int64_t t = t0 + lane;
+        int32_t v = -1, c = -1;
+        if (t < hi) {
+            v = list[t];
+            c = ldm(&a.prop[v]);
+        }
+        int64_t e0 = 0;
+        int32_t dv = 0;
+        if (c >= 0) {
+            const int32_t d = ldm(&a.C[v]);
+            const auto Kv = (typename P::tot)a.K[v];
+            atomic_add_acc(&a.Sig[d], -Kv);
+            atomic_add_acc(&a.Sig[c], Kv);
+            atomicSub(&a.size[d], 1);
+            atomicAdd(&a.size[c], 1);
+            a.C[v] = c;
+            if (P::det)
+                gacc_add(sm.dgain, B, graph_of<B>(a, v), ldm(&a.gain[v]), reinterpret_cast<long long *>(sm.dq));
+            else
+                gacc_add(sm.gain, B, graph_of<B>(a, v),
+                         (typename P::acc)__ldcg(reinterpret_cast<const float *>(a.gain) + v), sm.dq);
+            e0 = a.off[v];
+            dv = a.deg[v];
+            if (dv <= 32)
+                for (int32_t e = 0; e < dv; ++e) a.unproc[a.idx[e0 + e]] = 1;
+        }
+        unsigned longs = __ballot_sync(kFull, c >= 0 && dv > 32);
+        while (longs) {
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int64_t es = __shfl_sync(kFull, e0, src);
+            const int32_t ds = __shfl_sync(kFull, dv, src);
+            for (int32_t e = lane; e < ds; e += 32) a.unproc[a.idx[es + e]] = 1;
+        }
     }
 }
 
@@ -758,10 +798,10 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                                               sm, pc);
             }
             if (!(ok = grid_barrier(a.bar, a.err))) break;
-            // apply phase: deterministic mode, and refinement proposals where
-            // neighbours may share a step (asynchronous refinement applies
-            // its joins at once below the capped step)
-            if (P::det || (REFINE && k >= a.cap_step)) {
+            // apply phase: deterministic mode, and proposals where neighbours
+            // may share a step (below the capped step the asynchronous mode
+            // moves and joins at once)
+            if (P::det || k >= a.cap_step) {
                 if (REFINE) run_refine_apply<P, W, B>(a, list, b0, b8, k, sm);
                 else run_move_apply<P, W, B>(a, list, b0, b8, sm);
                 if (!(ok = grid_barrier(a.bar, a.err))) break;
@@ -917,8 +957,12 @@ template <class P, class W>
 __global__ void __launch_bounds__(256) k_move_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
     Sums<P> sm = scalar_sums(a);
     run_move_apply<P, W, false>(a, list, 0, count, sm);
-    const long long g = warp_sum(sm.dgain.v);
-    if ((threadIdx.x & 31) == 0 && g != 0) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), g);
+    if (P::det) {
+        const long long g = warp_sum(sm.dgain.v);
+        if ((threadIdx.x & 31) == 0 && g != 0) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), g);
+    } else {
+        flush_gain<P, W, false>(a, sm);
+    }
 }
 template <class P, class W>
 __global__ void __launch_bounds__(256) k_refine_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
@@ -1022,8 +1066,8 @@ cudaError_t launch_sweep_eval(const SweepCtx &c, int bin, const int32_t *list, i
 
 cudaError_t launch_move_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    if (!c.det) return cudaErrorInvalidValue;
-    if (c.g.w_int) k_move_apply<Det, int32_t><<<apply_grid(count), 256, 0, s>>>(view<Det, int32_t>(c), list, count);
+    if (!c.det) k_move_apply<Async, float><<<apply_grid(count), 256, 0, s>>>(view<Async, float>(c), list, count);
+    else if (c.g.w_int) k_move_apply<Det, int32_t><<<apply_grid(count), 256, 0, s>>>(view<Det, int32_t>(c), list, count);
     else k_move_apply<Det, float><<<apply_grid(count), 256, 0, s>>>(view<Det, float>(c), list, count);
     return cudaGetLastError();
 }

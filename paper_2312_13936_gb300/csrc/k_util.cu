@@ -233,26 +233,46 @@ __device__ __forceinline__ uint64_t mix_triple(uint64_t i, uint64_t j, uint32_t 
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
 }
-__global__ void k_validate(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int *err,
-                           unsigned long long *sums) {
-    unsigned long long fwd = 0, bwd = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t a = off[i], b = off[i + 1];
-        if (b < a) {
+// entries [from, to) of row i with stride step
+__device__ __forceinline__ void validate_part(int64_t n, int64_t i, const int32_t *idx, const float *w, int64_t a,
+                                              int64_t from, int64_t to, int step, int *err,
+                                              unsigned long long &fwd, unsigned long long &bwd) {
+    for (int64_t e = a + from; e < a + to; e += step) {
+        const int32_t j = idx[e];
+        if (j < 0 || j >= n) {
             set_error(err, 1);
             continue;
         }
-        for (int64_t e = a; e < b; ++e) {
-            const int32_t j = idx[e];
-            if (j < 0 || j >= n) {
+        const float x = w ? w[e] : 1.0f;
+        if (!(x >= 0.0f) || isinf(x)) set_error(err, 1);
+        const uint32_t bits = __float_as_uint(x);
+        fwd += mix_triple((uint64_t)i, (uint64_t)j, bits);
+        bwd += mix_triple((uint64_t)j, (uint64_t)i, bits);
+    }
+}
+
+__global__ void k_validate(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int *err,
+                           unsigned long long *sums) {
+    unsigned long long fwd = 0, bwd = 0;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        int64_t a = 0, d = 0;
+        if (i < n) {
+            a = off[i];
+            d = off[i + 1] - a;
+            if (d < 0) {
                 set_error(err, 1);
-                continue;
+                d = 0;
             }
-            const float x = w ? w[e] : 1.0f;
-            if (!(x >= 0.0f) || isinf(x)) set_error(err, 1);
-            const uint32_t bits = __float_as_uint(x);
-            fwd += mix_triple((uint64_t)i, (uint64_t)j, bits);
-            bwd += mix_triple((uint64_t)j, (uint64_t)i, bits);
+            if (d <= 64) validate_part(n, i, idx, w, a, 0, d, 1, err, fwd, bwd);
+        }
+        unsigned longs = __ballot_sync(kFull, i < n && d > 64);
+        while (longs) {  // long rows: the warp together (sums are order-free)
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            validate_part(n, __shfl_sync(kFull, i, src), idx, w, __shfl_sync(kFull, a, src), lane,
+                          __shfl_sync(kFull, d, src), 32, err, fwd, bwd);
         }
     }
     fwd = warp_sum(fwd);

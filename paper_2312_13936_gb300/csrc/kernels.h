@@ -22,6 +22,14 @@ constexpr int kBlockMaxDeg = 2048;
 constexpr int kWarpSlots = 512;     // 8 warp tables fill the same 48 KB as one block table
 constexpr int kBlockSlots = 4096;
 constexpr int kBinHub = 6;
+// rows longer than this are walked by a whole warp in the schedule and
+// modularity kernels (their long-row variants, chosen when a graph's degree
+// bound exceeds it)
+constexpr int32_t kLongRow = 64;
+// aggregation only: communities of more member entries than this form bin 7
+// and are aggregated one at a time by the whole GPU
+constexpr int64_t kGiantAggEntries = 1 << 20;
+constexpr int kBinGiant = 7;
 __host__ __device__ inline int degree_bin(int64_t d) {
     return d <= 0 ? 0 : d <= kThreadMaxDeg ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= kWarpMaxDeg ? 4 : d <= kBlockMaxDeg ? 5 : 6;
 }
@@ -123,6 +131,10 @@ struct AggCtx {
 };
 cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
                              cudaStream_t s);
+// one community of bin 7: every block inserts its member entries into one
+// global table (hub_keys/hub_vals, 2^hub_bits slots, cleared here), then the
+// distinct entries are written as row c
+cudaError_t launch_aggregate_giant(const AggCtx &c, int32_t comm, int blocks, cudaStream_t s);
 
 // ---- utilities (k_util.cu)
 cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s);
@@ -151,9 +163,10 @@ struct SchedWork {
 };
 // (gid, vseg: a batch of graphs, priorities drawn at indices inside each
 // graph; gpass: graphs at different passes, state + gpass[g] for graph g)
+// long_rows: some row may exceed kLongRow entries
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
                             int32_t *step, cudaStream_t s, const int32_t *gid = nullptr,
-                            const int64_t *vseg = nullptr, const int32_t *gpass = nullptr);
+                            const int64_t *vseg = nullptr, const int32_t *gpass = nullptr, bool long_rows = true);
 // key[i] = step*kNumBins + bin (step-major: one list per step and bin), or
 // bin*nsteps + step (bin-major: one step-ordered list per bin); vertices
 // without edges get key nsteps*kNumBins (a trailing bucket)
@@ -228,7 +241,7 @@ cudaError_t launch_canonical_batch(const int32_t *C0, const int32_t *minv, const
 cudaError_t launch_modularity_batch(int64_t n0, const int64_t *off, const int32_t *idx, const float *w,
                                     const int32_t *C, const int32_t *gid0, const int64_t *vseg0, int32_t G,
                                     double gamma, double *sigtot, double *gsum, double *bad, double *q,
-                                    cudaStream_t s);
+                                    cudaStream_t s, bool long_rows = true);
 
 // ---- pass bookkeeping (k_pass.cu)
 // Sigma[c] += K[i], size[c] += 1 over C (acc type)
@@ -249,7 +262,7 @@ cudaError_t launch_comm_counts(const int32_t *Cd, const int32_t *deg, int64_t n,
                                cudaStream_t s);
 cudaError_t launch_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, int32_t *cursor, int32_t *members,
                              cudaStream_t s);
-// bins of communities by total degree
+// bins of communities by total degree (bin 7: more than kGiantAggEntries)
 cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key, cudaStream_t s);
 // move-based labels: bnd[Cd[i]] = CB[i]; rep[b] = min s; label[s] = rep[bnd[s]] (Cd < 0: skipped)
 cudaError_t launch_bound_labels(const int32_t *Cd, const int32_t *CB, int64_t n, int64_t ncomm, int32_t *bnd,
@@ -263,7 +276,8 @@ cudaError_t launch_canonical(const int32_t *C0, const int32_t *minv, const int64
 // weight, sums[1] += 2m, sigtot[c] += K_i, sums[3] += labels out of range;
 // then sums[2] += sum_c sigtot[c]^2
 cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
-                                    const int32_t *C, double *sigtot, double *sums, cudaStream_t s);
+                                    const int32_t *C, double *sigtot, double *sums, cudaStream_t s,
+                                    bool long_rows = true);
 cudaError_t launch_sum_squares(const double *x, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_max_i64(const int64_t *a, int64_t n, unsigned long long *out, cudaStream_t s);
 // relabelling of a pass's graph for the asynchronous sweeps: vertex p of the

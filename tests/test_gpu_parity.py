@@ -44,6 +44,15 @@ def hub_graph(seed=7):
     return gen.from_edges(n, uu, vv, ww)
 
 
+def two_big_cliques(k=1500):
+    """Two cliques K_k joined by one edge: a refined community of more than
+    2^20 member entries, so the aggregation takes its whole-GPU path."""
+    iu, ju = np.triu_indices(k, 1)
+    u = np.concatenate([iu, iu + k, [0]])
+    v = np.concatenate([ju, ju + k, [k]])
+    return gen.from_edges(2 * k, u, v)
+
+
 DET_GRAPHS = {
     "ring5x16": lambda: gen.ring_of_cliques(5, 16),
     "sbm_workload": gen.sbm_workload,
@@ -52,6 +61,7 @@ DET_GRAPHS = {
     "gnp_weighted": lambda: gen.gnp(400, 0.03, seed=9, wmax=5),
     "rmat_12": lambda: gen.rmat(12, 16),
     "hubs": hub_graph,
+    "two_big_cliques": two_big_cliques,
 }
 
 
