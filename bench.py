@@ -481,6 +481,8 @@ def main():
         dist.barrier()
         ms = float(t.item())
     value = world * args.steps * g.nnz / (ms / 1e3)
+    # every community connected? (Algorithm 5 on the GPU, outside the timed region)
+    disconnected = lg.disconnected(off, idx, memb)
 
     # ---- end to end through the C ABI with host buffers (H2D and D2H inside)
     e2e = None
@@ -543,7 +545,8 @@ def main():
         "config": {"workload": wname, "n": g.n, "nnz": g.nnz, "mode": args.mode,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
                        (g.offsets.nbytes + g.indices.nbytes + g.weights.nbytes) / 1e9),
-                   "modularity": statistics.median(qs), "passes": st.passes,
+                   "modularity": statistics.median(qs), "disconnected_communities": disconnected,
+                   "passes": st.passes,
                    "move_sweeps": st.move_iterations, "refine_sweeps": st.refine_iterations,
                    "phase_ms": {"move": st.ms_move, "refine": st.ms_refine, "aggregate": st.ms_aggregate,
                                 "other": st.ms_other}},

@@ -256,6 +256,16 @@ leiden_status leiden_batch_info(leiden_graph_t g, int32_t *num_graphs, int32_t *
 leiden_status leiden_modularity(int64_t n, const int64_t *offsets, const int32_t *indices, const float *weights,
                                 const int32_t *membership, double gamma, void *stream, double *q_out);
 
+/* Number of communities of `membership` (n labels in [0, n)) whose vertices
+ * do not form one connected subgraph of the symmetric CSR (Appendix A.1,
+ * Algorithm 5; the paper runs a BFS per community, this computes the
+ * components of the intra-community subgraph for all communities at once).
+ * All pointers are device pointers; the result is written to *count (host).
+ * Device scratch of 8 bytes per vertex comes from the stream-ordered
+ * allocator. LEIDEN_ERR_INVALID for labels outside [0, n). */
+leiden_status leiden_disconnected(int64_t n, const int64_t *offsets, const int32_t *indices, const int32_t *membership,
+                                  void *stream, int64_t *count);
+
 /* Modularity as leiden_modularity computes it, without allocating any
  * device memory. The paper has no counterpart: this entry point is for
  * callers that cannot allocate device memory when they need the score (a

@@ -25,7 +25,7 @@ __all__ = [
     "leiden_status_string", "leiden_last_error", "Leiden", "modularity", "leiden_batch_create",
     "leiden_batch_run", "leiden_batch_info", "LeidenBatch", "pack_batch", "ServerState", "leiden_server_create",
     "leiden_server_submit", "leiden_server_step", "leiden_server_next", "leiden_server_result", "leiden_server_info",
-    "leiden_server_destroy", "LeidenServer",
+    "leiden_server_destroy", "LeidenServer", "leiden_disconnected", "disconnected",
 ]
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
@@ -119,11 +119,12 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
                                              ctypes.POINTER(_I32), ctypes.POINTER(_I64)]
         lib.leiden_server_info.argtypes = [_VP, ctypes.POINTER(ServerState)]
         lib.leiden_server_destroy.argtypes = [_VP]
+        lib.leiden_disconnected.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.POINTER(_I64)]
         for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
                   lib.leiden_trace_get, lib.leiden_profile_get, lib.leiden_batch_create, lib.leiden_batch_run,
                   lib.leiden_batch_info, lib.leiden_server_create, lib.leiden_server_submit, lib.leiden_server_step,
                   lib.leiden_server_next, lib.leiden_server_result, lib.leiden_server_info,
-                  lib.leiden_server_destroy):
+                  lib.leiden_server_destroy, lib.leiden_disconnected):
             f.restype = ctypes.c_int
         lib.leiden_status_string.argtypes = [_I32]
         lib.leiden_status_string.restype = ctypes.c_char_p
@@ -252,6 +253,12 @@ def leiden_modularity(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, 
     _check(library().leiden_modularity(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma, stream,
                                        ctypes.byref(q)))
     return q.value
+
+
+def leiden_disconnected(n, offsets_ptr, indices_ptr, membership_ptr, stream) -> int:
+    c = _I64(0)
+    _check(library().leiden_disconnected(n, offsets_ptr, indices_ptr, membership_ptr, stream, ctypes.byref(c)))
+    return c.value
 
 
 def leiden_modularity_noalloc(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma, stream) -> float:
@@ -491,6 +498,13 @@ class LeidenServer:
             self.close()
         except Exception:
             pass
+
+
+def disconnected(offsets, indices, membership, stream=None) -> int:
+    """Communities of ``membership`` that are not connected (Algorithm 5), on
+    a CSR held in CUDA tensors."""
+    n = int(offsets.numel() - 1)
+    return leiden_disconnected(n, _ptr(offsets), _ptr(indices), _ptr(membership), _stream_ptr(stream))
 
 
 def modularity(offsets, indices, weights, membership, resolution: float = 1.0, stream=None) -> float:

@@ -224,6 +224,11 @@ leiden_status leiden_modularity(int64_t n, const int64_t *offsets, const int32_t
                                   static_cast<cudaStream_t>(stream), q_out);
 }
 
+leiden_status leiden_disconnected(int64_t n, const int64_t *offsets, const int32_t *indices, const int32_t *membership,
+                                  void *stream, int64_t *count) {
+    return lgb::disconnected_device(n, offsets, indices, membership, static_cast<cudaStream_t>(stream), count);
+}
+
 leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, void *dst, int64_t *count) {
     if (!g) {
         lgb::set_last_error("NULL handle");

@@ -783,6 +783,70 @@ leiden_status Handle::profile_get(leiden_kernel_profile *out) const {
     return LEIDEN_OK;
 }
 
+// Communities of a membership that are not connected (Algorithm 5), on a
+// CSR given as device pointers, with scratch from the stream-ordered
+// allocator. Labels must lie in [0, n) (checked first).
+leiden_status disconnected_device(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *memb,
+                                  cudaStream_t s, int64_t *count) {
+    if (n < 0 || !count || (n > 0 && (!off || !idx || !memb))) {
+        set_last_error("invalid arguments to leiden_disconnected");
+        return LEIDEN_ERR_INVALID;
+    }
+    *count = 0;
+    if (n == 0) return LEIDEN_OK;
+    int32_t *buf = nullptr;
+    unsigned long long *flags = nullptr;
+    if (cudaMallocAsync(&buf, sizeof(int32_t) * 2 * n, s) != cudaSuccess ||
+        cudaMallocAsync(&flags, sizeof(unsigned long long) * 2, s) != cudaSuccess) {
+        if (buf) cudaFreeAsync(buf, s);
+        set_last_error("scratch allocation failed");
+        return LEIDEN_ERR_OOM;
+    }
+    int32_t *parent = buf, *roots = buf + n;
+    int *changed = reinterpret_cast<int *>(flags);
+    unsigned long long *cnt = flags + 1;
+    unsigned long long h[2] = {0, 0};
+    leiden_status st = LEIDEN_OK;
+    // labels out of range are an error
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned long long) * 2, s);
+    if (e == cudaSuccess) e = launch_cc_labels(n, memb, changed, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && (h[0] & 0xffffffffULL)) {
+        set_last_error("leiden_disconnected: membership labels must lie in [0, n)");
+        st = LEIDEN_ERR_INVALID;
+    }
+    if (e == cudaSuccess && st == LEIDEN_OK) {
+        e = launch_cc_init(n, parent, roots, s);
+        // a pass that finds an edge between two trees lowers some parent,
+        // and on the graphs here components settle within a few passes; 64
+        // is a safety bound, reported as a timeout
+        int pass = 0;
+        for (; e == cudaSuccess && pass < 64; ++pass) {
+            e = cudaMemsetAsync(flags, 0, sizeof(unsigned long long) * 2, s);
+            if (e == cudaSuccess) e = launch_cc_pass(n, off, idx, memb, parent, changed, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess || !(h[0] & 0xffffffffULL)) break;
+        }
+        if (e == cudaSuccess && pass == 64) {
+            set_last_error("leiden_disconnected: components did not settle");
+            st = LEIDEN_ERR_TIMEOUT;
+        }
+        if (e == cudaSuccess && st == LEIDEN_OK) e = launch_cc_count(n, memb, parent, roots, cnt, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && st == LEIDEN_OK) *count = (int64_t)h[1];
+    }
+    cudaFreeAsync(buf, s);
+    cudaFreeAsync(flags, s);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("leiden_disconnected: ") + cudaGetErrorString(e));
+        return LEIDEN_ERR_CUDA;
+    }
+    return st;
+}
+
 // Modularity (Eq. 1) of a membership on a CSR given as device pointers, with
 // scratch from the stream-ordered allocator.
 leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *idx, const float *w,

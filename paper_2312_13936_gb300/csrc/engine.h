@@ -49,6 +49,8 @@ class Handle {
     Impl *p;
 };
 
+leiden_status disconnected_device(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *memb,
+                                  cudaStream_t s, int64_t *count);
 leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                 const int32_t *memb, double gamma, cudaStream_t s, double *q_out);
 

@@ -243,6 +243,18 @@ cudaError_t launch_modularity_batch(int64_t n0, const int64_t *off, const int32_
                                     double gamma, double *sigtot, double *gsum, double *bad, double *q,
                                     cudaStream_t s, bool long_rows = true);
 
+// ---- disconnected communities (k_check.cu, Algorithm 5): components of the
+// intra-community subgraph by hooking and pointer jumping
+// *bad = 1 if a label lies outside [0, n)
+cudaError_t launch_cc_labels(int64_t n, const int32_t *C, int *bad, cudaStream_t s);
+cudaError_t launch_cc_init(int64_t n, int32_t *parent, int32_t *roots, cudaStream_t s);
+// one hooking pass and one jump; *changed = 1 if anything was hooked
+cudaError_t launch_cc_pass(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *C, int32_t *parent,
+                           int *changed, cudaStream_t s);
+// *count += communities with more than one component (labels C in [0, n))
+cudaError_t launch_cc_count(int64_t n, const int32_t *C, const int32_t *parent, int32_t *roots,
+                            unsigned long long *count, cudaStream_t s);
+
 // ---- pass bookkeeping (k_pass.cu)
 // Sigma[c] += K[i], size[c] += 1 over C (acc type)
 cudaError_t launch_community_totals(const int32_t *C, const void *K, bool det, int64_t n, void *Sig, int32_t *size,
