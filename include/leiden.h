@@ -104,8 +104,8 @@ typedef struct {
  * the aggregation (Algorithm 4), and bin 1..6 the degree bin (degree <= 8:
  * a thread per vertex, or a tile of 8 lanes per community; <= 16 and <= 32:
  * a tile of 16/32 lanes; <= 256: warp table; <= 2048: block table; larger:
- * global-memory table; aggregation bin 7: communities of more than 2^20
- * member entries, each aggregated by the whole GPU); bin 0 is the
+ * global-memory table, in the aggregation one packed table per community
+ * that every member vertex inserts into); bin 7 is unused; bin 0 is the
  * persistent kernel that runs a whole sweep (all bins) in one launch. bytes counts the
  * algorithmic bytes of the launches (each array element the method reads or
  * writes counted once at its own size; random gathers count their element,

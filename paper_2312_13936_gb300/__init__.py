@@ -34,7 +34,7 @@ FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE, FLAG_PROFILE, FLAG_STEP_LAU
     1, 2, 4, 8, 16, 32
 PROFILE_CLASSES = 24
 PROFILE_PHASES = ("move", "refine", "aggregate")
-PROFILE_BINS = ("sweep", "thread", "tile16", "tile32", "warp", "block", "global", "giant")
+PROFILE_BINS = ("sweep", "thread", "tile16", "tile32", "warp", "block", "global", "unused")
 TRACE_INIT, TRACE_MOVE, TRACE_REFINE, TRACE_COUNTS, TRACE_RENUMBER = 1, 2, 3, 4, 5
 TRACE_AGG_OFF, TRACE_AGG_DEG, TRACE_AGG_IDX, TRACE_AGG_W, TRACE_DENDRO = 6, 7, 8, 9, 10
 _TRACE_DTYPE = {1: np.int32, 2: np.int32, 3: np.int32, 4: np.int64, 5: np.int32, 6: np.int64, 7: np.int32,

@@ -207,7 +207,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
     CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));
     q.launches += 1;
-    // hub tables for bin 7
+    // global tables for bin 6 (one per block)
     int hub_bits = 0, hub_regions = 0;
     {
         const int maxdeg = q.hsc->maxdeg;
@@ -441,18 +441,8 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     // rows of communities without edges (bin 0) are never visited: empty
     CK(cudaMemsetAsync(q.agg[dst].deg, 0, sizeof(int32_t) * ncomm, s));
     {
-        int64_t mt = (int64_t)q.hsc->maxtdeg;
+        const int64_t mt = (int64_t)q.hsc->maxtdeg;
         r.deg_bound = mt < ncomm ? mt : ncomm;  // degrees of G'' (the next graph)
-        if (mt > kGiantAggEntries) mt = kGiantAggEntries;  // larger ones are bin 7
-        if (mt > ncomm) mt = ncomm;
-        int abits = 0, aregions = 0;
-        if (ako[kBinHub + 1] > ako[kBinHub]) {
-            abits = ceil_log2_h(2 * mt);
-            if (abits < 6) abits = 6;
-            const size_t per = ((size_t)1 << abits) * 12;
-            aregions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
-            ST(q.ensure_hub(abits, aregions, det));
-        }
         AggCtx ac;
         ac.g = G;
         ac.det = det;
@@ -465,42 +455,64 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         ac.out_w = q.agg[dst].w;
         ac.out_K = q.Kagg;
         ac.ncomm = ncomm;
-        ac.hub_keys = q.hub_keys;
-        ac.hub_vals = q.hub_vals;
-        ac.hub_bits = abits;
         ac.err = &q.dsc->err;
-        for (int b = 1; b < kBinGiant; ++b) {
+        for (int b = 1; b < kBinHub; ++b) {
             const int64_t lo = ako[b], hi = ako[b + 1];
             if (hi == lo) continue;
-            const int mb = b <= 4 ? tile_blocks : (b == 5 ? big_blocks : aregions);
             ac.prof = prof_begin(16 + b);
-            CK(launch_aggregate(ac, b, q.list + lo, hi - lo, mb, s));
+            CK(launch_aggregate(ac, b, q.list + lo, hi - lo, b <= 4 ? tile_blocks : big_blocks, s));
             prof_end();
             q.launches++;
         }
-        // giant communities: one at a time, the whole GPU on each
-        const int64_t ng = ako[kBinGiant + 1] - ako[kBinGiant];
-        if (ng > 0) {
-            std::vector<int32_t> giants((size_t)ng);
-            CK(cudaMemcpyAsync(giants.data(), q.list + ako[kBinGiant], sizeof(int32_t) * ng, cudaMemcpyDeviceToHost,
-                               s));
-            std::vector<int64_t> gdeg((size_t)ng);
+        // bin 6: one table per community, packed one after another; the
+        // tables go in chunks of at most kAggTableBytes (a table larger than
+        // that alone)
+        const int64_t K6 = ako[kBinHub + 1] - ako[kBinHub];
+        if (K6 > 0) {
+            const int32_t *list6 = q.list + ako[kBinHub];
+            int64_t *tsize = q.cnt, *toff = q.pos2;
+            int32_t *tidx = q.cursor;
+            CK(cudaMemsetAsync(tidx, 0xff, sizeof(int32_t) * ncomm, s));
+            CK(launch_table_sizes(list6, K6, q.tdeg, ncomm, tsize, tidx, s));
+            CK(launch_exclusive_scan(tsize, toff, K6, q.scan_tmp, s));
+            q.launches += 3;
+            int64_t total = 0;
+            CK(cudaMemcpyAsync(&total, toff + K6, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int64_t k = 0; k < ng; ++k)
-                CK(cudaMemcpyAsync(&gdeg[k], q.tdeg + giants[k], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            for (int64_t k = 0; k < ng; ++k) {
-                const int64_t cap = gdeg[k] < ncomm ? gdeg[k] : ncomm;  // distinct targets
-                int bits = ceil_log2_h(2 * cap);
-                if (bits < 6) bits = 6;
-                ST(q.ensure_hub(bits, 1, det));
+            const int64_t budget = kAggTableBytes / 12;  // slots: 4-byte key + 8-byte value
+            std::vector<int64_t> hoff;
+            if (total > budget) {
+                hoff.resize((size_t)K6 + 1);
+                CK(cudaMemcpyAsync(hoff.data(), toff, sizeof(int64_t) * (K6 + 1), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+            }
+            ac.tab_off = toff;
+            ac.tab_idx = tidx;
+            for (int64_t k0 = 0; k0 < K6;) {
+                int64_t k1 = K6;
+                if (total > budget) {
+                    k1 = k0 + 1;
+                    while (k1 < K6 && hoff[k1 + 1] - hoff[k0] <= budget) ++k1;
+                }
+                const int64_t base = total > budget ? hoff[k0] : 0;
+                const int64_t slots = total > budget ? hoff[k1] - base : total;
+                if (slots > INT32_MAX) {
+                    set_last_error("aggregation table of more than 2^31 slots");
+                    return LEIDEN_ERR_OOM;
+                }
+                ST(q.ensure_hub(0, (int)slots, det));
+                CK(cudaMemsetAsync(q.hub_keys, 0xff, sizeof(int32_t) * slots, s));
+                CK(cudaMemsetAsync(q.hub_vals, 0, 8 * slots, s));
                 ac.hub_keys = q.hub_keys;
                 ac.hub_vals = q.hub_vals;
-                ac.hub_bits = bits;
-                ac.prof = prof_begin(16 + kBinGiant);
-                CK(launch_aggregate_giant(ac, giants[k], q.sm * 8, s));
+                ac.tab_k0 = k0;
+                ac.tab_k1 = k1;
+                ac.tab_base = base;
+                ac.prof = prof_begin(16 + kBinHub);
+                CK(launch_aggregate_tables(ac, list6, q.sm * 8, s));
                 prof_end();
                 q.launches += 2;
+                k0 = k1;
             }
         }
     }

@@ -32,7 +32,9 @@ template <class P, class Wi, class Wo> struct AV {
     A *out_K;
     int32_t *hub_keys;
     A *hub_vals;
-    int hub_bits;
+    const int64_t *tab_off;
+    const int32_t *tab_idx;
+    int64_t tab_k0, tab_k1, tab_base;
     int64_t ncomm;
     int *err;
     unsigned long long *prof;
@@ -55,7 +57,11 @@ template <class P, class Wi, class Wo> AV<P, Wi, Wo> aview(const AggCtx &c) {
     a.out_K = static_cast<A *>(c.out_K);
     a.hub_keys = c.hub_keys;
     a.hub_vals = static_cast<A *>(c.hub_vals);
-    a.hub_bits = c.hub_bits;
+    a.tab_off = c.tab_off;
+    a.tab_idx = c.tab_idx;
+    a.tab_k0 = c.tab_k0;
+    a.tab_k1 = c.tab_k1;
+    a.tab_base = c.tab_base;
     a.ncomm = c.ncomm;
     a.err = c.err;
     a.prof = c.prof;
@@ -218,25 +224,18 @@ __global__ void __launch_bounds__(256) k_agg_warp(AV<P, Wi, Wo> a, const int32_t
     pc.flush(a.prof);
 }
 
-// ------------------------------------------------ block / hub table bins
+// ------------------------------------------------------ block table bin
 constexpr int kAggThreads = 512;
 
-template <class P, class Wi, class Wo, bool HUB>
+template <class P, class Wi, class Wo>
 __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, const int32_t *__restrict__ list,
                                                           int64_t count) {
     using A = typename P::acc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_written;
     __shared__ A s_k[kAggThreads / 32];
-    int32_t *keys;
-    A *vals;
-    if (HUB) {
-        keys = a.hub_keys + ((int64_t)blockIdx.x << a.hub_bits);
-        vals = a.hub_vals + ((int64_t)blockIdx.x << a.hub_bits);
-    } else {
-        vals = reinterpret_cast<A *>(smem_raw);
-        keys = reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
-    }
+    A *vals = reinterpret_cast<A *>(smem_raw);
+    int32_t *keys = reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
     ProfCounts pc;
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
@@ -248,10 +247,6 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
         int bits = ceil_log2(2 * cap);
         if (bits < 6) bits = 6;
         __syncthreads();
-        if (HUB && bits > a.hub_bits) {
-            if (tid == 0) set_error(a.err, kErrHashFull);
-            continue;
-        }
         const int64_t S = 1LL << bits;
         for (int64_t s = tid; s < S; s += blockDim.x) {
             keys[s] = -1;
@@ -303,65 +298,153 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
     pc.flush(a.prof);
 }
 
-// ------------------------------------------------------ giant communities
-// Every warp of the grid takes members of community c in turn; its lanes
-// stride over the member's entries and insert them into the one table.
-template <class P, class Wi, class Wo>
-__global__ void __launch_bounds__(256) k_agg_giant_insert(AV<P, Wi, Wo> a, int32_t c) {
-    using A = typename P::acc;
-    const int lane = threadIdx.x & 31;
-    const int64_t m0 = a.coff[c];
-    const int64_t nm = a.coff[c + 1] - m0;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < nm; k += warps) {
-        const int32_t u = a.members[m0 + k];
-        const int64_t e0 = a.off[u];
-        const int32_t du = a.deg[u];
-        for (int32_t e = lane; e < du; e += 32)
-            if (!hash_add(a.hub_keys, a.hub_vals, a.hub_bits, a.Cd[a.idx[e0 + e]], wconv<A>(a.w[e0 + e])))
-                set_error(a.err, kErrHashFull);
+// ------------------------------------------------- bin 6: packed tables
+__global__ void k_tab_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, int64_t ncomm,
+                            int64_t *tab_size, int32_t *tab_idx) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = list[k];
+        const int64_t cap = tdeg[c] < ncomm ? tdeg[c] : ncomm;  // distinct targets
+        int bits = ceil_log2(2 * cap);
+        if (bits < 6) bits = 6;
+        tab_size[k] = 1LL << bits;
+        tab_idx[c] = (int32_t)k;
     }
 }
-// Write the table's entries as row c (order unspecified); out_deg[c] counts
-// them (it starts at 0) and out_K[c] sums their weights (started at 0).
+
+// Sum of v over the lanes of peers (every lane of peers calls it, with the
+// same peers).
+template <class A>
+__device__ __forceinline__ A peer_sum(unsigned peers, A v) {
+    if (peers == kFull) return warp_sum(v);
+    A s = 0;
+    for (unsigned m = peers; m; m &= m - 1) s += __shfl_sync(peers, v, __ffs(m) - 1);
+    return s;
+}
+
+// Every vertex of a community with a table in [tab_k0, tab_k1) inserts its
+// entries. Vertices are taken in the order of the community-vertex CSR, so
+// the warps in flight share a few tables (which stay in L2) instead of
+// touching all of them. A warp takes 32 consecutive members and walks their
+// entries as
+// one flat range (lane j takes entry p0 + j; its row is found by a binary
+// search over the warp's inclusive degree sums), so rows of any length keep
+// every lane busy; entries of one step with the same (table, key) are summed
+// first and inserted once, which keeps hot keys (a large community's own
+// entries) from serialising on one address.
 template <class P, class Wi, class Wo>
-__global__ void __launch_bounds__(256) k_agg_giant_write(AV<P, Wi, Wo> a, int32_t c) {
+__global__ void __launch_bounds__(256) k_agg_tab_insert(AV<P, Wi, Wo> a) {
     using A = typename P::acc;
     const int lane = threadIdx.x & 31;
-    const int64_t S = 1LL << a.hub_bits;
-    const int64_t o0 = a.out_off[c];
-    A kpart = 0;
-    for (int64_t s0 = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)); s0 < S;
-         s0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = s0 + lane;
-        const int32_t k = s < S ? a.hub_keys[s] : -1;
-        const unsigned ball = __ballot_sync(kFull, k >= 0);
-        int base = 0;
-        if (lane == 0 && ball) base = atomicAdd(&a.out_deg[c], (int)__popc(ball));
-        base = __shfl_sync(kFull, base, 0);
+    const int64_t n = a.coff[a.ncomm];  // members of all communities
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    ProfCounts pc;
+    for (int64_t u0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; u0 < n; u0 += warps * 32) {
+        int64_t k = -1, d = 0, rstart = 0, base = 0;
+        int bits = 0;
+        int32_t u = 0;
+        if (u0 + lane < n) {
+            u = a.members[u0 + lane];
+            const int32_t c = a.Cd[u];
+            k = c >= 0 ? a.tab_idx[c] : -1;
+            if (k < a.tab_k0 || k >= a.tab_k1) k = -1;
+        }
         if (k >= 0) {
-            const int pos = base + __popc(ball & ((1u << lane) - 1u));
-            const Wo wo = out_weight<Wo>(a.hub_vals[s]);
-            a.out_idx[o0 + pos] = k;
-            a.out_w[o0 + pos] = wo;
-            kpart += wconv<A>(wo);
+            base = a.tab_off[k] - a.tab_base;
+            bits = __ffsll((long long)(a.tab_off[k + 1] - a.tab_off[k])) - 1;
+            rstart = a.off[u];
+            d = a.deg[u];
+            if (a.prof) {
+                pc.v[1]++;
+                pc.v[2] += d;
+            }
+        }
+        int64_t incl = d;  // inclusive sum of the warp's degrees
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t x = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += x;
+        }
+        rstart -= incl - d;  // entry p of the flat range is rstart + p of its owner
+        const int64_t total = __shfl_sync(kFull, incl, 31);
+        for (int64_t p0 = 0; p0 < total; p0 += 32) {
+            const int64_t p = p0 + lane;
+            int own = 0;  // lanes whose rows end at or before p
+            for (int st = 16; st >= 1; st >>= 1)
+                if (__shfl_sync(kFull, incl, own + st - 1) <= p) own += st;
+            own &= 31;
+            const int64_t e = __shfl_sync(kFull, rstart, own) + p;
+            const int64_t tb = __shfl_sync(kFull, base, own);
+            const int tbits = __shfl_sync(kFull, bits, own);
+            const int64_t tk = __shfl_sync(kFull, k, own);
+            const bool valid = p < total;
+            int32_t key = -1;
+            A v = 0;
+            if (valid) {
+                key = a.Cd[a.idx[e]];
+                v = wconv<A>(a.w[e]);
+            }
+            const unsigned long long pair =
+                valid ? ((unsigned long long)tk << 32) | (uint32_t)key : ~0ull;
+            const unsigned peers = __match_any_sync(kFull, pair);
+            v = peer_sum(peers, v);
+            if (valid && lane == __ffs(peers) - 1)
+                if (!hash_add(a.hub_keys + tb, a.hub_vals + tb, tbits, key, v)) set_error(a.err, kErrHashFull);
         }
     }
-    kpart = warp_sum(kpart);
-    if (lane == 0 && kpart != (A)0) atomic_add_acc(&a.out_K[c], kpart);
+    pc.flush(a.prof);
+}
+
+// One block per table: its distinct entries become the community's row
+// (order unspecified), their count out_deg[c] and their sum K''[c].
+template <class P, class Wi, class Wo>
+__global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const int32_t *__restrict__ list) {
+    using A = typename P::acc;
+    __shared__ int s_written;
+    __shared__ A s_k[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    ProfCounts pc;
+    for (int64_t k = a.tab_k0 + blockIdx.x; k < a.tab_k1; k += gridDim.x) {
+        const int32_t c = list[k];
+        const int64_t base = a.tab_off[k] - a.tab_base, S = a.tab_off[k + 1] - a.tab_off[k];
+        const int64_t o0 = a.out_off[c];
+        __syncthreads();
+        if (threadIdx.x == 0) s_written = 0;
+        __syncthreads();
+        A kpart = 0;
+        for (int64_t s0 = (int64_t)wib * 32; s0 < S; s0 += (int64_t)blockDim.x) {
+            const int64_t sl = s0 + lane;
+            const int32_t key = sl < S ? a.hub_keys[base + sl] : -1;
+            const unsigned ball = __ballot_sync(kFull, key >= 0);
+            int pos0 = 0;
+            if (lane == 0 && ball) pos0 = atomicAdd(&s_written, __popc(ball));
+            pos0 = __shfl_sync(kFull, pos0, 0);
+            if (key >= 0) {
+                const int pos = pos0 + __popc(ball & ((1u << lane) - 1u));
+                const Wo wo = out_weight<Wo>(a.hub_vals[base + sl]);
+                a.out_idx[o0 + pos] = key;
+                a.out_w[o0 + pos] = wo;
+                kpart += wconv<A>(wo);
+            }
+        }
+        kpart = warp_sum(kpart);
+        if (lane == 0) s_k[wib] = kpart;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            A ks = 0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) ks += s_k[w2];
+            a.out_deg[c] = s_written;
+            a.out_K[c] = ks;
+            pc.v[0]++;
+            pc.v[3] += s_written;
+        }
+    }
+    pc.flush(a.prof);
 }
 
 template <class P, class Wi, class Wo>
-cudaError_t giant_typed(const AggCtx &c, int32_t comm, int blocks, cudaStream_t s) {
-    using A = typename P::acc;
+cudaError_t tables_typed(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s) {
     auto a = aview<P, Wi, Wo>(c);
-    const size_t S = (size_t)1 << c.hub_bits;
-    cudaError_t e = cudaMemsetAsync(c.hub_keys, 0xff, S * sizeof(int32_t), s);  // keys -1: empty
-    if (e == cudaSuccess) e = cudaMemsetAsync(c.hub_vals, 0, S * sizeof(A), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(static_cast<A *>(c.out_K) + comm, 0, sizeof(A), s);
-    if (e != cudaSuccess) return e;
-    k_agg_giant_insert<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, comm);
-    k_agg_giant_write<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, comm);
+    k_agg_tab_insert<P, Wi, Wo><<<blocks, 256, 0, s>>>(a);
+    k_agg_tab_write<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, list);
     return cudaGetLastError();
 }
 
@@ -379,13 +462,12 @@ cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t cou
         case 4: k_agg_warp<P, Wi, Wo><<<grid(8), 256, 0, s>>>(a, list, count); break;
         case 5: {
             const size_t sm = (sizeof(typename P::acc) + sizeof(int32_t)) * kBlockSlots;
-            auto kern = k_agg_block<P, Wi, Wo, false>;
+            auto kern = k_agg_block<P, Wi, Wo>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             kern<<<grid(1), kAggThreads, sm, s>>>(a, list, count);
             break;
         }
-        case 6: k_agg_block<P, Wi, Wo, true><<<grid(1), kAggThreads, 0, s>>>(a, list, count); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -393,12 +475,21 @@ cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t cou
 
 }  // namespace
 
-cudaError_t launch_aggregate_giant(const AggCtx &c, int32_t comm, int blocks, cudaStream_t s) {
+cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, int64_t ncomm,
+                               int64_t *tab_size, int32_t *tab_idx, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t b = (count + 255) / 256;
+    k_tab_sizes<<<(int)(b < 2432 ? b : 2432), 256, 0, s>>>(list, count, tdeg, ncomm, tab_size, tab_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s) {
+    if (c.tab_k1 <= c.tab_k0) return cudaSuccess;
     if (c.det) {
-        if (c.g.w_int) return giant_typed<Det, int32_t, int32_t>(c, comm, blocks, s);
-        return giant_typed<Det, float, int32_t>(c, comm, blocks, s);
+        if (c.g.w_int) return tables_typed<Det, int32_t, int32_t>(c, list, blocks, s);
+        return tables_typed<Det, float, int32_t>(c, list, blocks, s);
     }
-    return giant_typed<Async, float, float>(c, comm, blocks, s);
+    return tables_typed<Async, float, float>(c, list, blocks, s);
 }
 
 cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,

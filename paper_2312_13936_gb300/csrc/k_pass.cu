@@ -56,7 +56,7 @@ __global__ void k_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, i
 }
 __global__ void k_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key) {
     GRID_STRIDE(c, ncomm) {
-        const int b = tdeg[c] > kGiantAggEntries ? kBinGiant : degree_bin(tdeg[c]);
+        const int b = degree_bin(tdeg[c]);
         key[c] = b == 0 ? -1 : b;
     }
 }

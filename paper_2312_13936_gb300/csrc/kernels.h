@@ -14,7 +14,8 @@ namespace lgb {
 //   bin 3  d <= 32     a tile of 32 lanes
 //   bin 4  d <= 256    one warp, shared-memory table
 //   bin 5  d <= 2048   one block, shared-memory table
-//   bin 6  larger      one block, global-memory table
+//   bin 6  larger      one block, global-memory table (aggregation: one
+//                      packed table per community, filled by all vertices)
 constexpr int kNumBins = 8;
 constexpr int kThreadMaxDeg = 8;
 constexpr int kWarpMaxDeg = 256;
@@ -22,14 +23,13 @@ constexpr int kBlockMaxDeg = 2048;
 constexpr int kWarpSlots = 512;     // 8 warp tables fill the same 48 KB as one block table
 constexpr int kBlockSlots = 4096;
 constexpr int kBinHub = 6;
+// the packed bin-6 tables of the aggregation are cleared and filled in
+// chunks of at most this many bytes (12 per slot)
+constexpr int64_t kAggTableBytes = (int64_t)8 << 30;
 // rows longer than this are walked by a whole warp in the schedule and
 // modularity kernels (their long-row variants, chosen when a graph's degree
 // bound exceeds it)
 constexpr int32_t kLongRow = 64;
-// aggregation only: communities of more member entries than this form bin 7
-// and are aggregated one at a time by the whole GPU
-constexpr int64_t kGiantAggEntries = 1 << 20;
-constexpr int kBinGiant = 7;
 __host__ __device__ inline int degree_bin(int64_t d) {
     return d <= 0 ? 0 : d <= kThreadMaxDeg ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= kWarpMaxDeg ? 4 : d <= kBlockMaxDeg ? 5 : 6;
 }
@@ -74,7 +74,7 @@ struct SweepCtx {
     int32_t *iters_out = nullptr;           // sweeps executed
     void *dq_acc = nullptr;       // sweep delta-modularity numerator (acc type)
     unsigned long long *moved = nullptr;  // refinement: accepted moves
-    int32_t *hub_keys = nullptr;  // global tables for bin 7 (one region per block)
+    int32_t *hub_keys = nullptr;  // global tables for bin 6 (one region per block)
     void *hub_vals = nullptr;
     int hub_bits = 0, hub_regions = 0;
     unsigned *bar = nullptr;      // grid barrier state (2 words, zero-initialised once)
@@ -123,18 +123,30 @@ struct AggCtx {
     void *out_w = nullptr;            // float (async) or int32 (det)
     void *out_K = nullptr;            // K'' (acc type): row sums of G''
     int64_t ncomm = 0;
+    // bin 6 (communities of more than kBlockMaxDeg member entries): one
+    // global table per community, packed: table k (community list[k]) owns
+    // slots [tab_off[k], tab_off[k+1]) (a power of two); tab_idx[c] = k or -1.
+    // A launch takes tables [tab_k0, tab_k1), whose slots start at tab_base
+    // within hub_keys/hub_vals.
     int32_t *hub_keys = nullptr;
     void *hub_vals = nullptr;
-    int hub_bits = 0;
+    const int64_t *tab_off = nullptr;
+    const int32_t *tab_idx = nullptr;
+    int64_t tab_k0 = 0, tab_k1 = 0, tab_base = 0;
     int *err = nullptr;
     unsigned long long *prof = nullptr;
 };
+// bins 1-5 of the aggregation: one community per tile, warp or block
 cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
                              cudaStream_t s);
-// one community of bin 7: every block inserts its member entries into one
-// global table (hub_keys/hub_vals, 2^hub_bits slots, cleared here), then the
-// distinct entries are written as row c
-cudaError_t launch_aggregate_giant(const AggCtx &c, int32_t comm, int blocks, cudaStream_t s);
+// bin 6 sizes: tab_size[k] = 2^max(6, ceil log2(2 min(tdeg, ncomm))) of
+// community list[k], tab_idx[list[k]] = k
+cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, int64_t ncomm,
+                               int64_t *tab_size, int32_t *tab_idx, cudaStream_t s);
+// bin 6, tables [tab_k0, tab_k1) (cleared by the caller): every vertex's
+// entries go into its community's table (long rows by the whole warp), then
+// one block per table writes its distinct entries as the community's row
+cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s);
 
 // ---- utilities (k_util.cu)
 cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s);
@@ -274,7 +286,7 @@ cudaError_t launch_comm_counts(const int32_t *Cd, const int32_t *deg, int64_t n,
                                cudaStream_t s);
 cudaError_t launch_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, int32_t *cursor, int32_t *members,
                              cudaStream_t s);
-// bins of communities by total degree (bin 7: more than kGiantAggEntries)
+// bins of communities by total degree
 cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key, cudaStream_t s);
 // move-based labels: bnd[Cd[i]] = CB[i]; rep[b] = min s; label[s] = rep[bnd[s]] (Cd < 0: skipped)
 cudaError_t launch_bound_labels(const int32_t *Cd, const int32_t *CB, int64_t n, int64_t ncomm, int32_t *bnd,
