@@ -87,6 +87,15 @@
  *       neighbour, hence in another step); in later steps it keeps every
  *       accepted vertex joined to a community that keeps the neighbour it
  *       saw.
+ *   Variants (flags, both modes):
+ *   V1  OG_REFINE_LABELS: refine-based super-vertex labels (Section 4.1):
+ *       every super-vertex starts a pass in its own community instead of
+ *       the move-based one of R3.
+ *   V2  OG_LOUVAIN: the Louvain method the paper compares with (Section 5):
+ *       no refinement; the refined partition of a pass is its local-moving
+ *       partition (so l_j = 0 and R5' reduces to l_i <= 1), and aggregation
+ *       merges the local-moving communities. Communities need not be
+ *       connected.
  *   Both modes:
  *   R5' The passes stop (global convergence) when the local-moving phase
  *       converged in its first sweep (l_i <= 1) and the refinement split no
@@ -100,7 +109,7 @@
 
 enum { OG_OK = 0, OG_ERR_INVALID = -1, OG_ERR_OOM = -3, OG_ERR_UNSUPPORTED = -6, OG_ERR_OVERFLOW = -7 };
 enum { OG_SEQ = 0, OG_SYNC = 1 };
-enum { OG_REFINE_SINGLE_SWEEP = 1, OG_NO_PRUNE = 2 };
+enum { OG_REFINE_SINGLE_SWEEP = 1, OG_NO_PRUNE = 2, OG_REFINE_LABELS = 4, OG_LOUVAIN = 8 };
 
 /* what-codes passed to the trace callback */
 enum {
@@ -124,7 +133,8 @@ typedef struct {
     int32_t max_iterations;       /* MAX_ITERATIONS, default 20 */
     int32_t max_passes;           /* MAX_PASSES (R1), default 10 */
     int32_t mode;                 /* OG_SEQ or OG_SYNC */
-    int32_t flags;                /* OG_REFINE_SINGLE_SWEEP, OG_NO_PRUNE (SEQ, tests only) */
+    int32_t flags;                /* OG_REFINE_SINGLE_SWEEP, OG_NO_PRUNE (SEQ, tests only),
+                                     OG_REFINE_LABELS, OG_LOUVAIN (V1, V2) */
     int32_t schedule_layers;      /* SYNC: L, priority layers (S0), default 32 */
     int32_t schedule_buckets;     /* SYNC: B, buckets after the last layer (S0), default 16 */
     uint64_t seed;                /* SYNC: priority seed (S0), default 0 */
@@ -880,16 +890,21 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
         if (li < 0) goto done;
         if (cb) cb(ctx, lp, OG_T_MOVE, Cp, n);
 
-        /* C'_B <- C'; C' <- [0..|V'|); Sigma' <- K' */
-        for (int64_t i = 0; i < n; ++i) {
-            CB[i] = Cp[i]; Cp[i] = (int32_t)i; Sig[i] = K[i]; Si[i] = Ki[i]; size[i] = 1;
-        }
-        /* refinement phase (Algorithm 3) */
-        int single = (p->flags & OG_REFINE_SINGLE_SWEEP) != 0;
-        int lj = sync ? refine_sync(&G, CB, Cp, Ki, Si, size, (int64_t)two_m, p->max_iterations, single,
+        int lj = 0;
+        if (p->flags & OG_LOUVAIN) { /* V2: the local-moving partition is the refined one */
+            for (int64_t i = 0; i < n; ++i) CB[i] = Cp[i];
+        } else {
+            /* C'_B <- C'; C' <- [0..|V'|); Sigma' <- K' */
+            for (int64_t i = 0; i < n; ++i) {
+                CB[i] = Cp[i]; Cp[i] = (int32_t)i; Sig[i] = K[i]; Si[i] = Ki[i]; size[i] = 1;
+            }
+            /* refinement phase (Algorithm 3) */
+            int single = (p->flags & OG_REFINE_SINGLE_SWEEP) != 0;
+            lj = sync ? refine_sync(&G, CB, Cp, Ki, Si, size, (int64_t)two_m, p->max_iterations, single,
                                     layer, nl, &H)
                       : refine_seq(&G, CB, Cp, K, Sig, size, gamma, two_m, p->max_iterations, single, &H);
-        if (lj < 0) goto done;
+            if (lj < 0) goto done;
+        }
         if (cb) cb(ctx, lp, OG_T_REFINE, Cp, n);
 
         /* |Gamma| (R4): number of non-empty refined communities */
@@ -931,6 +946,8 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
         for (int64_t s = 0; s < ncomm; ++s)
             if (rep[bound_of[s]] < 0) rep[bound_of[s]] = (int32_t)s;
         for (int64_t s = 0; s < ncomm; ++s) init[s] = rep[bound_of[s]];
+        if (p->flags & OG_REFINE_LABELS) /* V1: every super-vertex alone */
+            for (int64_t s = 0; s < ncomm; ++s) init[s] = (int32_t)s;
 
         graph_free(&G);
         G = G2;

@@ -371,3 +371,95 @@ def test_ties_go_to_the_lowest_community_id():
     g = gen.from_edges(3, [0, 0], [1, 2])
     r = oracle.leiden(g, mode=oracle.SEQ, max_passes=1, trace=True)
     assert r.trace[0][oracle.T_MOVE].tolist() == [1, 1, 1]
+
+
+# ------------------------------------- variants: refine-based labels, Louvain
+VARIANTS = (oracle.REFINE_LABELS, oracle.LOUVAIN)
+
+
+def _components_inside(g, membership):
+    """Disconnected communities counted with scipy's connected components on
+    the subgraph that keeps only intra-community edges (independent of the
+    oracle's own BFS)."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    rows = np.repeat(np.arange(g.n), np.diff(g.offsets))
+    keep = membership[rows] == membership[g.indices]
+    a = csr_matrix((np.ones(int(keep.sum())), (rows[keep], g.indices[keep])), shape=(g.n, g.n))
+    _, comp = connected_components(a, directed=False)
+    bad = 0
+    for c in np.unique(membership):
+        bad += np.unique(comp[membership == c]).size > 1
+    return bad
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("flags", VARIANTS)
+@pytest.mark.parametrize("k,r", [(5, 16), (8, 30)])
+def test_variants_find_the_cliques(mode, flags, k, r):
+    """Both variants keep the ring-of-cliques closed form of Eq. 1."""
+    res = oracle.leiden(gen.ring_of_cliques(k, r), mode=mode, flags=flags)
+    assert res.status == 0
+    L = k * (k - 1) / 2
+    assert abs(res.modularity - (L / (L + 1) - 1.0 / r)) < 1e-12
+    assert np.array_equal(res.membership, np.repeat(np.arange(r), k))
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("flags", VARIANTS)
+def test_variants_against_brute_force(mode, flags):
+    """Q <= Q_opt on seeded G(n, p) graphs, equality on the designated family."""
+    for seed in range(40):
+        g = gen.gnp(6 + seed % 5, 0.45, seed=seed, wmax=3)
+        if g.nnz == 0:
+            continue
+        q_opt, _ = oracle.brute_force(g)
+        r = oracle.leiden(g, mode=mode, flags=flags)
+        assert r.status == 0 and r.modularity <= q_opt + 1e-12
+    for g in (gen.ring_of_cliques(3, 4), _from_golden_edges(_golden("two_triangles_bridge.json"))):
+        q_opt, _ = oracle.brute_force(g)
+        assert abs(oracle.leiden(g, mode=mode, flags=flags).modularity - q_opt) < 1e-12
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_louvain_first_pass_is_the_local_moving_phase(mode):
+    """One Louvain pass is Algorithm 2 alone: its partition equals the
+    local-moving partition of the Leiden method's first pass."""
+    for g in (gen.sbm(2000, 10, 0.05, 0.002, seed=11), gen.road(40), gen.rmat(10, 8, seed=2)):
+        lv = oracle.leiden(g, mode=mode, flags=oracle.LOUVAIN, max_passes=1)
+        ld = oracle.leiden(g, mode=mode, trace=True)
+        moved = ld.trace[0][oracle.T_MOVE]
+        assert ari(lv.membership, moved) == 1.0
+        # and it stops with the local-moving count as |Gamma| (no refinement sweeps)
+        lt = oracle.leiden(g, mode=mode, flags=oracle.LOUVAIN, trace=True).trace[0]
+        assert lt[oracle.T_COUNTS][2] == 0
+        assert lt[oracle.T_COUNTS][3] == np.unique(lt[oracle.T_MOVE]).size
+
+
+def test_louvain_can_leave_a_community_disconnected():
+    """The shortcoming the refinement phase removes (Sections 2.2-2.3): on this
+    graph the Louvain variant returns an internally disconnected community,
+    while the Leiden method (either label rule) returns connected ones."""
+    g = gen.gnp(18, 0.25, seed=2108, wmax=3)
+    lv = oracle.leiden(g, mode=oracle.SEQ, flags=oracle.LOUVAIN)
+    assert _components_inside(g, lv.membership) >= 1
+    assert oracle.disconnected(g, lv.membership)[0] == _components_inside(g, lv.membership)
+    for flags in (0, oracle.REFINE_LABELS):
+        r = oracle.leiden(g, mode=oracle.SEQ, flags=flags)
+        assert _components_inside(g, r.membership) == 0
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_refine_labels_start_every_pass_from_singletons(mode):
+    g = gen.sbm(3000, 12, 0.04, 0.002, seed=17)
+    r = oracle.leiden(g, mode=mode, flags=oracle.REFINE_LABELS, trace=True)
+    assert r.passes >= 2
+    for lp in range(1, r.passes):
+        init = r.trace[lp][oracle.T_INIT_LABELS]
+        assert np.array_equal(init, np.arange(init.size))
+    # the default (move-based) rule does not: some super-vertices share a label
+    d = oracle.leiden(g, mode=mode, trace=True)
+    assert np.unique(d.trace[1][oracle.T_INIT_LABELS]).size < d.trace[1][oracle.T_INIT_LABELS].size
+    for flags in (0, oracle.REFINE_LABELS):
+        m = oracle.leiden(g, mode=mode, flags=flags).membership
+        assert _components_inside(g, m) == 0
