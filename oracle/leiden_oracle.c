@@ -57,13 +57,17 @@
  *       moves made in a sweep with tau; tau is divided by TOLERANCE_DROP
  *       after every aggregated pass.
  *   SYNC-only:
- *   S0  Sweep order: priority steps. prio(v) is output number v+1 of
- *       SplitMix64 (Steele, Lea & Flood 2014) from state seed + pass; u
- *       precedes v when prio(u) > prio(v), ties by smaller id. layer(v) =
+ *   S0  Sweep order: priority steps. h(v) is output number v+1 of
+ *       SplitMix64 (Steele, Lea & Flood 2014) from state seed + pass, and
+ *       prio(v) = deg(v) * 2^32 + (h(v) >> 32): the row length first, so
+ *       vertices of higher degree go first (an importance ordering, one of
+ *       the Louvain optimisations the paper carries over, Section 3), the
+ *       hash breaking ties at random; u precedes v when prio(u) > prio(v),
+ *       ties by smaller id. layer(v) =
  *       1 + max layer of v's preceding neighbours (0 if none) -- the rounds
  *       of Jones & Plassmann's parallel colouring. A vertex with
  *       layer(v) < L-1 (L = schedule_layers) takes step layer(v); every
- *       other vertex takes step L-1 + ((prio(v) >> 32) mod B) (B =
+ *       other vertex takes step L-1 + ((h(v) >> 32) mod B) (B =
  *       schedule_buckets). Steps are processed in increasing order. A step
  *       below L-1 holds no two adjacent vertices, so on those edges the two
  *       ends are handled in priority order as in a sequential sweep. Inside a
@@ -135,7 +139,7 @@ typedef struct {
     int32_t mode;                 /* OG_SEQ or OG_SYNC */
     int32_t flags;                /* OG_REFINE_SINGLE_SWEEP, OG_NO_PRUNE (SEQ, tests only),
                                      OG_REFINE_LABELS, OG_LOUVAIN (V1, V2) */
-    int32_t schedule_layers;      /* SYNC: L, priority layers (S0), default 32 */
+    int32_t schedule_layers;      /* SYNC: L, priority layers (S0), default 1000 */
     int32_t schedule_buckets;     /* SYNC: B, buckets after the last layer (S0), default 16 */
     uint64_t seed;                /* SYNC: priority seed (S0), default 0 */
 } og_params;
@@ -339,7 +343,10 @@ int32_t og_schedule(int64_t n, const int64_t *off, const int32_t *deg, const int
     int32_t *order = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
     uint8_t *done = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
     if (!prio || !order || !done || cap < 1 || buckets < 1) { free(prio); free(order); free(done); return -1; }
-    for (int64_t v = 0; v < n; ++v) { prio[v] = og_splitmix64_at(state, (uint64_t)v); order[v] = (int32_t)v; }
+    for (int64_t v = 0; v < n; ++v) {
+        prio[v] = ((uint64_t)deg[v] << 32) | (og_splitmix64_at(state, (uint64_t)v) >> 32);
+        order[v] = (int32_t)v;
+    }
     g_sort_prio = prio;
     qsort(order, (size_t)n, sizeof(int32_t), cmp_by_priority);
     int32_t used = 0;
@@ -354,7 +361,8 @@ int32_t og_schedule(int64_t n, const int64_t *off, const int32_t *deg, const int
         done[v] = 1;
     }
     for (int64_t v = 0; v < n; ++v) {
-        if (layer[v] == cap - 1) layer[v] = cap - 1 + (int32_t)((prio[v] >> 32) % (uint64_t)buckets);
+        if (layer[v] == cap - 1)
+            layer[v] = cap - 1 + (int32_t)((og_splitmix64_at(state, (uint64_t)v) >> 32) % (uint64_t)buckets);
         if (layer[v] + 1 > used) used = layer[v] + 1;
     }
     free(prio); free(order); free(done);
@@ -782,7 +790,7 @@ void og_params_default(og_params *p) {
     p->max_passes = 10;
     p->mode = OG_SEQ;
     p->flags = 0;
-    p->schedule_layers = 32;
+    p->schedule_layers = 1000;
     p->schedule_buckets = 16;
     p->seed = 0;
 }
