@@ -28,6 +28,11 @@ arrival times, by a plain server that runs one leiden_run at a time. The
 offered rate is set to 90% of the plain server's measured service rate;
 p50/p99 latency (arrival to result on the host), graphs/s and the mean
 modularity of both are reported. Rank 0 only.
+
+And the paper's variants on the bench graph ("variants", rank 0, outside the
+timed region): the Louvain method (no refinement) and refine-based
+super-vertex labels, each with its time, modularity and fraction of
+disconnected communities beside the Leiden run's.
 """
 import argparse
 import hashlib
@@ -58,7 +63,6 @@ def parse():
     ap.add_argument("--side", type=int, default=5000, help="road lattice side")
     ap.add_argument("--rmat-scale", type=int, default=25)
     ap.add_argument("--mode", default="async", choices=["async", "det"])
-    ap.add_argument("--relabel", action="store_true", help="sweep on a copy relabelled by schedule step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-side", type=int, default=3000, help="road side of the CPU-baseline sample")
@@ -68,10 +72,43 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-sample", type=int, default=128, help="graphs of the per-graph loop")
     ap.add_argument("--no-serve", action="store_true", help="skip the served form")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the Louvain and refine-based-label comparison on the same graph")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-pool", type=int, default=24, help="distinct graphs the requests cycle through")
     ap.add_argument("--serve-load", type=float, default=0.9, help="offered rate / plain server's service rate")
     return ap.parse_args()
+
+
+def variants_form(h, off, idx, mode, flags, stream, runs=5):
+    """The paper's comparisons on the bench graph (outside the timed region):
+    the Louvain variant (no refinement, Section 5: Leiden was 13% slower
+    and Louvain left 4.0% of its communities disconnected) and refine-based
+    super-vertex labels (Section 4.1: about the same time and modularity as
+    move-based ones). Median of `runs` device-timed runs each."""
+    import statistics
+
+    import torch
+
+    import paper_2312_13936_gb300 as lg
+    out = {}
+    for name, f in (("leiden", 0), ("louvain", lg.FLAG_LOUVAIN), ("refine_labels", lg.FLAG_REFINE_LABELS)):
+        h.run(mode=mode, flags=flags | f)
+        ts, qs = [], []
+        for _ in range(runs):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            memb, q, st = h.run(mode=mode, flags=flags | f)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            qs.append(q)
+        bad = lg.disconnected(off, idx, memb)
+        out[name] = {"ms": statistics.median(ts), "modularity": statistics.median(qs), "communities": st.communities,
+                     "disconnected": bad, "disconnected_frac": bad / max(1, st.communities), "passes": st.passes}
+    out["leiden_over_louvain_time"] = out["leiden"]["ms"] / out["louvain"]["ms"]
+    return out
 
 
 def workload(args):
@@ -439,7 +476,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     g, wname = workload(args)
     mode = lg.LEIDEN_ASYNC if args.mode == "async" else lg.LEIDEN_DETERMINISTIC
-    base_flags = lg.FLAG_RELABEL if args.relabel else 0
+    base_flags = 0
     dev = torch.device("cuda", local)
     off = torch.as_tensor(g.offsets).to(dev)
     idx = torch.as_tensor(g.indices).to(dev)
@@ -517,6 +554,7 @@ def main():
         e2e = {"value": world * ne * g.nnz / te, "unit": "edges/s",
                "h2d_bytes_per_step": hoff.nbytes + hidx.nbytes + hw.nbytes, "d2h_bytes_per_step": out.nbytes + 8}
 
+    variants = None if (args.no_variants or rank != 0) else variants_form(h, off, idx, mode, base_flags, stream)
     batched = None if args.no_batch else batched_form(args, rank, world, mode, base_flags)
 
     if rank != 0:
@@ -552,6 +590,7 @@ def main():
                                 "other": st.ms_other}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
         "batched": batched,
+        "variants": variants,
         "served": served,
         "kernel_classes": {f"{k[0]}/{k[1]}": v for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
     }

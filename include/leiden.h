@@ -66,10 +66,12 @@ enum {
     LEIDEN_FLAG_PROFILE = 8u,             /* time every sweep/aggregation launch (leiden_profile_get) */
     LEIDEN_FLAG_STEP_LAUNCHES = 16u,      /* one launch per schedule step and degree bin instead of one
                                              persistent launch per sweep (same results; for testing) */
-    LEIDEN_FLAG_RELABEL = 32u             /* asynchronous mode: sweep graphs of >= 65,536 vertices on a copy
-                                             relabelled so that every schedule step and degree bin is a
-                                             contiguous id range (measured slower than the graph's own
-                                             vertex order; kept for comparison) */
+    LEIDEN_FLAG_REFINE_LABELS = 64u,      /* refine-based super-vertex labels (Section 4.1): every
+                                             super-vertex starts the next pass in its own community
+                                             instead of its move-based one */
+    LEIDEN_FLAG_LOUVAIN = 128u            /* the Louvain method of the paper's comparison (Section 5):
+                                             no refinement phase; each pass aggregates its local-moving
+                                             communities, which need not be connected */
 };
 
 typedef struct {
@@ -81,7 +83,9 @@ typedef struct {
     int32_t max_passes;           /* MAX_PASSES (Algorithm 1; not given in the paper); default 10 */
     int32_t mode;                 /* LEIDEN_ASYNC or LEIDEN_DETERMINISTIC */
     uint32_t flags;               /* LEIDEN_FLAG_* */
-    int32_t schedule_layers;      /* L: priority layers of the sweep schedule; default 32 */
+    int32_t schedule_layers;      /* L: priority layers of the sweep schedule (L - 1 + B at most
+                                     1023); 0 (default): 1000 for a graph with a row of more than
+                                     2048 entries, else 32, graph by graph in a batch or server */
     int32_t schedule_buckets;     /* B: priority buckets after the last layer; default 16 */
     uint64_t seed;                /* seed of the schedule's vertex priorities; default 0 */
 } leiden_params;
@@ -208,7 +212,7 @@ leiden_status leiden_batch_run(leiden_graph_t g, const leiden_params *p, int32_t
  * max_graphs graphs in flight, and device_budget bytes for the submitted
  * graphs' own buffers (CSR copy and result; <= 0: half the free device
  * memory after the server's workspace). p fixes the parameters of every run
- * (LEIDEN_FLAG_RELABEL, _TRACE, _PROFILE and _STEP_LAUNCHES are ignored). */
+ * (LEIDEN_FLAG_TRACE, _PROFILE and _STEP_LAUNCHES are ignored). */
 leiden_status leiden_server_create(leiden_server_t *out, const leiden_params *p, int64_t max_vertices,
                                    int64_t max_entries, int32_t max_graphs, int64_t device_budget, void *stream);
 

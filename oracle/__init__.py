@@ -114,7 +114,7 @@ class Result:
 
 def leiden(g, mode: int = SEQ, resolution: float = 1.0, tolerance: float = 0.01,
            aggregation_tolerance: float = 0.8, tolerance_drop: float = 10.0, max_iterations: int = 20,
-           max_passes: int = 10, flags: int = 0, schedule_layers: int = 1000, schedule_buckets: int = 16,
+           max_passes: int = 10, flags: int = 0, schedule_layers: int = 0, schedule_buckets: int = 16,
            seed: int = 0,
            trace: bool = False) -> Result:
     """Algorithm 1 on a symmetric CSR ``g`` (fields n, offsets, indices, weights)."""

@@ -66,9 +66,15 @@
  *       ties by smaller id. layer(v) =
  *       1 + max layer of v's preceding neighbours (0 if none) -- the rounds
  *       of Jones & Plassmann's parallel colouring. A vertex with
- *       layer(v) < L-1 (L = schedule_layers) takes step layer(v); every
- *       other vertex takes step L-1 + ((h(v) >> 32) mod B) (B =
- *       schedule_buckets). Steps are processed in increasing order. A step
+ *       layer(v) < L-1 takes step layer(v); every other vertex takes step
+ *       L-1 + ((h(v) >> 32) mod B) (B = schedule_buckets). L is
+ *       schedule_layers, or, when that is 0 (the default), 1000 for an
+ *       input with a row of more than 2048 entries and 32 otherwise: on
+ *       heavy-tailed graphs the hubs must be handled one layer after another
+ *       (vertices past the cap share bucket steps with their neighbours,
+ *       and on R-MAT graphs the refinement of the last pass then splits
+ *       large communities), elsewhere a short schedule is as good and
+ *       cheaper. Steps are processed in increasing order. A step
  *       below L-1 holds no two adjacent vertices, so on those edges the two
  *       ends are handled in priority order as in a sequential sweep. Inside a
  *       step every vertex is evaluated against the state at the start of the
@@ -139,7 +145,7 @@ typedef struct {
     int32_t mode;                 /* OG_SEQ or OG_SYNC */
     int32_t flags;                /* OG_REFINE_SINGLE_SWEEP, OG_NO_PRUNE (SEQ, tests only),
                                      OG_REFINE_LABELS, OG_LOUVAIN (V1, V2) */
-    int32_t schedule_layers;      /* SYNC: L, priority layers (S0), default 1000 */
+    int32_t schedule_layers;      /* SYNC: L, priority layers (S0); 0 (default): by the graph, S0 */
     int32_t schedule_buckets;     /* SYNC: B, buckets after the last layer (S0), default 16 */
     uint64_t seed;                /* SYNC: priority seed (S0), default 0 */
 } og_params;
@@ -790,7 +796,7 @@ void og_params_default(og_params *p) {
     p->max_passes = 10;
     p->mode = OG_SEQ;
     p->flags = 0;
-    p->schedule_layers = 1000;
+    p->schedule_layers = 0;
     p->schedule_buckets = 16;
     p->seed = 0;
 }
@@ -820,7 +826,16 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
         if (w0 && (!isfinite(w0[e]) || w0[e] < 0.0f)) return OG_ERR_INVALID;
     }
     if (p->max_iterations < 1 || p->max_passes < 0 || !(p->tolerance_drop > 0)) return OG_ERR_INVALID;
-    if (p->mode == OG_SYNC && (p->schedule_layers < 1 || p->schedule_buckets < 1)) return OG_ERR_INVALID;
+    if (p->mode == OG_SYNC && (p->schedule_layers < 0 || p->schedule_buckets < 1)) return OG_ERR_INVALID;
+    /* S0: L of the run (0: 1000 for an input with a row of more than 2048
+     * entries, else 32) */
+    int32_t Ls = p->schedule_layers;
+    if (Ls == 0) {
+        int64_t maxdeg = 0;
+        for (int64_t i = 0; i < n0; ++i)
+            if (off0[i + 1] - off0[i] > maxdeg) maxdeg = off0[i + 1] - off0[i];
+        Ls = maxdeg > 2048 ? 1000 : 32;
+    }
     int sync = (p->mode == OG_SYNC);
     if (sync) {
         if (p->resolution != 1.0) return OG_ERR_UNSUPPORTED;
@@ -886,13 +901,12 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
         /* S0: priority steps of this pass's graph */
         int32_t nl = 0;
         if (sync) {
-            nl = og_schedule(n, G.off, G.deg, G.idx, p->seed + (uint64_t)lp, p->schedule_layers,
-                             p->schedule_buckets, layer);
+            nl = og_schedule(n, G.off, G.deg, G.idx, p->seed + (uint64_t)lp, Ls, p->schedule_buckets, layer);
             if (nl < 0) goto done;
         }
         /* local-moving phase (Algorithm 2) */
         int li = sync ? move_sync(&G, Cp, Ki, Si, size, tau, (int64_t)two_m, p->max_iterations,
-                                  p->schedule_layers, layer, nl, &H)
+                                  Ls, layer, nl, &H)
                       : move_seq(&G, Cp, K, Sig, tau, gamma, two_m, p->max_iterations,
                                  (p->flags & OG_NO_PRUNE) != 0, &H);
         if (li < 0) goto done;

@@ -22,7 +22,7 @@ void leiden_params_default(leiden_params *p) {
     p->max_passes = 10;
     p->mode = LEIDEN_ASYNC;
     p->flags = 0;
-    p->schedule_layers = 32;
+    p->schedule_layers = 0;
     p->schedule_buckets = 16;
     p->seed = 0;
 }

@@ -196,6 +196,16 @@ __device__ __forceinline__ void warp_add_by_key(double *arr, int64_t key, double
     }
 }
 
+// Sum of v over the lanes of peers (every lane of peers calls it, with the
+// same peers).
+template <class A>
+__device__ __forceinline__ A peer_sum(unsigned peers, A v) {
+    if (peers == kFull) return warp_sum(v);
+    A s = 0;
+    for (unsigned m = peers; m; m &= m - 1) s += __shfl_sync(peers, v, __ffs(m) - 1);
+    return s;
+}
+
 // Profiling counters: every lane holds partial counts; one atomic per warp.
 struct ProfCounts {
     unsigned long long v[6] = {0, 0, 0, 0, 0, 0};
@@ -213,6 +223,44 @@ struct ProfCounts {
 enum : int { kErrNone = 0, kErrHashFull = 1, kErrBadIndex = 2, kErrTimeout = 3 };
 __device__ __forceinline__ void set_error(int *err, int code) {
     if (err) atomicCAS(err, 0, code);
+}
+
+// Grid-wide barrier of a cooperative launch: blocks count in on bar[0]; the
+// last one resets it and advances the generation bar[1] that the others
+// poll. Spins are bounded: after about a second without progress the kernel
+// records kErrTimeout and every later barrier returns at once, so the launch
+// always ends. A grid of one block needs only __syncthreads.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (gridDim.x == 1) return true;
+    if (threadIdx.x == 0) {
+        int ok = *((volatile int *)err) == 0;
+        if (ok) {
+            volatile unsigned *gen = bar + 1;
+            const unsigned g = *gen;
+            __threadfence();
+            if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+                atomicExch(&bar[0], 0u);
+                __threadfence();
+                atomicAdd(&bar[1], 1u);
+            } else {
+                unsigned long long spins = 0;
+                while (*gen == g) {
+                    if (++spins > (1ULL << 24)) {
+                        set_error(err, kErrTimeout);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 }  // namespace lgb

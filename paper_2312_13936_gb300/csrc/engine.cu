@@ -11,6 +11,7 @@
 // stop tests and pass count (per-graph arrays of k_batch.cu), and a graph
 // that stops leaves the union at the next renumbering. A single graph is the
 // case G = 1 without per-vertex graph ids.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -89,6 +90,12 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
         CK(launch_graph_sums(q.K, false, q.gid0, n, q.gmsum, q.s));
         q.hgw.assign(G, 0.0);
         CK(cudaMemcpyAsync(q.hgw.data(), q.gmsum, sizeof(double) * G, cudaMemcpyDeviceToHost, q.s));
+        // largest degree of every graph (the default layer cap of its schedule)
+        ST(q.alloc(&q.gL, G));
+        CK(cudaMemsetAsync(q.gL, 0, sizeof(int32_t) * G, q.s));
+        CK(launch_graph_max_deg(q.deg0, q.gid0, n, q.gL, q.s));
+        q.hgmaxdeg.assign(G, 0);
+        CK(cudaMemcpyAsync(q.hgmaxdeg.data(), q.gL, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, q.s));
         CK(cudaStreamSynchronize(q.s));
     }
     return LEIDEN_OK;
@@ -103,7 +110,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     cudaStream_t s = q.s;
     const leiden_params &prm = *r.prm;
     const bool det = r.det, trace = r.trace, batch = r.batch;
-    const int32_t L = r.L, B = r.B, nsteps = r.nsteps, nkeys = r.nkeys, NG = r.NG;
+    const int32_t L = r.L, B = r.B, NG = r.NG;
     const int64_t n0 = r.n0;
     const int tile_blocks = q.sm * 8, big_blocks = q.sm * 2;
     GraphView &G = r.G;
@@ -140,10 +147,19 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     }
     q.launches += 1;
     // schedule and (step, bin) lists
-    SchedWork sw{q.scnt, q.slayer, q.sfcount};
+    // (the schedule's order arrays are the list and key buffers, rewritten below)
+    SchedWork sw{q.scnt, q.slayer, q.list, q.key, q.sfcount, &q.dsc->err};
     CK(launch_schedule(G, prm.seed + (r.gpass ? 0 : (uint64_t)lp), L, B, sw, q.step, s, cur_gid,
-                       batch ? q.vseg : nullptr, r.gpass, r.deg_bound > kLongRow));
-    q.launches += L > 1 ? L : 2;
+                       batch ? q.vseg : nullptr, r.gpass, r.deg_bound > kLongRow, batch ? r.gL : nullptr));
+    q.launches += 1;
+    // steps used: the layers produced, then the buckets if any vertex was
+    // not placed below L-1 (only steps that can hold vertices get lists)
+    int32_t sinfo[2] = {0, 0};
+    CK(cudaMemcpyAsync(sinfo, q.sfcount + 9, sizeof(sinfo), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const int32_t nsteps = sinfo[1] > 0 ? L - 1 + B : std::max<int32_t>(1, std::min<int32_t>(sinfo[0], L - 1));
+    const int32_t nkeys = nsteps * kNumBins;
+    ST(q.ensure_part_tmp(partition_tmp_bytes(n, nkeys + 1)));
     // one vertex list per (schedule step, degree bin), step-major
     CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
     CK(launch_partition(q.key, n, nkeys + 1, q.key_off, q.list, q.part_tmp, s));  // + edgeless bucket
@@ -167,49 +183,40 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     else if (lp == 0) CK(launch_iota(q.Cp, n, s));
     else CK(cudaMemcpyAsync(q.Cp, q.label, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     if (trace) q.record(lp, 1, q.Cp, n);
-    // Sweep space. On request (LEIDEN_FLAG_RELABEL) the asynchronous
-    // mode relabels large graphs so that every (step, bin) list is a
-    // contiguous id range, ascending in the ids of G'; the sweeps run on
-    // the relabelled copy and their labels are mapped back afterwards.
-    // Vertex p of the copy is vertex perm[p] = list[p] of G'. The copy
-    // costs about what it saves in the sweeps, so it is off by default.
-    const bool relabel = !det && (prm.flags & LEIDEN_FLAG_RELABEL) && n >= kRelabelMinVertices;
-    GraphView sG = G;
+    // the sweeps' graph and arrays
+    const GraphView sG = G;
     int32_t *sC = q.Cp, *sCB = q.CB, *sStep = q.step;
     const int32_t *sList = q.list;
     void *sK = q.K;
-    if (relabel) {
-        ST(q.ensure_relabel(Gcap));
-        const int32_t *perm = q.list;
-        CK(launch_inverse(perm, n, q.rinv, s));
-        CK(launch_gather_i32(G.deg, perm, n, q.rdeg, s));
-        CK(launch_exclusive_scan_i32(q.rdeg, q.roff, n, q.scan_tmp, s));
-        CK(launch_permute_rows(G, perm, q.rinv, q.roff, q.ridx, q.rw, s));
-        CK(launch_gather_i32(static_cast<const int32_t *>(q.K), perm, n, static_cast<int32_t *>(q.rK), s));  // fp32 K
-        CK(launch_gather_i32(q.step, perm, n, q.rstep, s));
-        CK(launch_labels_to_new(q.Cp, perm, q.rinv, n, q.rC, s));
-        q.launches += 9;
-        if (batch) {
-            CK(launch_gather_i32(cur_gid, perm, n, q.rgid, s));
-            q.launches++;
-        }
-        sG.off = q.roff;
-        sG.deg = q.rdeg;
-        sG.idx = q.ridx;
-        sG.w = q.rw;
-        sC = q.rC;
-        sCB = q.rCB;
-        sStep = q.rstep;
-        sList = q.iota_list;
-        sK = q.rK;
-    }
     CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
     CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
     CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));
     q.launches += 1;
+    const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
+    // bin 6: in the persistent sweep the whole grid takes each step's hubs
+    // (tables of one step at a time); per-step launches keep a global table
+    // per block
+    const std::vector<int64_t> &ko = q.hkey_off;
+    int64_t nhubs = 0;
+    for (int32_t k = 0; k < nsteps; ++k) nhubs += ko[(size_t)k * kNumBins + 7] - ko[(size_t)k * kNumBins + 6];
+    const bool grid_hubs = nhubs > 0 && !step_launches && sweep_coop_blocks_per_sm(det, sG.w_int, false) > 0 &&
+                           sweep_coop_blocks_per_sm(det, sG.w_int, true) > 0;
+    if (grid_hubs) {
+        ST(q.ensure_hubs(nhubs));
+        CK(launch_hub_prep(q.key_off, nsteps, sList, sG.deg, q.hubs, q.hspan, s));
+        q.launches += 1;
+        unsigned long long span = 0;
+        CK(cudaMemcpyAsync(&span, q.hspan, sizeof(span), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (span > (unsigned long long)INT32_MAX) {
+            set_last_error("hub tables of one step exceed 2^31 slots");
+            return LEIDEN_ERR_OOM;
+        }
+        ST(q.ensure_hub(0, (int)span, det));
+    }
     // global tables for bin 6 (one per block)
     int hub_bits = 0, hub_regions = 0;
-    {
+    if (!grid_hubs) {
         const int maxdeg = q.hsc->maxdeg;
         if (maxdeg > kBlockMaxDeg) {
             hub_bits = ceil_log2_h(2 * (int64_t)maxdeg);
@@ -240,19 +247,28 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     sc.hub_vals = q.hub_vals;
     sc.hub_bits = hub_bits;
     sc.err = &q.dsc->err;
-    const std::vector<int64_t> &ko = q.hkey_off;
+    sc.grid_hubs = grid_hubs;
+    sc.hubs = q.hubs;
+    sc.hj = q.hj;
+    sc.hinfo = q.hbase;
+    sc.htoff = q.htoff;
+    sc.heoff = q.heoff;
+    sc.hd = q.hd;
+    sc.hcand = q.hcand;
+    sc.hmv = q.hmv;
+    sc.hkey = q.hkey;
+    sc.hkvd = q.hkvd;
     sc.nsteps = nsteps;
     sc.key_off = q.key_off;
     sc.bar = q.bar;
     sc.hub_regions = hub_regions;
-    sc.gid = batch ? (relabel ? q.rgid : cur_gid) : nullptr;
+    sc.gid = batch ? cur_gid : nullptr;
     sc.gks = q.gks;
     sc.g2m = q.g2m;
     sc.gdone = q.gdone;
     sc.gactive = q.gactive;
     sc.gtau = r.gtau;
     sc.G = NG;
-    const bool step_launches = (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES) != 0;
     // one sweep as per-(step, bin) launches (fallback and test path)
     auto run_steps = [&](bool refine) -> leiden_status {
         sc.refine = refine;
@@ -345,28 +361,19 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     int li = 0;
     ST(run_phase(false, &li, q.gli));
     st.move_iterations += li;
-    if (trace) {
-        if (relabel) {
-            CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cd, s));
-            q.record(lp, 2, q.Cd, n);
-        } else {
-            q.record(lp, 2, q.Cp, n);
-        }
-    }
-    // ---- refinement phase (Algorithm 3)
+    if (trace) q.record(lp, 2, q.Cp, n);
+    // ---- refinement phase (Algorithm 3); the Louvain variant has none and
+    // takes its local-moving communities as the refined ones
     ST(mark(1));
     CK(cudaMemcpyAsync(sCB, sC, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-    CK(launch_iota(sC, n, s));
-    CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
-    CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
-    CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));  // Sigma' <- K', one member each
-    q.launches += 2;
     int lj = 0;
-    ST(run_phase(true, &lj, q.glj));
-    if (relabel) {  // back to the ids of G'
-        CK(launch_labels_to_old(sC, q.list, q.rinv, n, q.Cp, s));
-        CK(launch_labels_to_old(sCB, q.list, q.rinv, n, q.CB, s));
+    if (!(prm.flags & LEIDEN_FLAG_LOUVAIN)) {
+        CK(launch_iota(sC, n, s));
+        CK(cudaMemsetAsync(q.Sig, 0, accsz * n, s));
+        CK(cudaMemsetAsync(q.size, 0, sizeof(int32_t) * n, s));
+        CK(launch_community_totals(sC, sK, det, n, q.Sig, q.size, s));  // Sigma' <- K', one member each
         q.launches += 2;
+        ST(run_phase(true, &lj, q.glj));
     }
     st.refine_iterations += lj;
     if (trace) q.record(lp, 3, q.Cp, n);
@@ -516,9 +523,15 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             }
         }
     }
-    // move-based labels of the super-vertices (reading R3)
-    CK(launch_bound_labels(q.Cd, q.CB, n, ncomm, q.bnd, q.rep, q.label, s));
-    q.launches += 4;
+    // move-based labels of the super-vertices (reading R3), or each alone
+    // (refine-based labels)
+    if (prm.flags & LEIDEN_FLAG_REFINE_LABELS) {
+        CK(launch_iota(q.label, ncomm, s));
+        q.launches++;
+    } else {
+        CK(launch_bound_labels(q.Cd, q.CB, n, ncomm, q.bnd, q.rep, q.label, s));
+        q.launches += 4;
+    }
     if (batch) {  // graph of every super-vertex; segments of the next graph
         int32_t *nxt = cur_gid == q.gidA ? q.gidB : q.gidA;
         CK(launch_next_gid(q.Cd, cur_gid, n, nxt, s));
@@ -584,9 +597,22 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     cudaStream_t s = q.s;
     const bool det = prm.mode == LEIDEN_DETERMINISTIC;
     const bool trace = (prm.flags & LEIDEN_FLAG_TRACE) != 0;
-    const int32_t L = prm.schedule_layers, B = prm.schedule_buckets;
+    const int32_t B = prm.schedule_buckets;
     const int32_t NG = q.G;
     const bool batch = NG > 1;
+    // layer cap of every graph (reading S0): schedule_layers, or by the
+    // graph's largest degree when it is 0; L is the largest
+    int32_t L = prm.schedule_layers;
+    std::vector<int32_t> hgL;
+    if (L == 0) {
+        if (batch) {
+            hgL.resize((size_t)NG);
+            for (int32_t g = 0; g < NG; ++g) hgL[g] = auto_layers(q.hgmaxdeg[g]);
+            L = *std::max_element(hgL.begin(), hgL.end());
+        } else {
+            L = auto_layers(q.maxdeg0);
+        }
+    }
     if (prm.max_iterations < 1 || prm.max_passes < 0 || !(prm.tolerance_drop > 0) || L < 1 || B < 1 ||
         (prm.mode != LEIDEN_ASYNC && prm.mode != LEIDEN_DETERMINISTIC) || !(prm.resolution >= 0) ||
         !std::isfinite(prm.tolerance) || (q.n0 > 0 && !membership)) {
@@ -595,7 +621,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     }
     const int32_t nsteps = L - 1 + B;
     const int32_t nkeys = nsteps * kNumBins;
-    if (nkeys > q.key_cap || L > 4096) {
+    if (nkeys + 1 > q.key_cap || L > 4096) {
         set_last_error("schedule_layers + schedule_buckets too large");
         return LEIDEN_ERR_INVALID;
     }
@@ -603,7 +629,6 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         set_last_error("a batch of graphs runs without trace and without per-step launches");
         return LEIDEN_ERR_UNSUPPORTED;
     }
-    ST(q.ensure_part_tmp(partition_tmp_bytes(q.n0, nkeys + 1)));
     ST(q.ensure_phase(prm.max_iterations, NG));
     if (det) {
         if (prm.resolution != 1.0 || q.nonint) {
@@ -642,6 +667,11 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     r.nsteps = nsteps;
     r.nkeys = nkeys;
     r.NG = NG;
+    if (batch) {  // per-graph caps (all L when schedule_layers is given)
+        if (hgL.empty()) hgL.assign((size_t)NG, L);
+        CK(cudaMemcpyAsync(q.gL, hgL.data(), sizeof(int32_t) * NG, cudaMemcpyHostToDevice, s));
+        r.gL = q.gL;
+    }
     cudaEvent_t ev0, ev1;
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));

@@ -47,8 +47,6 @@ struct Scalars {  // device scalars, read back in one copy
         if (_s != LEIDEN_OK) return _s;        \
     } while (0)
 
-// graphs below this size fit in L2 and are swept without relabelling
-constexpr int64_t kRelabelMinVertices = 1 << 16;
 // vertices per block of the persistent sweep kernel (below a full grid):
 // a step's latency grows with the vertices each thread takes in turn, so
 // small graphs get many blocks (4096 per block measured slower than 2048 on
@@ -88,6 +86,7 @@ struct Run {
     const int32_t *gpass = nullptr;
     const double *gtau = nullptr;
     int32_t graph_max_passes = 0;
+    const int32_t *gL = nullptr;  // layer cap of every graph (batches; L is the largest)
 };
 
 // One graph submitted to a serving handle.
@@ -103,6 +102,7 @@ struct Request {
     float *w = nullptr;
     int32_t *memb = nullptr;  // result: canonical labels
     int64_t bytes = 0;        // device bytes held
+    int32_t L = 0;            // layer cap of its schedule (reading S0)
     // in flight
     int32_t pass = 0;
     int64_t n_cur = 0;        // vertices in the union
@@ -136,8 +136,9 @@ struct Serve {
     double *gtau = nullptr;
     // host mirrors of the per-graph arrays of a step
     std::vector<int64_t> hvseg, hvseg0;
-    std::vector<int32_t> hpass, hstate;
+    std::vector<int32_t> hpass, hstate, hL;
     std::vector<double> htau;
+    int32_t *gL = nullptr;
 };
 
 struct Handle::Impl {
@@ -199,8 +200,10 @@ struct Handle::Impl {
     int32_t G = 1;
     std::vector<int64_t> hvseg0;           // vertex offsets of the graphs in the input
     std::vector<double> hgw;               // weight sum of every graph (fp64)
+    std::vector<int32_t> hgmaxdeg;         // largest degree of every graph
+    int32_t *gL = nullptr;                 // layer cap of every graph (device)
     int64_t *vseg0 = nullptr, *vseg = nullptr, *vseg2 = nullptr;  // G+1 each: input, this pass, next pass
-    int32_t *gid0 = nullptr, *gidA = nullptr, *gidB = nullptr, *rgid = nullptr;
+    int32_t *gid0 = nullptr, *gidA = nullptr, *gidB = nullptr;
     int32_t *gstate = nullptr, *gdone = nullptr, *gli = nullptr, *glj = nullptr, *gpasses = nullptr;
     int64_t *gkeep = nullptr, *gcomm = nullptr;
     long long *gsumk = nullptr;            // per-graph sums of K (int64 or fp64 bits)
@@ -270,8 +273,6 @@ struct Handle::Impl {
         ST(alloc(&key_cnt, key_cap));
         ST(alloc(&key_off, key_cap + 1));
         ST(alloc(&sfcount, 4096 + 1));
-        ST(alloc(&iota_list, n));
-        CK(launch_iota(iota_list, n, s));
         for (int64_t **a : {&vseg0, &vseg, &vseg2}) ST(alloc(a, ng + 1));
         for (int32_t **a : {&gstate, &gdone, &gli, &glj, &gpasses}) ST(alloc(a, ng));
         for (int64_t **a : {&gkeep, &gcomm}) ST(alloc(a, ng));
@@ -423,32 +424,32 @@ struct Handle::Impl {
         prof_valid = true;
         return LEIDEN_OK;
     }
-    // relabelled copy of a pass's graph and arrays (asynchronous sweeps)
-    int64_t *roff = nullptr;
-    int32_t *rdeg = nullptr, *ridx = nullptr, *rinv = nullptr, *rC = nullptr, *rCB = nullptr, *rstep = nullptr,
-            *iota_list = nullptr;
-    void *rw = nullptr, *rK = nullptr;
-    int64_t rcap = -1;
-    leiden_status ensure_relabel(int64_t cap) {
-        if (!roff) {
-            if (G > 1) ST(alloc(&rgid, n0));
-            ST(alloc(&roff, n0 + 1));
-            for (int32_t **a : {&rdeg, &rinv, &rC, &rCB, &rstep}) ST(alloc(a, n0));
-            long long *k = nullptr;
-            ST(alloc(&k, n0));
-            rK = k;
+    // whole-grid bin 6 of the persistent sweep: per-hub arrays of a pass
+    int32_t *hubs = nullptr, *hd = nullptr, *hcand = nullptr, *hmv = nullptr, *hj = nullptr;
+    int64_t *htoff = nullptr, *heoff = nullptr, *hbase = nullptr;
+    unsigned long long *hkey = nullptr, *hspan = nullptr;
+    long long *hkvd = nullptr;
+    int64_t hubs_cap = -1;
+    leiden_status ensure_hubs(int64_t nh) {
+        if (!hbase) {
+            ST(alloc(&hbase, 4));  // a step's eligible hubs, table slots, entries
+            ST(alloc(&hspan, 1));
         }
-        if (cap > rcap) {
-            if (ridx) free_one(ridx);
-            if (rw) free_one(rw);
-            ridx = nullptr;
-            rw = nullptr;
-            ST(alloc(&ridx, cap));
-            int32_t *w = nullptr;
-            ST(alloc(&w, cap));
-            rw = w;
-            rcap = cap;
-        }
+        if (nh <= hubs_cap) return LEIDEN_OK;
+        for (void *p : {(void *)hubs, (void *)hd, (void *)hcand, (void *)hmv, (void *)hj, (void *)htoff,
+                        (void *)heoff, (void *)hkey, (void *)hkvd})
+            if (p) free_one(p);
+        hubs = hd = hcand = hmv = hj = nullptr;
+        htoff = heoff = nullptr;
+        hkey = nullptr;
+        hkvd = nullptr;
+        hubs_cap = -1;
+        for (int32_t **a : {&hubs, &hd, &hcand, &hmv, &hj}) ST(alloc(a, nh));
+        ST(alloc(&htoff, nh + 1));
+        ST(alloc(&heoff, nh + 1));
+        ST(alloc(&hkey, nh));
+        ST(alloc(&hkvd, nh));
+        hubs_cap = nh;
         return LEIDEN_OK;
     }
     size_t part_tmp_bytes = 0;

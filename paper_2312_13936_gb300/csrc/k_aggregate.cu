@@ -311,16 +311,6 @@ __global__ void k_tab_sizes(const int32_t *list, int64_t count, const int64_t *t
     }
 }
 
-// Sum of v over the lanes of peers (every lane of peers calls it, with the
-// same peers).
-template <class A>
-__device__ __forceinline__ A peer_sum(unsigned peers, A v) {
-    if (peers == kFull) return warp_sum(v);
-    A s = 0;
-    for (unsigned m = peers; m; m &= m - 1) s += __shfl_sync(peers, v, __ffs(m) - 1);
-    return s;
-}
-
 // Every vertex of a community with a table in [tab_k0, tab_k1) inserts its
 // entries. Vertices are taken in the order of the community-vertex CSR, so
 // the warps in flight share a few tables (which stay in L2) instead of

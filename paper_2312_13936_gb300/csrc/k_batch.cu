@@ -240,6 +240,10 @@ __global__ void k_graph_q(const double *gsum, int32_t G, double gamma, double *q
     }
 }
 
+__global__ void k_graph_max_deg(const int32_t *deg, const int32_t *gid, int64_t n, int32_t *out) {
+    GRID_STRIDE(v, n) atomicMax(&out[gid[v]], deg[v]);
+}
+
 }  // namespace
 
 cudaError_t launch_graph_ids(const int64_t *vseg, int32_t G, int64_t n, int32_t *gid, cudaStream_t s) {
@@ -251,6 +255,11 @@ cudaError_t launch_globalize_indices(const int64_t *vseg, const int32_t *gid, in
                                      int64_t m, int32_t *idx, int *err, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_globalize<<<grid_for(n, 256), 256, 0, s>>>(vseg, gid, n, off, m, idx, err);
+    return cudaGetLastError();
+}
+cudaError_t launch_graph_max_deg(const int32_t *deg, const int32_t *gid, int64_t n, int32_t *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_graph_max_deg<<<grid_for(n, 256), 256, 0, s>>>(deg, gid, n, out);
     return cudaGetLastError();
 }
 cudaError_t launch_graph_sums(const void *K, bool det, const int32_t *gid, int64_t n, void *out, cudaStream_t s) {

@@ -121,59 +121,6 @@ __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t 
         atomicAdd(&sums[1], tot);
     }
 }
-// ---- relabelling of a pass's graph for the sweeps (vertex p of the
-// relabelled graph is vertex perm[p] of G'; inv is the inverse permutation)
-__global__ void k_inverse(const int32_t *perm, int64_t n, int32_t *inv) {
-    GRID_STRIDE(p, n) inv[perm[p]] = (int32_t)p;
-}
-__global__ void k_gather_i32(const int32_t *src, const int32_t *map, int64_t n, int32_t *dst) {
-    GRID_STRIDE(p, n) dst[p] = src[map[p]];
-}
-__global__ void k_gather_u64(const unsigned long long *src, const int32_t *map, int64_t n, unsigned long long *dst) {
-    GRID_STRIDE(p, n) dst[p] = src[map[p]];
-}
-// dst[p] = inv[src[perm[p]]]: labels (vertex ids of G') into relabelled ids
-__global__ void k_labels_to_new(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst) {
-    GRID_STRIDE(p, n) dst[p] = inv[src[perm[p]]];
-}
-// dst[v] = perm[src[inv[v]]]: labels back to the vertex ids of G'
-__global__ void k_labels_to_old(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst) {
-    GRID_STRIDE(v, n) dst[v] = perm[src[inv[v]]];
-}
-// rows of the relabelled graph: row p is row perm[p] of G' with targets
-// renamed through inv; one thread per row, rows longer than 32 by the warp
-__global__ void k_permute_rows(int64_t n, const int64_t *off, const int32_t *deg, const int32_t *idx, const uint32_t *w,
-                               const int32_t *perm, const int32_t *inv, const int64_t *off2, int32_t *idx2,
-                               uint32_t *w2) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < n; p0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = p0 + threadIdx.x;
-        int32_t d = 0;
-        int64_t src = 0, dst = 0;
-        if (p < n) {
-            const int32_t v = perm[p];
-            d = deg[v];
-            src = off[v];
-            dst = off2[p];
-            if (d <= 32)
-                for (int32_t e = 0; e < d; ++e) {
-                    idx2[dst + e] = inv[idx[src + e]];
-                    w2[dst + e] = w[src + e];
-                }
-        }
-        unsigned longs = __ballot_sync(kFull, p < n && d > 32);
-        while (longs) {
-            const int l = __ffs(longs) - 1;
-            longs &= longs - 1;
-            const int32_t dl = __shfl_sync(kFull, d, l);
-            const int64_t sl = __shfl_sync(kFull, src, l), tl = __shfl_sync(kFull, dst, l);
-            for (int32_t e = lane; e < dl; e += 32) {
-                idx2[tl + e] = inv[idx[sl + e]];
-                w2[tl + e] = w[sl + e];
-            }
-        }
-    }
-}
 
 __global__ void k_max_i64(const int64_t *a, int64_t n, unsigned long long *out) {
     unsigned long long m = 0;
@@ -287,40 +234,6 @@ cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t
     if (n <= 0) return cudaSuccess;
     auto kern = long_rows ? k_modularity_parts<true> : k_modularity_parts<false>;
     kern<<<grid_for(n, 256), 256, 0, s>>>(n, off, idx, w, C, sigtot, sums);
-    return cudaGetLastError();
-}
-cudaError_t launch_inverse(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_inverse<<<grid_for(n, 256), 256, 0, s>>>(perm, n, inv);
-    return cudaGetLastError();
-}
-cudaError_t launch_gather_i32(const int32_t *src, const int32_t *map, int64_t n, int32_t *dst, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_gather_i32<<<grid_for(n, 256), 256, 0, s>>>(src, map, n, dst);
-    return cudaGetLastError();
-}
-cudaError_t launch_gather_8b(const void *src, const int32_t *map, int64_t n, void *dst, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_gather_u64<<<grid_for(n, 256), 256, 0, s>>>((const unsigned long long *)src, map, n, (unsigned long long *)dst);
-    return cudaGetLastError();
-}
-cudaError_t launch_labels_to_new(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst,
-                                 cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_labels_to_new<<<grid_for(n, 256), 256, 0, s>>>(src, perm, inv, n, dst);
-    return cudaGetLastError();
-}
-cudaError_t launch_labels_to_old(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst,
-                                 cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_labels_to_old<<<grid_for(n, 256), 256, 0, s>>>(src, perm, inv, n, dst);
-    return cudaGetLastError();
-}
-cudaError_t launch_permute_rows(const GraphView &g, const int32_t *perm, const int32_t *inv, const int64_t *off2,
-                                int32_t *idx2, void *w2, cudaStream_t s) {
-    if (g.n <= 0) return cudaSuccess;
-    k_permute_rows<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, g.off, g.deg, g.idx, (const uint32_t *)g.w, perm, inv, off2,
-                                                     idx2, (uint32_t *)w2);
     return cudaGetLastError();
 }
 cudaError_t launch_max_i64(const int64_t *a, int64_t n, unsigned long long *out, cudaStream_t s) {

@@ -66,6 +66,14 @@ template <class P, class W> struct SV {
     int32_t *hub_keys;
     A *hub_vals;
     int hub_bits, hub_regions;
+    // bin 6 on the whole grid (persistent sweep)
+    const int32_t *hubs;
+    int32_t *hj;
+    int64_t *htoff, *heoff, *hinfo;
+    int32_t *hd, *hcand, *hmv;
+    unsigned long long *hkey;
+    A *hkvd;
+    bool grid_hubs;
     unsigned *bar;
     int *err;
     unsigned long long *prof;
@@ -127,6 +135,17 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.hub_vals = static_cast<A *>(c.hub_vals);
     a.hub_bits = c.hub_bits;
     a.hub_regions = c.hub_regions;
+    a.hubs = c.hubs;
+    a.hj = c.hj;
+    a.htoff = c.htoff;
+    a.heoff = c.heoff;
+    a.hinfo = c.hinfo;
+    a.hd = c.hd;
+    a.hcand = c.hcand;
+    a.hmv = c.hmv;
+    a.hkey = c.hkey;
+    a.hkvd = static_cast<A *>(c.hkvd);
+    a.grid_hubs = c.grid_hubs;
     a.bar = c.bar;
     a.err = c.err;
     a.prof = c.prof;
@@ -633,6 +652,240 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
     __syncthreads();
 }
 
+// -------------------------------------------- bin 6 on the whole grid
+// In the persistent sweep the vertices of bin 6 (rows of more than
+// kBlockMaxDeg entries) of a step are evaluated by every block together:
+// degree-first schedules put a few hubs in each of many steps, and one block
+// per hub would leave the rest of the GPU waiting on the largest. Hub j of
+// the pass (its ordinal in list order) is hubs[j]. Phases, each ended by a
+// grid barrier: block 0 takes the eligibility of the step's hubs and lays
+// out the eligible ones (hj[p] = j; table slots [htoff[p], htoff[p+1]), a
+// power of two of at least 2 deg; row entries [heoff[p], heoff[p+1]) of the
+// flat walk); clearing; insertion of the rows (entries of one warp step
+// with equal (hub, community) summed first); the largest key per hub
+// (atomicMax on an order-preserving encoding); the smallest community id
+// among those with that key (atomicMin), which is the candidate a block's
+// own scan finds; the decision, one thread per hub; for an asynchronous
+// local-moving move, the neighbours' flags. A step whose hubs are all
+// ineligible ends after the first phase.
+__device__ __forceinline__ unsigned long long key_order(long long k) {
+    return (unsigned long long)k ^ 0x8000000000000000ULL;
+}
+__device__ __forceinline__ long long key_of_order(unsigned long long e, long long) {
+    return (long long)(e ^ 0x8000000000000000ULL);
+}
+__device__ __forceinline__ unsigned long long key_order(float k) {
+    const unsigned u = __float_as_uint(k);
+    return (unsigned long long)((u & 0x80000000u) ? ~u : (u | 0x80000000u));
+}
+__device__ __forceinline__ float key_of_order(unsigned long long e, float) {
+    const unsigned u = (unsigned)e;
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// the p in [0, np) whose range [off[p], off[p+1]) holds x (off ascending)
+__device__ __forceinline__ int64_t range_at(const int64_t *off, int64_t np, int64_t x) {
+    int64_t lo = 0, hi = np - 1;  // the last p with off[p] <= x
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldcg(&off[mid]) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// exclusive block scan of x (every thread of the block calls it); returns
+// the block total in *total
+__device__ __forceinline__ long long block_scan_excl(long long x, long long *total) {
+    __shared__ long long s_w[32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) s_w[wib] = inc;
+    __syncthreads();
+    long long before = 0, all = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < wib) before += s_w[w];
+        all += s_w[w];
+    }
+    *total = all;
+    return before + inc - x;
+}
+
+template <class P, class W, bool REFINE, bool B>
+__device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int64_t nh, int32_t cur_step,
+                                              Sums<P> &sm, ProfCounts &pc) {
+    using A = typename P::acc;
+    const int lane = threadIdx.x & 31;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t warps = nthreads >> 5, gw = tid >> 5;
+    // eligibility and layout (block 0)
+    if (blockIdx.x == 0) {
+        long long np = 0, ns = 0, ne = 0;
+        for (int64_t i0 = 0; i0 < nh; i0 += blockDim.x) {
+            const int64_t i = i0 + threadIdx.x;
+            bool e = false;
+            int64_t sz = 0, dv = 0;
+            if (i < nh) {
+                const int64_t j = j0 + i;
+                const int32_t v = __ldg(&a.hubs[j]);
+                const int32_t gv = graph_of<B>(a, v);
+                int32_t d = 0;
+                e = take_vertex<P, W, REFINE, B>(a, v, d, gv);
+                if (!e) {
+                    if (proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
+                    pc.v[1]++;
+                } else {
+                    dv = a.deg[v];
+                    int bits = ceil_log2(2 * dv);
+                    if (bits < 6) bits = 6;
+                    sz = 1LL << bits;
+                    a.hkey[j] = 0ULL;
+                    a.hcand[j] = INT_MAX;
+                    a.hkvd[j] = 0;
+                    a.hmv[j] = 0;
+                }
+                a.hd[j] = e ? d : -1;
+            }
+            long long tp, ts, te;
+            const long long p = block_scan_excl(e ? 1 : 0, &tp);
+            const long long so = block_scan_excl(sz, &ts);
+            const long long eo = block_scan_excl(dv, &te);
+            if (e) {
+                a.hj[np + p] = (int32_t)(j0 + i);
+                a.htoff[np + p] = ns + so;
+                a.heoff[np + p] = ne + eo;
+            }
+            np += tp;
+            ns += ts;
+            ne += te;
+        }
+        if (threadIdx.x == 0) {
+            a.htoff[np] = ns;
+            a.heoff[np] = ne;
+            a.hinfo[0] = np;
+            a.hinfo[1] = ns;
+            a.hinfo[2] = ne;
+        }
+    }
+    if (!grid_barrier(a.bar, a.err)) return false;
+    const int64_t np = __ldcg(&a.hinfo[0]), S = __ldcg(&a.hinfo[1]), E = __ldcg(&a.hinfo[2]);
+    if (np == 0) return true;
+    for (int64_t s = tid; s < S; s += nthreads) {
+        a.hub_keys[s] = -1;
+        a.hub_vals[s] = 0;
+    }
+    if (!grid_barrier(a.bar, a.err)) return false;
+    // insertion
+    for (int64_t x0 = gw * 32; x0 < E; x0 += warps * 32) {
+        const int64_t x = x0 + lane;
+        int64_t p = -1, tbase = 0;
+        int32_t key = -1, bits = 0;
+        A val = 0;
+        if (x < E) {
+            p = range_at(a.heoff, np, x);
+            const int32_t v = __ldg(&a.hubs[__ldcg(&a.hj[p])]);
+            const int64_t e = a.off[v] + (x - __ldcg(&a.heoff[p]));
+            const int32_t u = a.idx[e];
+            if (u != v && (!REFINE || __ldg(&a.CB[u]) == __ldg(&a.CB[v]))) {
+                key = ldm(&a.C[u]);
+                val = wconv<A>(a.w[e]);
+                tbase = __ldcg(&a.htoff[p]);
+                bits = __ffsll((long long)(__ldcg(&a.htoff[p + 1]) - tbase)) - 1;
+            }
+        }
+        const unsigned long long pair = key >= 0 ? ((unsigned long long)p << 32) | (uint32_t)key : ~0ULL;
+        const unsigned peers = __match_any_sync(kFull, pair);
+        val = peer_sum(peers, val);
+        if (key >= 0 && lane == __ffs(peers) - 1)
+            if (!hash_add(a.hub_keys + tbase, a.hub_vals + tbase, bits, key, val)) set_error(a.err, kErrHashFull);
+    }
+    if (!grid_barrier(a.bar, a.err)) return false;
+    // the largest key per hub (pass 0), then the smallest community id with
+    // it (pass 1); K_{v->d} from the slot of v's own community
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t s0 = gw * 32; s0 < S; s0 += warps * 32) {
+            const int64_t s = s0 + lane;
+            int64_t j = -1;
+            unsigned long long enc = 0ULL;
+            int32_t k = -1;
+            if (s < S) {
+                k = __ldcg(&a.hub_keys[s]);
+                if (k >= 0) {
+                    j = __ldcg(&a.hj[range_at(a.htoff, np, s)]);
+                    const int32_t d = __ldcg(&a.hd[j]);
+                    const A sum = __ldcg(&a.hub_vals[s]);
+                    if (k == d) {
+                        if (pass == 0) a.hkvd[j] = sum;
+                        k = -1;
+                    } else {
+                        const int32_t v = __ldg(&a.hubs[j]);
+                        const int32_t gv = graph_of<B>(a, v);
+                        enc = key_order(move_key(kscale_of<B>(a, gv), sum, a.K[v], ldm(&a.Sig[k]), a.gamma));
+                        if (pass == 0) pc.v[3]++;
+                    }
+                }
+            }
+            // one atomic per hub present in the warp
+            const unsigned long long grp = k >= 0 ? (unsigned long long)j : ~0ULL;
+            const unsigned peers = __match_any_sync(kFull, grp);
+            if (pass == 0) {
+                unsigned long long m = enc;
+                for (unsigned r = peers; r; r &= r - 1) {
+                    const unsigned long long o = __shfl_sync(peers, enc, __ffs(r) - 1);
+                    m = o > m ? o : m;
+                }
+                if (k >= 0 && lane == __ffs(peers) - 1) atomicMax(&a.hkey[j], m);
+            } else {
+                const bool best = k >= 0 && enc == __ldcg(&a.hkey[j]);
+                int32_t c = best ? k : INT_MAX;
+                for (unsigned r = peers; r; r &= r - 1) {
+                    const int32_t o = __shfl_sync(peers, c, __ffs(r) - 1);
+                    c = o < c ? o : c;
+                }
+                if (k >= 0 && lane == __ffs(peers) - 1 && c != INT_MAX) atomicMin(&a.hcand[j], c);
+            }
+        }
+        if (!grid_barrier(a.bar, a.err)) return false;
+    }
+    // decisions
+    for (int64_t p = tid; p < np; p += nthreads) {
+        const int64_t j = __ldcg(&a.hj[p]);
+        const int32_t d = __ldcg(&a.hd[j]);
+        const int32_t v = __ldg(&a.hubs[j]);
+        const int32_t gv = graph_of<B>(a, v);
+        const int32_t c = __ldcg(&a.hcand[j]);
+        const A bk = c == INT_MAX ? AccLimits<A>::lowest() : key_of_order(__ldcg(&a.hkey[j]), A(0));
+        const A kd = __ldcg(&a.hkvd[j]);
+        const bool mv = decide<P, W, REFINE, B>(a, v, d, a.K[v], bk, c, kd, sm, cur_step, gv, kscale_of<B>(a, gv));
+        const int32_t dv = a.deg[v];
+        pc.v[0]++;
+        pc.v[2] += dv;
+        if (proposing<P, REFINE>(cur_step, a.cap_step) ? (ldm(&a.prop[v]) >= 0) : mv) {
+            pc.v[4]++;
+            pc.v[5] += dv;
+        }
+        if (!REFINE && !P::det && mv) a.hmv[j] = 1;
+    }
+    if (!REFINE && !P::det) {
+        // an asynchronous local-moving move flags the hub's neighbours
+        if (!grid_barrier(a.bar, a.err)) return false;
+        for (int64_t x = tid; x < E; x += nthreads) {
+            const int64_t p = range_at(a.heoff, np, x);
+            const int64_t j = __ldcg(&a.hj[p]);
+            if (!__ldcg(&a.hmv[j])) continue;
+            const int32_t v = __ldg(&a.hubs[j]);
+            a.unproc[a.idx[a.off[v] + (x - __ldcg(&a.heoff[p]))]] = 1;
+        }
+    }
+    return true;
+}
+
 // ------------------------------------------------------------ apply steps
 // Local-moving proposals of one step (deterministic mode; asynchronous mode
 // in the capped steps): commit them.
@@ -704,44 +957,6 @@ __device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_
     }
 }
 
-// Grid-wide barrier of a cooperative launch: blocks count in on bar[0]; the
-// last one resets it and advances the generation bar[1] that the others
-// poll. Spins are bounded: after about a second without progress the kernel
-// records kErrTimeout and every later barrier returns at once, so the launch
-// always ends. A grid of one block needs only __syncthreads.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (gridDim.x == 1) return true;
-    if (threadIdx.x == 0) {
-        int ok = *((volatile int *)err) == 0;
-        if (ok) {
-            volatile unsigned *gen = bar + 1;
-            const unsigned g = *gen;
-            __threadfence();
-            if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
-                atomicExch(&bar[0], 0u);
-                __threadfence();
-                atomicAdd(&bar[1], 1u);
-            } else {
-                unsigned long long spins = 0;
-                while (*gen == g) {
-                    if (++spins > (1ULL << 24)) {
-                        set_error(err, kErrTimeout);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            __threadfence();
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // ------------------------------------------------------- persistent sweep
 constexpr int kCoopThreads = 256;
 
@@ -778,6 +993,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
         Sums<P> sm;
         sm.dq = a.dq_arr + (size_t)it * a.G;
         sm.mv = a.moved_arr + (size_t)it * a.G;
+        int64_t hub_j0 = 0;  // ordinal of the step's first hub
         for (int32_t k = 0; k < a.nsteps && ok; ++k) {
             const int64_t *ko = a.key_off + (int64_t)k * kNumBins;
             const int64_t b0 = __ldcg(&ko[0]), b8 = __ldcg(&ko[8]);
@@ -793,9 +1009,14 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                 run_block<P, W, REFINE, false, B>(a, list, b5, b6, k, skeys, svals, ceil_log2(kBlockSlots), sm, pc);
             }
             if (b7 > b6) {
-                const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
-                run_block<P, W, REFINE, true, B>(a, list, b6, b7, k, a.hub_keys + base, a.hub_vals + base, a.hub_bits,
-                                              sm, pc);
+                if (a.grid_hubs) {
+                    if (!(ok = run_hubs_grid<P, W, REFINE, B>(a, hub_j0, b7 - b6, k, sm, pc))) break;
+                } else {
+                    const int64_t base = (int64_t)blockIdx.x << a.hub_bits;
+                    run_block<P, W, REFINE, true, B>(a, list, b6, b7, k, a.hub_keys + base, a.hub_vals + base,
+                                                     a.hub_bits, sm, pc);
+                }
+                hub_j0 += b7 - b6;
             }
             if (!(ok = grid_barrier(a.bar, a.err))) break;
             // apply phase: deterministic mode, and proposals where neighbours

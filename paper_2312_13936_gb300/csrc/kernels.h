@@ -77,6 +77,17 @@ struct SweepCtx {
     int32_t *hub_keys = nullptr;  // global tables for bin 6 (one region per block)
     void *hub_vals = nullptr;
     int hub_bits = 0, hub_regions = 0;
+    // persistent sweep: bin 6 evaluated by the whole grid (launch_hub_prep
+    // fills hubs; hub_keys/hub_vals then hold one step's tables); per hub:
+    // hd, hcand, hmv, hkey, hkvd (8 bytes); per eligible hub of a step: hj,
+    // htoff, heoff (+1); hinfo: 3 words
+    bool grid_hubs = false;
+    const int32_t *hubs = nullptr;
+    int32_t *hj = nullptr;
+    int64_t *htoff = nullptr, *heoff = nullptr, *hinfo = nullptr;
+    int32_t *hd = nullptr, *hcand = nullptr, *hmv = nullptr;
+    unsigned long long *hkey = nullptr;
+    void *hkvd = nullptr;
     unsigned *bar = nullptr;      // grid barrier state (2 words, zero-initialised once)
     int *err = nullptr;
     unsigned long long *prof = nullptr;  // 8 work counters of this launch's class, or null
@@ -170,18 +181,31 @@ cudaError_t launch_validate(int64_t n, const int64_t *off, const int32_t *idx, c
 
 // ---- schedule (k_schedule.cu): step of every vertex (reading S0)
 struct SchedWork {
-    int32_t *cnt, *layer;  // n each
-    int32_t *settled;      // L+1: vertices placed in each layer
+    int32_t *cnt, *layer, *ord, *lord;  // n each
+    int32_t *scratch;                   // 11 words; after the launch scratch[9] = layers
+                                        // produced, scratch[10] = vertices in bucket steps
+    int *err;                    // kErrTimeout if a grid barrier gave up
 };
 // (gid, vseg: a batch of graphs, priorities drawn at indices inside each
 // graph; gpass: graphs at different passes, state + gpass[g] for graph g)
 // long_rows: some row may exceed kLongRow entries
+// gL: the layer cap of every graph of a batch (L is then the largest; a
+// graph's buckets follow step L-1, so its order of steps is its own)
 cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32_t B, const SchedWork &w,
                             int32_t *step, cudaStream_t s, const int32_t *gid = nullptr,
-                            const int64_t *vseg = nullptr, const int32_t *gpass = nullptr, bool long_rows = true);
+                            const int64_t *vseg = nullptr, const int32_t *gpass = nullptr, bool long_rows = true,
+                            const int32_t *gL = nullptr);
+// layer cap of a graph when schedule_layers is 0 (reading S0)
+inline int32_t auto_layers(int64_t maxdeg) { return maxdeg > kBlockMaxDeg ? 1000 : 32; }
 // key[i] = step*kNumBins + bin (step-major: one list per step and bin), or
 // bin*nsteps + step (bin-major: one step-ordered list per bin); vertices
 // without edges get key nsteps*kNumBins (a trailing bucket)
+// Hubs of a pass for the whole-grid bin 6 of the persistent sweep: the
+// bin-6 lists of the steps (key_off step-major, nsteps steps) compacted in
+// list order into hubs[]; *max_span (device) = the largest sum of one
+// step's table sizes (2^max(6, ceil log2 2 deg) slots each).
+cudaError_t launch_hub_prep(const int64_t *key_off, int32_t nsteps, const int32_t *list, const int32_t *deg,
+                            int32_t *hubs, unsigned long long *max_span, cudaStream_t s);
 cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
                                  int32_t *key, cudaStream_t s);
 
@@ -197,6 +221,8 @@ cudaError_t launch_globalize_indices(const int64_t *vseg, const int32_t *gid, in
                                      int64_t m, int32_t *idx, int *err, cudaStream_t s);
 // out[gid[i]] += x[i] (acc type of K: float -> double sums, int64 -> int64)
 cudaError_t launch_graph_sums(const void *K, bool det, const int32_t *gid, int64_t n, void *out, cudaStream_t s);
+// out[gid[v]] = max(out[gid[v]], deg[v]) (out cleared by the caller)
+cudaError_t launch_graph_max_deg(const int32_t *deg, const int32_t *gid, int64_t n, int32_t *out, cudaStream_t s);
 // per-graph key scale and 2m from the per-graph sums of K
 cudaError_t launch_graph_scales(const void *sums, bool det, int32_t G, void *gks, double *g2m, cudaStream_t s);
 // phase start: gdone[g] = (state[g] != active); giters[g] = 0
@@ -304,17 +330,6 @@ cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t
                                     bool long_rows = true);
 cudaError_t launch_sum_squares(const double *x, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_max_i64(const int64_t *a, int64_t n, unsigned long long *out, cudaStream_t s);
-// relabelling of a pass's graph for the asynchronous sweeps: vertex p of the
-// relabelled graph is vertex perm[p] of G'; inv is the inverse permutation
-cudaError_t launch_inverse(const int32_t *perm, int64_t n, int32_t *inv, cudaStream_t s);
-cudaError_t launch_gather_i32(const int32_t *src, const int32_t *map, int64_t n, int32_t *dst, cudaStream_t s);
-cudaError_t launch_gather_8b(const void *src, const int32_t *map, int64_t n, void *dst, cudaStream_t s);
-cudaError_t launch_labels_to_new(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst,
-                                 cudaStream_t s);
-cudaError_t launch_labels_to_old(const int32_t *src, const int32_t *perm, const int32_t *inv, int64_t n, int32_t *dst,
-                                 cudaStream_t s);
-cudaError_t launch_permute_rows(const GraphView &g, const int32_t *perm, const int32_t *inv, const int64_t *off2,
-                                int32_t *idx2, void *w2, cudaStream_t s);
 // nonint = 1 if some weight is not an integer; sum += sum of weights (fp64)
 cudaError_t launch_weight_props(const float *w, int64_t m, int *nonint, double *sum, cudaStream_t s);
 

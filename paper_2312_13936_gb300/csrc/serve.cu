@@ -12,6 +12,8 @@
 // vertices of the aggregated union. Finished graphs get canonical labels and
 // Eq. 1 on their own input. The dendrogram of every graph in flight lives in
 // one arena, compacted after each step in union order.
+#include <algorithm>
+
 #include "engine_impl.h"
 
 namespace lgb {
@@ -20,7 +22,7 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
                                   int32_t max_graphs, int64_t device_budget, void *stream) {
     Impl &q = *p;
     if (max_vertices < 1 || max_vertices > 0x7fffffffLL || max_entries < 1 || max_graphs < 1 ||
-        prm.max_iterations < 1 || prm.max_passes < 1 || !(prm.tolerance_drop > 0) || prm.schedule_layers < 1 ||
+        prm.max_iterations < 1 || prm.max_passes < 1 || !(prm.tolerance_drop > 0) || prm.schedule_layers < 0 ||
         prm.schedule_layers > 4096 || prm.schedule_buckets < 1 || !(prm.resolution >= 0) ||
         !std::isfinite(prm.tolerance) || (prm.mode != LEIDEN_ASYNC && prm.mode != LEIDEN_DETERMINISTIC)) {
         set_last_error("invalid server capacity or leiden_params");
@@ -30,8 +32,10 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
         set_last_error("deterministic mode needs resolution 1");
         return LEIDEN_ERR_UNSUPPORTED;
     }
-    const int32_t nkeys = (prm.schedule_layers - 1 + prm.schedule_buckets) * kNumBins;
-    if (nkeys > 8192) {
+    // the largest layer cap a graph can take (reading S0)
+    const int32_t nkeys = ((prm.schedule_layers > 0 ? prm.schedule_layers : auto_layers(INT64_MAX)) - 1 +
+                           prm.schedule_buckets) * kNumBins;
+    if (nkeys + 1 > 8192) {
         set_last_error("schedule_layers + schedule_buckets too large");
         return LEIDEN_ERR_INVALID;
     }
@@ -45,7 +49,7 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
     q.srv = new Serve;
     Serve &v = *q.srv;
     v.prm = prm;
-    v.prm.flags &= ~(uint32_t)(LEIDEN_FLAG_RELABEL | LEIDEN_FLAG_TRACE | LEIDEN_FLAG_PROFILE |
+    v.prm.flags &= ~(uint32_t)(LEIDEN_FLAG_TRACE | LEIDEN_FLAG_PROFILE |
                                LEIDEN_FLAG_STEP_LAUNCHES);
     v.cap_v = max_vertices;
     v.cap_e = max_entries;
@@ -59,6 +63,7 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
     for (int32_t **a : {&q.gid0, &q.gidA, &q.gidB}) ST(q.alloc(a, max_vertices));
     ST(q.alloc(&v.gpass, max_graphs));
     ST(q.alloc(&v.gtau, max_graphs));
+    ST(q.alloc(&v.gL, max_graphs));
     CK(cudaStreamSynchronize(q.s));
     if (device_budget <= 0) {
         size_t fr = 0, tot = 0;
@@ -107,6 +112,7 @@ static leiden_status upload(Handle::Impl &q, Request &r, const int64_t *off, con
     }
     CK(cudaMemsetAsync(q.dsc, 0, sizeof(Scalars), s));
     CK(launch_degrees(r.off, q.scnt, n, &q.dsc->err, s));
+    CK(launch_max_i32(q.scnt, n, &q.dsc->maxdeg, s));
     CK(launch_validate(n, r.off, r.idx, r.w, &q.dsc->err, s));
     CK(launch_weight_props(r.w, m, &q.dsc->nonint, &q.dsc->wsum, s));
     CK(cudaMemcpyAsync(q.hsc, q.dsc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
@@ -116,6 +122,8 @@ static leiden_status upload(Handle::Impl &q, Request &r, const int64_t *off, con
         set_last_error(e == 2 ? "CSR is not symmetric (w_ij != w_ji)" : "malformed CSR (offsets, indices or weights)");
         return e == 2 ? LEIDEN_ERR_NOT_SYMMETRIC : LEIDEN_ERR_INVALID;
     }
+    const int32_t pl = q.srv->prm.schedule_layers;
+    r.L = pl > 0 ? pl : auto_layers(q.hsc->maxdeg);
     if (q.srv->prm.mode == LEIDEN_DETERMINISTIC) {
         if (q.hsc->nonint) {
             set_last_error("deterministic mode needs integer weights");
@@ -267,8 +275,12 @@ leiden_status Handle::server_step(int32_t *finished_out) {
     v.hpass.assign(K, 0);
     v.hstate.assign(K, kGraphActive);
     v.htau.assign(K, 0.0);
+    v.hL.assign(K, 0);
+    int32_t Lmax = 1;
     for (int32_t k = 0; k < K; ++k) {
         const Request &r = v.reqs[v.inflight[k]];
+        v.hL[k] = r.L;
+        Lmax = std::max(Lmax, r.L);
         v.hvseg[k + 1] = v.hvseg[k] + r.n_cur;
         v.hvseg0[k + 1] = v.hvseg0[k] + r.n;
         v.hpass[k] = r.pass;
@@ -279,6 +291,7 @@ leiden_status Handle::server_step(int32_t *finished_out) {
     CK(cudaMemcpyAsync(v.gpass, v.hpass.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(q.gstate, v.hstate.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(v.gtau, v.htau.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(v.gL, v.hL.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
     CK(launch_graph_ids(q.vseg, K, v.n_union, q.gidA, s));
     CK(launch_graph_ids(q.vseg0, K, v.arena_n, q.gid0, s));
     q.C0 = v.arena[v.arena_cur];
@@ -287,7 +300,8 @@ leiden_status Handle::server_step(int32_t *finished_out) {
     r.prm = &prm;
     r.det = det;
     r.batch = true;
-    r.L = prm.schedule_layers;
+    r.L = Lmax;
+    r.gL = v.gL;
     r.B = prm.schedule_buckets;
     r.nsteps = r.L - 1 + r.B;
     r.nkeys = r.nsteps * kNumBins;

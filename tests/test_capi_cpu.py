@@ -32,7 +32,7 @@ def test_host_only_entry_points():
     lib = lg.library(build_if_missing=True)
     p = lg.leiden_params_default()
     assert (p.resolution, p.tolerance, p.aggregation_tolerance, p.tolerance_drop) == (1.0, 0.01, 0.8, 10.0)
-    assert (p.max_iterations, p.max_passes, p.mode, p.schedule_layers, p.schedule_buckets) == (20, 10, 0, 32, 16)
+    assert (p.max_iterations, p.max_passes, p.mode, p.schedule_layers, p.schedule_buckets) == (20, 10, 0, 0, 16)
     assert lg.leiden_status_string(0) == "LEIDEN_OK"
     assert lg.leiden_status_string(-7) == "LEIDEN_ERR_OVERFLOW"
     # argument checks that fail before any device work

@@ -83,20 +83,21 @@ def test_batch_deterministic_schedule_and_limits():
     b = gen.sbm_batch(8, seed=13, nmin=200, nmax=2000)
     graphs = [b.graph(g) for g in range(b.num_graphs)]
     for kw in ({"schedule_layers": 4, "schedule_buckets": 3, "seed": 9}, {"max_passes": 2},
-               {"max_iterations": 2}, {"flags": lg.FLAG_REFINE_SINGLE_SWEEP}):
+               {"max_iterations": 2}, {"flags": lg.FLAG_REFINE_SINGLE_SWEEP}, {"flags": lg.FLAG_LOUVAIN},
+               {"flags": lg.FLAG_REFINE_LABELS}):
         vseg, memb, q, _, _, _ = run_batch(graphs, lg.LEIDEN_DETERMINISTIC, **kw)
         for g, G in enumerate(graphs):
             ms = run_gpu(G, lg.LEIDEN_DETERMINISTIC, **kw)[0]
             assert np.array_equal(memb[vseg[g]:vseg[g + 1]], ms), (kw, g)
 
 
-@pytest.mark.parametrize("flags", [0, lg.FLAG_RELABEL])
+@pytest.mark.parametrize("flags", [0, lg.FLAG_REFINE_SINGLE_SWEEP])
 def test_batch_async_quality(flags):
-    # about 100k vertices in all: large enough for the relabelled sweep
     b = gen.sbm_batch(40, seed=12, nmin=500, nmax=8000)
     graphs = [b.graph(g) for g in range(b.num_graphs)]
     vseg, memb, q, st, passes, comm = run_batch(graphs, lg.LEIDEN_ASYNC, flags=flags)
-    seq_q = np.array([oracle.leiden(G, mode=oracle.SEQ).modularity for G in graphs])
+    oflags = oracle.REFINE_SINGLE_SWEEP if flags & lg.FLAG_REFINE_SINGLE_SWEEP else 0
+    seq_q = np.array([oracle.leiden(G, mode=oracle.SEQ, flags=oflags).modularity for G in graphs])
     assert q.mean() >= seq_q.mean() - Q_TOL_ASYNC, (q.mean(), seq_q.mean())
     for g, G in enumerate(graphs):
         mb = memb[vseg[g]:vseg[g + 1]]

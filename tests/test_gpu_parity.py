@@ -126,7 +126,7 @@ ASYNC_GRAPHS = {
 }
 
 
-@pytest.mark.parametrize("flags", [0, lg.FLAG_STEP_LAUNCHES, lg.FLAG_RELABEL])
+@pytest.mark.parametrize("flags", [0, lg.FLAG_STEP_LAUNCHES])
 @pytest.mark.parametrize("name", sorted(ASYNC_GRAPHS))
 def test_async_quality_and_connectivity(name, flags):
     g = ASYNC_GRAPHS[name]()
@@ -264,3 +264,51 @@ def test_modularity_entry_point(gamma):
         q = lg.modularity(off, idx, w, m, gamma)
         want = oracle.modularity(g, labels.astype(np.int32), gamma)
         assert abs(q - want) <= 1e-9 * max(1.0, abs(want))
+
+
+# ------------------------------------- variants: refine-based labels, Louvain
+VARIANT_FLAGS = [(lg.FLAG_REFINE_LABELS, oracle.REFINE_LABELS), (lg.FLAG_LOUVAIN, oracle.LOUVAIN)]
+
+
+@pytest.mark.parametrize("flags,oflags", VARIANT_FLAGS)
+@pytest.mark.parametrize("name", ["ring5x16", "sbm_workload", "road_300", "rmat_12", "hubs", "two_big_cliques"])
+def test_variants_deterministic_phases_bit_exact(name, flags, oflags):
+    g = DET_GRAPHS[name]()
+    ref = oracle.leiden(g, mode=oracle.SYNC, flags=oflags, trace=True)
+    assert ref.status == 0
+    memb, q, st, tr = run_gpu(g, lg.LEIDEN_DETERMINISTIC, trace=True, flags=flags)
+    bad = compare_traces(tr, ref.trace)
+    assert not bad, "\n".join(bad[:10])
+    assert st.passes == ref.passes
+    assert np.array_equal(memb, ref.membership)
+    assert abs(q - ref.modularity) <= Q_REL_REPORT * max(1.0, abs(ref.modularity))
+    if flags == lg.FLAG_LOUVAIN:
+        assert st.refine_iterations == 0
+
+
+@pytest.mark.parametrize("flags,oflags", VARIANT_FLAGS)
+@pytest.mark.parametrize("name", ["sbm_workload", "road_1000", "gnp_weighted"])
+def test_variants_async_quality(name, flags, oflags):
+    g = ASYNC_GRAPHS[name]()
+    seq = oracle.leiden(g, mode=oracle.SEQ, flags=oflags)
+    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC, flags=flags)
+    assert q >= seq.modularity - Q_TOL_ASYNC, (q, seq.modularity)
+    q_re = oracle.modularity(g, memb)
+    assert abs(q - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re))
+    if flags == lg.FLAG_REFINE_LABELS:  # the Leiden guarantee holds for either label rule
+        assert oracle.disconnected(g, memb)[0] == 0
+
+
+def test_louvain_deterministic_disconnected_counts():
+    """The Louvain variant's deterministic result is the oracle's, and the GPU
+    checker (Algorithm 5) counts its disconnected communities as the oracle's
+    BFS does, on graphs where the variant can leave some."""
+    import torch
+    for g in (gen.gnp(18, 0.25, seed=2108, wmax=3), gen.sbm(3000, 12, 0.04, 0.002, seed=4), gen.rmat(12, 16)):
+        ref = oracle.leiden(g, mode=oracle.SYNC, flags=oracle.LOUVAIN)
+        memb = run_gpu(g, lg.LEIDEN_DETERMINISTIC, flags=lg.FLAG_LOUVAIN)[0]
+        assert np.array_equal(memb, ref.membership)
+        off = torch.from_numpy(g.offsets).cuda()
+        idx = torch.from_numpy(g.indices).cuda()
+        m = torch.from_numpy(memb).cuda()
+        assert lg.disconnected(off, idx, m) == oracle.disconnected(g, memb)[0]

@@ -83,7 +83,8 @@ def test_serve_deterministic_matches_oracle():
 
 def test_serve_deterministic_limits():
     graphs = serve_mix()[:10]
-    for kw in ({"max_passes": 2}, {"max_iterations": 3}, {"schedule_layers": 5, "schedule_buckets": 2, "seed": 3}):
+    for kw in ({"max_passes": 2}, {"max_iterations": 3}, {"schedule_layers": 5, "schedule_buckets": 2, "seed": 3},
+               {"flags": lg.FLAG_LOUVAIN}, {"flags": lg.FLAG_REFINE_LABELS}):
         out, _, _ = serve(graphs, lg.LEIDEN_DETERMINISTIC, arrivals_per_step=4, **kw)
         for g, G in enumerate(graphs):
             ms = run_gpu(G, lg.LEIDEN_DETERMINISTIC, **kw)[0]

@@ -509,3 +509,17 @@ def test_rmat_sync_schedule_keeps_sequential_quality():
     syn = oracle.leiden(g, mode=oracle.SYNC)
     assert syn.modularity >= seq.modularity - 0.005, (syn.modularity, seq.modularity)
     assert oracle.disconnected(g, syn.membership)[0] == 0
+
+
+def test_schedule_layers_by_graph():
+    """S0: schedule_layers = 0 takes L = 1000 for an input with a row of more
+    than 2048 entries, else L = 32."""
+    light = gen.sbm(3000, 12, 0.04, 0.002, seed=4)
+    heavy = gen.rmat(14, 56, 0.57, 0.19, 0.19, seed=3)
+    assert np.diff(light.offsets).max() <= 2048 < np.diff(heavy.offsets).max()
+    for g, L in ((light, 32), (heavy, 1000)):
+        auto = oracle.leiden(g, mode=oracle.SYNC, trace=True)
+        fixed = oracle.leiden(g, mode=oracle.SYNC, schedule_layers=L, trace=True)
+        assert np.array_equal(auto.membership, fixed.membership)
+        for p in fixed.trace:
+            assert np.array_equal(auto.trace[p][oracle.T_MOVE], fixed.trace[p][oracle.T_MOVE])
