@@ -328,7 +328,14 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             CK(cudaMemsetAsync(q.gactive, 0, sizeof(unsigned) * prm.max_iterations, s));
             CK(cudaMemsetAsync(q.bar, 0, 2 * sizeof(unsigned), s));  // barrier state starts clean
             sc.prof = prof_begin(refine ? 8 : 0);
+            // steps without an eligible vertex are skipped where there are
+            // many steps (heavy-tailed schedules): in the refinement, and in
+            // the local-moving of a union of graphs, whose converged graphs
+            // leave whole steps idle (for one graph the marks of flagged
+            // neighbours cost about what they save)
+            sc.act = (nsteps > 64 && (refine || batch)) ? q.act : nullptr;
             CK(launch_sweep_coop(sc, sList, grid, s));
+            sc.act = nullptr;
             prof_end();
             q.launches++;
             ST(q.sync_scalars());

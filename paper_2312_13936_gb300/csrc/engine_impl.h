@@ -164,7 +164,7 @@ struct Handle::Impl {
     int32_t *C0 = nullptr, *Cp = nullptr, *CB = nullptr, *Cd = nullptr, *size = nullptr, *prop = nullptr,
             *step = nullptr, *key = nullptr, *list = nullptr, *flag = nullptr, *members = nullptr, *cursor = nullptr,
             *bnd = nullptr, *rep = nullptr, *label = nullptr, *minv = nullptr, *out = nullptr, *scnt = nullptr,
-            *slayer = nullptr, *sfcount = nullptr;
+            *slayer = nullptr, *sfcount = nullptr, *act = nullptr;
     int64_t *pos = nullptr, *pos2 = nullptr, *coff = nullptr, *cnt = nullptr, *tdeg = nullptr, *key_cnt = nullptr,
             *key_off = nullptr;
     void *K = nullptr, *Sig = nullptr, *Kagg = nullptr, *scan_tmp = nullptr, *part_tmp = nullptr;
@@ -273,6 +273,8 @@ struct Handle::Impl {
         ST(alloc(&key_cnt, key_cap));
         ST(alloc(&key_off, key_cap + 1));
         ST(alloc(&sfcount, 4096 + 1));
+        ST(alloc(&act, 1024));
+        CK(cudaMemsetAsync(act, 0, sizeof(int32_t) * 1024, s));
         for (int64_t **a : {&vseg0, &vseg, &vseg2}) ST(alloc(a, ng + 1));
         for (int32_t **a : {&gstate, &gdone, &gli, &glj, &gpasses}) ST(alloc(a, ng));
         for (int64_t **a : {&gkeep, &gcomm}) ST(alloc(a, ng));

@@ -77,6 +77,9 @@ template <class P, class W> struct SV {
     unsigned *bar;
     int *err;
     unsigned long long *prof;
+    // persistent sweep: act[k] == it + 1 marks step k as holding an eligible
+    // vertex in sweep it (steps without one are skipped); null elsewhere
+    int32_t *act;
     // batch of graphs (gid == null: one graph)
     const int32_t *gid;
     const A *gks;
@@ -97,6 +100,7 @@ template <class P> struct Sums {
     GAcc<unsigned long long> moved;
     typename P::tot *dq;
     unsigned long long *mv;
+    int32_t stamp = 0;  // this sweep's mark in act (persistent sweep)
 };
 
 template <class P, class W> SV<P, W> view(const SweepCtx &c) {
@@ -149,6 +153,7 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.bar = c.bar;
     a.err = c.err;
     a.prof = c.prof;
+    a.act = c.act;
     a.gid = c.gid;
     a.gks = static_cast<const A *>(c.gks);
     a.g2m = c.g2m;
@@ -256,6 +261,19 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
     return decide_sd<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, ldm(&a.Sig[d]), sm, cur_step, gv, kscale);
 }
 
+// act[k] = stamp, written only when it differs (a step's mark is read by
+// many threads and written about once)
+__device__ __forceinline__ void mark_step(int32_t *act, int32_t k, int32_t stamp) {
+    if (__ldcg(&act[k]) != stamp) act[k] = stamp;
+}
+// A neighbour u of a mover becomes unprocessed (Algorithm 2 pruning); its
+// step is marked active for the rest of this sweep.
+template <class P, class W>
+__device__ __forceinline__ void flag_unproc(const SV<P, W> &a, const Sums<P> &sm, int32_t u) {
+    a.unproc[u] = 1;
+    if (a.act) mark_step(a.act, a.step[u], sm.stamp);
+}
+
 // Eligibility: local-moving takes unprocessed vertices and marks them
 // processed (Algorithm 2 pruning); refinement takes isolated vertices (the
 // community of v has v as its only member, reading R7). In a batch, the
@@ -360,7 +378,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
         if (!REFINE && !P::det && mv) {
 #pragma unroll
             for (int k = 0; k < E; ++k)
-                if (k < dv) a.unproc[jj[k]] = 1;  // neighbours (self-loop included) of a mover
+                if (k < dv) flag_unproc(a, sm, jj[k]);  // neighbours (self-loop included) of a mover
         }
     }
 }
@@ -449,7 +467,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
         }
         if (!REFINE && !P::det) {
             mv = __shfl_sync(tmask, mv, 0, T);
-            if (mv && tl < dv) a.unproc[j] = 1;  // neighbours (self-loop included) of a mover
+            if (mv && tl < dv) flag_unproc(a, sm, j);  // neighbours (self-loop included) of a mover
         }
     }
 }
@@ -534,7 +552,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
         if (!REFINE && !P::det) {
             mv = __shfl_sync(kFull, mv, 0);
             if (mv)
-                for (int32_t e = lane; e < dv; e += 32) a.unproc[a.idx[e0 + e]] = 1;
+                for (int32_t e = lane; e < dv; e += 32) flag_unproc(a, sm, a.idx[e0 + e]);
         }
         __syncwarp();
     }
@@ -647,7 +665,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
         }
         __syncthreads();
         if (!REFINE && !P::det && s_mv)
-            for (int64_t e = tid; e < dv; e += blockDim.x) a.unproc[a.idx[e0 + e]] = 1;
+            for (int64_t e = tid; e < dv; e += blockDim.x) flag_unproc(a, sm, a.idx[e0 + e]);
     }
     __syncthreads();
 }
@@ -880,7 +898,7 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
             const int64_t j = __ldcg(&a.hj[p]);
             if (!__ldcg(&a.hmv[j])) continue;
             const int32_t v = __ldg(&a.hubs[j]);
-            a.unproc[a.idx[a.off[v] + (x - __ldcg(&a.heoff[p]))]] = 1;
+            flag_unproc(a, sm, a.idx[a.off[v] + (x - __ldcg(&a.heoff[p]))]);
         }
     }
     return true;
@@ -921,7 +939,7 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
             e0 = a.off[v];
             dv = a.deg[v];
             if (dv <= 32)
-                for (int32_t e = 0; e < dv; ++e) a.unproc[a.idx[e0 + e]] = 1;
+                for (int32_t e = 0; e < dv; ++e) flag_unproc(a, sm, a.idx[e0 + e]);
         }
         unsigned longs = __ballot_sync(kFull, c >= 0 && dv > 32);
         while (longs) {
@@ -929,7 +947,7 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
             longs &= longs - 1;
             const int64_t es = __shfl_sync(kFull, e0, src);
             const int32_t ds = __shfl_sync(kFull, dv, src);
-            for (int32_t e = lane; e < ds; e += 32) a.unproc[a.idx[es + e]] = 1;
+            for (int32_t e = lane; e < ds; e += 32) flag_unproc(a, sm, a.idx[es + e]);
         }
     }
 }
@@ -993,11 +1011,31 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
         Sums<P> sm;
         sm.dq = a.dq_arr + (size_t)it * a.G;
         sm.mv = a.moved_arr + (size_t)it * a.G;
+        sm.stamp = it + 1;
+        if (a.act) {
+            // steps holding an eligible vertex at the start of the sweep
+            // (unprocessed, or isolated in the refinement); moves mark the
+            // steps of the neighbours they flag as the sweep goes on, and
+            // nothing makes a vertex isolated during the refinement
+            const int64_t nl = __ldcg(&a.key_off[(int64_t)a.nsteps * kNumBins]);
+            for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl;
+                 t += (int64_t)gridDim.x * blockDim.x) {
+                const int32_t v = list[t];
+                if (B && ldm(&a.gdone[graph_of<B>(a, v)])) continue;
+                const bool e = REFINE ? ldm(&a.size[ldm(&a.C[v])]) == 1 : ldm(&a.unproc[v]) != 0;
+                if (e) mark_step(a.act, a.step[v], sm.stamp);
+            }
+            if (!(ok = grid_barrier(a.bar, a.err))) break;
+        }
         int64_t hub_j0 = 0;  // ordinal of the step's first hub
         for (int32_t k = 0; k < a.nsteps && ok; ++k) {
             const int64_t *ko = a.key_off + (int64_t)k * kNumBins;
             const int64_t b0 = __ldcg(&ko[0]), b8 = __ldcg(&ko[8]);
             if (b0 == b8) continue;  // empty step: every block sees the same counts
+            if (a.act && __ldcg(&a.act[k]) != sm.stamp) {  // nothing eligible: the same in every block
+                hub_j0 += __ldcg(&ko[7]) - __ldcg(&ko[6]);
+                continue;
+            }
             run_thread<P, W, REFINE, B>(a, list, __ldcg(&ko[1]), __ldcg(&ko[2]), k, sm, pc);
             run_tile<P, W, 16, REFINE, B>(a, list, __ldcg(&ko[2]), __ldcg(&ko[3]), k, sm, pc);
             run_tile<P, W, 32, REFINE, B>(a, list, __ldcg(&ko[3]), __ldcg(&ko[4]), k, sm, pc);

@@ -82,6 +82,7 @@ struct SweepCtx {
     // hd, hcand, hmv, hkey, hkvd (8 bytes); per eligible hub of a step: hj,
     // htoff, heoff (+1); hinfo: 3 words
     bool grid_hubs = false;
+    int32_t *act = nullptr;  // persistent sweep: per-step marks (1024 entries; null: no step skipped)
     const int32_t *hubs = nullptr;
     int32_t *hj = nullptr;
     int64_t *htoff = nullptr, *heoff = nullptr, *hinfo = nullptr;
