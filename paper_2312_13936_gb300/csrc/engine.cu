@@ -213,6 +213,9 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             return LEIDEN_ERR_OOM;
         }
         ST(q.ensure_hub(0, (int)span, det));
+        // clean tables; every step's last scan leaves them clean again
+        CK(cudaMemsetAsync(q.hub_keys, 0xff, sizeof(int32_t) * span, s));
+        CK(cudaMemsetAsync(q.hub_vals, 0, 8 * span, s));
     }
     // global tables for bin 6 (one per block)
     int hub_bits = 0, hub_regions = 0;

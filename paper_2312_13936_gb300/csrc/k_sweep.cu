@@ -794,12 +794,8 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     if (!grid_barrier(a.bar, a.err)) return false;
     const int64_t np = __ldcg(&a.hinfo[0]), S = __ldcg(&a.hinfo[1]), E = __ldcg(&a.hinfo[2]);
     if (np == 0) return true;
-    for (int64_t s = tid; s < S; s += nthreads) {
-        a.hub_keys[s] = -1;
-        a.hub_vals[s] = 0;
-    }
-    if (!grid_barrier(a.bar, a.err)) return false;
-    // insertion
+    // insertion (the tables are clean: the last scan of a step clears every
+    // slot it reads, and the engine clears them before the first sweep)
     for (int64_t x0 = gw * 32; x0 < E; x0 += warps * 32) {
         const int64_t x = x0 + lane;
         int64_t p = -1, tbase = 0;
@@ -824,9 +820,13 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
             if (!hash_add(a.hub_keys + tbase, a.hub_vals + tbase, bits, key, val)) set_error(a.err, kErrHashFull);
     }
     if (!grid_barrier(a.bar, a.err)) return false;
-    // the largest key per hub (pass 0), then the smallest community id with
-    // it (pass 1); K_{v->d} from the slot of v's own community
-    for (int pass = 0; pass < 2; ++pass) {
+    // deterministic mode: the largest key per hub (pass 0), then the
+    // smallest community id with it (pass 1); asynchronous mode: one pass,
+    // key and id packed in one word (fp32 key above the complemented id, so
+    // that the largest word is the largest key with the smallest id). K_{v->d}
+    // from the slot of v's own community. The last pass clears the slots.
+    constexpr int npass = P::det ? 2 : 1;
+    for (int pass = 0; pass < npass; ++pass) {
         for (int64_t s0 = gw * 32; s0 < S; s0 += warps * 32) {
             const int64_t s = s0 + lane;
             int64_t j = -1;
@@ -838,6 +838,10 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                     j = __ldcg(&a.hj[range_at(a.htoff, np, s)]);
                     const int32_t d = __ldcg(&a.hd[j]);
                     const A sum = __ldcg(&a.hub_vals[s]);
+                    if (pass == npass - 1) {
+                        a.hub_keys[s] = -1;
+                        a.hub_vals[s] = 0;
+                    }
                     if (k == d) {
                         if (pass == 0) a.hkvd[j] = sum;
                         k = -1;
@@ -845,6 +849,7 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                         const int32_t v = __ldg(&a.hubs[j]);
                         const int32_t gv = graph_of<B>(a, v);
                         enc = key_order(move_key(kscale_of<B>(a, gv), sum, a.K[v], ldm(&a.Sig[k]), a.gamma));
+                        if (!P::det) enc = (enc << 32) | (unsigned long long)(~(uint32_t)k);
                         if (pass == 0) pc.v[3]++;
                     }
                 }
@@ -877,8 +882,16 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
         const int32_t d = __ldcg(&a.hd[j]);
         const int32_t v = __ldg(&a.hubs[j]);
         const int32_t gv = graph_of<B>(a, v);
-        const int32_t c = __ldcg(&a.hcand[j]);
-        const A bk = c == INT_MAX ? AccLimits<A>::lowest() : key_of_order(__ldcg(&a.hkey[j]), A(0));
+        const unsigned long long best = __ldcg(&a.hkey[j]);
+        int32_t c;
+        A bk;
+        if (P::det) {
+            c = __ldcg(&a.hcand[j]);
+            bk = c == INT_MAX ? AccLimits<A>::lowest() : key_of_order(best, A(0));
+        } else {
+            c = best == 0ULL ? INT_MAX : (int32_t)~(uint32_t)best;
+            bk = best == 0ULL ? AccLimits<A>::lowest() : key_of_order(best >> 32, A(0));
+        }
         const A kd = __ldcg(&a.hkvd[j]);
         const bool mv = decide<P, W, REFINE, B>(a, v, d, a.K[v], bk, c, kd, sm, cur_step, gv, kscale_of<B>(a, gv));
         const int32_t dv = a.deg[v];
