@@ -34,8 +34,11 @@
  *       the smallest super-vertex id of that community; Sigma' is the sum of
  *       K' over each label.
  *   R4  |Gamma| is the number of non-empty refined communities and
- *       |Gamma_old| the vertex count of the current graph; stop if the ratio
- *       exceeds the aggregation tolerance.
+ *       |Gamma_old| the vertex count of the current graph, both without the
+ *       z vertices that have no edges (each is its own community in every
+ *       pass and can take part in no aggregation, Section 4.1's purpose of
+ *       the tolerance): stop if (|Gamma| - z) / (|Gamma_old| - z) exceeds
+ *       the aggregation tolerance.
  *   R5  l_i is the number of local-moving sweeps executed and l_j the
  *       number of refinement sweeps; see R5' for the stop test.
  *   R6  Refinement repeats sweeps over the still-isolated vertices until a
@@ -944,7 +947,9 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
         for (int64_t c = 0; c < n; ++c) size[c] = 0;
         for (int64_t i = 0; i < n; ++i) { if (!size[CB[i]]) nbound++; size[CB[i]] = 1; }
         if (li <= 1 && nbound == ncomm) { broke = 1; break; }                    /* R5' */
-        if ((double)ncomm / (double)n > p->aggregation_tolerance) { broke = 1; break; } /* R4 */
+        int64_t z = 0; /* R4: vertices without edges */
+        for (int64_t i = 0; i < n; ++i) z += G.deg[i] == 0;
+        if ((double)(ncomm - z) / (double)(n - z) > p->aggregation_tolerance) { broke = 1; break; } /* R4 */
 
         /* renumber communities in C' */
         for (int64_t i = 0; i < n; ++i) Cp[i] = newid[Cp[i]];

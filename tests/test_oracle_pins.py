@@ -523,3 +523,22 @@ def test_schedule_layers_by_graph():
         assert np.array_equal(auto.membership, fixed.membership)
         for p in fixed.trace:
             assert np.array_equal(auto.trace[p][oracle.T_MOVE], fixed.trace[p][oracle.T_MOVE])
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_vertices_without_edges_do_not_stop_the_passes(mode):
+    """R4: vertices without edges are left out of the aggregation-tolerance
+    ratio, so adding any number of them changes nothing else."""
+    g = gen.sbm(2000, 10, 0.05, 0.002, seed=11)
+    z = 6000
+    g2 = gen.CSR(g.n + z, np.concatenate([g.offsets, np.full(z, g.offsets[-1], dtype=g.offsets.dtype)]),
+                 g.indices, g.weights)
+    r = oracle.leiden(g, mode=mode)
+    r2 = oracle.leiden(g2, mode=mode)
+    assert r.passes >= 2
+    assert r2.passes == r.passes
+    assert np.array_equal(r2.membership[:g.n], r.membership)
+    assert np.array_equal(r2.membership[g.n:], np.arange(z) + r.membership.max() + 1)
+    # the ratio without the rule would be above the tolerance after the first pass
+    t = oracle.leiden(g2, mode=mode, trace=True).trace[0][oracle.T_COUNTS]
+    assert (t[3]) / t[0] > 0.8 and (t[3] - z) / (t[0] - z) <= 0.8
