@@ -400,7 +400,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     // the graphs that go on keep their refined communities, densely
     // renumbered after those of the graphs before them
     CK(launch_graph_stop(q.vseg, q.pos, q.pos2, q.gli, q.g2m, prm.aggregation_tolerance, NG, q.gstate, q.gkeep,
-                         q.gpasses, s, r.gpass, r.graph_max_passes));
+                         q.gpasses, s, r.gpass, r.graph_max_passes, G.deg, batch ? cur_gid : nullptr, n, q.gzero));
     CK(launch_exclusive_scan(q.gkeep, q.vseg2, NG, q.scan_tmp, s));
     q.launches += 14;
     int64_t counts[3];

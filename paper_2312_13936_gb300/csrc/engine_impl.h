@@ -206,6 +206,7 @@ struct Handle::Impl {
     int32_t *gid0 = nullptr, *gidA = nullptr, *gidB = nullptr;
     int32_t *gstate = nullptr, *gdone = nullptr, *gli = nullptr, *glj = nullptr, *gpasses = nullptr;
     int64_t *gkeep = nullptr, *gcomm = nullptr;
+    unsigned long long *gzero = nullptr;  // vertices without edges of every graph (reading R4)
     long long *gsumk = nullptr;            // per-graph sums of K (int64 or fp64 bits)
     long long *gks = nullptr;              // per-graph key scale (int64 2m or fp32 1/2m)
     double *g2m = nullptr, *gq = nullptr, *gmsum = nullptr;
@@ -278,6 +279,7 @@ struct Handle::Impl {
         for (int64_t **a : {&vseg0, &vseg, &vseg2}) ST(alloc(a, ng + 1));
         for (int32_t **a : {&gstate, &gdone, &gli, &glj, &gpasses}) ST(alloc(a, ng));
         for (int64_t **a : {&gkeep, &gcomm}) ST(alloc(a, ng));
+        ST(alloc(&gzero, ng));
         ST(alloc(&gsumk, ng));
         ST(alloc(&gks, ng));
         ST(alloc(&g2m, ng));

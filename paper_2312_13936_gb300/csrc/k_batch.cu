@@ -90,9 +90,24 @@ __global__ void k_phase_init(const int32_t *state, int32_t G, int32_t *gdone, in
     }
 }
 
+// gz[g] += vertices of graph g without edges (one atomic per graph per warp)
+__global__ void k_graph_zero_deg(const int32_t *deg, const int32_t *gid, int64_t n, unsigned long long *gz) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < n;
+         v0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + lane;
+        const bool z = v < n && deg[v] == 0;
+        if (!__ballot_sync(kFull, z)) continue;
+        const int32_t g = (z && gid) ? gid[v] : 0;
+        const unsigned peers = __match_any_sync(kFull, z ? g : -1);
+        if (z && lane == __ffs(peers) - 1) atomicAdd(&gz[g], (unsigned long long)__popc(peers));
+    }
+}
+
 __global__ void k_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                              const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
-                             int32_t *passes, const int32_t *gpass, int32_t max_passes) {
+                             int32_t *passes, const int32_t *gpass, int32_t max_passes,
+                             const unsigned long long *gz) {
     GRID_STRIDE(g, G) {
         if (state[g] != kGraphActive) {
             keep[g] = 0;
@@ -101,9 +116,11 @@ __global__ void k_graph_stop(const int64_t *vseg, const int64_t *pos, const int6
         passes[g]++;
         const int64_t a = vseg[g], b = vseg[g + 1];
         const int64_t ncomm = pos[b] - pos[a], nbound = pos2[b] - pos2[a];
+        // R4 leaves out the z vertices without edges (each is its own community)
+        const int64_t z = (int64_t)gz[g], live = (b - a) - z;
         const bool stop = !(g2m[g] > 0)                              // reading R12: no edges
                           || (li[g] <= 1 && nbound == ncomm)         // globally converged (R5')
-                          || (double)ncomm / (double)(b - a) > agg_tol   // low shrink (R4)
+                          || (live > 0 && (double)(ncomm - z) / (double)live > agg_tol)  // low shrink (R4)
                           || (gpass && gpass[g] + 1 >= max_passes);   // its MAX_PASSES
         if (stop) {
             state[g] = kGraphFinishing;
@@ -282,10 +299,14 @@ cudaError_t launch_phase_init(const int32_t *state, int32_t G, int32_t *gdone, i
 }
 cudaError_t launch_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                               const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
-                              int32_t *passes, cudaStream_t s, const int32_t *gpass, int32_t max_passes) {
+                              int32_t *passes, cudaStream_t s, const int32_t *gpass, int32_t max_passes,
+                              const int32_t *deg, const int32_t *gid, int64_t n, unsigned long long *gz) {
     if (G <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(gz, 0, sizeof(unsigned long long) * G, s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) k_graph_zero_deg<<<grid_for(n, 256), 256, 0, s>>>(deg, gid, n, gz);
     k_graph_stop<<<grid_for(G, 256), 256, 0, s>>>(vseg, pos, pos2, li, g2m, agg_tol, G, state, keep, passes, gpass,
-                                                  max_passes);
+                                                  max_passes, gz);
     return cudaGetLastError();
 }
 cudaError_t launch_renumber_batch(const int32_t *C, const int64_t *pos, const int32_t *gid, const int64_t *vseg,

@@ -234,10 +234,12 @@ cudaError_t launch_phase_init(const int32_t *state, int32_t G, int32_t *gdone, i
 // communities of the graphs that go on (0 otherwise); passes[g]++ for active
 // graphs. With gpass (graphs at different passes) a graph also stops when
 // gpass[g] + 1 reaches max_passes.
+// (deg, gid, n: the current graph; reading R4 leaves each graph's vertices
+// without edges out of its ratio, counted into gz, G entries of scratch)
 cudaError_t launch_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                               const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
-                              int32_t *passes, cudaStream_t s, const int32_t *gpass = nullptr,
-                              int32_t max_passes = 0);
+                              int32_t *passes, cudaStream_t s, const int32_t *gpass, int32_t max_passes,
+                              const int32_t *deg, const int32_t *gid, int64_t n, unsigned long long *gz);
 // C' at the start of local-moving: the first n_cont vertices continue with
 // their move-based labels, the others start as singletons
 cudaError_t launch_init_labels(const int32_t *label, int64_t n_cont, int64_t n, int32_t *Cp, cudaStream_t s);

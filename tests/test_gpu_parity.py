@@ -53,6 +53,13 @@ def two_big_cliques(k=1500):
     return gen.from_edges(2 * k, u, v)
 
 
+def with_isolated(g, z):
+    """g followed by z vertices without edges (reading R4 leaves them out of
+    the aggregation-tolerance ratio)."""
+    return gen.CSR(g.n + z, np.concatenate([g.offsets, np.full(z, g.offsets[-1], dtype=g.offsets.dtype)]),
+                   g.indices, g.weights)
+
+
 DET_GRAPHS = {
     "ring5x16": lambda: gen.ring_of_cliques(5, 16),
     "sbm_workload": gen.sbm_workload,
@@ -62,6 +69,7 @@ DET_GRAPHS = {
     "rmat_12": lambda: gen.rmat(12, 16),
     "hubs": hub_graph,
     "two_big_cliques": two_big_cliques,
+    "sbm_with_isolated": lambda: with_isolated(gen.sbm(2000, 10, 0.05, 0.002, seed=11), 6000),
 }
 
 
