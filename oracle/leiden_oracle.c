@@ -109,6 +109,14 @@
  *       partition (so l_j = 0 and R5' reduces to l_i <= 1), and aggregation
  *       merges the local-moving communities. Communities need not be
  *       connected.
+ *   V3  OG_RANDOM_REFINE (SEQ mode only): the randomized refinement of the
+ *       original Leiden method (Sections 2.2 and 4.1): an isolated vertex
+ *       joins one of the communities of positive gain within its bound with
+ *       probability proportional to the gain, instead of the best one. The
+ *       draw: the candidates in ascending community id, u = ((x >> 11) +
+ *       0.5) / 2^53 with x = SplitMix64 output number i+1 from state
+ *       seed + 0xD1B54A32D192ED03 * (64 pass + sweep + 1), the first
+ *       candidate whose running gain sum exceeds u times the total.
  *   Both modes:
  *   R5' The passes stop (global convergence) when the local-moving phase
  *       converged in its first sweep (l_i <= 1) and the refinement split no
@@ -122,7 +130,7 @@
 
 enum { OG_OK = 0, OG_ERR_INVALID = -1, OG_ERR_OOM = -3, OG_ERR_UNSUPPORTED = -6, OG_ERR_OVERFLOW = -7 };
 enum { OG_SEQ = 0, OG_SYNC = 1 };
-enum { OG_REFINE_SINGLE_SWEEP = 1, OG_NO_PRUNE = 2, OG_REFINE_LABELS = 4, OG_LOUVAIN = 8 };
+enum { OG_REFINE_SINGLE_SWEEP = 1, OG_NO_PRUNE = 2, OG_REFINE_LABELS = 4, OG_LOUVAIN = 8, OG_RANDOM_REFINE = 16 };
 
 /* what-codes passed to the trace callback */
 enum {
@@ -147,7 +155,8 @@ typedef struct {
     int32_t max_passes;           /* MAX_PASSES (R1), default 10 */
     int32_t mode;                 /* OG_SEQ or OG_SYNC */
     int32_t flags;                /* OG_REFINE_SINGLE_SWEEP, OG_NO_PRUNE (SEQ, tests only),
-                                     OG_REFINE_LABELS, OG_LOUVAIN (V1, V2) */
+                                     OG_REFINE_LABELS, OG_LOUVAIN (V1, V2),
+                                     OG_RANDOM_REFINE (V3, SEQ only) */
     int32_t schedule_layers;      /* SYNC: L, priority layers (S0); 0 (default): by the graph, S0 */
     int32_t schedule_buckets;     /* SYNC: B, buckets after the last layer (S0), default 16 */
     uint64_t seed;                /* SYNC: priority seed (S0), default 0 */
@@ -289,9 +298,18 @@ static int move_seq(const og_graph *g, int32_t *C, const double *K, double *Sig,
 }
 
 /* leidenRefine (Algorithm 3), sequential, with R6/R7: returns l_j. */
+uint64_t og_splitmix64_at(uint64_t s, uint64_t i);
+static int cmp_cand(const void *a, const void *b) {
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* rnd: NULL for the greedy refinement (Algorithm 3); else the state of V3's
+ * draws for this pass (seed + 0xD1B54A32D192ED03 * (64 pass + sweep + 1) is
+ * formed per sweep) and a scratch array of n candidate ids. */
 static int refine_seq(const og_graph *g, const int32_t *CB, int32_t *C, const double *K, double *Sig,
                       int32_t *size, double gamma, double two_m, int32_t max_it, int single_sweep,
-                      og_table *H) {
+                      og_table *H, const uint64_t *rnd, int32_t *cand) {
     int64_t n = g->n;
     double m = two_m / 2.0;
     int sweeps = 0;
@@ -306,11 +324,35 @@ static int refine_seq(const og_graph *g, const int32_t *CB, int32_t *C, const do
             double Kic_own = H->has[c] ? H->val[c] : 0.0;
             int32_t best = -1;
             double best_dq = 0.0;
-            for (int64_t k = 0; k < H->nkeys; ++k) {
-                int32_t cc = H->keys[k];
-                if (cc == c) continue;
-                double q = delta_q(H->val[cc], Kic_own, K[i], Sig[cc], Sig[c], m, gamma);
-                if (best < 0 || q > best_dq || (q == best_dq && cc < best)) { best = cc; best_dq = q; }
+            if (rnd) { /* V3: a candidate of positive gain, with probability proportional to it */
+                int64_t nc = 0;
+                for (int64_t k = 0; k < H->nkeys; ++k)
+                    if (H->keys[k] != c) cand[nc++] = H->keys[k];
+                qsort(cand, (size_t)nc, sizeof(int32_t), cmp_cand);
+                double total = 0.0;
+                for (int64_t k = 0; k < nc; ++k) {
+                    double q = delta_q(H->val[cand[k]], Kic_own, K[i], Sig[cand[k]], Sig[c], m, gamma);
+                    if (q > 0.0) total += q;
+                }
+                if (!(total > 0.0)) continue;
+                uint64_t x = og_splitmix64_at(*rnd + 0xD1B54A32D192ED03ULL * (uint64_t)(it + 1), (uint64_t)i);
+                double u = ((double)(x >> 11) + 0.5) / 9007199254740992.0;
+                double t = u * total, run = 0.0;
+                for (int64_t k = 0; k < nc; ++k) {
+                    double q = delta_q(H->val[cand[k]], Kic_own, K[i], Sig[cand[k]], Sig[c], m, gamma);
+                    if (!(q > 0.0)) continue;
+                    run += q;
+                    best = cand[k];
+                    best_dq = q;
+                    if (run > t) break;
+                }
+            } else {
+                for (int64_t k = 0; k < H->nkeys; ++k) {
+                    int32_t cc = H->keys[k];
+                    if (cc == c) continue;
+                    double q = delta_q(H->val[cc], Kic_own, K[i], Sig[cc], Sig[c], m, gamma);
+                    if (best < 0 || q > best_dq || (q == best_dq && cc < best)) { best = cc; best_dq = q; }
+                }
             }
             if (best < 0 || !(best_dq > 0.0)) continue;
             Sig[c] -= K[i];
@@ -830,6 +872,7 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
     }
     if (p->max_iterations < 1 || p->max_passes < 0 || !(p->tolerance_drop > 0)) return OG_ERR_INVALID;
     if (p->mode == OG_SYNC && (p->schedule_layers < 0 || p->schedule_buckets < 1)) return OG_ERR_INVALID;
+    if (p->mode == OG_SYNC && (p->flags & OG_RANDOM_REFINE)) return OG_ERR_UNSUPPORTED; /* V3: SEQ only */
     /* S0: L of the run (0: 1000 for an input with a row of more than 2048
      * entries, else 32) */
     int32_t Ls = p->schedule_layers;
@@ -925,9 +968,11 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
             }
             /* refinement phase (Algorithm 3) */
             int single = (p->flags & OG_REFINE_SINGLE_SWEEP) != 0;
+            const uint64_t rstate = p->seed + 0xD1B54A32D192ED03ULL * (uint64_t)(64 * lp); /* V3 draws */
             lj = sync ? refine_sync(&G, CB, Cp, Ki, Si, size, (int64_t)two_m, p->max_iterations, single,
                                     layer, nl, &H)
-                      : refine_seq(&G, CB, Cp, K, Sig, size, gamma, two_m, p->max_iterations, single, &H);
+                      : refine_seq(&G, CB, Cp, K, Sig, size, gamma, two_m, p->max_iterations, single, &H,
+                                   (p->flags & OG_RANDOM_REFINE) ? &rstate : NULL, newid);
             if (lj < 0) goto done;
         }
         if (cb) cb(ctx, lp, OG_T_REFINE, Cp, n);

@@ -542,3 +542,48 @@ def test_vertices_without_edges_do_not_stop_the_passes(mode):
     # the ratio without the rule would be above the tolerance after the first pass
     t = oracle.leiden(g2, mode=mode, trace=True).trace[0][oracle.T_COUNTS]
     assert (t[3]) / t[0] > 0.8 and (t[3] - z) / (t[0] - z) <= 0.8
+
+
+# ------------------------------------------- V3: randomized refinement
+def test_random_refinement_draws_in_proportion_to_the_gain():
+    """V3: the first isolated vertex of the refinement (vertex 0, with every
+    vertex still alone) joins the community of a neighbour j inside its
+    local-moving community with probability gain_j / (sum of the positive
+    gains), the gains from Eq. 2 on the singleton partition."""
+    u = [0, 0, 0, 0, 1, 2, 3, 4]
+    v = [1, 2, 3, 4, 2, 3, 4, 1]
+    w = [1.0, 2.0, 3.0, 4.0, 1.0, 1.0, 1.0, 1.0]
+    g = gen.from_edges(5, u, v, w)
+    bound = oracle.leiden(g, mode=oracle.SEQ, max_passes=1, trace=True).trace[0][oracle.T_MOVE]
+    cands = [j for j in range(1, 5) if bound[j] == bound[0]]
+    single = np.arange(5)
+    gains = np.array([oracle.delta_modularity(g, single, 0, j) for j in cands])
+    pos = np.clip(gains, 0, None)
+    assert len(cands) >= 2 and np.count_nonzero(pos) >= 2
+    expect = pos / pos.sum()
+    seeds = 600
+    counts = np.zeros(len(cands))
+    for s in range(seeds):
+        t = oracle.leiden(g, mode=oracle.SEQ, flags=oracle.RANDOM_REFINE, seed=s, max_passes=1, trace=True).trace[0]
+        assert np.array_equal(t[oracle.T_MOVE], bound)  # local-moving draws nothing
+        counts[cands.index(int(t[oracle.T_REFINE][0]))] += 1
+    freq = counts / seeds
+    sigma = np.sqrt(expect * (1 - expect) / seeds)
+    assert np.all(np.abs(freq - expect) <= 4 * sigma + 1e-12), (freq, expect)
+    # the greedy rule takes the largest gain every time
+    r = oracle.leiden(g, mode=oracle.SEQ, max_passes=1, trace=True)
+    assert int(r.trace[0][oracle.T_REFINE][0]) == cands[int(np.argmax(gains))]
+
+
+def test_random_refinement_keeps_the_leiden_guarantees():
+    for g in (gen.sbm(3000, 12, 0.04, 0.002, seed=4), gen.road(100), gen.rmat(12, 16, seed=2)):
+        r = oracle.leiden(g, mode=oracle.SEQ, flags=oracle.RANDOM_REFINE, seed=5, trace=True)
+        assert r.status == 0
+        assert _components_inside(g, r.membership) == 0
+        t0 = r.trace[0]
+        for c in np.unique(t0[oracle.T_REFINE]):
+            assert np.unique(t0[oracle.T_MOVE][t0[oracle.T_REFINE] == c]).size == 1
+    res = oracle.leiden(gen.ring_of_cliques(5, 16), mode=oracle.SEQ, flags=oracle.RANDOM_REFINE, seed=3)
+    assert np.array_equal(res.membership, np.repeat(np.arange(16), 5))
+    # SYNC mode has no randomized variant
+    assert oracle.leiden(gen.road(10), mode=oracle.SYNC, flags=oracle.RANDOM_REFINE).status == oracle.ERR_UNSUPPORTED
