@@ -85,14 +85,19 @@ def variants_form(h, off, idx, mode, flags, stream, runs=5):
     the Louvain variant (no refinement, Section 5: Leiden was 13% slower
     and Louvain left 4.0% of its communities disconnected) and refine-based
     super-vertex labels (Section 4.1: about the same time and modularity as
-    move-based ones). Median of `runs` device-timed runs each."""
+    move-based ones) and, in the asynchronous mode, the randomized refinement
+    of the original method (Section 4.1: the greedy one was faster and better).
+    Median of `runs` device-timed runs each."""
     import statistics
 
     import torch
 
     import paper_2312_13936_gb300 as lg
     out = {}
-    for name, f in (("leiden", 0), ("louvain", lg.FLAG_LOUVAIN), ("refine_labels", lg.FLAG_REFINE_LABELS)):
+    variants = [("leiden", 0), ("louvain", lg.FLAG_LOUVAIN), ("refine_labels", lg.FLAG_REFINE_LABELS)]
+    if mode == lg.LEIDEN_ASYNC:  # the randomized refinement has no deterministic mode
+        variants.append(("random_refine", lg.FLAG_RANDOM_REFINE))
+    for name, f in variants:
         h.run(mode=mode, flags=flags | f)
         ts, qs = [], []
         for _ in range(runs):

@@ -69,9 +69,14 @@ enum {
     LEIDEN_FLAG_REFINE_LABELS = 64u,      /* refine-based super-vertex labels (Section 4.1): every
                                              super-vertex starts the next pass in its own community
                                              instead of its move-based one */
-    LEIDEN_FLAG_LOUVAIN = 128u            /* the Louvain method of the paper's comparison (Section 5):
+    LEIDEN_FLAG_LOUVAIN = 128u,           /* the Louvain method of the paper's comparison (Section 5):
                                              no refinement phase; each pass aggregates its local-moving
                                              communities, which need not be connected */
+    LEIDEN_FLAG_RANDOM_REFINE = 256u      /* asynchronous mode: randomized refinement (Sections 2.2, 4.1):
+                                             an isolated vertex joins a community of positive gain within
+                                             its bound with probability proportional to the gain, drawn
+                                             from the seed, pass, sweep, vertex and community; the
+                                             deterministic mode refuses it (LEIDEN_ERR_UNSUPPORTED) */
 };
 
 typedef struct {

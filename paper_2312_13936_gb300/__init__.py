@@ -20,7 +20,7 @@ from . import _build
 __all__ = [
     "LEIDEN_HOST", "LEIDEN_DEVICE", "LEIDEN_ASYNC", "LEIDEN_DETERMINISTIC", "FLAG_VALIDATE",
     "FLAG_REFINE_SINGLE_SWEEP", "FLAG_TRACE", "FLAG_PROFILE", "FLAG_STEP_LAUNCHES",
-    "FLAG_REFINE_LABELS", "FLAG_LOUVAIN", "LeidenError", "Params", "Stats", "KernelProfile",
+    "FLAG_REFINE_LABELS", "FLAG_LOUVAIN", "FLAG_RANDOM_REFINE", "LeidenError", "Params", "Stats", "KernelProfile",
     "library", "leiden_params_default", "leiden_create", "leiden_run", "leiden_destroy", "leiden_modularity",
     "leiden_trace_get", "leiden_profile_get", "leiden_modularity_noalloc",
     "leiden_status_string", "leiden_last_error", "Leiden", "modularity", "leiden_batch_create",
@@ -32,7 +32,7 @@ __all__ = [
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
 LEIDEN_ASYNC, LEIDEN_DETERMINISTIC = 0, 1
 FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE, FLAG_PROFILE, FLAG_STEP_LAUNCHES = 1, 2, 4, 8, 16
-FLAG_REFINE_LABELS, FLAG_LOUVAIN = 64, 128
+FLAG_REFINE_LABELS, FLAG_LOUVAIN, FLAG_RANDOM_REFINE = 64, 128, 256
 PROFILE_CLASSES = 24
 PROFILE_PHASES = ("move", "refine", "aggregate")
 PROFILE_BINS = ("sweep", "thread", "tile16", "tile32", "warp", "block", "global", "unused")

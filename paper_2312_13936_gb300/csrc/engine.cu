@@ -304,6 +304,9 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     // otherwise one host-driven sweep at a time. Returns the sweeps run.
     auto run_phase = [&](bool refine, int *iters, int32_t *giters) -> leiden_status {
         sc.refine = refine;
+        // randomized refinement (asynchronous mode; run() refuses it otherwise)
+        sc.rand_refine = refine && (prm.flags & LEIDEN_FLAG_RANDOM_REFINE) != 0;
+        sc.rseed = prm.seed + 0xD1B54A32D192ED03ULL * (uint64_t)(64 * (r.gpass ? 0 : lp));
         const bool single = refine && (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP);
         const int per_sm = step_launches ? 0 : sweep_coop_blocks_per_sm(det, sG.w_int, refine);
         CK(launch_phase_init(q.gstate, NG, q.gdone, giters, s));
@@ -351,6 +354,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             k++;
             CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double) + sizeof(long long), s));
             CK(cudaMemsetAsync(&q.dsc->moved, 0, sizeof(unsigned long long), s));
+            sc.sweep = it;
             ST(run_steps(refine));
             ST(q.sync_scalars());
             if (refine) {
@@ -634,6 +638,10 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     if (nkeys + 1 > q.key_cap || L > 4096) {
         set_last_error("schedule_layers + schedule_buckets too large");
         return LEIDEN_ERR_INVALID;
+    }
+    if (det && (prm.flags & LEIDEN_FLAG_RANDOM_REFINE)) {
+        set_last_error("the randomized refinement has no deterministic mode");
+        return LEIDEN_ERR_UNSUPPORTED;
     }
     if (batch && (trace || (prm.flags & LEIDEN_FLAG_STEP_LAUNCHES))) {
         set_last_error("a batch of graphs runs without trace and without per-step launches");

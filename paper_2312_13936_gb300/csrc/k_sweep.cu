@@ -80,6 +80,12 @@ template <class P, class W> struct SV {
     // persistent sweep: act[k] == it + 1 marks step k as holding an eligible
     // vertex in sweep it (steps without one are skipped); null elsewhere
     int32_t *act;
+    // randomized refinement (asynchronous mode): draws from SplitMix64 with
+    // state rseed + 0xD1B54A32D192ED03 * (sweep + 1); sweep: the sweep of a
+    // per-step launch
+    bool rand_refine;
+    uint64_t rseed;
+    int32_t sweep;
     // batch of graphs (gid == null: one graph)
     const int32_t *gid;
     const A *gks;
@@ -154,6 +160,9 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.err = c.err;
     a.prof = c.prof;
     a.act = c.act;
+    a.rand_refine = c.rand_refine;
+    a.rseed = c.rseed;
+    a.sweep = c.sweep;
     a.gid = c.gid;
     a.gks = static_cast<const A *>(c.gks);
     a.g2m = c.g2m;
@@ -261,6 +270,24 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
     return decide_sd<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, ldm(&a.Sig[d]), sm, cur_step, gv, kscale);
 }
 
+// Key of candidate community c for vertex v. The randomized refinement
+// (asynchronous mode) replaces the gain key > 0 of an isolated vertex (whose
+// staying key is 0) by 1 / (1 - ln(U) / key), U uniform in (0, 1) from the
+// vertex, the community and the sweep: the largest of these keys is a draw
+// with probability proportional to the gain (Efraimidis and Spirakis'
+// weighted sampling, in an order-preserving form), and it stays positive, so
+// the vertex moves exactly when some gain is positive.
+template <class P, class W, bool REFINE>
+__device__ __forceinline__ typename P::acc cand_key(const SV<P, W> &a, const Sums<P> &sm, int32_t v, int32_t c,
+                                                    typename P::acc kk) {
+    if (!REFINE || P::det || !a.rand_refine) return kk;
+    if (!(kk > 0)) return AccLimits<typename P::acc>::lowest();
+    const uint64_t h = splitmix64_at(a.rseed + 0xD1B54A32D192ED03ULL * (uint64_t)sm.stamp,
+                                     ((uint64_t)(uint32_t)v << 32) | (uint32_t)c);
+    const float u = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
+    return (typename P::acc)(1.0f / (1.0f - logf(u) / (float)kk));
+}
+
 // act[k] = stamp, written only when it differs (a step's mark is read by
 // many threads and written about once)
 __device__ __forceinline__ void mark_step(int32_t *act, int32_t k, int32_t stamp) {
@@ -359,7 +386,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
                 kvd = wt[k];
                 continue;
             }
-            const A kk = move_key(ks, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma);
+            const A kk = cand_key<P, W, REFINE>(a, sm, v, c[k], move_key(ks, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma));
             if (better(kk, c[k], key, cand)) {
                 key = kk;
                 cand = c[k];
@@ -439,7 +466,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
         int32_t cand = INT_MAX;
         const A ks = kscale_of<B>(a, gv);
         if (lead && c != d) {
-            key = move_key(ks, sum, Kv, ldm(&a.Sig[c]), a.gamma);
+            key = cand_key<P, W, REFINE>(a, sm, v, c, move_key(ks, sum, Kv, ldm(&a.Sig[c]), a.gamma));
             cand = c;
         }
 #pragma unroll
@@ -524,7 +551,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma);
+            const A kk = cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma));
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -624,7 +651,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
                 kvd = sum;
                 continue;
             }
-            const A kk = move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma);
+            const A kk = cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma));
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
@@ -848,7 +875,8 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                     } else {
                         const int32_t v = __ldg(&a.hubs[j]);
                         const int32_t gv = graph_of<B>(a, v);
-                        enc = key_order(move_key(kscale_of<B>(a, gv), sum, a.K[v], ldm(&a.Sig[k]), a.gamma));
+                        enc = key_order(cand_key<P, W, REFINE>(
+                            a, sm, v, k, move_key(kscale_of<B>(a, gv), sum, a.K[v], ldm(&a.Sig[k]), a.gamma)));
                         if (!P::det) enc = (enc << 32) | (unsigned long long)(~(uint32_t)k);
                         if (pass == 0) pc.v[3]++;
                     }
@@ -1164,6 +1192,7 @@ template <class P, class W> __device__ __forceinline__ Sums<P> scalar_sums(const
     Sums<P> sm;
     sm.dq = a.dq_acc;
     sm.mv = a.moved;
+    sm.stamp = a.sweep + 1;
     return sm;
 }
 template <class P, class W, bool REFINE>

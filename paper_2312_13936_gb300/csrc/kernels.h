@@ -83,6 +83,9 @@ struct SweepCtx {
     // htoff, heoff (+1); hinfo: 3 words
     bool grid_hubs = false;
     int32_t *act = nullptr;  // persistent sweep: per-step marks (1024 entries; null: no step skipped)
+    bool rand_refine = false;  // randomized refinement (asynchronous mode)
+    uint64_t rseed = 0;        // its draws: seed + 0xD1B54A32D192ED03 * 64 * pass
+    int32_t sweep = 0;         // sweep index of a per-step launch
     const int32_t *hubs = nullptr;
     int32_t *hj = nullptr;
     int64_t *htoff = nullptr, *heoff = nullptr, *hinfo = nullptr;

@@ -28,6 +28,10 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
         set_last_error("invalid server capacity or leiden_params");
         return LEIDEN_ERR_INVALID;
     }
+    if (prm.mode == LEIDEN_DETERMINISTIC && (prm.flags & LEIDEN_FLAG_RANDOM_REFINE)) {
+        set_last_error("the randomized refinement has no deterministic mode");
+        return LEIDEN_ERR_UNSUPPORTED;
+    }
     if (prm.mode == LEIDEN_DETERMINISTIC && prm.resolution != 1.0) {
         set_last_error("deterministic mode needs resolution 1");
         return LEIDEN_ERR_UNSUPPORTED;

@@ -320,3 +320,33 @@ def test_louvain_deterministic_disconnected_counts():
         idx = torch.from_numpy(g.indices).cuda()
         m = torch.from_numpy(memb).cuda()
         assert lg.disconnected(off, idx, m) == oracle.disconnected(g, memb)[0]
+
+
+# ------------------------------------------- randomized refinement (V3)
+@pytest.mark.parametrize("name", ["sbm_workload", "road_1000", "gnp_weighted"])
+def test_random_refinement_async(name):
+    """Asynchronous randomized refinement: modularity within 0.005 of the
+    oracle's sequential randomized run (SEQ with V3), every community
+    connected, the reported modularity equal to the recomputation."""
+    g = ASYNC_GRAPHS[name]()
+    seq = oracle.leiden(g, mode=oracle.SEQ, flags=oracle.RANDOM_REFINE)
+    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC, flags=lg.FLAG_RANDOM_REFINE)
+    assert q >= seq.modularity - Q_TOL_ASYNC, (q, seq.modularity)
+    assert oracle.disconnected(g, memb)[0] == 0
+    q_re = oracle.modularity(g, memb)
+    assert abs(q - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re))
+
+
+def test_random_refinement_draws_and_refusals():
+    g = gen.road(300)
+    greedy = run_gpu(g, lg.LEIDEN_ASYNC)[0]
+    a = run_gpu(g, lg.LEIDEN_ASYNC, flags=lg.FLAG_RANDOM_REFINE, seed=1)[0]
+    b = run_gpu(g, lg.LEIDEN_ASYNC, flags=lg.FLAG_RANDOM_REFINE, seed=2)[0]
+    assert not np.array_equal(a, greedy)  # the draws change the refinement
+    assert not np.array_equal(a, b)       # and follow the seed
+    # per-step launches draw from the same counters
+    c = run_gpu(g, lg.LEIDEN_ASYNC, flags=lg.FLAG_RANDOM_REFINE | lg.FLAG_STEP_LAUNCHES, seed=1)[0]
+    assert oracle.disconnected(g, c)[0] == 0
+    with pytest.raises(lg.LeidenError) as e:
+        run_gpu(g, lg.LEIDEN_DETERMINISTIC, flags=lg.FLAG_RANDOM_REFINE)
+    assert e.value.status == -6
