@@ -291,6 +291,26 @@ leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *offsets, const
                                         const float *weights, const int32_t *membership, double gamma, void *stream,
                                         double *q_out);
 
+/* Edge list to symmetric CSR on the GPU: the input preparation of the
+ * paper's experiments (edges undirected, reverse edges added, weight 1 by
+ * default; Section 5.1 and Table 2, |E| counting both directions). The n
+ * vertices are 0..n-1; edge e is (src[e], dst[e]) with weight w[e] (w NULL:
+ * 1.0), m edges in host (where = LEIDEN_HOST) or device memory (LEIDEN_DEVICE,
+ * on stream). An edge u != v gives the entries (u, v) and (v, u); a
+ * self-loop gives the single entry (u, u) (one CSR entry, counted once in K
+ * and 2m), or none when drop_self_loops != 0. Entries with the same
+ * (row, target) are merged: weights summed (combine = 0) or the largest
+ * kept (combine = 1). Rows list their targets in ascending order.
+ * Outputs, in the same kind of memory as the input: offsets[n+1], and
+ * indices/weights with room for *nnz entries as passed in (2m always
+ * suffices); *nnz receives the entry count. Returns LEIDEN_ERR_INVALID for an
+ * endpoint outside [0, n), a negative or non-finite weight, more than 2^30
+ * edges, or too small a capacity (*nnz then holds the count needed); scratch
+ * is allocated and freed on stream. */
+leiden_status leiden_csr_from_edges(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w,
+                                    int32_t where, int32_t drop_self_loops, int32_t combine, int64_t *offsets,
+                                    int32_t *indices, float *weights, int64_t *nnz, void *stream);
+
 /* Per-pass trace of the last leiden_run made with LEIDEN_FLAG_TRACE. what:
  * 1 C' at the start of local-moving (int32[n']), 2 C' after local-moving
  * (int32[n']), 3 C' after refinement (int32[n']), 4 counts (int64[4]: n',

@@ -232,3 +232,33 @@ def schedule(n, off, deg, idx, state: int, layers: int = 1000, buckets: int = 16
     if used < 0:
         raise ValueError("schedule failed")
     return out[:n], int(used)
+
+
+def csr_from_edges(n: int, src, dst, weights=None, drop_self_loops: bool = False, combine: str = "sum"):
+    """Symmetric CSR of an undirected edge list, by its definition (the input
+    preparation of Section 5.1 and Table 2): every edge u != v gives the
+    entries (u, v) and (v, u), a self-loop one entry (u, u) or none when
+    dropped; entries with the same (row, target) merged by summing their
+    weights (or keeping the largest); rows in ascending target order.
+    Returns (offsets int64[n+1], indices int32, weights float32), the weights
+    summed in fp64 and then rounded once."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    w = np.ones(src.size) if weights is None else np.asarray(weights, dtype=np.float64)
+    keep = ~(src == dst) if drop_self_loops else np.ones(src.size, bool)
+    back = src != dst
+    rows = np.concatenate([src[keep], dst[back]])
+    cols = np.concatenate([dst[keep], src[back]])
+    ws = np.concatenate([w[keep], w[back]])
+    key = rows * max(n, 1) + cols
+    uniq, inv = np.unique(key, return_inverse=True)
+    merged = np.zeros(uniq.size)
+    if combine == "sum":
+        np.add.at(merged, inv, ws)
+    else:
+        merged[:] = -np.inf
+        np.maximum.at(merged, inv, ws)
+    r = uniq // max(n, 1)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(off, r + 1, 1)
+    return np.cumsum(off), (uniq % max(n, 1)).astype(np.int32), merged.astype(np.float32)

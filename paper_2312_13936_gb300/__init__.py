@@ -26,7 +26,8 @@ __all__ = [
     "leiden_status_string", "leiden_last_error", "Leiden", "modularity", "leiden_batch_create",
     "leiden_batch_run", "leiden_batch_info", "LeidenBatch", "pack_batch", "ServerState", "leiden_server_create",
     "leiden_server_submit", "leiden_server_step", "leiden_server_next", "leiden_server_result", "leiden_server_info",
-    "leiden_server_destroy", "LeidenServer", "leiden_disconnected", "disconnected",
+    "leiden_server_destroy", "LeidenServer", "leiden_disconnected", "disconnected", "leiden_csr_from_edges",
+    "csr_from_edges",
 ]
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
@@ -121,6 +122,8 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.leiden_server_info.argtypes = [_VP, ctypes.POINTER(ServerState)]
         lib.leiden_server_destroy.argtypes = [_VP]
         lib.leiden_disconnected.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.POINTER(_I64)]
+        lib.leiden_csr_from_edges.argtypes = [_I64, _I64, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, _VP, _VP, _VP, ctypes.POINTER(_I64), _VP]
         for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
                   lib.leiden_trace_get, lib.leiden_profile_get, lib.leiden_batch_create, lib.leiden_batch_run,
                   lib.leiden_batch_info, lib.leiden_server_create, lib.leiden_server_submit, lib.leiden_server_step,
@@ -260,6 +263,15 @@ def leiden_disconnected(n, offsets_ptr, indices_ptr, membership_ptr, stream) -> 
     c = _I64(0)
     _check(library().leiden_disconnected(n, offsets_ptr, indices_ptr, membership_ptr, stream, ctypes.byref(c)))
     return c.value
+
+
+def leiden_csr_from_edges(n, m, src_ptr, dst_ptr, w_ptr, where, drop_self_loops, combine, offsets_ptr, indices_ptr,
+                          weights_ptr, capacity, stream) -> int:
+    """Edge list to symmetric CSR (see include/leiden.h); returns the entry count."""
+    nnz = _I64(capacity)
+    _check(library().leiden_csr_from_edges(n, m, src_ptr, dst_ptr, w_ptr, where, drop_self_loops, combine, offsets_ptr,
+                                           indices_ptr, weights_ptr, ctypes.byref(nnz), stream))
+    return nnz.value
 
 
 def leiden_modularity_noalloc(n, offsets_ptr, indices_ptr, weights_ptr, membership_ptr, gamma, stream) -> float:
@@ -499,6 +511,25 @@ class LeidenServer:
             self.close()
         except Exception:
             pass
+
+
+def csr_from_edges(n: int, src, dst, weights=None, drop_self_loops: bool = False, combine: str = "sum",
+                   stream=None):
+    """Symmetric CSR (offsets int64[n+1], indices int32, weights float32, as
+    CUDA tensors) of an undirected edge list held in CUDA tensors (src, dst
+    int32[m], weights float32[m] or None for unit weights), built on the GPU:
+    reverse entries added, duplicates merged (combine "sum" or "max"),
+    self-loops kept as one entry or dropped, rows sorted by target."""
+    import torch
+    m = int(src.numel())
+    dev = src.device
+    off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    idx = torch.empty(max(2 * m, 1), dtype=torch.int32, device=dev)
+    w = torch.empty(max(2 * m, 1), dtype=torch.float32, device=dev)
+    nnz = leiden_csr_from_edges(n, m, _ptr(src), _ptr(dst), _ptr(weights) if weights is not None else None,
+                                LEIDEN_DEVICE, 1 if drop_self_loops else 0, 0 if combine == "sum" else 1, _ptr(off),
+                                _ptr(idx), _ptr(w), 2 * m, _stream_ptr(stream))
+    return off, idx[:nnz], w[:nnz]
 
 
 def disconnected(offsets, indices, membership, stream=None) -> int:

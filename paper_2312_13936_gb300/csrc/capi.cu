@@ -229,6 +229,13 @@ leiden_status leiden_disconnected(int64_t n, const int64_t *offsets, const int32
     return lgb::disconnected_device(n, offsets, indices, membership, static_cast<cudaStream_t>(stream), count);
 }
 
+leiden_status leiden_csr_from_edges(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w,
+                                    int32_t where, int32_t drop_self_loops, int32_t combine, int64_t *offsets,
+                                    int32_t *indices, float *weights, int64_t *nnz, void *stream) {
+    return lgb::csr_from_edges(n, m, src, dst, w, where, drop_self_loops, combine, offsets, indices, weights, nnz,
+                               static_cast<cudaStream_t>(stream));
+}
+
 leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, void *dst, int64_t *count) {
     if (!g) {
         lgb::set_last_error("NULL handle");

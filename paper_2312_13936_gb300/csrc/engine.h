@@ -51,6 +51,9 @@ class Handle {
 
 leiden_status disconnected_device(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *memb,
                                   cudaStream_t s, int64_t *count);
+leiden_status csr_from_edges(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w, int where,
+                             int drop_self, int combine, int64_t *offsets, int32_t *indices, float *weights,
+                             int64_t *nnz_io, cudaStream_t s);
 leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                 const int32_t *memb, double gamma, cudaStream_t s, double *q_out);
 

@@ -587,3 +587,21 @@ def test_random_refinement_keeps_the_leiden_guarantees():
     assert np.array_equal(res.membership, np.repeat(np.arange(16), 5))
     # SYNC mode has no randomized variant
     assert oracle.leiden(gen.road(10), mode=oracle.SYNC, flags=oracle.RANDOM_REFINE).status == oracle.ERR_UNSUPPORTED
+
+
+def test_golden_edges_to_csr():
+    """The edge-list to CSR definition on a hand-derived example."""
+    d = _golden("edges_to_csr.json")
+    e = np.array(d["edges"])
+    u, v, w = e[:, 0].astype(int), e[:, 1].astype(int), e[:, 2]
+    for name, kw in (("sum", {}), ("max", {"combine": "max"}), ("sum_drop_self", {"drop_self_loops": True})):
+        off, idx, ww = oracle.csr_from_edges(d["n"], u, v, w, **kw)
+        assert off.tolist() == d[name]["offsets"], name
+        assert idx.tolist() == d[name]["indices"], name
+        assert ww.tolist() == d[name]["weights"], name
+    # a generated symmetric CSR comes back from its edges (u <= v) unchanged
+    g = gen.gnp(60, 0.1, seed=3, wmax=4)
+    rows = np.repeat(np.arange(g.n), np.diff(g.offsets))
+    up = rows <= g.indices
+    off, idx, ww = oracle.csr_from_edges(g.n, rows[up], g.indices[up], g.weights[up])
+    assert np.array_equal(off, g.offsets) and np.array_equal(idx, g.indices) and np.array_equal(ww, g.weights)
