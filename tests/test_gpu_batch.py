@@ -163,3 +163,23 @@ def test_batch_invalid_inputs():
         assert e.value.status == -6
     finally:
         h.close()
+
+
+def mixed_layer_caps():
+    """Graphs with rows longer than 2048 (layer cap 1000 by reading S0) next
+    to graphs without (cap 32)."""
+    from tests.test_gpu_parity import hub_graph
+    return [gen.sbm(3000, 12, 0.04, 0.002, seed=4), hub_graph(), gen.ring_of_cliques(5, 8),
+            gen.rmat(12, 56, seed=2), gen.road(40)]
+
+
+def test_batch_mixed_layer_caps_equal_single_runs():
+    graphs = mixed_layer_caps()
+    assert max(np.diff(g.offsets).max() for g in graphs) > 2048 >= min(np.diff(g.offsets).max() for g in graphs)
+    vseg, memb, q, st, passes, comm = run_batch(graphs, lg.LEIDEN_DETERMINISTIC)
+    for g, G in enumerate(graphs):
+        ms, qs, sts, _ = run_gpu(G, lg.LEIDEN_DETERMINISTIC)
+        assert np.array_equal(memb[vseg[g]:vseg[g + 1]], ms), g
+        assert passes[g] == sts.passes, g
+        ref = oracle.leiden(G, mode=oracle.SYNC)
+        assert np.array_equal(ms, ref.membership), g

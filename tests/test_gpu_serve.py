@@ -162,3 +162,15 @@ def test_serve_rejects_bad_graphs():
         assert srv.info()["device_bytes"] == 0
     finally:
         srv.close()
+
+
+def test_serve_mixed_layer_caps_same_alone_and_in_mix():
+    """Graphs of layer cap 1000 and 32 (reading S0) in flight together: each
+    equals its single run bit for bit."""
+    from tests.test_gpu_batch import mixed_layer_caps
+    graphs = mixed_layer_caps()
+    out, info, _ = serve(graphs, lg.LEIDEN_DETERMINISTIC, arrivals_per_step=2)
+    for g, (G, (memb, q, passes, comm)) in enumerate(zip(graphs, out)):
+        ms, qs, sts, _ = run_gpu(G, lg.LEIDEN_DETERMINISTIC)
+        assert np.array_equal(memb, ms), g
+        assert passes == sts.passes, g
