@@ -210,6 +210,31 @@ def traffic_for(cls_name, workload_name):
         return None
 
 
+def shard_range(G, rank, world):
+    """The contiguous share of G graphs of a rank (shares differ by at most one)."""
+    return rank * G // world, (rank + 1) * G // world
+
+
+def shard_batch(b, lo, hi):
+    """Graphs [lo, hi) of a packed batch as a packed batch of their own
+    (vertex segments, offsets, local indices, weights)."""
+    v0, v1 = int(b.vseg[lo]), int(b.vseg[hi])
+    e0, e1 = int(b.offsets[v0]), int(b.offsets[v1])
+    return b.vseg[lo:hi + 1] - v0, b.offsets[v0:v1 + 1] - e0, b.indices[e0:e1], b.weights[e0:e1]
+
+
+def reduce_stats(stats, nmax, world):
+    """All-reduce a 1-D tensor over the ranks: its first nmax entries (times)
+    take the maximum over ranks, the others the sum. No collective for one rank."""
+    if world > 1:
+        import torch.distributed as dist
+        mx = stats[:nmax].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(stats, op=dist.ReduceOp.SUM)
+        stats[:nmax] = mx
+    return stats
+
+
 def batched_form(args, rank, world, mode, flags):
     """graphs/s of one leiden_batch_run over this rank's share of the batch,
     and of a per-graph loop of plain leiden_run calls on a sample of it."""
@@ -221,12 +246,8 @@ def batched_form(args, rank, world, mode, flags):
     import paper_2312_13936_gb300 as lg
     b = gen.sbm_batch(args.batch_graphs, seed=4)
     G = b.num_graphs
-    lo, hi = rank * G // world, (rank + 1) * G // world
-    v0, v1 = int(b.vseg[lo]), int(b.vseg[hi])
-    e0, e1 = int(b.offsets[v0]), int(b.offsets[v1])
-    vseg = b.vseg[lo:hi + 1] - v0
-    off = b.offsets[v0:v1 + 1] - e0
-    h = lg.LeidenBatch(vseg, off, b.indices[e0:e1], b.weights[e0:e1])
+    lo, hi = shard_range(G, rank, world)
+    h = lg.LeidenBatch(*shard_batch(b, lo, hi))
     h.run(mode=mode, flags=flags)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
@@ -263,12 +284,7 @@ def batched_form(args, rank, world, mode, flags):
         hh.close()
     stats = torch.tensor([ms, tl / S, float(q.sum()), float(len(q)), float(np.sum(ql)), float(np.sum(q[pick])),
                           float(S)], dtype=torch.float64, device=dev)
-    if world > 1:
-        mx = stats[:2].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(stats, op=dist.ReduceOp.SUM)
-        stats[:2] = mx
-    ms, per_graph_s, qsum, qn, qls, qbs, ns = stats.tolist()
+    ms, per_graph_s, qsum, qn, qls, qbs, ns = reduce_stats(stats, 2, world).tolist()
     return {
         "workload": (f"{G} SBM graphs, vertices log-uniform in [100, 100000], 4-64 blocks, mean degree 8-32, "
                      f"p_out/p_in 0.02, unit weights, seed 4; one segmented CSR per rank"),
@@ -518,10 +534,8 @@ def main():
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(reduce_stats(torch.tensor([ms], device=dev), 1, world).item())
         dist.barrier()
-        ms = float(t.item())
     value = world * args.steps * g.nnz / (ms / 1e3)
     # every community connected? (Algorithm 5 on the GPU, outside the timed region)
     disconnected = lg.disconnected(off, idx, memb)
@@ -553,9 +567,7 @@ def main():
             one()
         te = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+            te = float(reduce_stats(torch.tensor([te], device=dev), 1, world).item())
         e2e = {"value": world * ne * g.nnz / te, "unit": "edges/s",
                "h2d_bytes_per_step": hoff.nbytes + hidx.nbytes + hw.nbytes, "d2h_bytes_per_step": out.nbytes + 8}
 
