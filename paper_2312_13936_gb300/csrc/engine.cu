@@ -253,7 +253,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     sc.grid_hubs = grid_hubs;
     sc.hubs = q.hubs;
     sc.hj = q.hj;
-    sc.hinfo = q.hbase;
+    sc.hinfo = q.hinfo;
     sc.htoff = q.htoff;
     sc.heoff = q.heoff;
     sc.hd = q.hd;
@@ -682,8 +682,6 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     r.batch = batch;
     r.L = L;
     r.B = B;
-    r.nsteps = nsteps;
-    r.nkeys = nkeys;
     r.NG = NG;
     if (batch) {  // per-graph caps (all L when schedule_layers is given)
         if (hgL.empty()) hgL.assign((size_t)NG, L);

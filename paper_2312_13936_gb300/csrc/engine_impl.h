@@ -66,7 +66,7 @@ using namespace detail;
 struct Run {
     const leiden_params *prm = nullptr;
     bool det = false, trace = false, profile = false, batch = false;
-    int32_t L = 0, B = 0, nsteps = 0, nkeys = 0, NG = 1;
+    int32_t L = 0, B = 0, NG = 1;  // L: the largest layer cap of the run's graphs
     leiden_stats st{};
     std::vector<std::pair<cudaEvent_t, int>> marks;  // phase boundary events (phase id of the span that starts)
     GraphView G;                  // current graph G'
@@ -430,13 +430,13 @@ struct Handle::Impl {
     }
     // whole-grid bin 6 of the persistent sweep: per-hub arrays of a pass
     int32_t *hubs = nullptr, *hd = nullptr, *hcand = nullptr, *hmv = nullptr, *hj = nullptr;
-    int64_t *htoff = nullptr, *heoff = nullptr, *hbase = nullptr;
+    int64_t *htoff = nullptr, *heoff = nullptr, *hinfo = nullptr;
     unsigned long long *hkey = nullptr, *hspan = nullptr;
     long long *hkvd = nullptr;
     int64_t hubs_cap = -1;
     leiden_status ensure_hubs(int64_t nh) {
-        if (!hbase) {
-            ST(alloc(&hbase, 4));  // a step's eligible hubs, table slots, entries
+        if (!hinfo) {
+            ST(alloc(&hinfo, 4));  // a step's eligible hubs, table slots, entries
             ST(alloc(&hspan, 1));
         }
         if (nh <= hubs_cap) return LEIDEN_OK;

@@ -307,8 +307,6 @@ leiden_status Handle::server_step(int32_t *finished_out) {
     r.L = Lmax;
     r.gL = v.gL;
     r.B = prm.schedule_buckets;
-    r.nsteps = r.L - 1 + r.B;
-    r.nkeys = r.nsteps * kNumBins;
     r.NG = K;
     const Impl::Agg &u = q.agg[v.cur];
     r.G.n = v.n_union;
