@@ -210,6 +210,34 @@ def traffic_for(cls_name, workload_name):
         return None
 
 
+def phase_roofline(prof, peak, step_ms):
+    """HBM roofline per phase and overall from a profiled run.
+
+    prof maps (phase, bin) to {"launches", "ms", "bytes"}: the algorithmic
+    bytes of the sweep and aggregation launches and their CUDA-event time.
+    A phase's achieved bandwidth is its bytes over its launches' time. Overall
+    is the same over all profiled launches ("profiled"), and the same bytes
+    over the whole step ("step"), whose time also holds the schedule, setup
+    and modularity kernels that count no bytes: a lower bound."""
+    by_phase = {}
+    for (phase, _), a in prof.items():
+        e = by_phase.setdefault(phase, {"bytes": 0.0, "ms": 0.0, "launches": 0})
+        e["bytes"] += a["bytes"]
+        e["ms"] += a["ms"]
+        e["launches"] += a["launches"]
+    for e in by_phase.values():
+        e["achieved"] = e["bytes"] / (e["ms"] / 1e3) / 1e9 if e["ms"] > 0 else 0.0
+        e["frac"] = e["achieved"] / peak
+    tb = sum(e["bytes"] for e in by_phase.values())
+    tms = sum(e["ms"] for e in by_phase.values())
+    over = {"bytes": tb, "profiled_ms": tms, "step_ms": step_ms}
+    over["achieved_profiled"] = tb / (tms / 1e3) / 1e9 if tms > 0 else 0.0
+    over["frac_profiled"] = over["achieved_profiled"] / peak
+    over["achieved_step"] = tb / (step_ms / 1e3) / 1e9 if step_ms > 0 else 0.0
+    over["frac_step"] = over["achieved_step"] / peak
+    return by_phase, over
+
+
 def shard_range(G, rank, world):
     """The contiguous share of G graphs of a rank (shares differ by at most one)."""
     return rank * G // world, (rank + 1) * G // world
@@ -591,6 +619,7 @@ def main():
                     "traffic": traffic, "kernel": cls, "peak_source": f"{peak_kind} hbm_gbs",
                     "bytes_per_launch": a["bytes"] / a["launches"], "ms_per_launch": a["ms"] / a["launches"],
                     "share_of_profiled_ms": a["ms"] / total_ms}
+        roofline["by_phase"], roofline["overall"] = phase_roofline(prof, peak, ms / args.steps)
     cpu = None if (args.no_cpu or world > 1) else cpu_baseline(args.cpu_side)
     served = None if (args.no_serve or world > 1) else served_form(args, mode, base_flags)
     line = {
