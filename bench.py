@@ -238,17 +238,51 @@ def phase_roofline(prof, peak, step_ms):
     return by_phase, over
 
 
-def shard_range(G, rank, world):
-    """The contiguous share of G graphs of a rank (shares differ by at most one)."""
-    return rank * G // world, (rank + 1) * G // world
+def lpt_shares(m, world):
+    """Graph ids of each rank: longest-processing-time-first by entry count.
+
+    Graphs in decreasing m (ties by smaller id) go one by one to the rank with
+    the least load so far (ties by smaller rank). Each rank's ids come back in
+    increasing order. The largest load is at most 4/3 of the best possible
+    one (Graham's LPT bound) and at most the mean load plus the largest m."""
+    import heapq
+
+    import numpy as np
+    m = np.asarray(m, dtype=np.int64)
+    order = np.lexsort((np.arange(len(m)), -m))
+    heap = [(0, r) for r in range(world)]
+    shares = [[] for _ in range(world)]
+    for g in order:
+        load, r = heapq.heappop(heap)
+        shares[r].append(int(g))
+        heapq.heappush(heap, (load + int(m[g]), r))
+    return [np.array(sorted(x), dtype=np.int64) for x in shares]
 
 
-def shard_batch(b, lo, hi):
-    """Graphs [lo, hi) of a packed batch as a packed batch of their own
-    (vertex segments, offsets, local indices, weights)."""
-    v0, v1 = int(b.vseg[lo]), int(b.vseg[hi])
-    e0, e1 = int(b.offsets[v0]), int(b.offsets[v1])
-    return b.vseg[lo:hi + 1] - v0, b.offsets[v0:v1 + 1] - e0, b.indices[e0:e1], b.weights[e0:e1]
+def graph_entries(b):
+    """Directed CSR entries of every graph of a packed batch."""
+    return b.offsets[b.vseg[1:]] - b.offsets[b.vseg[:-1]]
+
+
+def pack_graphs(b, ids):
+    """The graphs ids (increasing) of a packed batch as a packed batch of their
+    own: vertex segments, offsets, local indices, weights."""
+    import numpy as np
+    ids = np.asarray(ids, dtype=np.int64)
+    nv = b.vseg[ids + 1] - b.vseg[ids]
+    vseg = np.zeros(len(ids) + 1, dtype=np.int64)
+    np.cumsum(nv, out=vseg[1:])
+    offs, idxs, ws = [np.zeros(1, dtype=np.int64)], [], []
+    base = 0
+    for g in ids:
+        v0, v1 = int(b.vseg[g]), int(b.vseg[g + 1])
+        e0, e1 = int(b.offsets[v0]), int(b.offsets[v1])
+        offs.append(b.offsets[v0 + 1:v1 + 1] - e0 + base)
+        idxs.append(b.indices[e0:e1])  # local to their graph already
+        ws.append(b.weights[e0:e1])
+        base += e1 - e0
+    cat = (lambda xs, dt: np.concatenate(xs).astype(dt, copy=False) if xs else np.zeros(0, dtype=dt))
+    return vseg, cat(offs, np.int64), cat(idxs, b.indices.dtype), cat(ws, b.weights.dtype)
 
 
 def reduce_stats(stats, nmax, world):
@@ -274,8 +308,8 @@ def batched_form(args, rank, world, mode, flags):
     import paper_2312_13936_gb300 as lg
     b = gen.sbm_batch(args.batch_graphs, seed=4)
     G = b.num_graphs
-    lo, hi = shard_range(G, rank, world)
-    h = lg.LeidenBatch(*shard_batch(b, lo, hi))
+    ids = lpt_shares(graph_entries(b), world)[rank]
+    h = lg.LeidenBatch(*pack_graphs(b, ids))
     h.run(mode=mode, flags=flags)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
@@ -293,12 +327,12 @@ def batched_form(args, rank, world, mode, flags):
     passes, comm = h.info()
     h.close()
     # per-graph loop of plain launches on a sample of the same graphs
-    S = max(1, min(args.batch_sample, hi - lo))
-    pick = np.linspace(0, hi - lo - 1, S).astype(int)
+    S = max(1, min(args.batch_sample, len(ids)))
+    pick = np.linspace(0, len(ids) - 1, S).astype(int)
     dev = torch.device("cuda", torch.cuda.current_device())
     hs = []
     for k in pick:
-        gk = b.graph(lo + int(k))
+        gk = b.graph(int(ids[k]))
         hs.append(lg.Leiden(torch.as_tensor(gk.offsets).to(dev), torch.as_tensor(gk.indices).to(dev),
                             torch.as_tensor(gk.weights).to(dev)))
     for hh in hs[:4]:
@@ -315,7 +349,8 @@ def batched_form(args, rank, world, mode, flags):
     ms, per_graph_s, qsum, qn, qls, qbs, ns = reduce_stats(stats, 2, world).tolist()
     return {
         "workload": (f"{G} SBM graphs, vertices log-uniform in [100, 100000], 4-64 blocks, mean degree 8-32, "
-                     f"p_out/p_in 0.02, unit weights, seed 4; one segmented CSR per rank"),
+                     f"p_out/p_in 0.02, unit weights, seed 4; one segmented CSR per rank, "
+                     f"graphs dealt to ranks longest-first by entries"),
         "graphs": G, "vertices": b.n, "entries": b.nnz, "mode": "async" if mode == lg.LEIDEN_ASYNC else "det",
         "graphs_per_s": G / (ms / 1e3), "ms_per_batch": ms, "edges_per_s": b.nnz / (ms / 1e3),
         "steps": args.batch_steps, "union_passes_rank0": st.passes, "max_graph_passes_rank0": int(passes.max()),

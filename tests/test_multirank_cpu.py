@@ -1,8 +1,9 @@
 """The multi-rank host logic of bench.py on CPU: two processes over the gloo
-backend (127.0.0.1). The batched form's graphs are split in contiguous
-shares that cover the batch exactly once; per-rank sums add up and per-rank
-times reduce to the largest, as they do over NCCL on GPUs; each rank's work
-here is the oracle on its share."""
+backend (127.0.0.1). The batched form's graphs are dealt to ranks
+longest-first by entry count, in shares that cover the batch exactly once;
+per-rank sums add up and per-rank times reduce to the largest, as they do
+over NCCL on GPUs; each rank's work here is the oracle on its share."""
+import itertools
 import os
 import socket
 
@@ -31,17 +32,17 @@ def _rank(rank, world, port, out):
         import gen
         import oracle
         b = gen.sbm_batch(9, seed=3, nmin=50, nmax=600)
-        lo, hi = bench.shard_range(b.num_graphs, rank, world)
-        vseg, off, idx, w = bench.shard_batch(b, lo, hi)
+        ids = bench.lpt_shares(bench.graph_entries(b), world)[rank]
+        vseg, off, idx, w = bench.pack_graphs(b, ids)
         q = []
-        for g in range(hi - lo):
+        for g in range(len(ids)):
             a, c = int(vseg[g]), int(vseg[g + 1])
             e0, e1 = int(off[a]), int(off[c])
             G = gen.CSR(c - a, off[a:c + 1] - e0, idx[e0:e1].copy(), w[e0:e1].copy())
             q.append(oracle.leiden(G, mode=oracle.SEQ).modularity)
         stats = torch.tensor([float(rank + 1), float(np.sum(q)), float(len(q))], dtype=torch.float64)
         red = bench.reduce_stats(stats, 1, world)
-        out.put((rank, lo, hi, red.tolist()))
+        out.put((rank, ids.tolist(), red.tolist()))
     finally:
         dist.destroy_process_group()
 
@@ -64,11 +65,11 @@ def test_two_ranks_shard_and_reduce():
     import gen
     import oracle
     b = gen.sbm_batch(9, seed=3, nmin=50, nmax=600)
-    # the shares are contiguous, disjoint and cover every graph once
-    assert res[0][1] == 0 and res[0][2] == res[1][1] and res[1][2] == b.num_graphs
+    # the shares are disjoint and cover every graph once
+    assert sorted(res[0][1] + res[1][1]) == list(range(b.num_graphs))
     # every rank holds the same reduced stats: the largest time, the sums
-    assert res[0][3] == res[1][3]
-    t, qsum, count = res[0][3]
+    assert res[0][2] == res[1][2]
+    t, qsum, count = res[0][2]
     assert t == float(world)
     assert count == b.num_graphs
     ref = sum(oracle.leiden(b.graph(g), mode=oracle.SEQ).modularity for g in range(b.num_graphs))
@@ -81,5 +82,61 @@ def test_one_rank_needs_no_collective():
     import bench
     s = torch.tensor([3.0, 4.0])
     assert bench.reduce_stats(s, 1, 1).tolist() == [3.0, 4.0]
-    assert bench.shard_range(10, 0, 1) == (0, 10)
-    assert [bench.shard_range(10, r, 3) for r in range(3)] == [(0, 3), (3, 6), (6, 10)]
+    (only,) = bench.lpt_shares([5, 1, 7], 1)
+    assert only.tolist() == [0, 1, 2]
+
+
+def test_lpt_shares_by_hand():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    # 7, 5, 4, 3, 3, 2 onto 2 ranks: 7->r0, 5->r1, 4->r1 (9), 3->r0 (10),
+    # 3->r1 (12), 2->r0 (12)
+    m = [3, 7, 2, 5, 4, 3]
+    r0, r1 = bench.lpt_shares(m, 2)
+    assert r0.tolist() == [0, 1, 2] and r1.tolist() == [3, 4, 5]
+    # more ranks than graphs: some shares are empty, none repeats a graph
+    sh = bench.lpt_shares([4, 4], 3)
+    assert [x.tolist() for x in sh] == [[0], [1], []]
+
+
+def test_lpt_within_graham_bound_of_brute_force():
+    """The largest load is at most 4/3 of the optimum, which brute force over
+    every assignment finds on tiny instances."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(11)
+    for _ in range(60):
+        n, world = int(rng.integers(1, 8)), int(rng.integers(2, 4))
+        m = rng.integers(1, 50, size=n)
+        sh = bench.lpt_shares(m, world)
+        assert sorted(np.concatenate(sh).tolist()) == list(range(n))
+        lpt = max(int(m[x].sum()) for x in sh)
+        best = min(max(sum(int(m[g]) for g in range(n) if a[g] == r) for r in range(world))
+                   for a in itertools.product(range(world), repeat=n))
+        assert lpt * 3 <= 4 * best
+        assert lpt <= m.sum() / world + m.max()
+
+
+def test_pack_graphs_round_trip():
+    """A packed share holds each chosen graph entry for entry."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import gen
+    b = gen.sbm_batch(7, seed=2, nmin=30, nmax=300)
+    ids = np.array([1, 4, 6])
+    vseg, off, idx, w = bench.pack_graphs(b, ids)
+    assert len(vseg) == 4 and off[-1] == len(idx) == len(w)
+    for k, g in enumerate(ids):
+        a, c = int(vseg[k]), int(vseg[k + 1])
+        e0, e1 = int(off[a]), int(off[c])
+        ref = b.graph(int(g))
+        assert c - a == ref.n
+        assert np.array_equal(off[a:c + 1] - e0, ref.offsets)
+        assert np.array_equal(idx[e0:e1], ref.indices)
+        assert np.array_equal(w[e0:e1], ref.weights)
+    assert np.array_equal(bench.graph_entries(b)[ids], np.diff(off[vseg]))
+    empty = bench.pack_graphs(b, np.zeros(0, dtype=np.int64))
+    assert empty[0].tolist() == [0] and empty[1].tolist() == [0] and len(empty[2]) == 0
