@@ -1,5 +1,5 @@
-"""Host arithmetic of bench.py's roofline on CPU: the per-phase and overall
-HBM fractions from a hand-made profile, whose numbers are checked by hand."""
+"""Host side of bench.py on CPU: the roofline arithmetic from a hand-made
+profile (numbers checked by hand) and the reference arm's JSON line."""
 import os
 import sys
 
@@ -38,3 +38,38 @@ def test_phase_roofline_empty_profile():
     by, over = bench.phase_roofline({}, 1000.0, 5.0)
     assert by == {}
     assert over["achieved_step"] == 0.0 and over["achieved_profiled"] == 0.0
+
+
+def _bench(args, env_extra=None):
+    import json
+    import subprocess
+    env = dict(os.environ, **(env_extra or {}))
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_line():
+    """The reference arm (the oracle on host cores) prints one JSON line with
+    the contract's keys, the same metric and unit as the GPU arm, and an e2e
+    that moves no bytes."""
+    (line,) = _bench(["--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-side", "60"])
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "edges/s"
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": "edges/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert 0.5 < line["config"]["modularity"] < 1.0
+
+
+def test_reference_arm_other_ranks_silent():
+    """Under torchrun only rank 0 runs the oracle; the others exit 0 quietly."""
+    assert _bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-side", "60"],
+                  {"RANK": "1", "WORLD_SIZE": "2"}) == []
