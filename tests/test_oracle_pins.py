@@ -304,6 +304,11 @@ def test_aggregation_invariants(seed):
         assert np.all(np.diff(row) > 0)
         W[c, row] = w2[off2[c]:off2[c] + deg2[c]]
     assert np.array_equal(W, W.T)
+    # closed form of Algorithm 4: W = S^T A S with S the n x |Gamma| indicator
+    # of the membership (integer weights, so the fp64 sums are exact)
+    S = np.zeros((g.n, ncomm))
+    S[np.arange(g.n), memb] = 1.0
+    assert np.array_equal(W, S.T @ dense(g) @ S)
     # Q(G'', L) == Q(G, L o memb) for any partition L of the super-vertices
     for _ in range(5):
         L = rng.integers(0, 3, ncomm).astype(np.int32)
