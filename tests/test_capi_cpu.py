@@ -41,3 +41,82 @@ def test_host_only_entry_points():
     assert lib.leiden_create(ctypes.byref(h), -1, 0, None, None, None, 0, 0, None) == -1
     assert lib.leiden_run(None, None, None, 0, None, None) == -1
     assert lib.leiden_destroy(None) == 0
+
+
+def test_argument_checks_before_device_work():
+    """Every entry point rejects malformed arguments on the host, before any
+    device call, with LEIDEN_ERR_INVALID and a one-line leiden_last_error;
+    empty inputs of the stateless entry points succeed without a device."""
+    import numpy as np
+    lib = lg.library(build_if_missing=True)
+    INV = -1
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    p = lg.leiden_params_default()
+    i64 = ctypes.c_int64()
+
+    def bad(rc):
+        assert rc == INV
+        assert lib.leiden_last_error()  # a description is left behind
+
+    # single graph: bad where, huge n, missing indices, host offsets that do not frame nnz
+    off = np.array([0, 1, 2], np.int64)
+    idx = np.array([1, 0], np.int32)
+    bad(lib.leiden_create(ctypes.byref(h), 2, 2, vp(off), vp(idx), None, 7, 0, None))
+    bad(lib.leiden_create(ctypes.byref(h), 1 << 31, 2, vp(off), vp(idx), None, 0, 0, None))
+    bad(lib.leiden_create(ctypes.byref(h), 2, 2, vp(off), None, None, 0, 0, None))
+    bad(lib.leiden_create(ctypes.byref(h), 2, 3, vp(off), vp(idx), None, 0, 0, None))
+    bad(lib.leiden_create(ctypes.byref(h), 2, 2, vp(np.array([1, 1, 2], np.int64)), vp(idx), None, 0, 0, None))
+    assert h.value is None
+    # batch: no graphs, vtx_seg not starting at 0 or decreasing, offsets not framing nnz
+    bad(lib.leiden_batch_create(ctypes.byref(h), 0, vp(np.array([0], np.int64)), 0, vp(off), None, None, 0, 0,
+                                None))
+    bad(lib.leiden_batch_create(ctypes.byref(h), 1, vp(np.array([1, 2], np.int64)), 2, vp(off), vp(idx), None,
+                                0, 0, None))
+    bad(lib.leiden_batch_create(ctypes.byref(h), 2, vp(np.array([0, 2, 1], np.int64)), 2, vp(off), vp(idx),
+                                None, 0, 0, None))
+    bad(lib.leiden_batch_create(ctypes.byref(h), 1, vp(np.array([0, 2], np.int64)), 1, vp(off), vp(idx), None,
+                                0, 0, None))
+    # handles that are NULL
+    bad(lib.leiden_batch_run(None, ctypes.byref(p), None, 0, None, None))
+    bad(lib.leiden_batch_info(None, None, None, None))
+    bad(lib.leiden_trace_get(None, 0, 0, None, ctypes.byref(i64)))
+    bad(lib.leiden_profile_get(None, None))
+    bad(lib.leiden_server_create(None, ctypes.byref(p), 10, 10, 1, 0, None))
+    bad(lib.leiden_server_create(ctypes.byref(h), None, 10, 10, 1, 0, None))
+    bad(lib.leiden_server_submit(None, 2, 2, vp(off), vp(idx), None, 0, ctypes.byref(i64)))
+    bad(lib.leiden_server_step(None, None))
+    bad(lib.leiden_server_next(None, ctypes.byref(i64)))
+    bad(lib.leiden_server_result(None, 0, None, 0, None, None, None))
+    bad(lib.leiden_server_info(None, None))
+    assert lib.leiden_server_destroy(None) == 0
+    # stateless entry points
+    q = ctypes.c_double(5.0)
+    bad(lib.leiden_modularity(-1, None, None, None, None, 1.0, None, ctypes.byref(q)))
+    bad(lib.leiden_modularity(2, vp(off), vp(idx), None, None, 1.0, None, ctypes.byref(q)))
+    bad(lib.leiden_modularity(2, vp(off), vp(idx), None, vp(idx), 1.0, None, None))
+    bad(lib.leiden_modularity_noalloc(-1, None, None, None, None, 1.0, None, ctypes.byref(q)))
+    bad(lib.leiden_modularity_noalloc(1 << 21, vp(off), vp(idx), None, vp(idx), 1.0, None, ctypes.byref(q)))
+    bad(lib.leiden_disconnected(-1, None, None, None, None, ctypes.byref(i64)))
+    bad(lib.leiden_disconnected(2, vp(off), None, vp(idx), None, ctypes.byref(i64)))
+    assert lib.leiden_modularity(0, None, None, None, None, 1.0, None, ctypes.byref(q)) == 0 and q.value == 0.0
+    q.value = 5.0
+    assert lib.leiden_modularity_noalloc(0, None, None, None, None, 1.0, None, ctypes.byref(q)) == 0
+    assert q.value == 0.0
+    i64.value = 9
+    assert lib.leiden_disconnected(0, None, None, None, None, ctypes.byref(i64)) == 0 and i64.value == 0
+    # edge list to CSR: negative n, more than 2^30 edges, unknown combine or where, no nnz slot
+    src = np.array([0], np.int32)
+    o3 = np.zeros(3, np.int64)
+    i64.value = 4
+    bad(lib.leiden_csr_from_edges(-1, 1, vp(src), vp(src), None, 0, 0, 0, vp(o3), None, None, ctypes.byref(i64),
+                                  None))
+    bad(lib.leiden_csr_from_edges(2, (1 << 30) + 1, vp(src), vp(src), None, 0, 0, 0, vp(o3), None, None,
+                                  ctypes.byref(i64), None))
+    bad(lib.leiden_csr_from_edges(2, 1, vp(src), vp(src), None, 0, 0, 2, vp(o3), None, None, ctypes.byref(i64),
+                                  None))
+    bad(lib.leiden_csr_from_edges(2, 1, vp(src), vp(src), None, 3, 0, 0, vp(o3), None, None, ctypes.byref(i64),
+                                  None))
+    bad(lib.leiden_csr_from_edges(2, 1, vp(src), vp(src), None, 0, 0, 0, vp(o3), None, None, None, None))
+    bad(lib.leiden_csr_from_edges(2, 1, None, vp(src), None, 0, 0, 0, vp(o3), None, None, ctypes.byref(i64),
+                                  None))
