@@ -765,6 +765,7 @@ int64_t og_delta_key(int64_t n, const int64_t *off, const int32_t *deg, const in
  * Returns the number of disconnected communities, or -1 on error.
  * --------------------------------------------------------------------- */
 int64_t og_disconnected(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *C, uint8_t *flags) {
+    if (n < 0) return -1;
     int64_t *S = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
     uint8_t *vis = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
     int32_t *queue = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));

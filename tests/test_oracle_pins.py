@@ -610,3 +610,72 @@ def test_golden_edges_to_csr():
     up = rows <= g.indices
     off, idx, ww = oracle.csr_from_edges(g.n, rows[up], g.indices[up], g.weights[up])
     assert np.array_equal(off, g.offsets) and np.array_equal(idx, g.indices) and np.array_equal(ww, g.weights)
+
+
+# ---------------------------------------------------- pass-loop controls (Algorithm 1)
+def _li(r):
+    """Local-moving sweeps of every pass (the trace's counts: n, l_i, l_j, |Gamma|)."""
+    return [int(r.trace[p][oracle.T_COUNTS][1]) for p in sorted(r.trace)]
+
+
+def test_threshold_scaling_divides_tau_between_passes():
+    """tau is divided by the drop factor after each pass: a factor below 1 makes
+    tau grow past any sweep's gain, so every pass after the first stops after
+    one sweep; kept constant or shrinking, the second pass sweeps several times.
+    The first pass, on tau0 alone, is the same in every run."""
+    g = gen.gnp(300, 0.03, seed=1, wmax=3)
+    grow = oracle.leiden(g, mode=oracle.SEQ, tolerance=1e-3, tolerance_drop=1e-6, trace=True)
+    same = oracle.leiden(g, mode=oracle.SEQ, tolerance=1e-3, tolerance_drop=1.0, trace=True)
+    shrink = oracle.leiden(g, mode=oracle.SEQ, tolerance=1e-3, tolerance_drop=1e6, trace=True)
+    assert grow.passes >= 2 and _li(grow)[0] > 1 and all(x == 1 for x in _li(grow)[1:])
+    assert _li(same)[1] > 1 and _li(shrink)[1] > 1
+    for r in (same, shrink):
+        assert np.array_equal(r.trace[0][oracle.T_MOVE], grow.trace[0][oracle.T_MOVE])
+
+
+def test_huge_tolerance_and_one_iteration_stop_after_one_sweep():
+    """A sweep's total gain never exceeds a tau of 1e9, and max_iterations = 1
+    allows one sweep: either way l_i = 1 in every pass, and the second also
+    caps the refinement at one sweep."""
+    g = gen.gnp(300, 0.03, seed=1, wmax=3)
+    huge = oracle.leiden(g, mode=oracle.SEQ, tolerance=1e9, trace=True)
+    assert all(x == 1 for x in _li(huge))
+    one = oracle.leiden(g, mode=oracle.SEQ, max_iterations=1, trace=True)
+    assert all(x == 1 for x in _li(one))
+    assert all(int(one.trace[p][oracle.T_COUNTS][2]) <= 1 for p in one.trace)
+
+
+def test_aggregation_tolerance_zero_stops_after_the_first_pass():
+    """With tau_agg = 0 any non-empty refined partition exceeds the ratio, so
+    the result is pass 0's refined partition in canonical labels."""
+    g = gen.gnp(300, 0.03, seed=1, wmax=3)
+    r = oracle.leiden(g, mode=oracle.SEQ, aggregation_tolerance=0.0, trace=True)
+    assert r.passes == 1
+    ref = r.trace[0][oracle.T_REFINE]
+    _, canon = np.unique(ref, return_index=True)
+    first = {c: k for k, c in enumerate(ref[np.sort(canon)])}
+    assert np.array_equal(r.membership, np.array([first[c] for c in ref], dtype=np.int32))
+
+
+def test_convergence_stop_without_the_ratio():
+    """Two disjoint triangles: pass 0 finds them; in pass 1 nobody moves and
+    the refinement keeps both super-vertices, so the loop stops there (R5)
+    even with tau_agg = 1, where the ratio test never fires."""
+    t = gen.from_edges(6, np.array([0, 1, 2, 3, 4, 5]), np.array([1, 2, 0, 4, 5, 3]))
+    r = oracle.leiden(t, mode=oracle.SEQ, aggregation_tolerance=1.0, max_passes=10, trace=True)
+    assert r.passes == 2 and _li(r) == [2, 1]
+    assert r.membership.tolist() == [0, 0, 0, 1, 1, 1] and r.modularity == 0.5
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.6])
+def test_zero_passes_leave_singletons(gamma):
+    """max_passes = 0 runs no pass: every vertex alone, whose Eq. 1 score is
+    trace(A)/2m - gamma * sum_i (K_i / 2m)^2 (self-loops included)."""
+    g = random_graph_with_loops(40, 0.12, 3, wmax=5)
+    r = oracle.leiden(g, mode=oracle.SEQ, max_passes=0, resolution=gamma)
+    assert r.passes == 0
+    assert np.array_equal(r.membership, np.arange(g.n))
+    A = dense(g)
+    two_m = A.sum()
+    q = np.trace(A) / two_m - gamma * np.sum((A.sum(axis=1) / two_m) ** 2)
+    assert abs(r.modularity - q) < 1e-12
