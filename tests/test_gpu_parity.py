@@ -109,7 +109,9 @@ def test_deterministic_schedule_parameters(L, B, seed):
 def test_deterministic_single_sweep_refinement_and_limits():
     g = gen.sbm(3000, 12, 0.04, 0.002, seed=4)
     for kw in ({"flags": lg.FLAG_REFINE_SINGLE_SWEEP}, {"max_passes": 1}, {"max_iterations": 2},
-               {"tolerance": 0.0, "max_iterations": 7}, {"aggregation_tolerance": 0.99}):
+               {"tolerance": 0.0, "max_iterations": 7}, {"aggregation_tolerance": 0.99},
+               {"max_passes": 0}, {"aggregation_tolerance": 0.0}, {"tolerance": 1e9},
+               {"tolerance": 1e-3, "tolerance_drop": 1e-6}, {"tolerance": 1e-3, "tolerance_drop": 1.0}):
         okw = dict(kw)
         if "flags" in okw:
             okw["flags"] = oracle.REFINE_SINGLE_SWEEP
