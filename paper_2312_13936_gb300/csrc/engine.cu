@@ -688,7 +688,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(cudaMemcpyAsync(q.gL, hgL.data(), sizeof(int32_t) * NG, cudaMemcpyHostToDevice, s));
         r.gL = q.gL;
     }
-    cudaEvent_t ev0, ev1;
+    cudaEvent_t &ev0 = r.ev0, &ev1 = r.ev1;  // destroyed with the run
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
     CK(cudaEventRecord(ev0, s));
@@ -813,9 +813,6 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         st.kernel_launches = q.launches;
         *stats = st;
     }
-    for (auto &m : marks) cudaEventDestroy(m.first);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     if (profile) ST(q.finish_profile());
     return LEIDEN_OK;
 }

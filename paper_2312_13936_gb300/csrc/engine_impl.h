@@ -87,6 +87,16 @@ struct Run {
     const double *gtau = nullptr;
     int32_t graph_max_passes = 0;
     const int32_t *gL = nullptr;  // layer cap of every graph (batches; L is the largest)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // start and end of a whole run
+
+    Run() = default;
+    Run(const Run &) = delete;
+    Run &operator=(const Run &) = delete;
+    ~Run() {  // the run's events go on every return path, errors included
+        for (auto &m : marks) cudaEventDestroy(m.first);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
 };
 
 // One graph submitted to a serving handle.
@@ -302,8 +312,8 @@ struct Handle::Impl {
     leiden_status mark(Run &r, int phase) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
+        r.marks.push_back({e, phase});  // owned by the run from here
         CK(cudaEventRecord(e, s));
-        r.marks.push_back({e, phase});
         return LEIDEN_OK;
     }
     cudaEvent_t next_event() {

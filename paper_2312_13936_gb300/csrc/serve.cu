@@ -326,7 +326,6 @@ leiden_status Handle::server_step(int32_t *finished_out) {
     r.graph_max_passes = prm.max_passes;
     bool stop = false;
     ST(q.pass(r, 0, stop));
-    for (auto &m : r.marks) cudaEventDestroy(m.first);
     v.steps++;
     // ---- graphs that stopped leave with their results
     CK(cudaMemcpyAsync(v.hstate.data(), q.gstate, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s));
