@@ -120,3 +120,23 @@ def test_argument_checks_before_device_work():
     bad(lib.leiden_csr_from_edges(2, 1, vp(src), vp(src), None, 0, 0, 0, vp(o3), None, None, None, None))
     bad(lib.leiden_csr_from_edges(2, 1, None, vp(src), None, 0, 0, 0, vp(o3), None, None, ctypes.byref(i64),
                                   None))
+
+
+def test_last_error_is_per_thread():
+    """leiden_last_error describes the last failure of the calling thread."""
+    import threading
+    lib = lg.library(build_if_missing=True)
+    seen = {}
+
+    def worker():
+        assert lib.leiden_create(None, 0, 0, None, None, None, 0, 0, None) == -1
+        seen["worker"] = lib.leiden_last_error().decode()
+
+    h = ctypes.c_void_p()
+    assert lib.leiden_batch_create(ctypes.byref(h), 0, None, 0, None, None, None, 0, 0, None) == -1
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    mine = lib.leiden_last_error().decode()
+    assert "out is NULL" in seen["worker"]
+    assert "batch" in mine and mine != seen["worker"]
