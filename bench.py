@@ -238,6 +238,17 @@ def phase_roofline(prof, peak, step_ms):
     return by_phase, over
 
 
+def optional_leg(fn, *args):
+    """One optional part of the JSON line. A failure takes the part's place as
+    {"error": ...}, with the traceback on stderr, so the headline still prints."""
+    try:
+        return fn(*args)
+    except Exception as e:
+        import traceback
+        traceback.print_exc()
+        return {"error": f"{type(e).__name__}: {e}"[:400]}
+
+
 def lpt_shares(m, world):
     """Graph ids of each rank: longest-processing-time-first by entry count.
 
@@ -606,8 +617,7 @@ def main():
     disconnected = lg.disconnected(off, idx, memb)
 
     # ---- end to end through the C ABI with host buffers (H2D and D2H inside)
-    e2e = None
-    if not args.no_e2e:
+    def e2e_leg():
         import ctypes
         # the user's buffers, staged once in page-locked host memory (outside
         # the timed region), as a caller that streams graphs would keep them
@@ -649,13 +659,23 @@ def main():
         te = time.perf_counter() - t0
         if world > 1:
             te = float(reduce_stats(torch.tensor([te], device=dev), 1, world).item())
-        e2e = {"value": world * ne * g.nnz / te, "unit": "edges/s",
-               "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in hbuf),
-               "d2h_bytes_per_step": g.n * 4 + 8, "pinned": pinned, "ms_per_step": te * 1e3 / ne,
-               "create_ms": split[0] * 1e3 / ne, "run_ms": split[1] * 1e3 / ne, "destroy_ms": split[2] * 1e3 / ne}
+        return {"value": world * ne * g.nnz / te, "unit": "edges/s",
+                "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in hbuf),
+                "d2h_bytes_per_step": g.n * 4 + 8, "pinned": pinned, "ms_per_step": te * 1e3 / ne,
+                "create_ms": split[0] * 1e3 / ne, "run_ms": split[1] * 1e3 / ne,
+                "destroy_ms": split[2] * 1e3 / ne}
 
-    variants = None if (args.no_variants or rank != 0) else variants_form(h, off, idx, mode, base_flags, stream)
-    batched = None if args.no_batch else batched_form(args, rank, world, mode, base_flags)
+    # legs with collectives run bare under several ranks: a rank that stopped
+    # on its own error would leave the others waiting
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_leg() if world > 1 else optional_leg(e2e_leg)
+    variants = None if (args.no_variants or rank != 0) else optional_leg(variants_form, h, off, idx, mode,
+                                                                         base_flags, stream)
+    batched = None
+    if not args.no_batch:
+        batched = (batched_form(args, rank, world, mode, base_flags) if world > 1
+                   else optional_leg(batched_form, args, rank, world, mode, base_flags))
 
     if rank != 0:
         dist.destroy_process_group()
@@ -675,8 +695,8 @@ def main():
                     "bytes_per_launch": a["bytes"] / a["launches"], "ms_per_launch": a["ms"] / a["launches"],
                     "share_of_profiled_ms": a["ms"] / total_ms}
         roofline["by_phase"], roofline["overall"] = phase_roofline(prof, peak, ms / args.steps)
-    cpu = None if (args.no_cpu or world > 1) else cpu_baseline(args.cpu_side)
-    served = None if (args.no_serve or world > 1) else served_form(args, mode, base_flags)
+    cpu = None if (args.no_cpu or world > 1) else optional_leg(cpu_baseline, args.cpu_side)
+    served = None if (args.no_serve or world > 1) else optional_leg(served_form, args, mode, base_flags)
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -73,3 +73,14 @@ def test_reference_arm_other_ranks_silent():
     """Under torchrun only rank 0 runs the oracle; the others exit 0 quietly."""
     assert _bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-side", "60"],
                   {"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_optional_leg_reports_a_failure_in_its_place(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.optional_leg(lambda a, b: a + b, 2, 3) == 5
+
+    def broken():
+        raise ValueError("no such graph")
+    assert bench.optional_leg(broken) == {"error": "ValueError: no such graph"}
+    assert "no such graph" in capsys.readouterr().err
