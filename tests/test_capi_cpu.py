@@ -140,3 +140,39 @@ def test_last_error_is_per_thread():
     mine = lib.leiden_last_error().decode()
     assert "out is NULL" in seen["worker"]
     assert "batch" in mine and mine != seen["worker"]
+
+
+def test_plain_c_consumer(tmp_path):
+    """A C99 program includes the header, links the library and calls its
+    host-only entry points: the boundary needs no C++ or Python on the caller's
+    side."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        import pytest
+        pytest.skip("no C compiler")
+    lg.library(build_if_missing=True)
+    lib = lg._build.LIB
+    src = tmp_path / "consumer.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "leiden.h"
+int main(void) {
+    leiden_params p;
+    leiden_params_default(&p);
+    leiden_graph_t g = 0;
+    leiden_status s = leiden_create(&g, -1, 0, NULL, NULL, NULL, LEIDEN_HOST, 0, NULL);
+    printf("%g %d %d %s %s|%s\n", p.resolution, p.max_passes, p.max_iterations, leiden_status_string(s),
+           leiden_status_string(LEIDEN_OK), leiden_last_error());
+    return (s == LEIDEN_ERR_INVALID && g == NULL && strlen(leiden_last_error()) > 0) ? 0 : 1;
+}
+''')
+    exe = tmp_path / "consumer"
+    inc = os.path.join(os.path.dirname(HEADER))
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", inc, str(src), lib, "-o", str(exe),
+                        f"-Wl,-rpath,{os.path.dirname(lib)}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.startswith("1 10 20 LEIDEN_ERR_INVALID LEIDEN_OK|")
