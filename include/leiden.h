@@ -226,7 +226,9 @@ leiden_status leiden_server_create(leiden_server_t *out, const leiden_params *p,
  * once: to device memory when the budget allows, else to host memory until
  * it does. *request_id receives the graph's id. Graphs without vertices are
  * finished at once. Returns LEIDEN_ERR_INVALID for a graph larger than the
- * server's capacity; in deterministic mode LEIDEN_ERR_UNSUPPORTED or
+ * server's capacity, LEIDEN_ERR_OOM for a graph whose own buffers
+ * (8 (n + 1) + 4 n + 8 nnz bytes) exceed the device budget, since it could
+ * never be admitted; in deterministic mode LEIDEN_ERR_UNSUPPORTED or
  * LEIDEN_ERR_OVERFLOW as leiden_run would. */
 leiden_status leiden_server_submit(leiden_server_t s, int64_t n, int64_t nnz, const int64_t *offsets,
                                    const int32_t *indices, const float *weights, int32_t where, int64_t *request_id);

@@ -80,10 +80,12 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
 
 namespace {
 
-int64_t request_bytes(const Request &r) {
-    return (int64_t)sizeof(int64_t) * (r.n + 1) + (int64_t)(sizeof(int32_t) + sizeof(float)) * r.m +
-           (int64_t)sizeof(int32_t) * r.n;
+// device bytes of a graph's own buffers: CSR copy and result
+int64_t graph_bytes(int64_t n, int64_t m) {
+    return (int64_t)sizeof(int64_t) * (n + 1) + (int64_t)(sizeof(int32_t) + sizeof(float)) * m +
+           (int64_t)sizeof(int32_t) * n;
 }
+int64_t request_bytes(const Request &r) { return graph_bytes(r.n, r.m); }
 
 }  // namespace
 
@@ -178,6 +180,11 @@ leiden_status Handle::server_submit(int64_t n, int64_t nnz, const int64_t *off, 
     if (n > v.cap_v || nnz > v.cap_e) {
         set_last_error("graph larger than the server's capacity");
         return LEIDEN_ERR_INVALID;
+    }
+    if (graph_bytes(n, nnz) > v.budget) {  // could never be admitted, and would hold up every later graph
+        set_last_error("graph needs " + std::to_string(graph_bytes(n, nnz)) + " device bytes, more than the " +
+                       "server's device budget of " + std::to_string(v.budget));
+        return LEIDEN_ERR_OOM;
     }
     if (where == LEIDEN_HOST && (off[0] != 0 || off[n] != nnz)) {
         set_last_error("offsets[0] must be 0 and offsets[n] must equal nnz");

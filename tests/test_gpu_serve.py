@@ -139,6 +139,29 @@ def test_serve_admission_waits_for_capacity():
         srv.close()
 
 
+def test_serve_refuses_a_graph_over_the_budget():
+    """A graph whose own buffers exceed the device budget could never be
+    admitted: it is refused at submit, and later graphs still run."""
+    g = gen.ring_of_cliques(4, 5)  # 20 vertices, 70 entries: 8*21 + 4*20 + 8*70 = 808 bytes
+    small = gen.from_edges(2, np.array([0]), np.array([1]))  # 8*3 + 4*2 + 8*2 = 48 bytes
+    srv = lg.LeidenServer(1000, 10000, device_budget=200, mode=lg.LEIDEN_DETERMINISTIC)
+    try:
+        with pytest.raises(lg.LeidenError) as e:
+            srv.submit(g.offsets, g.indices, g.weights)
+        assert e.value.status == -3
+        rid = srv.submit(small.offsets, small.indices, small.weights)
+        res = {}
+        for _ in range(50):
+            srv.step()
+            for r in srv.results():
+                res[r[0]] = r[1]
+            if res:
+                break
+        assert np.array_equal(res[rid], oracle.leiden(small, mode=oracle.SYNC).membership)
+    finally:
+        srv.close()
+
+
 def test_serve_rejects_bad_graphs():
     g = gen.ring_of_cliques(4, 5)
     srv = lg.LeidenServer(1000, 10000, mode=lg.LEIDEN_DETERMINISTIC)
