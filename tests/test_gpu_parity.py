@@ -152,6 +152,25 @@ def test_async_quality_and_connectivity(name, flags):
     assert memb.max() + 1 == st.communities
 
 
+def test_full_size_road_async():
+    """The benchmarked workload at full size (road lattice 5000 x 5000, 25M
+    vertices, 90,981,444 entries) in the benchmark's launch configuration
+    (asynchronous mode, default flags), held to the properties that hold at
+    any size: modularity within the tolerance of the oracle's sequential run,
+    every community connected (the oracle's BFS), the reported modularity
+    equal to the oracle's recomputation, and canonical labels."""
+    g = gen.road_workload()
+    memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC)
+    seq = oracle.leiden(g, mode=oracle.SEQ)
+    assert q >= seq.modularity - Q_TOL_ASYNC, (q, seq.modularity)
+    assert oracle.disconnected(g, memb)[0] == 0
+    q_re = oracle.modularity(g, memb)
+    assert abs(q - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re))
+    first = np.unique(memb, return_index=True)[1]
+    assert np.array_equal(np.sort(first), first)
+    assert memb.max() + 1 == st.communities
+
+
 def test_async_hubs_connected_and_consistent():
     g = hub_graph()
     memb, q, st, _ = run_gpu(g, lg.LEIDEN_ASYNC)
