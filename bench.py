@@ -19,7 +19,8 @@ The same line carries the batched form ("batched"): 4096 seeded SBM graphs
 p_out/p_in = 0.02; ~61M vertices, ~1.2e9 entries) packed as one segmented CSR
 and solved by leiden_batch_run, in graphs/s, next to a per-graph loop of
 plain leiden_run calls timed on a sample of the same graphs. With N > 1 the
-graphs are split across ranks in contiguous ranges.
+graphs are dealt to ranks longest-first by entry count, each to the rank with
+the least work so far.
 
 And the served form ("served"): a Poisson stream of seeded SBM (1k-4M
 vertices) and R-MAT (scale 14-22, edge factor 16) graphs from host memory,
@@ -33,6 +34,15 @@ And the paper's variants on the bench graph ("variants", rank 0, outside the
 timed region): the Louvain method (no refinement) and refine-based
 super-vertex labels, each with its time, modularity and fraction of
 disconnected communities beside the Leiden run's.
+
+"roofline" rates the dominant kernel class against the measured HBM copy
+bandwidth: its algorithmic bytes (counted by the kernels in the first timed
+step) over its CUDA-event time. "by_phase" and "overall" give the same for
+each phase and for all profiled launches, and the profiled bytes over the
+whole step. "e2e" runs the C ABI from page-locked host buffers (the copies in
+and out inside the timed region) and splits a step into create, run and
+destroy. An optional part that fails is reported as {"error": ...} in its
+place.
 """
 import argparse
 import hashlib
