@@ -24,7 +24,7 @@
  *              weights, exact int64 move decisions. The bit-exact reference
  *              for the GPU's deterministic mode.
  *
- * Readings of points the paper leaves open (numbered as in the design notes):
+ * Readings of points the paper leaves open, numbered R1-R14, S0-S5 and V1-V3:
  *   R1  MAX_PASSES is not given; it is a parameter (default 10).
  *   R2  Candidates are the communities in the scan table other than the
  *       vertex's own; the best one is taken (ties: lowest community id) and
@@ -71,28 +71,37 @@
  *       of Jones & Plassmann's parallel colouring. A vertex with
  *       layer(v) < L-1 takes step layer(v); every other vertex takes step
  *       L-1 + ((h(v) >> 32) mod B) (B = schedule_buckets). L is
- *       schedule_layers, or, when that is 0 (the default), 1000 for an
- *       input with a row of more than 2048 entries and 32 otherwise: on
- *       heavy-tailed graphs the hubs must be handled one layer after another
- *       (vertices past the cap share bucket steps with their neighbours,
- *       and on R-MAT graphs the refinement of the last pass then splits
- *       large communities), elsewhere a short schedule is as good and
- *       cheaper. Steps are processed in increasing order. A step
+ *       schedule_layers, or, when that is 0 (the default), 1000 for a
+ *       heavy-tailed input -- one whose largest degree exceeds 64 times its
+ *       mean degree nnz/n (edgeless vertices counted) -- and 32 otherwise:
+ *       on heavy-tailed graphs the hubs must be handled one layer after
+ *       another (vertices past the cap share bucket steps with their
+ *       neighbours, and on R-MAT graphs the refinement of the last pass then
+ *       splits large communities), elsewhere a short schedule is as good and
+ *       cheaper. (Lattices, block models and G(n, p) graphs have ratios
+ *       below 4; R-MAT graphs from scale 13 up have ratios above 90.) Steps
+ *       are processed in increasing order. A step
  *       below L-1 holds no two adjacent vertices, so on those edges the two
  *       ends are handled in priority order as in a sequential sweep. Inside a
  *       step every vertex is evaluated against the state at the start of the
  *       step, then all accepted moves are applied.
  *   S1  Move decisions use key(c) = 2m*K_{i->c} - K_i*Sigma_c (Eq. 2 times
  *       2m^2 up to a term common to all c); the vertex moves iff
- *       key(c*) > 2m*K_{i->d} - K_i*(Sigma_d - K_i). Requires integer
- *       weights, gamma = 1 and 2m < 2^31 so every product fits in int64.
+ *       key(c*) > 2m*K_{i->d} - K_i*(Sigma_d - K_i). Weights, K, Sigma and
+ *       2m are int64, keys and their differences 128-bit integers (every
+ *       product is below (2m)^2). Requires integer weights, gamma = 1 and
+ *       2m < 2^53 (the weight sum is then exact in fp64 and every key
+ *       difference, and a sweep's sum of them, fits in 128 bits).
  *   S2  In steps >= L-1 only (where neighbours can move together), a
  *       vertex alone in its community does not move into another
  *       single-vertex community with a larger id (no endless label swaps).
  *   S3  Pruning as in Algorithm 2: a vertex is marked processed when it is
  *       evaluated; the CSR neighbours (self-loop included) of a vertex that
  *       moved are marked unprocessed when its layer's moves are applied.
- *   S4  Sweep delta-modularity = 2*sum(key gains) / (2m)^2 in fp64.
+ *   S4  Sweep delta-modularity = 2*num / (2m)^2 in fp64, num the sweep's
+ *       sum of key gains (an unsigned 128-bit integer, every gain being
+ *       positive) converted as (double)(num >> 64) * 2^64 + (double)(num
+ *       mod 2^64), each conversion and the sum rounded to nearest.
  *   S5  Refinement accepts a proposal i -> t unless t is a single-vertex
  *       community whose vertex proposes in the same step; of two vertices
  *       proposing to each other, the one with the larger id moves. Below
@@ -127,6 +136,14 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+typedef __int128 og_i128;            /* S1 keys (a GCC extension on 64-bit targets) */
+typedef unsigned __int128 og_u128;   /* S4 sweep sums */
+
+/* S4: a sweep's gain sum as a double, in a fixed order of roundings */
+static double u128_to_double(og_u128 x) {
+    return (double)(uint64_t)(x >> 64) * 18446744073709551616.0 + (double)(uint64_t)x;
+}
 
 enum { OG_OK = 0, OG_ERR_INVALID = -1, OG_ERR_OOM = -3, OG_ERR_UNSUPPORTED = -6, OG_ERR_OVERFLOW = -7 };
 enum { OG_SEQ = 0, OG_SYNC = 1 };
@@ -442,7 +459,7 @@ static int move_sync(const og_graph *g, int32_t *C, const int64_t *K, int64_t *S
     int64_t n = g->n;
     uint8_t *unprocessed = (uint8_t *)malloc((size_t)(n ? n : 1));
     int32_t *prop = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
-    int64_t *gain = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    og_i128 *gain = (og_i128 *)malloc((size_t)(n ? n : 1) * sizeof(og_i128));
     int64_t *lo = NULL;
     int32_t *lst = NULL;
     if (!unprocessed || !prop || !gain || layer_lists(n, layer, nl, &lo, &lst)) {
@@ -452,7 +469,7 @@ static int move_sync(const og_graph *g, int32_t *C, const int64_t *K, int64_t *S
     int sweeps = 0;
     for (int32_t it = 0; it < max_it; ++it) {
         sweeps++;
-        int64_t num = 0;
+        og_u128 num = 0;
         for (int32_t k = 0; k < nl; ++k) {
             /* evaluate the layer against the state at its start */
             for (int64_t q = lo[k]; q < lo[k + 1]; ++q) {
@@ -464,13 +481,13 @@ static int move_sync(const og_graph *g, int32_t *C, const int64_t *K, int64_t *S
                 scan_communities(H, g, C, i, 0);
                 int32_t d = C[i];
                 int64_t Kid = H->has[d] ? H->ival[d] : 0;
-                int64_t key_d = two_m * Kid - K[i] * (Sig[d] - K[i]);
+                og_i128 key_d = (og_i128)two_m * Kid - (og_i128)K[i] * (Sig[d] - K[i]);
                 int32_t best = -1;
-                int64_t best_key = 0;
+                og_i128 best_key = 0;
                 for (int64_t t = 0; t < H->nkeys; ++t) {
                     int32_t c = H->keys[t];
                     if (c == d) continue;
-                    int64_t key = two_m * H->ival[c] - K[i] * Sig[c];
+                    og_i128 key = (og_i128)two_m * H->ival[c] - (og_i128)K[i] * Sig[c];
                     if (best < 0 || key > best_key || (key == best_key && c < best)) { best = c; best_key = key; }
                 }
                 if (best < 0 || best_key <= key_d) continue;
@@ -488,11 +505,11 @@ static int move_sync(const og_graph *g, int32_t *C, const int64_t *K, int64_t *S
                 size[d]--;
                 size[c]++;
                 C[i] = c;
-                num += gain[i];
+                num += (og_u128)gain[i];
                 for (int64_t e = g->off[i]; e < g->off[i] + g->deg[i]; ++e) unprocessed[g->idx[e]] = 1;
             }
         }
-        double dQ = 2.0 * (double)num / ((double)two_m * (double)two_m); /* S4 */
+        double dQ = 2.0 * u128_to_double(num) / ((double)two_m * (double)two_m); /* S4 */
         if (dQ <= tau) break;
     }
     free(unprocessed); free(prop); free(gain); free(lo); free(lst);
@@ -522,13 +539,13 @@ static int refine_sync(const og_graph *g, const int32_t *CB, int32_t *C, const i
                 table_clear(H);
                 scan_bounded(H, g, CB, C, i, 0);
                 int64_t Kic_own = H->has[c] ? H->ival[c] : 0;
-                int64_t key_c = two_m * Kic_own - K[i] * (Sig[c] - K[i]);
+                og_i128 key_c = (og_i128)two_m * Kic_own - (og_i128)K[i] * (Sig[c] - K[i]);
                 int32_t best = -1;
-                int64_t best_key = 0;
+                og_i128 best_key = 0;
                 for (int64_t t = 0; t < H->nkeys; ++t) {
                     int32_t cc = H->keys[t];
                     if (cc == c) continue;
-                    int64_t key = two_m * H->ival[cc] - K[i] * Sig[cc];
+                    og_i128 key = (og_i128)two_m * H->ival[cc] - (og_i128)K[i] * Sig[cc];
                     if (best < 0 || key > best_key || (key == best_key && cc < best)) { best = cc; best_key = key; }
                 }
                 if (best >= 0 && best_key > key_c) prop[i] = best;
@@ -874,14 +891,14 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
     if (p->max_iterations < 1 || p->max_passes < 0 || !(p->tolerance_drop > 0)) return OG_ERR_INVALID;
     if (p->mode == OG_SYNC && (p->schedule_layers < 0 || p->schedule_buckets < 1)) return OG_ERR_INVALID;
     if (p->mode == OG_SYNC && (p->flags & OG_RANDOM_REFINE)) return OG_ERR_UNSUPPORTED; /* V3: SEQ only */
-    /* S0: L of the run (0: 1000 for an input with a row of more than 2048
-     * entries, else 32) */
+    /* S0: L of the run (0: 1000 for a heavy-tailed input, largest degree
+     * above 64 times the mean degree nnz/n; else 32) */
     int32_t Ls = p->schedule_layers;
     if (Ls == 0) {
         int64_t maxdeg = 0;
         for (int64_t i = 0; i < n0; ++i)
             if (off0[i + 1] - off0[i] > maxdeg) maxdeg = off0[i + 1] - off0[i];
-        Ls = maxdeg > 2048 ? 1000 : 32;
+        Ls = (og_i128)maxdeg * n0 > (og_i128)64 * nnz ? 1000 : 32;
     }
     int sync = (p->mode == OG_SYNC);
     if (sync) {
@@ -892,7 +909,7 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
             if (x != floor(x)) return OG_ERR_UNSUPPORTED;
             s += x;
         }
-        if (s >= 2147483648.0) return OG_ERR_OVERFLOW;
+        if (s >= 9007199254740992.0) return OG_ERR_OVERFLOW; /* S1: 2m < 2^53 */
     }
     if (passes_out) *passes_out = 0;
     if (q_out) *q_out = 0.0;

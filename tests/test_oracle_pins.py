@@ -221,12 +221,38 @@ def test_sync_mode_validation():
     bad = gen.CSR(g.n, g.offsets, g.indices, w)
     assert oracle.leiden(bad, mode=oracle.SYNC).status == oracle.ERR_UNSUPPORTED
     assert oracle.leiden(g, mode=oracle.SYNC, resolution=0.5).status == oracle.ERR_UNSUPPORTED
-    big = gen.CSR(g.n, g.offsets, g.indices, np.full_like(g.weights, 2.0 ** 26))
+    # S1: 2m < 2^53 (48 entries of weight 2^48 give 2m = 1.5 * 2^53)
+    big = gen.CSR(g.n, g.offsets, g.indices, np.full_like(g.weights, 2.0 ** 48))
+    assert g.nnz * 2.0 ** 48 >= 2.0 ** 53
     assert oracle.leiden(big, mode=oracle.SYNC).status == oracle.ERR_OVERFLOW
     idx = g.indices.copy()
     idx[3] = g.n
     assert oracle.leiden(gen.CSR(g.n, g.offsets, idx, g.weights)).status == oracle.ERR_INVALID
     assert oracle.leiden(g, mode=oracle.SEQ, resolution=0.5).status == 0
+
+
+@pytest.mark.parametrize("shift", [26, 32])
+def test_sync_keys_exact_beyond_32_bits(shift):
+    """S1/S4: scaling every integer weight by 2^shift scales each key by
+    2^(2 shift) and a sweep's gain sum and (2m)^2 alike, so every decision and
+    every tolerance test is the same: the run equals the unscaled one pass for
+    pass, although 2m (~2^44 and ~2^50) and the keys (~2^90 and ~2^102) are
+    far beyond 64-bit products."""
+    g = gen.road(60)
+    scaled = gen.CSR(g.n, g.offsets, g.indices, (g.weights.astype(np.float64) * 2.0 ** shift).astype(np.float32))
+    assert float(scaled.weights.astype(np.float64).sum()) >= 2.0 ** 40
+    a = oracle.leiden(g, mode=oracle.SYNC, trace=True)
+    b = oracle.leiden(scaled, mode=oracle.SYNC, trace=True)
+    assert a.status == 0 and b.status == 0
+    assert np.array_equal(a.membership, b.membership)
+    assert a.passes == b.passes
+    assert a.modularity == b.modularity
+    assert sorted(a.trace) == sorted(b.trace)
+    for p in a.trace:
+        assert sorted(a.trace[p]) == sorted(b.trace[p])
+        for w, x in a.trace[p].items():
+            y = b.trace[p][w]
+            assert np.array_equal(x * 2.0 ** shift if w == oracle.T_AGG_W else x, y), (p, w)
 
 
 def test_planted_partition_recovered():
@@ -516,13 +542,24 @@ def test_rmat_sync_schedule_keeps_sequential_quality():
     assert oracle.disconnected(g, syn.membership)[0] == 0
 
 
+def heavy_tailed(g):
+    """S0's graph property: the largest degree exceeds 64 times the mean
+    degree nnz/n."""
+    return int(np.diff(g.offsets).max()) * g.n > 64 * g.nnz
+
+
 def test_schedule_layers_by_graph():
-    """S0: schedule_layers = 0 takes L = 1000 for an input with a row of more
-    than 2048 entries, else L = 32."""
+    """S0: schedule_layers = 0 takes L = 1000 for a heavy-tailed input
+    (largest degree above 64 times the mean degree), else L = 32. A star's
+    hub is heavy-tailed at any size; a block model, a lattice and a small
+    R-MAT graph are not."""
     light = gen.sbm(3000, 12, 0.04, 0.002, seed=4)
     heavy = gen.rmat(14, 56, 0.57, 0.19, 0.19, seed=3)
-    assert np.diff(light.offsets).max() <= 2048 < np.diff(heavy.offsets).max()
-    for g, L in ((light, 32), (heavy, 1000)):
+    star = gen.from_edges(200, np.zeros(199, np.int64), np.arange(1, 200))
+    for g, h in ((light, False), (heavy, True), (star, True), (gen.road(50), False),
+                 (gen.rmat(12, 16), False)):
+        assert heavy_tailed(g) == h
+    for g, L in ((light, 32), (heavy, 1000), (star, 1000)):
         auto = oracle.leiden(g, mode=oracle.SYNC, trace=True)
         fixed = oracle.leiden(g, mode=oracle.SYNC, schedule_layers=L, trace=True)
         assert np.array_equal(auto.membership, fixed.membership)
