@@ -128,9 +128,15 @@
  *       candidate whose running gain sum exceeds u times the total.
  *   Both modes:
  *   R5' The passes stop (global convergence) when the local-moving phase
- *       converged in its first sweep (l_i <= 1) and the refinement split no
+ *       converged in its first sweep (l_i <= 1), the refinement split no
  *       local-moving community (as many refined communities as local-moving
- *       ones): another pass could then change nothing.
+ *       ones), and the pass began with every super-vertex in its own
+ *       community (pass 0; a pass after one whose refinement split nothing;
+ *       every pass under V1): another pass could then change nothing. A pass
+ *       that began from move-based labels (R3) grouping several
+ *       super-vertices cannot merge two communities by moving single
+ *       super-vertices, but the next pass, whose super-vertices are those
+ *       communities, can.
  */
 #include <math.h>
 #include <stdint.h>
@@ -936,6 +942,7 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
     if (to_graph(n0, off0, idx0, w0, &G) != OG_OK) goto done;
 
     for (int64_t v = 0; v < n0; ++v) C[v] = (int32_t)v; /* C <- [0..|V|) */
+    int fresh = 1; /* R5': the pass begins with every super-vertex in its own community */
     double tau = p->tolerance;
     double gamma = p->resolution;
     int broke = 0, passes = 0;
@@ -1009,10 +1016,14 @@ int og_leiden(int64_t n0, const int64_t *off0, const int32_t *idx0, const float 
         int64_t nbound = 0;
         for (int64_t c = 0; c < n; ++c) size[c] = 0;
         for (int64_t i = 0; i < n; ++i) { if (!size[CB[i]]) nbound++; size[CB[i]] = 1; }
-        if (li <= 1 && nbound == ncomm) { broke = 1; break; }                    /* R5' */
+        if (li <= 1 && nbound == ncomm && fresh) { broke = 1; break; }           /* R5' */
         int64_t z = 0; /* R4: vertices without edges */
         for (int64_t i = 0; i < n; ++i) z += G.deg[i] == 0;
         if ((double)(ncomm - z) / (double)(n - z) > p->aggregation_tolerance) { broke = 1; break; } /* R4 */
+        /* R5': the next pass starts from singletons when every local-moving
+         * community is one refined community (move-based labels, R3) or
+         * under refine-based labels (V1) */
+        fresh = (p->flags & OG_REFINE_LABELS) || nbound == ncomm;
 
         /* renumber communities in C' */
         for (int64_t i = 0; i < n; ++i) Cp[i] = newid[Cp[i]];

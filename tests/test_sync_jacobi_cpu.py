@@ -22,15 +22,17 @@ deterministic readings alone, in Python integers:
     community whose vertex proposes too (of a mutual pair the larger id
     moves);
   - the stop tests (local-moving converged in one sweep with no community
-    split; refined communities over non-edgeless vertices above the
-    aggregation tolerance), renumbering in ascending id order, aggregation
+    split, in a pass that began with every super-vertex alone; refined
+    communities over non-edgeless vertices above the aggregation
+    tolerance), renumbering in ascending id order, aggregation
     with self-loops, move-based labels by the smallest super-vertex of each
     bound, threshold scaling, the refined partition of the last pass as the
     result, canonical labels.
 
 It must equal oracle.leiden(mode=SYNC, schedule_layers=1,
-schedule_buckets=1) bit for bit: membership, pass count, and per pass the
-local-moving and refinement labels and the counts (n', l_i, l_j, |Gamma|).
+schedule_buckets=1) bit for bit on twelve seeded graphs: membership, pass
+count, and per pass the local-moving and refinement labels and the counts
+(n', l_i, l_j, |Gamma|).
 """
 import numpy as np
 import pytest
@@ -56,7 +58,7 @@ def _best(H, own, K_i, Sig, two_m):
     return best
 
 
-def jacobi_leiden(g, tol=0.01, agg_tol=0.8, drop=10.0, max_it=20, max_passes=10):
+def jacobi_leiden(g, tol=0.01, agg_tol=0.8, drop=10.0, max_it=20, max_passes=10, fresh_rule=True):
     n0 = g.n
     rows = [[(int(g.indices[e]), int(g.weights[e])) for e in range(g.offsets[i], g.offsets[i + 1])]
             for i in range(n0)]
@@ -64,6 +66,7 @@ def jacobi_leiden(g, tol=0.01, agg_tol=0.8, drop=10.0, max_it=20, max_passes=10)
     init = list(range(n0))
     tau = tol
     passes, trace, last = 0, {}, None
+    fresh = True  # the pass begins with every super-vertex in its own community
     for lp in range(max_passes):
         n = len(rows)
         K = [sum(x for _, x in r) for r in rows]
@@ -150,11 +153,12 @@ def jacobi_leiden(g, tol=0.01, agg_tol=0.8, drop=10.0, max_it=20, max_passes=10)
         ncomm = len(present)
         trace[lp] = {"move": moved_labels, "refine": list(refined), "counts": [n, li, lj, ncomm]}
         last = refined
-        if li <= 1 and len(set(CB)) == ncomm:
+        if li <= 1 and len(set(CB)) == ncomm and (fresh or not fresh_rule):
             break
         z = sum(1 for r in rows if not r)
         if (ncomm - z) / (n - z) > agg_tol:
             break
+        fresh = len(set(CB)) == ncomm
         # ---- renumber, dendrogram lookup, aggregation (Algorithm 4)
         newid = {c: k for k, c in enumerate(present)}
         dendro = [newid[refined[v]] for v in dendro]
@@ -203,6 +207,8 @@ def _graphs():
         "rmat_8": gen.rmat(8, 8, seed=35),
         "loops_100": random_graph_with_loops(100, 0.05, seed=36),
         "lattice_with_isolated": lattice_isolated,
+        "sbm_210_blocks_3": gen.sbm(210, 3, 0.2, 0.01, seed=106),
+        "sbm_280_blocks_4": gen.sbm(280, 4, 0.2, 0.01, seed=113),
     }
 
 
@@ -230,6 +236,9 @@ def test_jacobi_restatement_is_not_vacuous():
     and a mutual refinement proposal."""
     multi = sum(1 for g in GRAPHS.values() if jacobi_leiden(g)[1] >= 2)
     assert multi >= 5
+    # the global-convergence test waits for a pass that began from
+    # singletons: without that condition some runs stop a pass earlier
+    assert any(jacobi_leiden(g)[1] != jacobi_leiden(g, fresh_rule=False)[1] for g in GRAPHS.values())
     split = 0
     for g in GRAPHS.values():
         _, _, tr = jacobi_leiden(g)
