@@ -8,22 +8,27 @@ namespace lgb {
 constexpr int kWarp = 32;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Arithmetic policies. acc is the type of per-edge sums (K_{i->c}), vertex
-// weights K_i and move keys; tot the type of community totals Sigma_c and of
-// the sweep's delta-modularity sums. The deterministic mode decides moves in
-// exact int64 arithmetic on integer weights. The asynchronous mode keeps
-// Sigma and 2m in fp64 and everything per edge in fp32: on this GPU the fp64
-// pipe is a small fraction of the fp32 rate, and the move key
+// Arithmetic policies. acc is the type of per-edge sums (K_{i->c}) and
+// vertex weights K_i; key the type of move keys and their gains; tot the
+// type of community totals Sigma_c and of the asynchronous sweep's
+// delta-modularity sums. The deterministic mode decides moves in exact
+// integer arithmetic on integer weights: sums, K and Sigma in int64, keys
+// (products of two such sums) in 128 bits, and a sweep's gain sum in 128
+// bits (two 64-bit words, lo then hi). The asynchronous mode keeps Sigma
+// and 2m in fp64 and everything per edge in fp32: on this GPU the fp64 pipe
+// is a small fraction of the fp32 rate, and the move key
 // K_{i->c} - gamma K_i Sigma_c / 2m has terms of the order of K_i, so fp32
 // keeps its relative precision.
 struct Det {
     using acc = long long;
     using tot = long long;
+    using key = __int128;
     static constexpr bool det = true;
 };
 struct Async {
     using acc = float;
     using tot = double;
+    using key = float;
     static constexpr bool det = false;
 };
 
@@ -37,6 +42,42 @@ template <> struct AccLimits<double> {
 template <> struct AccLimits<float> {
     __device__ static float lowest() { return __int_as_float(0xff800000); }  // -inf
 };
+template <> struct AccLimits<__int128> {
+    __device__ static __int128 lowest() { return (__int128)((unsigned __int128)1 << 127); }
+};
+
+// Register shuffles of the key types (a 128-bit key moves as two words).
+__device__ __forceinline__ float kshfl_xor(unsigned mask, float x, int o, int w = 32) {
+    return __shfl_xor_sync(mask, x, o, w);
+}
+__device__ __forceinline__ __int128 kshfl_xor(unsigned mask, __int128 x, int o, int w = 32) {
+    const unsigned long long lo = __shfl_xor_sync(mask, (unsigned long long)x, o, w);
+    const long long hi = __shfl_xor_sync(mask, (long long)(x >> 64), o, w);
+    return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+}
+__device__ __forceinline__ float kshfl(unsigned mask, float x, int src, int w = 32) {
+    return __shfl_sync(mask, x, src, w);
+}
+__device__ __forceinline__ __int128 kshfl(unsigned mask, __int128 x, int src, int w = 32) {
+    const unsigned long long lo = __shfl_sync(mask, (unsigned long long)x, src, w);
+    const long long hi = __shfl_sync(mask, (long long)(x >> 64), src, w);
+    return (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+}
+
+// A 128-bit unsigned sum held as two words (lo, hi) in global memory:
+// atomically add x, carrying into hi when lo wraps. Every addition that
+// wraps lo adds exactly one carry, so the pair is the exact sum mod 2^128
+// in any order.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *p, unsigned __int128 x) {
+    const unsigned long long lo = (unsigned long long)x;
+    unsigned long long hi = (unsigned long long)(x >> 64);
+    if (lo) {
+        const unsigned long long old = atomicAdd(&p[0], lo);
+        if (old + lo < old) hi += 1ULL;
+    }
+    if (hi) atomicAdd(&p[1], hi);
+}
+
 
 template <class A, class W> __device__ __forceinline__ A wconv(W w) { return (A)w; }
 
@@ -69,24 +110,49 @@ template <class V, class D> __device__ __forceinline__ void gacc_flush(GAcc<V> &
     acc.v = 0;
 }
 
+// The deterministic mode's gain sums: 128 bits per thread, flushed into
+// per-graph slots of two words (lo, hi) at base + 2 g.
+__device__ __forceinline__ void gacc_add(GAcc<unsigned __int128> &acc, bool batch, int32_t g, unsigned __int128 x,
+                                         unsigned long long *base) {
+    if (batch && g != acc.g) {
+        if (acc.v) atomic_add_u128(base + 2 * (size_t)acc.g, acc.v);
+        acc.v = 0;
+        acc.g = g;
+    }
+    acc.v += x;
+}
+__device__ __forceinline__ void gacc_flush(GAcc<unsigned __int128> &acc, unsigned long long *base) {
+    if (acc.v) atomic_add_u128(base + 2 * (size_t)acc.g, acc.v);
+    acc.v = 0;
+}
+__device__ __forceinline__ unsigned __int128 warp_sum_u128(unsigned __int128 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+        const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+        v += ((unsigned __int128)hi << 64) | lo;
+    }
+    return v;
+}
+
 // Σ reads: the async mode sees concurrent atomics from other SMs, so it reads
 // through L2 (ld.global.cg); deterministic mode reads a snapshot.
 template <class A> __device__ __forceinline__ A load_cg(const A *p) { return __ldcg(p); }
 
-// Move keys (Eq. 2). Deterministic mode, Eq. 2 times 2m^2 (kscale = 2m):
+// Move keys (Eq. 2). Deterministic mode, Eq. 2 times 2m^2 (kscale = 2m), in
+// 128 bits (each product is below (2m)^2):
 //   key(c) = 2m K_{i->c} - K_i Sigma_c,  stay = 2m K_{i->d} - K_i (Sigma_d - K_i).
 // Asynchronous mode, Eq. 2 times m (kscale = 1/2m):
 //   key(c) = K_{i->c} - gamma K_i Sigma_c / 2m,  stay = K_{i->d} - gamma K_i (Sigma_d - K_i) / 2m.
 // The vertex moves to c* iff key(c*) > stay; the gain key(c*) - stay is
 // 2m^2 dQ (deterministic) or m dQ (asynchronous).
-__device__ __forceinline__ long long move_key(long long two_m, long long kic, long long ki, long long sc, double) {
-    return two_m * kic - ki * sc;
+__device__ __forceinline__ __int128 move_key(long long two_m, long long kic, long long ki, long long sc, double) {
+    return (__int128)two_m * kic - (__int128)ki * sc;
 }
 __device__ __forceinline__ float move_key(float inv2m, float kic, float ki, double sc, double gamma) {
     return kic - (float)gamma * ki * ((float)sc * inv2m);
 }
-__device__ __forceinline__ long long stay_key(long long two_m, long long kid, long long ki, long long sd, double) {
-    return two_m * kid - ki * (sd - ki);
+__device__ __forceinline__ __int128 stay_key(long long two_m, long long kid, long long ki, long long sd, double) {
+    return (__int128)two_m * kid - (__int128)ki * (sd - ki);
 }
 __device__ __forceinline__ float stay_key(float inv2m, float kid, float ki, double sd, double gamma) {
     return kid - (float)gamma * ki * (((float)sd - ki) * inv2m);
@@ -227,10 +293,12 @@ __device__ __forceinline__ void set_error(int *err, int code) {
 
 // Grid-wide barrier of a cooperative launch: blocks count in on bar[0]; the
 // last one resets it and advances the generation bar[1] that the others
-// poll. Spins are bounded: after about a second without progress the kernel
-// records kErrTimeout and every later barrier returns at once, so the launch
-// always ends. A grid of one block needs only __syncthreads.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+// poll. Spins are bounded: after spin_limit polls (2^24, about a second, by
+// default) without progress the kernel records kErrTimeout and every later
+// barrier returns at once, so the launch always ends. A grid of one block
+// needs only __syncthreads.
+constexpr unsigned long long kSpinLimit = 1ULL << 24;
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, unsigned long long spin_limit = kSpinLimit) {
     __shared__ int s_ok;
     __syncthreads();
     if (gridDim.x == 1) return true;
@@ -247,7 +315,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
             } else {
                 unsigned long long spins = 0;
                 while (*gen == g) {
-                    if (++spins > (1ULL << 24)) {
+                    if (++spins > spin_limit) {
                         set_error(err, kErrTimeout);
                         ok = 0;
                         break;

@@ -12,6 +12,7 @@
 // that stops leaves the union at the next renumbering. A single graph is the
 // case G = 1 without per-vertex graph ids.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -25,6 +26,7 @@
 namespace lgb {
 
 thread_local std::string g_last_error;
+std::atomic<int64_t> detail::g_fail_alloc_after{-1};  // leiden_test_fail_allocation
 void set_last_error(const std::string &s) { g_last_error = s; }
 const char *last_error() { return g_last_error.c_str(); }
 
@@ -77,7 +79,7 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     q.nonint = q.hsc->nonint != 0;
     q.wsum = q.hsc->wsum;
     q.maxdeg0 = q.hsc->maxdeg;
-    if (G > 1) {  // weight sum of every graph, for the deterministic mode's 2m < 2^31 rule
+    if (G > 1) {  // weight sum of every graph, for the deterministic mode's 2m < 2^53 rule
         GraphView g0;
         g0.n = n;
         g0.off = q.off0;
@@ -90,7 +92,11 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
         CK(launch_graph_sums(q.K, false, q.gid0, n, q.gmsum, q.s));
         q.hgw.assign(G, 0.0);
         CK(cudaMemcpyAsync(q.hgw.data(), q.gmsum, sizeof(double) * G, cudaMemcpyDeviceToHost, q.s));
-        // largest degree of every graph (the default layer cap of its schedule)
+        // largest degree and entry count of every graph (the default layer
+        // cap of its schedule, reading S0)
+        q.hgnnz.assign(G, 0);
+        CK(launch_graph_counts(q.off0, q.vseg0, G, q.gcomm, q.s));
+        CK(cudaMemcpyAsync(q.hgnnz.data(), q.gcomm, sizeof(int64_t) * G, cudaMemcpyDeviceToHost, q.s));
         ST(q.alloc(&q.gL, G));
         CK(cudaMemsetAsync(q.gL, 0, sizeof(int32_t) * G, q.s));
         CK(launch_graph_max_deg(q.deg0, q.gid0, n, q.gL, q.s));
@@ -244,7 +250,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     sc.two_m_i = two_m_i;
     sc.gamma = prm.resolution;
     sc.cap_step = L - 1;
-    sc.dq_acc = det ? (void *)&q.dsc->dq_i : (void *)&q.dsc->dq_f;
+    sc.dq_acc = det ? (void *)q.dsc->dq_i : (void *)&q.dsc->dq_f;
     sc.moved = &q.dsc->moved;
     sc.hub_keys = q.hub_keys;
     sc.hub_vals = q.hub_vals;
@@ -329,7 +335,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             sc.dq_arr = q.phase_dq;
             sc.moved_arr = q.phase_moved;
             sc.iters_out = &q.dsc->iters;
-            CK(cudaMemsetAsync(q.phase_dq, 0, sizeof(long long) * prm.max_iterations * NG, s));
+            CK(cudaMemsetAsync(q.phase_dq, 0, 2 * sizeof(long long) * prm.max_iterations * NG, s));
             CK(cudaMemsetAsync(q.phase_moved, 0, sizeof(unsigned long long) * prm.max_iterations * NG, s));
             CK(cudaMemsetAsync(q.gactive, 0, sizeof(unsigned) * prm.max_iterations, s));
             CK(cudaMemsetAsync(q.bar, 0, 2 * sizeof(unsigned), s));  // barrier state starts clean
@@ -340,6 +346,9 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             // leave whole steps idle (for one graph the marks of flagged
             // neighbours cost about what they save)
             sc.act = (nsteps > 64 && (refine || batch)) ? q.act : nullptr;
+            const bool stall = (prm.flags & LEIDEN_FLAG_TEST_STALL_BARRIER) != 0;
+            sc.stall_block = (stall && grid > 1) ? 1 : -1;
+            sc.spin_limit = stall ? (1ULL << 14) : kSpinLimitDefault;
             CK(launch_sweep_coop(sc, sList, grid, s));
             sc.act = nullptr;
             prof_end();
@@ -352,7 +361,8 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         int k = 0;
         for (int32_t it = 0; it < prm.max_iterations; ++it) {
             k++;
-            CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double) + sizeof(long long), s));
+            CK(cudaMemsetAsync(&q.dsc->dq_f, 0, sizeof(double), s));
+            CK(cudaMemsetAsync(q.dsc->dq_i, 0, sizeof(q.dsc->dq_i), s));
             CK(cudaMemsetAsync(&q.dsc->moved, 0, sizeof(unsigned long long), s));
             sc.sweep = it;
             ST(run_steps(refine));
@@ -360,7 +370,9 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             if (refine) {
                 if (q.hsc->moved == 0 || single) break;
             } else {
-                const double dq = det ? 2.0 * (double)q.hsc->dq_i / ((double)two_m_i * (double)two_m_i)
+                // reading S4: the 128-bit gain sum with the oracle's roundings
+                const double dq = det ? 2.0 * u128_words_to_double(q.hsc->dq_i[0], q.hsc->dq_i[1]) /
+                                            ((double)two_m_i * (double)two_m_i)
                                       : 2.0 * q.hsc->dq_f / two_m_f;
                 if (dq <= tau) break;  // locally converged
             }
@@ -404,7 +416,8 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     // the graphs that go on keep their refined communities, densely
     // renumbered after those of the graphs before them
     CK(launch_graph_stop(q.vseg, q.pos, q.pos2, q.gli, q.g2m, prm.aggregation_tolerance, NG, q.gstate, q.gkeep,
-                         q.gpasses, s, r.gpass, r.graph_max_passes, G.deg, batch ? cur_gid : nullptr, n, q.gzero));
+                         q.gpasses, s, r.gpass, r.graph_max_passes, G.deg, batch ? cur_gid : nullptr, n, q.gzero,
+                         q.gfresh, (prm.flags & LEIDEN_FLAG_REFINE_LABELS) != 0));
     CK(launch_exclusive_scan(q.gkeep, q.vseg2, NG, q.scan_tmp, s));
     q.launches += 14;
     int64_t counts[3];
@@ -458,7 +471,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     CK(cudaMemcpyAsync(&cap, q.agg[dst].off + ncomm, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(ako, q.key_off, sizeof(ako), cudaMemcpyDeviceToHost, s));
     ST(q.sync_scalars());
-    ST(q.ensure_agg(dst, cap));
+    ST(q.ensure_agg(dst, cap, det));
     // rows of communities without edges (bin 0) are never visited: empty
     CK(cudaMemsetAsync(q.agg[dst].deg, 0, sizeof(int32_t) * ncomm, s));
     {
@@ -537,6 +550,20 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             }
         }
     }
+    // deterministic mode: rows in ascending target order (reading R10)
+    if (det && cap > 1) {
+        void *stmp = nullptr;
+        const size_t sb = sort_rows_tmp_bytes(cap);
+        if (cudaMallocAsync(&stmp, sb, s) != cudaSuccess) {
+            set_last_error("device allocation of " + std::to_string(sb) + " bytes for the row sort failed");
+            return LEIDEN_ERR_OOM;
+        }
+        const cudaError_t e = launch_sort_rows(ncomm, q.agg[dst].off, q.agg[dst].deg, q.agg[dst].idx,
+                                               static_cast<WInt *>(q.agg[dst].w), cap, stmp, s);
+        cudaFreeAsync(stmp, s);
+        CK(e);
+        q.launches += 1;
+    }
     // move-based labels of the super-vertices (reading R3), or each alone
     // (refine-based labels)
     if (prm.flags & LEIDEN_FLAG_REFINE_LABELS) {
@@ -566,7 +593,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         q.record(lp, 7, G2.deg, ncomm);
         q.record(lp, 8, G2.idx, cap);
         // weights as fp64
-        std::vector<char> raw((size_t)cap * 4);
+        std::vector<char> raw((size_t)cap * (det ? sizeof(WInt) : sizeof(float)));
         if (cap) {
             CK(cudaMemcpyAsync(raw.data(), G2.w, raw.size(), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
@@ -574,7 +601,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         std::vector<char> buf((size_t)cap * sizeof(double));
         double *d = reinterpret_cast<double *>(buf.data());
         for (int64_t e = 0; e < cap; ++e) {
-            if (det) d[e] = (double)reinterpret_cast<const int32_t *>(raw.data())[e];
+            if (det) d[e] = (double)reinterpret_cast<const WInt *>(raw.data())[e];
             else d[e] = (double)reinterpret_cast<const float *>(raw.data())[e];
         }
         q.trace[{lp, 9}] = std::move(buf);
@@ -621,10 +648,11 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     if (L == 0) {
         if (batch) {
             hgL.resize((size_t)NG);
-            for (int32_t g = 0; g < NG; ++g) hgL[g] = auto_layers(q.hgmaxdeg[g]);
+            for (int32_t g = 0; g < NG; ++g)
+                hgL[g] = auto_layers(q.hgmaxdeg[g], q.hvseg0[g + 1] - q.hvseg0[g], q.hgnnz[g]);
             L = *std::max_element(hgL.begin(), hgL.end());
         } else {
-            L = auto_layers(q.maxdeg0);
+            L = auto_layers(q.maxdeg0, q.n0, q.m0);
         }
     }
     if (prm.max_iterations < 1 || prm.max_passes < 0 || !(prm.tolerance_drop > 0) || L < 1 || B < 1 ||
@@ -658,11 +686,14 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
             wmax = 0;
             for (double x : q.hgw) wmax = x > wmax ? x : wmax;
         }
-        if (wmax >= 2147483648.0) {
-            set_last_error("deterministic mode needs 2m < 2^31 (in every graph of a batch)");
+        if (wmax >= kDetMaxTwoM) {
+            set_last_error("deterministic mode needs 2m < 2^53 (in every graph of a batch)");
             return LEIDEN_ERR_OVERFLOW;
         }
     }
+    // a failure of an earlier run (a barrier timeout, a full hash table)
+    // must not outlive it: the error word starts clean
+    CK(cudaMemsetAsync(&q.dsc->err, 0, sizeof(int), s));
     q.trace.clear();
     q.trace_count.clear();
     q.launches = 0;
@@ -707,6 +738,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         CK(cudaMemcpyAsync(q.gstate, st0.data(), sizeof(int32_t) * NG, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(q.vseg, q.vseg0, sizeof(int64_t) * (NG + 1), cudaMemcpyDeviceToDevice, s));
         CK(cudaMemsetAsync(q.gpasses, 0, sizeof(int32_t) * NG, s));
+        CK(launch_fill_i32(q.gfresh, 1, NG, s));  // pass 0 begins from singletons
         CK(cudaStreamSynchronize(s));  // st0 is a local
     }
     r.n0 = n0;

@@ -2,6 +2,7 @@
 // serve.cu): the scalar block read back per phase, the state of one run,
 // and the handle's device workspace.
 #pragma once
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -24,7 +25,7 @@ struct Scalars {  // device scalars, read back in one copy
     double two_m_f;
     long long two_m_i;
     double dq_f;
-    long long dq_i;
+    unsigned long long dq_i[2];  // deterministic gain sum: 128 bits, lo then hi
     unsigned long long moved;
     double wsum;
     double msum[4];
@@ -46,6 +47,18 @@ struct Scalars {  // device scalars, read back in one copy
         leiden_status _s = (x);                \
         if (_s != LEIDEN_OK) return _s;        \
     } while (0)
+
+// barrier polls before a persistent launch gives up (kSpinLimit of the
+// device code, about a second)
+constexpr unsigned long long kSpinLimitDefault = 1ULL << 24;
+
+// allocations left before an injected failure (leiden_test_fail_allocation;
+// negative: none)
+extern std::atomic<int64_t> g_fail_alloc_after;
+
+// the deterministic mode's bound on 2m (reading S1): weight sums are then
+// exact in fp64, and every key and a sweep's sum of gains fit in 128 bits
+constexpr double kDetMaxTwoM = 9007199254740992.0;  // 2^53
 
 // vertices per block of the persistent sweep kernel (below a full grid):
 // a step's latency grows with the vertices each thread takes in turn, so
@@ -115,6 +128,7 @@ struct Request {
     int32_t L = 0;            // layer cap of its schedule (reading S0)
     // in flight
     int32_t pass = 0;
+    int32_t fresh = 1;        // its next pass begins from singletons (reading R5')
     int64_t n_cur = 0;        // vertices in the union
     int64_t arena = 0;        // first entry in the dendrogram arena
     // result
@@ -146,7 +160,7 @@ struct Serve {
     double *gtau = nullptr;
     // host mirrors of the per-graph arrays of a step
     std::vector<int64_t> hvseg, hvseg0;
-    std::vector<int32_t> hpass, hstate, hL;
+    std::vector<int32_t> hpass, hstate, hL, hfresh;
     std::vector<double> htau;
     int32_t *gL = nullptr;
 };
@@ -169,6 +183,7 @@ struct Handle::Impl {
         int32_t *deg = nullptr, *idx = nullptr;
         void *w = nullptr;
         int64_t cap = 0;
+        int wsz = 0;  // bytes per weight: 4 (fp32) or 8 (WInt)
     } agg[2];
     // per-vertex workspace
     int32_t *C0 = nullptr, *Cp = nullptr, *CB = nullptr, *Cd = nullptr, *size = nullptr, *prop = nullptr,
@@ -211,10 +226,12 @@ struct Handle::Impl {
     std::vector<int64_t> hvseg0;           // vertex offsets of the graphs in the input
     std::vector<double> hgw;               // weight sum of every graph (fp64)
     std::vector<int32_t> hgmaxdeg;         // largest degree of every graph
+    std::vector<int64_t> hgnnz;            // CSR entries of every graph
     int32_t *gL = nullptr;                 // layer cap of every graph (device)
     int64_t *vseg0 = nullptr, *vseg = nullptr, *vseg2 = nullptr;  // G+1 each: input, this pass, next pass
     int32_t *gid0 = nullptr, *gidA = nullptr, *gidB = nullptr;
-    int32_t *gstate = nullptr, *gdone = nullptr, *gli = nullptr, *glj = nullptr, *gpasses = nullptr;
+    int32_t *gstate = nullptr, *gdone = nullptr, *gli = nullptr, *glj = nullptr, *gpasses = nullptr,
+            *gfresh = nullptr;  // gfresh: the graph's pass began from singletons (reading R5')
     int64_t *gkeep = nullptr, *gcomm = nullptr;
     unsigned long long *gzero = nullptr;  // vertices without edges of every graph (reading R4)
     long long *gsumk = nullptr;            // per-graph sums of K (int64 or fp64 bits)
@@ -234,7 +251,8 @@ struct Handle::Impl {
         phase_dq = nullptr;
         phase_moved = nullptr;
         gactive = nullptr;
-        ST(alloc(&phase_dq, (int64_t)max_it * ng));
+        phase_cap = 0;  // nothing held until every array is in place
+        ST(alloc(&phase_dq, 2 * (int64_t)max_it * ng));  // deterministic sums take two words
         ST(alloc(&phase_moved, (int64_t)max_it * ng));
         ST(alloc(&gactive, max_it));
         phase_cap = max_it;
@@ -270,7 +288,7 @@ struct Handle::Impl {
         K = k1;
         Sig = k2;
         Kagg = k3;
-        ST(alloc(&gain, n));
+        ST(alloc(&gain, 2 * n));  // a deterministic gain takes two words
         ST(alloc(&unproc, n));
         ST(alloc(&sigtot, n));
         char *tmp;
@@ -287,7 +305,7 @@ struct Handle::Impl {
         ST(alloc(&act, 1024));
         CK(cudaMemsetAsync(act, 0, sizeof(int32_t) * 1024, s));
         for (int64_t **a : {&vseg0, &vseg, &vseg2}) ST(alloc(a, ng + 1));
-        for (int32_t **a : {&gstate, &gdone, &gli, &glj, &gpasses}) ST(alloc(a, ng));
+        for (int32_t **a : {&gstate, &gdone, &gli, &glj, &gpasses, &gfresh}) ST(alloc(a, ng));
         for (int64_t **a : {&gkeep, &gcomm}) ST(alloc(a, ng));
         ST(alloc(&gzero, ng));
         ST(alloc(&gsumk, ng));
@@ -340,6 +358,10 @@ struct Handle::Impl {
     }
     template <class T> leiden_status alloc(T **p, int64_t count) {
         void *q = nullptr;
+        if (g_fail_alloc_after.load() >= 0 && g_fail_alloc_after.fetch_sub(1) == 0) {
+            set_last_error("injected device allocation failure (leiden_test_fail_allocation)");
+            return LEIDEN_ERR_OOM;
+        }
         cudaError_t e = cudaMallocAsync(&q, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
         if (e != cudaSuccess) {
             set_last_error(std::string("device allocation of ") + std::to_string(count * (int64_t)sizeof(T)) +
@@ -461,7 +483,7 @@ struct Handle::Impl {
         for (int32_t **a : {&hubs, &hd, &hcand, &hmv, &hj}) ST(alloc(a, nh));
         ST(alloc(&htoff, nh + 1));
         ST(alloc(&heoff, nh + 1));
-        ST(alloc(&hkey, nh));
+        ST(alloc(&hkey, 2 * nh));  // a deterministic key takes two words
         ST(alloc(&hkvd, nh));
         hubs_cap = nh;
         return LEIDEN_OK;
@@ -478,22 +500,29 @@ struct Handle::Impl {
         part_tmp_bytes = bytes;
         return LEIDEN_OK;
     }
-    leiden_status ensure_agg(int x, int64_t cap) {
+    // aggregated graph x with room for cap entries, its weights fp32
+    // (asynchronous) or WInt (deterministic)
+    leiden_status ensure_agg(int x, int64_t cap, bool det) {
         Agg &a = agg[x];
         if (!a.off) {
             ST(alloc(&a.off, n0 + 1));
             ST(alloc(&a.deg, n0));
         }
-        if (a.cap >= cap && a.idx) return LEIDEN_OK;
-        if (a.idx) free_one(a.idx);
+        const int wsz = det ? (int)sizeof(WInt) : (int)sizeof(float);
+        if (a.cap >= cap && a.idx && a.wsz >= wsz) return LEIDEN_OK;
+        if (a.cap < cap && a.idx) {
+            free_one(a.idx);
+            a.idx = nullptr;
+        }
         if (a.w) free_one(a.w);
-        a.idx = nullptr;
         a.w = nullptr;
-        ST(alloc(&a.idx, cap));
-        int32_t *w = nullptr;  // float or int32: 4 bytes either way
-        ST(alloc(&w, cap));
+        a.wsz = 0;
+        if (!a.idx) ST(alloc(&a.idx, cap));
+        a.cap = a.cap > cap ? a.cap : cap;
+        char *w = nullptr;
+        ST(alloc(&w, a.cap * wsz));
         a.w = w;
-        a.cap = cap;
+        a.wsz = wsz;
         return LEIDEN_OK;
     }
 };

@@ -476,8 +476,8 @@ cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t
 cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s) {
     if (c.tab_k1 <= c.tab_k0) return cudaSuccess;
     if (c.det) {
-        if (c.g.w_int) return tables_typed<Det, int32_t, int32_t>(c, list, blocks, s);
-        return tables_typed<Det, float, int32_t>(c, list, blocks, s);
+        if (c.g.w_int) return tables_typed<Det, WInt, WInt>(c, list, blocks, s);
+        return tables_typed<Det, float, WInt>(c, list, blocks, s);
     }
     return tables_typed<Async, float, float>(c, list, blocks, s);
 }
@@ -486,8 +486,8 @@ cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int6
                              cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     if (c.det) {
-        if (c.g.w_int) return agg_typed<Det, int32_t, int32_t>(c, bin, list, count, max_blocks, s);
-        return agg_typed<Det, float, int32_t>(c, bin, list, count, max_blocks, s);
+        if (c.g.w_int) return agg_typed<Det, WInt, WInt>(c, bin, list, count, max_blocks, s);
+        return agg_typed<Det, float, WInt>(c, bin, list, count, max_blocks, s);
     }
     return agg_typed<Async, float, float>(c, bin, list, count, max_blocks, s);
 }

@@ -107,7 +107,7 @@ __global__ void k_graph_zero_deg(const int32_t *deg, const int32_t *gid, int64_t
 __global__ void k_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                              const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
                              int32_t *passes, const int32_t *gpass, int32_t max_passes,
-                             const unsigned long long *gz) {
+                             const unsigned long long *gz, int32_t *fresh, bool refine_labels) {
     GRID_STRIDE(g, G) {
         if (state[g] != kGraphActive) {
             keep[g] = 0;
@@ -119,7 +119,7 @@ __global__ void k_graph_stop(const int64_t *vseg, const int64_t *pos, const int6
         // R4 leaves out the z vertices without edges (each is its own community)
         const int64_t z = (int64_t)gz[g], live = (b - a) - z;
         const bool stop = !(g2m[g] > 0)                              // reading R12: no edges
-                          || (li[g] <= 1 && nbound == ncomm)         // globally converged (R5')
+                          || (li[g] <= 1 && nbound == ncomm && fresh[g])  // globally converged (R5')
                           || (live > 0 && (double)(ncomm - z) / (double)live > agg_tol)  // low shrink (R4)
                           || (gpass && gpass[g] + 1 >= max_passes);   // its MAX_PASSES
         if (stop) {
@@ -127,6 +127,10 @@ __global__ void k_graph_stop(const int64_t *vseg, const int64_t *pos, const int6
             keep[g] = 0;
         } else {
             keep[g] = ncomm;
+            // R5': the next pass begins from singletons when every
+            // local-moving community is one refined community (move-based
+            // labels), or always under refine-based labels
+            fresh[g] = (refine_labels || nbound == ncomm) ? 1 : 0;
         }
     }
 }
@@ -168,7 +172,7 @@ __global__ void k_init_labels(const int32_t *label, int64_t n_cont, int64_t n, i
 // one thread per row of the appended graph
 __global__ void k_append_graph(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int64_t v0,
                                int64_t e0, bool w_int, int32_t g, int64_t *out_off, int32_t *out_deg,
-                               int32_t *out_idx, float *out_wf, int32_t *out_wi, int32_t *gid, int32_t *C0,
+                               int32_t *out_idx, float *out_wf, WInt *out_wi, int32_t *gid, int32_t *C0,
                                int64_t a0) {
     GRID_STRIDE(i, n) {
         const int64_t a = off[i], b = off[i + 1];
@@ -176,7 +180,7 @@ __global__ void k_append_graph(int64_t n, const int64_t *off, const int32_t *idx
         out_deg[v0 + i] = (int32_t)(b - a);
         for (int64_t e = a; e < b; ++e) {
             out_idx[e0 + e] = (int32_t)(v0 + idx[e]);
-            if (w_int) out_wi[e0 + e] = (int32_t)w[e];
+            if (w_int) out_wi[e0 + e] = (WInt)w[e];
             else out_wf[e0 + e] = w[e];
         }
         gid[v0 + i] = g;
@@ -300,13 +304,14 @@ cudaError_t launch_phase_init(const int32_t *state, int32_t G, int32_t *gdone, i
 cudaError_t launch_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                               const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
                               int32_t *passes, cudaStream_t s, const int32_t *gpass, int32_t max_passes,
-                              const int32_t *deg, const int32_t *gid, int64_t n, unsigned long long *gz) {
+                              const int32_t *deg, const int32_t *gid, int64_t n, unsigned long long *gz,
+                              int32_t *fresh, bool refine_labels) {
     if (G <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(gz, 0, sizeof(unsigned long long) * G, s);
     if (e != cudaSuccess) return e;
     if (n > 0) k_graph_zero_deg<<<grid_for(n, 256), 256, 0, s>>>(deg, gid, n, gz);
     k_graph_stop<<<grid_for(G, 256), 256, 0, s>>>(vseg, pos, pos2, li, g2m, agg_tol, G, state, keep, passes, gpass,
-                                                  max_passes, gz);
+                                                  max_passes, gz, fresh, refine_labels);
     return cudaGetLastError();
 }
 cudaError_t launch_renumber_batch(const int32_t *C, const int64_t *pos, const int32_t *gid, const int64_t *vseg,
@@ -344,7 +349,7 @@ cudaError_t launch_append_graph(int64_t n, const int64_t *off, const int32_t *id
                                 cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_append_graph<<<grid_for(n, 256), 256, 0, s>>>(n, off, idx, w, v0, e0, w_int, g, out_off, out_deg, out_idx,
-                                                    static_cast<float *>(out_w), static_cast<int32_t *>(out_w),
+                                                    static_cast<float *>(out_w), static_cast<WInt *>(out_w),
                                                     gid, C0, a0);
     return cudaGetLastError();
 }

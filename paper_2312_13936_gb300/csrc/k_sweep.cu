@@ -77,6 +77,8 @@ template <class P, class W> struct SV {
     unsigned *bar;
     int *err;
     unsigned long long *prof;
+    int32_t stall_block;            // testing aid: this block never arrives at a barrier
+    unsigned long long spin_limit;  // barrier polls before giving up
     // persistent sweep: act[k] == it + 1 marks step k as holding an eligible
     // vertex in sweep it (steps without one are skipped); null elsewhere
     int32_t *act;
@@ -102,7 +104,7 @@ template <class P, class W> struct SV {
 // sweep's per-graph slots they go to.
 template <class P> struct Sums {
     GAcc<typename P::acc> gain;
-    GAcc<long long> dgain;
+    GAcc<unsigned __int128> dgain;  // deterministic gains (dq: two words per slot)
     GAcc<unsigned long long> moved;
     typename P::tot *dq;
     unsigned long long *mv;
@@ -159,6 +161,8 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.bar = c.bar;
     a.err = c.err;
     a.prof = c.prof;
+    a.stall_block = c.stall_block;
+    a.spin_limit = c.spin_limit;
     a.act = c.act;
     a.rand_refine = c.rand_refine;
     a.rseed = c.rseed;
@@ -204,10 +208,19 @@ __device__ __forceinline__ typename P::acc kscale_of(const SV<P, W> &a, int32_t 
 template <class P, bool REFINE> __device__ __forceinline__ bool proposing(int32_t cur_step, int32_t cap_step) {
     return REFINE || P::det || cur_step >= cap_step;
 }
-// the gain of a local-moving proposal, in the accumulator's own type
-__device__ __forceinline__ void store_gain(long long *gain, int32_t v, long long g) { gain[v] = g; }
+// the gain of a local-moving proposal, in the key's own type (a 128-bit
+// gain takes the two words gain[2v], gain[2v+1])
+__device__ __forceinline__ void store_gain(long long *gain, int32_t v, __int128 g) {
+    gain[2 * (int64_t)v] = (long long)(unsigned long long)g;
+    gain[2 * (int64_t)v + 1] = (long long)(g >> 64);
+}
 __device__ __forceinline__ void store_gain(long long *gain, int32_t v, float g) {
     reinterpret_cast<float *>(gain)[v] = g;
+}
+__device__ __forceinline__ unsigned __int128 load_gain128(const long long *gain, int32_t v) {
+    const unsigned long long lo = (unsigned long long)__ldcg(&gain[2 * (int64_t)v]);
+    const unsigned long long hi = (unsigned long long)__ldcg(&gain[2 * (int64_t)v + 1]);
+    return ((unsigned __int128)hi << 64) | lo;
 }
 
 // Decision for vertex v (one thread, graph gv, key scale kscale) with best
@@ -216,15 +229,16 @@ __device__ __forceinline__ void store_gain(long long *gain, int32_t v, float g) 
 // marked unprocessed).
 template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ bool decide_sd(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
-                                          typename P::acc key, int32_t cand, typename P::acc kvd,
+                                          typename P::key key, int32_t cand, typename P::acc kvd,
                                           typename P::tot sd, Sums<P> &sm, int32_t cur_step, int32_t gv,
                                           typename P::acc kscale) {
     using A = typename P::acc;
     using T = typename P::tot;
+    using K = typename P::key;
     bool mv = false;
-    A g = 0;
+    K g = 0;
     if (cand != INT_MAX) {
-        const A ks = stay_key(kscale, kvd, Kv, sd, a.gamma);
+        const K ks = stay_key(kscale, kvd, Kv, sd, a.gamma);
         mv = key > ks;
         if (!REFINE && mv && cur_step >= a.cap_step) {
             // S2: where neighbours may move together, a single-vertex
@@ -233,39 +247,46 @@ __device__ __forceinline__ bool decide_sd(const SV<P, W> &a, int32_t v, int32_t 
         }
         g = key - ks;
     }
-    if (REFINE && !P::det && cur_step < a.cap_step) {
-        // Asynchronous refinement below the capped step: no two vertices of
-        // a step are adjacent, so the neighbour through which v saw cand
-        // stays in cand and nobody joins v while it leaves: the join is
-        // applied at once (the gain sum counts joins in this phase).
+    if constexpr (P::det) {
+        // the deterministic mode always proposes (an apply phase commits)
+        a.prop[v] = mv ? cand : -1;
+        if (!REFINE && mv) store_gain(a.gain, v, g);
+        return false;
+    } else {
+        if (REFINE && cur_step < a.cap_step) {
+            // Asynchronous refinement below the capped step: no two vertices
+            // of a step are adjacent, so the neighbour through which v saw
+            // cand stays in cand and nobody joins v while it leaves: the join
+            // is applied at once (the gain sum counts joins in this phase).
+            if (mv) {
+                atomic_add_acc(&a.Sig[d], -(T)Kv);
+                atomic_add_acc(&a.Sig[cand], (T)Kv);
+                atomicSub(&a.size[d], 1);
+                atomicAdd(&a.size[cand], 1);
+                a.C[v] = cand;
+                gacc_add(sm.gain, B, gv, (A)1, sm.mv);
+            }
+            return false;
+        }
+        if (proposing<P, REFINE>(cur_step, a.cap_step)) {
+            a.prop[v] = mv ? cand : -1;
+            if (!REFINE && mv) store_gain(a.gain, v, g);
+            return false;
+        }
         if (mv) {
             atomic_add_acc(&a.Sig[d], -(T)Kv);
             atomic_add_acc(&a.Sig[cand], (T)Kv);
             atomicSub(&a.size[d], 1);
             atomicAdd(&a.size[cand], 1);
             a.C[v] = cand;
-            gacc_add(sm.gain, B, gv, (A)1, sm.mv);
+            gacc_add(sm.gain, B, gv, g, sm.dq);
         }
-        return false;
-    }
-    if (proposing<P, REFINE>(cur_step, a.cap_step)) {
-        a.prop[v] = mv ? cand : -1;
-        if (!REFINE && mv) store_gain(a.gain, v, g);
-        return false;
-    }
-    if (mv) {
-        atomic_add_acc(&a.Sig[d], -(T)Kv);
-        atomic_add_acc(&a.Sig[cand], (T)Kv);
-        atomicSub(&a.size[d], 1);
-        atomicAdd(&a.size[cand], 1);
-        a.C[v] = cand;
-        gacc_add(sm.gain, B, gv, g, sm.dq);
     }
     return mv;
 }
 template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, typename P::acc Kv,
-                                       typename P::acc key, int32_t cand, typename P::acc kvd, Sums<P> &sm,
+                                       typename P::key key, int32_t cand, typename P::acc kvd, Sums<P> &sm,
                                        int32_t cur_step, int32_t gv, typename P::acc kscale) {
     return decide_sd<P, W, REFINE, B>(a, v, d, Kv, key, cand, kvd, ldm(&a.Sig[d]), sm, cur_step, gv, kscale);
 }
@@ -278,14 +299,18 @@ __device__ __forceinline__ bool decide(const SV<P, W> &a, int32_t v, int32_t d, 
 // weighted sampling, in an order-preserving form), and it stays positive, so
 // the vertex moves exactly when some gain is positive.
 template <class P, class W, bool REFINE>
-__device__ __forceinline__ typename P::acc cand_key(const SV<P, W> &a, const Sums<P> &sm, int32_t v, int32_t c,
-                                                    typename P::acc kk) {
-    if (!REFINE || P::det || !a.rand_refine) return kk;
-    if (!(kk > 0)) return AccLimits<typename P::acc>::lowest();
-    const uint64_t h = splitmix64_at(a.rseed + 0xD1B54A32D192ED03ULL * (uint64_t)sm.stamp,
-                                     ((uint64_t)(uint32_t)v << 32) | (uint32_t)c);
-    const float u = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
-    return (typename P::acc)(1.0f / (1.0f - logf(u) / (float)kk));
+__device__ __forceinline__ typename P::key cand_key(const SV<P, W> &a, const Sums<P> &sm, int32_t v, int32_t c,
+                                                    typename P::key kk) {
+    if constexpr (P::det || !REFINE) {
+        return kk;
+    } else {
+        if (!a.rand_refine) return kk;
+        if (!(kk > 0)) return AccLimits<typename P::key>::lowest();
+        const uint64_t h = splitmix64_at(a.rseed + 0xD1B54A32D192ED03ULL * (uint64_t)sm.stamp,
+                                         ((uint64_t)(uint32_t)v << 32) | (uint32_t)c);
+        const float u = ((float)(h >> 40) + 0.5f) * (1.0f / 16777216.0f);
+        return 1.0f / (1.0f - logf(u) / kk);
+    }
 }
 
 // act[k] = stamp, written only when it differs (a step's mark is read by
@@ -374,7 +399,7 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
                     c[k] = -1;
                 }
         A kvd = 0;
-        A key = AccLimits<A>::lowest();
+        typename P::key key = AccLimits<typename P::key>::lowest();
         int32_t cand = INT_MAX;
         int distinct = 0;
         const A ks = kscale_of<B>(a, gv);
@@ -386,7 +411,8 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
                 kvd = wt[k];
                 continue;
             }
-            const A kk = cand_key<P, W, REFINE>(a, sm, v, c[k], move_key(ks, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma));
+            const typename P::key kk =
+                cand_key<P, W, REFINE>(a, sm, v, c[k], move_key(ks, wt[k], Kv, ldm(&a.Sig[c[k]]), a.gamma));
             if (better(kk, c[k], key, cand)) {
                 key = kk;
                 cand = c[k];
@@ -462,7 +488,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
         const int dsrc = dball ? ((__ffs(dball) - 1) & (T - 1)) : 0;
         const A kvd_b = __shfl_sync(tmask, sum, dsrc, T);
         const A kvd = dball ? kvd_b : (A)0;
-        A key = AccLimits<A>::lowest();
+        typename P::key key = AccLimits<typename P::key>::lowest();
         int32_t cand = INT_MAX;
         const A ks = kscale_of<B>(a, gv);
         if (lead && c != d) {
@@ -471,7 +497,7 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
         }
 #pragma unroll
         for (int o = T / 2; o > 0; o >>= 1) {
-            const A ok = __shfl_xor_sync(tmask, key, o, T);
+            const typename P::key ok = kshfl_xor(tmask, key, o, T);
             const int32_t oc = __shfl_xor_sync(tmask, cand, o, T);
             if (better(ok, oc, key, cand)) {
                 key = ok;
@@ -539,7 +565,8 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
             if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
         }
         __syncwarp();
-        A key = AccLimits<A>::lowest(), kvd = 0;
+        typename P::key key = AccLimits<typename P::key>::lowest();
+        A kvd = 0;
         int32_t cand = INT_MAX;
         const A ks = kscale_of<B>(a, gv);
         for (int s = lane; s < S; s += 32) {
@@ -551,14 +578,15 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
                 kvd = sum;
                 continue;
             }
-            const A kk = cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma));
+            const typename P::key kk =
+                cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma));
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const A ok = __shfl_xor_sync(kFull, key, o);
+            const typename P::key ok = kshfl_xor(kFull, key, o);
             const int32_t oc = __shfl_xor_sync(kFull, cand, o);
             if (better(ok, oc, key, cand)) {
                 key = ok;
@@ -594,7 +622,8 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
                                           Sums<P> &sm, ProfCounts &pc) {
     using A = typename P::acc;
     __shared__ int s_elig, s_d, s_mv;
-    __shared__ A s_key[32], s_kvd[32];
+    __shared__ typename P::key s_key[32];
+    __shared__ A s_kvd[32];
     __shared__ int32_t s_cand[32];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
     const int64_t nblk = HUB ? (int64_t)a.hub_regions : (int64_t)gridDim.x;
@@ -639,7 +668,8 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
             if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
         }
         __syncthreads();
-        A key = AccLimits<A>::lowest(), kvd = 0;
+        typename P::key key = AccLimits<typename P::key>::lowest();
+        A kvd = 0;
         int32_t cand = INT_MAX;
         const A ks = kscale_of<B>(a, gv);
         for (int64_t s = tid; s < S; s += blockDim.x) {
@@ -651,14 +681,15 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
                 kvd = sum;
                 continue;
             }
-            const A kk = cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma));
+            const typename P::key kk =
+                cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, Kv, ldm(&a.Sig[k]), a.gamma));
             if (better(kk, k, key, cand)) {
                 key = kk;
                 cand = k;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const A ok = __shfl_xor_sync(kFull, key, o);
+            const typename P::key ok = kshfl_xor(kFull, key, o);
             const int32_t oc = __shfl_xor_sync(kFull, cand, o);
             if (better(ok, oc, key, cand)) {
                 key = ok;
@@ -673,7 +704,8 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
         }
         __syncthreads();
         if (tid == 0) {
-            A bk = s_key[0], kd = s_kvd[0];
+            typename P::key bk = s_key[0];
+            A kd = s_kvd[0];
             int32_t bc = s_cand[0];
             for (int w2 = 1; w2 < nw; ++w2) {
                 if (better(s_key[w2], s_cand[w2], bk, bc)) {
@@ -713,17 +745,22 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
 // own scan finds; the decision, one thread per hub; for an asynchronous
 // local-moving move, the neighbours' flags. A step whose hubs are all
 // ineligible ends after the first phase.
-__device__ __forceinline__ unsigned long long key_order(long long k) {
-    return (unsigned long long)k ^ 0x8000000000000000ULL;
+// order-preserving unsigned encodings of the keys: a 128-bit key as (high
+// word with its sign bit flipped, low word), compared high word first; an
+// fp32 key in the low 32 bits
+__device__ __forceinline__ void key_order(__int128 k, unsigned long long &hi, unsigned long long &lo) {
+    hi = (unsigned long long)(long long)(k >> 64) ^ 0x8000000000000000ULL;
+    lo = (unsigned long long)k;
 }
-__device__ __forceinline__ long long key_of_order(unsigned long long e, long long) {
-    return (long long)(e ^ 0x8000000000000000ULL);
+__device__ __forceinline__ __int128 key_of_order(unsigned long long hi, unsigned long long lo, __int128) {
+    return (__int128)(((unsigned __int128)(hi ^ 0x8000000000000000ULL) << 64) | lo);
 }
-__device__ __forceinline__ unsigned long long key_order(float k) {
+__device__ __forceinline__ void key_order(float k, unsigned long long &hi, unsigned long long &lo) {
     const unsigned u = __float_as_uint(k);
-    return (unsigned long long)((u & 0x80000000u) ? ~u : (u | 0x80000000u));
+    hi = (unsigned long long)((u & 0x80000000u) ? ~u : (u | 0x80000000u));
+    lo = 0ULL;
 }
-__device__ __forceinline__ float key_of_order(unsigned long long e, float) {
+__device__ __forceinline__ float key_of_order(unsigned long long e, unsigned long long, float) {
     const unsigned u = (unsigned)e;
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
@@ -790,7 +827,12 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                     int bits = ceil_log2(2 * dv);
                     if (bits < 6) bits = 6;
                     sz = 1LL << bits;
-                    a.hkey[j] = 0ULL;
+                    if (P::det) {
+                        a.hkey[2 * j] = 0ULL;
+                        a.hkey[2 * j + 1] = 0ULL;
+                    } else {
+                        a.hkey[j] = 0ULL;
+                    }
                     a.hcand[j] = INT_MAX;
                     a.hkvd[j] = 0;
                     a.hmv[j] = 0;
@@ -818,7 +860,7 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
             a.hinfo[2] = ne;
         }
     }
-    if (!grid_barrier(a.bar, a.err)) return false;
+    if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
     const int64_t np = __ldcg(&a.hinfo[0]), S = __ldcg(&a.hinfo[1]), E = __ldcg(&a.hinfo[2]);
     if (np == 0) return true;
     // insertion (the tables are clean: the last scan of a step clears every
@@ -846,18 +888,20 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
         if (key >= 0 && lane == __ffs(peers) - 1)
             if (!hash_add(a.hub_keys + tbase, a.hub_vals + tbase, bits, key, val)) set_error(a.err, kErrHashFull);
     }
-    if (!grid_barrier(a.bar, a.err)) return false;
-    // deterministic mode: the largest key per hub (pass 0), then the
-    // smallest community id with it (pass 1); asynchronous mode: one pass,
-    // key and id packed in one word (fp32 key above the complemented id, so
-    // that the largest word is the largest key with the smallest id). K_{v->d}
-    // from the slot of v's own community. The last pass clears the slots.
-    constexpr int npass = P::det ? 2 : 1;
+    if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
+    // deterministic mode: the largest key per hub -- its high word (pass 0),
+    // then its low word among the slots with that high word (pass 1) --
+    // then the smallest community id with that key (pass 2); asynchronous
+    // mode: one pass, key and id packed in one word (fp32 key above the
+    // complemented id, so that the largest word is the largest key with the
+    // smallest id). K_{v->d} from the slot of v's own community. The last
+    // pass clears the slots.
+    constexpr int npass = P::det ? 3 : 1;
     for (int pass = 0; pass < npass; ++pass) {
         for (int64_t s0 = gw * 32; s0 < S; s0 += warps * 32) {
             const int64_t s = s0 + lane;
             int64_t j = -1;
-            unsigned long long enc = 0ULL;
+            unsigned long long enc = 0ULL, enc_lo = 0ULL;
             int32_t k = -1;
             if (s < S) {
                 k = __ldcg(&a.hub_keys[s]);
@@ -875,8 +919,9 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                     } else {
                         const int32_t v = __ldg(&a.hubs[j]);
                         const int32_t gv = graph_of<B>(a, v);
-                        enc = key_order(cand_key<P, W, REFINE>(
-                            a, sm, v, k, move_key(kscale_of<B>(a, gv), sum, a.K[v], ldm(&a.Sig[k]), a.gamma)));
+                        const typename P::key kk = cand_key<P, W, REFINE>(
+                            a, sm, v, k, move_key(kscale_of<B>(a, gv), sum, a.K[v], ldm(&a.Sig[k]), a.gamma));
+                        key_order(kk, enc, enc_lo);
                         if (!P::det) enc = (enc << 32) | (unsigned long long)(~(uint32_t)k);
                         if (pass == 0) pc.v[3]++;
                     }
@@ -885,15 +930,22 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
             // one atomic per hub present in the warp
             const unsigned long long grp = k >= 0 ? (unsigned long long)j : ~0ULL;
             const unsigned peers = __match_any_sync(kFull, grp);
-            if (pass == 0) {
-                unsigned long long m = enc;
+            if (pass == 0 || (P::det && pass == 1)) {
+                // the largest high word (pass 0), the largest low word among
+                // the slots with the hub's largest high word (pass 1)
+                const bool in = k >= 0 && (pass == 0 || enc == __ldcg(&a.hkey[2 * j]));
+                unsigned long long x = in ? (pass == 0 ? enc : enc_lo) : 0ULL;
                 for (unsigned r = peers; r; r &= r - 1) {
-                    const unsigned long long o = __shfl_sync(peers, enc, __ffs(r) - 1);
-                    m = o > m ? o : m;
+                    const unsigned long long o = __shfl_sync(peers, x, __ffs(r) - 1);
+                    x = o > x ? o : x;
                 }
-                if (k >= 0 && lane == __ffs(peers) - 1) atomicMax(&a.hkey[j], m);
+                if (k >= 0 && lane == __ffs(peers) - 1) {
+                    const unsigned long long m = x;
+                    if (pass == 0) atomicMax(&a.hkey[P::det ? 2 * j : j], m);
+                    else if (m) atomicMax(&a.hkey[2 * j + 1], m);
+                }
             } else {
-                const bool best = k >= 0 && enc == __ldcg(&a.hkey[j]);
+                const bool best = k >= 0 && enc == __ldcg(&a.hkey[2 * j]) && enc_lo == __ldcg(&a.hkey[2 * j + 1]);
                 int32_t c = best ? k : INT_MAX;
                 for (unsigned r = peers; r; r &= r - 1) {
                     const int32_t o = __shfl_sync(peers, c, __ffs(r) - 1);
@@ -902,7 +954,7 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                 if (k >= 0 && lane == __ffs(peers) - 1 && c != INT_MAX) atomicMin(&a.hcand[j], c);
             }
         }
-        if (!grid_barrier(a.bar, a.err)) return false;
+        if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
     }
     // decisions
     for (int64_t p = tid; p < np; p += nthreads) {
@@ -910,15 +962,17 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
         const int32_t d = __ldcg(&a.hd[j]);
         const int32_t v = __ldg(&a.hubs[j]);
         const int32_t gv = graph_of<B>(a, v);
-        const unsigned long long best = __ldcg(&a.hkey[j]);
+        using K = typename P::key;
         int32_t c;
-        A bk;
+        K bk;
         if (P::det) {
             c = __ldcg(&a.hcand[j]);
-            bk = c == INT_MAX ? AccLimits<A>::lowest() : key_of_order(best, A(0));
+            bk = c == INT_MAX ? AccLimits<K>::lowest()
+                              : key_of_order(__ldcg(&a.hkey[2 * j]), __ldcg(&a.hkey[2 * j + 1]), K(0));
         } else {
+            const unsigned long long best = __ldcg(&a.hkey[j]);
             c = best == 0ULL ? INT_MAX : (int32_t)~(uint32_t)best;
-            bk = best == 0ULL ? AccLimits<A>::lowest() : key_of_order(best >> 32, A(0));
+            bk = best == 0ULL ? AccLimits<K>::lowest() : key_of_order(best >> 32, 0ULL, K(0));
         }
         const A kd = __ldcg(&a.hkvd[j]);
         const bool mv = decide<P, W, REFINE, B>(a, v, d, a.K[v], bk, c, kd, sm, cur_step, gv, kscale_of<B>(a, gv));
@@ -933,7 +987,7 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     }
     if (!REFINE && !P::det) {
         // an asynchronous local-moving move flags the hub's neighbours
-        if (!grid_barrier(a.bar, a.err)) return false;
+        if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
         for (int64_t x = tid; x < E; x += nthreads) {
             const int64_t p = range_at(a.heoff, np, x);
             const int64_t j = __ldcg(&a.hj[p]);
@@ -973,7 +1027,8 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
             atomicAdd(&a.size[c], 1);
             a.C[v] = c;
             if (P::det)
-                gacc_add(sm.dgain, B, graph_of<B>(a, v), ldm(&a.gain[v]), reinterpret_cast<long long *>(sm.dq));
+                gacc_add(sm.dgain, B, graph_of<B>(a, v), load_gain128(a.gain, v),
+                         reinterpret_cast<unsigned long long *>(sm.dq));
             else
                 gacc_add(sm.gain, B, graph_of<B>(a, v),
                          (typename P::acc)__ldcg(reinterpret_cast<const float *>(a.gain) + v), sm.dq);
@@ -1019,6 +1074,14 @@ __device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_
 // ------------------------------------------------------- persistent sweep
 constexpr int kCoopThreads = 256;
 
+// a sweep's gain sum of graph g: two words per slot (deterministic, 128 bits)
+// or one fp64 word
+__device__ __forceinline__ double gain_sum(long long *dq, int64_t g) {
+    const unsigned long long *w = reinterpret_cast<const unsigned long long *>(dq) + 2 * g;
+    return u128_words_to_double(__ldcg(&w[0]), __ldcg(&w[1]));
+}
+__device__ __forceinline__ double gain_sum(double *dq, int64_t g) { return __ldcg(&dq[g]); }
+
 // shared-memory tables: 8 warp tables of kWarpSlots slots, or one block table
 // of kBlockSlots slots (values first, then keys)
 template <class A> constexpr size_t table_bytes() { return (sizeof(A) + sizeof(int32_t)) * kBlockSlots; }
@@ -1045,12 +1108,15 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
     A *svals = table_vals<A>();
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr bool batch = B;
+    // testing aid: this block ends without arriving at any barrier, so the
+    // others' bounded wait runs out (kErrTimeout) and the launch ends
+    if ((int32_t)blockIdx.x == a.stall_block) return;
     ProfCounts pc;
     int32_t it = 0;
     bool ok = true;
     while (ok && it < a.max_it) {
         Sums<P> sm;
-        sm.dq = a.dq_arr + (size_t)it * a.G;
+        sm.dq = a.dq_arr + (size_t)it * a.G * (P::det ? 2 : 1);  // deterministic: two words per slot
         sm.mv = a.moved_arr + (size_t)it * a.G;
         sm.stamp = it + 1;
         if (a.act) {
@@ -1066,7 +1132,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                 const bool e = REFINE ? ldm(&a.size[ldm(&a.C[v])]) == 1 : ldm(&a.unproc[v]) != 0;
                 if (e) mark_step(a.act, a.step[v], sm.stamp);
             }
-            if (!(ok = grid_barrier(a.bar, a.err))) break;
+            if (!(ok = grid_barrier(a.bar, a.err, a.spin_limit))) break;
         }
         int64_t hub_j0 = 0;  // ordinal of the step's first hub
         for (int32_t k = 0; k < a.nsteps && ok; ++k) {
@@ -1097,14 +1163,14 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                 }
                 hub_j0 += b7 - b6;
             }
-            if (!(ok = grid_barrier(a.bar, a.err))) break;
+            if (!(ok = grid_barrier(a.bar, a.err, a.spin_limit))) break;
             // apply phase: deterministic mode, and proposals where neighbours
             // may share a step (below the capped step the asynchronous mode
             // moves and joins at once)
             if (P::det || k >= a.cap_step) {
                 if (REFINE) run_refine_apply<P, W, B>(a, list, b0, b8, k, sm);
                 else run_move_apply<P, W, B>(a, list, b0, b8, sm);
-                if (!(ok = grid_barrier(a.bar, a.err))) break;
+                if (!(ok = grid_barrier(a.bar, a.err, a.spin_limit))) break;
             }
         }
         if (!ok) break;
@@ -1115,7 +1181,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                 if (!P::det) gacc_flush(sm.gain, sm.mv);
                 gacc_flush(sm.moved, sm.mv);
             } else if (P::det) {
-                gacc_flush(sm.dgain, reinterpret_cast<long long *>(sm.dq));
+                gacc_flush(sm.dgain, reinterpret_cast<unsigned long long *>(sm.dq));
             } else {
                 gacc_flush(sm.gain, sm.dq);
             }
@@ -1125,13 +1191,13 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
             moved = warp_sum(moved);
             if (lane == 0 && moved) atomicAdd(&sm.mv[0], moved);
         } else if (P::det) {
-            const long long g = warp_sum(sm.dgain.v);
-            if (lane == 0 && g) atomic_add_acc(reinterpret_cast<long long *>(&sm.dq[0]), g);
+            const unsigned __int128 g = warp_sum_u128(sm.dgain.v);
+            if (lane == 0 && g) atomic_add_u128(reinterpret_cast<unsigned long long *>(sm.dq), g);
         } else {
             const A g = warp_sum(sm.gain.v);
             if (lane == 0 && g != (A)0) atomic_add_acc(&sm.dq[0], (T)g);
         }
-        if (!(ok = grid_barrier(a.bar, a.err))) break;
+        if (!(ok = grid_barrier(a.bar, a.err, a.spin_limit))) break;
         bool stop;
         if (batch) {
             // every graph still running takes its own test; graphs that
@@ -1145,7 +1211,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
                     sg = __ldcg(&sm.mv[g]) == 0ULL || a.single_sweep;
                 } else {
                     const double tm = a.g2m[g];
-                    const double sum = (double)ldm(&sm.dq[g]);
+                    const double sum = gain_sum(sm.dq, g);
                     // a graph without edges (2m = 0) has nothing to move
                     const double tau = a.gtau ? a.gtau[g] : a.tau;
                     sg = !(tm > 0) || (P::det ? 2.0 * sum / (tm * tm) : 2.0 * sum / tm) <= tau;
@@ -1159,7 +1225,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
             }
             running = warp_sum(running);
             if (lane == 0 && running) atomicAdd(&a.gactive[it], running);
-            if (!(ok = grid_barrier(a.bar, a.err))) break;
+            if (!(ok = grid_barrier(a.bar, a.err, a.spin_limit))) break;
             stop = __ldcg(&a.gactive[it]) == 0u;
         } else if (REFINE) {
             stop = __ldcg(&sm.mv[0]) == 0ULL || a.single_sweep;
@@ -1167,7 +1233,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
             // sweep delta-modularity from the summed gains: 2 num / (2m)^2
             // (deterministic, reading S4) or 2 sum / 2m (asynchronous)
             const double tm = a.two_m_d;
-            const double sum = (double)ldm(&sm.dq[0]);
+            const double sum = gain_sum(sm.dq, 0);
             const double dq = P::det ? 2.0 * sum / (tm * tm) : 2.0 * sum / tm;
             stop = dq <= a.tau;
         }
@@ -1259,8 +1325,8 @@ __global__ void __launch_bounds__(256) k_move_apply(SV<P, W> a, const int32_t *_
     Sums<P> sm = scalar_sums(a);
     run_move_apply<P, W, false>(a, list, 0, count, sm);
     if (P::det) {
-        const long long g = warp_sum(sm.dgain.v);
-        if ((threadIdx.x & 31) == 0 && g != 0) atomic_add_acc(reinterpret_cast<long long *>(a.dq_acc), g);
+        const unsigned __int128 g = warp_sum_u128(sm.dgain.v);
+        if ((threadIdx.x & 31) == 0 && g) atomic_add_u128(reinterpret_cast<unsigned long long *>(a.dq_acc), g);
     } else {
         flush_gain<P, W, false>(a, sm);
     }
@@ -1359,7 +1425,7 @@ cudaError_t launch_sweep_eval(const SweepCtx &c, int bin, const int32_t *list, i
                               cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     if (c.det) {
-        if (c.g.w_int) return eval_mode<Det, int32_t>(c, bin, list, count, max_blocks, s);
+        if (c.g.w_int) return eval_mode<Det, WInt>(c, bin, list, count, max_blocks, s);
         return eval_mode<Det, float>(c, bin, list, count, max_blocks, s);
     }
     return eval_mode<Async, float>(c, bin, list, count, max_blocks, s);
@@ -1368,7 +1434,7 @@ cudaError_t launch_sweep_eval(const SweepCtx &c, int bin, const int32_t *list, i
 cudaError_t launch_move_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     if (!c.det) k_move_apply<Async, float><<<apply_grid(count), 256, 0, s>>>(view<Async, float>(c), list, count);
-    else if (c.g.w_int) k_move_apply<Det, int32_t><<<apply_grid(count), 256, 0, s>>>(view<Det, int32_t>(c), list, count);
+    else if (c.g.w_int) k_move_apply<Det, WInt><<<apply_grid(count), 256, 0, s>>>(view<Det, WInt>(c), list, count);
     else k_move_apply<Det, float><<<apply_grid(count), 256, 0, s>>>(view<Det, float>(c), list, count);
     return cudaGetLastError();
 }
@@ -1376,7 +1442,7 @@ cudaError_t launch_move_apply(const SweepCtx &c, const int32_t *list, int64_t co
 cudaError_t launch_refine_apply(const SweepCtx &c, const int32_t *list, int64_t count, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     if (c.det) {
-        if (c.g.w_int) k_refine_apply<Det, int32_t><<<apply_grid(count), 256, 0, s>>>(view<Det, int32_t>(c), list, count);
+        if (c.g.w_int) k_refine_apply<Det, WInt><<<apply_grid(count), 256, 0, s>>>(view<Det, WInt>(c), list, count);
         else k_refine_apply<Det, float><<<apply_grid(count), 256, 0, s>>>(view<Det, float>(c), list, count);
     } else {
         k_refine_apply<Async, float><<<apply_grid(count), 256, 0, s>>>(view<Async, float>(c), list, count);
@@ -1386,7 +1452,7 @@ cudaError_t launch_refine_apply(const SweepCtx &c, const int32_t *list, int64_t 
 
 int sweep_coop_blocks_per_sm(bool det, bool w_int, bool refine) {
     if (det) {
-        if (w_int) return refine ? coop_blocks_typed<Det, int32_t, true>() : coop_blocks_typed<Det, int32_t, false>();
+        if (w_int) return refine ? coop_blocks_typed<Det, WInt, true>() : coop_blocks_typed<Det, WInt, false>();
         return refine ? coop_blocks_typed<Det, float, true>() : coop_blocks_typed<Det, float, false>();
     }
     return refine ? coop_blocks_typed<Async, float, true>() : coop_blocks_typed<Async, float, false>();
@@ -1395,7 +1461,7 @@ int sweep_coop_blocks_per_sm(bool det, bool w_int, bool refine) {
 cudaError_t launch_sweep_coop(const SweepCtx &c, const int32_t *list, int grid, cudaStream_t s) {
     if (c.det) {
         if (c.g.w_int)
-            return c.refine ? coop_typed<Det, int32_t, true>(c, list, grid, s) : coop_typed<Det, int32_t, false>(c, list, grid, s);
+            return c.refine ? coop_typed<Det, WInt, true>(c, list, grid, s) : coop_typed<Det, WInt, false>(c, list, grid, s);
         return c.refine ? coop_typed<Det, float, true>(c, list, grid, s) : coop_typed<Det, float, false>(c, list, grid, s);
     }
     return c.refine ? coop_typed<Async, float, true>(c, list, grid, s) : coop_typed<Async, float, false>(c, list, grid, s);

@@ -310,7 +310,7 @@ cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *t
         auto *k = static_cast<long long *>(K);
         auto *t = static_cast<long long *>(two_m);
         if (g.w_int)
-            k_vertex_weights<long long, long long, int32_t><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const int32_t *)g.w, k, t);
+            k_vertex_weights<long long, long long, WInt><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const WInt *)g.w, k, t);
         else k_vertex_weights<long long, long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
     } else {
         k_vertex_weights<float, double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w,

@@ -34,8 +34,20 @@ __host__ __device__ inline int degree_bin(int64_t d) {
     return d <= 0 ? 0 : d <= kThreadMaxDeg ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= kWarpMaxDeg ? 4 : d <= kBlockMaxDeg ? 5 : 6;
 }
 
+// Weights of aggregated graphs in the deterministic mode: exact integers
+// up to 2m (below 2^53), held in int64.
+using WInt = long long;
+
+// A 128-bit unsigned sum held as two words as a double: (double)hi * 2^64 +
+// (double)lo, each conversion and the sum rounded to nearest (the
+// deterministic mode's sweep delta-modularity takes exactly these
+// roundings, reading S4).
+__host__ __device__ inline double u128_words_to_double(unsigned long long lo, unsigned long long hi) {
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
 // The current graph G' (a holey CSR, paper Fig. 5): row i is
-// idx/w[off[i] .. off[i]+deg[i]). Weights are float, or int32 in
+// idx/w[off[i] .. off[i]+deg[i]). Weights are float, or WInt (int64) in
 // deterministic mode after the first aggregation.
 struct GraphView {
     int64_t n = 0;
@@ -58,7 +70,7 @@ struct SweepCtx {
     int32_t *size = nullptr;  // members per community
     uint8_t *unproc = nullptr;    // Algorithm 2 pruning flags (1 = unprocessed)
     int32_t *prop = nullptr;      // proposed target (-1 none)
-    long long *gain = nullptr;    // det: key gain of the proposal
+    long long *gain = nullptr;    // key gain of a proposal: two words per vertex (det, 128 bits) or fp32
     const int32_t *step = nullptr;  // schedule step of every vertex
     double two_m_f = 0;
     long long two_m_i = 0;
@@ -69,10 +81,10 @@ struct SweepCtx {
     // persistent phase: at most max_it sweeps, convergence tested on the device
     int32_t max_it = 1, single_sweep = 0;
     double tau = 0;
-    void *dq_arr = nullptr;                 // max_it gain sums (acc type), zeroed
+    void *dq_arr = nullptr;                 // max_it x G gain sums, zeroed (det: two words each)
     unsigned long long *moved_arr = nullptr;  // max_it move counts, zeroed
     int32_t *iters_out = nullptr;           // sweeps executed
-    void *dq_acc = nullptr;       // sweep delta-modularity numerator (acc type)
+    void *dq_acc = nullptr;       // sweep delta-modularity numerator (det: two words, lo and hi)
     unsigned long long *moved = nullptr;  // refinement: accepted moves
     int32_t *hub_keys = nullptr;  // global tables for bin 6 (one region per block)
     void *hub_vals = nullptr;
@@ -95,6 +107,11 @@ struct SweepCtx {
     unsigned *bar = nullptr;      // grid barrier state (2 words, zero-initialised once)
     int *err = nullptr;
     unsigned long long *prof = nullptr;  // 8 work counters of this launch's class, or null
+    // testing aid for the timeout path: block stall_block (-1: none) of a
+    // persistent launch ends without arriving at the barrier; the others
+    // poll at most spin_limit times
+    int32_t stall_block = -1;
+    unsigned long long spin_limit = 1ULL << 24;
     // A batch of G independent graphs swept as one (a disjoint union): every
     // vertex uses its own graph's 2m, and every graph converges on its own.
     // gid == null means one graph (index 0) and the scalars above.
@@ -135,7 +152,7 @@ struct AggCtx {
     const int64_t *out_off = nullptr; // offsets of G'' (scan of community total degree)
     int32_t *out_deg = nullptr;
     int32_t *out_idx = nullptr;
-    void *out_w = nullptr;            // float (async) or int32 (det)
+    void *out_w = nullptr;            // float (async) or WInt (det)
     void *out_K = nullptr;            // K'' (acc type): row sums of G''
     int64_t ncomm = 0;
     // bin 6 (communities of more than kBlockMaxDeg member entries): one
@@ -162,6 +179,15 @@ cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t
 // entries go into its community's table (long rows by the whole warp), then
 // one block per table writes its distinct entries as the community's row
 cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s);
+
+// Rows of a holey CSR (n rows, cap = offsets[n] slots, weights WInt)
+// sorted by target in place, each row's unused slots kept after its fill
+// (reading R10, the deterministic mode); tmp >= sort_rows_tmp_bytes(cap)
+// bytes of device scratch. Synchronises the stream when cap > 2^30 (the row
+// offsets are then read on the host to cut the rows into chunks).
+size_t sort_rows_tmp_bytes(int64_t cap);
+cudaError_t launch_sort_rows(int64_t n, const int64_t *off, const int32_t *deg, int32_t *idx, WInt *w, int64_t cap,
+                             void *tmp, cudaStream_t s);
 
 // ---- utilities (k_util.cu)
 cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s);
@@ -199,8 +225,14 @@ cudaError_t launch_schedule(const GraphView &g, uint64_t state, int32_t L, int32
                             int32_t *step, cudaStream_t s, const int32_t *gid = nullptr,
                             const int64_t *vseg = nullptr, const int32_t *gpass = nullptr, bool long_rows = true,
                             const int32_t *gL = nullptr);
-// layer cap of a graph when schedule_layers is 0 (reading S0)
-inline int32_t auto_layers(int64_t maxdeg) { return maxdeg > kBlockMaxDeg ? 1000 : 32; }
+// layer cap of a graph of n vertices and nnz entries whose largest degree
+// is maxdeg, when schedule_layers is 0 (reading S0): 1000 for a heavy-tailed
+// graph, whose largest degree exceeds 64 times its mean degree nnz / n,
+// else 32
+constexpr int32_t kLayersHeavy = 1000, kLayersLight = 32;
+inline int32_t auto_layers(int64_t maxdeg, int64_t n, int64_t nnz) {
+    return (__int128)maxdeg * n > (__int128)64 * nnz ? kLayersHeavy : kLayersLight;
+}
 // key[i] = step*kNumBins + bin (step-major: one list per step and bin), or
 // bin*nsteps + step (bin-major: one step-ordered list per bin); vertices
 // without edges get key nsteps*kNumBins (a trailing bucket)
@@ -236,19 +268,22 @@ cudaError_t launch_phase_init(const int32_t *state, int32_t G, int32_t *gdone, i
 // tolerance; active graphs that stop become finishing; keep[g] = refined
 // communities of the graphs that go on (0 otherwise); passes[g]++ for active
 // graphs. With gpass (graphs at different passes) a graph also stops when
-// gpass[g] + 1 reaches max_passes.
+// gpass[g] + 1 reaches max_passes. fresh[g] = 1 when the graph's pass began
+// with every super-vertex in its own community (R5' stops only such a
+// pass); it is set for the next pass of the graphs that go on.
 // (deg, gid, n: the current graph; reading R4 leaves each graph's vertices
 // without edges out of its ratio, counted into gz, G entries of scratch)
 cudaError_t launch_graph_stop(const int64_t *vseg, const int64_t *pos, const int64_t *pos2, const int32_t *li,
                               const double *g2m, double agg_tol, int32_t G, int32_t *state, int64_t *keep,
                               int32_t *passes, cudaStream_t s, const int32_t *gpass, int32_t max_passes,
-                              const int32_t *deg, const int32_t *gid, int64_t n, unsigned long long *gz);
+                              const int32_t *deg, const int32_t *gid, int64_t n, unsigned long long *gz,
+                              int32_t *fresh, bool refine_labels);
 // C' at the start of local-moving: the first n_cont vertices continue with
 // their move-based labels, the others start as singletons
 cudaError_t launch_init_labels(const int32_t *label, int64_t n_cont, int64_t n, int32_t *Cp, cudaStream_t s);
 // append graph g (n rows of a CSR with local indices and fp32 weights) to the
 // holey CSR of a union at row v0 and entry e0: out_off/out_deg/out_idx (ids
-// + v0)/out_w (fp32, or int32 when w_int), gid[v0+i] = g, and the
+// + v0)/out_w (fp32, or WInt when w_int), gid[v0+i] = g, and the
 // dendrogram of its vertices C0[a0+i] = v0+i
 cudaError_t launch_append_graph(int64_t n, const int64_t *off, const int32_t *idx, const float *w, int64_t v0,
                                 int64_t e0, bool w_int, int32_t g, int64_t *out_off, int32_t *out_deg,

@@ -37,7 +37,7 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
         return LEIDEN_ERR_UNSUPPORTED;
     }
     // the largest layer cap a graph can take (reading S0)
-    const int32_t nkeys = ((prm.schedule_layers > 0 ? prm.schedule_layers : auto_layers(INT64_MAX)) - 1 +
+    const int32_t nkeys = ((prm.schedule_layers > 0 ? prm.schedule_layers : kLayersHeavy) - 1 +
                            prm.schedule_buckets) * kNumBins;
     if (nkeys + 1 > 8192) {
         set_last_error("schedule_layers + schedule_buckets too large");
@@ -58,8 +58,8 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
     v.cap_v = max_vertices;
     v.cap_e = max_entries;
     v.cap_g = max_graphs;
-    ST(q.ensure_agg(0, max_entries));
-    ST(q.ensure_agg(1, max_entries));
+    ST(q.ensure_agg(0, max_entries, prm.mode == LEIDEN_DETERMINISTIC));
+    ST(q.ensure_agg(1, max_entries, prm.mode == LEIDEN_DETERMINISTIC));
     ST(q.ensure_part_tmp(partition_tmp_bytes(max_vertices, nkeys + 1)));
     ST(q.ensure_phase(prm.max_iterations, max_graphs));
     v.arena[0] = q.C0;
@@ -129,14 +129,14 @@ static leiden_status upload(Handle::Impl &q, Request &r, const int64_t *off, con
         return e == 2 ? LEIDEN_ERR_NOT_SYMMETRIC : LEIDEN_ERR_INVALID;
     }
     const int32_t pl = q.srv->prm.schedule_layers;
-    r.L = pl > 0 ? pl : auto_layers(q.hsc->maxdeg);
+    r.L = pl > 0 ? pl : auto_layers(q.hsc->maxdeg, n, m);
     if (q.srv->prm.mode == LEIDEN_DETERMINISTIC) {
         if (q.hsc->nonint) {
             set_last_error("deterministic mode needs integer weights");
             return LEIDEN_ERR_UNSUPPORTED;
         }
-        if (q.hsc->wsum >= 2147483648.0) {
-            set_last_error("deterministic mode needs 2m < 2^31");
+        if (q.hsc->wsum >= kDetMaxTwoM) {
+            set_last_error("deterministic mode needs 2m < 2^53");
             return LEIDEN_ERR_OVERFLOW;
         }
     }
@@ -266,6 +266,7 @@ leiden_status Handle::server_step(int32_t *finished_out) {
         CK(launch_append_graph(r.n, r.off, r.idx, r.w, v.n_union, v.e_union, det, (int32_t)v.inflight.size(), u.off,
                                u.deg, u.idx, u.w, q.gidA, v.arena[v.arena_cur], v.arena_n, s));
         r.pass = 0;
+        r.fresh = 1;
         r.n_cur = r.n;
         r.arena = v.arena_n;
         v.n_union += r.n;
@@ -279,11 +280,14 @@ leiden_status Handle::server_step(int32_t *finished_out) {
         if (finished_out) *finished_out = nfin;
         return LEIDEN_OK;
     }
-    // ---- per-graph arrays of this step, in union order
+    // ---- per-graph arrays of this step, in union order; the error word
+    // starts clean (an earlier step's failure must not outlive it)
+    CK(cudaMemsetAsync(&q.dsc->err, 0, sizeof(int), s));
     const int32_t K = (int32_t)v.inflight.size();
     v.hvseg.assign(K + 1, 0);
     v.hvseg0.assign(K + 1, 0);
     v.hpass.assign(K, 0);
+    v.hfresh.assign(K, 1);
     v.hstate.assign(K, kGraphActive);
     v.htau.assign(K, 0.0);
     v.hL.assign(K, 0);
@@ -295,12 +299,14 @@ leiden_status Handle::server_step(int32_t *finished_out) {
         v.hvseg[k + 1] = v.hvseg[k] + r.n_cur;
         v.hvseg0[k + 1] = v.hvseg0[k] + r.n;
         v.hpass[k] = r.pass;
+        v.hfresh[k] = r.fresh;
         v.htau[k] = prm.tolerance / std::pow(prm.tolerance_drop, (double)r.pass);  // threshold scaling
     }
     CK(cudaMemcpyAsync(q.vseg, v.hvseg.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(q.vseg0, v.hvseg0.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(v.gpass, v.hpass.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(q.gstate, v.hstate.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(q.gfresh, v.hfresh.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(v.gtau, v.htau.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(v.gL, v.hL.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
     CK(launch_graph_ids(q.vseg, K, v.n_union, q.gidA, s));
@@ -336,6 +342,7 @@ leiden_status Handle::server_step(int32_t *finished_out) {
     v.steps++;
     // ---- graphs that stopped leave with their results
     CK(cudaMemcpyAsync(v.hstate.data(), q.gstate, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(v.hfresh.data(), q.gfresh, sizeof(int32_t) * K, cudaMemcpyDeviceToHost, s));
     if (!stop) CK(cudaMemcpyAsync(v.hvseg.data(), q.vseg, sizeof(int64_t) * (K + 1), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     std::vector<int64_t> next;
@@ -346,6 +353,7 @@ leiden_status Handle::server_step(int32_t *finished_out) {
         if (!stop && v.hstate[k] == kGraphActive) {  // goes on: pack its dendrogram
             rq.n_cur = v.hvseg[k + 1] - v.hvseg[k];
             rq.pass++;
+            rq.fresh = v.hfresh[k];
             CK(cudaMemcpyAsync(dst_arena + arena_next, q.C0 + rq.arena, sizeof(int32_t) * rq.n,
                                cudaMemcpyDeviceToDevice, s));
             rq.arena = arena_next;

@@ -5,12 +5,12 @@ Every graph of a batch must come out as it does alone. Deterministic mode:
 membership, pass count, community count and modularity bit-exact against
 single-graph runs of the same library, and membership against the oracle's
 SYNC mode. Asynchronous mode: every community connected, reported modularity
-within 1e-9 of the recomputation, and modularity against the oracle's SEQ
-mode within 0.005 on the batch mean. A single small graph may end in
-another local optimum than SEQ's sequential order finds (on the sparse SBM
-graphs here the deterministic schedule itself lands up to 0.008 below SEQ on
-one graph and 0.002 above on the mean), so each graph is held to a looser
-floor of 0.04; the same holds for a graph alone and in the batch.
+within 1e-9 of the recomputation, the batch's mean modularity within 0.005
+of the oracle SEQ mean, and every graph's expected modularity (the mean over
+schedule seeds) within 0.005 of the oracle's sequential reference (the lower
+of its identity-order run and its mean over random vertex orders): on these
+small sparse graphs one sequential order alone spreads by up to 0.018 under
+relabelling, and one asynchronous draw by as much.
 """
 import numpy as np
 import pytest
@@ -18,12 +18,11 @@ import pytest
 import gen
 import oracle
 import paper_2312_13936_gb300 as lg
-from tests._gpu import run_gpu
+from tests._gpu import SEEDS, run_gpu, seq_reference
 
 pytestmark = pytest.mark.gpu
 
-Q_TOL_ASYNC = 0.005        # on the mean over a batch's graphs
-Q_TOL_ASYNC_GRAPH = 0.04   # on each graph
+Q_TOL_ASYNC = 0.005        # modularity tolerance of the asynchronous mode
 Q_REL_REPORT = 1e-9
 
 
@@ -95,29 +94,45 @@ def test_batch_deterministic_schedule_and_limits():
 def test_batch_async_quality(flags):
     b = gen.sbm_batch(40, seed=12, nmin=500, nmax=8000)
     graphs = [b.graph(g) for g in range(b.num_graphs)]
-    vseg, memb, q, st, passes, comm = run_batch(graphs, lg.LEIDEN_ASYNC, flags=flags)
     oflags = oracle.REFINE_SINGLE_SWEEP if flags & lg.FLAG_REFINE_SINGLE_SWEEP else 0
     seq_q = np.array([oracle.leiden(G, mode=oracle.SEQ, flags=oflags).modularity for G in graphs])
-    assert q.mean() >= seq_q.mean() - Q_TOL_ASYNC, (q.mean(), seq_q.mean())
-    for g, G in enumerate(graphs):
-        mb = memb[vseg[g]:vseg[g + 1]]
-        assert q[g] >= seq_q[g] - Q_TOL_ASYNC_GRAPH, (g, q[g], seq_q[g])
-        assert oracle.disconnected(G, mb)[0] == 0, g
-        q_re = oracle.modularity(G, mb)
-        assert abs(q[g] - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re)), g
-        first = np.unique(mb, return_index=True)[1]
-        assert np.array_equal(np.sort(first), first)
-        assert mb.max() + 1 == comm[g]
+    ref = np.array([seq_reference(G, oflags) for G in graphs])
+    qs = []
+    for seed in range(SEEDS):
+        vseg, memb, q, st, passes, comm = run_batch(graphs, lg.LEIDEN_ASYNC, flags=flags, seed=seed)
+        qs.append(q)
+        assert q.mean() >= seq_q.mean() - Q_TOL_ASYNC, (seed, q.mean(), seq_q.mean())
+        for g, G in enumerate(graphs):
+            mb = memb[vseg[g]:vseg[g + 1]]
+            assert oracle.disconnected(G, mb)[0] == 0, g
+            q_re = oracle.modularity(G, mb)
+            assert abs(q[g] - q_re) <= Q_REL_REPORT * max(1.0, abs(q_re)), g
+            first = np.unique(mb, return_index=True)[1]
+            assert np.array_equal(np.sort(first), first)
+            assert mb.max() + 1 == comm[g]
+    expect = np.mean(qs, axis=0)
+    for g in range(len(graphs)):
+        assert expect[g] >= ref[g] - Q_TOL_ASYNC, (g, expect[g], ref[g])
 
 
 def test_batch_async_same_alone_and_in_batch():
+    """Alone and in the batch, every graph's expected modularity is within
+    the tolerance of the oracle's sequential reference, and the batch's mean
+    modularity is within the tolerance of the mean of the graphs alone."""
     graphs = mixed_graphs()
-    vseg, memb, q, _, _, _ = run_batch(graphs, lg.LEIDEN_ASYNC)
-    alone = np.array([run_gpu(G, lg.LEIDEN_ASYNC)[1] for G in graphs])
-    assert abs(q.mean() - alone.mean()) <= Q_TOL_ASYNC, (q.mean(), alone.mean())
-    for g, G in enumerate(graphs):
-        assert abs(q[g] - alone[g]) <= Q_TOL_ASYNC_GRAPH, (g, q[g], alone[g])
-        assert oracle.disconnected(G, memb[vseg[g]:vseg[g + 1]])[0] == 0
+    ref = np.array([seq_reference(G) for G in graphs])
+    qb, qa = [], []
+    for seed in range(SEEDS):
+        vseg, memb, q, _, _, _ = run_batch(graphs, lg.LEIDEN_ASYNC, seed=seed)
+        qb.append(q)
+        qa.append([run_gpu(G, lg.LEIDEN_ASYNC, seed=seed)[1] for G in graphs])
+        for g, G in enumerate(graphs):
+            assert oracle.disconnected(G, memb[vseg[g]:vseg[g + 1]])[0] == 0
+    qb, qa = np.mean(qb, axis=0), np.mean(qa, axis=0)
+    assert abs(qb.mean() - qa.mean()) <= Q_TOL_ASYNC, (qb.mean(), qa.mean())
+    for g in range(len(graphs)):
+        assert qb[g] >= ref[g] - Q_TOL_ASYNC, (g, qb[g], ref[g])
+        assert qa[g] >= ref[g] - Q_TOL_ASYNC, (g, qa[g], ref[g])
 
 
 def test_batch_of_one_equals_single_run():
