@@ -84,6 +84,9 @@ def _lib():
         lib.gg_sbm_batch.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, P64] + out
         lib.gg_sbm_batch.restype = ctypes.c_int
+        lib.gg_rmat_edges.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_uint64, P32, P32, ctypes.POINTER(ctypes.c_int64)]
+        lib.gg_rmat_edges.restype = ctypes.c_int
         lib.gg_free.argtypes = [ctypes.c_void_p]
         lib.gg_free.restype = None
         _lib_handle = lib
@@ -131,6 +134,28 @@ def rmat(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: floa
          seed: int = 3) -> CSR:
     """Symmetrised, deduplicated R-MAT graph without self-loops, unit weights."""
     return _call(_lib().gg_rmat, scale, edge_factor, a, b, c, seed, n=1 << scale)
+
+
+def rmat_edges(scale: int, edge_factor: int, a: float = 0.57, b: float = 0.19, c: float = 0.19, seed: int = 3):
+    """The edge list of rmat() before its CSR is built: (u, v) int32 arrays
+    with u < v, self-loops dropped, duplicates kept. Turning it into the
+    symmetric deduplicated CSR (reverse entries added, duplicates merged to
+    weight 1) gives rmat()'s graph."""
+    lib = _lib()
+    u = ctypes.POINTER(ctypes.c_int32)()
+    v = ctypes.POINTER(ctypes.c_int32)()
+    m = ctypes.c_int64(0)
+    rc = lib.gg_rmat_edges(scale, edge_factor, a, b, c, seed, ctypes.byref(u), ctypes.byref(v), ctypes.byref(m))
+    if rc != 0:
+        raise RuntimeError(f"graph generator failed with code {rc}")
+    try:
+        k = m.value
+        uu = np.ctypeslib.as_array(u, shape=(max(k, 1),))[:k].copy()
+        vv = np.ctypeslib.as_array(v, shape=(max(k, 1),))[:k].copy()
+    finally:
+        for p in (u, v):
+            lib.gg_free(ctypes.cast(p, ctypes.c_void_p))
+    return uu, vv
 
 
 def gnp(n: int, p: float, seed: int, wmax: int = 1) -> CSR:

@@ -371,8 +371,28 @@ int gg_road(int32_t side, double drop, double diag_frac, int32_t wmin, int32_t w
  * result is symmetrised and deduplicated; unit weights. Edges are drawn in
  * fixed chunks, each chunk with its own stream seeded from (seed, chunk), so
  * the graph does not depend on the thread count. */
+/* The R-MAT edge list of gg_rmat before the CSR is built: the same draws,
+ * self-loops compacted away, each edge oriented u < v (duplicates kept).
+ * *m_out receives the edge count; eu/ev are malloc'ed (free with gg_free). */
+int gg_rmat_edges(int32_t scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
+                  int32_t **eu_out, int32_t **ev_out, int64_t *m_out);
+
 int gg_rmat(int32_t scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
             int64_t **off_out, int32_t **idx_out, float **w_out, int64_t *nnz_out) {
+    int32_t *eu = NULL, *ev = NULL;
+    int64_t m = 0;
+    int rc = gg_rmat_edges(scale, edge_factor, a, b, c, seed, &eu, &ev, &m);
+    if (rc) return rc;
+    float *ew = (float *)malloc((size_t)(m ? m : 1) * sizeof(float));
+    if (!ew) { free(eu); free(ev); return -1; }
+    for (int64_t e = 0; e < m; ++e) ew[e] = 1.0f;
+    rc = build_csr((int64_t)1 << scale, m, eu, ev, ew, 1, off_out, idx_out, w_out, nnz_out);
+    free(eu); free(ev); free(ew);
+    return rc;
+}
+
+int gg_rmat_edges(int32_t scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
+                  int32_t **eu_out, int32_t **ev_out, int64_t *m_out) {
     if (scale < 1 || scale > 30 || edge_factor < 0) return -2;
     int64_t n = 1LL << scale;
     int64_t ne = edge_factor * n;
@@ -403,6 +423,7 @@ int gg_rmat(int32_t scale, int64_t edge_factor, double a, double b, double c, ui
     }
     /* compact away self-loops, orient u < v so each undirected edge appears
      * once before symmetrisation (duplicates are removed after sorting) */
+    (void)n;
     int64_t m = 0;
     for (int64_t e = 0; e < ne; ++e) {
         if (eu[e] == ev[e]) continue;
@@ -410,12 +431,10 @@ int gg_rmat(int32_t scale, int64_t edge_factor, double a, double b, double c, ui
         if (x > y) { int32_t t = x; x = y; y = t; }
         eu[m] = x; ev[m] = y; m++;
     }
-    float *ew = (float *)malloc((size_t)(m ? m : 1) * sizeof(float));
-    if (!ew) { free(eu); free(ev); return -1; }
-    for (int64_t e = 0; e < m; ++e) ew[e] = 1.0f;
-    int rc = build_csr(n, m, eu, ev, ew, 1, off_out, idx_out, w_out, nnz_out);
-    free(eu); free(ev); free(ew);
-    return rc;
+    *eu_out = eu;
+    *ev_out = ev;
+    *m_out = m;
+    return 0;
 }
 
 /* ---------------------------------------------------- G(n, p) (tiny tests) */

@@ -105,14 +105,12 @@ def test_argument_checks_before_device_work():
     assert q.value == 0.0
     i64.value = 9
     assert lib.leiden_disconnected(0, None, None, None, None, ctypes.byref(i64)) == 0 and i64.value == 0
-    # edge list to CSR: negative n, more than 2^30 edges, unknown combine or where, no nnz slot
+    # edge list to CSR: negative n, unknown combine or where, no nnz slot, missing sources
     src = np.array([0], np.int32)
     o3 = np.zeros(3, np.int64)
     i64.value = 4
     bad(lib.leiden_csr_from_edges(-1, 1, vp(src), vp(src), None, 0, 0, 0, vp(o3), None, None, ctypes.byref(i64),
                                   None))
-    bad(lib.leiden_csr_from_edges(2, (1 << 30) + 1, vp(src), vp(src), None, 0, 0, 0, vp(o3), None, None,
-                                  ctypes.byref(i64), None))
     bad(lib.leiden_csr_from_edges(2, 1, vp(src), vp(src), None, 0, 0, 2, vp(o3), None, None, ctypes.byref(i64),
                                   None))
     bad(lib.leiden_csr_from_edges(2, 1, vp(src), vp(src), None, 3, 0, 0, vp(o3), None, None, ctypes.byref(i64),
