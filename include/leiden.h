@@ -53,9 +53,9 @@ enum { LEIDEN_HOST = 0, LEIDEN_DEVICE = 1 };
 /* mode: LEIDEN_ASYNC applies local-moving moves inside the kernels as soon
  * as they are decided (the paper's asynchronous execution, Section 4.1);
  * LEIDEN_DETERMINISTIC evaluates each schedule step against the state at
- * the start of the step and decides in exact int64 arithmetic, so results
- * are reproducible bit for bit (requires integer weights, resolution 1 and
- * 2m < 2^31). */
+ * the start of the step and decides in exact integer arithmetic (int64
+ * sums, 128-bit move keys), so results are reproducible bit for bit
+ * (requires integer weights, resolution 1 and 2m < 2^53). */
 enum { LEIDEN_ASYNC = 0, LEIDEN_DETERMINISTIC = 1 };
 
 /* flags */
@@ -72,11 +72,17 @@ enum {
     LEIDEN_FLAG_LOUVAIN = 128u,           /* the Louvain method of the paper's comparison (Section 5):
                                              no refinement phase; each pass aggregates its local-moving
                                              communities, which need not be connected */
-    LEIDEN_FLAG_RANDOM_REFINE = 256u      /* asynchronous mode: randomized refinement (Sections 2.2, 4.1):
+    LEIDEN_FLAG_RANDOM_REFINE = 256u,     /* asynchronous mode: randomized refinement (Sections 2.2, 4.1):
                                              an isolated vertex joins a community of positive gain within
                                              its bound with probability proportional to the gain, drawn
                                              from the seed, pass, sweep, vertex and community; the
                                              deterministic mode refuses it (LEIDEN_ERR_UNSUPPORTED) */
+    LEIDEN_FLAG_TEST_STALL_BARRIER = 512u /* testing aid for the timeout path: block 1 of every persistent
+                                             sweep launch of more than one block ends without arriving at
+                                             the grid barrier, and the other blocks wait about a
+                                             millisecond instead of about a second before they give up;
+                                             the run then returns LEIDEN_ERR_TIMEOUT and the handle stays
+                                             usable. Not for production use. */
 };
 
 typedef struct {
@@ -89,8 +95,9 @@ typedef struct {
     int32_t mode;                 /* LEIDEN_ASYNC or LEIDEN_DETERMINISTIC */
     uint32_t flags;               /* LEIDEN_FLAG_* */
     int32_t schedule_layers;      /* L: priority layers of the sweep schedule (L - 1 + B at most
-                                     1023); 0 (default): 1000 for a graph with a row of more than
-                                     2048 entries, else 32, graph by graph in a batch or server */
+                                     1023); 0 (default): 1000 for a heavy-tailed graph (largest
+                                     degree above 64 times the mean degree nnz/n), else 32, graph
+                                     by graph in a batch or server */
     int32_t schedule_buckets;     /* B: priority buckets after the last layer; default 16 */
     uint64_t seed;                /* seed of the schedule's vertex priorities; default 0 */
 } leiden_params;
@@ -285,8 +292,9 @@ leiden_status leiden_disconnected(int64_t n, const int64_t *offsets, const int32
  * scratch is a fixed static device array (8 MiB + 32 bytes) that every GPU
  * loading the library keeps until the process exits, so n is limited to
  * 1,048,576 vertices (larger n returns LEIDEN_ERR_INVALID). The first call
- * on a device looks up the array's address there; make that call before any
- * stream capture. All calls on a device share the array: calls whose work
+ * on a device looks up the array's address there and keeps it; make that
+ * call before any stream capture, and do not call this entry point again
+ * after a reset of the device (cudaDeviceReset) in the same process. All calls on a device share the array: calls whose work
  * overlaps on the GPU race and must be serialised by the caller. Arguments
  * and result as for leiden_modularity. */
 leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *offsets, const int32_t *indices,
@@ -301,14 +309,18 @@ leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *offsets, const
  * on stream). An edge u != v gives the entries (u, v) and (v, u); a
  * self-loop gives the single entry (u, u) (one CSR entry, counted once in K
  * and 2m), or none when drop_self_loops != 0. Entries with the same
- * (row, target) are merged: weights summed (combine = 0) or the largest
- * kept (combine = 1). Rows list their targets in ascending order.
+ * (row, target) are merged: weights summed in fp64 and rounded once to fp32
+ * (combine = 0) or the largest kept (combine = 1). Rows list their targets
+ * in ascending order. m may exceed 2^31 (positions are 64-bit; rows are
+ * sorted in chunks of at most 2^30 entries).
  * Outputs, in the same kind of memory as the input: offsets[n+1], and
  * indices/weights with room for *nnz entries as passed in (2m always
  * suffices); *nnz receives the entry count. Returns LEIDEN_ERR_INVALID for an
- * endpoint outside [0, n), a negative or non-finite weight, more than 2^30
- * edges, or too small a capacity (*nnz then holds the count needed); scratch
- * is allocated and freed on stream. */
+ * endpoint outside [0, n), a negative or non-finite weight, a row of more
+ * than 2^30 entries before merging, or too small a capacity (*nnz then holds
+ * the count needed). Device scratch, allocated and freed on stream: 8 bytes
+ * per entry before merging (12 with weights), about 32 bytes per entry of the
+ * largest chunk, 32 bytes per vertex, and a device copy of a host edge list. */
 leiden_status leiden_csr_from_edges(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w,
                                     int32_t where, int32_t drop_self_loops, int32_t combine, int64_t *offsets,
                                     int32_t *indices, float *weights, int64_t *nnz, void *stream);
@@ -329,6 +341,15 @@ leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, voi
  * out (host memory). Returns LEIDEN_ERR_INVALID if the last run was not
  * profiled. */
 leiden_status leiden_profile_get(leiden_graph_t g, leiden_kernel_profile *out);
+
+/* Testing aid for the out-of-memory paths. The paper has no counterpart.
+ * After `after` more successful device allocations made by handles
+ * (leiden_create, leiden_batch_create, leiden_run, leiden_batch_run and the
+ * server's workspace), the next one fails as if the device were out of
+ * memory (LEIDEN_ERR_OOM); the calls made after that allocate normally
+ * again. A negative value switches the injection off (the default). The
+ * counter is process-wide. Not for production use. */
+leiden_status leiden_test_fail_allocation(int64_t after);
 
 /* Human-readable name of a status code. */
 const char *leiden_status_string(int32_t status);

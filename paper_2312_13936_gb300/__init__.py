@@ -27,13 +27,14 @@ __all__ = [
     "leiden_batch_run", "leiden_batch_info", "LeidenBatch", "pack_batch", "ServerState", "leiden_server_create",
     "leiden_server_submit", "leiden_server_step", "leiden_server_next", "leiden_server_result", "leiden_server_info",
     "leiden_server_destroy", "LeidenServer", "leiden_disconnected", "disconnected", "leiden_csr_from_edges",
-    "csr_from_edges",
+    "csr_from_edges", "FLAG_TEST_STALL_BARRIER", "leiden_test_fail_allocation",
 ]
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
 LEIDEN_ASYNC, LEIDEN_DETERMINISTIC = 0, 1
 FLAG_VALIDATE, FLAG_REFINE_SINGLE_SWEEP, FLAG_TRACE, FLAG_PROFILE, FLAG_STEP_LAUNCHES = 1, 2, 4, 8, 16
 FLAG_REFINE_LABELS, FLAG_LOUVAIN, FLAG_RANDOM_REFINE = 64, 128, 256
+FLAG_TEST_STALL_BARRIER = 512  # testing aid: the persistent sweep's barrier wait runs out
 PROFILE_CLASSES = 24
 PROFILE_PHASES = ("move", "refine", "aggregate")
 PROFILE_BINS = ("sweep", "thread", "tile16", "tile32", "warp", "block", "global", "unused")
@@ -122,6 +123,8 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.leiden_server_info.argtypes = [_VP, ctypes.POINTER(ServerState)]
         lib.leiden_server_destroy.argtypes = [_VP]
         lib.leiden_disconnected.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.POINTER(_I64)]
+        lib.leiden_test_fail_allocation.argtypes = [_I64]
+        lib.leiden_test_fail_allocation.restype = ctypes.c_int
         lib.leiden_csr_from_edges.argtypes = [_I64, _I64, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32, _VP, _VP, _VP, ctypes.POINTER(_I64), _VP]
         for f in (lib.leiden_create, lib.leiden_run, lib.leiden_destroy, lib.leiden_modularity,
@@ -246,6 +249,12 @@ def leiden_server_info(server) -> dict:
 
 def leiden_server_destroy(server) -> None:
     _check(library().leiden_server_destroy(server))
+
+
+def leiden_test_fail_allocation(after: int) -> None:
+    """Testing aid: the handle allocation after `after` more successful ones
+    fails with LEIDEN_ERR_OOM (negative: no injection)."""
+    _check(library().leiden_test_fail_allocation(after))
 
 
 def leiden_destroy(handle) -> None:

@@ -1,7 +1,7 @@
 // extern "C" entry points declared in include/leiden.h.
 #include <new>
 
-#include "engine.h"
+#include "engine_impl.h"
 
 struct leiden_graph_s {
     lgb::Handle h;
@@ -11,6 +11,11 @@ struct leiden_server_s {
 };
 
 extern "C" {
+
+leiden_status leiden_test_fail_allocation(int64_t after) {
+    lgb::g_fail_alloc_after.store(after < 0 ? -1 : after);
+    return LEIDEN_OK;
+}
 
 void leiden_params_default(leiden_params *p) {
     if (!p) return;
