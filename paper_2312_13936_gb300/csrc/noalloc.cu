@@ -15,7 +15,10 @@
 //     LEIDEN_ERR_INVALID before any device work.
 //   - The first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current and caches it; make
-//     that first call before any stream capture on the device.
+//     that first call before any stream capture on the device. A reset of
+//     the device (cudaDeviceReset) reloads the module at another address and
+//     leaves the cached one stale: after a reset this entry point must not be
+//     called again in the same process.
 //   - All calls on a device share the one array. Calls whose work overlaps
 //     on the GPU (different streams, or threads racing on one stream) race
 //     on it and give wrong results; serialise them.
