@@ -3,37 +3,43 @@
 
 One step is one leiden_run (every phase of the method: local-moving,
 refinement, aggregation over all passes, final labels and modularity) on the
-road-network workload: a 5000 x 5000 lattice with 10% of its edges dropped,
-1% diagonal shortcuts and integer weights in [1, 10] (25M vertices, ~91M
-directed CSR entries). value = directed CSR entries / step time, with the
+largest single-GPU workload: an R-MAT graph of scale 25 (33.5M vertices),
+edge factor 56, (a, b, c) = (0.57, 0.19, 0.19), symmetrised, duplicates and
+self-loops removed, unit weights (3,554,875,526 directed CSR entries; the
+stand-in for the paper's sk-2005 web graph, Section 5.2 and Table 2). Its
+edge list is drawn on the host and turned into the CSR on the GPU by
+leiden_csr_from_edges. value = directed CSR entries / step time, with the
 input resident in HBM. Prints one JSON line.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload rmat|road|sbm]
 
 With N > 1 (torchrun, one process per GPU) every rank solves its own replica
 of the workload: the method has no data-parallel split of one graph, so the
 multi-GPU form is independent replicas ("scaling": "weak").
 
-The same line carries the batched form ("batched"): 4096 seeded SBM graphs
-(vertex counts log-uniform in [100, 100000], 4-64 blocks, mean degree 8-32,
-p_out/p_in = 0.02; ~61M vertices, ~1.2e9 entries) packed as one segmented CSR
-and solved by leiden_batch_run, in graphs/s, next to a per-graph loop of
-plain leiden_run calls timed on a sample of the same graphs. With N > 1 the
-graphs are dealt to ranks longest-first by entry count, each to the rank with
-the least work so far.
+The same line carries the road-network workload ("road"): a 5000 x 5000
+lattice with 10% of its edges dropped, 1% diagonal shortcuts and integer
+weights in [1, 10] (25M vertices, ~91M entries), timed the same way, with its
+own roofline, its CPU baseline (one oracle run on the full graph) and the
+paper's variants on it ("variants"): the Louvain method (no refinement),
+refine-based super-vertex labels and the randomized refinement, each with its
+time, modularity and fraction of disconnected communities.
 
-And the served form ("served"): a Poisson stream of seeded SBM (1k-4M
-vertices) and R-MAT (scale 14-22, edge factor 16) graphs from host memory,
-served by the continuous-batching server (leiden_server_*) and, on the same
-arrival times, by a plain server that runs one leiden_run at a time. The
-offered rate is set to 90% of the plain server's measured service rate;
-p50/p99 latency (arrival to result on the host), graphs/s and the mean
-modularity of both are reported. Rank 0 only.
+The batched form ("batched"): 4096 seeded SBM graphs (vertex counts
+log-uniform in [100, 100000], 4-64 blocks, mean degree 8-32, p_out/p_in =
+0.02; ~61M vertices, ~1.2e9 entries) packed as one segmented CSR and solved by
+leiden_batch_run, in graphs/s, next to a per-graph loop of plain leiden_run
+calls timed on a sample of the same graphs. With N > 1 the graphs are dealt
+to ranks longest-first by entry count, each to the rank with the least work
+so far.
 
-And the paper's variants on the bench graph ("variants", rank 0, outside the
-timed region): the Louvain method (no refinement) and refine-based
-super-vertex labels, each with its time, modularity and fraction of
-disconnected communities beside the Leiden run's.
+The served form ("served"): a Poisson stream of seeded SBM (1k-4M vertices)
+and R-MAT (scale 14-22, edge factor 16) graphs from host memory, served by
+the continuous-batching server (leiden_server_*) and, on the same arrival
+times, by a plain server that runs one leiden_run at a time. The offered rate
+is set to 90% of the plain server's measured service rate; p50/p99 latency
+(arrival to result on the host), graphs/s and the mean modularity of both are
+reported. Rank 0 only.
 
 "roofline" rates the dominant kernel class against the measured HBM copy
 bandwidth: its algorithmic bytes (counted by the kernels in the first timed
@@ -41,8 +47,9 @@ step) over its CUDA-event time. "by_phase" and "overall" give the same for
 each phase and for all profiled launches, and the profiled bytes over the
 whole step. "e2e" runs the C ABI from page-locked host buffers (the copies in
 and out inside the timed region) and splits a step into create, run and
-destroy. An optional part that fails is reported as {"error": ...} in its
-place.
+destroy. "cpu_baseline" is the oracle (sequential, one host core) on a
+bounded sample of the same R-MAT recipe (scale 20). An optional part that
+fails is reported as {"error": ...} in its place.
 """
 import argparse
 import hashlib
@@ -69,21 +76,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="road", choices=["road", "sbm", "rmat"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "road", "sbm"])
     ap.add_argument("--side", type=int, default=5000, help="road lattice side")
     ap.add_argument("--rmat-scale", type=int, default=25)
     ap.add_argument("--mode", default="async", choices=["async", "det"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-side", type=int, default=3000, help="road side of the CPU-baseline sample")
-    ap.add_argument("--ref-side", type=int, default=1500, help="road side of each reference-arm step")
+    ap.add_argument("--no-road", action="store_true", help="skip the road object (when the headline is not road)")
+    ap.add_argument("--cpu-scale", type=int, default=20, help="R-MAT scale of the CPU-baseline sample")
+    ap.add_argument("--ref-scale", type=int, default=18, help="R-MAT scale of each reference-arm step")
+    ap.add_argument("--ref-side", type=int, default=1500, help="road side of each reference-arm step (--workload road)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--batch-sample", type=int, default=128, help="graphs of the per-graph loop")
     ap.add_argument("--no-serve", action="store_true", help="skip the served form")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the Louvain and refine-based-label comparison on the same graph")
+                    help="skip the Louvain and refine-based-label comparison on the road graph")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-pool", type=int, default=24, help="distinct graphs the requests cycle through")
     ap.add_argument("--serve-load", type=float, default=0.9, help="offered rate / plain server's service rate")
@@ -126,19 +135,40 @@ def variants_form(h, off, idx, mode, flags, stream, runs=5):
     return out
 
 
-def workload(args):
+RMAT_ABC = (0.57, 0.19, 0.19)
+
+
+def rmat_name(scale):
+    return (f"R-MAT scale {scale}, edge factor 56, (0.57,0.19,0.19,0.05), symmetrised, duplicates and self-loops "
+            f"removed, unit weights, seed 3")
+
+
+def road_name(side):
+    return (f"road lattice {side}x{side}, 10% edges dropped, 1% diagonal shortcuts, integer weights 1-10, seed 2")
+
+
+def workload(args, dev):
+    """The headline graph on the device: (name, n, nnz, off, idx, w as CUDA
+    tensors). R-MAT: the edge list is drawn on the host and its CSR built on
+    the GPU (leiden_csr_from_edges: reverse entries added, duplicates merged
+    to weight 1, self-loops dropped); the others are generated on the host."""
+    import torch
+
     import gen
+    import paper_2312_13936_gb300 as lg
+    if args.workload == "rmat":
+        u, v = gen.rmat_edges(args.rmat_scale, 56, *RMAT_ABC, seed=3)
+        du, dv = torch.from_numpy(u).to(dev), torch.from_numpy(v).to(dev)
+        del u, v
+        off, idx, w = lg.csr_from_edges(1 << args.rmat_scale, du, dv, None, drop_self_loops=True, combine="max")
+        del du, dv
+        torch.cuda.synchronize()
+        return rmat_name(args.rmat_scale), 1 << args.rmat_scale, int(idx.numel()), off, idx, w
     if args.workload == "road":
-        g = gen.road(args.side, 0.10, 0.01, 1, 10, seed=2)
-        name = (f"road lattice {args.side}x{args.side}, 10% edges dropped, 1% diagonal shortcuts, "
-                f"integer weights 1-10, seed 2")
-    elif args.workload == "sbm":
-        g = gen.sbm_workload()
-        name = "SBM 10,000 vertices, 50 blocks, p_in 0.05, p_out 0.0005, seed 1"
+        g, name = gen.road(args.side, 0.10, 0.01, 1, 10, seed=2), road_name(args.side)
     else:
-        g = gen.rmat(args.rmat_scale, 56, 0.57, 0.19, 0.19, seed=3)
-        name = f"R-MAT scale {args.rmat_scale}, edge factor 56, (0.57,0.19,0.19,0.05), seed 3"
-    return g, name
+        g, name = gen.sbm_workload(), "SBM 10,000 vertices, 50 blocks, p_in 0.05, p_out 0.0005, seed 1"
+    return (name, g.n, g.nnz) + tuple(torch.as_tensor(a).to(dev) for a in (g.offsets, g.indices, g.weights))
 
 
 class Clocks:
@@ -524,27 +554,41 @@ def served_form(args, mode, flags):
     }
 
 
-def cpu_baseline(side):
+def cpu_baseline(kind, size):
+    """The oracle (SEQ mode, sequential, one host core) on one bounded sample
+    of a recipe: R-MAT of the given scale, or the road lattice of the given
+    side."""
     import gen
     import oracle
-    g = gen.road(side, 0.10, 0.01, 1, 10, seed=2)
+    if kind == "rmat":
+        g = gen.rmat(size, 56, *RMAT_ABC, seed=3)
+        what = rmat_name(size)
+    else:
+        g = gen.road(size, 0.10, 0.01, 1, 10, seed=2)
+        what = road_name(size)
     t = time.perf_counter()
     r = oracle.leiden(g, mode=oracle.SEQ)
     dt = time.perf_counter() - t
     assert r.status == 0
     return {"value": g.nnz / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one sequential oracle run (SEQ mode) on the same recipe at side {side}: "
-                       f"{g.n} vertices, {g.nnz} directed entries, {dt:.1f} s on 1 host core "
-                       f"of {os.cpu_count()}")}
+            "sample": (f"one sequential oracle run (SEQ mode) on {what}: {g.n} vertices, {g.nnz} directed "
+                       f"entries, {dt:.1f} s on 1 host core of {os.cpu_count()}"),
+            "modularity": r.modularity}
 
 
 def run_reference(args, rank):
-    """Reference arm: the CPU oracle timed on host cores, same metric and unit."""
+    """Reference arm: the CPU oracle timed on host cores, same metric and unit,
+    each step one run on a bounded sample of the GPU arm's workload."""
     if rank != 0:
         return
     import gen
     import oracle
-    g = gen.road(args.ref_side, 0.10, 0.01, 1, 10, seed=2)
+    if args.workload == "road":
+        g = gen.road(args.ref_side, 0.10, 0.01, 1, 10, seed=2)
+        wl = f"{road_name(args.ref_side)} (bounded sample of the {args.side}x{args.side} workload)"
+    else:
+        g = gen.rmat(args.ref_scale, 56, *RMAT_ABC, seed=3)
+        wl = f"{rmat_name(args.ref_scale)} (bounded sample of the scale-{args.rmat_scale} workload)"
     for _ in range(args.warmup):
         oracle.leiden(g, mode=oracle.SEQ)
     t = time.perf_counter()
@@ -552,17 +596,106 @@ def run_reference(args, rank):
         r = oracle.leiden(g, mode=oracle.SEQ)
     dt = time.perf_counter() - t
     value = args.steps * g.nnz / dt
-    sample = (f"each step one sequential oracle run (SEQ mode) on the road recipe at side {args.ref_side}: "
-              f"{g.n} vertices, {g.nnz} directed entries, 1 host core of {os.cpu_count()}")
+    sample = (f"each step one sequential oracle run (SEQ mode) on {wl}: {g.n} vertices, {g.nnz} directed entries, "
+              f"1 host core of {os.cpu_count()}")
     print(json.dumps({
         "metric": METRIC, "value": value, "unit": "edges/s", "impl": "reference", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"road lattice {args.ref_side}x{args.ref_side} (bounded sample of the "
-                               f"{args.side}x{args.side} workload)", "modularity": r.modularity},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_ORACLE,
+        "data": "synthetic", "config": {"workload": wl, "modularity": r.modularity},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def timed_runs(h, mode, flags, steps, warmup, stream, world, dev, clocks=None):
+    """W untimed runs, then K runs between barriers and synchronisations,
+    timed with CUDA events on the run's stream (max over ranks); the first
+    timed run is profiled (events around every sweep and aggregation launch,
+    work counters in the kernels). Returns (ms for the K runs, stats of the
+    last run, membership, modularities, profile, kernel launches)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2312_13936_gb300 as lg
+    for _ in range(warmup):
+        h.run(mode=mode, flags=flags)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    prof, launches, qs = {}, 0, []
+    for i in range(steps):
+        memb, q, st = h.run(mode=mode, flags=flags | (lg.FLAG_PROFILE if i == 0 else 0))
+        qs.append(q)
+        launches += st.kernel_launches
+        if i == 0:
+            for k, v in h.profile().items():
+                prof[k] = {"launches": v["launches"], "ms": v["ms"], "bytes": v["bytes"]}
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        ms = float(reduce_stats(torch.tensor([ms], device=dev), 1, world).item())
+        dist.barrier()
+    return ms, st, memb, qs, prof, launches, ck
+
+
+def roofline_of(prof, peak, peak_kind, wname, step_ms):
+    """Roofline object of the dominant kernel class of a profiled run."""
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    if not top:
+        return None
+    (phase, binname), a = top
+    achieved = a["bytes"] / (a["ms"] / 1e3) / 1e9
+    cls = f"{phase}/{binname}"
+    total_ms = sum(v["ms"] for v in prof.values())
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+         "traffic": traffic_for(cls, wname), "kernel": cls, "peak_source": f"{peak_kind} hbm_gbs",
+         "bytes_per_launch": a["bytes"] / a["launches"], "ms_per_launch": a["ms"] / a["launches"],
+         "share_of_profiled_ms": a["ms"] / total_ms}
+    r["by_phase"], r["overall"] = phase_roofline(prof, peak, step_ms)
+    return r
+
+
+def road_form(args, mode, flags, stream, world, dev, peak, peak_kind):
+    """The road workload as a second object: device-timed edges/s, roofline,
+    modularity and connectivity, the paper's variants on it, and the
+    oracle's CPU baseline on the full graph."""
+    import torch
+
+    import gen
+    import paper_2312_13936_gb300 as lg
+    g = gen.road(args.side, 0.10, 0.01, 1, 10, seed=2)
+    name = road_name(args.side)
+    off, idx, w = (torch.as_tensor(a).to(dev) for a in (g.offsets, g.indices, g.weights))
+    h = lg.Leiden(off, idx, w)
+    ms, st, memb, qs, prof, launches, _ = timed_runs(h, mode, flags, args.steps, args.warmup, stream, world, dev)
+    out = {"workload": name, "n": g.n, "nnz": g.nnz, "value": world * args.steps * g.nnz / (ms / 1e3),
+           "unit": "edges/s", "ms_per_step": ms / args.steps, "modularity": statistics.median(qs),
+           "disconnected_communities": lg.disconnected(off, idx, memb), "passes": st.passes,
+           "phase_ms": {"move": st.ms_move, "refine": st.ms_refine, "aggregate": st.ms_aggregate,
+                        "other": st.ms_other},
+           "gpu_launches": launches,
+           "roofline": roofline_of(prof, peak, peak_kind, name, ms / args.steps),
+           "kernel_classes": {f"{k[0]}/{k[1]}": v for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+    if not args.no_variants and world == 1:
+        out["variants"] = optional_leg(variants_form, h, off, idx, mode, flags, stream)
+    h.close()
+    if not args.no_cpu and world == 1:
+        out["cpu_baseline"] = optional_leg(cpu_baseline, "road", args.side)
+    return out
+
+
+DTYPE = ("fp32 edge weights, per-edge sums and move keys; fp64 community totals, 2m and modularity "
+         "(asynchronous mode); int64 sums and 128-bit keys (deterministic mode)")
+DTYPE_ORACLE = "f64 (the oracle's sequential mode)"
 
 
 def main():
@@ -581,50 +714,25 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    g, wname = workload(args)
+    dev = torch.device("cuda", local)
+    t_build = time.perf_counter()
+    wname, n, nnz, off, idx, w = workload(args, dev)
+    t_build = time.perf_counter() - t_build
     mode = lg.LEIDEN_ASYNC if args.mode == "async" else lg.LEIDEN_DETERMINISTIC
     base_flags = 0
-    dev = torch.device("cuda", local)
-    off = torch.as_tensor(g.offsets).to(dev)
-    idx = torch.as_tensor(g.indices).to(dev)
-    w = torch.as_tensor(g.weights).to(dev)
     stream = torch.cuda.current_stream()
     h = lg.Leiden(off, idx, w)
-    for _ in range(args.warmup):
-        h.run(mode=mode, flags=base_flags)
-    torch.cuda.synchronize()
+    peak, peak_kind = hbm_peak()
 
     # ---- timed region (device time, CUDA events on the run's stream)
     clocks = Clocks(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    prof = {}
-    launches = 0
-    qs = []
-    for i in range(args.steps):
-        # the first timed step is profiled (CUDA events around every sweep and
-        # aggregation launch on the run's stream); the others run plain
-        memb, q, st = h.run(mode=mode, flags=base_flags | (lg.FLAG_PROFILE if i == 0 else 0))
-        qs.append(q)
-        launches += st.kernel_launches
-        if i == 0:
-            for k, v in h.profile().items():
-                prof[k] = {"launches": v["launches"], "ms": v["ms"], "bytes": v["bytes"]}
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        ms = float(reduce_stats(torch.tensor([ms], device=dev), 1, world).item())
-        dist.barrier()
-    value = world * args.steps * g.nnz / (ms / 1e3)
+    ms, st, memb, qs, prof, launches, ck = timed_runs(h, mode, base_flags, args.steps, args.warmup, stream, world,
+                                                      dev, clocks)
+    value = world * args.steps * nnz / (ms / 1e3)
     # every community connected? (Algorithm 5 on the GPU, outside the timed region)
     disconnected = lg.disconnected(off, idx, memb)
+    h.close()
+    graph_bytes = 8 * (n + 1) + 8 * nnz
 
     # ---- end to end through the C ABI with host buffers (H2D and D2H inside)
     def e2e_leg():
@@ -632,14 +740,15 @@ def main():
         # the user's buffers, staged once in page-locked host memory (outside
         # the timed region), as a caller that streams graphs would keep them
         try:
-            hbuf = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-                    for a in (g.offsets, g.indices, g.weights)]
-            hout = torch.empty(max(g.n, 1), dtype=torch.int32).pin_memory()
+            hbuf = [torch.empty(t.numel(), dtype=t.dtype, pin_memory=True) for t in (off, idx, w)]
+            hout = torch.empty(max(n, 1), dtype=torch.int32, pin_memory=True)
             pinned = True
         except RuntimeError:
-            hbuf = [torch.from_numpy(np.ascontiguousarray(a)) for a in (g.offsets, g.indices, g.weights)]
-            hout = torch.empty(max(g.n, 1), dtype=torch.int32)
+            hbuf = [torch.empty(t.numel(), dtype=t.dtype) for t in (off, idx, w)]
+            hout = torch.empty(max(n, 1), dtype=torch.int32)
             pinned = False
+        for hb, t in zip(hbuf, (off, idx, w)):
+            hb.copy_(t)
         P = lg.leiden_params_default()
         P.mode = mode
         P.flags = base_flags
@@ -648,7 +757,7 @@ def main():
 
         def one():
             t0 = time.perf_counter()
-            hh = lg.leiden_create(g.n, g.nnz, vp(hbuf[0].data_ptr()), vp(hbuf[1].data_ptr()),
+            hh = lg.leiden_create(n, nnz, vp(hbuf[0].data_ptr()), vp(hbuf[1].data_ptr()),
                                   vp(hbuf[2].data_ptr()), lg.LEIDEN_HOST, 0, vp(stream.cuda_stream))
             stream.synchronize()
             t1 = time.perf_counter()
@@ -660,7 +769,7 @@ def main():
                 split[k] += dt
         one()
         split[:] = [0.0, 0.0, 0.0]
-        ne = max(2, args.steps // 2)
+        ne = max(2, args.steps // 4)
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -669,9 +778,9 @@ def main():
         te = time.perf_counter() - t0
         if world > 1:
             te = float(reduce_stats(torch.tensor([te], device=dev), 1, world).item())
-        return {"value": world * ne * g.nnz / te, "unit": "edges/s",
+        return {"value": world * ne * nnz / te, "unit": "edges/s",
                 "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in hbuf),
-                "d2h_bytes_per_step": g.n * 4 + 8, "pinned": pinned, "ms_per_step": te * 1e3 / ne,
+                "d2h_bytes_per_step": n * 4 + 8, "pinned": pinned, "steps": ne, "ms_per_step": te * 1e3 / ne,
                 "create_ms": split[0] * 1e3 / ne, "run_ms": split[1] * 1e3 / ne,
                 "destroy_ms": split[2] * 1e3 / ne}
 
@@ -680,8 +789,12 @@ def main():
     e2e = None
     if not args.no_e2e:
         e2e = e2e_leg() if world > 1 else optional_leg(e2e_leg)
-    variants = None if (args.no_variants or rank != 0) else optional_leg(variants_form, h, off, idx, mode,
-                                                                         base_flags, stream)
+    del off, idx, w
+    torch.cuda.empty_cache()
+    road = None
+    if args.workload != "road" and not args.no_road:
+        road = (road_form(args, mode, base_flags, stream, world, dev, peak, peak_kind) if world > 1
+                else optional_leg(road_form, args, mode, base_flags, stream, world, dev, peak, peak_kind))
     batched = None
     if not args.no_batch:
         batched = (batched_form(args, rank, world, mode, base_flags) if world > 1
@@ -690,43 +803,32 @@ def main():
     if rank != 0:
         dist.destroy_process_group()
         return
-    # ---- roofline of the dominant kernel class (algorithmic bytes / event time)
-    peak, peak_kind = hbm_peak()
-    top = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
-    roofline = None
-    if top:
-        (phase, binname), a = top
-        achieved = a["bytes"] / (a["ms"] / 1e3) / 1e9
-        cls = f"{phase}/{binname}"
-        traffic = traffic_for(cls, wname)
-        total_ms = sum(v["ms"] for v in prof.values())
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": traffic, "kernel": cls, "peak_source": f"{peak_kind} hbm_gbs",
-                    "bytes_per_launch": a["bytes"] / a["launches"], "ms_per_launch": a["ms"] / a["launches"],
-                    "share_of_profiled_ms": a["ms"] / total_ms}
-        roofline["by_phase"], roofline["overall"] = phase_roofline(prof, peak, ms / args.steps)
-    cpu = None if (args.no_cpu or world > 1) else optional_leg(cpu_baseline, args.cpu_side)
+    roofline = roofline_of(prof, peak, peak_kind, wname, ms / args.steps)
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = (optional_leg(cpu_baseline, "rmat", args.cpu_scale) if args.workload == "rmat"
+               else optional_leg(cpu_baseline, "road", min(args.side, 5000)) if args.workload == "road" else None)
     served = None if (args.no_serve or world > 1) else optional_leg(served_form, args, mode, base_flags)
     line = {
         "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wname, "n": g.n, "nnz": g.nnz, "mode": args.mode,
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (CSR %.2f GB)" % (
-                       (g.offsets.nbytes + g.indices.nbytes + g.weights.nbytes) / 1e9),
+        "vs_baseline": None, "dtype": DTYPE, "data": "synthetic",
+        "config": {"workload": wname, "n": n, "nnz": nnz, "mode": args.mode,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (CSR %.2f GB)" % (graph_bytes / 1e9),
+                   "build_s": t_build,
                    "modularity": statistics.median(qs), "disconnected_communities": disconnected,
                    "passes": st.passes,
                    "move_sweeps": st.move_iterations, "refine_sweeps": st.refine_iterations,
                    "phase_ms": {"move": st.ms_move, "refine": st.ms_refine, "aggregate": st.ms_aggregate,
                                 "other": st.ms_other}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
+        "road": road,
         "batched": batched,
-        "variants": variants,
         "served": served,
         "kernel_classes": {f"{k[0]}/{k[1]}": v for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
     }
     print(json.dumps(line), flush=True)
-    h.close()
     if world > 1:
         dist.destroy_process_group()
 

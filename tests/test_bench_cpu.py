@@ -55,7 +55,8 @@ def test_reference_arm_line():
     """The reference arm (the oracle on host cores) prints one JSON line with
     the contract's keys, the same metric and unit as the GPU arm, and an e2e
     that moves no bytes."""
-    (line,) = _bench(["--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-side", "60"])
+    (line,) = _bench(["--impl", "reference", "--workload", "road", "--steps", "2", "--warmup", "1",
+                      "--ref-side", "60"])
     sys.path.insert(0, ROOT)
     import bench
     assert line["impl"] == "reference"
@@ -67,6 +68,16 @@ def test_reference_arm_line():
     assert line["e2e"] == {"value": line["value"], "unit": "edges/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert 0.5 < line["config"]["modularity"] < 1.0
+
+
+def test_reference_arm_rmat_sample():
+    """The default workload's reference arm runs the oracle on a bounded
+    sample of the same R-MAT recipe and names it."""
+    (line,) = _bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-scale", "10"])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["config"]["workload"].startswith("R-MAT scale 10, edge factor 56")
+    assert "bounded sample of the scale-25 workload" in line["config"]["workload"]
+    assert 0.0 < line["config"]["modularity"] < 0.5
 
 
 def test_reference_arm_other_ranks_silent():
