@@ -507,12 +507,24 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             int64_t *tsize = q.cnt, *toff = q.pos2;
             int32_t *tidx = q.cursor;
             CK(cudaMemsetAsync(tidx, 0xff, sizeof(int32_t) * ncomm, s));
-            CK(launch_table_sizes(list6, K6, q.tdeg, ncomm, tsize, tidx, s));
+            CK(launch_table_sizes(list6, K6, q.tdeg, q.coff, ncomm, det, tsize, tidx, q.tnm, q.Kagg, s));
             CK(launch_exclusive_scan(tsize, toff, K6, q.scan_tmp, s));
-            q.launches += 3;
-            int64_t total = 0;
+            CK(launch_exclusive_scan(q.tnm, q.tmoff, K6, q.scan_tmp, s));
+            q.launches += 4;
+            int64_t total = 0, M6 = 0;
             CK(cudaMemcpyAsync(&total, toff + K6, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(&M6, q.tmoff + K6, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
+            // the flat member list of the tables and its entry scan (the
+            // per-vertex schedule arrays are free during the aggregation)
+            int32_t *fm = q.step, *ft = q.prop, *fd = q.scnt;
+            CK(launch_table_members(list6, K6, q.tmoff, M6, q.coff, q.members, G.deg, fm, ft, fd, s));
+            CK(launch_exclusive_scan_i32(fd, q.teoff, M6, q.scan_tmp, s));
+            q.launches += 4;
+            ac.fm = fm;
+            ac.ft = ft;
+            ac.moff = q.tmoff;
+            ac.eoff = q.teoff;
             const int64_t budget = kAggTableBytes / 12;  // slots: 4-byte key + 8-byte value
             std::vector<int64_t> hoff;
             if (total > budget) {

@@ -192,6 +192,7 @@ struct Handle::Impl {
             *slayer = nullptr, *sfcount = nullptr, *act = nullptr;
     int64_t *pos = nullptr, *pos2 = nullptr, *coff = nullptr, *cnt = nullptr, *tdeg = nullptr, *key_cnt = nullptr,
             *key_off = nullptr;
+    int64_t *tnm = nullptr, *tmoff = nullptr, *teoff = nullptr;  // bin-6 aggregation: member counts and scans
     void *K = nullptr, *Sig = nullptr, *Kagg = nullptr, *scan_tmp = nullptr, *part_tmp = nullptr;
     long long *gain = nullptr;
     uint8_t *unproc = nullptr;
@@ -279,7 +280,7 @@ struct Handle::Impl {
         for (int32_t **a : {&C0, &Cp, &CB, &Cd, &size, &prop, &step, &key, &list, &flag, &members, &cursor, &bnd,
                             &rep, &label, &minv, &out, &scnt, &slayer})
             ST(alloc(a, n));
-        for (int64_t **a : {&pos, &pos2, &coff}) ST(alloc(a, n + 1));
+        for (int64_t **a : {&pos, &pos2, &coff, &tnm, &tmoff, &teoff}) ST(alloc(a, n + 1));
         for (int64_t **a : {&cnt, &tdeg}) ST(alloc(a, n));
         long long *k1, *k2, *k3;
         ST(alloc(&k1, n));

@@ -299,8 +299,12 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
 }
 
 // ------------------------------------------------- bin 6: packed tables
-__global__ void k_tab_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, int64_t ncomm,
-                            int64_t *tab_size, int32_t *tab_idx) {
+// tab_size[k] = 2^max(6, ceil log2 2 min(tdeg, ncomm)) of community list[k]
+// (its distinct targets are at most that many), tab_idx[c] = k, the member
+// count tab_nm[k], and out_K[c] = 0 (the write adds into it)
+template <class A>
+__global__ void k_tab_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, const int64_t *coff,
+                            int64_t ncomm, int64_t *tab_size, int32_t *tab_idx, int64_t *tab_nm, A *out_K) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = list[k];
         const int64_t cap = tdeg[c] < ncomm ? tdeg[c] : ncomm;  // distinct targets
@@ -308,123 +312,145 @@ __global__ void k_tab_sizes(const int32_t *list, int64_t count, const int64_t *t
         if (bits < 6) bits = 6;
         tab_size[k] = 1LL << bits;
         tab_idx[c] = (int32_t)k;
+        tab_nm[k] = coff[c + 1] - coff[c];
+        out_K[c] = 0;
     }
 }
 
-// Every vertex of a community with a table in [tab_k0, tab_k1) inserts its
-// entries. Vertices are taken in the order of the community-vertex CSR, so
-// the warps in flight share a few tables (which stay in L2) instead of
-// touching all of them. A warp takes 32 consecutive members and walks their
-// entries as
-// one flat range (lane j takes entry p0 + j; its row is found by a binary
-// search over the warp's inclusive degree sums), so rows of any length keep
-// every lane busy; entries of one step with the same (table, key) are summed
-// first and inserted once, which keeps hot keys (a large community's own
-// entries) from serialising on one address.
+// The members of the bin-6 communities as one flat list in table order
+// (member t of table k at moff[k] + t): its vertex fm[t], its table ft[t]
+// and its degree fd[t] (the row lengths whose scan makes the flat entry
+// range of the insertion). Every member of such a community has an edge.
+__global__ void k_tab_members(const int32_t *list, int64_t K6, const int64_t *moff, const int64_t *coff,
+                              const int32_t *members, const int32_t *deg, int32_t *fm, int32_t *ft, int32_t *fd) {
+    const int64_t M6 = moff[K6];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < M6; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = K6 - 1;  // the last table k with moff[k] <= t
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (moff[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int32_t u = members[coff[list[lo]] + (t - moff[lo])];
+        fm[t] = u;
+        ft[t] = (int32_t)lo;
+        fd[t] = deg[u];
+    }
+}
+
+// Insertion of tables [tab_k0, tab_k1): their members' entries form the
+// flat range [eoff[moff[k0]], eoff[moff[k1]]) (eoff: the scan of the flat
+// members' degrees); a warp takes 32 consecutive entries, so rows of any
+// length spread over all warps. Lane 0 finds the member of the first entry
+// by binary search; 32 entries span at most 32 members (every member has an
+// edge), whose ends the lanes hold, and each lane finds its own by a search
+// over them. Entries of one step with the same (table, key) are summed first
+// and inserted once, which keeps hot keys (a large community's own entries)
+// from serialising on one address. Members come in community order, so the
+// warps in flight share a few tables.
 template <class P, class Wi, class Wo>
-__global__ void __launch_bounds__(256) k_agg_tab_insert(AV<P, Wi, Wo> a) {
+__global__ void __launch_bounds__(256) k_agg_tab_insert(AV<P, Wi, Wo> a, const int32_t *__restrict__ fm,
+                                                        const int32_t *__restrict__ ft, const int64_t *__restrict__ eoff,
+                                                        const int64_t *__restrict__ moff) {
     using A = typename P::acc;
     const int lane = threadIdx.x & 31;
-    const int64_t n = a.coff[a.ncomm];  // members of all communities
+    const int64_t mlo = moff[a.tab_k0], mhi = moff[a.tab_k1];
+    const int64_t x_begin = eoff[mlo], x_end = eoff[mhi];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     ProfCounts pc;
-    for (int64_t u0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; u0 < n; u0 += warps * 32) {
-        int64_t k = -1, d = 0, rstart = 0, base = 0;
-        int bits = 0;
-        int32_t u = 0;
-        if (u0 + lane < n) {
-            u = a.members[u0 + lane];
-            const int32_t c = a.Cd[u];
-            k = c >= 0 ? a.tab_idx[c] : -1;
-            if (k < a.tab_k0 || k >= a.tab_k1) k = -1;
+    for (int64_t x0 = x_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; x0 < x_end;
+         x0 += warps * 32) {
+        int64_t m0 = 0;
+        if (lane == 0) {
+            int64_t lo = mlo, hi = mhi - 1;  // the last member with eoff[m] <= x0
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (eoff[mid] <= x0) lo = mid;
+                else hi = mid - 1;
+            }
+            m0 = lo;
         }
-        if (k >= 0) {
-            base = a.tab_off[k] - a.tab_base;
-            bits = __ffsll((long long)(a.tab_off[k + 1] - a.tab_off[k])) - 1;
-            rstart = a.off[u];
-            d = a.deg[u];
+        m0 = __shfl_sync(kFull, m0, 0);
+        const int64_t mine = m0 + lane < mhi ? eoff[m0 + lane + 1] : INT64_MAX;  // end of member m0 + lane
+        const int64_t x = x0 + lane;
+        int own = 0;  // members before x's: lanes whose member ends at or before x
+        for (int st = 16; st >= 1; st >>= 1)
+            if (__shfl_sync(kFull, mine, own + st - 1) <= x) own += st;
+        own &= 31;
+        const bool valid = x < x_end;
+        int32_t key = -1, tk = -1;
+        int64_t tb = 0;
+        int tbits = 0;
+        A v = 0;
+        if (valid) {
+            const int64_t m = m0 + own;
+            const int32_t u = fm[m];
+            const int64_t e = a.off[u] + (x - eoff[m]);
+            tk = ft[m];
+            tb = a.tab_off[tk] - a.tab_base;
+            tbits = __ffsll((long long)(a.tab_off[tk + 1] - a.tab_off[tk])) - 1;
+            key = a.Cd[a.idx[e]];
+            v = wconv<A>(a.w[e]);
             if (a.prof) {
-                pc.v[1]++;
-                pc.v[2] += d;
+                pc.v[2]++;
+                if (x == eoff[m]) pc.v[1]++;
             }
         }
-        int64_t incl = d;  // inclusive sum of the warp's degrees
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t x = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += x;
-        }
-        rstart -= incl - d;  // entry p of the flat range is rstart + p of its owner
-        const int64_t total = __shfl_sync(kFull, incl, 31);
-        for (int64_t p0 = 0; p0 < total; p0 += 32) {
-            const int64_t p = p0 + lane;
-            int own = 0;  // lanes whose rows end at or before p
-            for (int st = 16; st >= 1; st >>= 1)
-                if (__shfl_sync(kFull, incl, own + st - 1) <= p) own += st;
-            own &= 31;
-            const int64_t e = __shfl_sync(kFull, rstart, own) + p;
-            const int64_t tb = __shfl_sync(kFull, base, own);
-            const int tbits = __shfl_sync(kFull, bits, own);
-            const int64_t tk = __shfl_sync(kFull, k, own);
-            const bool valid = p < total;
-            int32_t key = -1;
-            A v = 0;
-            if (valid) {
-                key = a.Cd[a.idx[e]];
-                v = wconv<A>(a.w[e]);
-            }
-            const unsigned long long pair =
-                valid ? ((unsigned long long)tk << 32) | (uint32_t)key : ~0ull;
-            const unsigned peers = __match_any_sync(kFull, pair);
-            v = peer_sum(peers, v);
-            if (valid && lane == __ffs(peers) - 1)
-                if (!hash_add(a.hub_keys + tb, a.hub_vals + tb, tbits, key, v)) set_error(a.err, kErrHashFull);
-        }
+        const unsigned long long pair = valid ? ((unsigned long long)(uint32_t)tk << 32) | (uint32_t)key : ~0ull;
+        const unsigned peers = __match_any_sync(kFull, pair);
+        v = peer_sum(peers, v);
+        if (valid && lane == __ffs(peers) - 1)
+            if (!hash_add(a.hub_keys + tb, a.hub_vals + tb, tbits, key, v)) set_error(a.err, kErrHashFull);
     }
     pc.flush(a.prof);
 }
 
-// One block per table: its distinct entries become the community's row
-// (order unspecified), their count out_deg[c] and their sum K''[c].
+// The distinct entries of tables [tab_k0, tab_k1) become their communities'
+// rows (order unspecified: each warp takes 32 slots of one table -- tables
+// are at least 64 slots and start at multiples of 64 -- and appends its
+// entries at the row's running fill), out_deg[c] their count and K''[c]
+// their sum (both start at 0).
 template <class P, class Wi, class Wo>
 __global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const int32_t *__restrict__ list) {
     using A = typename P::acc;
-    __shared__ int s_written;
-    __shared__ A s_k[8];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t s_begin = a.tab_off[a.tab_k0], s_end = a.tab_off[a.tab_k1];
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     ProfCounts pc;
-    for (int64_t k = a.tab_k0 + blockIdx.x; k < a.tab_k1; k += gridDim.x) {
-        const int32_t c = list[k];
-        const int64_t base = a.tab_off[k] - a.tab_base, S = a.tab_off[k + 1] - a.tab_off[k];
-        const int64_t o0 = a.out_off[c];
-        __syncthreads();
-        if (threadIdx.x == 0) s_written = 0;
-        __syncthreads();
-        A kpart = 0;
-        for (int64_t s0 = (int64_t)wib * 32; s0 < S; s0 += (int64_t)blockDim.x) {
-            const int64_t sl = s0 + lane;
-            const int32_t key = sl < S ? a.hub_keys[base + sl] : -1;
-            const unsigned ball = __ballot_sync(kFull, key >= 0);
-            int pos0 = 0;
-            if (lane == 0 && ball) pos0 = atomicAdd(&s_written, __popc(ball));
-            pos0 = __shfl_sync(kFull, pos0, 0);
-            if (key >= 0) {
-                const int pos = pos0 + __popc(ball & ((1u << lane) - 1u));
-                const Wo wo = out_weight<Wo>(a.hub_vals[base + sl]);
-                a.out_idx[o0 + pos] = key;
-                a.out_w[o0 + pos] = wo;
-                kpart += wconv<A>(wo);
+    for (int64_t s0 = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; s0 < s_end;
+         s0 += warps * 32) {
+        int64_t k = 0;
+        if (lane == 0) {
+            int64_t lo = a.tab_k0, hi = a.tab_k1 - 1;  // the table holding slot s0
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (a.tab_off[mid] <= s0) lo = mid;
+                else hi = mid - 1;
             }
+            k = lo;
         }
-        kpart = warp_sum(kpart);
-        if (lane == 0) s_k[wib] = kpart;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            A ks = 0;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) ks += s_k[w2];
-            a.out_deg[c] = s_written;
-            a.out_K[c] = ks;
-            pc.v[0]++;
-            pc.v[3] += s_written;
+        k = __shfl_sync(kFull, k, 0);
+        const int32_t c = list[k];
+        const int64_t sl = s0 + lane - a.tab_base;
+        const int32_t key = a.hub_keys[sl];
+        const unsigned ball = __ballot_sync(kFull, key >= 0);
+        if (!ball) continue;
+        int pos0 = 0;
+        if (lane == 0) pos0 = atomicAdd(&a.out_deg[c], __popc(ball));
+        pos0 = __shfl_sync(kFull, pos0, 0);
+        A part = 0;
+        if (key >= 0) {
+            const int64_t o = a.out_off[c] + pos0 + __popc(ball & ((1u << lane) - 1u));
+            const Wo wo = out_weight<Wo>(a.hub_vals[sl]);
+            a.out_idx[o] = key;
+            a.out_w[o] = wo;
+            part = wconv<A>(wo);
+        }
+        part = warp_sum(part);
+        if (lane == 0) {
+            atomic_add_acc(&a.out_K[c], part);
+            pc.v[3] += __popc(ball);
+            if (s0 == a.tab_off[k]) pc.v[0]++;
         }
     }
     pc.flush(a.prof);
@@ -433,7 +459,7 @@ __global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const in
 template <class P, class Wi, class Wo>
 cudaError_t tables_typed(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s) {
     auto a = aview<P, Wi, Wo>(c);
-    k_agg_tab_insert<P, Wi, Wo><<<blocks, 256, 0, s>>>(a);
+    k_agg_tab_insert<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, c.fm, c.ft, c.eoff, c.moff);
     k_agg_tab_write<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, list);
     return cudaGetLastError();
 }
@@ -465,11 +491,27 @@ cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t cou
 
 }  // namespace
 
-cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, int64_t ncomm,
-                               int64_t *tab_size, int32_t *tab_idx, cudaStream_t s) {
+cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, const int64_t *coff,
+                               int64_t ncomm, bool det, int64_t *tab_size, int32_t *tab_idx, int64_t *tab_nm,
+                               void *out_K, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     const int64_t b = (count + 255) / 256;
-    k_tab_sizes<<<(int)(b < 2432 ? b : 2432), 256, 0, s>>>(list, count, tdeg, ncomm, tab_size, tab_idx);
+    const int g = (int)(b < 2432 ? b : 2432);
+    if (det)
+        k_tab_sizes<long long><<<g, 256, 0, s>>>(list, count, tdeg, coff, ncomm, tab_size, tab_idx, tab_nm,
+                                                 static_cast<long long *>(out_K));
+    else
+        k_tab_sizes<float><<<g, 256, 0, s>>>(list, count, tdeg, coff, ncomm, tab_size, tab_idx, tab_nm,
+                                             static_cast<float *>(out_K));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_members(const int32_t *list, int64_t K6, const int64_t *moff, int64_t M6, const int64_t *coff,
+                                 const int32_t *members, const int32_t *deg, int32_t *fm, int32_t *ft, int32_t *fd,
+                                 cudaStream_t s) {
+    if (K6 <= 0 || M6 <= 0) return cudaSuccess;
+    const int64_t b = (M6 + 255) / 256;
+    k_tab_members<<<(int)(b < 2432 ? b : 2432), 256, 0, s>>>(list, K6, moff, coff, members, deg, fm, ft, fd);
     return cudaGetLastError();
 }
 

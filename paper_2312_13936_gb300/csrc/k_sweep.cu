@@ -798,6 +798,23 @@ __device__ __forceinline__ long long block_scan_excl(long long x, long long *tot
     return before + inc - x;
 }
 
+// The neighbours of the step's moving hubs become unprocessed (Algorithm 2
+// pruning), the whole grid walking the hubs' rows as one flat range (the
+// layout of run_hubs_grid: eligible hub p owns entries [heoff[p],
+// heoff[p+1]) of hub hj[p]). A hub moved when hmv[j] is set (a move made at
+// once) or, in an apply phase (by_prop), when its proposal is set.
+template <class P, class W>
+__device__ __forceinline__ void hub_flags(const SV<P, W> &a, const Sums<P> &sm, int64_t np, int64_t E, bool by_prop) {
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E; x += nthreads) {
+        const int64_t p = range_at(a.heoff, np, x);
+        const int64_t j = __ldcg(&a.hj[p]);
+        const int32_t v = __ldg(&a.hubs[j]);
+        if (by_prop ? (ldm(&a.prop[v]) < 0) : !__ldcg(&a.hmv[j])) continue;
+        flag_unproc(a, sm, a.idx[a.off[v] + (x - __ldcg(&a.heoff[p]))]);
+    }
+}
+
 template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int64_t nh, int32_t cur_step,
                                               Sums<P> &sm, ProfCounts &pc) {
@@ -988,13 +1005,7 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     if (!REFINE && !P::det) {
         // an asynchronous local-moving move flags the hub's neighbours
         if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
-        for (int64_t x = tid; x < E; x += nthreads) {
-            const int64_t p = range_at(a.heoff, np, x);
-            const int64_t j = __ldcg(&a.hj[p]);
-            if (!__ldcg(&a.hmv[j])) continue;
-            const int32_t v = __ldg(&a.hubs[j]);
-            flag_unproc(a, sm, a.idx[a.off[v] + (x - __ldcg(&a.heoff[p]))]);
-        }
+        hub_flags<P, W>(a, sm, np, E, false);
     }
     return true;
 }
@@ -1002,9 +1013,11 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
 // ------------------------------------------------------------ apply steps
 // Local-moving proposals of one step (deterministic mode; asynchronous mode
 // in the capped steps): commit them.
+// (grid_hub_flags: the neighbours of rows longer than kBlockMaxDeg are
+// flagged by hub_flags over the step's hub layout instead of by one warp)
 template <class P, class W, bool B>
 __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t *__restrict__ list, int64_t lo,
-                                               int64_t hi, Sums<P> &sm) {
+                                               int64_t hi, Sums<P> &sm, bool grid_hub_flags) {
     // whole warps step through the list, so that the neighbours of a mover
     // with a long row are flagged by the whole warp
     const int lane = threadIdx.x & 31;
@@ -1037,7 +1050,7 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
             if (dv <= 32)
                 for (int32_t e = 0; e < dv; ++e) flag_unproc(a, sm, a.idx[e0 + e]);
         }
-        unsigned longs = __ballot_sync(kFull, c >= 0 && dv > 32);
+        unsigned longs = __ballot_sync(kFull, c >= 0 && dv > 32 && !(grid_hub_flags && dv > kBlockMaxDeg));
         while (longs) {
             const int src = __ffs(longs) - 1;
             longs &= longs - 1;
@@ -1168,8 +1181,13 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
             // may share a step (below the capped step the asynchronous mode
             // moves and joins at once)
             if (P::det || k >= a.cap_step) {
-                if (REFINE) run_refine_apply<P, W, B>(a, list, b0, b8, k, sm);
-                else run_move_apply<P, W, B>(a, list, b0, b8, sm);
+                if (REFINE) {
+                    run_refine_apply<P, W, B>(a, list, b0, b8, k, sm);
+                } else {
+                    const bool hub_layout = a.grid_hubs && b7 > b6;  // run_hubs_grid laid out this step's hubs
+                    run_move_apply<P, W, B>(a, list, b0, b8, sm, hub_layout);
+                    if (hub_layout) hub_flags<P, W>(a, sm, __ldcg(&a.hinfo[0]), __ldcg(&a.hinfo[2]), true);
+                }
                 if (!(ok = grid_barrier(a.bar, a.err, a.spin_limit))) break;
             }
         }
@@ -1323,7 +1341,7 @@ __global__ void __launch_bounds__(256) k_eval_block(SV<P, W> a, const int32_t *_
 template <class P, class W>
 __global__ void __launch_bounds__(256) k_move_apply(SV<P, W> a, const int32_t *__restrict__ list, int64_t count) {
     Sums<P> sm = scalar_sums(a);
-    run_move_apply<P, W, false>(a, list, 0, count, sm);
+    run_move_apply<P, W, false>(a, list, 0, count, sm, false);
     if (P::det) {
         const unsigned __int128 g = warp_sum_u128(sm.dgain.v);
         if ((threadIdx.x & 31) == 0 && g) atomic_add_u128(reinterpret_cast<unsigned long long *>(a.dq_acc), g);

@@ -165,6 +165,11 @@ struct AggCtx {
     const int64_t *tab_off = nullptr;
     const int32_t *tab_idx = nullptr;
     int64_t tab_k0 = 0, tab_k1 = 0, tab_base = 0;
+    // the members of the bin-6 communities as one flat list in table order:
+    // member t of table k is at moff[k] + t, its vertex fm[t], its table
+    // ft[t]; eoff: the scan of their degrees (the flat entry range)
+    const int32_t *fm = nullptr, *ft = nullptr;
+    const int64_t *moff = nullptr, *eoff = nullptr;
     int *err = nullptr;
     unsigned long long *prof = nullptr;
 };
@@ -172,12 +177,20 @@ struct AggCtx {
 cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,
                              cudaStream_t s);
 // bin 6 sizes: tab_size[k] = 2^max(6, ceil log2(2 min(tdeg, ncomm))) of
-// community list[k], tab_idx[list[k]] = k
-cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, int64_t ncomm,
-                               int64_t *tab_size, int32_t *tab_idx, cudaStream_t s);
-// bin 6, tables [tab_k0, tab_k1) (cleared by the caller): every vertex's
-// entries go into its community's table (long rows by the whole warp), then
-// one block per table writes its distinct entries as the community's row
+// community list[k], tab_idx[list[k]] = k, tab_nm[k] its member count
+// (coff: the community-vertex CSR), out_K[list[k]] = 0 (acc type)
+cudaError_t launch_table_sizes(const int32_t *list, int64_t count, const int64_t *tdeg, const int64_t *coff,
+                               int64_t ncomm, bool det, int64_t *tab_size, int32_t *tab_idx, int64_t *tab_nm,
+                               void *out_K, cudaStream_t s);
+// the flat member list of the K6 bin-6 tables (moff: the scan of tab_nm, M6
+// members): fm[t] = vertex, ft[t] = table, fd[t] = degree
+cudaError_t launch_table_members(const int32_t *list, int64_t K6, const int64_t *moff, int64_t M6, const int64_t *coff,
+                                 const int32_t *members, const int32_t *deg, int32_t *fm, int32_t *ft, int32_t *fd,
+                                 cudaStream_t s);
+// bin 6, tables [tab_k0, tab_k1) (cleared by the caller): the flat entry
+// range of their members goes into their tables, 32 entries per warp, then
+// the whole grid writes the tables' distinct entries as the communities'
+// rows, 32 slots per warp
 cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s);
 
 // Rows of a holey CSR (n rows, cap = offsets[n] slots, weights WInt)
