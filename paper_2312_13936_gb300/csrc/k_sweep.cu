@@ -805,13 +805,27 @@ __device__ __forceinline__ long long block_scan_excl(long long x, long long *tot
 // once) or, in an apply phase (by_prop), when its proposal is set.
 template <class P, class W>
 __device__ __forceinline__ void hub_flags(const SV<P, W> &a, const Sums<P> &sm, int64_t np, int64_t E, bool by_prop) {
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < E; x += nthreads) {
-        const int64_t p = range_at(a.heoff, np, x);
-        const int64_t j = __ldcg(&a.hj[p]);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // a contiguous range of entries per warp, following the hub as it goes
+    // (a row is longer than 32 entries: 32 consecutive ones span at most two)
+    const int64_t per = ((E + warps - 1) / warps + 31) & ~(int64_t)31;
+    const int64_t x1 = (gw + 1) * per < E ? (gw + 1) * per : E;
+    if (gw * per >= x1) return;
+    int64_t p = 0;
+    if (lane == 0) p = range_at(a.heoff, np, gw * per);
+    p = __shfl_sync(kFull, p, 0);
+    int64_t nb = __ldcg(&a.heoff[p + 1]);
+    for (int64_t x0 = gw * per; x0 < x1; x0 += 32) {
+        while (x0 >= nb) nb = __ldcg(&a.heoff[++p + 1]);
+        const int64_t x = x0 + lane;
+        if (x >= x1) continue;
+        const int64_t pl = x >= nb ? p + 1 : p;
+        const int64_t j = __ldcg(&a.hj[pl]);
         const int32_t v = __ldg(&a.hubs[j]);
         if (by_prop ? (ldm(&a.prop[v]) < 0) : !__ldcg(&a.hmv[j])) continue;
-        flag_unproc(a, sm, a.idx[a.off[v] + (x - __ldcg(&a.heoff[p]))]);
+        flag_unproc(a, sm, a.idx[a.off[v] + (x - __ldcg(&a.heoff[pl]))]);
     }
 }
 
@@ -880,30 +894,47 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
     const int64_t np = __ldcg(&a.hinfo[0]), S = __ldcg(&a.hinfo[1]), E = __ldcg(&a.hinfo[2]);
     if (np == 0) return true;
+    // Each warp takes one contiguous range of entries (insertion) or slots
+    // (key passes), 32 at a time, and follows the hub they belong to as it
+    // goes: one binary search at the start of its range, then a step to the
+    // next hub when a boundary is passed. A hub's row is longer than 32
+    // entries, so 32 consecutive entries span at most two hubs; its table is
+    // a power of two of at least 8192 slots, so 32 aligned slots lie in one.
     // insertion (the tables are clean: the last scan of a step clears every
     // slot it reads, and the engine clears them before the first sweep)
-    for (int64_t x0 = gw * 32; x0 < E; x0 += warps * 32) {
-        const int64_t x = x0 + lane;
-        int64_t p = -1, tbase = 0;
-        int32_t key = -1, bits = 0;
-        A val = 0;
-        if (x < E) {
-            p = range_at(a.heoff, np, x);
-            const int32_t v = __ldg(&a.hubs[__ldcg(&a.hj[p])]);
-            const int64_t e = a.off[v] + (x - __ldcg(&a.heoff[p]));
-            const int32_t u = a.idx[e];
-            if (u != v && (!REFINE || __ldg(&a.CB[u]) == __ldg(&a.CB[v]))) {
-                key = ldm(&a.C[u]);
-                val = wconv<A>(a.w[e]);
-                tbase = __ldcg(&a.htoff[p]);
-                bits = __ffsll((long long)(__ldcg(&a.htoff[p + 1]) - tbase)) - 1;
-            }
+    {
+        const int64_t per = ((E + warps - 1) / warps + 31) & ~(int64_t)31;
+        const int64_t x1 = (gw + 1) * per < E ? (gw + 1) * per : E;
+        int64_t p = 0, nb = 0;  // hub of the warp's current entry and the end of its row
+        if (gw * per < x1) {
+            if (lane == 0) p = range_at(a.heoff, np, gw * per);
+            p = __shfl_sync(kFull, p, 0);
+            nb = __ldcg(&a.heoff[p + 1]);
         }
-        const unsigned long long pair = key >= 0 ? ((unsigned long long)p << 32) | (uint32_t)key : ~0ULL;
-        const unsigned peers = __match_any_sync(kFull, pair);
-        val = peer_sum(peers, val);
-        if (key >= 0 && lane == __ffs(peers) - 1)
-            if (!hash_add(a.hub_keys + tbase, a.hub_vals + tbase, bits, key, val)) set_error(a.err, kErrHashFull);
+        for (int64_t x0 = gw * per; x0 < x1; x0 += 32) {
+            while (x0 >= nb) nb = __ldcg(&a.heoff[++p + 1]);  // the same on every lane
+            const int64_t x = x0 + lane;
+            const int64_t pl = x >= nb ? p + 1 : p;
+            int32_t key = -1, bits = 0;
+            int64_t tbase = 0;
+            A val = 0;
+            if (x < x1) {
+                const int32_t v = __ldg(&a.hubs[__ldcg(&a.hj[pl])]);
+                const int64_t e = a.off[v] + (x - (pl == p ? nb - a.deg[v] : nb));
+                const int32_t u = a.idx[e];
+                if (u != v && (!REFINE || __ldg(&a.CB[u]) == __ldg(&a.CB[v]))) {
+                    key = ldm(&a.C[u]);
+                    val = wconv<A>(a.w[e]);
+                    tbase = __ldcg(&a.htoff[pl]);
+                    bits = __ffsll((long long)(__ldcg(&a.htoff[pl + 1]) - tbase)) - 1;
+                }
+            }
+            const unsigned long long pair = key >= 0 ? ((unsigned long long)pl << 32) | (uint32_t)key : ~0ULL;
+            const unsigned peers = __match_any_sync(kFull, pair);
+            val = peer_sum(peers, val);
+            if (key >= 0 && lane == __ffs(peers) - 1)
+                if (!hash_add(a.hub_keys + tbase, a.hub_vals + tbase, bits, key, val)) set_error(a.err, kErrHashFull);
+        }
     }
     if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
     // deterministic mode: the largest key per hub -- its high word (pass 0),
@@ -912,19 +943,36 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     // mode: one pass, key and id packed in one word (fp32 key above the
     // complemented id, so that the largest word is the largest key with the
     // smallest id). K_{v->d} from the slot of v's own community. The last
-    // pass clears the slots.
+    // pass clears the slots. The lanes of a warp read one hub's table, so
+    // each pass needs one reduction over the warp and one atomic.
     constexpr int npass = P::det ? 3 : 1;
+    const int64_t sper = ((S + warps - 1) / warps + 31) & ~(int64_t)31;
+    const int64_t s1 = (gw + 1) * sper < S ? (gw + 1) * sper : S;
     for (int pass = 0; pass < npass; ++pass) {
-        for (int64_t s0 = gw * 32; s0 < S; s0 += warps * 32) {
+        int64_t p = 0, nb = 0;  // table of the warp's current slots and its end
+        if (gw * sper < s1) {
+            if (lane == 0) p = range_at(a.htoff, np, gw * sper);
+            p = __shfl_sync(kFull, p, 0);
+            nb = __ldcg(&a.htoff[p + 1]);
+        }
+        int64_t j = -1;
+        int32_t d = -1, v = 0;
+        typename P::acc kv = 0, ks = 0;
+        for (int64_t s0 = gw * sper; s0 < s1; s0 += 32) {
+            if (s0 >= nb || j < 0) {  // the warp enters a table: its hub's constants
+                while (s0 >= nb) nb = __ldcg(&a.htoff[++p + 1]);
+                j = __ldcg(&a.hj[p]);
+                d = __ldcg(&a.hd[j]);
+                v = __ldg(&a.hubs[j]);
+                kv = a.K[v];
+                ks = kscale_of<B>(a, graph_of<B>(a, v));
+            }
             const int64_t s = s0 + lane;
-            int64_t j = -1;
             unsigned long long enc = 0ULL, enc_lo = 0ULL;
             int32_t k = -1;
-            if (s < S) {
+            if (s < s1) {
                 k = __ldcg(&a.hub_keys[s]);
                 if (k >= 0) {
-                    j = __ldcg(&a.hj[range_at(a.htoff, np, s)]);
-                    const int32_t d = __ldcg(&a.hd[j]);
                     const A sum = __ldcg(&a.hub_vals[s]);
                     if (pass == npass - 1) {
                         a.hub_keys[s] = -1;
@@ -934,41 +982,36 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                         if (pass == 0) a.hkvd[j] = sum;
                         k = -1;
                     } else {
-                        const int32_t v = __ldg(&a.hubs[j]);
-                        const int32_t gv = graph_of<B>(a, v);
-                        const typename P::key kk = cand_key<P, W, REFINE>(
-                            a, sm, v, k, move_key(kscale_of<B>(a, gv), sum, a.K[v], ldm(&a.Sig[k]), a.gamma));
+                        const typename P::key kk =
+                            cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, kv, ldm(&a.Sig[k]), a.gamma));
                         key_order(kk, enc, enc_lo);
                         if (!P::det) enc = (enc << 32) | (unsigned long long)(~(uint32_t)k);
                         if (pass == 0) pc.v[3]++;
                     }
                 }
             }
-            // one atomic per hub present in the warp
-            const unsigned long long grp = k >= 0 ? (unsigned long long)j : ~0ULL;
-            const unsigned peers = __match_any_sync(kFull, grp);
+            if (!__any_sync(kFull, k >= 0)) continue;
             if (pass == 0 || (P::det && pass == 1)) {
                 // the largest high word (pass 0), the largest low word among
                 // the slots with the hub's largest high word (pass 1)
                 const bool in = k >= 0 && (pass == 0 || enc == __ldcg(&a.hkey[2 * j]));
                 unsigned long long x = in ? (pass == 0 ? enc : enc_lo) : 0ULL;
-                for (unsigned r = peers; r; r &= r - 1) {
-                    const unsigned long long o = __shfl_sync(peers, x, __ffs(r) - 1);
-                    x = o > x ? o : x;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(kFull, x, o);
+                    x = y > x ? y : x;
                 }
-                if (k >= 0 && lane == __ffs(peers) - 1) {
-                    const unsigned long long m = x;
-                    if (pass == 0) atomicMax(&a.hkey[P::det ? 2 * j : j], m);
-                    else if (m) atomicMax(&a.hkey[2 * j + 1], m);
+                if (lane == 0) {
+                    if (pass == 0) atomicMax(&a.hkey[P::det ? 2 * j : j], x);
+                    else if (x) atomicMax(&a.hkey[2 * j + 1], x);
                 }
             } else {
                 const bool best = k >= 0 && enc == __ldcg(&a.hkey[2 * j]) && enc_lo == __ldcg(&a.hkey[2 * j + 1]);
                 int32_t c = best ? k : INT_MAX;
-                for (unsigned r = peers; r; r &= r - 1) {
-                    const int32_t o = __shfl_sync(peers, c, __ffs(r) - 1);
-                    c = o < c ? o : c;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int32_t y = __shfl_xor_sync(kFull, c, o);
+                    c = y < c ? y : c;
                 }
-                if (k >= 0 && lane == __ffs(peers) - 1 && c != INT_MAX) atomicMin(&a.hcand[j], c);
+                if (lane == 0 && c != INT_MAX) atomicMin(&a.hcand[j], c);
             }
         }
         if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
