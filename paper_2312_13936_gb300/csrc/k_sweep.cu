@@ -946,7 +946,9 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     // pass clears the slots. The lanes of a warp read one hub's table, so
     // each pass needs one reduction over the warp and one atomic.
     constexpr int npass = P::det ? 3 : 1;
-    const int64_t sper = ((S + warps - 1) / warps + 31) & ~(int64_t)31;
+    constexpr int Q = 4;  // slots per lane and iteration: 128 aligned slots lie in one table
+    using T = typename P::tot;
+    const int64_t sper = ((S + warps - 1) / warps + 32 * Q - 1) & ~(int64_t)(32 * Q - 1);
     const int64_t s1 = (gw + 1) * sper < S ? (gw + 1) * sper : S;
     for (int pass = 0; pass < npass; ++pass) {
         int64_t p = 0, nb = 0;  // table of the warp's current slots and its end
@@ -958,7 +960,8 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
         int64_t j = -1;
         int32_t d = -1, v = 0;
         typename P::acc kv = 0, ks = 0;
-        for (int64_t s0 = gw * sper; s0 < s1; s0 += 32) {
+        unsigned long long hhi = 0, hlo = 0;  // the hub's largest key so far (passes 1 and 2)
+        for (int64_t s0 = gw * sper; s0 < s1; s0 += 32 * Q) {
             if (s0 >= nb || j < 0) {  // the warp enters a table: its hub's constants
                 while (s0 >= nb) nb = __ldcg(&a.htoff[++p + 1]);
                 j = __ldcg(&a.hj[p]);
@@ -966,52 +969,76 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                 v = __ldg(&a.hubs[j]);
                 kv = a.K[v];
                 ks = kscale_of<B>(a, graph_of<B>(a, v));
-            }
-            const int64_t s = s0 + lane;
-            unsigned long long enc = 0ULL, enc_lo = 0ULL;
-            int32_t k = -1;
-            if (s < s1) {
-                k = __ldcg(&a.hub_keys[s]);
-                if (k >= 0) {
-                    const A sum = __ldcg(&a.hub_vals[s]);
-                    if (pass == npass - 1) {
-                        a.hub_keys[s] = -1;
-                        a.hub_vals[s] = 0;
-                    }
-                    if (k == d) {
-                        if (pass == 0) a.hkvd[j] = sum;
-                        k = -1;
-                    } else {
-                        const typename P::key kk =
-                            cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, sum, kv, ldm(&a.Sig[k]), a.gamma));
-                        key_order(kk, enc, enc_lo);
-                        if (!P::det) enc = (enc << 32) | (unsigned long long)(~(uint32_t)k);
-                        if (pass == 0) pc.v[3]++;
-                    }
+                if (P::det && pass > 0) {
+                    hhi = __ldcg(&a.hkey[2 * j]);
+                    hlo = __ldcg(&a.hkey[2 * j + 1]);
                 }
             }
-            if (!__any_sync(kFull, k >= 0)) continue;
-            if (pass == 0 || (P::det && pass == 1)) {
+            // the lane's slots s0 + lane + 32 q: keys first, then the sums
+            // and the candidates' totals, all loads of a round in flight
+            int32_t kq[Q];
+            A vq[Q];
+            T sq[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int64_t sl = s0 + 32 * q + lane;
+                kq[q] = sl < s1 ? __ldcg(&a.hub_keys[sl]) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                vq[q] = 0;
+                sq[q] = 0;
+                if (kq[q] >= 0) {
+                    vq[q] = __ldcg(&a.hub_vals[s0 + 32 * q + lane]);
+                    if (kq[q] != d) sq[q] = ldm(&a.Sig[kq[q]]);
+                }
+            }
+            unsigned long long lmax = 0ULL;
+            int32_t lmin = INT_MAX;
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int32_t k = kq[q];
+                if (k < 0) continue;
+                if (pass == npass - 1) {
+                    a.hub_keys[s0 + 32 * q + lane] = -1;
+                    a.hub_vals[s0 + 32 * q + lane] = 0;
+                }
+                if (k == d) {
+                    if (pass == 0) a.hkvd[j] = vq[q];
+                    continue;
+                }
+                unsigned long long enc, enc_lo;
+                key_order(cand_key<P, W, REFINE>(a, sm, v, k, move_key(ks, vq[q], kv, sq[q], a.gamma)), enc, enc_lo);
+                if (!P::det) enc = (enc << 32) | (unsigned long long)(~(uint32_t)k);
+                any = true;
+                if (pass == 0) {
+                    pc.v[3]++;
+                    lmax = enc > lmax ? enc : lmax;
+                } else if (pass == 1) {
+                    if (enc == hhi) lmax = enc_lo > lmax ? enc_lo : lmax;
+                } else if (enc == hhi && enc_lo == hlo) {
+                    lmin = k < lmin ? k : lmin;
+                }
+            }
+            if (!__any_sync(kFull, any)) continue;
+            if (pass < 2) {
                 // the largest high word (pass 0), the largest low word among
                 // the slots with the hub's largest high word (pass 1)
-                const bool in = k >= 0 && (pass == 0 || enc == __ldcg(&a.hkey[2 * j]));
-                unsigned long long x = in ? (pass == 0 ? enc : enc_lo) : 0ULL;
                 for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long y = __shfl_xor_sync(kFull, x, o);
-                    x = y > x ? y : x;
+                    const unsigned long long y = __shfl_xor_sync(kFull, lmax, o);
+                    lmax = y > lmax ? y : lmax;
                 }
                 if (lane == 0) {
-                    if (pass == 0) atomicMax(&a.hkey[P::det ? 2 * j : j], x);
-                    else if (x) atomicMax(&a.hkey[2 * j + 1], x);
+                    if (pass == 0) atomicMax(&a.hkey[P::det ? 2 * j : j], lmax);
+                    else if (lmax) atomicMax(&a.hkey[2 * j + 1], lmax);
                 }
             } else {
-                const bool best = k >= 0 && enc == __ldcg(&a.hkey[2 * j]) && enc_lo == __ldcg(&a.hkey[2 * j + 1]);
-                int32_t c = best ? k : INT_MAX;
                 for (int o = 16; o > 0; o >>= 1) {
-                    const int32_t y = __shfl_xor_sync(kFull, c, o);
-                    c = y < c ? y : c;
+                    const int32_t y = __shfl_xor_sync(kFull, lmin, o);
+                    lmin = y < lmin ? y : lmin;
                 }
-                if (lane == 0 && c != INT_MAX) atomicMin(&a.hcand[j], c);
+                if (lane == 0 && lmin != INT_MAX) atomicMin(&a.hcand[j], lmin);
             }
         }
         if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
