@@ -332,12 +332,11 @@ __device__ __forceinline__ void flag_unproc(const SV<P, W> &a, const Sums<P> &sm
 // vertices of a graph whose phase has converged are left alone.
 template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ bool take_vertex(const SV<P, W> &a, int32_t v, int32_t &d, int32_t gv) {
-    if (B && ldm(&a.gdone[gv])) return false;
     if (REFINE) {
         d = ldm(&a.C[v]);
-        return ldm(&a.size[d]) == 1;
+        return ldm(&a.size[d]) == 1 && !(B && ldm(&a.gdone[gv]));
     }
-    const bool e = ldm(&a.unproc[v]) != 0;
+    const bool e = ldm(&a.unproc[v]) != 0 && !(B && ldm(&a.gdone[gv]));
     if (e) {
         a.unproc[v] = 0;
         d = ldm(&a.C[v]);
@@ -354,20 +353,31 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += nthreads) {
         const int32_t v = list[t];
-        // the vertex's header loads are independent: issue them together
-        const int32_t d = ldm(&a.C[v]);
-        const uint8_t up = REFINE ? (uint8_t)1 : ldm(&a.unproc[v]);
-        const A Kv = a.K[v];
-        const int64_t e0 = a.off[v];
-        const int32_t dv = a.deg[v];
-        const int32_t gv = graph_of<B>(a, v);
-        const bool elig = (REFINE ? (ldm(&a.size[d]) == 1) : (up != 0)) && !(B && ldm(&a.gdone[gv]));
+        // eligibility first (Algorithm 2 pruning: the unprocessed flag;
+        // refinement: the size of the vertex's community), so that a pruned
+        // vertex costs one flag load and none of the header loads below
+        int32_t d = 0;
+        bool elig;
+        if (REFINE) {
+            d = ldm(&a.C[v]);
+            elig = ldm(&a.size[d]) == 1;
+        } else {
+            elig = ldm(&a.unproc[v]) != 0;
+        }
+        const int32_t gv = (B && elig) ? graph_of<B>(a, v) : 0;
+        if (B && elig) elig = !ldm(&a.gdone[gv]);
         if (!elig) {
             if (proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
             pc.v[1]++;
             continue;
         }
-        if (!REFINE) a.unproc[v] = 0;  // processed (Algorithm 2 pruning)
+        if (!REFINE) {
+            a.unproc[v] = 0;  // processed (Algorithm 2 pruning)
+            d = ldm(&a.C[v]);
+        }
+        const A Kv = a.K[v];
+        const int64_t e0 = a.off[v];
+        const int32_t dv = a.deg[v];
         const typename P::tot sd = ldm(&a.Sig[d]);
         const int32_t bv = REFINE ? a.CB[v] : 0;
         int32_t jj[E];
