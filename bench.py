@@ -289,55 +289,6 @@ def optional_leg(fn, *args):
         return {"error": f"{type(e).__name__}: {e}"[:400]}
 
 
-def lpt_shares(m, world):
-    """Graph ids of each rank: longest-processing-time-first by entry count.
-
-    Graphs in decreasing m (ties by smaller id) go one by one to the rank with
-    the least load so far (ties by smaller rank). Each rank's ids come back in
-    increasing order. The largest load is at most 4/3 of the best possible
-    one (Graham's LPT bound) and at most the mean load plus the largest m."""
-    import heapq
-
-    import numpy as np
-    m = np.asarray(m, dtype=np.int64)
-    order = np.lexsort((np.arange(len(m)), -m))
-    heap = [(0, r) for r in range(world)]
-    shares = [[] for _ in range(world)]
-    for g in order:
-        load, r = heapq.heappop(heap)
-        shares[r].append(int(g))
-        heapq.heappush(heap, (load + int(m[g]), r))
-    return [np.array(sorted(x), dtype=np.int64) for x in shares]
-
-
-def graph_entries(b):
-    """Directed CSR entries of every graph of a packed batch."""
-    return b.offsets[b.vseg[1:]] - b.offsets[b.vseg[:-1]]
-
-
-def pack_graphs(b, ids):
-    """The graphs ids (increasing) of a packed batch as a packed batch of their
-    own: vertex segments, offsets, local indices, weights."""
-    import numpy as np
-    ids = np.asarray(ids, dtype=np.int64)
-    if len(ids) == b.num_graphs and np.array_equal(ids, np.arange(b.num_graphs)):
-        return b.vseg, b.offsets, b.indices, b.weights  # the whole batch: no copy
-    nv = b.vseg[ids + 1] - b.vseg[ids]
-    vseg = np.zeros(len(ids) + 1, dtype=np.int64)
-    np.cumsum(nv, out=vseg[1:])
-    offs, idxs, ws = [np.zeros(1, dtype=np.int64)], [], []
-    base = 0
-    for g in ids:
-        v0, v1 = int(b.vseg[g]), int(b.vseg[g + 1])
-        e0, e1 = int(b.offsets[v0]), int(b.offsets[v1])
-        offs.append(b.offsets[v0 + 1:v1 + 1] - e0 + base)
-        idxs.append(b.indices[e0:e1])  # local to their graph already
-        ws.append(b.weights[e0:e1])
-        base += e1 - e0
-    cat = (lambda xs, dt: np.concatenate(xs).astype(dt, copy=False) if xs else np.zeros(0, dtype=dt))
-    return vseg, cat(offs, np.int64), cat(idxs, b.indices.dtype), cat(ws, b.weights.dtype)
-
-
 def reduce_stats(stats, nmax, world):
     """All-reduce a 1-D tensor over the ranks: its first nmax entries (times)
     take the maximum over ranks, the others the sum. No collective for one rank."""
@@ -361,8 +312,8 @@ def batched_form(args, rank, world, mode, flags):
     import paper_2312_13936_gb300 as lg
     b = gen.sbm_batch(args.batch_graphs, seed=4)
     G = b.num_graphs
-    ids = lpt_shares(graph_entries(b), world)[rank]
-    h = lg.LeidenBatch(*pack_graphs(b, ids))
+    ids = lg.shard.lpt_shares(lg.shard.graph_entries(b), world)[rank]
+    h = lg.LeidenBatch(*lg.shard.pack_share(b, ids))
     h.run(mode=mode, flags=flags)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()

@@ -553,3 +553,5 @@ def modularity(offsets, indices, weights, membership, resolution: float = 1.0, s
     n = int(offsets.numel() - 1)
     return leiden_modularity(n, _ptr(offsets), _ptr(indices), _ptr(weights), _ptr(membership), resolution,
                              _stream_ptr(stream))
+
+from . import shard  # noqa: E402  (batches on several GPUs; uses the names above)

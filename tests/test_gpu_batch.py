@@ -198,3 +198,22 @@ def test_batch_mixed_layer_caps_equal_single_runs():
         assert passes[g] == sts.passes, g
         ref = oracle.leiden(G, mode=oracle.SYNC)
         assert np.array_equal(ms, ref.membership), g
+
+
+def test_sharded_batch_api_one_rank_equals_batch_run():
+    """paper_2312_13936_gb300.shard.run_sharded on one rank: the LPT share is
+    the whole batch, and its gathered per-graph results equal the graphs'
+    single runs (deterministic mode)."""
+    graphs = mixed_graphs()
+    vseg, off, idx, w = lg.pack_batch(graphs)
+
+    class Packed:
+        pass
+    b = Packed()
+    b.num_graphs, b.vseg, b.offsets, b.indices, b.weights = len(graphs), vseg, off, idx, w
+    memb, q, ids, st = lg.shard.run_sharded(b, 0, 1, mode=lg.LEIDEN_DETERMINISTIC)
+    assert ids.tolist() == list(range(len(graphs)))
+    for g, G in enumerate(graphs):
+        ms, qs, _, _ = run_gpu(G, lg.LEIDEN_DETERMINISTIC)
+        assert np.array_equal(memb[g], ms), g
+        assert q[g] == qs, g
