@@ -559,6 +559,28 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+def tuning_report(h, mode, flags, runs=3):
+    """The launch shape the handle took (the autotuner cache's entry for this
+    GPU and graph class, else the defaults) and the median device time of a
+    run with it and with the defaults (outside the timed region)."""
+    import statistics as st_
+
+    import paper_2312_13936_gb300 as lg
+    shape = h.tuning()
+    default = lg.leiden_tuning_default().as_dict()
+
+    def med():
+        return st_.median(h.run(mode=mode, flags=flags)[2].ms_total for _ in range(runs))
+    tuned_ms = med()
+    default_ms = tuned_ms
+    if shape != default:
+        h.set_tuning(**default)
+        default_ms = med()
+        h.set_tuning(**shape)
+    return {"shape": shape, "from_cache": shape != default, "tuned_ms": tuned_ms, "default_ms": default_ms,
+            "cache": "paper_2312_13936_gb300/tuning_cache.json"}
+
+
 def timed_runs(h, mode, flags, steps, warmup, stream, world, dev, clocks=None):
     """W untimed runs, then K runs between barriers and synchronisations,
     timed with CUDA events on the run's stream (max over ranks); the first
@@ -636,6 +658,8 @@ def road_form(args, mode, flags, stream, world, dev, peak, peak_kind):
            "gpu_launches": launches,
            "roofline": roofline_of(prof, peak, peak_kind, name, ms / args.steps),
            "kernel_classes": {f"{k[0]}/{k[1]}": v for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}}
+    if world == 1:
+        out["tuning"] = optional_leg(tuning_report, h, mode, flags)
     if not args.no_variants and world == 1:
         out["variants"] = optional_leg(variants_form, h, off, idx, mode, flags, stream)
     h.close()
@@ -682,6 +706,7 @@ def main():
     value = world * args.steps * nnz / (ms / 1e3)
     # every community connected? (Algorithm 5 on the GPU, outside the timed region)
     disconnected = lg.disconnected(off, idx, memb)
+    tuning = optional_leg(tuning_report, h, mode, base_flags) if world == 1 else None
     h.close()
     graph_bytes = 8 * (n + 1) + 8 * nnz
 
@@ -774,6 +799,7 @@ def main():
                    "phase_ms": {"move": st.ms_move, "refine": st.ms_refine, "aggregate": st.ms_aggregate,
                                 "other": st.ms_other}},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck, "gpu_launches": launches,
+        "tuning": tuning,
         "road": road,
         "batched": batched,
         "served": served,

@@ -342,6 +342,54 @@ leiden_status leiden_trace_get(leiden_graph_t g, int32_t pass, int32_t what, voi
  * profiled. */
 leiden_status leiden_profile_get(leiden_graph_t g, leiden_kernel_profile *out);
 
+/* Launch shape of a handle's kernels: degree-bin bounds and the persistent
+ * sweep's grid. None of them changes a result of the deterministic mode (the
+ * bins only choose how a vertex's or community's neighbour weights are
+ * gathered; every decision is exact), and in the asynchronous mode they
+ * change only the order of concurrent updates. The paper's counterpart is
+ * the OpenMP dynamic schedule and its chunk size (Section 4.1), which it
+ * tuned by measurement; here an autotuner measures the candidates per GPU
+ * and graph class and stores the best in a cache (leiden_tuning_lookup). */
+typedef struct {
+    int32_t thread_max_deg;      /* sweeps: rows up to this many entries take one thread each (1..8); default 8 */
+    int32_t warp_max_deg;        /* rows (community entries) up to this many take one warp and a shared-memory
+                                    table (32..256); default 256 */
+    int32_t block_max_deg;       /* rows up to this many take one block and a shared-memory table (128..2048,
+                                    >= warp_max_deg); longer rows take the whole grid (sweeps) or a global
+                                    table (aggregation); default 2048 */
+    int32_t coop_blocks_per_sm;  /* blocks per SM of the persistent sweep (0: as many as fit); default 0 */
+    int32_t vertices_per_block;  /* persistent sweep: vertices per block below a full grid (256..65536);
+                                    default 2048 */
+    int32_t reserved[3];
+} leiden_tuning;
+
+/* Fill *t with the defaults listed above. */
+void leiden_tuning_default(leiden_tuning *t);
+
+/* Set (or read) the launch shape of a handle (single graph or batch); it
+ * holds for its later runs. LEIDEN_ERR_INVALID for a value outside the
+ * ranges above. leiden_create and leiden_batch_create start from the
+ * defaults, or, when the environment variable LEIDEN_TUNING_CACHE names a
+ * cache file, from leiden_tuning_lookup of that cache for the current GPU
+ * and the input graph (the defaults when nothing matches). */
+leiden_status leiden_set_tuning(leiden_graph_t g, const leiden_tuning *t);
+leiden_status leiden_get_tuning(leiden_graph_t g, leiden_tuning *t);
+
+/* Autotuner cache lookup (host only). The cache is a JSON file
+ * {"format": 1, "entries": [{"gpu": <name>, "heavy_tailed": 0|1,
+ * "log2_vertices": <int>, "log2_mean_degree": <int>, "thread_max_deg": ...,
+ * "warp_max_deg": ..., "block_max_deg": ..., "coop_blocks_per_sm": ...,
+ * "vertices_per_block": ..., other keys ignored}, ...]}. A graph of n
+ * vertices, nnz CSR entries and largest degree max_degree has the class
+ * (heavy_tailed = max_degree > 64 nnz / n, log2_vertices = round(log2 n),
+ * log2_mean_degree = round(log2(nnz / n))); among the entries of gpu_name
+ * with the same heavy_tailed, the one nearest in |d log2_vertices| +
+ * |d log2_mean_degree| (ties: the first in the file) fills *out.
+ * LEIDEN_ERR_INVALID (and *out untouched) if the file cannot be read or
+ * parsed or no entry matches. */
+leiden_status leiden_tuning_lookup(const char *cache_path, const char *gpu_name, int64_t n, int64_t nnz,
+                                   int64_t max_degree, leiden_tuning *out);
+
 /* Testing aid for the out-of-memory paths. The paper has no counterpart.
  * After `after` more successful device allocations made by handles
  * (leiden_create, leiden_batch_create, leiden_run, leiden_batch_run and the

@@ -27,7 +27,8 @@ __all__ = [
     "leiden_batch_run", "leiden_batch_info", "LeidenBatch", "pack_batch", "ServerState", "leiden_server_create",
     "leiden_server_submit", "leiden_server_step", "leiden_server_next", "leiden_server_result", "leiden_server_info",
     "leiden_server_destroy", "LeidenServer", "leiden_disconnected", "disconnected", "leiden_csr_from_edges",
-    "csr_from_edges", "FLAG_TEST_STALL_BARRIER", "leiden_test_fail_allocation",
+    "csr_from_edges", "FLAG_TEST_STALL_BARRIER", "leiden_test_fail_allocation", "Tuning", "leiden_tuning_default",
+    "leiden_set_tuning", "leiden_get_tuning", "leiden_tuning_lookup", "TUNING_CACHE",
 ]
 
 LEIDEN_HOST, LEIDEN_DEVICE = 0, 1
@@ -73,6 +74,22 @@ class KernelProfile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double),
                 ("items", ctypes.c_int64), ("skipped", ctypes.c_int64), ("edges", ctypes.c_int64),
                 ("distinct", ctypes.c_int64), ("moved", ctypes.c_int64)]
+
+
+class Tuning(ctypes.Structure):
+    """Launch shape of a handle (leiden_tuning): degree-bin bounds and the
+    persistent sweep's grid; none changes a deterministic result."""
+    _fields_ = [("thread_max_deg", ctypes.c_int32), ("warp_max_deg", ctypes.c_int32),
+                ("block_max_deg", ctypes.c_int32), ("coop_blocks_per_sm", ctypes.c_int32),
+                ("vertices_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+    KEYS = ("thread_max_deg", "warp_max_deg", "block_max_deg", "coop_blocks_per_sm", "vertices_per_block")
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k in self.KEYS}
+
+
+# the autotuner's cache shipped with the package (LEIDEN_TUNING_CACHE overrides it)
+TUNING_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 
 
 class ServerState(ctypes.Structure):
@@ -123,6 +140,15 @@ def library(build_if_missing: bool = False) -> ctypes.CDLL:
         lib.leiden_server_info.argtypes = [_VP, ctypes.POINTER(ServerState)]
         lib.leiden_server_destroy.argtypes = [_VP]
         lib.leiden_disconnected.argtypes = [_I64, _VP, _VP, _VP, _VP, ctypes.POINTER(_I64)]
+        lib.leiden_tuning_default.argtypes = [ctypes.POINTER(Tuning)]
+        lib.leiden_tuning_default.restype = None
+        lib.leiden_set_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
+        lib.leiden_set_tuning.restype = ctypes.c_int
+        lib.leiden_get_tuning.argtypes = [_VP, ctypes.POINTER(Tuning)]
+        lib.leiden_get_tuning.restype = ctypes.c_int
+        lib.leiden_tuning_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, _I64, _I64, _I64,
+                                             ctypes.POINTER(Tuning)]
+        lib.leiden_tuning_lookup.restype = ctypes.c_int
         lib.leiden_test_fail_allocation.argtypes = [_I64]
         lib.leiden_test_fail_allocation.restype = ctypes.c_int
         lib.leiden_csr_from_edges.argtypes = [_I64, _I64, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_int32,
@@ -251,6 +277,63 @@ def leiden_server_destroy(server) -> None:
     _check(library().leiden_server_destroy(server))
 
 
+def leiden_tuning_default() -> Tuning:
+    t = Tuning()
+    library().leiden_tuning_default(ctypes.byref(t))
+    return t
+
+
+def leiden_set_tuning(handle, t: Tuning) -> None:
+    _check(library().leiden_set_tuning(handle, ctypes.byref(t)))
+
+
+def leiden_get_tuning(handle) -> Tuning:
+    t = Tuning()
+    _check(library().leiden_get_tuning(handle, ctypes.byref(t)))
+    return t
+
+
+def leiden_tuning_lookup(cache_path: str, gpu_name: str, n: int, nnz: int, max_degree: int):
+    """The cache entry for the GPU and the graph's class, or None."""
+    t = Tuning()
+    rc = library().leiden_tuning_lookup(cache_path.encode(), gpu_name.encode(), n, nnz, max_degree, ctypes.byref(t))
+    return t if rc == 0 else None
+
+
+def _apply_cached_tuning(handle, n, nnz, max_degree):
+    """Launch shape of a new handle from the autotuner cache (the package's,
+    or LEIDEN_TUNING_CACHE's) for the current GPU and the graph's class; the
+    library's defaults when there is no entry."""
+    if os.environ.get("LEIDEN_TUNING_CACHE"):
+        return  # leiden_create has applied it already
+    if not os.path.exists(TUNING_CACHE):
+        return
+    import torch
+    t = leiden_tuning_lookup(TUNING_CACHE, torch.cuda.get_device_name(), n, nnz, max_degree)
+    if t is not None:
+        leiden_set_tuning(handle, t)
+
+
+def _set_tuning(handle, tuning=None, **kw):
+    t = leiden_get_tuning(handle) if tuning is None else tuning
+    if isinstance(t, dict):
+        kw = {**t, **kw}
+        t = leiden_get_tuning(handle)
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    leiden_set_tuning(handle, t)
+
+
+def _init_tuning(handle, tuning, off, n, nnz):
+    if isinstance(tuning, str) and tuning == "cache":
+        maxdeg = int((off[1:] - off[:-1]).max().item()) if n > 0 else 0
+        _apply_cached_tuning(handle, n, nnz, maxdeg)
+    elif tuning is None:
+        leiden_set_tuning(handle, leiden_tuning_default())
+    else:
+        _set_tuning(handle, tuning)
+
+
 def leiden_test_fail_allocation(after: int) -> None:
     """Testing aid: the handle allocation after `after` more successful ones
     fails with LEIDEN_ERR_OOM (negative: no injection)."""
@@ -329,7 +412,10 @@ class Leiden:
     stats) with membership a torch.int32 CUDA tensor of canonical labels.
     """
 
-    def __init__(self, offsets, indices, weights=None, validate: bool = False, stream=None):
+    def __init__(self, offsets, indices, weights=None, validate: bool = False, stream=None, tuning="cache"):
+        """tuning: "cache" (the autotuner cache's entry for this GPU and the
+        graph's class, else the defaults), None (the defaults), or a Tuning
+        or dict of its fields."""
         import torch
         self._torch = torch
         self.stream = stream
@@ -343,6 +429,14 @@ class Leiden:
                                     int(validate), _stream_ptr(stream))
         self.device = dev
         self._input = (off, idx, w)  # kept for modularity checks
+        _init_tuning(self.handle, tuning, off, self.n, self.nnz)
+
+    def set_tuning(self, tuning=None, **kw):
+        """Set the launch shape: a Tuning, or fields by name over the current one."""
+        _set_tuning(self.handle, tuning, **kw)
+
+    def tuning(self) -> dict:
+        return leiden_get_tuning(self.handle).as_dict()
 
     def run(self, mode: int = LEIDEN_ASYNC, trace: bool = False, **kw):
         p = leiden_params_default()
@@ -405,7 +499,8 @@ class LeidenBatch:
     local to the graph, in the packed vertex order.
     """
 
-    def __init__(self, vtx_seg, offsets, indices, weights=None, validate: bool = False, stream=None):
+    def __init__(self, vtx_seg, offsets, indices, weights=None, validate: bool = False, stream=None,
+                 tuning="cache"):
         import torch
         self._torch = torch
         self.stream = stream
@@ -420,6 +515,13 @@ class LeidenBatch:
         self.handle = leiden_batch_create(self.num_graphs, self.vtx_seg, self.nnz, _ptr(off), _ptr(idx), _ptr(w),
                                           LEIDEN_DEVICE, int(validate), _stream_ptr(stream))
         self.device = dev
+        _init_tuning(self.handle, tuning, off, self.n, self.nnz)
+
+    def set_tuning(self, tuning=None, **kw):
+        _set_tuning(self.handle, tuning, **kw)
+
+    def tuning(self) -> dict:
+        return leiden_get_tuning(self.handle).as_dict()
 
     def run(self, mode: int = LEIDEN_ASYNC, **kw):
         p = leiden_params_default()

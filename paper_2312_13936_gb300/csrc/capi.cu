@@ -12,6 +12,35 @@ struct leiden_server_s {
 
 extern "C" {
 
+void leiden_tuning_default(leiden_tuning *t) {
+    if (t) lgb::tuning_default(*t);
+}
+
+leiden_status leiden_set_tuning(leiden_graph_t g, const leiden_tuning *t) {
+    if (!g || !t) {
+        lgb::set_last_error("NULL handle or tuning");
+        return LEIDEN_ERR_INVALID;
+    }
+    return g->h.set_tuning(*t);
+}
+
+leiden_status leiden_get_tuning(leiden_graph_t g, leiden_tuning *t) {
+    if (!g) {
+        lgb::set_last_error("NULL handle");
+        return LEIDEN_ERR_INVALID;
+    }
+    return g->h.get_tuning(t);
+}
+
+leiden_status leiden_tuning_lookup(const char *cache_path, const char *gpu_name, int64_t n, int64_t nnz,
+                                   int64_t max_degree, leiden_tuning *out) {
+    if (!cache_path || !gpu_name || !out || n < 0 || nnz < 0 || max_degree < 0) {
+        lgb::set_last_error("invalid arguments to leiden_tuning_lookup");
+        return LEIDEN_ERR_INVALID;
+    }
+    return lgb::tuning_lookup(cache_path, gpu_name, n, nnz, max_degree, *out);
+}
+
 leiden_status leiden_test_fail_allocation(int64_t after) {
     lgb::g_fail_alloc_after.store(after < 0 ? -1 : after);
     return LEIDEN_OK;

@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -79,6 +80,18 @@ leiden_status Handle::create(int64_t n, int64_t nnz, const int64_t *offsets, con
     q.nonint = q.hsc->nonint != 0;
     q.wsum = q.hsc->wsum;
     q.maxdeg0 = q.hsc->maxdeg;
+    // launch shape from the autotuner cache named by LEIDEN_TUNING_CACHE,
+    // for this GPU and this graph's class (the defaults otherwise)
+    if (const char *cache = std::getenv("LEIDEN_TUNING_CACHE")) {
+        int dev = 0;
+        cudaDeviceProp prop;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+            leiden_tuning t;
+            const std::string keep = last_error();
+            if (tuning_lookup(cache, prop.name, n, nnz, q.maxdeg0, t) == LEIDEN_OK) q.tune = t;
+            set_last_error(keep);
+        }
+    }
     if (G > 1) {  // weight sum of every graph, for the deterministic mode's 2m < 2^53 rule
         GraphView g0;
         g0.n = n;
@@ -167,7 +180,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     const int32_t nkeys = nsteps * kNumBins;
     ST(q.ensure_part_tmp(partition_tmp_bytes(n, nkeys + 1)));
     // one vertex list per (schedule step, degree bin), step-major
-    CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.key, s));
+    CK(launch_step_bin_keys(q.step, G.deg, n, nsteps, false, q.bins(), q.key, s));
     CK(launch_partition(q.key, n, nkeys + 1, q.key_off, q.list, q.part_tmp, s));  // + edgeless bucket
     CK(launch_max_i32(G.deg, n, &q.dsc->maxdeg, s));
     q.launches += 7;
@@ -227,7 +240,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     int hub_bits = 0, hub_regions = 0;
     if (!grid_hubs) {
         const int maxdeg = q.hsc->maxdeg;
-        if (maxdeg > kBlockMaxDeg) {
+        if (maxdeg > q.tune.block_max_deg) {
             hub_bits = ceil_log2_h(2 * (int64_t)maxdeg);
             const size_t per = ((size_t)1 << hub_bits) * 12;
             hub_regions = (int)std::max<size_t>(1, std::min<size_t>((size_t)q.sm, ((size_t)4 << 30) / per));
@@ -270,6 +283,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
     sc.nsteps = nsteps;
     sc.key_off = q.key_off;
     sc.bar = q.bar;
+    sc.block_max = q.tune.block_max_deg;
     sc.hub_regions = hub_regions;
     sc.gid = batch ? cur_gid : nullptr;
     sc.gks = q.gks;
@@ -314,7 +328,9 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         sc.rand_refine = refine && (prm.flags & LEIDEN_FLAG_RANDOM_REFINE) != 0;
         sc.rseed = prm.seed + 0xD1B54A32D192ED03ULL * (uint64_t)(64 * (r.gpass ? 0 : lp));
         const bool single = refine && (prm.flags & LEIDEN_FLAG_REFINE_SINGLE_SWEEP);
-        const int per_sm = step_launches ? 0 : sweep_coop_blocks_per_sm(det, sG.w_int, refine);
+        int per_sm = step_launches ? 0 : sweep_coop_blocks_per_sm(det, sG.w_int, refine);
+        if (per_sm > 0 && q.tune.coop_blocks_per_sm > 0 && q.tune.coop_blocks_per_sm < per_sm)
+            per_sm = q.tune.coop_blocks_per_sm;  // the handle's launch shape
         CK(launch_phase_init(q.gstate, NG, q.gdone, giters, s));
         sc.giters = giters;
         if (batch && per_sm <= 0) {
@@ -322,11 +338,12 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             return LEIDEN_ERR_UNSUPPORTED;
         }
         if (per_sm > 0) {
-            // enough blocks for the graph (about kCoopVerticesPerBlock
-            // each), so small graphs do not pay a full-GPU barrier per step
-            // and graphs of one block synchronise with __syncthreads only
+            // enough blocks for the graph (about vertices_per_block each),
+            // so small graphs do not pay a full-GPU barrier per step and
+            // graphs of one block synchronise with __syncthreads only
             int grid = per_sm * q.sm;
-            const int64_t want = (n + kCoopVerticesPerBlock - 1) / kCoopVerticesPerBlock;
+            const int64_t vpb = q.tune.vertices_per_block;
+            const int64_t want = (n + vpb - 1) / vpb;
             if (want < grid) grid = (int)(want < 1 ? 1 : want);
             sc.hub_regions = hub_regions > grid ? grid : hub_regions;
             sc.max_it = prm.max_iterations;
@@ -462,7 +479,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         ST(q.alloc(&q.agg[dst].deg, q.n0));
     }
     CK(launch_exclusive_scan(q.tdeg, q.agg[dst].off, ncomm, q.scan_tmp, s));
-    CK(launch_comm_bin_keys(q.tdeg, ncomm, q.key, s));
+    CK(launch_comm_bin_keys(q.tdeg, ncomm, q.bins(), q.key, s));
     CK(launch_partition(q.key, ncomm, kNumBins, q.key_off, q.list, q.part_tmp, s));
     CK(launch_max_i64(q.tdeg, ncomm, &q.dsc->maxtdeg, s));
     q.launches += 16;
@@ -870,6 +887,24 @@ leiden_status Handle::graph_info(int32_t *passes, int64_t *communities) const {
     }
     if (passes) std::memcpy(passes, p->hpasses.data(), sizeof(int32_t) * p->G);
     if (communities) std::memcpy(communities, p->hcomm.data(), sizeof(int64_t) * p->G);
+    return LEIDEN_OK;
+}
+
+leiden_status Handle::set_tuning(const leiden_tuning &t) {
+    if (!tuning_valid(t)) {
+        set_last_error("leiden_tuning value outside its range");
+        return LEIDEN_ERR_INVALID;
+    }
+    p->tune = t;
+    return LEIDEN_OK;
+}
+
+leiden_status Handle::get_tuning(leiden_tuning *t) const {
+    if (!t) {
+        set_last_error("tuning is NULL");
+        return LEIDEN_ERR_INVALID;
+    }
+    *t = p->tune;
     return LEIDEN_OK;
 }
 

@@ -41,6 +41,9 @@ class Handle {
                                 int64_t *communities);
     leiden_status server_info(leiden_server_state *out) const;
     leiden_status trace_get(int pass, int what, void *dst, int64_t *count) const;
+    // launch shape of later runs (leiden_tuning)
+    leiden_status set_tuning(const leiden_tuning &t);
+    leiden_status get_tuning(leiden_tuning *t) const;
     leiden_status profile_get(leiden_kernel_profile *out) const;
 
     struct Impl;  // device state (engine_impl.h)
@@ -54,6 +57,11 @@ leiden_status disconnected_device(int64_t n, const int64_t *off, const int32_t *
 leiden_status csr_from_edges(int64_t n, int64_t m, const int32_t *src, const int32_t *dst, const float *w, int where,
                              int drop_self, int combine, int64_t *offsets, int32_t *indices, float *weights,
                              int64_t *nnz_io, cudaStream_t s);
+// launch-shape defaults, range check and the autotuner cache (tuning.cu)
+void tuning_default(leiden_tuning &t);
+bool tuning_valid(const leiden_tuning &t);
+leiden_status tuning_lookup(const char *path, const char *gpu, int64_t n, int64_t nnz, int64_t maxdeg,
+                            leiden_tuning &out);
 leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                 const int32_t *memb, double gamma, cudaStream_t s, double *q_out);
 

@@ -60,12 +60,6 @@ extern std::atomic<int64_t> g_fail_alloc_after;
 // exact in fp64, and every key and a sweep's sum of gains fit in 128 bits
 constexpr double kDetMaxTwoM = 9007199254740992.0;  // 2^53
 
-// vertices per block of the persistent sweep kernel (below a full grid):
-// a step's latency grows with the vertices each thread takes in turn, so
-// small graphs get many blocks (4096 per block measured slower than 2048 on
-// the aggregated passes of the road workload)
-constexpr int64_t kCoopVerticesPerBlock = 2048;
-
 inline int ceil_log2_h(int64_t x) {
     int b = 0;
     while ((1LL << b) < x) ++b;
@@ -167,6 +161,18 @@ struct Serve {
 
 struct Handle::Impl {
     int64_t n0 = 0, m0 = 0;
+    leiden_tuning tune = [] {
+        leiden_tuning t;
+        tuning_default(t);
+        return t;
+    }();
+    BinBounds bins() const {
+        BinBounds b;
+        b.thread_max = tune.thread_max_deg;
+        b.warp_max = tune.warp_max_deg;
+        b.block_max = tune.block_max_deg;
+        return b;
+    }
     int64_t maxdeg0 = INT64_MAX;  // largest degree of the input graph
     Serve *srv = nullptr;
     cudaStream_t s = nullptr;

@@ -54,9 +54,9 @@ __global__ void k_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, i
         members[coff[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
     }
 }
-__global__ void k_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key) {
+__global__ void k_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, BinBounds bb, int32_t *key) {
     GRID_STRIDE(c, ncomm) {
-        const int b = degree_bin(tdeg[c]);
+        const int b = degree_bin(tdeg[c], bb);
         key[c] = b == 0 ? -1 : b;
     }
 }
@@ -195,9 +195,10 @@ cudaError_t launch_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, 
     k_comm_fill<<<grid_for(n, 256), 256, 0, s>>>(Cd, n, coff, cursor, members);
     return cudaGetLastError();
 }
-cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key, cudaStream_t s) {
+cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, const BinBounds &bb, int32_t *key,
+                                 cudaStream_t s) {
     if (ncomm <= 0) return cudaSuccess;
-    k_comm_bin_keys<<<grid_for(ncomm, 256), 256, 0, s>>>(tdeg, ncomm, key);
+    k_comm_bin_keys<<<grid_for(ncomm, 256), 256, 0, s>>>(tdeg, ncomm, bb, key);
     return cudaGetLastError();
 }
 cudaError_t launch_bound_labels(const int32_t *Cd, const int32_t *CB, int64_t n, int64_t ncomm, int32_t *bnd,

@@ -288,9 +288,9 @@ template <bool LONG> int sched_blocks_per_sm() {
 }
 
 __global__ void k_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
-                                int32_t *key) {
+                                BinBounds bb, int32_t *key) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int b = degree_bin(deg[v]);
+        const int b = degree_bin(deg[v], bb);
         // vertices without edges go to a trailing bucket (never swept)
         key[v] = b == 0 ? nsteps * kNumBins : (bin_major ? b * nsteps + step[v] : step[v] * kNumBins + b);
     }
@@ -388,9 +388,9 @@ cudaError_t launch_hub_prep(const int64_t *key_off, int32_t nsteps, const int32_
     return cudaGetLastError();
 }
 cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
-                                 int32_t *key, cudaStream_t s) {
+                                 const BinBounds &bb, int32_t *key, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_step_bin_keys<<<grid_for(n, 256), 256, 0, s>>>(step, deg, n, nsteps, bin_major, key);
+    k_step_bin_keys<<<grid_for(n, 256), 256, 0, s>>>(step, deg, n, nsteps, bin_major, bb, key);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,7 @@ template <class P, class W> struct SV {
     unsigned *bar;
     int *err;
     unsigned long long *prof;
+    int32_t block_max;              // rows longer than this are bin 6 (the hubs)
     int32_t stall_block;            // testing aid: this block never arrives at a barrier
     unsigned long long spin_limit;  // barrier polls before giving up
     // persistent sweep: act[k] == it + 1 marks step k as holding an eligible
@@ -161,6 +162,7 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.bar = c.bar;
     a.err = c.err;
     a.prof = c.prof;
+    a.block_max = c.block_max;
     a.stall_block = c.stall_block;
     a.spin_limit = c.spin_limit;
     a.act = c.act;
@@ -1130,7 +1132,7 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
             if (dv <= 32)
                 for (int32_t e = 0; e < dv; ++e) flag_unproc(a, sm, a.idx[e0 + e]);
         }
-        unsigned longs = __ballot_sync(kFull, c >= 0 && dv > 32 && !(grid_hub_flags && dv > kBlockMaxDeg));
+        unsigned longs = __ballot_sync(kFull, c >= 0 && dv > 32 && !(grid_hub_flags && dv > a.block_max));
         while (longs) {
             const int src = __ffs(longs) - 1;
             longs &= longs - 1;

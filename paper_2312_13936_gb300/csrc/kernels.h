@@ -8,14 +8,17 @@ namespace lgb {
 
 // Degree bins of the sweep and aggregation kernels: a vertex (or community)
 // of degree d goes to the first bin whose bound holds it. Bin 0 (no edges)
-// is never listed; bin 7 is unused.
+// is never listed; bin 7 is unused. The bounds of bins 1, 4 and 5 are the
+// handle's launch shape (leiden_tuning); the defaults and their largest
+// values are:
 //   bin 1  d <= 8      one thread per vertex (sweeps), a tile of 8 lanes (aggregation)
 //   bin 2  d <= 16     a tile of 16 lanes
 //   bin 3  d <= 32     a tile of 32 lanes
 //   bin 4  d <= 256    one warp, shared-memory table
 //   bin 5  d <= 2048   one block, shared-memory table
-//   bin 6  larger      one block, global-memory table (aggregation: one
-//                      packed table per community, filled by all vertices)
+//   bin 6  larger      the whole grid (persistent sweep) or one block with a
+//                      global-memory table; aggregation: one packed table
+//                      per community, filled by all vertices
 constexpr int kNumBins = 8;
 constexpr int kThreadMaxDeg = 8;
 constexpr int kWarpMaxDeg = 256;
@@ -30,8 +33,13 @@ constexpr int64_t kAggTableBytes = (int64_t)8 << 30;
 // modularity kernels (their long-row variants, chosen when a graph's degree
 // bound exceeds it)
 constexpr int32_t kLongRow = 64;
-__host__ __device__ inline int degree_bin(int64_t d) {
-    return d <= 0 ? 0 : d <= kThreadMaxDeg ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= kWarpMaxDeg ? 4 : d <= kBlockMaxDeg ? 5 : 6;
+// the bounds of bins 1, 4 and 5 (at most kThreadMaxDeg, kWarpMaxDeg and
+// kBlockMaxDeg, which the kernels' registers and shared-memory tables hold)
+struct BinBounds {
+    int32_t thread_max = kThreadMaxDeg, warp_max = kWarpMaxDeg, block_max = kBlockMaxDeg;
+};
+__host__ __device__ inline int degree_bin(int64_t d, const BinBounds &b) {
+    return d <= 0 ? 0 : d <= b.thread_max ? 1 : d <= 16 ? 2 : d <= 32 ? 3 : d <= b.warp_max ? 4 : d <= b.block_max ? 5 : 6;
 }
 
 // Weights of aggregated graphs in the deterministic mode: exact integers
@@ -107,6 +115,7 @@ struct SweepCtx {
     unsigned *bar = nullptr;      // grid barrier state (2 words, zero-initialised once)
     int *err = nullptr;
     unsigned long long *prof = nullptr;  // 8 work counters of this launch's class, or null
+    int32_t block_max = kBlockMaxDeg;    // rows longer than this are bin 6 (the hubs)
     // testing aid for the timeout path: block stall_block (-1: none) of a
     // persistent launch ends without arriving at the barrier; the others
     // poll at most spin_limit times
@@ -256,7 +265,7 @@ inline int32_t auto_layers(int64_t maxdeg, int64_t n, int64_t nnz) {
 cudaError_t launch_hub_prep(const int64_t *key_off, int32_t nsteps, const int32_t *list, const int32_t *deg,
                             int32_t *hubs, unsigned long long *max_span, cudaStream_t s);
 cudaError_t launch_step_bin_keys(const int32_t *step, const int32_t *deg, int64_t n, int32_t nsteps, bool bin_major,
-                                 int32_t *key, cudaStream_t s);
+                                 const BinBounds &bb, int32_t *key, cudaStream_t s);
 
 // ---- batches of graphs (k_batch.cu). vseg has G+1 vertex offsets (graph g
 // owns vertices [vseg[g], vseg[g+1])); gid maps a vertex to its graph.
@@ -367,7 +376,8 @@ cudaError_t launch_comm_counts(const int32_t *Cd, const int32_t *deg, int64_t n,
 cudaError_t launch_comm_fill(const int32_t *Cd, int64_t n, const int64_t *coff, int32_t *cursor, int32_t *members,
                              cudaStream_t s);
 // bins of communities by total degree
-cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, int32_t *key, cudaStream_t s);
+cudaError_t launch_comm_bin_keys(const int64_t *tdeg, int64_t ncomm, const BinBounds &bb, int32_t *key,
+                                 cudaStream_t s);
 // move-based labels: bnd[Cd[i]] = CB[i]; rep[b] = min s; label[s] = rep[bnd[s]] (Cd < 0: skipped)
 cudaError_t launch_bound_labels(const int32_t *Cd, const int32_t *CB, int64_t n, int64_t ncomm, int32_t *bnd,
                                 int32_t *rep, int32_t *label, cudaStream_t s);
