@@ -144,13 +144,13 @@ typedef struct leiden_server_s *leiden_server_t;
 /* State of a serving handle (filled by leiden_server_info). */
 typedef struct {
     int32_t waiting;          /* submitted graphs not yet in flight */
-    int32_t in_flight;        /* graphs in the union */
+    int32_t in_flight;        /* graphs in the lanes' unions */
     int32_t finished;         /* finished graphs whose results are unread */
     int32_t reserved;
-    int64_t union_vertices;   /* vertices of the union's current graph */
-    int64_t union_entries;    /* CSR entries of the union's current graph */
+    int64_t union_vertices;   /* vertices of the unions' current graphs */
+    int64_t union_entries;    /* CSR entries of the unions' current graphs */
     int64_t device_bytes;     /* device bytes held by the requests' own buffers */
-    int64_t steps;            /* steps run */
+    int64_t steps;            /* steps that ran a pass */
 } leiden_server_state;
 
 /* Fill *p with the defaults listed above. */
@@ -210,14 +210,24 @@ leiden_status leiden_batch_create(leiden_graph_t *out, int32_t num_graphs, const
 leiden_status leiden_batch_run(leiden_graph_t g, const leiden_params *p, int32_t *membership, int32_t where,
                                double *modularity, leiden_stats *stats);
 
-/* Serving with continuous batching. A server holds a union of graphs in
- * flight, each at its own pass of Algorithm 1. leiden_server_step admits
- * waiting graphs at the pass boundary (first come, first served, while a
- * slot, union capacity and the device budget allow), then runs one pass of
- * every graph in flight with one set of launches; graphs that stop leave
- * the union with their results. Every graph's result is the one leiden_run
+/* Serving with continuous batching. A server holds graphs in flight, each
+ * at its own pass of Algorithm 1, in two lanes: graphs whose schedule takes
+ * the light layer cap in lane 0, heavy-tailed graphs (largest degree times n
+ * above 64 nnz, the 1000-layer schedule of schedule_layers = 0) in lane 1;
+ * with a fixed schedule_layers every graph is in lane 0. Each lane is a
+ * union of its graphs. leiden_server_step runs one pass of one lane -- of
+ * the lanes with graphs in flight or waiting, the one whose steps have taken
+ * the least time so far (a lane that becomes busy starts level with the
+ * other), so that light graphs are not paced by a heavy graph's schedule and
+ * each lane holds at least half the GPU while both have work. The step
+ * admits that lane's waiting graphs at the pass boundary (first come, first
+ * served, while a slot, union capacity and the device budget allow), then
+ * runs one pass of every graph in it with one set of launches; graphs that
+ * stop leave with their results. Every graph's result is the one leiden_run
  * gives alone (bit for bit in deterministic mode). The caller drives the
  * loop: submit graphs as they arrive, call step, read finished results.
+ * Capacities and max_graphs hold per lane; lane 1 reserves its workspace
+ * when its first graph is submitted. The device budget is shared.
  *
  * Create a server for graphs of up to max_vertices vertices and max_entries
  * CSR entries in flight together (one graph may not exceed either), at most
@@ -240,12 +250,12 @@ leiden_status leiden_server_create(leiden_server_t *out, const leiden_params *p,
 leiden_status leiden_server_submit(leiden_server_t s, int64_t n, int64_t nnz, const int64_t *offsets,
                                    const int32_t *indices, const float *weights, int32_t where, int64_t *request_id);
 
-/* One step: admit, run one pass of every graph in flight, finish the graphs
- * that stop. *finished (nullable) receives the number of graphs finished by
+/* One step of one lane: admit, run one pass of every graph in flight in
+ * the lane, finish the graphs that stop. *finished (nullable) receives the number of graphs finished by
  * the step. Returns at once when nothing is in flight or waiting. */
 leiden_status leiden_server_step(leiden_server_t s, int32_t *finished);
 
-/* Id of the oldest finished graph whose result is unread, or -1. */
+/* Id of the earliest finished graph whose result is unread, or -1. */
 leiden_status leiden_server_next(leiden_server_t s, int64_t *request_id);
 
 /* Read and release the result of a finished graph: membership (n int32,

@@ -7,7 +7,7 @@ struct leiden_graph_s {
     lgb::Handle h;
 };
 struct leiden_server_s {
-    lgb::Handle h;
+    lgb::Server h;
 };
 
 extern "C" {
@@ -187,7 +187,7 @@ leiden_status leiden_server_create(leiden_server_t *out, const leiden_params *p,
         lgb::set_last_error("host allocation failed");
         return LEIDEN_ERR_OOM;
     }
-    leiden_status st = sv->h.server_init(*p, max_vertices, max_entries, max_graphs, device_budget, stream);
+    leiden_status st = sv->h.init(*p, max_vertices, max_entries, max_graphs, device_budget, stream);
     if (st != LEIDEN_OK) {
         delete sv;
         return st;
@@ -202,7 +202,7 @@ leiden_status leiden_server_submit(leiden_server_t s, int64_t n, int64_t nnz, co
         lgb::set_last_error("NULL server");
         return LEIDEN_ERR_INVALID;
     }
-    return s->h.server_submit(n, nnz, offsets, indices, weights, where, request_id);
+    return s->h.submit(n, nnz, offsets, indices, weights, where, request_id);
 }
 
 leiden_status leiden_server_step(leiden_server_t s, int32_t *finished) {
@@ -210,7 +210,7 @@ leiden_status leiden_server_step(leiden_server_t s, int32_t *finished) {
         lgb::set_last_error("NULL server");
         return LEIDEN_ERR_INVALID;
     }
-    return s->h.server_step(finished);
+    return s->h.step(finished);
 }
 
 leiden_status leiden_server_next(leiden_server_t s, int64_t *request_id) {
@@ -218,7 +218,7 @@ leiden_status leiden_server_next(leiden_server_t s, int64_t *request_id) {
         lgb::set_last_error("NULL server");
         return LEIDEN_ERR_INVALID;
     }
-    return s->h.server_next(request_id);
+    return s->h.next(request_id);
 }
 
 leiden_status leiden_server_result(leiden_server_t s, int64_t request_id, int32_t *membership, int32_t where,
@@ -231,7 +231,7 @@ leiden_status leiden_server_result(leiden_server_t s, int64_t request_id, int32_
         lgb::set_last_error("invalid where");
         return LEIDEN_ERR_INVALID;
     }
-    return s->h.server_result(request_id, membership, where, modularity, passes, communities);
+    return s->h.result(request_id, membership, where, modularity, passes, communities);
 }
 
 leiden_status leiden_server_info(leiden_server_t s, leiden_server_state *out) {
@@ -239,7 +239,7 @@ leiden_status leiden_server_info(leiden_server_t s, leiden_server_state *out) {
         lgb::set_last_error("NULL server");
         return LEIDEN_ERR_INVALID;
     }
-    return s->h.server_info(out);
+    return s->h.info(out);
 }
 
 leiden_status leiden_server_destroy(leiden_server_t s) {

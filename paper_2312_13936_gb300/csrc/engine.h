@@ -12,6 +12,8 @@ namespace lgb {
 void set_last_error(const std::string &s);
 const char *last_error();
 
+struct ServeShared;
+
 class Handle {
   public:
     Handle();
@@ -32,7 +34,7 @@ class Handle {
     // step admits waiting graphs at the pass boundary and runs one pass of
     // every graph in flight
     leiden_status server_init(const leiden_params &p, int64_t max_vertices, int64_t max_entries, int32_t max_graphs,
-                              int64_t device_budget, void *stream);
+                              int64_t device_budget, void *stream, ServeShared *shared = nullptr);
     leiden_status server_submit(int64_t n, int64_t nnz, const int64_t *off, const int32_t *idx, const float *w,
                                 int where, int64_t *id);
     leiden_status server_step(int32_t *finished);
@@ -40,6 +42,11 @@ class Handle {
     leiden_status server_result(int64_t id, int32_t *membership, int where, double *q, int32_t *passes,
                                 int64_t *communities);
     leiden_status server_info(leiden_server_state *out) const;
+    bool server_busy() const;  // graphs in flight or waiting
+    bool server_has(int64_t id) const;  // a request the lane still holds
+    // finishing order (ServeShared::fin_seq) of the oldest unread result and
+    // its id, or -1 when no result is unread
+    int64_t server_oldest(int64_t *id) const;
     leiden_status trace_get(int pass, int what, void *dst, int64_t *count) const;
     // launch shape of later runs (leiden_tuning)
     leiden_status set_tuning(const leiden_tuning &t);
@@ -50,6 +57,36 @@ class Handle {
 
   private:
     Impl *p;
+};
+
+// A serving handle of two lanes. Each lane is a union of its own
+// (Handle::server_*): graphs whose schedule takes the light layer cap go to
+// lane 0, heavy-tailed ones (reading S0) to lane 1, so that no graph's sweeps
+// are paced by another's thousand-layer schedule. A step runs one pass of
+// one lane: of the busy lanes, the one that has had the least device time
+// (a lane that becomes busy starts level with the other), so each lane holds
+// at least half the GPU while both have work. Ids, the finishing order and
+// the device budget are shared; results come out in finishing order.
+class Server {
+  public:
+    Server();
+    ~Server();
+    Server(const Server &) = delete;
+    Server &operator=(const Server &) = delete;
+    leiden_status init(const leiden_params &p, int64_t max_vertices, int64_t max_entries, int32_t max_graphs,
+                       int64_t device_budget, void *stream);
+    leiden_status submit(int64_t n, int64_t nnz, const int64_t *off, const int32_t *idx, const float *w, int where,
+                         int64_t *id);
+    leiden_status step(int32_t *finished);
+    leiden_status next(int64_t *id);
+    leiden_status result(int64_t id, int32_t *membership, int where, double *q, int32_t *passes,
+                         int64_t *communities);
+    leiden_status info(leiden_server_state *out) const;
+
+    struct State;
+
+  private:
+    State *st;
 };
 
 leiden_status disconnected_device(int64_t n, const int64_t *off, const int32_t *idx, const int32_t *memb,

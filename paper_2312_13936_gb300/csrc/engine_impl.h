@@ -130,6 +130,15 @@ struct Request {
     double q = 0;
     int32_t passes = 0;
     int64_t communities = 0;
+    int64_t fin_seq = 0;      // place in the server's finishing order
+};
+
+// Counters shared by the lanes of one server: request ids, the finishing
+// order, and the device bytes charged against the one budget.
+struct ServeShared {
+    int64_t next_id = 1;
+    int64_t fin_seq = 0;
+    int64_t budget = 0, used = 0;  // device bytes of the requests' own buffers
 };
 
 // Serving state (continuous batching): graphs wait, join the union at a pass
@@ -139,13 +148,14 @@ struct Serve {
     leiden_params prm{};
     int64_t cap_v = 0, cap_e = 0;  // union capacity: vertices (also the dendrogram arena), entries
     int32_t cap_g = 0;             // graphs in flight
-    int64_t budget = 0, used = 0;  // device bytes of the requests' own buffers
+    ServeShared own;               // counters when the union serves alone
+    ServeShared *sh = &own;        // else those of the server it is a lane of
     std::map<int64_t, Request> reqs;
     std::deque<int64_t> waiting;   // submitted, not yet in the union (first come, first served)
     int32_t on_host = 0;           // waiting graphs still held on the host
     std::vector<int64_t> inflight; // in union order
     std::deque<int64_t> finished;  // results not yet read
-    int64_t next_id = 1, steps = 0;
+    int64_t steps = 0;
     int64_t n_union = 0, e_union = 0, n_cont = 0, arena_n = 0;
     int cur = 0;                   // the union lives in agg[cur]
     int32_t *arena[2] = {nullptr, nullptr};

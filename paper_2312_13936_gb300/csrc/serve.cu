@@ -13,13 +13,14 @@
 // Eq. 1 on their own input. The dendrogram of every graph in flight lives in
 // one arena, compacted after each step in union order.
 #include <algorithm>
+#include <chrono>
 
 #include "engine_impl.h"
 
 namespace lgb {
 
 leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices, int64_t max_entries,
-                                  int32_t max_graphs, int64_t device_budget, void *stream) {
+                                  int32_t max_graphs, int64_t device_budget, void *stream, ServeShared *shared) {
     Impl &q = *p;
     if (max_vertices < 1 || max_vertices > 0x7fffffffLL || max_entries < 1 || max_graphs < 1 ||
         prm.max_iterations < 1 || prm.max_passes < 1 || !(prm.tolerance_drop > 0) || prm.schedule_layers < 0 ||
@@ -52,6 +53,7 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
     ST(q.alloc_workspace(max_vertices, max_graphs));
     q.srv = new Serve;
     Serve &v = *q.srv;
+    if (shared) v.sh = shared;
     v.prm = prm;
     v.prm.flags &= ~(uint32_t)(LEIDEN_FLAG_TRACE | LEIDEN_FLAG_PROFILE |
                                LEIDEN_FLAG_STEP_LAUNCHES);
@@ -69,12 +71,14 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
     ST(q.alloc(&v.gtau, max_graphs));
     ST(q.alloc(&v.gL, max_graphs));
     CK(cudaStreamSynchronize(q.s));
-    if (device_budget <= 0) {
-        size_t fr = 0, tot = 0;
-        CK(cudaMemGetInfo(&fr, &tot));
-        device_budget = (int64_t)(fr / 2);
+    if (v.sh->budget <= 0) {  // the first lane of a server sets the budget
+        if (device_budget <= 0) {
+            size_t fr = 0, tot = 0;
+            CK(cudaMemGetInfo(&fr, &tot));
+            device_budget = (int64_t)(fr / 2);
+        }
+        v.sh->budget = device_budget;
     }
-    v.budget = device_budget;
     return LEIDEN_OK;
 }
 
@@ -104,7 +108,7 @@ static leiden_status upload(Handle::Impl &q, Request &r, const int64_t *off, con
         return LEIDEN_OK;
     };
     r.bytes = request_bytes(r);  // charged first: free_request() gives back exactly this
-    q.srv->used += r.bytes;
+    q.srv->sh->used += r.bytes;
     ST(get((void **)&r.off, sizeof(int64_t) * (n + 1)));
     ST(get((void **)&r.idx, sizeof(int32_t) * m));
     ST(get((void **)&r.w, sizeof(float) * m));
@@ -150,7 +154,7 @@ static void release_input(Handle::Impl &q, Request &r) {
         *b = nullptr;
     }
     const int64_t keep = r.memb ? (int64_t)sizeof(int32_t) * r.n : 0;
-    q.srv->used -= r.bytes - keep;
+    q.srv->sh->used -= r.bytes - keep;
     r.bytes = keep;
     std::vector<int64_t>().swap(r.hoff);
     std::vector<int32_t>().swap(r.hidx);
@@ -161,7 +165,7 @@ static void free_request(Handle::Impl &q, Request &r) {
     release_input(q, r);
     if (r.memb) cudaFreeAsync(r.memb, q.s);
     r.memb = nullptr;
-    q.srv->used -= r.bytes;
+    q.srv->sh->used -= r.bytes;
     r.bytes = 0;
 }
 
@@ -181,9 +185,9 @@ leiden_status Handle::server_submit(int64_t n, int64_t nnz, const int64_t *off, 
         set_last_error("graph larger than the server's capacity");
         return LEIDEN_ERR_INVALID;
     }
-    if (graph_bytes(n, nnz) > v.budget) {  // could never be admitted, and would hold up every later graph
+    if (graph_bytes(n, nnz) > v.sh->budget) {  // could never be admitted, and would hold up every later graph
         set_last_error("graph needs " + std::to_string(graph_bytes(n, nnz)) + " device bytes, more than the " +
-                       "server's device budget of " + std::to_string(v.budget));
+                       "server's device budget of " + std::to_string(v.sh->budget));
         return LEIDEN_ERR_OOM;
     }
     if (where == LEIDEN_HOST && (off[0] != 0 || off[n] != nnz)) {
@@ -191,11 +195,12 @@ leiden_status Handle::server_submit(int64_t n, int64_t nnz, const int64_t *off, 
         return LEIDEN_ERR_INVALID;
     }
     Request r;
-    const int64_t rid = v.next_id++;
+    const int64_t rid = v.sh->next_id++;
     r.id = rid;
     r.n = n;
     r.m = nnz;
     if (n == 0) {  // nothing to cluster: finished at once
+        r.fin_seq = v.sh->fin_seq++;
         v.reqs[rid] = std::move(r);
         v.finished.push_back(rid);
         *id = rid;
@@ -204,7 +209,7 @@ leiden_status Handle::server_submit(int64_t n, int64_t nnz, const int64_t *off, 
     const cudaMemcpyKind kind = where == LEIDEN_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     // copied to the device at once unless the budget is spent or an earlier
     // graph still waits on the host (uploads keep the order of arrival)
-    if (v.used + request_bytes(r) <= v.budget && v.on_host == 0) {
+    if (v.sh->used + request_bytes(r) <= v.sh->budget && v.on_host == 0) {
         leiden_status st = upload(q, r, off, idx, w, kind);
         if (st != LEIDEN_OK) {
             free_request(q, r);
@@ -247,12 +252,13 @@ leiden_status Handle::server_step(int32_t *finished_out) {
     while (!v.waiting.empty()) {
         Request &r = v.reqs[v.waiting.front()];
         if (!r.on_device) {
-            if (v.used + request_bytes(r) > v.budget) break;
+            if (v.sh->used + request_bytes(r) > v.sh->budget) break;
             v.on_host--;
             leiden_status st = upload(q, r, r.hoff.data(), r.hidx.data(), r.hw.data(), cudaMemcpyHostToDevice);
             if (st != LEIDEN_OK) {  // the graph fails; its error is its result
                 r.status = st;
                 release_input(q, r);
+                r.fin_seq = v.sh->fin_seq++;
                 v.finished.push_back(r.id);
                 v.waiting.pop_front();
                 nfin++;
@@ -381,6 +387,7 @@ leiden_status Handle::server_step(int32_t *finished_out) {
         rq.passes = rq.pass + 1;
         rq.status = LEIDEN_OK;
         release_input(q, rq);
+        rq.fin_seq = v.sh->fin_seq++;
         v.finished.push_back(rq.id);
         nfin++;
     }
@@ -465,7 +472,201 @@ leiden_status Handle::server_info(leiden_server_state *out) const {
     out->reserved = 0;
     out->union_vertices = v.n_union;
     out->union_entries = v.e_union;
-    out->device_bytes = v.used;
+    out->device_bytes = v.sh->used;
+    out->steps = v.steps;
+    return LEIDEN_OK;
+}
+
+bool Handle::server_busy() const {
+    const Serve *v = p->srv;
+    return v && (!v->inflight.empty() || !v->waiting.empty());
+}
+
+bool Handle::server_has(int64_t id) const { return p->srv && p->srv->reqs.count(id) > 0; }
+
+int64_t Handle::server_oldest(int64_t *id) const {
+    const Serve *v = p->srv;
+    if (!v || v->finished.empty()) return -1;
+    *id = v->finished.front();
+    return v->reqs.at(*id).fin_seq;
+}
+
+// ---------------------------------------------------------------- two lanes
+
+namespace {
+
+// largest row length of a device CSR (offsets only)
+__global__ void k_max_row_len(const int64_t *__restrict__ off, int64_t n, unsigned long long *out) {
+    unsigned long long mx = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = off[i + 1] - off[i];
+        if (d > 0 && (unsigned long long)d > mx) mx = (unsigned long long)d;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(out, mx);
+}
+
+}  // namespace
+
+struct Server::State {
+    leiden_params prm{};
+    int64_t cap_v = 0, cap_e = 0, budget_arg = 0;
+    int32_t cap_g = 0;
+    cudaStream_t s = nullptr;
+    ServeShared sh;
+    Handle lane[2];
+    bool ready[2] = {false, false};
+    double vtime[2] = {0.0, 0.0};  // device time (ms) each lane's steps have taken
+    std::map<int64_t, int> lane_of;  // unread request ids -> lane
+    unsigned long long *dmax = nullptr;
+    int64_t steps = 0;
+};
+
+Server::Server() : st(new State) {}
+
+Server::~Server() {
+    if (st->dmax) cudaFreeAsync(st->dmax, st->s);
+    delete st;  // the lanes free their own state
+}
+
+leiden_status Server::init(const leiden_params &prm, int64_t max_vertices, int64_t max_entries, int32_t max_graphs,
+                           int64_t device_budget, void *stream) {
+    State &v = *st;
+    v.prm = prm;
+    v.cap_v = max_vertices;
+    v.cap_e = max_entries;
+    v.cap_g = max_graphs;
+    v.budget_arg = device_budget;
+    v.s = static_cast<cudaStream_t>(stream);
+    // lane 0 now (it checks the parameters and fixes the budget), lane 1 when
+    // its first graph comes
+    ST(v.lane[0].server_init(prm, max_vertices, max_entries, max_graphs, device_budget, stream, &v.sh));
+    v.ready[0] = true;
+    if (cudaMallocAsync((void **)&v.dmax, sizeof(unsigned long long), v.s) != cudaSuccess) {
+        set_last_error("device allocation for the server failed");
+        return LEIDEN_ERR_OOM;
+    }
+    return LEIDEN_OK;
+}
+
+leiden_status Server::submit(int64_t n, int64_t nnz, const int64_t *off, const int32_t *idx, const float *w,
+                             int where, int64_t *id) {
+    State &v = *st;
+    int k = 0;
+    // the lane of a graph: its schedule's layer cap (reading S0); with a fixed
+    // cap every graph shares lane 0. Malformed arguments are left to the
+    // lane's own checks.
+    if (v.prm.schedule_layers == 0 && n > 0 && nnz > 0 && off && (where == LEIDEN_HOST || where == LEIDEN_DEVICE) &&
+        n <= v.cap_v && nnz <= v.cap_e) {
+        int64_t maxdeg = 0;
+        if (where == LEIDEN_HOST) {
+            for (int64_t i = 0; i < n; ++i) maxdeg = std::max(maxdeg, off[i + 1] - off[i]);
+        } else {
+            unsigned long long h = 0;
+            CK(cudaMemsetAsync(v.dmax, 0, sizeof(unsigned long long), v.s));
+            const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+            k_max_row_len<<<(unsigned)blocks, 256, 0, v.s>>>(off, n, v.dmax);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&h, v.dmax, sizeof(h), cudaMemcpyDeviceToHost, v.s));
+            CK(cudaStreamSynchronize(v.s));
+            maxdeg = (int64_t)std::min<unsigned long long>(h, (unsigned long long)nnz);
+        }
+        k = auto_layers(maxdeg, n, nnz) == kLayersHeavy ? 1 : 0;
+    }
+    if (!v.ready[k]) {
+        ST(v.lane[k].server_init(v.prm, v.cap_v, v.cap_e, v.cap_g, v.budget_arg, v.s, &v.sh));
+        v.ready[k] = true;
+    }
+    const bool was_busy = v.lane[k].server_busy();
+    ST(v.lane[k].server_submit(n, nnz, off, idx, w, where, id));
+    v.lane_of[*id] = k;
+    const int o = k ^ 1;
+    if (!was_busy && v.ready[o] && v.lane[o].server_busy())  // starts level: no burst to catch up
+        v.vtime[k] = std::max(v.vtime[k], v.vtime[o]);
+    return LEIDEN_OK;
+}
+
+leiden_status Server::step(int32_t *finished) {
+    State &v = *st;
+    if (finished) *finished = 0;
+    const int first = v.vtime[0] <= v.vtime[1] ? 0 : 1;
+    // the busy lane with less device time first; if it runs no pass (its
+    // waiting graphs do not fit the budget the other lane holds), the other
+    int32_t total = 0;
+    for (int k : {first, first ^ 1}) {
+        if (!v.ready[k] || !v.lane[k].server_busy()) continue;
+        leiden_server_state a{}, b{};
+        ST(v.lane[k].server_info(&a));
+        int32_t f = 0;
+        const auto t0 = std::chrono::steady_clock::now();
+        ST(v.lane[k].server_step(&f));  // returns after the step's work is done
+        v.vtime[k] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        ST(v.lane[k].server_info(&b));
+        total += f;
+        if (b.steps > a.steps) {
+            v.steps++;
+            break;
+        }
+    }
+    if (finished) *finished = total;
+    return LEIDEN_OK;
+}
+
+leiden_status Server::next(int64_t *id) {
+    State &v = *st;
+    if (!id) {
+        set_last_error("request_id is NULL");
+        return LEIDEN_ERR_INVALID;
+    }
+    *id = -1;
+    int64_t best = -1;
+    for (int k = 0; k < 2; ++k) {
+        if (!v.ready[k]) continue;
+        int64_t rid = -1;
+        const int64_t seq = v.lane[k].server_oldest(&rid);
+        if (seq >= 0 && (best < 0 || seq < best)) {
+            best = seq;
+            *id = rid;
+        }
+    }
+    return LEIDEN_OK;
+}
+
+leiden_status Server::result(int64_t id, int32_t *membership, int where, double *q, int32_t *passes,
+                             int64_t *communities) {
+    State &v = *st;
+    auto it = v.lane_of.find(id);
+    if (it == v.lane_of.end()) {
+        set_last_error("unknown or unfinished request id");
+        return LEIDEN_ERR_INVALID;
+    }
+    const int k = it->second;
+    const leiden_status s = v.lane[k].server_result(id, membership, where, q, passes, communities);
+    if (!v.lane[k].server_has(id)) v.lane_of.erase(it);  // released by the read
+    return s;
+}
+
+leiden_status Server::info(leiden_server_state *out) const {
+    const State &v = *st;
+    if (!out) {
+        set_last_error("out is NULL");
+        return LEIDEN_ERR_INVALID;
+    }
+    leiden_server_state t{};
+    *out = leiden_server_state{};
+    for (int k = 0; k < 2; ++k) {
+        if (!v.ready[k]) continue;
+        ST(v.lane[k].server_info(&t));
+        out->waiting += t.waiting;
+        out->in_flight += t.in_flight;
+        out->finished += t.finished;
+        out->union_vertices += t.union_vertices;
+        out->union_entries += t.union_entries;
+        out->device_bytes = t.device_bytes;  // shared
+    }
     out->steps = v.steps;
     return LEIDEN_OK;
 }

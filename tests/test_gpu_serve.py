@@ -207,3 +207,23 @@ def test_serve_mixed_layer_caps_same_alone_and_in_mix():
         ms, qs, sts, _ = run_gpu(G, lg.LEIDEN_DETERMINISTIC)
         assert np.array_equal(memb, ms), g
         assert passes == sts.passes, g
+
+
+def test_serve_lanes_by_layer_cap():
+    """A heavy-tailed graph (layer cap 1000) and light ones go to separate
+    lanes, and a step runs one pass of one lane: the steps add up to the
+    graphs' passes (one union would advance all of them together), and each
+    result still equals its single run bit for bit."""
+    from tests.test_gpu_parity import hub_graph
+    heavy, light = hub_graph(), gen.road(40)
+    assert int(np.diff(heavy.offsets).max()) * heavy.n > 64 * heavy.nnz
+    assert int(np.diff(light.offsets).max()) * light.n <= 64 * light.nnz
+    out, info, steps = serve([heavy, light], lg.LEIDEN_DETERMINISTIC, arrivals_per_step=2)
+    alone = [run_gpu(G, lg.LEIDEN_DETERMINISTIC) for G in (heavy, light)]
+    assert steps == info["steps"] == alone[0][2].passes + alone[1][2].passes
+    for (memb, q, passes, comm), (ms, qs, sts, _) in zip(out, alone):
+        assert np.array_equal(memb, ms) and passes == sts.passes
+    # with a fixed layer cap every graph shares one lane
+    out, info, steps = serve([heavy, light], lg.LEIDEN_DETERMINISTIC, arrivals_per_step=2, schedule_layers=32)
+    p = [run_gpu(G, lg.LEIDEN_DETERMINISTIC, schedule_layers=32)[2].passes for G in (heavy, light)]
+    assert steps == max(p)
