@@ -164,7 +164,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
         CK(launch_graph_scales(det ? (void *)&q.dsc->two_m_i : (void *)&q.dsc->two_m_f, det, 1, q.gks, q.g2m, s));
         q.launches += 1;
     }
-    q.launches += 1;
+    q.launches += 2;  // the vertex weights' two kernels
     // schedule and (step, bin) lists
     // (the schedule's order arrays are the list and key buffers, rewritten below)
     SchedWork sw{q.scnt, q.slayer, q.list, q.key, q.sfcount, &q.dsc->err};
@@ -572,7 +572,7 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
                 ac.tab_k1 = k1;
                 ac.tab_base = base;
                 ac.prof = prof_begin(16 + kBinHub);
-                CK(launch_aggregate_tables(ac, list6, q.sm * 8, s));
+                CK(launch_aggregate_tables(ac, list6, q.sm, s));
                 prof_end();
                 q.launches += 2;
                 k0 = k1;
@@ -824,7 +824,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
     } else {
         CK(launch_modularity_parts(n0, q.off0, q.idx0, q.w0, outp, q.sigtot, q.dsc->msum, s, q.maxdeg0 > kLongRow));
         CK(launch_sum_squares(q.sigtot, n0, &q.dsc->msum[2], s));
-        q.launches += 2;
+        q.launches += q.maxdeg0 > kLongRow ? 3 : 2;
     }
     int64_t ncomm_out = 0;
     CK(cudaMemcpyAsync(&ncomm_out, q.pos + n0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));

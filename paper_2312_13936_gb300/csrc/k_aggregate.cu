@@ -226,7 +226,22 @@ __global__ void __launch_bounds__(256) k_agg_warp(AV<P, Wi, Wo> a, const int32_t
 
 // ------------------------------------------------------ block table bin
 constexpr int kAggThreads = 512;
+static_assert(4 * kAggThreads >= kBlockMaxDeg, "the block kernel's threads hold four members each");
+// shared memory of the block kernel: the table, then the members' entry
+// prefix (nm + 1 int32) and row starts (nm int64)
+template <class A> constexpr size_t block_smem_bytes() {
+    return (sizeof(A) + sizeof(int32_t)) * kBlockSlots + sizeof(int64_t) * kBlockMaxDeg +
+           sizeof(int32_t) * (kBlockMaxDeg + 2);
+}
 
+// One block per community. Its members' entries are taken as one flat
+// range: the members' row starts and the prefix sums of their degrees go to
+// shared memory, then the warps take 32 consecutive entries at a time
+// across member boundaries (each lane finds its member by binary search
+// over the prefix), so every lane has an entry and the loads of different
+// chunks overlap. Every member of a community with an edge has one, so a
+// community has at most as many members as entries (bin 5: at most
+// kBlockMaxDeg); a larger member count takes the members one per warp.
 template <class P, class Wi, class Wo>
 __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, const int32_t *__restrict__ list,
                                                           int64_t count) {
@@ -234,8 +249,11 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_written;
     __shared__ A s_k[kAggThreads / 32];
+    __shared__ int32_t s_part[kAggThreads / 32];
     A *vals = reinterpret_cast<A *>(smem_raw);
-    int32_t *keys = reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots);
+    int64_t *mrow = reinterpret_cast<int64_t *>(smem_raw + sizeof(A) * kBlockSlots);
+    int32_t *keys = reinterpret_cast<int32_t *>(smem_raw + sizeof(A) * kBlockSlots + sizeof(int64_t) * kBlockMaxDeg);
+    int32_t *pre = keys + kBlockSlots;
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5, nw = blockDim.x >> 5;
     ProfCounts pc;
     for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
@@ -253,15 +271,65 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_block(AV<P, Wi, Wo> a, cons
             vals[s] = 0;
         }
         if (tid == 0) s_written = 0;
-        __syncthreads();
-        // warps take members round-robin, lanes stride over a member's edges
-        for (int32_t k = wib; k < nm; k += nw) {
-            const int32_t u = a.members[m0 + k];
-            const int64_t e0 = a.off[u];
-            const int32_t du = a.deg[u];
-            for (int32_t e = lane; e < du; e += 32)
-                if (!hash_add(keys, vals, bits, a.Cd[a.idx[e0 + e]], wconv<A>(a.w[e0 + e])))
-                    set_error(a.err, kErrHashFull);
+        if (nm <= kBlockMaxDeg) {
+            // members' row starts and the exclusive prefix of their degrees:
+            // thread tid holds members [4 tid, 4 tid + 4)
+            int32_t d4[4], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t k = 4 * tid + q;
+                d4[q] = 0;
+                if (k < nm) {
+                    const int32_t u = a.members[m0 + k];
+                    mrow[k] = a.off[u];
+                    d4[q] = a.deg[u];
+                }
+                sum += d4[q];
+            }
+            int32_t inc = sum;  // inclusive scan of the threads' sums: warps, then the warp totals
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_part[wib] = inc;
+            __syncthreads();
+            int32_t before = 0;
+            for (int w2 = 0; w2 < wib; ++w2) before += s_part[w2];
+            int32_t run = before + inc - sum;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t k = 4 * tid + q;
+                if (k < nm) pre[k] = run;
+                run += d4[q];
+                if (k == nm - 1) pre[nm] = run;
+            }
+            if (nm == 0 && tid == 0) pre[0] = 0;
+            __syncthreads();
+            const int32_t T = pre[nm];
+            for (int32_t x0 = wib * 32; x0 < T; x0 += nw * 32) {
+                const int32_t x = x0 + lane;
+                if (x < T) {
+                    int32_t lo = 0, hi = nm - 1;  // the last member k with pre[k] <= x
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi + 1) >> 1;
+                        if (pre[mid] <= x) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int64_t e = mrow[lo] + (x - pre[lo]);
+                    if (!hash_add(keys, vals, bits, a.Cd[a.idx[e]], wconv<A>(a.w[e]))) set_error(a.err, kErrHashFull);
+                }
+            }
+        } else {
+            __syncthreads();
+            // warps take members round-robin, lanes stride over a member's edges
+            for (int32_t k = wib; k < nm; k += nw) {
+                const int32_t u = a.members[m0 + k];
+                const int64_t e0 = a.off[u];
+                const int32_t du = a.deg[u];
+                for (int32_t e = lane; e < du; e += 32)
+                    if (!hash_add(keys, vals, bits, a.Cd[a.idx[e0 + e]], wconv<A>(a.w[e0 + e])))
+                        set_error(a.err, kErrHashFull);
+            }
         }
         __syncthreads();
         const int64_t o0 = a.out_off[c];
@@ -340,14 +408,16 @@ __global__ void k_tab_members(const int32_t *list, int64_t K6, const int64_t *mo
 
 // Insertion of tables [tab_k0, tab_k1): their members' entries form the
 // flat range [eoff[moff[k0]], eoff[moff[k1]]) (eoff: the scan of the flat
-// members' degrees); a warp takes 32 consecutive entries, so rows of any
-// length spread over all warps. Lane 0 finds the member of the first entry
-// by binary search; 32 entries span at most 32 members (every member has an
-// edge), whose ends the lanes hold, and each lane finds its own by a search
-// over them. Entries of one step with the same (table, key) are summed first
-// and inserted once, which keeps hot keys (a large community's own entries)
-// from serialising on one address. Members come in community order, so the
-// warps in flight share a few tables.
+// members' degrees), cut into chunks of 32 consecutive entries, so rows of
+// any length spread over all warps; each warp takes a contiguous run of
+// chunks. Lane 0 finds the member of the warp's first entry by binary
+// search; 32 entries span at most 32 members (every member has an edge),
+// whose ends the lanes hold, and each lane finds its own by a search over
+// them; the next chunk starts at the member after the ones that ended. Entries
+// of one chunk with the same (table, key) are summed first and inserted
+// once, which keeps hot keys (a large community's own entries) from
+// serialising on one address. Members come in community order, so a warp's
+// run shares a few tables.
 template <class P, class Wi, class Wo>
 __global__ void __launch_bounds__(256) k_agg_tab_insert(AV<P, Wi, Wo> a, const int32_t *__restrict__ fm,
                                                         const int32_t *__restrict__ ft, const int64_t *__restrict__ eoff,
@@ -357,20 +427,23 @@ __global__ void __launch_bounds__(256) k_agg_tab_insert(AV<P, Wi, Wo> a, const i
     const int64_t mlo = moff[a.tab_k0], mhi = moff[a.tab_k1];
     const int64_t x_begin = eoff[mlo], x_end = eoff[mhi];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nch = (x_end - x_begin + 31) / 32;
+    const int64_t c0 = nch * wid / warps, c1 = nch * (wid + 1) / warps;
     ProfCounts pc;
-    for (int64_t x0 = x_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; x0 < x_end;
-         x0 += warps * 32) {
-        int64_t m0 = 0;
-        if (lane == 0) {
-            int64_t lo = mlo, hi = mhi - 1;  // the last member with eoff[m] <= x0
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if (eoff[mid] <= x0) lo = mid;
-                else hi = mid - 1;
-            }
-            m0 = lo;
+    int64_t m0 = 0;
+    if (c0 < c1 && lane == 0) {
+        const int64_t x0 = x_begin + c0 * 32;
+        int64_t lo = mlo, hi = mhi - 1;  // the last member with eoff[m] <= x0
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (eoff[mid] <= x0) lo = mid;
+            else hi = mid - 1;
         }
-        m0 = __shfl_sync(kFull, m0, 0);
+        m0 = lo;
+    }
+    m0 = __shfl_sync(kFull, m0, 0);
+    for (int64_t x0 = x_begin + c0 * 32; x0 < x_begin + c1 * 32; x0 += 32) {
         const int64_t mine = m0 + lane < mhi ? eoff[m0 + lane + 1] : INT64_MAX;  // end of member m0 + lane
         const int64_t x = x0 + lane;
         int own = 0;  // members before x's: lanes whose member ends at or before x
@@ -401,14 +474,16 @@ __global__ void __launch_bounds__(256) k_agg_tab_insert(AV<P, Wi, Wo> a, const i
         v = peer_sum(peers, v);
         if (valid && lane == __ffs(peers) - 1)
             if (!hash_add(a.hub_keys + tb, a.hub_vals + tb, tbits, key, v)) set_error(a.err, kErrHashFull);
+        m0 += __popc(__ballot_sync(kFull, mine <= x0 + 32));  // the member of the next chunk's first entry
     }
     pc.flush(a.prof);
 }
 
 // The distinct entries of tables [tab_k0, tab_k1) become their communities'
-// rows (order unspecified: each warp takes 32 slots of one table -- tables
-// are at least 64 slots and start at multiples of 64 -- and appends its
-// entries at the row's running fill), out_deg[c] their count and K''[c]
+// rows (order unspecified: the slots go in chunks of 32 -- tables are at
+// least 64 slots and start at multiples of 64, so a chunk lies in one table
+// -- each warp takes a contiguous run of chunks and appends each chunk's
+// entries at its row's running fill), out_deg[c] their count and K''[c]
 // their sum (both start at 0).
 template <class P, class Wi, class Wo>
 __global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const int32_t *__restrict__ list) {
@@ -416,20 +491,24 @@ __global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const in
     const int lane = threadIdx.x & 31;
     const int64_t s_begin = a.tab_off[a.tab_k0], s_end = a.tab_off[a.tab_k1];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nch = (s_end - s_begin) / 32;
+    const int64_t c0 = nch * wid / warps, c1 = nch * (wid + 1) / warps;
     ProfCounts pc;
-    for (int64_t s0 = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; s0 < s_end;
-         s0 += warps * 32) {
-        int64_t k = 0;
-        if (lane == 0) {
-            int64_t lo = a.tab_k0, hi = a.tab_k1 - 1;  // the table holding slot s0
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if (a.tab_off[mid] <= s0) lo = mid;
-                else hi = mid - 1;
-            }
-            k = lo;
+    int64_t k = 0;
+    if (c0 < c1 && lane == 0) {
+        const int64_t s0 = s_begin + c0 * 32;
+        int64_t lo = a.tab_k0, hi = a.tab_k1 - 1;  // the table holding slot s0
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (a.tab_off[mid] <= s0) lo = mid;
+            else hi = mid - 1;
         }
-        k = __shfl_sync(kFull, k, 0);
+        k = lo;
+    }
+    k = __shfl_sync(kFull, k, 0);
+    for (int64_t s0 = s_begin + c0 * 32; s0 < s_begin + c1 * 32; s0 += 32) {
+        while (a.tab_off[k + 1] <= s0) ++k;  // the same on every lane
         const int32_t c = list[k];
         const int64_t sl = s0 + lane - a.tab_base;
         const int32_t key = a.hub_keys[sl];
@@ -457,10 +536,17 @@ __global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const in
 }
 
 template <class P, class Wi, class Wo>
-cudaError_t tables_typed(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s) {
+cudaError_t tables_typed(const AggCtx &c, const int32_t *list, int sms, cudaStream_t s) {
     auto a = aview<P, Wi, Wo>(c);
-    k_agg_tab_insert<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, c.fm, c.ft, c.eoff, c.moff);
-    k_agg_tab_write<P, Wi, Wo><<<blocks, 256, 0, s>>>(a, list);
+    // one wave: as many blocks as are resident at once (the warps take
+    // equal runs of chunks, so a second wave would leave a tail)
+    static int bi = 0, bw = 0;
+    if (!bi && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bi, k_agg_tab_insert<P, Wi, Wo>, 256, 0) != cudaSuccess)
+        bi = 0;
+    if (!bw && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_agg_tab_write<P, Wi, Wo>, 256, 0) != cudaSuccess)
+        bw = 0;
+    k_agg_tab_insert<P, Wi, Wo><<<sms * (bi > 0 ? bi : 4), 256, 0, s>>>(a, c.fm, c.ft, c.eoff, c.moff);
+    k_agg_tab_write<P, Wi, Wo><<<sms * (bw > 0 ? bw : 4), 256, 0, s>>>(a, list);
     return cudaGetLastError();
 }
 
@@ -477,7 +563,7 @@ cudaError_t agg_typed(const AggCtx &c, int bin, const int32_t *list, int64_t cou
         case 3: k_agg_tile<P, Wi, Wo, 32><<<grid(8), 256, 0, s>>>(a, list, count); break;
         case 4: k_agg_warp<P, Wi, Wo><<<grid(8), 256, 0, s>>>(a, list, count); break;
         case 5: {
-            const size_t sm = (sizeof(typename P::acc) + sizeof(int32_t)) * kBlockSlots;
+            const size_t sm = block_smem_bytes<typename P::acc>();
             auto kern = k_agg_block<P, Wi, Wo>;
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
@@ -515,13 +601,13 @@ cudaError_t launch_table_members(const int32_t *list, int64_t K6, const int64_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s) {
+cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int sms, cudaStream_t s) {
     if (c.tab_k1 <= c.tab_k0) return cudaSuccess;
     if (c.det) {
-        if (c.g.w_int) return tables_typed<Det, WInt, WInt>(c, list, blocks, s);
-        return tables_typed<Det, float, WInt>(c, list, blocks, s);
+        if (c.g.w_int) return tables_typed<Det, WInt, WInt>(c, list, sms, s);
+        return tables_typed<Det, float, WInt>(c, list, sms, s);
     }
-    return tables_typed<Async, float, float>(c, list, blocks, s);
+    return tables_typed<Async, float, float>(c, list, sms, s);
 }
 
 cudaError_t launch_aggregate(const AggCtx &c, int bin, const int32_t *list, int64_t count, int max_blocks,

@@ -91,9 +91,11 @@ __global__ void k_canonical(const int32_t *C0, const int32_t *minv, const int64_
     GRID_STRIDE(v, n0) out[v] = (int32_t)rank[minv[C0[v]]];
 }
 
-// Eq. 1: intra-community weight, 2m and Sigma_c of each community (whole
-// warps step through the vertices so that Sigma_c is summed per label in
-// the warp before its atomic; LONG: long rows by the whole warp).
+// Eq. 1: intra-community weight, 2m and Sigma_c of each community, in two
+// kernels. Rows of up to kLongRow entries: each by its own lane, whole warps
+// stepping through the vertices so that Sigma_c is summed per label in the
+// warp before its atomic; every label is range-checked here. Longer rows
+// (LONG): by k_modularity_long below, so that no warp walks a hub alone.
 template <bool LONG>
 __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                    const int32_t *C, double *sigtot, double *sums) {
@@ -108,8 +110,11 @@ __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t 
                 atomicAdd(&sums[3], 1.0);
                 ci = -1;
             }
+            if (ci >= 0) {
+                const int64_t e0 = off[i], d = off[i + 1] - e0;
+                if (!LONG || d <= kLongRow) row_part(idx, w, C, e0, 0, d, 1, ci, k, in);
+            }
         }
-        warp_rows<LONG>(off, idx, w, C, ci >= 0, i, ci, k, in);
         warp_add_by_key(sigtot, k != 0.0 ? ci : -1, k);
         intra += in;
         tot += k;
@@ -117,6 +122,77 @@ __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t 
     intra = warp_sum(intra);
     tot = warp_sum(tot);
     if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sums[0], intra);
+        atomicAdd(&sums[1], tot);
+    }
+}
+
+// Rows longer than kLongRow, balanced by entries: warp k of W takes entries
+// [m k / W, m (k+1) / W) (W at most m / 4096), finds the row holding its
+// first entry by binary search over the offsets, then walks the rows that
+// overlap its range, 32 at a time, and sums the long ones' parts with all
+// lanes, four entries per lane in flight. A hub's row is thus shared by the
+// warps whose ranges it spans.
+constexpr int kModUnroll = 4;
+constexpr int64_t kModMinRange = 4096;
+__global__ void k_modularity_long(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                                  const int32_t *C, double *sigtot, double *sums) {
+    const int lane = threadIdx.x & 31;
+    const int64_t m = off[n];
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t Wg = ((int64_t)gridDim.x * blockDim.x) >> 5, Wm = (m + kModMinRange - 1) / kModMinRange;
+    const int64_t W = Wg < Wm ? Wg : Wm;
+    if (wid >= W) return;
+    const int64_t E0 = (int64_t)((__int128)m * wid / W), E1 = (int64_t)((__int128)m * (wid + 1) / W);
+    if (E0 >= E1) return;
+    // the last row r with off[r] <= E0 (off[0] = 0 <= E0; rows are [off[r], off[r+1]))
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (off[mid] <= E0) lo = mid;
+        else hi = mid;
+    }
+    double intra = 0, tot = 0;
+    for (int64_t r = lo; r < n; r += 32) {
+        const int64_t row = r + lane;
+        const bool valid = row < n;
+        const int64_t a = valid ? off[row] : m, b = valid ? off[row + 1] : m;
+        const bool mine = valid && b - a > kLongRow && a < E1 && b > E0;
+        int32_t ci = mine ? C[row] : -1;
+        if (ci >= n) ci = -1;  // out of range: counted by k_modularity_parts
+        unsigned todo = __ballot_sync(kFull, mine && ci >= 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t as = __shfl_sync(kFull, a, src), bs = __shfl_sync(kFull, b, src);
+            const int64_t s = as > E0 ? as : E0, t = bs < E1 ? bs : E1;
+            const int32_t c = __shfl_sync(kFull, ci, src);
+            double kl = 0, il = 0;
+            for (int64_t x0 = s + lane; x0 < t; x0 += 32 * kModUnroll) {
+                int32_t j[kModUnroll];
+                float wv[kModUnroll];
+#pragma unroll
+                for (int u = 0; u < kModUnroll; ++u) {
+                    const int64_t x = x0 + 32 * u;
+                    j[u] = x < t ? idx[x] : -1;
+                    wv[u] = x < t ? (w ? w[x] : 1.0f) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < kModUnroll; ++u)
+                    if (j[u] >= 0) {
+                        kl += (double)wv[u];
+                        if (C[j[u]] == c) il += (double)wv[u];
+                    }
+            }
+            kl = warp_sum(kl);
+            il = warp_sum(il);
+            if (lane == 0 && kl != 0.0) atomicAdd(&sigtot[c], kl);
+            intra += il;
+            tot += kl;
+        }
+        if (__ballot_sync(kFull, !valid || b >= E1)) break;  // the range ends in this batch of rows
+    }
+    if (lane == 0) {
         atomicAdd(&sums[0], intra);
         atomicAdd(&sums[1], tot);
     }
@@ -235,6 +311,8 @@ cudaError_t launch_modularity_parts(int64_t n, const int64_t *off, const int32_t
     if (n <= 0) return cudaSuccess;
     auto kern = long_rows ? k_modularity_parts<true> : k_modularity_parts<false>;
     kern<<<grid_for(n, 256), 256, 0, s>>>(n, off, idx, w, C, sigtot, sums);
+    if (!long_rows) return cudaGetLastError();
+    k_modularity_long<<<152 * 8, 256, 0, s>>>(n, off, idx, w, C, sigtot, sums);
     return cudaGetLastError();
 }
 cudaError_t launch_max_i64(const int64_t *a, int64_t n, unsigned long long *out, cudaStream_t s) {

@@ -31,38 +31,73 @@ __global__ void k_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err)
 }
 
 // K_i = sum of row i. One thread per row; rows longer than 64 entries are
-// summed by the whole warp, one such row after another.
+// left to k_vertex_weights_long (their K_i starts at 0 here).
 template <class A, class T, class W>
 __global__ void k_vertex_weights(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K, T *two_m) {
     const int lane = threadIdx.x & 31;
     T local = 0;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
-        const int32_t d = i < n ? deg[i] : 0;
-        if (i < n && d <= 64) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = deg[i];
+        A s = 0;
+        if (d <= 64) {
             const int64_t e0 = off[i];
-            A s = 0;
             for (int32_t e = 0; e < d; ++e) s += wconv<A>(w[e0 + e]);
-            K[i] = s;
             local += s;
         }
-        unsigned longs = __ballot_sync(kFull, i < n && d > 64);
-        while (longs) {
-            const int src = __ffs(longs) - 1;
-            longs &= longs - 1;
-            const int64_t r = __shfl_sync(kFull, i, src);
-            const int32_t dr = __shfl_sync(kFull, d, src);
-            const int64_t e0 = off[r];
-            A s = 0;
-            for (int32_t e = lane; e < dr; e += 32) s += wconv<A>(w[e0 + e]);
-            s = warp_sum(s);
-            if (lane == src) {
-                K[r] = s;
-                local += s;
-            }
-        }
+        K[i] = s;
     }
     local = warp_sum(local);
+    if (lane == 0 && local != (T)0) atomic_add_acc(two_m, local);
+}
+
+// K_i of the rows longer than 64 entries, balanced by entries (holey CSR:
+// row r holds entries [off[r], off[r] + deg[r]) of [off[r], off[r+1])):
+// warp k of W takes entries [M k / W, M (k+1) / W) of the M = off[n-1] +
+// deg[n-1] entries (W at most M / 4096), finds the row holding its first
+// entry by binary search over the offsets, walks the rows that overlap its
+// range 32 at a time and adds the long ones' parts, summed by all lanes, to
+// their K_i and to 2m; a hub's row is shared by the warps its entries span.
+template <class A, class T, class W>
+__global__ void k_vertex_weights_long(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K,
+                                      T *two_m) {
+    constexpr int64_t kMinRange = 4096;
+    const int lane = threadIdx.x & 31;
+    const int64_t M = off[n - 1] + deg[n - 1];
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t Wg = ((int64_t)gridDim.x * blockDim.x) >> 5, Wm = (M + kMinRange - 1) / kMinRange;
+    const int64_t Wn = Wg < Wm ? Wg : Wm;
+    if (wid >= Wn) return;
+    const int64_t E0 = (int64_t)((__int128)M * wid / Wn), E1 = (int64_t)((__int128)M * (wid + 1) / Wn);
+    if (E0 >= E1) return;
+    int64_t lo = 0, hi = n;  // the last row r < n with off[r] <= E0
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (off[mid] <= E0) lo = mid;
+        else hi = mid;
+    }
+    T local = 0;
+    for (int64_t r = lo; r < n; r += 32) {
+        const int64_t row = r + lane;
+        const bool valid = row < n;
+        const int64_t a = valid ? off[row] : M;
+        const int32_t d = valid ? deg[row] : 0;
+        const int64_t next = row + 1 < n ? off[row + 1] : M;
+        unsigned todo = __ballot_sync(kFull, valid && d > 64 && a < E1 && a + d > E0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t as = __shfl_sync(kFull, a, src), bs = as + __shfl_sync(kFull, d, src);
+            const int64_t s0 = as > E0 ? as : E0, t0 = bs < E1 ? bs : E1;
+            A sum = 0;
+            for (int64_t x = s0 + lane; x < t0; x += 32) sum += wconv<A>(w[x]);
+            sum = warp_sum(sum);
+            if (lane == 0 && sum != (A)0) {
+                atomic_add_acc(&K[r + src], sum);
+                local += (T)sum;
+            }
+        }
+        if (__ballot_sync(kFull, !valid || next >= E1)) break;  // the range ends in this batch of rows
+    }
     if (lane == 0 && local != (T)0) atomic_add_acc(two_m, local);
 }
 
@@ -306,15 +341,24 @@ cudaError_t launch_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err
 cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *two_m, cudaStream_t s) {
     if (g.n <= 0) return cudaSuccess;
     const int gb = grid_for(g.n, 256);
+    const int gl = 152 * 8;
     if (det) {
         auto *k = static_cast<long long *>(K);
         auto *t = static_cast<long long *>(two_m);
-        if (g.w_int)
+        if (g.w_int) {
             k_vertex_weights<long long, long long, WInt><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const WInt *)g.w, k, t);
-        else k_vertex_weights<long long, long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+            k_vertex_weights_long<long long, long long, WInt>
+                <<<gl, 256, 0, s>>>(g.n, g.off, g.deg, (const WInt *)g.w, k, t);
+        } else {
+            k_vertex_weights<long long, long long, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+            k_vertex_weights_long<long long, long long, float>
+                <<<gl, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+        }
     } else {
-        k_vertex_weights<float, double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w,
-                                                                 static_cast<float *>(K), static_cast<double *>(two_m));
+        auto *k = static_cast<float *>(K);
+        auto *t = static_cast<double *>(two_m);
+        k_vertex_weights<float, double, float><<<gb, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
+        k_vertex_weights_long<float, double, float><<<gl, 256, 0, s>>>(g.n, g.off, g.deg, (const float *)g.w, k, t);
     }
     return cudaGetLastError();
 }

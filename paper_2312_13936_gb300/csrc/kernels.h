@@ -29,9 +29,10 @@ constexpr int kBinHub = 6;
 // the packed bin-6 tables of the aggregation are cleared and filled in
 // chunks of at most this many bytes (12 per slot)
 constexpr int64_t kAggTableBytes = (int64_t)8 << 30;
-// rows longer than this are walked by a whole warp in the schedule and
-// modularity kernels (their long-row variants, chosen when a graph's degree
-// bound exceeds it)
+// rows longer than this are walked by a whole warp in the schedule kernel
+// (its long-row variant, chosen when a graph's degree bound exceeds it) and
+// shared by the warps their entries span in the vertex-weight and
+// modularity kernels
 constexpr int32_t kLongRow = 64;
 // the bounds of bins 1, 4 and 5 (at most kThreadMaxDeg, kWarpMaxDeg and
 // kBlockMaxDeg, which the kernels' registers and shared-memory tables hold)
@@ -200,7 +201,7 @@ cudaError_t launch_table_members(const int32_t *list, int64_t K6, const int64_t 
 // range of their members goes into their tables, 32 entries per warp, then
 // the whole grid writes the tables' distinct entries as the communities'
 // rows, 32 slots per warp
-cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int blocks, cudaStream_t s);
+cudaError_t launch_aggregate_tables(const AggCtx &c, const int32_t *list, int sms, cudaStream_t s);
 
 // Rows of a holey CSR (n rows, cap = offsets[n] slots, weights WInt)
 // sorted by target in place, each row's unused slots kept after its fill
