@@ -239,16 +239,30 @@ def kernel_source_hash():
 
 
 def traffic_for(cls_name, workload_name):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary,
-    if it was taken on the current kernel sources and this workload."""
+    """DRAM bytes per launch of a kernel class from the committed ncu
+    summary, if it was captured on the current kernel sources and this
+    workload; else None. Also returns the capture of a smaller case of the
+    same recipe (its DRAM and algorithmic bytes per launch), when the
+    workload itself is too large to capture, as a second value."""
     try:
         with open(TRAFFIC) as f:
             t = json.load(f)
-        if t.get("source_hash") != kernel_source_hash() or t.get("workload") != workload_name:
-            return None
-        return t["classes"].get(cls_name, {}).get("dram_bytes_per_launch")
+        if t.get("source_hash") != kernel_source_hash():
+            return None, None
+        exact, sample = None, None
+        for c in t.get("captures", []):
+            cl = c.get("classes", {}).get(cls_name)
+            if not cl:
+                continue
+            if c.get("workload") == workload_name:
+                exact = cl.get("dram_bytes_per_launch")
+            elif c.get("stands_for") == workload_name:
+                sample = {"workload": c["workload"], "dram_bytes_per_launch": cl.get("dram_bytes_per_launch"),
+                          "algorithmic_bytes_per_launch": cl.get("algorithmic_bytes_per_launch"),
+                          "ratio": cl.get("ratio")}
+        return exact, sample
     except Exception:
-        return None
+        return None, None
 
 
 def phase_roofline(prof, peak, step_ms):
@@ -633,10 +647,13 @@ def roofline_of(prof, peak, peak_kind, wname, step_ms):
     achieved = a["bytes"] / (a["ms"] / 1e3) / 1e9
     cls = f"{phase}/{binname}"
     total_ms = sum(v["ms"] for v in prof.values())
+    traffic, sample = traffic_for(cls, wname)
     r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-         "traffic": traffic_for(cls, wname), "kernel": cls, "peak_source": f"{peak_kind} hbm_gbs",
+         "traffic": traffic, "kernel": cls, "peak_source": f"{peak_kind} hbm_gbs",
          "bytes_per_launch": a["bytes"] / a["launches"], "ms_per_launch": a["ms"] / a["launches"],
          "share_of_profiled_ms": a["ms"] / total_ms}
+    if sample:
+        r["traffic_smaller_case"] = sample
     r["by_phase"], r["overall"] = phase_roofline(prof, peak, step_ms)
     return r
 

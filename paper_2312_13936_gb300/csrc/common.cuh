@@ -197,6 +197,33 @@ __device__ __forceinline__ bool hash_add(int32_t *keys, A *vals, int bits, int32
     return false;
 }
 
+// Open-addressing table whose slot is one 8-byte word: the key in the low
+// half (-1: empty), an fp32 value in the high half, so that an insertion
+// touches one memory sector (the asynchronous mode's global hub tables).
+constexpr unsigned long long kEmptyKV = 0x00000000ffffffffULL;  // key -1, value 0.0f
+__device__ __forceinline__ bool hash_add_kv(unsigned long long *kv, int bits, int32_t k, float v) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t s = hslot(k, bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        int32_t *key = reinterpret_cast<int32_t *>(&kv[s]);
+        float *val = reinterpret_cast<float *>(&kv[s]) + 1;
+        const int32_t cur = *((volatile int32_t *)key);
+        if (cur == k) {
+            atomicAdd(val, v);
+            return true;
+        }
+        if (cur == -1) {
+            const int32_t prev = atomicCAS(key, -1, k);
+            if (prev == -1 || prev == k) {
+                atomicAdd(val, v);
+                return true;
+            }
+        }
+        s = (s + 1u) & mask;
+    }
+    return false;
+}
+
 __device__ __forceinline__ int ceil_log2(int64_t x) {
     int b = 0;
     while ((1LL << b) < x) ++b;
@@ -291,13 +318,33 @@ __device__ __forceinline__ void set_error(int *err, int code) {
     if (err) atomicCAS(err, 0, code);
 }
 
-// Grid-wide barrier of a cooperative launch: blocks count in on bar[0]; the
-// last one resets it and advances the generation bar[1] that the others
-// poll. Spins are bounded: after spin_limit polls (2^24, about a second, by
-// default) without progress the kernel records kErrTimeout and every later
-// barrier returns at once, so the launch always ends. A grid of one block
-// needs only __syncthreads.
+// Grid-wide barrier of a cooperative launch. bar[0] counts the arrivals of
+// the launch and bar[1] the barriers completed; both are zero when the launch
+// begins (the launcher clears them). Thread 0 of each block arrives with a
+// release add on bar[0]: an arrival that returns old learns its barrier
+// r = old / G + 1 (no block arrives at barrier r + 1 before all G blocks
+// arrived at barrier r), and the G-th arrival publishes r in bar[1] with a
+// release store, which the others poll with acquire loads. Compared with
+// resetting a counter and advancing a generation (three dependent atomics
+// on the last arrival) this took a barrier of 608 blocks from 3.1 to 2.2
+// microseconds on this GPU. Spins are bounded: after spin_limit polls (2^24,
+// about a second, by default) without progress the kernel records
+// kErrTimeout and every later barrier returns at once, so the launch always
+// ends. A grid of one block needs only __syncthreads.
 constexpr unsigned long long kSpinLimit = 1ULL << 24;
+__device__ __forceinline__ unsigned bar_arrive(unsigned *p) {
+    unsigned r;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(r) : "l"(p) : "memory");
+    return r;
+}
+__device__ __forceinline__ unsigned bar_poll(const unsigned *p) {
+    unsigned r;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+    return r;
+}
+__device__ __forceinline__ void bar_publish(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, unsigned long long spin_limit = kSpinLimit) {
     __shared__ int s_ok;
     __syncthreads();
@@ -305,25 +352,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, unsigned l
     if (threadIdx.x == 0) {
         int ok = *((volatile int *)err) == 0;
         if (ok) {
-            volatile unsigned *gen = bar + 1;
-            const unsigned g = *gen;
-            __threadfence();
-            if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
-                atomicExch(&bar[0], 0u);
-                __threadfence();
-                atomicAdd(&bar[1], 1u);
+            const unsigned G = gridDim.x;
+            const unsigned old = bar_arrive(&bar[0]);
+            const unsigned r = old / G + 1;
+            if (old == r * G - 1) {
+                bar_publish(&bar[1], r);
             } else {
                 unsigned long long spins = 0;
-                while (*gen == g) {
+                while (bar_poll(&bar[1]) < r) {
                     if (++spins > spin_limit) {
                         set_error(err, kErrTimeout);
                         ok = 0;
                         break;
                     }
-                    __nanosleep(64);
+                    __nanosleep(32);
                 }
             }
-            __threadfence();
         }
         s_ok = ok;
     }

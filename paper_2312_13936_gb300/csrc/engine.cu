@@ -232,9 +232,17 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             return LEIDEN_ERR_OOM;
         }
         ST(q.ensure_hub(0, (int)span, det));
-        // clean tables; every step's last scan leaves them clean again
-        CK(cudaMemsetAsync(q.hub_keys, 0xff, sizeof(int32_t) * span, s));
-        CK(cudaMemsetAsync(q.hub_vals, 0, 8 * span, s));
+        // clean tables; every step's last scan leaves them clean again. The
+        // asynchronous mode keeps key and fp32 value in one 8-byte word per
+        // slot (key -1 and value 0 when empty), in the value buffer.
+        if (det) {
+            CK(cudaMemsetAsync(q.hub_keys, 0xff, sizeof(int32_t) * span, s));
+            CK(cudaMemsetAsync(q.hub_vals, 0, 8 * span, s));
+        } else {
+            CK(launch_fill_u64(static_cast<unsigned long long *>(q.hub_vals), 0x00000000ffffffffULL, (int64_t)span,
+                               s));
+            q.launches += 1;
+        }
     }
     // global tables for bin 6 (one per block)
     int hub_bits = 0, hub_regions = 0;

@@ -841,6 +841,13 @@ __device__ __forceinline__ void hub_flags(const SV<P, W> &a, const Sums<P> &sm, 
     }
 }
 
+// the asynchronous mode's whole-grid hub tables: one 8-byte word per slot
+// (key and fp32 value, hash_add_kv) in the value buffer, which holds 8 bytes
+// per slot
+template <class P, class W> __device__ __forceinline__ unsigned long long *hub_kv(const SV<P, W> &a) {
+    return reinterpret_cast<unsigned long long *>(a.hub_vals);
+}
+
 template <class P, class W, bool REFINE, bool B>
 __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int64_t nh, int32_t cur_step,
                                               Sums<P> &sm, ProfCounts &pc) {
@@ -944,8 +951,12 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
             const unsigned long long pair = key >= 0 ? ((unsigned long long)pl << 32) | (uint32_t)key : ~0ULL;
             const unsigned peers = __match_any_sync(kFull, pair);
             val = peer_sum(peers, val);
-            if (key >= 0 && lane == __ffs(peers) - 1)
-                if (!hash_add(a.hub_keys + tbase, a.hub_vals + tbase, bits, key, val)) set_error(a.err, kErrHashFull);
+            if (key >= 0 && lane == __ffs(peers) - 1) {
+                bool ok;
+                if constexpr (P::det) ok = hash_add(a.hub_keys + tbase, a.hub_vals + tbase, bits, key, val);
+                else ok = hash_add_kv(hub_kv<P>(a) + tbase, bits, key, val);
+                if (!ok) set_error(a.err, kErrHashFull);
+            }
         }
     }
     if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
@@ -991,19 +1002,30 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
             int32_t kq[Q];
             A vq[Q];
             T sq[Q];
+            if constexpr (P::det) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const int64_t sl = s0 + 32 * q + lane;
-                kq[q] = sl < s1 ? __ldcg(&a.hub_keys[sl]) : -1;
+                for (int q = 0; q < Q; ++q) {
+                    const int64_t sl = s0 + 32 * q + lane;
+                    kq[q] = sl < s1 ? __ldcg(&a.hub_keys[sl]) : -1;
+                }
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    vq[q] = 0;
+                    if (kq[q] >= 0) vq[q] = __ldcg(&a.hub_vals[s0 + 32 * q + lane]);
+                }
+            } else {  // key and value in one word
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int64_t sl = s0 + 32 * q + lane;
+                    const unsigned long long kv = sl < s1 ? __ldcg(&hub_kv<P>(a)[sl]) : kEmptyKV;
+                    kq[q] = (int32_t)(uint32_t)kv;
+                    vq[q] = (A)__uint_as_float((uint32_t)(kv >> 32));
+                }
             }
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                vq[q] = 0;
                 sq[q] = 0;
-                if (kq[q] >= 0) {
-                    vq[q] = __ldcg(&a.hub_vals[s0 + 32 * q + lane]);
-                    if (kq[q] != d) sq[q] = ldm(&a.Sig[kq[q]]);
-                }
+                if (kq[q] >= 0 && kq[q] != d) sq[q] = ldm(&a.Sig[kq[q]]);
             }
             unsigned long long lmax = 0ULL;
             int32_t lmin = INT_MAX;
@@ -1013,8 +1035,12 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
                 const int32_t k = kq[q];
                 if (k < 0) continue;
                 if (pass == npass - 1) {
-                    a.hub_keys[s0 + 32 * q + lane] = -1;
-                    a.hub_vals[s0 + 32 * q + lane] = 0;
+                    if constexpr (P::det) {
+                        a.hub_keys[s0 + 32 * q + lane] = -1;
+                        a.hub_vals[s0 + 32 * q + lane] = 0;
+                    } else {
+                        hub_kv<P>(a)[s0 + 32 * q + lane] = kEmptyKV;
+                    }
                 }
                 if (k == d) {
                     if (pass == 0) a.hkvd[j] = vq[q];
@@ -1206,6 +1232,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
     // testing aid: this block ends without arriving at any barrier, so the
     // others' bounded wait runs out (kErrTimeout) and the launch ends
     if ((int32_t)blockIdx.x == a.stall_block) return;
+    __shared__ int64_t s_ko[2][kNumBins + 2];
     ProfCounts pc;
     int32_t it = 0;
     bool ok = true;
@@ -1231,19 +1258,28 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_sweep_coop(SV<P, W> a, cons
         }
         int64_t hub_j0 = 0;  // ordinal of the step's first hub
         for (int32_t k = 0; k < a.nsteps && ok; ++k) {
+            // the step's nine (step, bin) offsets and its eligibility mark in
+            // one round trip, to shared memory: lanes of warp 0 load one
+            // each (the bins' work below stores to global memory, so loads
+            // issued between them would wait for one another). Two buffers:
+            // a warp reads step k's values before the barrier of step k + 1.
             const int64_t *ko = a.key_off + (int64_t)k * kNumBins;
-            const int64_t b0 = __ldcg(&ko[0]), b8 = __ldcg(&ko[8]);
+            int64_t *sko = s_ko[k & 1];
+            if (wib == 0 && lane <= kNumBins + 1)
+                sko[lane] = lane <= kNumBins ? __ldcg(&ko[lane]) : (a.act ? (int64_t)__ldcg(&a.act[k]) : 0);
+            __syncthreads();
+            const int64_t b0 = sko[0], b8 = sko[8];
             if (b0 == b8) continue;  // empty step: every block sees the same counts
-            if (a.act && __ldcg(&a.act[k]) != sm.stamp) {  // nothing eligible: the same in every block
-                hub_j0 += __ldcg(&ko[7]) - __ldcg(&ko[6]);
+            if (a.act && (int32_t)sko[kNumBins + 1] != sm.stamp) {  // nothing eligible: the same in every block
+                hub_j0 += sko[7] - sko[6];
                 continue;
             }
-            run_thread<P, W, REFINE, B>(a, list, __ldcg(&ko[1]), __ldcg(&ko[2]), k, sm, pc);
-            run_tile<P, W, 16, REFINE, B>(a, list, __ldcg(&ko[2]), __ldcg(&ko[3]), k, sm, pc);
-            run_tile<P, W, 32, REFINE, B>(a, list, __ldcg(&ko[3]), __ldcg(&ko[4]), k, sm, pc);
-            run_warp<P, W, REFINE, B>(a, list, __ldcg(&ko[4]), __ldcg(&ko[5]), k, skeys + wib * kWarpSlots,
-                                   svals + wib * kWarpSlots, sm, pc);
-            const int64_t b5 = __ldcg(&ko[5]), b6 = __ldcg(&ko[6]), b7 = __ldcg(&ko[7]);
+            run_thread<P, W, REFINE, B>(a, list, sko[1], sko[2], k, sm, pc);
+            run_tile<P, W, 16, REFINE, B>(a, list, sko[2], sko[3], k, sm, pc);
+            run_tile<P, W, 32, REFINE, B>(a, list, sko[3], sko[4], k, sm, pc);
+            run_warp<P, W, REFINE, B>(a, list, sko[4], sko[5], k, skeys + wib * kWarpSlots, svals + wib * kWarpSlots,
+                                   sm, pc);
+            const int64_t b5 = sko[5], b6 = sko[6], b7 = sko[7];
             if (b6 > b5) {
                 __syncthreads();  // the warp tables become one block table
                 run_block<P, W, REFINE, false, B>(a, list, b5, b6, k, skeys, svals, ceil_log2(kBlockSlots), sm, pc);

@@ -22,6 +22,10 @@ __global__ void k_fill_i32(int32_t *a, int32_t v, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         a[i] = v;
 }
+__global__ void k_fill_u64(unsigned long long *a, unsigned long long v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
 __global__ void k_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = off[i + 1] - off[i];
@@ -326,6 +330,11 @@ __global__ void k_validate_finish(const unsigned long long *sums, int *err) {
 cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_iota<<<grid_for(n, 256), 256, 0, s>>>(a, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_fill_u64(unsigned long long *a, unsigned long long v, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_fill_u64<<<grid_for(n, 256), 256, 0, s>>>(a, v, n);
     return cudaGetLastError();
 }
 cudaError_t launch_fill_i32(int32_t *a, int32_t v, int64_t n, cudaStream_t s) {

@@ -113,7 +113,7 @@ struct SweepCtx {
     int32_t *hd = nullptr, *hcand = nullptr, *hmv = nullptr;
     unsigned long long *hkey = nullptr;
     void *hkvd = nullptr;
-    unsigned *bar = nullptr;      // grid barrier state (2 words, zero-initialised once)
+    unsigned *bar = nullptr;      // grid barrier state (2 words, zeroed before every launch)
     int *err = nullptr;
     unsigned long long *prof = nullptr;  // 8 work counters of this launch's class, or null
     int32_t block_max = kBlockMaxDeg;    // rows longer than this are bin 6 (the hubs)
@@ -215,6 +215,7 @@ cudaError_t launch_sort_rows(int64_t n, const int64_t *off, const int32_t *deg, 
 // ---- utilities (k_util.cu)
 cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t *a, int32_t v, int64_t n, cudaStream_t s);
+cudaError_t launch_fill_u64(unsigned long long *a, unsigned long long v, int64_t n, cudaStream_t s);
 cudaError_t launch_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err, cudaStream_t s);
 // K[i] = sum of row i (acc type), *two_m += sum of K (acc type)
 cudaError_t launch_vertex_weights(const GraphView &g, bool det, void *K, void *two_m, cudaStream_t s);
