@@ -127,29 +127,30 @@ __global__ void k_modularity_parts(int64_t n, const int64_t *off, const int32_t 
     }
 }
 
-// Rows longer than kLongRow, balanced by entries: warp k of W takes entries
-// [m k / W, m (k+1) / W) (W at most m / 4096), finds the row holding its
-// first entry by binary search over the offsets, then walks the rows that
-// overlap its range, 32 at a time, and sums the long ones' parts with all
-// lanes, four entries per lane in flight. A hub's row is thus shared by the
-// warps whose ranges it spans.
+// Rows longer than kLongRow, balanced over rows and entries together: row r
+// and its entry e take positions r + off[r] and r + 1 + e of one merged
+// sequence of n + m items; warp k of W takes positions [T k / W,
+// T (k+1) / W) (W at most T / 4096), finds the row at its first position by
+// binary search over r + off[r], walks its rows 32 at a time and sums the
+// long rows' entries in its range with all lanes, four entries per lane in
+// flight. A hub's row is thus shared by the warps its entries span, and no
+// warp walks more than its share of rows.
 constexpr int kModUnroll = 4;
 constexpr int64_t kModMinRange = 4096;
 __global__ void k_modularity_long(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                   const int32_t *C, double *sigtot, double *sums) {
     const int lane = threadIdx.x & 31;
-    const int64_t m = off[n];
+    const int64_t m = off[n], Tn = n + m;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t Wg = ((int64_t)gridDim.x * blockDim.x) >> 5, Wm = (m + kModMinRange - 1) / kModMinRange;
+    const int64_t Wg = ((int64_t)gridDim.x * blockDim.x) >> 5, Wm = (Tn + kModMinRange - 1) / kModMinRange;
     const int64_t W = Wg < Wm ? Wg : Wm;
     if (wid >= W) return;
-    const int64_t E0 = (int64_t)((__int128)m * wid / W), E1 = (int64_t)((__int128)m * (wid + 1) / W);
-    if (E0 >= E1) return;
-    // the last row r with off[r] <= E0 (off[0] = 0 <= E0; rows are [off[r], off[r+1]))
-    int64_t lo = 0, hi = n;
+    const int64_t P0 = (int64_t)((__int128)Tn * wid / W), P1 = (int64_t)((__int128)Tn * (wid + 1) / W);
+    if (P0 >= P1) return;
+    int64_t lo = 0, hi = n;  // the last row r with r + off[r] <= P0
     while (hi - lo > 1) {
         const int64_t mid = lo + (hi - lo) / 2;
-        if (off[mid] <= E0) lo = mid;
+        if (mid + off[mid] <= P0) lo = mid;
         else hi = mid;
     }
     double intra = 0, tot = 0;
@@ -157,15 +158,16 @@ __global__ void k_modularity_long(int64_t n, const int64_t *off, const int32_t *
         const int64_t row = r + lane;
         const bool valid = row < n;
         const int64_t a = valid ? off[row] : m, b = valid ? off[row + 1] : m;
-        const bool mine = valid && b - a > kLongRow && a < E1 && b > E0;
+        const int64_t s0 = a > P0 - row - 1 ? a : P0 - row - 1;  // its entries in the range
+        const int64_t t0 = b < P1 - row - 1 ? b : P1 - row - 1;
+        const bool mine = valid && b - a > kLongRow && s0 < t0;
         int32_t ci = mine ? C[row] : -1;
         if (ci >= n) ci = -1;  // out of range: counted by k_modularity_parts
         unsigned todo = __ballot_sync(kFull, mine && ci >= 0);
         while (todo) {
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
-            const int64_t as = __shfl_sync(kFull, a, src), bs = __shfl_sync(kFull, b, src);
-            const int64_t s = as > E0 ? as : E0, t = bs < E1 ? bs : E1;
+            const int64_t s = __shfl_sync(kFull, s0, src), t = __shfl_sync(kFull, t0, src);
             const int32_t c = __shfl_sync(kFull, ci, src);
             double kl = 0, il = 0;
             for (int64_t x0 = s + lane; x0 < t; x0 += 32 * kModUnroll) {
@@ -190,7 +192,8 @@ __global__ void k_modularity_long(int64_t n, const int64_t *off, const int32_t *
             intra += il;
             tot += kl;
         }
-        if (__ballot_sync(kFull, !valid || b >= E1)) break;  // the range ends in this batch of rows
+        const int64_t next = row + 1 < n ? row + 1 + off[row + 1] : Tn;  // the next row's position
+        if (__ballot_sync(kFull, !valid || next >= P1)) break;  // the range ends in this batch of rows
     }
     if (lane == 0) {
         atomicAdd(&sums[0], intra);

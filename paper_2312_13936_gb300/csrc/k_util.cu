@@ -54,29 +54,34 @@ __global__ void k_vertex_weights(int64_t n, const int64_t *off, const int32_t *d
     if (lane == 0 && local != (T)0) atomic_add_acc(two_m, local);
 }
 
-// K_i of the rows longer than 64 entries, balanced by entries (holey CSR:
-// row r holds entries [off[r], off[r] + deg[r]) of [off[r], off[r+1])):
-// warp k of W takes entries [M k / W, M (k+1) / W) of the M = off[n-1] +
-// deg[n-1] entries (W at most M / 4096), finds the row holding its first
-// entry by binary search over the offsets, walks the rows that overlap its
-// range 32 at a time and adds the long ones' parts, summed by all lanes, to
-// their K_i and to 2m; a hub's row is shared by the warps its entries span.
+// K_i of the rows longer than 64 entries, balanced over rows and entries
+// together (holey CSR: row r holds entries [off[r], off[r] + deg[r]) of
+// [off[r], off[r+1])). Row r and entry e of it take positions r + off[r]
+// and r + 1 + e of one merged sequence of T = n + M items (M = off[n-1] +
+// deg[n-1]); warp k of W takes positions [T k / W, T (k+1) / W) (W at most
+// T / 4096), finds the row at its first position by binary search over
+// r + off[r], walks its rows 32 at a time and sums the long ones' entries
+// that fall in its range with all lanes, adding them to K_i and 2m. A hub's
+// row is thus shared by the warps its entries span, and no warp walks more
+// than its share of rows (a graph of millions of empty rows and few entries,
+// as late aggregated graphs are, would leave a range of entries a walk over
+// millions of rows).
 template <class A, class T, class W>
 __global__ void k_vertex_weights_long(int64_t n, const int64_t *off, const int32_t *deg, const W *w, A *K,
                                       T *two_m) {
     constexpr int64_t kMinRange = 4096;
     const int lane = threadIdx.x & 31;
-    const int64_t M = off[n - 1] + deg[n - 1];
+    const int64_t M = off[n - 1] + deg[n - 1], Tn = n + M;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t Wg = ((int64_t)gridDim.x * blockDim.x) >> 5, Wm = (M + kMinRange - 1) / kMinRange;
+    const int64_t Wg = ((int64_t)gridDim.x * blockDim.x) >> 5, Wm = (Tn + kMinRange - 1) / kMinRange;
     const int64_t Wn = Wg < Wm ? Wg : Wm;
     if (wid >= Wn) return;
-    const int64_t E0 = (int64_t)((__int128)M * wid / Wn), E1 = (int64_t)((__int128)M * (wid + 1) / Wn);
-    if (E0 >= E1) return;
-    int64_t lo = 0, hi = n;  // the last row r < n with off[r] <= E0
+    const int64_t P0 = (int64_t)((__int128)Tn * wid / Wn), P1 = (int64_t)((__int128)Tn * (wid + 1) / Wn);
+    if (P0 >= P1) return;
+    int64_t lo = 0, hi = n;  // the last row r with r + off[r] <= P0
     while (hi - lo > 1) {
         const int64_t mid = lo + (hi - lo) / 2;
-        if (off[mid] <= E0) lo = mid;
+        if (mid + off[mid] <= P0) lo = mid;
         else hi = mid;
     }
     T local = 0;
@@ -85,22 +90,23 @@ __global__ void k_vertex_weights_long(int64_t n, const int64_t *off, const int32
         const bool valid = row < n;
         const int64_t a = valid ? off[row] : M;
         const int32_t d = valid ? deg[row] : 0;
-        const int64_t next = row + 1 < n ? off[row + 1] : M;
-        unsigned todo = __ballot_sync(kFull, valid && d > 64 && a < E1 && a + d > E0);
+        const int64_t s0 = a > P0 - row - 1 ? a : P0 - row - 1;  // its entries in the range
+        const int64_t t0 = a + d < P1 - row - 1 ? a + d : P1 - row - 1;
+        const int64_t next = row + 1 < n ? row + 1 + off[row + 1] : Tn;  // the next row's position
+        unsigned todo = __ballot_sync(kFull, valid && d > 64 && s0 < t0);
         while (todo) {
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
-            const int64_t as = __shfl_sync(kFull, a, src), bs = as + __shfl_sync(kFull, d, src);
-            const int64_t s0 = as > E0 ? as : E0, t0 = bs < E1 ? bs : E1;
+            const int64_t x0 = __shfl_sync(kFull, s0, src), x1 = __shfl_sync(kFull, t0, src);
             A sum = 0;
-            for (int64_t x = s0 + lane; x < t0; x += 32) sum += wconv<A>(w[x]);
+            for (int64_t x = x0 + lane; x < x1; x += 32) sum += wconv<A>(w[x]);
             sum = warp_sum(sum);
             if (lane == 0 && sum != (A)0) {
                 atomic_add_acc(&K[r + src], sum);
                 local += (T)sum;
             }
         }
-        if (__ballot_sync(kFull, !valid || next >= E1)) break;  // the range ends in this batch of rows
+        if (__ballot_sync(kFull, !valid || next >= P1)) break;  // the range ends in this batch of rows
     }
     if (lane == 0 && local != (T)0) atomic_add_acc(two_m, local);
 }
