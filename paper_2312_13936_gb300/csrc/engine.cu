@@ -550,7 +550,9 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             ac.ft = ft;
             ac.moff = q.tmoff;
             ac.eoff = q.teoff;
-            const int64_t budget = kAggTableBytes / 12;  // slots: 4-byte key + 8-byte value
+            // slots: a 4-byte key and an 8-byte value (deterministic), or key
+            // and fp32 value in one 8-byte word (asynchronous)
+            const int64_t budget = kAggTableBytes / (det ? 12 : 8);
             std::vector<int64_t> hoff;
             if (total > budget) {
                 hoff.resize((size_t)K6 + 1);
@@ -572,8 +574,14 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
                     return LEIDEN_ERR_OOM;
                 }
                 ST(q.ensure_hub(0, (int)slots, det));
-                CK(cudaMemsetAsync(q.hub_keys, 0xff, sizeof(int32_t) * slots, s));
-                CK(cudaMemsetAsync(q.hub_vals, 0, 8 * slots, s));
+                if (det) {
+                    CK(cudaMemsetAsync(q.hub_keys, 0xff, sizeof(int32_t) * slots, s));
+                    CK(cudaMemsetAsync(q.hub_vals, 0, 8 * slots, s));
+                } else {
+                    CK(launch_fill_u64(static_cast<unsigned long long *>(q.hub_vals), 0x00000000ffffffffULL, slots,
+                                       s));
+                    q.launches += 1;
+                }
                 ac.hub_keys = q.hub_keys;
                 ac.hub_vals = q.hub_vals;
                 ac.tab_k0 = k0;

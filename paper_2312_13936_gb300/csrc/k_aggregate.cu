@@ -472,8 +472,12 @@ __global__ void __launch_bounds__(256) k_agg_tab_insert(AV<P, Wi, Wo> a, const i
         const unsigned long long pair = valid ? ((unsigned long long)(uint32_t)tk << 32) | (uint32_t)key : ~0ull;
         const unsigned peers = __match_any_sync(kFull, pair);
         v = peer_sum(peers, v);
-        if (valid && lane == __ffs(peers) - 1)
-            if (!hash_add(a.hub_keys + tb, a.hub_vals + tb, tbits, key, v)) set_error(a.err, kErrHashFull);
+        if (valid && lane == __ffs(peers) - 1) {
+            bool ok;
+            if constexpr (P::det) ok = hash_add(a.hub_keys + tb, a.hub_vals + tb, tbits, key, v);
+            else ok = hash_add_kv(reinterpret_cast<unsigned long long *>(a.hub_vals) + tb, tbits, key, v);
+            if (!ok) set_error(a.err, kErrHashFull);
+        }
         m0 += __popc(__ballot_sync(kFull, mine <= x0 + 32));  // the member of the next chunk's first entry
     }
     pc.flush(a.prof);
@@ -511,7 +515,16 @@ __global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const in
         while (a.tab_off[k + 1] <= s0) ++k;  // the same on every lane
         const int32_t c = list[k];
         const int64_t sl = s0 + lane - a.tab_base;
-        const int32_t key = a.hub_keys[sl];
+        int32_t key;
+        A val;
+        if constexpr (P::det) {
+            key = a.hub_keys[sl];
+            val = key >= 0 ? a.hub_vals[sl] : (A)0;
+        } else {  // key and fp32 value in one word
+            const unsigned long long kv = reinterpret_cast<const unsigned long long *>(a.hub_vals)[sl];
+            key = (int32_t)(uint32_t)kv;
+            val = (A)__uint_as_float((uint32_t)(kv >> 32));
+        }
         const unsigned ball = __ballot_sync(kFull, key >= 0);
         if (!ball) continue;
         int pos0 = 0;
@@ -520,7 +533,7 @@ __global__ void __launch_bounds__(256) k_agg_tab_write(AV<P, Wi, Wo> a, const in
         A part = 0;
         if (key >= 0) {
             const int64_t o = a.out_off[c] + pos0 + __popc(ball & ((1u << lane) - 1u));
-            const Wo wo = out_weight<Wo>(a.hub_vals[sl]);
+            const Wo wo = out_weight<Wo>(val);
             a.out_idx[o] = key;
             a.out_w[o] = wo;
             part = wconv<A>(wo);

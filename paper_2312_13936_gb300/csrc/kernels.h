@@ -27,7 +27,8 @@ constexpr int kWarpSlots = 512;     // 8 warp tables fill the same 48 KB as one 
 constexpr int kBlockSlots = 4096;
 constexpr int kBinHub = 6;
 // the packed bin-6 tables of the aggregation are cleared and filled in
-// chunks of at most this many bytes (12 per slot)
+// chunks of at most this many bytes (12 per slot; 8 in the asynchronous
+// mode, whose slot holds key and fp32 value in one word)
 constexpr int64_t kAggTableBytes = (int64_t)8 << 30;
 // rows longer than this are walked by a whole warp in the schedule kernel
 // (its long-row variant, chosen when a graph's degree bound exceeds it) and
