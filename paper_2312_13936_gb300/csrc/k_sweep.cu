@@ -856,63 +856,123 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t warps = nthreads >> 5, gw = tid >> 5;
-    // eligibility and layout (block 0)
-    if (blockIdx.x == 0) {
-        long long np = 0, ns = 0, ne = 0;
-        for (int64_t i0 = 0; i0 < nh; i0 += blockDim.x) {
-            const int64_t i = i0 + threadIdx.x;
-            bool e = false;
-            int64_t sz = 0, dv = 0;
-            if (i < nh) {
-                const int64_t j = j0 + i;
-                const int32_t v = __ldg(&a.hubs[j]);
-                const int32_t gv = graph_of<B>(a, v);
-                int32_t d = 0;
-                e = take_vertex<P, W, REFINE, B>(a, v, d, gv);
-                if (!e) {
-                    if (proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
-                    pc.v[1]++;
+    // A layered step (below cap_step: no two of its vertices are adjacent)
+    // with one hub: every block reads the hub's eligibility itself -- no
+    // vertex of the step can change it (a flag is set, or a community joined,
+    // only by a neighbour), and the grid barriers of the previous step made
+    // its last writes visible -- so the layout needs no barrier of its own.
+    // Block 0 records the layout and resets the hub's state before the
+    // insertion barrier, and clears the pruning flag after it, once every
+    // block has read the flag.
+    const bool single = nh == 1 && cur_step < a.cap_step;
+    int64_t np, S, E;
+    int32_t sv = -1, sbits = 0;  // single: the hub and its table's log2 size
+    if (single) {
+        const int32_t v = __ldg(&a.hubs[j0]);
+        const int32_t gv = graph_of<B>(a, v);
+        int32_t d = 0;
+        bool e;
+        if (REFINE) {
+            d = ldm(&a.C[v]);
+            e = ldm(&a.size[d]) == 1 && !(B && ldm(&a.gdone[gv]));
+        } else {
+            e = ldm(&a.unproc[v]) != 0 && !(B && ldm(&a.gdone[gv]));
+            if (e) d = ldm(&a.C[v]);
+        }
+        const int32_t dv = e ? a.deg[v] : 0;
+        sbits = ceil_log2(2 * (int64_t)dv);
+        if (sbits < 6) sbits = 6;
+        np = e ? 1 : 0;
+        S = e ? (1LL << sbits) : 0;
+        E = dv;
+        sv = v;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (!e) {
+                if (proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
+                pc.v[1]++;
+            } else {
+                if (P::det) {
+                    a.hkey[2 * j0] = 0ULL;
+                    a.hkey[2 * j0 + 1] = 0ULL;
                 } else {
-                    dv = a.deg[v];
-                    int bits = ceil_log2(2 * dv);
-                    if (bits < 6) bits = 6;
-                    sz = 1LL << bits;
-                    if (P::det) {
-                        a.hkey[2 * j] = 0ULL;
-                        a.hkey[2 * j + 1] = 0ULL;
-                    } else {
-                        a.hkey[j] = 0ULL;
-                    }
-                    a.hcand[j] = INT_MAX;
-                    a.hkvd[j] = 0;
-                    a.hmv[j] = 0;
+                    a.hkey[j0] = 0ULL;
                 }
-                a.hd[j] = e ? d : -1;
+                a.hcand[j0] = INT_MAX;
+                a.hkvd[j0] = 0;
+                a.hmv[j0] = 0;
+                a.hj[0] = (int32_t)j0;
+                a.htoff[0] = 0;
+                a.heoff[0] = 0;
+                a.htoff[1] = S;
+                a.heoff[1] = E;
+                a.hinfo[0] = np;
+                a.hinfo[1] = S;
+                a.hinfo[2] = E;
             }
-            long long tp, ts, te;
-            const long long p = block_scan_excl(e ? 1 : 0, &tp);
-            const long long so = block_scan_excl(sz, &ts);
-            const long long eo = block_scan_excl(dv, &te);
-            if (e) {
-                a.hj[np + p] = (int32_t)(j0 + i);
-                a.htoff[np + p] = ns + so;
-                a.heoff[np + p] = ne + eo;
+            a.hd[j0] = e ? d : -1;
+        }
+        if (np == 0) return true;  // the same in every block
+    } else {
+        // eligibility and layout (block 0)
+        if (blockIdx.x == 0) {
+            long long np = 0, ns = 0, ne = 0;
+            for (int64_t i0 = 0; i0 < nh; i0 += blockDim.x) {
+                const int64_t i = i0 + threadIdx.x;
+                bool e = false;
+                int64_t sz = 0, dv = 0;
+                if (i < nh) {
+                    const int64_t j = j0 + i;
+                    const int32_t v = __ldg(&a.hubs[j]);
+                    const int32_t gv = graph_of<B>(a, v);
+                    int32_t d = 0;
+                    e = take_vertex<P, W, REFINE, B>(a, v, d, gv);
+                    if (!e) {
+                        if (proposing<P, REFINE>(cur_step, a.cap_step)) a.prop[v] = -1;
+                        pc.v[1]++;
+                    } else {
+                        dv = a.deg[v];
+                        int bits = ceil_log2(2 * dv);
+                        if (bits < 6) bits = 6;
+                        sz = 1LL << bits;
+                        if (P::det) {
+                            a.hkey[2 * j] = 0ULL;
+                            a.hkey[2 * j + 1] = 0ULL;
+                        } else {
+                            a.hkey[j] = 0ULL;
+                        }
+                        a.hcand[j] = INT_MAX;
+                        a.hkvd[j] = 0;
+                        a.hmv[j] = 0;
+                    }
+                    a.hd[j] = e ? d : -1;
+                }
+                long long tp, ts, te;
+                const long long p = block_scan_excl(e ? 1 : 0, &tp);
+                const long long so = block_scan_excl(sz, &ts);
+                const long long eo = block_scan_excl(dv, &te);
+                if (e) {
+                    a.hj[np + p] = (int32_t)(j0 + i);
+                    a.htoff[np + p] = ns + so;
+                    a.heoff[np + p] = ne + eo;
+                }
+                np += tp;
+                ns += ts;
+                ne += te;
             }
-            np += tp;
-            ns += ts;
-            ne += te;
+            if (threadIdx.x == 0) {
+                a.htoff[np] = ns;
+                a.heoff[np] = ne;
+                a.hinfo[0] = np;
+                a.hinfo[1] = ns;
+                a.hinfo[2] = ne;
+            }
         }
-        if (threadIdx.x == 0) {
-            a.htoff[np] = ns;
-            a.heoff[np] = ne;
-            a.hinfo[0] = np;
-            a.hinfo[1] = ns;
-            a.hinfo[2] = ne;
-        }
+        if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
+        np = __ldcg(&a.hinfo[0]);
+        S = __ldcg(&a.hinfo[1]);
+        E = __ldcg(&a.hinfo[2]);
+        if (np == 0) return true;
     }
-    if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
-    const int64_t np = __ldcg(&a.hinfo[0]), S = __ldcg(&a.hinfo[1]), E = __ldcg(&a.hinfo[2]);
-    if (np == 0) return true;
     // Each warp takes one contiguous range of entries (insertion) or slots
     // (key passes), 32 at a time, and follows the hub they belong to as it
     // goes: one binary search at the start of its range, then a step to the
@@ -921,7 +981,32 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
     // a power of two of at least 8192 slots, so 32 aligned slots lie in one.
     // insertion (the tables are clean: the last scan of a step clears every
     // slot it reads, and the engine clears them before the first sweep)
-    {
+    if (single) {  // one hub: its entries [0, E), its table [0, S); the layout in registers
+        const int64_t per = ((E + warps - 1) / warps + 31) & ~(int64_t)31;
+        const int64_t x1 = (gw + 1) * per < E ? (gw + 1) * per : E;
+        const int64_t e0 = a.off[sv];
+        const int32_t bv = REFINE ? __ldg(&a.CB[sv]) : 0;
+        for (int64_t x0 = gw * per; x0 < x1; x0 += 32) {
+            const int64_t x = x0 + lane;
+            int32_t key = -1;
+            A val = 0;
+            if (x < x1) {
+                const int32_t u = a.idx[e0 + x];
+                if (u != sv && (!REFINE || __ldg(&a.CB[u]) == bv)) {
+                    key = ldm(&a.C[u]);
+                    val = wconv<A>(a.w[e0 + x]);
+                }
+            }
+            const unsigned peers = __match_any_sync(kFull, key);
+            val = peer_sum(peers, val);
+            if (key >= 0 && lane == __ffs(peers) - 1) {
+                bool ok;
+                if constexpr (P::det) ok = hash_add(a.hub_keys, a.hub_vals, sbits, key, val);
+                else ok = hash_add_kv(hub_kv<P>(a), sbits, key, val);
+                if (!ok) set_error(a.err, kErrHashFull);
+            }
+        }
+    } else {
         const int64_t per = ((E + warps - 1) / warps + 31) & ~(int64_t)31;
         const int64_t x1 = (gw + 1) * per < E ? (gw + 1) * per : E;
         int64_t p = 0, nb = 0;  // hub of the warp's current entry and the end of its row
@@ -960,6 +1045,8 @@ __device__ __forceinline__ bool run_hubs_grid(const SV<P, W> &a, int64_t j0, int
         }
     }
     if (!grid_barrier(a.bar, a.err, a.spin_limit)) return false;
+    // every block has read the single hub's pruning flag: it is processed
+    if (single && !REFINE && blockIdx.x == 0 && threadIdx.x == 0) a.unproc[sv] = 0;
     // deterministic mode: the largest key per hub -- its high word (pass 0),
     // then its low word among the slots with that high word (pass 1) --
     // then the smallest community id with that key (pass 2); asynchronous
