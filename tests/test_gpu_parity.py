@@ -267,6 +267,38 @@ def test_degenerate_graphs(mode):
         assert abs(q - ref.modularity) <= 1e-12
 
 
+def hubs_among_isolated(seed=9):
+    """Four hubs of 6000 leaves each (leaves chained in pairs, so that
+    communities form), scattered among 1.2 million vertices of which almost
+    all are isolated: the long-row kernels of the vertex weights and of Eq. 1
+    see hub rows next to long runs of empty rows."""
+    rng = np.random.default_rng(seed)
+    n = 1_200_000
+    ids = rng.permutation(n)
+    src, dst = [], []
+    for h in range(4):
+        hub = ids[h]
+        leaves = ids[4 + h * 6000: 4 + (h + 1) * 6000]
+        src += [hub] * len(leaves)
+        dst += leaves.tolist()
+        src += leaves[0::2].tolist()
+        dst += leaves[1::2].tolist()
+    return gen.from_edges(n, np.array(src), np.array(dst))
+
+
+@pytest.mark.parametrize("mode", [lg.LEIDEN_DETERMINISTIC, lg.LEIDEN_ASYNC])
+def test_hubs_among_isolated_vertices(mode):
+    g = hubs_among_isolated()
+    assert int(np.diff(g.offsets).max()) > 2048 and int((np.diff(g.offsets) == 0).sum()) > 1_000_000
+    memb, q, st, _ = run_gpu(g, mode)
+    assert abs(q - oracle.modularity(g, memb)) <= Q_REL_REPORT * max(1.0, abs(q))
+    assert oracle.disconnected(g, memb)[0] == 0
+    if mode == lg.LEIDEN_DETERMINISTIC:
+        ref = oracle.leiden(g, mode=oracle.SYNC)
+        assert np.array_equal(memb, ref.membership)
+        assert st.passes == ref.passes
+
+
 def test_empty_graph():
     import torch
     h = lg.Leiden(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
