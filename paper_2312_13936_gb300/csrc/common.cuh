@@ -199,25 +199,23 @@ __device__ __forceinline__ bool hash_add(int32_t *keys, A *vals, int bits, int32
 
 // Open-addressing table whose slot is one 8-byte word: the key in the low
 // half (-1: empty), an fp32 value in the high half, so that an insertion
-// touches one memory sector (the asynchronous mode's global hub tables).
+// touches one memory sector (the asynchronous mode's global tables). A new
+// key goes in with its value by one 64-bit compare-and-swap against the
+// empty word; a failed swap returns the slot's word, and if its key is ours
+// the value is added to the high half. A slot's key never changes once set,
+// so the key half of a returned word is exact even while other threads add
+// to its value half.
 constexpr unsigned long long kEmptyKV = 0x00000000ffffffffULL;  // key -1, value 0.0f
 __device__ __forceinline__ bool hash_add_kv(unsigned long long *kv, int bits, int32_t k, float v) {
     const uint32_t mask = (1u << bits) - 1u;
+    const unsigned long long mine = ((unsigned long long)__float_as_uint(v) << 32) | (uint32_t)k;
     uint32_t s = hslot(k, bits);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        int32_t *key = reinterpret_cast<int32_t *>(&kv[s]);
-        float *val = reinterpret_cast<float *>(&kv[s]) + 1;
-        const int32_t cur = *((volatile int32_t *)key);
-        if (cur == k) {
-            atomicAdd(val, v);
+        const unsigned long long cur = atomicCAS(&kv[s], kEmptyKV, mine);
+        if (cur == kEmptyKV) return true;
+        if ((int32_t)(uint32_t)cur == k) {
+            atomicAdd(reinterpret_cast<float *>(&kv[s]) + 1, v);
             return true;
-        }
-        if (cur == -1) {
-            const int32_t prev = atomicCAS(key, -1, k);
-            if (prev == -1 || prev == k) {
-                atomicAdd(val, v);
-                return true;
-            }
         }
         s = (s + 1u) & mask;
     }
