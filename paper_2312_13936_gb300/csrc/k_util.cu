@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kPartThreads) k_spart_scatter(const int32_t *k
         s_wcnt[wib][lane] = (lane == leader && k >= 0) ? __popc(peers) : 0;
         __syncthreads();
         if (k >= 0) {
-            int before = 0;  // items of key k in lower warps of this round
+            int before = 0;  // items of key k in lower warps of this iteration (r)
             for (int w2 = 0; w2 < wib; ++w2)
                 for (int l2 = 0; l2 < 32; ++l2)
                     if (s_wkey[w2][l2] == k) before += s_wcnt[w2][l2];
