@@ -17,8 +17,8 @@ times.
   python -m paper_2312_13936_gb300.tune --out CACHE.json [--graphs road:2000,rmat:21,...]
 
 tunes on the repository's synthetic recipes (road lattices, block models,
-R-MAT graphs; needs the ``gen`` module beside the package) and merges the
-entries into CACHE.json.
+R-MAT graphs, batches of block models; needs the ``gen`` module beside the
+package) and merges the entries into CACHE.json.
 """
 from __future__ import annotations
 
@@ -117,6 +117,9 @@ def _graph(spec: str):
     if kind == "sbm":
         n = int(arg or 100000)
         return f"SBM {n} vertices, 100 blocks", gen.sbm(n, 100, 15.0 / (n / 100), 0.0003 * 1e4 / n, seed=7)
+    if kind == "batch":
+        G = int(arg or 4096)
+        return f"batch of {G} SBM graphs, 100-100000 vertices", gen.sbm_batch(G, seed=4)
     raise ValueError(f"unknown graph spec {spec}")
 
 
@@ -124,11 +127,11 @@ def main(argv=None):
     import numpy as np
     import torch
 
-    from . import LEIDEN_ASYNC, LEIDEN_DETERMINISTIC, Leiden
+    from . import LEIDEN_ASYNC, LEIDEN_DETERMINISTIC, Leiden, LeidenBatch
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--out", required=True, help="cache file to create or extend")
     ap.add_argument("--graphs", default="road:2000,sbm:200000,rmat:21",
-                    help="comma-separated specs: road:SIDE, sbm:N, rmat:SCALE")
+                    help="comma-separated specs: road:SIDE, sbm:N, rmat:SCALE, batch:GRAPHS")
     ap.add_argument("--mode", default="async", choices=["async", "det"])
     ap.add_argument("--runs", type=int, default=3)
     ap.add_argument("--rounds", type=int, default=2)
@@ -138,12 +141,17 @@ def main(argv=None):
     entries = []
     for spec in args.graphs.split(","):
         name, g = _graph(spec)
-        h = Leiden(g.offsets, g.indices, g.weights, tuning=None)
+        if hasattr(g, "num_graphs"):  # a packed batch: one LeidenBatch handle
+            h = LeidenBatch(g.vseg, g.offsets, g.indices, g.weights, tuning=None)
+            n, nnz = int(g.vseg[-1]), int(g.offsets[-1])
+        else:
+            h = Leiden(g.offsets, g.indices, g.weights, tuning=None)
+            n, nnz = g.n, g.nnz
         t0 = time.perf_counter()
         best, ms0, ms1, trials = tune_handle(h, mode, args.runs, args.rounds)
         h.close()
-        maxdeg = int(np.diff(g.offsets).max()) if g.n else 0
-        e = {"gpu": gpu, **graph_class(g.n, g.nnz, maxdeg), **best, "graph": name, "mode": args.mode,
+        maxdeg = int(np.diff(g.offsets).max()) if n else 0
+        e = {"gpu": gpu, **graph_class(n, nnz, maxdeg), **best, "graph": name, "mode": args.mode,
              "ms_default": ms0, "ms_tuned": ms1, "trials": len(trials), "tune_s": time.perf_counter() - t0}
         entries.append(e)
         print(json.dumps(e), flush=True)
