@@ -227,3 +227,31 @@ def test_serve_lanes_by_layer_cap():
     out, info, steps = serve([heavy, light], lg.LEIDEN_DETERMINISTIC, arrivals_per_step=2, schedule_layers=32)
     p = [run_gpu(G, lg.LEIDEN_DETERMINISTIC, schedule_layers=32)[2].passes for G in (heavy, light)]
     assert steps == max(p)
+
+
+def test_serve_device_submissions_take_their_lanes():
+    """Graphs submitted as CUDA tensors are classed on the device (their
+    largest row length) like host ones: a heavy-tailed graph and a light one
+    in separate lanes (the steps add up to their passes), each result equal to
+    its single run, and results read back to device memory."""
+    import torch
+    from tests.test_gpu_parity import hub_graph
+    heavy, light = hub_graph(), gen.road(40)
+    srv = lg.LeidenServer(heavy.n + light.n, heavy.nnz + light.nnz, max_graphs=4, mode=lg.LEIDEN_DETERMINISTIC)
+    try:
+        ids = [srv.submit(torch.as_tensor(G.offsets).cuda(), torch.as_tensor(G.indices).cuda(),
+                          torch.as_tensor(G.weights).cuda()) for G in (heavy, light)]
+        res, steps = {}, 0
+        while len(res) < 2:
+            srv.step()
+            steps += 1
+            for rid, memb, q, passes, comm in srv.results(device=True):
+                assert memb.is_cuda
+                res[rid] = (memb.cpu().numpy(), passes)
+            assert steps < 200
+        alone = [run_gpu(G, lg.LEIDEN_DETERMINISTIC) for G in (heavy, light)]
+        assert steps == alone[0][2].passes + alone[1][2].passes
+        for rid, (ms, qs, sts, _) in zip(ids, alone):
+            assert np.array_equal(res[rid][0], ms) and res[rid][1] == sts.passes
+    finally:
+        srv.close()
