@@ -1,10 +1,12 @@
 // Rows of a holey CSR sorted by target: the deterministic mode writes every
 // aggregated row in ascending target order (reading R10), so the stored
 // super-vertex graph is the same bit for bit whatever order the hash tables
-// held. Every entry gets the key (row << 32) | target, and the unused slots
-// after a row's fill the key (row << 32) | 0xffffffff, so a stable LSD radix
-// sort of the keys (8-bit digits, the counting sort of k_util.cu) leaves
-// every row in place with its entries ascending and its unused slots last.
+// held. Every entry gets the key (row << tb) | target, and the unused slots
+// after a row's fill the key (row << tb) | (2^tb - 1), with tb the fewest
+// bits that hold every target below the marker, so a stable LSD radix sort
+// of the key's tb + row bits (8-bit digits, the counting sort of k_util.cu)
+// leaves every row in place with its entries ascending and its unused slots
+// last.
 // The sort carries a permutation; targets and weights are gathered by it.
 // Rows go in chunks of at most 2^30 entries (the counting sort's positions
 // are int32).
@@ -28,21 +30,52 @@ inline int sgrid(int64_t n) {
 #define SGRID_STRIDE(i, n) \
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-// keys of the slots [e0, e0 + M) of rows [r0, r1), rows relative to r0
-// (the row of a slot by binary search over the offsets); ord = iota
+// keys of the slots [e0, e0 + M) of rows [r0, r1): (row - r0) << tb |
+// target, and (row - r0) << tb | (2^tb - 1) for a row's unused slots (the
+// targets are below 2^tb - 1); ord = iota. Rows and slots take positions of
+// one merged sequence (row rr = r - r0 at rr + off[r] - e0, its slot e at
+// rr + 1 + e - e0) and warp k of W takes an equal range of it: a binary
+// search over the rows finds where its range starts, then it walks its rows
+// 32 at a time and writes the keys of their slots in the range with all
+// lanes. No per-slot search, and no warp walks more than its share of rows.
 __global__ void k_row_keys(const int64_t *off, const int32_t *deg, const int32_t *idx, int64_t r0, int64_t r1,
-                           int64_t e0, int64_t M, unsigned long long *key, int32_t *ord) {
-    SGRID_STRIDE(i, M) {
-        const int64_t e = e0 + i;
-        int64_t lo = r0, hi = r1 - 1;  // the last row starting at or before e
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (off[mid] <= e) lo = mid;
-            else hi = mid - 1;
+                           int64_t e0, int64_t M, int tb, unsigned long long *key, int32_t *ord) {
+    const int lane = threadIdx.x & 31;
+    const int64_t R = r1 - r0, Tn = R + M;
+    const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t P0 = (int64_t)((__int128)Tn * wid / W), P1 = (int64_t)((__int128)Tn * (wid + 1) / W);
+    if (P0 >= P1) return;
+    const unsigned long long gap = (1ULL << tb) - 1ULL;
+    int64_t lo = 0, hi = R;  // the last row rr with rr + off[r0 + rr] - e0 <= P0
+    while (hi - lo > 1) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (mid + off[r0 + mid] - e0 <= P0) lo = mid;
+        else hi = mid;
+    }
+    for (int64_t rb = lo; rb < R; rb += 32) {
+        const int64_t rr = rb + lane;
+        const bool valid = rr < R;
+        const int64_t a = valid ? off[r0 + rr] - e0 : M;
+        const int64_t b = valid ? (rr + 1 < R ? off[r0 + rr + 1] - e0 : M) : M;
+        const int32_t d = valid ? deg[r0 + rr] : 0;
+        const int64_t s0 = a > P0 - rr - 1 ? a : P0 - rr - 1;  // its slots in the range
+        const int64_t t0 = b < P1 - rr - 1 ? b : P1 - rr - 1;
+        unsigned todo = __ballot_sync(0xffffffffu, valid && s0 < t0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t xs = __shfl_sync(0xffffffffu, s0, src), xt = __shfl_sync(0xffffffffu, t0, src);
+            const int64_t as = __shfl_sync(0xffffffffu, a, src);
+            const int32_t ds = __shfl_sync(0xffffffffu, d, src);
+            const unsigned long long hk = (unsigned long long)(rb + src) << tb;
+            for (int64_t x = xs + lane; x < xt; x += 32) {
+                key[x] = hk | (x < as + ds ? (unsigned long long)(uint32_t)idx[e0 + x] : gap);
+                ord[x] = (int32_t)x;
+            }
         }
-        const uint32_t t = e < off[lo] + deg[lo] ? (uint32_t)idx[e] : 0xffffffffu;
-        key[i] = ((unsigned long long)(lo - r0) << 32) | t;
-        ord[i] = (int32_t)i;
+        const int64_t next = rr + 1 < R ? rr + 1 + off[r0 + rr + 1] - e0 : Tn;  // the next row's position
+        if (__ballot_sync(0xffffffffu, !valid || next >= P1)) break;
     }
 }
 __global__ void k_key_digit(const unsigned long long *key, int64_t M, int shift, int32_t *digit) {
@@ -119,20 +152,23 @@ cudaError_t launch_sort_rows(int64_t n, const int64_t *off, const int32_t *deg, 
     auto *w_copy = reinterpret_cast<WInt *>(take(8 * M1));
     int64_t *key_off = reinterpret_cast<int64_t *>(take(8 * ((1 << kSortDigitBits) + 2)));
     void *part_tmp = take(partition_tmp_bytes(M1, 1 << kSortDigitBits));
-    int tbits = 1;  // targets are row ids of the same graph
-    while ((1LL << tbits) < n) ++tbits;
+    int tbits = 1;  // targets are row ids of the same graph: below n <= 2^tbits - 1, the gap marker
+    while ((1LL << tbits) - 1 < n) ++tbits;
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
         const int64_t r0 = cut[k], r1 = cut[k + 1];
         const int64_t e0 = at(r0), M = at(r1) - e0;
         if (M <= 1) continue;
         int rbits = 0;
         while ((1LL << rbits) < r1 - r0) ++rbits;
-        k_row_keys<<<sgrid(M), 256, 0, s>>>(off, deg, idx, r0, r1, e0, M, key, ord);
+        if (rbits + tbits > 64) return cudaErrorInvalidValue;
+        // warps of about 4096 merged positions each, at most one resident wave's worth of blocks per pass
+        const int64_t kb = ((r1 - r0) + M + 8 * 4096 - 1) / (8 * 4096);
+        k_row_keys<<<(int)(kb < 1 ? 1 : (kb > 152 * 64 ? 152 * 64 : kb)), 256, 0, s>>>(off, deg, idx, r0, r1, e0, M,
+                                                                                      tbits, key, ord);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // the key's bits: targets and the gap marker, then the row
         std::vector<int> shifts;
-        (void)tbits;
-        for (int sh = 0; sh < 32; sh += kSortDigitBits) shifts.push_back(sh);  // targets and the gap marker
-        for (int sh = 0; sh < rbits; sh += kSortDigitBits) shifts.push_back(32 + sh);
+        for (int sh = 0; sh < tbits + rbits; sh += kSortDigitBits) shifts.push_back(sh);
         unsigned long long *ck = key, *ck2 = key2;
         int32_t *co = ord, *co2 = ord2;
         for (int sh : shifts) {
