@@ -95,3 +95,29 @@ def test_optional_leg_reports_a_failure_in_its_place(capsys):
         raise ValueError("no such graph")
     assert bench.optional_leg(broken) == {"error": "ValueError: no such graph"}
     assert "no such graph" in capsys.readouterr().err
+
+
+def test_traffic_lookup(tmp_path, monkeypatch):
+    """The DRAM traffic of the committed ncu summary is reported only for the
+    same kernel sources and workload; a capture of a smaller case of the same
+    recipe is carried beside a workload too large to capture, not as its
+    traffic."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    f = tmp_path / "traffic.json"
+    h = bench.kernel_source_hash()
+    cap = {"move/sweep": {"dram_bytes_per_launch": 7.0e9, "algorithmic_bytes_per_launch": 3.5e9, "ratio": 2.0}}
+    f.write_text(json.dumps({"source_hash": h, "captures": [
+        {"workload": "road A", "classes": {"move/sweep": {"dram_bytes_per_launch": 4.0e9}}},
+        {"workload": "R-MAT small", "stands_for": "R-MAT large", "classes": cap}]}))
+    monkeypatch.setattr(bench, "TRAFFIC", str(f))
+    assert bench.traffic_for("move/sweep", "road A") == (4.0e9, None)
+    exact, sample = bench.traffic_for("move/sweep", "R-MAT large")
+    assert exact is None and sample["workload"] == "R-MAT small" and sample["ratio"] == 2.0
+    assert bench.traffic_for("refine/sweep", "road A") == (None, None)
+    assert bench.traffic_for("move/sweep", "another workload") == (None, None)
+    # other kernel sources: nothing
+    f.write_text(json.dumps({"source_hash": "0" * 16, "captures": [
+        {"workload": "road A", "classes": {"move/sweep": {"dram_bytes_per_launch": 4.0e9}}}]}))
+    assert bench.traffic_for("move/sweep", "road A") == (None, None)
