@@ -370,7 +370,11 @@ typedef struct {
     int32_t coop_blocks_per_sm;  /* blocks per SM of the persistent sweep (0: as many as fit); default 0 */
     int32_t vertices_per_block;  /* persistent sweep: vertices per block below a full grid (256..65536);
                                     default 2048 */
-    int32_t reserved[3];
+    int32_t list_order_min_vertices; /* a pass whose graph has at least this many vertices, no row longer than
+                                    block_max_deg and one graph gives its sweeps a copy of its rows and
+                                    vertex weights in the order of the schedule's (step, bin) lists, so
+                                    that each step reads them contiguously (0: never); default 1048576 */
+    int32_t reserved[2];
 } leiden_tuning;
 
 /* Fill *t with the defaults listed above. */

@@ -81,8 +81,10 @@ class Tuning(ctypes.Structure):
     persistent sweep's grid; none changes a deterministic result."""
     _fields_ = [("thread_max_deg", ctypes.c_int32), ("warp_max_deg", ctypes.c_int32),
                 ("block_max_deg", ctypes.c_int32), ("coop_blocks_per_sm", ctypes.c_int32),
-                ("vertices_per_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
-    KEYS = ("thread_max_deg", "warp_max_deg", "block_max_deg", "coop_blocks_per_sm", "vertices_per_block")
+                ("vertices_per_block", ctypes.c_int32), ("list_order_min_vertices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+    KEYS = ("thread_max_deg", "warp_max_deg", "block_max_deg", "coop_blocks_per_sm", "vertices_per_block",
+            "list_order_min_vertices")
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k in self.KEYS}

@@ -255,8 +255,33 @@ leiden_status Handle::Impl::pass(Run &r, int32_t lp, bool &stop) {
             ST(q.ensure_hub(hub_bits, hub_regions, det));
         }
     }
+    // the rows and vertex weights in the order of the (step, bin) lists, so
+    // that a sweep step reads them contiguously instead of one sector per
+    // vertex spread over the whole graph (one graph without rows beyond the
+    // block bin, from list_order_min_vertices vertices; values unchanged)
+    const int64_t nl = q.hkey_off[(size_t)nkeys];
+    const bool list_order = !batch && q.tune.list_order_min_vertices > 0 &&
+                            n >= (int64_t)q.tune.list_order_min_vertices &&
+                            (int64_t)q.hsc->maxdeg <= (int64_t)q.tune.block_max_deg && nl > 0;
+    if (list_order) {
+        ST(q.ensure_list_order(nl, 0));
+        CK(launch_list_lens(q.list, nl, G.deg, q.lo_len, s));
+        CK(launch_exclusive_scan_i32(q.lo_len, q.lo_off, nl, q.scan_tmp, s));
+        int64_t ne = 0;
+        CK(cudaMemcpyAsync(&ne, q.lo_off + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ST(q.ensure_list_order(nl, ne));
+        CK(launch_list_rows(q.list, nl, G, q.K, det, q.lo_off, q.lo_idx, q.lo_w, q.lo_K, s));
+        q.launches += 3;
+    }
     SweepCtx sc;
     sc.g = sG;
+    if (list_order) {
+        sc.loff = q.lo_off;
+        sc.lidx = q.lo_idx;
+        sc.lw = q.lo_w;
+        sc.lK = q.lo_K;
+    }
     sc.det = det;
     sc.C = sC;
     sc.CB = sCB;

@@ -483,6 +483,42 @@ struct Handle::Impl {
     unsigned long long *hkey = nullptr, *hspan = nullptr;
     long long *hkvd = nullptr;
     int64_t hubs_cap = -1;
+    // the rows and vertex weights of a pass's graph in list order
+    // (leiden_tuning.list_order_min_vertices): offsets (nv + 1), row
+    // lengths (nv), entries (ne, weights of wsz bytes) and weights (asz bytes)
+    int64_t *lo_off = nullptr;
+    int32_t *lo_len = nullptr, *lo_idx = nullptr;
+    void *lo_w = nullptr, *lo_K = nullptr;
+    int64_t lo_cap_v = 0, lo_cap_e = 0;
+    leiden_status ensure_list_order(int64_t nv, int64_t ne) {
+        if (nv > lo_cap_v) {
+            for (void *p : {(void *)lo_off, (void *)lo_len, lo_K})
+                if (p) free_one(p);
+            lo_off = nullptr;
+            lo_len = nullptr;
+            lo_K = nullptr;
+            lo_cap_v = 0;
+            ST(alloc(&lo_off, nv + 1));
+            ST(alloc(&lo_len, nv));
+            long long *k = nullptr;
+            ST(alloc(&k, nv));  // 8 bytes: int64 (deterministic) or fp32 weights
+            lo_K = k;
+            lo_cap_v = nv;
+        }
+        if (ne > lo_cap_e) {
+            for (void *p : {(void *)lo_idx, lo_w})
+                if (p) free_one(p);
+            lo_idx = nullptr;
+            lo_w = nullptr;
+            lo_cap_e = 0;
+            ST(alloc(&lo_idx, ne > 0 ? ne : 1));
+            long long *w = nullptr;
+            ST(alloc(&w, ne > 0 ? ne : 1));  // 8 bytes: WInt or fp32 weights
+            lo_w = w;
+            lo_cap_e = ne;
+        }
+        return LEIDEN_OK;
+    }
     leiden_status ensure_hubs(int64_t nh) {
         if (!hinfo) {
             ST(alloc(&hinfo, 4));  // a step's eligible hubs, table slots, entries

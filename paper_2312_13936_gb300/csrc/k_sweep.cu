@@ -51,6 +51,10 @@ template <class P, class W> struct SV {
     int32_t *prop;
     long long *gain;
     const int32_t *step;
+    const int64_t *loff;  // rows and weights in list order (null: by vertex)
+    const int32_t *lidx;
+    const W *lw;
+    const A *lK;
     A kscale;       // 2m (deterministic) or 1/2m (asynchronous), see move_key
     double two_m_d;
     double gamma;
@@ -100,6 +104,26 @@ template <class P, class W> struct SV {
     int32_t G;
 };
 
+// The row and weight of the vertex v at list position t: from the copy in
+// list order when the pass made one (a step's rows then lie together), else
+// from the vertex's own row.
+template <class W> struct RowOf {
+    int64_t e0;
+    int32_t dv;
+    const int32_t *idx;
+    const W *w;
+};
+template <class P, class W> __device__ __forceinline__ RowOf<W> row_of(const SV<P, W> &a, int32_t v, int64_t t) {
+    if (a.loff) {
+        const int64_t e0 = a.loff[t];
+        return {e0, (int32_t)(a.loff[t + 1] - e0), a.lidx, a.lw};
+    }
+    return {a.off[v], a.deg[v], a.idx, a.w};
+}
+template <class P, class W> __device__ __forceinline__ typename P::acc k_of(const SV<P, W> &a, int32_t v, int64_t t) {
+    return a.lK ? a.lK[t] : a.K[v];
+}
+
 // A thread's sweep sums: gains or joins (asynchronous), applied gains
 // (deterministic local-moving), applied proposals (refinement), and this
 // sweep's per-graph slots they go to.
@@ -129,6 +153,10 @@ template <class P, class W> SV<P, W> view(const SweepCtx &c) {
     a.prop = c.prop;
     a.gain = c.gain;
     a.step = c.step;
+    a.loff = c.loff;
+    a.lidx = c.lidx;
+    a.lw = static_cast<const W *>(c.lw);
+    a.lK = static_cast<const A *>(c.lK);
     a.kscale = P::det ? (A)c.two_m_i : (A)(1.0 / c.two_m_f);
     a.two_m_d = P::det ? (double)c.two_m_i : c.two_m_f;
     a.gamma = c.gamma;
@@ -377,9 +405,10 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
             a.unproc[v] = 0;  // processed (Algorithm 2 pruning)
             d = ldm(&a.C[v]);
         }
-        const A Kv = a.K[v];
-        const int64_t e0 = a.off[v];
-        const int32_t dv = a.deg[v];
+        const A Kv = k_of(a, v, t);
+        const RowOf<W> row = row_of(a, v, t);
+        const int64_t e0 = row.e0;
+        const int32_t dv = row.dv;
         const typename P::tot sd = ldm(&a.Sig[d]);
         const int32_t bv = REFINE ? a.CB[v] : 0;
         int32_t jj[E];
@@ -389,8 +418,8 @@ __device__ __forceinline__ void run_thread(const SV<P, W> &a, const int32_t *__r
             jj[k] = -1;
             wt[k] = 0;
             if (k < dv) {
-                jj[k] = a.idx[e0 + k];
-                wt[k] = wconv<A>(a.w[e0 + k]);
+                jj[k] = row.idx[e0 + k];
+                wt[k] = wconv<A>(row.w[e0 + k]);
             }
         }
         int32_t c[E];
@@ -470,15 +499,16 @@ __device__ __forceinline__ void run_tile(const SV<P, W> &a, const int32_t *__res
             if (tl == 0) pc.v[1]++;
             continue;
         }
-        const A Kv = a.K[v];
-        const int64_t e0 = a.off[v];
-        const int32_t dv = a.deg[v];
+        const A Kv = k_of(a, v, t);
+        const RowOf<W> row = row_of(a, v, t);
+        const int64_t e0 = row.e0;
+        const int32_t dv = row.dv;
         const int32_t bv = REFINE ? a.CB[v] : 0;
         int32_t j = -1, c = -1;
         A wv = 0;
         if (tl < dv) {
-            j = a.idx[e0 + tl];
-            wv = wconv<A>(a.w[e0 + tl]);
+            j = row.idx[e0 + tl];
+            wv = wconv<A>(row.w[e0 + tl]);
             bool ok = (j != v);
             if (REFINE && ok) ok = (__ldg(&a.CB[j]) == bv);
             if (ok) c = ldm(&a.C[j]);
@@ -558,9 +588,10 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
             if (lane == 0) pc.v[1]++;
             continue;
         }
-        const A Kv = a.K[v];
-        const int64_t e0 = a.off[v];
-        const int32_t dv = a.deg[v];
+        const A Kv = k_of(a, v, t);
+        const RowOf<W> row = row_of(a, v, t);
+        const int64_t e0 = row.e0;
+        const int32_t dv = row.dv;
         const int32_t bv = REFINE ? a.CB[v] : 0;
         int bits = ceil_log2(2 * (int64_t)dv);
         if (bits < 6) bits = 6;
@@ -571,10 +602,10 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
         }
         __syncwarp();
         for (int32_t e = lane; e < dv; e += 32) {
-            const int32_t j = a.idx[e0 + e];
+            const int32_t j = row.idx[e0 + e];
             if (j == v) continue;
             if (REFINE && __ldg(&a.CB[j]) != bv) continue;
-            if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
+            if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(row.w[e0 + e]))) set_error(a.err, kErrHashFull);
         }
         __syncwarp();
         typename P::key key = AccLimits<typename P::key>::lowest();
@@ -619,7 +650,7 @@ __device__ __forceinline__ void run_warp(const SV<P, W> &a, const int32_t *__res
         if (!REFINE && !P::det) {
             mv = __shfl_sync(kFull, mv, 0);
             if (mv)
-                for (int32_t e = lane; e < dv; e += 32) flag_unproc(a, sm, a.idx[e0 + e]);
+                for (int32_t e = lane; e < dv; e += 32) flag_unproc(a, sm, row.idx[e0 + e]);
         }
         __syncwarp();
     }
@@ -654,9 +685,10 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
         __syncthreads();
         if (!s_elig) continue;
         const int32_t d = s_d;
-        const A Kv = a.K[v];
-        const int64_t e0 = a.off[v];
-        const int32_t dv = a.deg[v];
+        const A Kv = k_of(a, v, t);
+        const RowOf<W> row = row_of(a, v, t);
+        const int64_t e0 = row.e0;
+        const int32_t dv = row.dv;
         const int32_t bv = REFINE ? a.CB[v] : 0;
         int bits = ceil_log2(2 * (int64_t)dv);
         if (bits < 6) bits = 6;
@@ -674,10 +706,10 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
         }
         __syncthreads();
         for (int64_t e = tid; e < dv; e += blockDim.x) {
-            const int32_t j = a.idx[e0 + e];
+            const int32_t j = row.idx[e0 + e];
             if (j == v) continue;
             if (REFINE && __ldg(&a.CB[j]) != bv) continue;
-            if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(a.w[e0 + e]))) set_error(a.err, kErrHashFull);
+            if (!hash_add(keys, vals, bits, ldm(&a.C[j]), wconv<A>(row.w[e0 + e]))) set_error(a.err, kErrHashFull);
         }
         __syncthreads();
         typename P::key key = AccLimits<typename P::key>::lowest();
@@ -736,7 +768,7 @@ __device__ __forceinline__ void run_block(const SV<P, W> &a, const int32_t *__re
         }
         __syncthreads();
         if (!REFINE && !P::det && s_mv)
-            for (int64_t e = tid; e < dv; e += blockDim.x) flag_unproc(a, sm, a.idx[e0 + e]);
+            for (int64_t e = tid; e < dv; e += blockDim.x) flag_unproc(a, sm, row.idx[e0 + e]);
     }
     __syncthreads();
 }
@@ -1226,9 +1258,10 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
         }
         int64_t e0 = 0;
         int32_t dv = 0;
+        const int32_t *ridx = a.idx;
         if (c >= 0) {
             const int32_t d = ldm(&a.C[v]);
-            const auto Kv = (typename P::tot)a.K[v];
+            const auto Kv = (typename P::tot)k_of(a, v, t);
             atomic_add_acc(&a.Sig[d], -Kv);
             atomic_add_acc(&a.Sig[c], Kv);
             atomicSub(&a.size[d], 1);
@@ -1240,10 +1273,12 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
             else
                 gacc_add(sm.gain, B, graph_of<B>(a, v),
                          (typename P::acc)__ldcg(reinterpret_cast<const float *>(a.gain) + v), sm.dq);
-            e0 = a.off[v];
-            dv = a.deg[v];
+            const RowOf<W> row = row_of(a, v, t);
+            e0 = row.e0;
+            dv = row.dv;
+            ridx = row.idx;
             if (dv <= 32)
-                for (int32_t e = 0; e < dv; ++e) flag_unproc(a, sm, a.idx[e0 + e]);
+                for (int32_t e = 0; e < dv; ++e) flag_unproc(a, sm, ridx[e0 + e]);
         }
         unsigned longs = __ballot_sync(kFull, c >= 0 && dv > 32 && !(grid_hub_flags && dv > a.block_max));
         while (longs) {
@@ -1251,7 +1286,8 @@ __device__ __forceinline__ void run_move_apply(const SV<P, W> &a, const int32_t 
             longs &= longs - 1;
             const int64_t es = __shfl_sync(kFull, e0, src);
             const int32_t ds = __shfl_sync(kFull, dv, src);
-            for (int32_t e = lane; e < ds; e += 32) flag_unproc(a, sm, a.idx[es + e]);
+            const int32_t *is = a.loff ? a.lidx : a.idx;  // the same on every lane
+            for (int32_t e = lane; e < ds; e += 32) flag_unproc(a, sm, is[es + e]);
         }
     }
 }
@@ -1269,7 +1305,7 @@ __device__ __forceinline__ void run_refine_apply(const SV<P, W> &a, const int32_
         if (tg < 0) continue;
         const int32_t pt = (__ldg(&a.step[tg]) == cur_step) ? ldm(&a.prop[tg]) : -1;
         if (!(pt < 0 || (pt == v && v > tg))) continue;
-        const auto Kv = (typename P::tot)a.K[v];
+        const auto Kv = (typename P::tot)k_of(a, v, t);
         atomic_add_acc(&a.Sig[v], -Kv);
         atomic_add_acc(&a.Sig[tg], Kv);
         atomicSub(&a.size[v], 1);

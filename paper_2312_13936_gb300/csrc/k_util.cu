@@ -338,6 +338,45 @@ cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s) {
     k_iota<<<grid_for(n, 256), 256, 0, s>>>(a, n);
     return cudaGetLastError();
 }
+namespace {
+__global__ void k_list_lens(const int32_t *list, int64_t nl, const int32_t *deg, int32_t *len) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x)
+        len[t] = deg[list[t]];
+}
+template <class W, class A>
+__global__ void k_list_rows(const int32_t *list, int64_t nl, const int64_t *off, const int32_t *idx, const W *w,
+                            const A *K, const int64_t *loff, int32_t *lidx, W *lw, A *lK) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = list[t];
+        const int64_t e0 = off[v], o = loff[t], d = loff[t + 1] - o;
+        for (int64_t k = 0; k < d; ++k) {
+            lidx[o + k] = idx[e0 + k];
+            lw[o + k] = w[e0 + k];
+        }
+        lK[t] = K[v];
+    }
+}
+}  // namespace
+cudaError_t launch_list_lens(const int32_t *list, int64_t nl, const int32_t *deg, int32_t *len, cudaStream_t s) {
+    if (nl <= 0) return cudaSuccess;
+    k_list_lens<<<grid_for(nl, 256), 256, 0, s>>>(list, nl, deg, len);
+    return cudaGetLastError();
+}
+cudaError_t launch_list_rows(const int32_t *list, int64_t nl, const GraphView &g, const void *K, bool det,
+                             const int64_t *loff, int32_t *lidx, void *lw, void *lK, cudaStream_t s) {
+    if (nl <= 0) return cudaSuccess;
+    const int gb = grid_for(nl, 256);
+    if (det && g.w_int)
+        k_list_rows<WInt, long long><<<gb, 256, 0, s>>>(list, nl, g.off, g.idx, (const WInt *)g.w,
+                                                        (const long long *)K, loff, lidx, (WInt *)lw, (long long *)lK);
+    else if (det)
+        k_list_rows<float, long long><<<gb, 256, 0, s>>>(list, nl, g.off, g.idx, (const float *)g.w,
+                                                         (const long long *)K, loff, lidx, (float *)lw, (long long *)lK);
+    else
+        k_list_rows<float, float><<<gb, 256, 0, s>>>(list, nl, g.off, g.idx, (const float *)g.w, (const float *)K,
+                                                     loff, lidx, (float *)lw, (float *)lK);
+    return cudaGetLastError();
+}
 cudaError_t launch_fill_u64(unsigned long long *a, unsigned long long v, int64_t n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_fill_u64<<<grid_for(n, 256), 256, 0, s>>>(a, v, n);

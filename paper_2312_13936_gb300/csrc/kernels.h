@@ -82,6 +82,13 @@ struct SweepCtx {
     int32_t *prop = nullptr;      // proposed target (-1 none)
     long long *gain = nullptr;    // key gain of a proposal: two words per vertex (det, 128 bits) or fp32
     const int32_t *step = nullptr;  // schedule step of every vertex
+    // the rows and vertex weights in the order of the (step, bin) lists, or
+    // null (read by vertex): list position t's row is lidx/lw[loff[t] ..
+    // loff[t+1]) and its weight lK[t] (values as in g and K)
+    const int64_t *loff = nullptr;
+    const int32_t *lidx = nullptr;
+    const void *lw = nullptr;
+    const void *lK = nullptr;
     double two_m_f = 0;
     long long two_m_i = 0;
     double gamma = 1;
@@ -216,6 +223,13 @@ cudaError_t launch_sort_rows(int64_t n, const int64_t *off, const int32_t *deg, 
 // ---- utilities (k_util.cu)
 cudaError_t launch_iota(int32_t *a, int64_t n, cudaStream_t s);
 cudaError_t launch_fill_i32(int32_t *a, int32_t v, int64_t n, cudaStream_t s);
+// rows of the sweeps' list in list order: len[t] = deg[list[t]] (then the
+// caller scans len into loff), and the copy of list position t's row and
+// vertex weight to lidx/lw[loff[t] ..) and lK[t] (weights WInt or fp32,
+// vertex weights int64 (det) or fp32)
+cudaError_t launch_list_lens(const int32_t *list, int64_t nl, const int32_t *deg, int32_t *len, cudaStream_t s);
+cudaError_t launch_list_rows(const int32_t *list, int64_t nl, const GraphView &g, const void *K, bool det,
+                             const int64_t *loff, int32_t *lidx, void *lw, void *lK, cudaStream_t s);
 cudaError_t launch_fill_u64(unsigned long long *a, unsigned long long v, int64_t n, cudaStream_t s);
 cudaError_t launch_degrees(const int64_t *off, int32_t *deg, int64_t n, int *err, cudaStream_t s);
 // K[i] = sum of row i (acc type), *two_m += sum of K (acc type)

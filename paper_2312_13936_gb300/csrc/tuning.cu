@@ -148,13 +148,14 @@ void tuning_default(leiden_tuning &t) {
     t.block_max_deg = 2048;
     t.coop_blocks_per_sm = 0;
     t.vertices_per_block = 2048;
+    t.list_order_min_vertices = 1 << 20;
 }
 
 bool tuning_valid(const leiden_tuning &t) {
     return t.thread_max_deg >= 1 && t.thread_max_deg <= 8 && t.warp_max_deg >= 32 && t.warp_max_deg <= 256 &&
            t.block_max_deg >= 128 && t.block_max_deg <= 2048 && t.block_max_deg >= t.warp_max_deg &&
            t.coop_blocks_per_sm >= 0 && t.coop_blocks_per_sm <= 32 && t.vertices_per_block >= 256 &&
-           t.vertices_per_block <= 65536;
+           t.vertices_per_block <= 65536 && t.list_order_min_vertices >= 0;
 }
 
 leiden_status tuning_lookup(const char *path, const char *gpu, int64_t n, int64_t nnz, int64_t maxdeg,
@@ -203,6 +204,7 @@ leiden_status tuning_lookup(const char *path, const char *gpu, int64_t n, int64_
     take("block_max_deg", t.block_max_deg);
     take("coop_blocks_per_sm", t.coop_blocks_per_sm);
     take("vertices_per_block", t.vertices_per_block);
+    take("list_order_min_vertices", t.list_order_min_vertices);
     if (!tuning_valid(t)) {
         set_last_error("tuning cache entry outside the valid ranges");
         return LEIDEN_ERR_INVALID;

@@ -1,6 +1,7 @@
 """Launch shapes on the GPU: every candidate shape of the autotuner leaves
 the deterministic mode bit-exact against the oracle's SYNC mode (single
-graphs, including hubs, and batches), an asynchronous run under a tuned
+graphs, including hubs, and batches; rows copied in list order for every
+pass, for passes of 1000 vertices and more, and never), an asynchronous run under a tuned
 shape keeps the quality checks, and a handle created with
 LEIDEN_TUNING_CACHE set takes the cache's entry for the GPU and the graph's
 class."""
@@ -20,11 +21,11 @@ pytestmark = pytest.mark.gpu
 
 SHAPES = [
     {"thread_max_deg": 4, "warp_max_deg": 64, "block_max_deg": 512, "coop_blocks_per_sm": 2,
-     "vertices_per_block": 1024},
+     "vertices_per_block": 1024, "list_order_min_vertices": 1},
     {"thread_max_deg": 1, "warp_max_deg": 32, "block_max_deg": 128, "coop_blocks_per_sm": 1,
-     "vertices_per_block": 256},
+     "vertices_per_block": 256, "list_order_min_vertices": 0},
     {"thread_max_deg": 8, "warp_max_deg": 128, "block_max_deg": 1024, "coop_blocks_per_sm": 3,
-     "vertices_per_block": 4096},
+     "vertices_per_block": 4096, "list_order_min_vertices": 1000},
 ]
 GRAPHS = {"road_200": lambda: gen.road(200), "hubs": hub_graph, "rmat_12": lambda: gen.rmat(12, 16),
           "sbm": lambda: gen.sbm(4000, 16, 0.04, 0.002, seed=5)}

@@ -28,7 +28,19 @@ def _cache(tmp_path, entries, name="cache.json"):
 
 def test_defaults():
     assert lg.leiden_tuning_default().as_dict() == {"thread_max_deg": 8, "warp_max_deg": 256, "block_max_deg": 2048,
-                                                    "coop_blocks_per_sm": 0, "vertices_per_block": 2048}
+                                                    "coop_blocks_per_sm": 0, "vertices_per_block": 2048,
+                                                    "list_order_min_vertices": 1 << 20}
+
+
+def test_lookup_reads_the_list_order_threshold(tmp_path):
+    """An entry may set list_order_min_vertices (0: never); entries without
+    it keep the default."""
+    path = _cache(tmp_path, [_entry(0, 10, 3, list_order_min_vertices=0)])
+    assert lg.leiden_tuning_lookup(path, GPU, 1 << 10, 8 << 10, 10).as_dict()["list_order_min_vertices"] == 0
+    path = _cache(tmp_path, [_entry(0, 10, 3)])
+    assert lg.leiden_tuning_lookup(path, GPU, 1 << 10, 8 << 10, 10).as_dict()["list_order_min_vertices"] == 1 << 20
+    path = _cache(tmp_path, [_entry(0, 10, 3, list_order_min_vertices=-5)])  # outside the range: no entry
+    assert lg.leiden_tuning_lookup(path, GPU, 1 << 10, 8 << 10, 10) is None
 
 
 def test_lookup_takes_the_nearest_entry_of_the_same_gpu_and_tail(tmp_path):
