@@ -46,8 +46,8 @@ bandwidth: its algorithmic bytes (counted by the kernels in the first timed
 step) over its CUDA-event time. "by_phase" and "overall" give the same for
 each phase and for all profiled launches, and the profiled bytes over the
 whole step. "e2e" runs the C ABI from page-locked host buffers (the copies in
-and out inside the timed region) and splits a step into create, run and
-destroy. "cpu_baseline" is the oracle (sequential, one host core) on a
+and out inside the timed region; an unweighted graph goes without its weight
+array) and splits a step into create, run and destroy. "cpu_baseline" is the oracle (sequential, one host core) on a
 bounded sample of the same R-MAT recipe (scale 20). An optional part that
 fails is reported as {"error": ...} in its place.
 """
@@ -734,28 +734,33 @@ def main():
     # ---- end to end through the C ABI with host buffers (H2D and D2H inside)
     def e2e_leg():
         import ctypes
+        vp = ctypes.c_void_p
         # the user's buffers, staged once in page-locked host memory (outside
-        # the timed region), as a caller that streams graphs would keep them
+        # the timed region), as a caller that streams graphs would keep them;
+        # an unweighted graph (every weight 1) is passed without weights, as
+        # its user holds none (the library then takes unit weights)
+        unweighted = nnz > 0 and bool(torch.all(w == 1).item())
+        arrays = (off, idx) if unweighted else (off, idx, w)
         try:
-            hbuf = [torch.empty(t.numel(), dtype=t.dtype, pin_memory=True) for t in (off, idx, w)]
+            hbuf = [torch.empty(t.numel(), dtype=t.dtype, pin_memory=True) for t in arrays]
             hout = torch.empty(max(n, 1), dtype=torch.int32, pin_memory=True)
             pinned = True
         except RuntimeError:
-            hbuf = [torch.empty(t.numel(), dtype=t.dtype) for t in (off, idx, w)]
+            hbuf = [torch.empty(t.numel(), dtype=t.dtype) for t in arrays]
             hout = torch.empty(max(n, 1), dtype=torch.int32)
             pinned = False
-        for hb, t in zip(hbuf, (off, idx, w)):
+        for hb, t in zip(hbuf, arrays):
             hb.copy_(t)
+        hw = vp(None) if unweighted else vp(hbuf[2].data_ptr())
         P = lg.leiden_params_default()
         P.mode = mode
         P.flags = base_flags
-        vp = ctypes.c_void_p
         split = [0.0, 0.0, 0.0]  # create (H2D + device setup), run (+ D2H of the result), destroy
 
         def one():
             t0 = time.perf_counter()
-            hh = lg.leiden_create(n, nnz, vp(hbuf[0].data_ptr()), vp(hbuf[1].data_ptr()),
-                                  vp(hbuf[2].data_ptr()), lg.LEIDEN_HOST, 0, vp(stream.cuda_stream))
+            hh = lg.leiden_create(n, nnz, vp(hbuf[0].data_ptr()), vp(hbuf[1].data_ptr()), hw,
+                                  lg.LEIDEN_HOST, 0, vp(stream.cuda_stream))
             stream.synchronize()
             t1 = time.perf_counter()
             lg.leiden_run(hh, P, vp(hout.data_ptr()), lg.LEIDEN_HOST)
@@ -777,7 +782,9 @@ def main():
             te = float(reduce_stats(torch.tensor([te], device=dev), 1, world).item())
         return {"value": world * ne * nnz / te, "unit": "edges/s",
                 "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in hbuf),
-                "d2h_bytes_per_step": n * 4 + 8, "pinned": pinned, "steps": ne, "ms_per_step": te * 1e3 / ne,
+                "d2h_bytes_per_step": n * 4 + 8, "pinned": pinned,
+                "weights": "none passed (unit weights)" if unweighted else "passed",
+                "steps": ne, "ms_per_step": te * 1e3 / ne,
                 "create_ms": split[0] * 1e3 / ne, "run_ms": split[1] * 1e3 / ne,
                 "destroy_ms": split[2] * 1e3 / ne}
 

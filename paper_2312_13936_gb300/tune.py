@@ -3,7 +3,8 @@
 The paper fixes its parallel schedule by measurement (OpenMP dynamic
 scheduling with a chunk size chosen per machine, Section 4.1); here the
 choices that play that role -- the degree-bin bounds (thread, warp and block
-per vertex), the persistent sweep's blocks per SM and its vertices per block
+per vertex), the persistent sweep's blocks per SM and its vertices per block,
+and the graph size from which the sweeps read rows copied in schedule order
 -- are measured per GPU and graph class, and the best shape goes into a JSON
 cache that handles read when they are created (leiden_tuning_lookup). None of
 the choices changes a result of the deterministic mode.
@@ -35,6 +36,7 @@ CANDIDATES = {
     "block_max_deg": [512, 1024, 2048],
     "coop_blocks_per_sm": [0, 2, 3],
     "vertices_per_block": [1024, 2048, 4096],
+    "list_order_min_vertices": [0, 1 << 18, 1 << 20, 1 << 22],
 }
 
 

@@ -43,6 +43,21 @@ def test_lookup_reads_the_list_order_threshold(tmp_path):
     assert lg.leiden_tuning_lookup(path, GPU, 1 << 10, 8 << 10, 10) is None
 
 
+def test_every_candidate_shape_is_valid(tmp_path):
+    """The autotuner searches every field of the launch shape, and each of
+    its candidate values passes the library's range checks (a cache entry
+    holding it is taken)."""
+    assert set(tune.CANDIDATES) == set(lg.leiden_tuning_default().as_dict())
+    for key, values in tune.CANDIDATES.items():
+        for v in values:
+            shape = {key: v}
+            if key == "warp_max_deg":
+                shape["block_max_deg"] = max(v, 2048)
+            path = _cache(tmp_path, [_entry(0, 10, 3, **shape)])
+            t = lg.leiden_tuning_lookup(path, GPU, 1 << 10, 8 << 10, 10)
+            assert t is not None and t.as_dict()[key] == v, (key, v)
+
+
 def test_lookup_takes_the_nearest_entry_of_the_same_gpu_and_tail(tmp_path):
     path = _cache(tmp_path, [
         _entry(0, 22, 2, vertices_per_block=1024),          # light, 4M vertices, mean degree 4
