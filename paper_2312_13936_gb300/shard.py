@@ -8,7 +8,12 @@ solves it with one ``leiden_batch_run`` on its own GPU, and the results come
 back to every rank by one gather of host arrays at the end.
 
 ``lpt_shares``, ``pack_share`` and ``gather_results`` are plain host logic;
-``run_sharded`` puts them around the library's batch handle. A packed batch is
+``run_sharded`` puts them around the library's batch handle.
+
+The served form spreads over the GPUs of one process with ``ServeRouter``:
+one continuous-batching server per device, each request admitted to the
+device with the least outstanding work, every device stepped by its own host
+thread. A packed batch is
 any object with ``num_graphs``, ``vseg`` (G+1 vertex offsets), ``offsets``,
 ``indices`` (local to each graph) and ``weights`` numpy arrays, the layout of
 ``pack_batch``.
@@ -16,6 +21,8 @@ any object with ``num_graphs``, ``vseg`` (G+1 vertex offsets), ``offsets``,
 from __future__ import annotations
 
 import heapq
+import itertools
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -107,3 +114,80 @@ def run_sharded(b, rank: int, world: int, mode: int = 0, group=None, **params):
         h.close()
     memb_all, q_all = gather_results(b.num_graphs, ids, np.diff(vseg), labels, q, world, group)
     return memb_all, q_all, ids, st
+
+
+class ServeRouter:
+    """Continuous batching on several GPUs of one process.
+
+    One server per device (``make_server(device)``, by default a
+    ``LeidenServer`` created on that device). A request goes to the device
+    with the least outstanding work -- the CSR entries of its requests not
+    yet returned by ``results`` -- ties to the earlier device, so that the
+    devices fill like the LPT dealing of a batch, but online: a request is
+    placed when it arrives. Every device has one host thread of its own,
+    bound to it by ``bind(device)`` (by default ``torch.cuda.set_device``),
+    and all calls to its server run there; ``step`` steps every server at
+    once, each in its thread (the library's calls release the interpreter
+    lock), and returns the number of graphs finished. Request ids are the
+    router's own; ``results`` drains every device, device by device, each in
+    its finishing order, as (id, membership, modularity, passes,
+    communities)."""
+
+    def __init__(self, devices, make_server=None, bind=None, **server_args):
+        self.devices = list(devices)
+        if not self.devices:
+            raise ValueError("ServeRouter needs at least one device")
+        if make_server is None:
+            from . import LeidenServer
+
+            def make_server(device):
+                return LeidenServer(**server_args)
+        if bind is None:
+            def bind(device):
+                import torch
+                torch.cuda.set_device(device)
+        self._pools = [ThreadPoolExecutor(max_workers=1, initializer=bind, initargs=(d,)) for d in self.devices]
+        self.servers = [self._on(k, make_server, d) for k, d in enumerate(self.devices)]
+        self.load = [0] * len(self.devices)  # outstanding CSR entries per device
+        self._ids = itertools.count()
+        self._route = {}  # (device index, server id) -> (router id, entries)
+
+    def _on(self, k, fn, *args):
+        return self._pools[k].submit(fn, *args).result()
+
+    def pick(self) -> int:
+        """Index of the device a request would go to now."""
+        return min(range(len(self.devices)), key=lambda k: (self.load[k], k))
+
+    def submit(self, offsets, indices, weights=None) -> int:
+        k = self.pick()
+        m = int(len(indices))
+        sid = self._on(k, self.servers[k].submit, offsets, indices, weights)
+        rid = next(self._ids)
+        self._route[(k, sid)] = (rid, m)
+        self.load[k] += m
+        return rid
+
+    def step(self) -> int:
+        futs = [pool.submit(srv.step) for pool, srv in zip(self._pools, self.servers)]
+        return sum(int(f.result()) for f in futs)
+
+    def results(self, device: bool = False):
+        out = []
+        for k, srv in enumerate(self.servers):
+            for sid, memb, q, passes, comm in self._on(k, srv.results, device):
+                rid, m = self._route.pop((k, sid))
+                self.load[k] -= m
+                out.append((rid, memb, q, passes, comm))
+        return out
+
+    def busy(self) -> bool:
+        """Requests submitted and not yet returned by ``results``."""
+        return bool(self._route)
+
+    def close(self):
+        for k, srv in enumerate(getattr(self, "servers", [])):
+            self._on(k, srv.close)
+        for pool in getattr(self, "_pools", []):
+            pool.shutdown()
+        self.servers, self._pools = [], []

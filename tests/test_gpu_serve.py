@@ -255,3 +255,37 @@ def test_serve_device_submissions_take_their_lanes():
             assert np.array_equal(res[rid][0], ms) and res[rid][1] == sts.passes
     finally:
         srv.close()
+
+
+def test_router_on_one_device_matches_the_oracle():
+    """The multi-device router (paper_2312_13936_gb300.shard.ServeRouter) on the
+    one GPU of the test: its server runs on the router's own thread for the
+    device, and every graph's deterministic result equals the oracle's SYNC
+    run, under the router's ids."""
+    import torch
+
+    from paper_2312_13936_gb300.shard import ServeRouter
+    graphs = serve_mix()[:10]
+    cap_v = max(1, sum(g.n for g in graphs))
+    cap_e = max(1, sum(g.nnz for g in graphs))
+    r = ServeRouter([torch.cuda.current_device()], max_vertices=cap_v, max_entries=cap_e,
+                    max_graphs=len(graphs) + 1, mode=lg.LEIDEN_DETERMINISTIC)
+    res = {}
+    try:
+        ids = []
+        for k, g in enumerate(graphs):
+            ids.append(r.submit(g.offsets, g.indices, g.weights))
+            if k % 3 == 2:
+                r.step()
+                res.update({rid: memb for rid, memb, *_ in r.results()})
+        steps = 0
+        while r.busy():
+            r.step()
+            res.update({rid: memb for rid, memb, *_ in r.results()})
+            steps += 1
+            assert steps < 1000
+    finally:
+        r.close()
+    assert ids == list(range(len(graphs)))
+    for rid, G in zip(ids, graphs):
+        assert np.array_equal(res[rid], oracle.leiden(G, mode=oracle.SYNC).membership), rid
