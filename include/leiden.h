@@ -90,7 +90,11 @@ typedef struct {
     double tolerance;             /* tau: initial per-iteration tolerance (Algorithm 2); default 0.01 */
     double aggregation_tolerance; /* tau_agg: stop when |Gamma|/|V'| exceeds it (Algorithm 1); default 0.8 */
     double tolerance_drop;        /* TOLERANCE_DROP: tau /= drop after each pass (Algorithm 1); default 10 */
-    int32_t max_iterations;       /* MAX_ITERATIONS per phase (Algorithm 2); default 20 */
+    int32_t max_iterations;       /* MAX_ITERATIONS per phase (Algorithm 2); default 20. The persistent
+                                     sweep's grid barrier counts arrivals in 32 bits, so a limit with
+                                     max_iterations * (8 steps + 4) * resident blocks > 2^32 - 1
+                                     (steps = layers - 1 + buckets) is LEIDEN_ERR_INVALID: on a GB300 (608
+                                     blocks) above 869 with the 1000-layer schedule, 18,589 with 32 */
     int32_t max_passes;           /* MAX_PASSES (Algorithm 1; not given in the paper); default 10 */
     int32_t mode;                 /* LEIDEN_ASYNC or LEIDEN_DETERMINISTIC */
     uint32_t flags;               /* LEIDEN_FLAG_* */

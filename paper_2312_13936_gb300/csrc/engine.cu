@@ -31,6 +31,28 @@ std::atomic<int64_t> detail::g_fail_alloc_after{-1};  // leiden_test_fail_alloca
 void set_last_error(const std::string &s) { g_last_error = s; }
 const char *last_error() { return g_last_error.c_str(); }
 
+// The persistent sweeps' grid barrier counts arrivals in 32 bits, from zero
+// at every launch. One phase takes at most max_iterations sweeps of at most
+// 8 barriers per schedule step (layout, insertion, three key passes, hub
+// flags, step end, apply) and 4 more per sweep, on at most the resident
+// grid; a limit under which that count could pass 2^32 - 1 is refused
+// rather than let the count wrap.
+leiden_status check_barrier_budget(int32_t max_iterations, int32_t nsteps, bool det, int sm) {
+    int per_sm = 0;
+    for (int w = 0; w < 2; ++w)
+        for (int r = 0; r < 2; ++r) {
+            const int b = sweep_coop_blocks_per_sm(det, w != 0, r != 0);
+            per_sm = b > per_sm ? b : per_sm;
+        }
+    const int64_t arrivals = (int64_t)max_iterations * (8 * (int64_t)nsteps + 4) * per_sm * sm;
+    if (arrivals > (int64_t)0xffffffffLL) {
+        set_last_error("max_iterations too large for this schedule: one phase could take more than 2^32 - 1 "
+                       "grid-barrier arrivals");
+        return LEIDEN_ERR_INVALID;
+    }
+    return LEIDEN_OK;
+}
+
 Handle::Handle() : p(new Impl) {}
 Handle::~Handle() { delete p; }
 
@@ -737,6 +759,7 @@ leiden_status Handle::run(const leiden_params &prm, int32_t *membership, int whe
         set_last_error("schedule_layers + schedule_buckets too large");
         return LEIDEN_ERR_INVALID;
     }
+    ST(check_barrier_budget(prm.max_iterations, nsteps, det, q.sm));
     if (det && (prm.flags & LEIDEN_FLAG_RANDOM_REFINE)) {
         set_last_error("the randomized refinement has no deterministic mode");
         return LEIDEN_ERR_UNSUPPORTED;

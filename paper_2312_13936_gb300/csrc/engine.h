@@ -101,5 +101,8 @@ leiden_status tuning_lookup(const char *path, const char *gpu, int64_t n, int64_
                             leiden_tuning &out);
 leiden_status modularity_device(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                 const int32_t *memb, double gamma, cudaStream_t s, double *q_out);
+// refuses an iteration limit under which one persistent phase of a schedule
+// of nsteps steps could count more grid-barrier arrivals than 32 bits hold
+leiden_status check_barrier_budget(int32_t max_iterations, int32_t nsteps, bool det, int sm);
 
 }  // namespace lgb

@@ -50,6 +50,7 @@ leiden_status Handle::server_init(const leiden_params &prm, int64_t max_vertices
     q.G = max_graphs;
     q.hvseg0 = {0, 0};
     ST(q.init_device());
+    ST(check_barrier_budget(prm.max_iterations, nkeys / kNumBins, prm.mode == LEIDEN_DETERMINISTIC, q.sm));
     ST(q.alloc_workspace(max_vertices, max_graphs));
     q.srv = new Serve;
     Serve &v = *q.srv;

@@ -62,3 +62,28 @@ def test_injected_allocation_failures_leave_the_library_usable():
     finally:
         lg.leiden_test_fail_allocation(-1)
     assert outcomes["create"] > 0 and outcomes["run"] > 0 and outcomes["ok"] > 0, outcomes
+
+
+def test_iteration_limit_beyond_the_barrier_count_is_refused():
+    """The persistent sweep's grid barrier counts arrivals in 32 bits: an
+    iteration limit under which one phase could count past that is refused
+    (LEIDEN_ERR_INVALID) before any work, by leiden_run and by
+    leiden_server_create, and the handle then runs normally."""
+    g = gen.road(60)
+    ref = oracle.leiden(g, mode=oracle.SYNC)
+    h = lg.Leiden(g.offsets, g.indices, g.weights)
+    try:
+        for mode in (lg.LEIDEN_ASYNC, lg.LEIDEN_DETERMINISTIC):
+            with pytest.raises(lg.LeidenError) as e:
+                h.run(mode=mode, max_iterations=2_000_000_000)
+            assert e.value.status == -1 and "barrier" in lg.leiden_last_error()
+            with pytest.raises(lg.LeidenError):
+                h.run(mode=mode, max_iterations=20_000, schedule_layers=1000)
+        memb, q, st = h.run(mode=lg.LEIDEN_DETERMINISTIC, max_iterations=200)  # well inside the count
+        assert np.array_equal(memb.cpu().numpy(), oracle.leiden(g, mode=oracle.SYNC, max_iterations=200).membership)
+        memb, q, st = h.run(mode=lg.LEIDEN_DETERMINISTIC)
+        assert np.array_equal(memb.cpu().numpy(), ref.membership)
+    finally:
+        h.close()
+    with pytest.raises(lg.LeidenError):
+        lg.LeidenServer(1000, 10000, mode=lg.LEIDEN_DETERMINISTIC, max_iterations=2_000_000_000)
