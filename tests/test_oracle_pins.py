@@ -277,6 +277,22 @@ def test_disconnected_counter():
     assert oracle.disconnected(g, np.array([0, 1, 0, 3, 4, 3]))[0] == 2
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_disconnected_counter_against_scipy(seed):
+    """Algorithm 5's count on random labellings (few labels, so that most
+    communities span several pieces; singletons; one label for all) equals
+    the count from scipy's connected components of the intra-community
+    subgraph, and a community is flagged exactly when it is counted."""
+    rng = np.random.default_rng(seed)
+    g = gen.gnp(400, 0.006 + 0.002 * seed, seed=seed + 11, wmax=3)
+    for labels in (rng.integers(0, 5 + 10 * seed, g.n), np.arange(g.n), np.zeros(g.n, dtype=np.int64),
+                   rng.integers(0, g.n, g.n)):
+        m = np.asarray(labels, dtype=np.int32)
+        k, flags = oracle.disconnected(g, m)
+        assert k == _components_inside(g, m)
+        assert int(np.count_nonzero(flags)) == k
+
+
 @pytest.mark.parametrize("mode", MODES)
 def test_every_community_connected(mode):
     graphs = [gen.sbm_workload(), gen.road(150), gen.rmat(12, 16), gen.gnp(300, 0.02, seed=5, wmax=4)]
