@@ -186,8 +186,17 @@ class ServeRouter:
         return bool(self._route)
 
     def close(self):
-        for k, srv in enumerate(getattr(self, "servers", [])):
-            self._on(k, srv.close)
-        for pool in getattr(self, "_pools", []):
-            pool.shutdown()
+        servers, pools = getattr(self, "servers", []), getattr(self, "_pools", [])
         self.servers, self._pools = [], []
+        try:
+            for pool, srv in zip(pools, servers):
+                pool.submit(srv.close).result()
+        finally:
+            for pool in pools:
+                pool.shutdown()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
