@@ -188,12 +188,18 @@ class ServeRouter:
     def close(self):
         servers, pools = getattr(self, "servers", []), getattr(self, "_pools", [])
         self.servers, self._pools = [], []
+        err = None
         try:
-            for pool, srv in zip(pools, servers):
-                pool.submit(srv.close).result()
+            for pool, srv in zip(pools, servers):  # every server, even after one fails
+                try:
+                    pool.submit(srv.close).result()
+                except Exception as e:
+                    err = err or e
         finally:
             for pool in pools:
                 pool.shutdown()
+        if err is not None:
+            raise err
 
     def __del__(self):
         try:

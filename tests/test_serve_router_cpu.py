@@ -154,3 +154,19 @@ def test_one_device_is_a_plain_server_and_no_device_is_refused():
         r.close()
     with pytest.raises(ValueError):
         ServeRouter([], make_server=make, bind=_bind)
+
+
+def test_close_shuts_every_device_thread_down_when_a_server_fails_to_close():
+    class Failing(OracleServer):
+        def close(self):
+            raise RuntimeError("close failed")
+
+    servers = {}
+    make = lambda d: servers.setdefault(d, (Failing if d == 0 else OracleServer)(d))  # noqa: E731
+    r = ServeRouter([0, 1], make_server=make, bind=_bind)
+    pools = list(r._pools)
+    with pytest.raises(RuntimeError):
+        r.close()
+    assert all(p._shutdown for p in pools) and r.servers == []
+    assert servers[1].closed  # the other device's server was closed all the same
+    r.close()  # a second close does nothing
