@@ -197,7 +197,7 @@ leiden_status leiden_destroy(leiden_graph_t g);
  * indices of graph g are LOCAL to it (in [0, n_g)): each graph's CSR is
  * appended unchanged but for the shift of its offsets. Other arguments and
  * checks as for leiden_create; a local index outside its graph returns
- * LEIDEN_ERR_INVALID. In deterministic mode the 2m < 2^31 rule holds per
+ * LEIDEN_ERR_INVALID. In deterministic mode the 2m < 2^53 rule holds per
  * graph. */
 leiden_status leiden_batch_create(leiden_graph_t *out, int32_t num_graphs, const int64_t *vtx_seg, int64_t nnz,
                                   const int64_t *offsets, const int32_t *indices, const float *weights, int32_t where,
@@ -397,7 +397,8 @@ leiden_status leiden_get_tuning(leiden_graph_t g, leiden_tuning *t);
  * {"format": 1, "entries": [{"gpu": <name>, "heavy_tailed": 0|1,
  * "log2_vertices": <int>, "log2_mean_degree": <int>, "thread_max_deg": ...,
  * "warp_max_deg": ..., "block_max_deg": ..., "coop_blocks_per_sm": ...,
- * "vertices_per_block": ..., other keys ignored}, ...]}. A graph of n
+ * "vertices_per_block": ..., "list_order_min_vertices": ... (optional),
+ * other keys ignored}, ...]}; a field an entry leaves out keeps its default. A graph of n
  * vertices, nnz CSR entries and largest degree max_degree has the class
  * (heavy_tailed = max_degree > 64 nnz / n, log2_vertices = round(log2 n),
  * log2_mean_degree = round(log2(nnz / n))); among the entries of gpu_name
