@@ -2,6 +2,7 @@
 reader and nearest-class selection), the defaults and range checks, the
 Python class function and the cache merge. No device work."""
 import json
+import os
 import math
 
 import pytest
@@ -119,3 +120,53 @@ def test_merge_cache_replaces_the_same_class(tmp_path):
     cache = tune.merge_cache(path, [_entry(0, 10, 3, vertices_per_block=4096)])
     light = [e for e in cache["entries"] if e["heavy_tailed"] == 0]
     assert len(cache["entries"]) == 2 and len(light) == 1 and light[0]["vertices_per_block"] == 4096
+
+
+_FUZZ = r'''
+import json, random, sys
+import paper_2312_13936_gb300 as lg
+path, out = sys.argv[1], sys.argv[2]
+base = open(lg.TUNING_CACHE).read()
+rng = random.Random(7)
+special = '{}[]",:0123456789.-+eE \\ntfu'
+taken = 0
+for k in range(400):
+    s = list(base)
+    for _ in range(rng.randint(1, 6)):
+        if not s:
+            break
+        i = rng.randrange(len(s))
+        op = rng.randrange(4)
+        if op == 0:
+            del s[i:i + rng.randint(1, 40)]
+        elif op == 1:
+            s[i:i] = s[i:i + rng.randint(1, 40)]
+        elif op == 2:
+            s[i] = rng.choice(special)
+        else:
+            s = s[:i]
+    text = ''.join(s) if k % 50 else '[' * 100000 + ']' * 100000
+    open(out, 'w').write(text)
+    t = lg.leiden_tuning_lookup(out, 'NVIDIA GB300', 25_000_000, 90_981_444, 8)
+    if t is not None:
+        taken += 1
+        d = t.as_dict()
+        assert 1 <= d['thread_max_deg'] <= 8 and d['warp_max_deg'] <= d['block_max_deg'], d
+print('ok', taken)
+'''
+
+
+def test_lookup_survives_mutated_caches(tmp_path):
+    """The cache reader (host C++) on 400 random mutations of the shipped
+    cache -- spans deleted, repeated or truncated, bytes replaced by JSON
+    punctuation, and nesting 100,000 deep -- returns an entry within the
+    valid ranges or refuses the file; it never crashes the process (run in a
+    subprocess so a crash fails the test)."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "fuzz.py"
+    script.write_text(_FUZZ)
+    r = subprocess.run([sys.executable, str(script), lg.TUNING_CACHE, str(tmp_path / "m.json")], cwd=root,
+                       capture_output=True, text=True, timeout=300, env=dict(os.environ, PYTHONPATH=root))
+    assert r.returncode == 0 and r.stdout.startswith("ok"), (r.returncode, r.stdout[-500:], r.stderr[-2000:])
