@@ -72,7 +72,7 @@ enum {
     LEIDEN_FLAG_LOUVAIN = 128u,           /* the Louvain method of the paper's comparison (Section 5):
                                              no refinement phase; each pass aggregates its local-moving
                                              communities, which need not be connected */
-    LEIDEN_FLAG_RANDOM_REFINE = 256u,     /* asynchronous mode: randomized refinement (Sections 2.2, 4.1):
+    LEIDEN_FLAG_RANDOM_REFINE = 256u,     /* asynchronous mode: randomized refinement (Sections 3.4, 4.1):
                                              an isolated vertex joins a community of positive gain within
                                              its bound with probability proportional to the gain, drawn
                                              from the seed, pass, sweep, vertex and community; the

@@ -27,7 +27,7 @@ REFINE_SINGLE_SWEEP = 1
 NO_PRUNE = 2  # SEQ local-moving visits every vertex in every sweep (tests only)
 REFINE_LABELS = 4  # refine-based super-vertex labels (Section 4.1)
 LOUVAIN = 8  # no refinement: the Louvain method of the paper's comparison (Section 5)
-RANDOM_REFINE = 16  # randomized refinement (Sections 2.2, 4.1), SEQ mode only
+RANDOM_REFINE = 16  # randomized refinement (Sections 3.4, 4.1), SEQ mode only
 
 T_INIT_LABELS, T_MOVE, T_REFINE, T_COUNTS, T_RENUMBER = 1, 2, 3, 4, 5
 T_AGG_OFF, T_AGG_DEG, T_AGG_IDX, T_AGG_W, T_DENDRO = 6, 7, 8, 9, 10

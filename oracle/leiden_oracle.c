@@ -119,7 +119,7 @@
  *       merges the local-moving communities. Communities need not be
  *       connected.
  *   V3  OG_RANDOM_REFINE (SEQ mode only): the randomized refinement of the
- *       original Leiden method (Sections 2.2 and 4.1): an isolated vertex
+ *       original Leiden method (Sections 3.4 and 4.1): an isolated vertex
  *       joins one of the communities of positive gain within its bound with
  *       probability proportional to the gain, instead of the best one. The
  *       draw: the candidates in ascending community id, u = ((x >> 11) +

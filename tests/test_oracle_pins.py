@@ -484,7 +484,7 @@ def test_louvain_first_pass_is_the_local_moving_phase(mode):
 
 
 def test_louvain_can_leave_a_community_disconnected():
-    """The shortcoming the refinement phase removes (Sections 2.2-2.3): on this
+    """The shortcoming the refinement phase removes (Sections 3.3-3.4): on this
     graph the Louvain variant returns an internally disconnected community,
     while the Leiden method (either label rule) returns connected ones."""
     g = gen.gnp(18, 0.25, seed=2108, wmax=3)
