@@ -131,7 +131,9 @@ class ServeRouter:
     lock), and returns the number of graphs finished. Request ids are the
     router's own; ``results`` drains every device, device by device, each in
     its finishing order, as (id, membership, modularity, passes,
-    communities)."""
+    communities), the membership a numpy array, or with ``device=True`` a
+    tensor on the GPU that ran the graph. ``close`` releases every server and
+    thread."""
 
     def __init__(self, devices, make_server=None, bind=None, **server_args):
         self.devices = list(devices)
